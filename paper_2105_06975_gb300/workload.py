@@ -1,0 +1,151 @@
+"""Seeded synthetic inputs for the weak-constraint 4D-Var saddle-point workloads.
+
+This module holds the workload definitions (sizes, covariance parameters,
+model coefficients) and the seeded random draws both the CUDA library and
+the FP64 oracle consume.  It contains none of the method's arithmetic: no
+covariance matrix, no model operator, no preconditioner.  Everything that
+turns these draws into a saddle-point problem is done separately by each side.
+
+Workloads (all synthetic; the paper's own datasets and Lorenz-96 code are not
+available, so these stand in for its experiments with the shapes below):
+
+* ``tiny``  -- 1D periodic advection-diffusion, s=100, N=10, p=50 (every 2nd
+  point), SOAR B/Q/R, block-diagonal preconditioner with exact D, R and Schur
+  complement, MINRES.  n = (2s+p)(N+1) = 2750.
+* ``scale`` -- the same covariances at s=2048, N=64, p=1024 observed points
+  drawn without replacement and sorted.  n = 332,800.
+* ``l96``   -- Lorenz-96, s=1000, F=8, RK4 dt=0.025 with 5 steps per
+  observation time, N=50, every 2nd variable observed, 3 Gauss-Newton loops.
+
+Seeds: master seed m in {0, 1, 2}; window w of a batch uses m*1000 + w.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+MODEL_STENCIL3 = 0
+MODEL_BANDED = 1
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    s: int
+    N: int
+    p: int
+    # observation pattern: "even" (every 2nd grid point) or "random" (sorted
+    # draw without replacement, shared by all times, Sec. 6.1)
+    obs: str
+    # model: "advdiff" (periodic 3-point stencil) or "l96"
+    model: str
+    # SOAR (variance, length as a fraction of the periodic unit domain)
+    soar_b: tuple
+    soar_q: tuple
+    soar_r: tuple
+    # advection-diffusion: upwind Courant number c and diffusion number d give
+    # x'_j = (c+d) x_{j-1} + (1-c-2d) x_j + d x_{j+1}
+    courant: float = 0.5
+    diffusion: float = 0.2
+    # Lorenz-96
+    forcing: float = 8.0
+    dt: float = 0.025
+    steps_per_obs: int = 5
+    spinup_steps: int = 2000
+    outer_loops: int = 1
+    # synthetic truth for the linear model: Gaussian bump of this width
+    bump_width: float = 0.05
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+    @property
+    def n(self) -> int:
+        return (2 * self.s + self.p) * (self.N + 1)
+
+    def stencil(self) -> tuple:
+        c, d = self.courant, self.diffusion
+        return (c + d, 1.0 - c - 2.0 * d, d)
+
+
+TINY = Workload(name="tiny", s=100, N=10, p=50, obs="even", model="advdiff",
+                soar_b=(1.0, 0.1), soar_q=(0.05, 0.05), soar_r=(0.1, 0.05))
+
+SCALE = Workload(name="scale", s=2048, N=64, p=1024, obs="random", model="advdiff",
+                 soar_b=(1.0, 0.1), soar_q=(0.05, 0.05), soar_r=(0.1, 0.05))
+
+L96 = Workload(name="l96", s=1000, N=50, p=500, obs="even", model="l96",
+               soar_b=(1.0, 5.0 / 1000), soar_q=(0.1, 5.0 / 1000),
+               soar_r=(0.5, 4.0 / 1000), outer_loops=3)
+
+WORKLOADS = {w.name: w for w in (TINY, SCALE, L96)}
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+@dataclass
+class Draws:
+    """Raw seeded draws for one assimilation window (no method arithmetic)."""
+    obs_idx: np.ndarray            # int32 [p], sorted, distinct, in [0, s)
+    bump_center: float             # truth bump centre in [0, 1)
+    z_b: np.ndarray                # [s]        standard normal (background error)
+    z_q: np.ndarray                # [N, s]     standard normal (model error)
+    z_r: np.ndarray                # [N+1, p]   standard normal (observation error)
+    x0_pert: np.ndarray            # [s]        standard normal (Lorenz-96 initial state)
+    rhs_probe: np.ndarray          # [n]        standard normal (generic right-hand side)
+    extra: dict = field(default_factory=dict)
+
+
+def observed_indices(w: Workload, g: np.random.Generator) -> np.ndarray:
+    if w.obs == "even":
+        step = w.s // w.p
+        idx = np.arange(w.p, dtype=np.int64) * step
+    elif w.obs == "random":
+        idx = np.sort(g.choice(w.s, size=w.p, replace=False))
+    else:
+        raise ValueError(w.obs)
+    return idx.astype(np.int32)
+
+
+def draws(w: Workload, seed: int = 0) -> Draws:
+    g = rng(seed)
+    obs_idx = observed_indices(w, g)
+    center = float(g.random())
+    z_b = g.standard_normal(w.s)
+    z_q = g.standard_normal((w.N, w.s))
+    z_r = g.standard_normal((w.N + 1, w.p))
+    x0_pert = g.standard_normal(w.s)
+    rhs_probe = g.standard_normal(w.n)
+    return Draws(obs_idx=obs_idx, bump_center=center, z_b=z_b, z_q=z_q, z_r=z_r,
+                 x0_pert=x0_pert, rhs_probe=rhs_probe)
+
+
+def bump(w: Workload, center: float) -> np.ndarray:
+    """Synthetic truth initial state for the linear workloads: a unit Gaussian
+    bump of width ``w.bump_width`` centred at ``center`` on the periodic unit
+    domain, sampled at x_j = j/s."""
+    x = np.arange(w.s) / w.s
+    d = np.abs(x - center)
+    d = np.minimum(d, 1.0 - d)
+    return np.exp(-0.5 * (d / w.bump_width) ** 2)
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    return rng(seed).standard_normal(n)
+
+
+def small(w: Workload, s: int, N: int, p: Optional[int] = None, **kw) -> Workload:
+    """A reduced copy of a workload (same covariance lengths as fractions of
+    the domain) for tests the oracle finishes in seconds."""
+    p = p if p is not None else max(1, (s * w.p) // w.s)
+    if w.model == "l96":
+        # Lorenz-96 lengths are fixed in grid points, not domain fractions
+        f = w.s / s
+        kw.setdefault("soar_b", (w.soar_b[0], w.soar_b[1] * f))
+        kw.setdefault("soar_q", (w.soar_q[0], w.soar_q[1] * f))
+        kw.setdefault("soar_r", (w.soar_r[0], w.soar_r[1] * f))
+    return w.with_(s=s, N=N, p=p, **kw)
