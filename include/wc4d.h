@@ -1,0 +1,223 @@
+/*
+ * wc4d -- weak-constraint 4D-Var saddle-point solver, C ABI.
+ *
+ * Tabeart & Pearson, "Saddle point preconditioners for weak-constraint
+ * 4D-Var".  The library solves the inner-loop saddle-point system
+ * (Sec. 2.1, Eq. saddlepointsystem)
+ *
+ *     [ D   0   L ] [d_eta]   [b]
+ *     [ 0   R   H ] [d_nu ] = [d]          A = Eq. saddlepointA
+ *     [ L^T H^T 0 ] [d_x  ]   [0]
+ *
+ * with D = blkdiag(B, Q_1..Q_N), R = blkdiag(R_0..R_N), H = blkdiag(H_i),
+ * L block lower bidiagonal with I on the diagonal and -M_i below it
+ * (Eq. def:L), preconditioned by the block-diagonal P_D or the inexact
+ * constraint P_I (Eq. prec) built from Lhat = L_M(k) (Definition 1) and a
+ * reconditioned Rhat (Sec. 5, Alg. 1 and 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Vectors of length n = (2s+p)(N+1) are time-major FP64:
+ *       [eta_0..eta_N (each s) | nu_0..nu_N (each p) | x_0..x_N (each s)],
+ *   each block contiguous, so block k of a part is the column k of an
+ *   s x (N+1) (or p x (N+1)) column-major matrix.
+ * - Q_i = Q and R_i = R for every time level and H_i selects the same sorted
+ *   observed grid points at every time (Sec. 6.1).
+ * - Dense matrices are column-major, symmetric, FP64.
+ * - "device" pointers are CUDA global-memory addresses on the current
+ *   device (e.g. torch tensor data_ptr()); "host" pointers are ordinary CPU
+ *   memory.  The library never takes ownership of caller memory; everything
+ *   it needs is copied into library-owned device buffers at setup.
+ * - All work is ordered on the CUDA stream given at setup.  Calls return
+ *   after the work is enqueued, except where stated (solve: returns after
+ *   the solution is final, because the convergence test reads a device flag).
+ * - Every call returns a status code (WC4D_OK = 0 on success).  No C++
+ *   exception crosses the ABI.  The message of the last failure on the
+ *   calling thread is returned by wc4d_last_error().
+ * - A problem handle must not be used from two host threads at once.
+ */
+#ifndef WC4D_H
+#define WC4D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  WC4D_OK = 0,
+  WC4D_ERR_ARG = 1,        /* invalid argument or size                         */
+  WC4D_ERR_NOT_SPD = 2,    /* Cholesky met a non-positive pivot                */
+  WC4D_ERR_NONFINITE = 3,  /* NaN/Inf in inputs or Krylov scalars              */
+  WC4D_ERR_BREAKDOWN = 4,  /* Lanczos/Arnoldi breakdown before convergence     */
+  WC4D_ERR_MAXIT = 5,      /* tolerance not reached within maxit iterations    */
+  WC4D_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                    */
+  WC4D_ERR_CUDA = 7,       /* CUDA runtime error                               */
+  WC4D_ERR_NOMEM = 8       /* device allocation failed                         */
+};
+
+/* model operator M_i (Eq. def:L) */
+enum {
+  WC4D_MODEL_STENCIL3 = 0, /* (M x)_j = c0 x_{j-1} + c1 x_j + c2 x_{j+1}, periodic, same for all i */
+  WC4D_MODEL_BANDED = 1    /* per-time banded M_i, offsets -band_lo..band_hi, periodic wrap        */
+};
+/* covariance source */
+enum {
+  WC4D_COV_DENSE = 0,      /* caller passes dense B (s x s), Q (s x s), R (p x p)                   */
+  WC4D_COV_SOAR = 1        /* library builds SOAR matrices on the device (Sec. 6.1, Eq. SOAR):
+                              c(r) = sigma2 (1 + r/ell) exp(-r/ell), r = chordal distance between
+                              points x_j = j/s of the periodic unit domain, r = sin(pi |dx|)/pi;
+                              R uses the observed points x = obs_idx/s                              */
+};
+enum { WC4D_MEM_HOST = 0, WC4D_MEM_DEVICE = 1 };
+
+enum { WC4D_PRECOND_PD = 0, WC4D_PRECOND_PI = 1 };          /* Eq. prec                     */
+enum { WC4D_RHAT_EXACT = 0, WC4D_RHAT_RR = 1,               /* Rhat = R; Alg. 1 ridge       */
+       WC4D_RHAT_ME = 2, WC4D_RHAT_DIAG = 3 };              /* Alg. 2 min-eig; Sec. 5.1     */
+enum { WC4D_SHAT_PAPER = 0, WC4D_SHAT_EXACT = 1 };          /* Lhat^T D^-1 Lhat ; S (Sec 2.2) */
+enum { WC4D_DHAT_EXACT = 0, WC4D_DHAT_SHIFT = 1 };          /* D ; D + delta I (Sec. 6.1)   */
+enum { WC4D_KRYLOV_MINRES = 0, WC4D_KRYLOV_GMRES = 1, WC4D_KRYLOV_FGMRES = 2 };
+enum { WC4D_PREC_FP64 = 0,        /* every product in FP64                                   */
+       WC4D_PREC_MIXED = 1 };     /* FGMRES(FP64 A) outer, FP32 inner GMRES preconditioned by
+                                     an FP32 copy of the chosen preconditioner (not in the paper) */
+
+typedef struct {
+  int32_t s;                 /* state size per time level, >= 2                         */
+  int32_t N;                 /* number of subwindows; N+1 time levels, >= 0             */
+  int32_t p;                 /* observations per time level, 1 <= p <= s                */
+  int32_t model_kind;        /* WC4D_MODEL_*                                            */
+  double stencil[3];         /* STENCIL3 coefficients (c0, c1, c2)                      */
+  int32_t band_lo, band_hi;  /* BANDED: offsets; band_lo + band_hi + 1 <= s             */
+  const double* bands;       /* BANDED: [N][s][band_lo+band_hi+1],
+                                bands[i-1][j][o+band_lo] = (M_i)[j][(j+o) mod s]        */
+  const int32_t* obs_idx;    /* [p] strictly increasing indices in [0, s)               */
+  int32_t cov_kind;          /* WC4D_COV_*                                              */
+  const double* B;           /* DENSE: s x s                                            */
+  const double* Q;           /* DENSE: s x s                                            */
+  const double* R;           /* DENSE: p x p                                            */
+  double soar_b[2];          /* SOAR: (sigma2, ell) of B, ell as a fraction of the domain */
+  double soar_q[2];          /* SOAR: (sigma2, ell) of Q                                */
+  double soar_r[2];          /* SOAR: (sigma2, ell) of R                                */
+  int32_t mem_kind;          /* where bands/obs_idx/B/Q/R live: WC4D_MEM_HOST|DEVICE    */
+} wc4d_problem_desc;
+
+typedef struct {
+  int32_t precond;           /* WC4D_PRECOND_PD (MINRES) or WC4D_PRECOND_PI (GMRES)        */
+  int32_t k;                 /* Lhat = L_M(k), 1 <= k <= N+1; 1 gives L_0 = I, N+1 gives L */
+  int32_t rhat;              /* WC4D_RHAT_*                                                 */
+  double kappa_max;          /* Alg. 1 / Alg. 2 target condition number (> 1)               */
+  int32_t shat;              /* WC4D_SHAT_*; EXACT needs s(N+1) <= 8192                     */
+  int32_t dhat;              /* WC4D_DHAT_*                                                 */
+  double dhat_delta;         /* SHIFT: Dhat = D + delta I                                   */
+  int32_t krylov;            /* WC4D_KRYLOV_*                                               */
+  double tol;                /* relative residual in the 2-norm (1e-6 in Sec. 7)            */
+  int32_t maxit;             /* outer iteration cap (1000 in Sec. 7)                        */
+  int32_t precision;         /* WC4D_PREC_*                                                 */
+  int32_t inner_iters;       /* MIXED: inner GMRES steps per outer FGMRES step              */
+  int32_t check_every;       /* host polls the device convergence flag every this many steps */
+} wc4d_solve_opts;
+
+typedef struct {
+  int32_t status;            /* WC4D_OK or the failure code                              */
+  int32_t iters;             /* outer Krylov iterations                                  */
+  int32_t inner_iters;       /* MIXED: total inner iterations                            */
+  double relres_true;        /* ||rhs - A x||_2 / ||rhs||_2 recomputed in FP64 at exit   */
+  double relres_est;         /* recurrence estimate at exit                              */
+  double ms;                 /* wall time of the solve call                              */
+  int64_t n_apply_A;         /* FP64 applications of A                                   */
+  int64_t n_apply_P;         /* applications of the preconditioner (any precision)      */
+} wc4d_info;
+
+typedef struct wc4d_problem wc4d_problem;   /* opaque, library-owned */
+
+/* Fill opts with the defaults of Sec. 7: P_I + GMRES, k = 1, Rhat = R,
+ * kappa_max = 100, paper Shat, exact Dhat, tol 1e-6, maxit 1000, FP64. */
+void wc4d_default_opts(wc4d_solve_opts* opts);
+
+/* Build a problem: copy/generate B, Q, R, M_i and H on the device, build
+ * Rhat (Alg. 1/2 or Sec. 5.1), factor Dhat, Rhat (and S when requested) with
+ * FP64 Cholesky, invert the triangular factors, and allocate the Krylov
+ * workspace for opts->maxit iterations.  cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream).  On success *out owns all device memory it uses;
+ * release it with wc4d_destroy.  Errors: ARG (sizes, indices, options),
+ * NOT_SPD (Cholesky of Dhat/Rhat/S failed), NONFINITE, NOMEM, CUDA.
+ * Synchronises the stream before returning. */
+int wc4d_setup_problem(const wc4d_problem_desc* desc, const wc4d_solve_opts* opts,
+                       void* cuda_stream, wc4d_problem** out);
+
+/* out = A v (Sec. 6.2: c1 = D v1 + L v3, c2 = R v2 + H v3, c3 = L^T v1 + H^T v2).
+ * v, out: device, n doubles each, must not overlap.  Stream-ordered, async. */
+int wc4d_apply_saddle(wc4d_problem* prob, const double* v, double* out);
+
+/* out = P^{-1} v for which = WC4D_PRECOND_PD (Dhat^{-1} v1, Rhat^{-1} v2,
+ * Lhat^{-1} D Lhat^{-T} v3, Sec. 6.2) or WC4D_PRECOND_PI (c1 = Lhat^{-T} v3,
+ * c2 = Rhat^{-1} v2, c3 = Lhat^{-1}(v1 - D c1)).  P_D needs a problem set up
+ * with opts->precond = PD (its Dhat factors); P_I is always available.
+ * v, out: device, n doubles each, must not overlap.  Stream-ordered, async. */
+int wc4d_apply_precond(wc4d_problem* prob, int32_t which, const double* v, double* out);
+
+/* Solve A x = rhs with the Krylov method and preconditioner chosen at setup
+ * (Sec. 6.2 / 7): MINRES for P_D, GMRES without restarts for P_I, FGMRES for
+ * the mixed-precision mode.  rhs and x are FP64 vectors of length n, both on
+ * the device (mem_kind = WC4D_MEM_DEVICE) or both on the host (HOST: copied
+ * in and out through the problem's buffers).  x is the initial guess when
+ * use_x0 != 0, otherwise it is ignored on input.  Blocks until the solution
+ * is written.  info (may be NULL) receives iteration counts, residuals and
+ * timings.  Returns MAXIT if the tolerance was not reached (x then holds the
+ * last iterate), BREAKDOWN, NONFINITE or CUDA on failure. */
+int wc4d_solve(wc4d_problem* prob, const double* rhs, double* x, int32_t use_x0,
+               int32_t mem_kind, wc4d_info* info);
+
+/* Synthetic right-hand side (b, d, 0) of the first outer loop for a
+ * STENCIL3 (linear) model, built on the device from standard-normal draws.
+ * Follows the data-assimilation setting of Sec. 1 / Sec. 2.1: background
+ * x_b = x_0^t + chol(B) z_b, truth x_i^t = M x_{i-1}^t (perfect model),
+ * observations y_i = H x_i^t + chol(R) z_i, and the first linearisation
+ * trajectory is the background forecast x^(0)_i = M x^(0)_{i-1}, x^(0)_0 = x_b.
+ * Then b = 0 and d_i = y_i - H x^(0)_i = -H M^i chol(B) z_b + chol(R) z_i
+ * (the truth cancels for a linear model, so it is not an argument).
+ * z_b: s doubles; z_r: (N+1) p doubles, time-major; rhs: n doubles out.  All
+ * three on the host or all on the device per mem_kind.  Uses the problem's
+ * B and R (not Rhat).  Synchronises the stream.  Errors: ARG (banded model),
+ * NOT_SPD, NOMEM, CUDA. */
+int wc4d_synthesize_rhs(wc4d_problem* prob, const double* z_b, const double* z_r, int32_t mem_kind, double* rhs);
+
+/* Problem sizes: n (vector length), s, N, p. */
+int wc4d_problem_dims(const wc4d_problem* prob, int64_t* n, int32_t* s, int32_t* N, int32_t* p);
+
+/* Copy a library-built covariance (which = 0: B, 1: Q, 2: R, 3: Rhat) into
+ * dst (device, col-major, s*s or p*p doubles).  For tests and diagnostics. */
+int wc4d_get_matrix(wc4d_problem* prob, int32_t which, double* dst);
+
+/* Rhat parameter used at setup: gamma (Alg. 1) or T (Alg. 2); 0 otherwise. */
+double wc4d_rhat_param(const wc4d_problem* prob);
+
+/* Process-wide counters for measurement (no counterpart in the paper).
+ * launches: kernels the library launched since the last reset.  With
+ * profiling enabled the library also brackets every launch of its two
+ * dominant kernel classes with CUDA events on the launching stream: the
+ * stream-K covariance GEMM (work = algorithmic FLOPs: 2 x multiply-adds over
+ * the non-zero triangle) and the Arnoldi orthogonalisation passes (work =
+ * bytes the pass must read and write); launches that exit early on a solve
+ * that has already converged are not counted.  wc4d_get_stats synchronises
+ * the device.  Not thread-safe across concurrent solves. */
+typedef struct {
+  int64_t launches;
+  double gemm_ms, gemm_flops;
+  int64_t gemm_launches;
+  double orth_ms, orth_bytes;
+  int64_t orth_launches;
+} wc4d_stats;
+void wc4d_set_profiling(int32_t enable);
+void wc4d_reset_stats(void);
+int wc4d_get_stats(wc4d_stats* out);
+
+void wc4d_destroy(wc4d_problem* prob);
+const char* wc4d_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WC4D_H */

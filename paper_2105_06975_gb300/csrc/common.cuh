@@ -1,0 +1,181 @@
+// Internal declarations shared by the wc4d translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "wc4d.h"
+
+namespace wc4d {
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void set_error(const std::string& msg);
+#define WC4D_CUDA(call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      throw ::wc4d::Error{WC4D_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+// every kernel launch of the library is followed by this: it counts the
+// launch (wc4d_get_stats) and turns a launch error into an exception
+void note_launch();
+#define WC4D_LAUNCH_CHECK()                \
+  do {                                     \
+    ::wc4d::note_launch();                 \
+    WC4D_CUDA(cudaGetLastError());         \
+  } while (0)
+#define WC4D_CHECK(cond, code, msg)                        \
+  do {                                                     \
+    if (!(cond)) throw ::wc4d::Error{(code), (msg)};       \
+  } while (0)
+
+// ------------------------------------------------------------ model on device
+// M_t for t = 1..N (maps time t-1 to t).  STENCIL3: same 3-point periodic
+// stencil for all t.  BANDED: bands[(t-1)*s*w + j*w + (o+lo)] = M_t[j][(j+o) mod s].
+struct ModelDev {
+  int kind;
+  int s, N;
+  double c0, c1, c2;
+  const double* bands;
+  int lo, hi;
+};
+
+// ------------------------------------------------------- stream-K FP64 GEMM
+// One operand product C = op(At) * X with op(v)_i = sum_k At[k + i*lda] v_k
+// (the "TN" form: the k index is contiguous in both operands).  Symmetric
+// covariances are their own At; a lower-triangular factor W is applied through
+// its stored transpose and vice versa.
+constexpr int GEMM_BM = 64;
+constexpr int GEMM_BN = 64;
+constexpr int GEMM_BK = 16;
+constexpr int GEMM_MAX_OPS = 4;
+
+enum { TRI_FULL = 0, TRI_LOWER = 1, TRI_UPPER = 2 };  // op(At) lower: k <= i; upper: k >= i
+
+template <typename T>
+struct GemmOpT {
+  const T* At;
+  int64_t lda;
+  const T* X;
+  int64_t ldx;
+  int m, kdim, ncols, tri;
+};
+template <typename T>
+struct GemmOpsT {
+  GemmOpT<T> op[GEMM_MAX_OPS];
+  int nops;
+};
+using GemmOp = GemmOpT<double>;
+using GemmOps = GemmOpsT<double>;
+
+struct GemmSeg {
+  int op, row0, col0, k0, k1, slot, colw;
+};
+
+// Epilogue of the split-K reduction, per op.
+enum {
+  EPI_STORE = 0,      // C = acc
+  EPI_SADDLE_C1 = 1,  // C = acc + (L v3) at time t = col + t0
+  EPI_SADDLE_C2 = 2,  // C = acc + v3_t[obs[r]]
+  EPI_SUB_FROM = 3,   // C = Y - acc
+  EPI_NEG_STORE = 4   // C = -acc
+};
+template <typename T>
+struct EpiT {
+  int mode;
+  T* C;
+  int64_t ldc;
+  int t0;          // time index of output column 0
+  const T* v3;     // EPI_SADDLE_*: x part of the input vector (time-major, s per time)
+  const T* Y;      // EPI_SUB_FROM: minuend, same layout as C
+};
+template <typename T>
+struct EpisT {
+  EpiT<T> e[GEMM_MAX_OPS];
+};
+using Epi = EpiT<double>;
+using Epis = EpisT<double>;
+
+struct OpShape {
+  int m, kdim, ncols, tri;
+};
+
+// Static schedule for one set of op shapes: CTA c processes segments
+// [seg_start[c], seg_start[c+1]); every segment writes one partial tile slot;
+// the reduction sums the slots of each output tile in k order.
+struct GemmPlan {
+  int nops = 0;
+  OpShape shape[GEMM_MAX_OPS];
+  int nctas = 0;
+  int nslots = 0;
+  int* d_seg_start = nullptr;
+  GemmSeg* d_segs = nullptr;
+  int ntiles = 0;
+  int tile_base[GEMM_MAX_OPS];
+  int col_tiles[GEMM_MAX_OPS];
+  int col_width[GEMM_MAX_OPS];
+  int* d_tile_start = nullptr;
+  int* d_tile_slots = nullptr;
+  int64_t total_out = 0;          // sum over ops of m * ncols
+  int64_t out_base[GEMM_MAX_OPS];  // prefix of m * ncols
+  double flops = 0;               // 2 * useful multiply-adds
+};
+
+void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas);
+// persistent CTAs for the stream-K GEMM: SMs x resident CTAs per SM
+int gemm_resident_ctas();
+
+// Opt-in kernel profile: CUDA events around the timed kernel classes on the
+// launching stream; the kernel itself marks whether it did work (launches that
+// exit early on a converged solve do not count).
+enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_CLASSES = 2 };
+bool prof_enabled();
+// returns a device int* the kernel sets to 1 when it runs (nullptr when off)
+int* prof_begin(int cls, double work, cudaStream_t st);
+void prof_end(cudaStream_t st);
+void plan_free(GemmPlan& plan);
+
+template <typename T>
+void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis, T* partial,
+              const ModelDev& model, const int* obs, const int* done, cudaStream_t st);
+
+// ---------------------------------------------------------------- kernels
+void launch_soar_fill(double* M, int m, const int* idx, int s, double sigma2, double ell, cudaStream_t st);
+void launch_copy_d(double* dst, const double* src, int64_t n, cudaStream_t st);
+void launch_fill_d(double* dst, double v, int64_t n, cudaStream_t st);
+void launch_add_diag(double* A, int m, int64_t lda, const double* shift_dev, double shift, cudaStream_t st);
+void launch_keep_diag(double* A, int m, cudaStream_t st);
+void launch_transpose(const double* A, double* At, int m, cudaStream_t st);
+void launch_symmetrize(double* A, int m, cudaStream_t st);
+void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t st);
+void launch_inv_map(const int* obs, int p, int* inv, int s, cudaStream_t st);
+void launch_check_obs(const int* obs, int p, int s, int* flag, cudaStream_t st);
+void launch_check_finite(const double* a, int64_t n, int* flag, cudaStream_t st);
+
+// Cholesky A = L L^T in place (lower), A is m x m col-major; *info = first bad pivot (1-based) or 0.
+void cholesky(double* A, int m, int* info, cudaStream_t st, double* scratch);
+// W = L^{-1} for lower-triangular L (m x m); Wt = W^T. scratch >= m*64 doubles.
+void tri_inverse(const double* L, double* W, double* Wt, int m, cudaStream_t st, double* scratch);
+// Symmetric eigen-decomposition by cyclic Jacobi: A (m x m, overwritten by a
+// near-diagonal matrix), V eigenvectors (columns).  m even; returns sweeps used.
+int jacobi_eigh(double* A, double* V, int m, cudaStream_t st, double* rot, int* d_count, int max_sweeps);
+// Rhat builders on device (lam: diag of the Jacobi result)
+void launch_rr_shift(const double* Adiag_src, int m, double kappa, double* gamma_out, cudaStream_t st);
+void launch_me_scale(const double* Ajac, const double* V, int m, double kappa, double* U, double* T_out,
+                     cudaStream_t st);
+
+// Model / time operators
+void launch_lhat_sweep(const ModelDev& md, int k, const double* v, double* z, bool transpose, bool identity_model,
+                       const int* done, cudaStream_t st);
+void launch_saddle_c3(const ModelDev& md, const double* v1, const double* v2, const int* inv, int p, double* c3,
+                      const int* done, cudaStream_t st);
+
+}  // namespace wc4d

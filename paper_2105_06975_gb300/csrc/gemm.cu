@@ -1,0 +1,357 @@
+// Stream-K batched GEMM for the multi-right-hand-side covariance products.
+//
+// Every covariance product of the method is C = Sigma * V with V the s x (N+1)
+// (or p x (N+1)) time-block matrix of a Krylov vector: the D pass and R pass of
+// A v (Sec. 6.2), the Dhat^{-1} / Rhat^{-1} solves (applied as products with
+// the inverse Cholesky factors) and the D pass inside Shat^{-1} and P_I^{-1}.
+// Several independent products of one dependency level go into one launch.
+// The work (tiles x k-blocks, weighted by their multiply-adds) is cut into
+// exactly equal contiguous ranges, one per persistent CTA, so every SM gets the
+// same share of FP64 work; partial tiles are summed in a fixed order by the
+// reduction, which also applies the fused epilogue (the L v3 / H v3 terms of
+// A v, the v1 - D c1 of P_I).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "model_dev.cuh"
+
+namespace wc4d {
+
+// --------------------------------------------------------------- planning
+void plan_free(GemmPlan& plan) {
+  cudaFree(plan.d_seg_start);
+  cudaFree(plan.d_segs);
+  cudaFree(plan.d_tile_start);
+  cudaFree(plan.d_tile_slots);
+  plan = GemmPlan();
+}
+
+void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas) {
+  plan_free(plan);
+  WC4D_CHECK((int)shapes.size() <= GEMM_MAX_OPS, WC4D_ERR_ARG, "too many GEMM ops in one launch");
+  plan.nops = (int)shapes.size();
+  struct Tile {
+    int op, row0, col0, kb0, kb1;
+    double cost_per_kb;
+  };
+  std::vector<Tile> tiles;
+  int64_t outpos = 0;
+  double flops = 0;
+  for (int o = 0; o < plan.nops; ++o) {
+    const OpShape& sh = shapes[o];
+    plan.shape[o] = sh;
+    const int rt = (sh.m + GEMM_BM - 1) / GEMM_BM;
+    const int ct = std::max(1, (sh.ncols + GEMM_BN - 1) / GEMM_BN);
+    // equal-width column tiles (65 time columns -> 33 + 32, not 64 + 1)
+    const int cw = std::max(1, (sh.ncols + ct - 1) / ct);
+    plan.tile_base[o] = (int)tiles.size();
+    plan.col_tiles[o] = ct;
+    plan.col_width[o] = cw;
+    plan.out_base[o] = outpos;
+    outpos += (int64_t)sh.m * sh.ncols;
+    if (sh.m <= 0 || sh.ncols <= 0) continue;
+    for (int r = 0; r < rt; ++r) {
+      for (int c = 0; c < ct; ++c) {
+        const int row0 = r * GEMM_BM;
+        int klo = 0, khi = sh.kdim;
+        if (sh.tri == TRI_LOWER) khi = std::min(sh.kdim, row0 + GEMM_BM);
+        if (sh.tri == TRI_UPPER) klo = std::min(sh.kdim, row0);
+        const int cols = std::min(cw, sh.ncols - c * cw);
+        const int rows = std::min(GEMM_BM, sh.m - row0);
+        // clocks per k-block: multiply-adds at 2 DFMA/clk/SM plus the tile
+        // load and barriers; a one-column (GEMV) tile is latency-bound
+        const double cost = (cols == 1) ? 2048.0 : 0.5 * GEMM_BM * cols * GEMM_BK + 512.0;
+        Tile t{o, row0, c * cw, klo / GEMM_BK, (khi + GEMM_BK - 1) / GEMM_BK, cost};
+        tiles.push_back(t);
+        flops += 2.0 * rows * cols * (double)(khi - klo);
+      }
+    }
+  }
+  plan.ntiles = (int)tiles.size();
+  plan.total_out = outpos;
+  plan.flops = flops;
+  double W = 0;
+  int64_t nkb = 0;
+  for (auto& t : tiles) {
+    W += t.cost_per_kb * (t.kb1 - t.kb0);
+    nkb += t.kb1 - t.kb0;
+  }
+  const int C = (int)std::max<int64_t>(1, std::min<int64_t>(max_ctas, nkb));
+  plan.nctas = C;
+  std::vector<GemmSeg> segs;
+  std::vector<int> seg_start(C + 1, 0);
+  std::vector<std::vector<int>> tile_slots(tiles.size());
+  // walk the linearised (tile, k-block) list; the CTA of an item is fixed by
+  // the midpoint of its cost interval
+  double cum = 0;
+  int cur_cta = -1;
+  std::vector<std::vector<GemmSeg>> per_cta(C);
+  for (int ti = 0; ti < (int)tiles.size(); ++ti) {
+    const Tile& t = tiles[ti];
+    for (int kb = t.kb0; kb < t.kb1; ++kb) {
+      const double mid = cum + 0.5 * t.cost_per_kb;
+      cum += t.cost_per_kb;
+      int cta = (int)std::floor(mid / W * C);
+      cta = std::min(std::max(cta, 0), C - 1);
+      auto& lst = per_cta[cta];
+      const int k0 = kb * GEMM_BK;
+      const int k1 = std::min(shapes[t.op].kdim, (kb + 1) * GEMM_BK);
+      if (!lst.empty() && lst.back().op == t.op && lst.back().row0 == t.row0 && lst.back().col0 == t.col0 &&
+          lst.back().k1 == k0 && cur_cta == cta) {
+        lst.back().k1 = k1;
+      } else {
+        lst.push_back(GemmSeg{t.op, t.row0, t.col0, k0, k1, ti /* tile id, slot assigned below */,
+                              plan.col_width[t.op]});
+      }
+      cur_cta = cta;
+    }
+  }
+  int slot = 0;
+  for (int c = 0; c < C; ++c) {
+    seg_start[c] = (int)segs.size();
+    for (auto sg : per_cta[c]) {
+      const int ti = sg.slot;
+      sg.slot = slot++;
+      tile_slots[ti].push_back(sg.slot);
+      segs.push_back(sg);
+    }
+  }
+  seg_start[C] = (int)segs.size();
+  plan.nslots = slot;
+  // slots of a tile in k order (segments were appended in k order per CTA and
+  // CTAs in increasing order, which is also increasing k within a tile)
+  std::vector<int> tstart(tiles.size() + 1, 0), tslots;
+  for (size_t i = 0; i < tiles.size(); ++i) {
+    tstart[i] = (int)tslots.size();
+    for (int sl : tile_slots[i]) tslots.push_back(sl);
+  }
+  tstart[tiles.size()] = (int)tslots.size();
+  if (tslots.empty()) tslots.push_back(0);
+  if (segs.empty()) segs.push_back(GemmSeg{0, 0, 0, 0, 0, 0, 1});
+  WC4D_CUDA(cudaMalloc(&plan.d_seg_start, sizeof(int) * seg_start.size()));
+  WC4D_CUDA(cudaMalloc(&plan.d_segs, sizeof(GemmSeg) * segs.size()));
+  WC4D_CUDA(cudaMalloc(&plan.d_tile_start, sizeof(int) * tstart.size()));
+  WC4D_CUDA(cudaMalloc(&plan.d_tile_slots, sizeof(int) * tslots.size()));
+  WC4D_CUDA(cudaMemcpy(plan.d_seg_start, seg_start.data(), sizeof(int) * seg_start.size(), cudaMemcpyHostToDevice));
+  WC4D_CUDA(cudaMemcpy(plan.d_segs, segs.data(), sizeof(GemmSeg) * segs.size(), cudaMemcpyHostToDevice));
+  WC4D_CUDA(cudaMemcpy(plan.d_tile_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice));
+  WC4D_CUDA(cudaMemcpy(plan.d_tile_slots, tslots.data(), sizeof(int) * tslots.size(), cudaMemcpyHostToDevice));
+}
+
+// ---------------------------------------------------------------- kernels
+// 256 threads; thread (tx, ty) owns rows row0 + tx + 16 i and columns
+// col0 + ty + 16 j (i, j < 4): conflict-free shared reads and coalesced
+// column-major partial stores.  The next k-block is prefetched into registers
+// while the current one is multiplied.  A one-column tile (a single time level,
+// e.g. B v1_0) switches to a GEMV mapping: every thread takes one row and a
+// quarter of the k-block, so all four SM sub-partitions share the work.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_streamk_kernel(GemmOpsT<T> ops, const GemmSeg* __restrict__ segs,
+                                                           const int* __restrict__ seg_start, T* __restrict__ partial,
+                                                           const int* __restrict__ done, int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  __shared__ T As[GEMM_BK][GEMM_BM + 1];
+  __shared__ T Xs[GEMM_BK][GEMM_BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  constexpr int LA = (GEMM_BM * GEMM_BK) / 256;
+  constexpr int LX = (GEMM_BN * GEMM_BK) / 256;
+  const int sbeg = seg_start[blockIdx.x], send = seg_start[blockIdx.x + 1];
+  for (int si = sbeg; si < send; ++si) {
+    const GemmSeg sg = segs[si];
+    const GemmOpT<T> op = ops.op[sg.op];
+    const int ncv = min(sg.colw, op.ncols - sg.col0);  // columns present in this tile
+    T ra[LA], rx[LX];
+    auto fetch = [&](int k) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = tid + 256 * q;
+        const int kk = e % GEMM_BK, ii = e / GEMM_BK;
+        const int gi = sg.row0 + ii, gk = k + kk;
+        ra[q] = (gi < op.m && gk < sg.k1) ? op.At[gk + (int64_t)gi * op.lda] : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < LX; ++q) {
+        const int e = tid + 256 * q;
+        const int kk = e % GEMM_BK, cc = e / GEMM_BK;
+        const int gk = k + kk;
+        rx[q] = (cc < ncv && gk < sg.k1) ? op.X[gk + (int64_t)(sg.col0 + cc) * op.ldx] : T(0);
+      }
+    };
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    fetch(sg.k0);
+    for (int k = sg.k0; k < sg.k1; k += GEMM_BK) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = tid + 256 * q;
+        As[e % GEMM_BK][e / GEMM_BK] = ra[q];
+      }
+#pragma unroll
+      for (int q = 0; q < LX; ++q) {
+        const int e = tid + 256 * q;
+        Xs[e % GEMM_BK][e / GEMM_BK] = rx[q];
+      }
+      __syncthreads();
+      if (k + GEMM_BK < sg.k1) fetch(k + GEMM_BK);
+      if (ncv == 1) {
+        // GEMV mapping: row tid % 64, k-slice tid / 64
+        const int r = tid & 63, q0 = tid >> 6;
+#pragma unroll
+        for (int kk = q0; kk < GEMM_BK; kk += 4) acc[0][0] = fma(As[kk][r], Xs[kk][0], acc[0][0]);
+      } else if (ncv >= GEMM_BN - 15) {
+#pragma unroll
+        for (int kk = 0; kk < GEMM_BK; ++kk) {
+          T a[4], x[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) x[j] = Xs[kk][ty + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], x[j], acc[i][j]);
+        }
+      } else if (ty < ncv) {
+#pragma unroll
+        for (int kk = 0; kk < GEMM_BK; ++kk) {
+          T a[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (ty + 16 * j < ncv) {
+              const T x = Xs[kk][ty + 16 * j];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) acc[i][j] = fma(a[i], x, acc[i][j]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    T* dst = partial + (int64_t)sg.slot * (GEMM_BM * GEMM_BN);
+    if (ncv == 1) {
+      // combine the four k-slices of each row (reuses As as scratch)
+      T* red = &As[0][0];
+      red[tid] = acc[0][0];
+      __syncthreads();
+      if (tid < GEMM_BM) dst[tid] = (red[tid] + red[tid + 64]) + (red[tid + 128] + red[tid + 192]);
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[(ty + 16 * j) * GEMM_BM + tx + 16 * i] = acc[i][j];
+    }
+  }
+}
+
+struct ReduceMeta {
+  int nops;
+  int tile_base[GEMM_MAX_OPS];
+  int col_tiles[GEMM_MAX_OPS];
+  int col_width[GEMM_MAX_OPS];
+  int m[GEMM_MAX_OPS];
+  int ncols[GEMM_MAX_OPS];
+  int64_t out_base[GEMM_MAX_OPS];
+  int64_t total;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT<T> epis, const T* __restrict__ partial,
+                                                          const int* __restrict__ tile_start,
+                                                          const int* __restrict__ tile_slots, ModelDev md,
+                                                          const int* __restrict__ obs, const int* __restrict__ done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < meta.total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int o = 0;
+    while (o + 1 < meta.nops && g >= meta.out_base[o + 1]) ++o;
+    const int64_t e = g - meta.out_base[o];
+    const int m = meta.m[o];
+    const int r = (int)(e % m), c = (int)(e / m);
+    const int cw = meta.col_width[o];
+    const int tile = meta.tile_base[o] + (r / GEMM_BM) * meta.col_tiles[o] + c / cw;
+    const int off = (c % cw) * GEMM_BM + (r % GEMM_BM);
+    T acc = T(0);
+    for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q)
+      acc += partial[(int64_t)tile_slots[q] * (GEMM_BM * GEMM_BN) + off];
+    const EpiT<T>& ep = epis.e[o];
+    T val;
+    switch (ep.mode) {
+      case EPI_SADDLE_C1: {
+        const int t = c + ep.t0;
+        const int s = md.s;
+        T lv = ep.v3[(int64_t)t * s + r];
+        if (t >= 1) lv -= model_apply<T>(md, t, ep.v3 + (int64_t)(t - 1) * s, r);
+        val = acc + lv;
+        break;
+      }
+      case EPI_SADDLE_C2: {
+        const int t = c + ep.t0;
+        val = acc + ep.v3[(int64_t)t * md.s + obs[r]];
+        break;
+      }
+      case EPI_SUB_FROM:
+        val = ep.Y[r + (int64_t)c * ep.ldc] - acc;
+        break;
+      case EPI_NEG_STORE:
+        val = -acc;
+        break;
+      default:
+        val = acc;
+    }
+    ep.C[r + (int64_t)c * ep.ldc] = val;
+  }
+}
+
+template <typename T>
+void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis, T* partial, const ModelDev& model,
+              const int* obs, const int* done, cudaStream_t st) {
+  if (plan.total_out == 0) return;
+  if (plan.nslots > 0) {
+    int* ran = prof_begin(PROF_GEMM, plan.flops, st);
+    gemm_streamk_kernel<T><<<plan.nctas, 256, 0, st>>>(ops, plan.d_segs, plan.d_seg_start, partial, done, ran);
+    WC4D_LAUNCH_CHECK();
+    if (ran) prof_end(st);
+  }
+  ReduceMeta meta;
+  meta.nops = plan.nops;
+  for (int o = 0; o < GEMM_MAX_OPS; ++o) {
+    meta.tile_base[o] = o < plan.nops ? plan.tile_base[o] : 0;
+    meta.col_tiles[o] = o < plan.nops ? plan.col_tiles[o] : 1;
+    meta.col_width[o] = o < plan.nops ? std::max(1, plan.col_width[o]) : 1;
+    meta.m[o] = o < plan.nops ? std::max(1, plan.shape[o].m) : 1;
+    meta.ncols[o] = o < plan.nops ? plan.shape[o].ncols : 0;
+    meta.out_base[o] = o < plan.nops ? plan.out_base[o] : plan.total_out;
+  }
+  meta.total = plan.total_out;
+  const int64_t nb = std::min<int64_t>((plan.total_out + 255) / 256, 152 * 8);
+  gemm_reduce_kernel<T><<<(int)nb, 256, 0, st>>>(meta, epis, partial, plan.d_tile_start, plan.d_tile_slots, model,
+                                                 obs, done);
+  WC4D_LAUNCH_CHECK();
+}
+
+int gemm_resident_ctas() {
+  static int cached = 0;
+  if (cached) return cached;
+  int dev = 0, sms = 0, per = 0;
+  WC4D_CUDA(cudaGetDevice(&dev));
+  WC4D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gemm_streamk_kernel<double>, 256, 0));
+  cached = std::max(1, sms * std::max(1, per));
+  return cached;
+}
+
+template void gemm_run<double>(const GemmPlan&, const GemmOpsT<double>&, const EpisT<double>&, double*,
+                               const ModelDev&, const int*, const int*, cudaStream_t);
+template void gemm_run<float>(const GemmPlan&, const GemmOpsT<float>&, const EpisT<float>&, float*, const ModelDev&,
+                              const int*, const int*, cudaStream_t);
+
+}  // namespace wc4d

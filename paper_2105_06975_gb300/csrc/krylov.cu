@@ -1,0 +1,472 @@
+// Krylov kernels: MINRES (preconditioned Lanczos form, Elman-Silvester-Wathen
+// Ch. 4) and right-preconditioned (F)GMRES with CGS2 Arnoldi.  Dot products use
+// a fixed grid of DOT_BLOCKS blocks and warp-shuffle block reductions; the
+// partial sums are added in a fixed order by every consumer, so results are
+// bitwise reproducible run to run.
+#include <algorithm>
+#include <cmath>
+
+#include "krylov.cuh"
+
+namespace wc4d {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum, result valid in every thread
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += sh[i];
+  return t;
+}
+
+// sum of DOT_BLOCKS partials in fixed order (whole block cooperates, same result everywhere)
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < DOT_BLOCKS; i += blockDim.x) v += part[i];
+  return block_sum(v, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DOT_THREADS) dot_partial_kernel(const T* __restrict__ a, const T* __restrict__ b,
+                                                                  int64_t n, double* __restrict__ part,
+                                                                  const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    v += (double)a[e] * (double)b[e];
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+template <typename T>
+void dot_partial(const T* a, const T* b, int64_t n, double* part, const int* done, cudaStream_t st) {
+  dot_partial_kernel<T><<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(a, b, n, part, done);
+  WC4D_LAUNCH_CHECK();
+}
+template void dot_partial<double>(const double*, const double*, int64_t, double*, const int*, cudaStream_t);
+template void dot_partial<float>(const float*, const float*, int64_t, double*, const int*, cudaStream_t);
+
+__global__ void dot_finish_kernel(const double* part, double* out, int sqrt_it) {
+  __shared__ double sh[32];
+  const double v = sum_partials(part, sh);
+  if (threadIdx.x == 0) *out = sqrt_it ? sqrt(fmax(v, 0.0)) : v;
+}
+void dot_finish(const double* part, double* out, int sqrt_it, cudaStream_t st) {
+  dot_finish_kernel<<<1, DOT_THREADS, 0, st>>>(part, out, sqrt_it);
+  WC4D_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ MINRES
+__global__ void minres_init_kernel(const double* part_gamma, double* sc, DevStatus* stat, double tol) {
+  __shared__ double sh[32];
+  const double g2 = sum_partials(part_gamma, sh);
+  if (threadIdx.x == 0) {
+    const double g = sqrt(fmax(g2, 0.0));
+    sc[MS_GAMMA] = g;
+    sc[MS_GAMMA_OLD] = 1.0;
+    sc[MS_ETA] = g;
+    sc[MS_ETA0] = g > 0.0 ? g : 1.0;
+    sc[MS_C] = 1.0;
+    sc[MS_C_OLD] = 1.0;
+    sc[MS_S] = 0.0;
+    sc[MS_S_OLD] = 0.0;
+    stat->done = 0;
+    stat->status = 0;
+    stat->iters = 0;
+    stat->est = 1.0;
+    stat->tol_est = tol;
+    if (!(g2 >= 0.0) || !isfinite(g2)) {
+      stat->done = 1;
+      stat->status = isfinite(g2) ? WC4D_ERR_BREAKDOWN : WC4D_ERR_NONFINITE;
+    } else if (g == 0.0) {
+      stat->done = 1;
+      stat->est = 0.0;
+    }
+  }
+}
+void minres_init(const double* part_gamma, double* sc, DevStatus* stat, double tol, cudaStream_t st) {
+  minres_init_kernel<<<1, DOT_THREADS, 0, st>>>(part_gamma, sc, stat, tol);
+  WC4D_LAUNCH_CHECK();
+}
+
+// v_new = A z / gamma - (delta/gamma) v - (gamma/gamma_old) v_old with
+// delta = <A z, z> / gamma^2  (z is the unscaled P^{-1} v)
+__global__ void __launch_bounds__(DOT_THREADS) minres_v_kernel(const double* part_delta, const double* sc,
+                                                               const double* __restrict__ Az,
+                                                               const double* __restrict__ v,
+                                                               const double* __restrict__ v_old,
+                                                               double* __restrict__ v_new, int64_t n,
+                                                               const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  __shared__ double sh[32];
+  const double g = sc[MS_GAMMA], go = sc[MS_GAMMA_OLD];
+  const double delta = sum_partials(part_delta, sh) / (g * g);
+  const double a = 1.0 / g, b = delta / g, c = g / go;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    v_new[e] = a * Az[e] - b * v[e] - c * v_old[e];
+}
+void minres_v_update(const double* part_delta, const double* sc, const double* Az, const double* v,
+                     const double* v_old, double* v_new, int64_t n, const int* done, cudaStream_t st) {
+  minres_v_kernel<<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(part_delta, sc, Az, v, v_old, v_new, n, done);
+  WC4D_LAUNCH_CHECK();
+}
+
+// MINRES scalars of one iteration from the two dot products (identical in
+// every block: same inputs, same summation order).
+struct MinresStep {
+  double g, gn, gn2, delta, c, s, cn, sn, a1, a2, a3, eta;
+};
+__device__ __forceinline__ MinresStep minres_scalars(const double* part_delta, const double* part_gamma,
+                                                     const double* sc, double* sh) {
+  MinresStep m;
+  m.g = sc[MS_GAMMA];
+  m.delta = sum_partials(part_delta, sh) / (m.g * m.g);
+  m.gn2 = sum_partials(part_gamma, sh);
+  m.gn = sqrt(fmax(m.gn2, 0.0));
+  m.c = sc[MS_C];
+  m.s = sc[MS_S];
+  m.eta = sc[MS_ETA];
+  const double co = sc[MS_C_OLD], so = sc[MS_S_OLD];
+  const double a0 = m.c * m.delta - co * m.s * m.g;
+  m.a1 = hypot(a0, m.gn);
+  m.a2 = m.s * m.delta + co * m.c * m.g;
+  m.a3 = so * m.g;
+  m.cn = a0 / m.a1;
+  m.sn = m.gn / m.a1;
+  return m;
+}
+
+// w_new = (z/gamma - a3 w_old - a2 w) / a1,  x += c_new eta w_new
+__global__ void __launch_bounds__(DOT_THREADS) minres_update_kernel(
+    const double* part_delta, const double* part_gamma, const double* sc, const double* __restrict__ z,
+    const double* __restrict__ w_old, const double* __restrict__ w, double* __restrict__ w_new, double* __restrict__ x,
+    int64_t n, const int* done) {
+  if (*(volatile const int*)done) return;
+  __shared__ double sh[32];
+  const MinresStep m = minres_scalars(part_delta, part_gamma, sc, sh);
+  const double ig = 1.0 / m.g, ia1 = 1.0 / m.a1, step = m.cn * m.eta;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double wn = (z[e] * ig - m.a3 * w_old[e] - m.a2 * w[e]) * ia1;
+    w_new[e] = wn;
+    x[e] += step * wn;
+  }
+}
+
+// commits the new scalar state and the stopping decision (separate launch, so
+// the flag it sets is only seen by later kernels)
+__global__ void minres_commit_kernel(const double* part_delta, const double* part_gamma, const double* sc,
+                                     double* sc_out, DevStatus* stat) {
+  if (*(volatile const int*)&stat->done) return;
+  __shared__ double sh[32];
+  const MinresStep m = minres_scalars(part_delta, part_gamma, sc, sh);
+  if (threadIdx.x != 0) return;
+  const double eta_n = -m.sn * m.eta;
+  sc_out[MS_GAMMA] = m.gn;
+  sc_out[MS_GAMMA_OLD] = m.g;
+  sc_out[MS_ETA] = eta_n;
+  sc_out[MS_ETA0] = sc[MS_ETA0];
+  sc_out[MS_C] = m.cn;
+  sc_out[MS_C_OLD] = m.c;
+  sc_out[MS_S] = m.sn;
+  sc_out[MS_S_OLD] = m.s;
+  const double est = fabs(eta_n) / sc[MS_ETA0];
+  stat->iters += 1;
+  stat->est = est;
+  if (!isfinite(est) || !isfinite(m.gn2)) {
+    stat->status = WC4D_ERR_NONFINITE;
+    stat->done = 1;
+  } else if (m.gn2 < 0.0) {
+    stat->status = WC4D_ERR_BREAKDOWN;
+    stat->done = 1;
+  } else if (est <= stat->tol_est || m.gn == 0.0) {
+    stat->done = 1;
+  }
+}
+
+void minres_update(const double* part_delta, const double* part_gamma, const double* sc_in, double* sc_out,
+                   const double* z, const double* w_old, const double* w, double* w_new, double* x, int64_t n,
+                   DevStatus* stat, cudaStream_t st) {
+  minres_update_kernel<<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(part_delta, part_gamma, sc_in, z, w_old, w, w_new, x, n,
+                                                           &stat->done);
+  WC4D_LAUNCH_CHECK();
+  minres_commit_kernel<<<1, DOT_THREADS, 0, st>>>(part_delta, part_gamma, sc_in, sc_out, stat);
+  WC4D_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------- GMRES
+// part[i * DOT_BLOCKS + b] = sum over block b's slice of V_i . w
+template <typename T>
+__global__ void __launch_bounds__(DOT_THREADS) gm_mdot_kernel(const T* __restrict__ V, int64_t ldv, int cnt,
+                                                              const T* __restrict__ w, int64_t n,
+                                                              double* __restrict__ part, const int* done,
+                                                              int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = blockIdx.x * chunk;
+  const int64_t e1 = min(n, e0 + chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < cnt; i += nw) {
+    const T* vi = V + (int64_t)i * ldv;
+    double acc = 0.0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) acc += (double)vi[e] * (double)w[e];
+    acc = warp_sum(acc);
+    if (lane == 0) part[(int64_t)i * DOT_BLOCKS + blockIdx.x] = acc;
+  }
+}
+template <typename T>
+void gm_mdot(const T* V, int64_t ldv, int cnt, const T* w, int64_t n, double* part, const int* done,
+             cudaStream_t st) {
+  int* ran = prof_begin(PROF_ORTH, (double)(cnt + 1) * n * sizeof(T), st);
+  gm_mdot_kernel<T><<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(V, ldv, cnt, w, n, part, done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+template void gm_mdot<double>(const double*, int64_t, int, const double*, int64_t, double*, const int*, cudaStream_t);
+template void gm_mdot<float>(const float*, int64_t, int, const float*, int64_t, double*, const int*, cudaStream_t);
+
+__global__ void gm_mdot_reduce_kernel(const double* part, double* h, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  __shared__ double sh[32];
+  const double v = sum_partials(part + (int64_t)blockIdx.x * DOT_BLOCKS, sh);
+  if (threadIdx.x == 0) h[blockIdx.x] = v;
+}
+void gm_mdot_reduce(const double* part, int cnt, double* h, const int* done, cudaStream_t st) {
+  gm_mdot_reduce_kernel<<<cnt, DOT_THREADS, 0, st>>>(part, h, done);
+  WC4D_LAUNCH_CHECK();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DOT_THREADS) gm_mupdate_kernel(const T* __restrict__ V, int64_t ldv, int cnt,
+                                                                 const double* __restrict__ h, T* __restrict__ w,
+                                                                 int64_t n, const int* done, int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  extern __shared__ double hs[];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < cnt; ++i) acc += hs[i] * (double)V[(int64_t)i * ldv + e];
+    w[e] = (T)((double)w[e] - acc);
+  }
+}
+template <typename T>
+void gm_mupdate(const T* V, int64_t ldv, int cnt, const double* h, T* w, int64_t n, const int* done,
+                cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + DOT_THREADS - 1) / DOT_THREADS, 152 * 8);
+  int* ran = prof_begin(PROF_ORTH, (double)(cnt + 2) * n * sizeof(T), st);
+  gm_mupdate_kernel<T><<<nb, DOT_THREADS, sizeof(double) * cnt, st>>>(V, ldv, cnt, h, w, n, done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+template void gm_mupdate<double>(const double*, int64_t, int, const double*, double*, int64_t, const int*,
+                                 cudaStream_t);
+template void gm_mupdate<float>(const float*, int64_t, int, const double*, float*, int64_t, const int*, cudaStream_t);
+
+// v0 = r0 / beta, g = (beta, 0, ...), status reset
+template <typename T>
+__global__ void gm_init_kernel(const T* __restrict__ r0, const double* part_beta, T* __restrict__ v0, double* g,
+                               DevStatus* stat, double tol, int64_t n) {
+  __shared__ double sh[32];
+  const double beta = sqrt(fmax(sum_partials(part_beta, sh), 0.0));
+  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    v0[e] = (T)((double)r0[e] * ib);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    g[0] = beta;
+    stat->done = (beta == 0.0) ? 1 : 0;
+    stat->status = isfinite(beta) ? 0 : WC4D_ERR_NONFINITE;
+    if (!isfinite(beta)) stat->done = 1;
+    stat->iters = 0;
+    stat->est = 1.0;
+    stat->tol_est = tol;
+  }
+}
+template <typename T>
+void gm_init(const T* r0, const double* part_beta, T* v0, double* g, DevStatus* stat, double tol, int64_t n,
+             cudaStream_t st) {
+  gm_init_kernel<T><<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(r0, part_beta, v0, g, stat, tol, n);
+  WC4D_LAUNCH_CHECK();
+}
+template void gm_init<double>(const double*, const double*, double*, double*, DevStatus*, double, int64_t,
+                              cudaStream_t);
+template void gm_init<float>(const float*, const double*, float*, double*, DevStatus*, double, int64_t, cudaStream_t);
+
+// Column j of the Hessenberg matrix, previous Givens rotations, the new one,
+// the residual estimate |g_{j+1}| / ||b||.  The column and the rotations are
+// staged in shared memory so the serial rotation chain runs at shared-memory
+// latency (the chain has j dependent steps).
+__global__ void gm_hessenberg_kernel(int j, const double* h1, const double* h2, const double* part_norm, double* H,
+                                     int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
+                                     const double* bnorm) {
+  extern __shared__ double sm[];  // col[j+2], c[j], s[j]
+  __shared__ double sh[32];
+  if (*(volatile const int*)&stat->done) return;
+  const double nrm2 = sum_partials(part_norm, sh);
+  double* col = sm;
+  double* c_ = sm + (j + 2);
+  double* s_ = c_ + j;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = h1[i] + h2[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    c_[i] = cs[i];
+    s_[i] = sn[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double hn = sqrt(fmax(nrm2, 0.0));
+    col[j + 1] = hn;
+    *hnext = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = col[i], b = col[i + 1];
+      col[i] = c_[i] * a + s_[i] * b;
+      col[i + 1] = -s_[i] * a + c_[i] * b;
+    }
+    double c = 1.0, s = 0.0;
+    if (col[j + 1] != 0.0) {
+      const double r = hypot(col[j], col[j + 1]);
+      c = col[j] / r;
+      s = col[j + 1] / r;
+    }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = c * col[j] + s * col[j + 1];
+    col[j + 1] = 0.0;
+    const double gj = g[j];
+    g[j + 1] = -s * gj;
+    g[j] = c * gj;
+    const double est = fabs(g[j + 1]) / *bnorm;
+    stat->iters = j + 1;
+    stat->est = est;
+    if (!isfinite(est) || !isfinite(hn)) {
+      stat->status = WC4D_ERR_NONFINITE;
+      stat->done = 1;
+    } else if (est <= stat->tol_est || hn == 0.0) {
+      stat->done = 1;
+    }
+  }
+  __syncthreads();
+  double* out = H + (int64_t)j * ldh;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) out[i] = col[i];
+}
+void gm_hessenberg(int j, const double* h1, const double* h2, const double* part_norm, double* H, int ldh, double* cs,
+                   double* sn, double* g, double* hnext, DevStatus* stat, const double* bnorm, cudaStream_t st) {
+  gm_hessenberg_kernel<<<1, DOT_THREADS, sizeof(double) * (3 * (size_t)j + 2), st>>>(j, h1, h2, part_norm, H, ldh,
+                                                                                       cs, sn, g, hnext, stat, bnorm);
+  WC4D_LAUNCH_CHECK();
+}
+
+template <typename T>
+__global__ void gm_normalize_kernel(const T* __restrict__ w, const double* hnext, T* __restrict__ v, int64_t n,
+                                    const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  const double h = *hnext;
+  const double ih = h > 0.0 ? 1.0 / h : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    v[e] = (T)((double)w[e] * ih);
+}
+template <typename T>
+void gm_normalize(const T* w, const double* hnext, T* v, int64_t n, const int* done, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  gm_normalize_kernel<T><<<nb, 256, 0, st>>>(w, hnext, v, n, done);
+  WC4D_LAUNCH_CHECK();
+}
+template void gm_normalize<double>(const double*, const double*, double*, int64_t, const int*, cudaStream_t);
+template void gm_normalize<float>(const float*, const double*, float*, int64_t, const int*, cudaStream_t);
+
+// y = R^{-1} g[0:k] with R the rotated (upper triangular) k x k Hessenberg
+// block: column-oriented back substitution, one block, the right-hand side in
+// shared memory.
+__global__ void gm_solve_y_kernel(const double* H, int ldh, const double* g, int k, double* y) {
+  extern __shared__ double rhs[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = g[i];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    const double yi = rhs[i] / H[i + (int64_t)i * ldh];
+    __syncthreads();
+    for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= H[r + (int64_t)i * ldh] * yi;
+    if (threadIdx.x == 0) y[i] = yi;
+    __syncthreads();
+  }
+}
+void gm_solve_y(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t st) {
+  gm_solve_y_kernel<<<1, 256, sizeof(double) * (size_t)std::max(k, 1), st>>>(H, ldh, g, k, y);
+  WC4D_LAUNCH_CHECK();
+}
+
+// x = x0 + sum_i y_i Z_i
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(256) gm_combine_kernel(const TZ* __restrict__ Z, int64_t ldz, int k,
+                                                         const double* __restrict__ y, const T* x0, T* x, int64_t n) {
+  extern __shared__ double ys[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = x0 ? (double)x0[e] : 0.0;
+    for (int i = 0; i < k; ++i) acc += ys[i] * (double)Z[(int64_t)i * ldz + e];
+    x[e] = (T)acc;
+  }
+}
+template <typename T, typename TZ>
+void gm_combine(const TZ* Z, int64_t ldz, int k, const double* y, const T* x0, T* x, int64_t n, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  gm_combine_kernel<T, TZ><<<nb, 256, sizeof(double) * std::max(k, 1), st>>>(Z, ldz, k, y, x0, x, n);
+  WC4D_LAUNCH_CHECK();
+}
+template void gm_combine<double, double>(const double*, int64_t, int, const double*, const double*, double*, int64_t,
+                                         cudaStream_t);
+template void gm_combine<float, float>(const float*, int64_t, int, const double*, const float*, float*, int64_t,
+                                       cudaStream_t);
+template void gm_combine<double, float>(const float*, int64_t, int, const double*, const double*, double*, int64_t,
+                                        cudaStream_t);
+
+// ---------------------------------------------------------------- vectors
+template <typename T>
+__global__ void axpby_kernel(T* y, const T* x, double a, double b, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (T)(a * (double)x[e] + b * (double)y[e]);
+}
+template <typename T>
+void vec_axpby(T* y, const T* x, double a, double b, int64_t n, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  axpby_kernel<T><<<nb, 256, 0, st>>>(y, x, a, b, n);
+  WC4D_LAUNCH_CHECK();
+}
+template void vec_axpby<double>(double*, const double*, double, double, int64_t, cudaStream_t);
+template void vec_axpby<float>(float*, const float*, double, double, int64_t, cudaStream_t);
+
+__global__ void sub_kernel(const double* a, const double* b, double* o, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    o[e] = a[e] - b[e];
+}
+void vec_sub(const double* a, const double* b, double* out, int64_t n, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  sub_kernel<<<nb, 256, 0, st>>>(a, b, out, n);
+  WC4D_LAUNCH_CHECK();
+}
+
+template <typename TD, typename TS>
+__global__ void convert_kernel(const TS* s, TD* d, int64_t n, double scale) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (TD)((double)s[e] * scale);
+}
+template <typename TD, typename TS>
+void vec_convert(const TS* src, TD* dst, int64_t n, double scale, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  convert_kernel<TD, TS><<<nb, 256, 0, st>>>(src, dst, n, scale);
+  WC4D_LAUNCH_CHECK();
+}
+template void vec_convert<float, double>(const double*, float*, int64_t, double, cudaStream_t);
+template void vec_convert<double, float>(const float*, double*, int64_t, double, cudaStream_t);
+template void vec_convert<double, double>(const double*, double*, int64_t, double, cudaStream_t);
+
+}  // namespace wc4d

@@ -1,0 +1,60 @@
+// Device-resident Krylov kernels (FP64 recurrences, deterministic reductions).
+#pragma once
+#include "common.cuh"
+
+namespace wc4d {
+
+constexpr int DOT_BLOCKS = 304;  // 2 per SM on a 152-SM GB300; fixed for deterministic sums
+constexpr int DOT_THREADS = 256;
+
+struct DevStatus {
+  int done;
+  int status;
+  int iters;
+  int pad;
+  double est;      // recurrence residual estimate (relative)
+  double tol_est;  // threshold the estimate is compared with
+};
+
+// MINRES scalar state (double buffered: read sc_in, block 0 writes sc_out)
+enum { MS_GAMMA = 0, MS_GAMMA_OLD, MS_ETA, MS_ETA0, MS_C, MS_C_OLD, MS_S, MS_S_OLD, MS_COUNT };
+
+template <typename T>
+void dot_partial(const T* a, const T* b, int64_t n, double* part, const int* done, cudaStream_t st);
+void dot_finish(const double* part, double* out, int sqrt_it, cudaStream_t st);
+
+void minres_init(const double* part_gamma, double* sc, DevStatus* stat, double tol, cudaStream_t st);
+void minres_v_update(const double* part_delta, const double* sc, const double* Az, const double* v,
+                     const double* v_old, double* v_new, int64_t n, const int* done, cudaStream_t st);
+void minres_update(const double* part_delta, const double* part_gamma, const double* sc_in, double* sc_out,
+                   const double* z, const double* w_old, const double* w, double* w_new, double* x, int64_t n,
+                   DevStatus* stat, cudaStream_t st);
+
+// GMRES / FGMRES (Arnoldi with classical Gram-Schmidt and one reorthogonalisation)
+template <typename T>
+void gm_mdot(const T* V, int64_t ldv, int cnt, const T* w, int64_t n, double* part, const int* done,
+             cudaStream_t st);
+void gm_mdot_reduce(const double* part, int cnt, double* h, const int* done, cudaStream_t st);
+template <typename T>
+void gm_mupdate(const T* V, int64_t ldv, int cnt, const double* h, T* w, int64_t n, const int* done,
+                cudaStream_t st);
+template <typename T>
+void gm_init(const T* r0, const double* part_beta, T* v0, double* g, DevStatus* stat, double tol, int64_t n,
+             cudaStream_t st);
+void gm_hessenberg(int j, const double* h1, const double* h2, const double* part_norm, double* H, int ldh,
+                   double* cs, double* sn, double* g, double* hnext, DevStatus* stat, const double* bnorm,
+                   cudaStream_t st);
+template <typename T>
+void gm_normalize(const T* w, const double* hnext, T* v, int64_t n, const int* done, cudaStream_t st);
+void gm_solve_y(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t st);
+template <typename T, typename TZ>
+void gm_combine(const TZ* Z, int64_t ldz, int k, const double* y, const T* x0, T* x, int64_t n, cudaStream_t st);
+
+// small vector ops
+template <typename T>
+void vec_axpby(T* y, const T* x, double a, double b, int64_t n, cudaStream_t st);  // y = a x + b y
+void vec_sub(const double* a, const double* b, double* out, int64_t n, cudaStream_t st);
+template <typename TD, typename TS>
+void vec_convert(const TS* src, TD* dst, int64_t n, double scale, cudaStream_t st);
+
+}  // namespace wc4d

@@ -1,0 +1,1052 @@
+// wc4d C ABI: problem setup, the saddle-point operator A (Eq. saddlepointA),
+// the preconditioners P_D and P_I (Eq. prec, applied as in Sec. 6.2) and the
+// device-resident MINRES / GMRES / FGMRES drivers.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "krylov.cuh"
+
+namespace wc4d {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+template <typename T>
+void lhat_sweep(const ModelDev& md, int k, const T* v, T* z, bool transpose, bool identity_model, const int* done,
+                cudaStream_t st);
+template <typename T>
+void saddle_c3(const ModelDev& md, const T* v1, const T* v2, const int* inv, int p, T* c3, const int* done,
+               cudaStream_t st);
+
+// Operator data in one precision: covariances, inverse Cholesky factors and
+// the GEMM partial buffer.
+template <typename T>
+struct OpSet {
+  T *B = nullptr, *Q = nullptr, *R = nullptr;
+  T *WB = nullptr, *WBt = nullptr, *WQ = nullptr, *WQt = nullptr, *WR = nullptr, *WRt = nullptr;
+  T *WS = nullptr, *WSt = nullptr;
+  T* partial = nullptr;
+  T *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;  // n-length scratch
+};
+
+}  // namespace wc4d
+
+using namespace wc4d;
+
+struct wc4d_problem {
+  int s = 0, N = 0, p = 0;
+  int64_t n = 0, ns = 0, np = 0;
+  cudaStream_t st = nullptr;
+  wc4d_solve_opts o{};
+  ModelDev md{};
+  int *d_obs = nullptr, *d_inv = nullptr;
+  double* d_bands = nullptr;
+  double* d_Rhat = nullptr;
+  double rhat_param = 0.0;
+  int nS = 0;
+  bool have_pd = false;
+  OpSet<double> f64;
+  GemmPlan plan_A, plan_pd1, plan_pd2, plan_pi1, plan_pi2;
+  // Krylov workspace
+  int maxit = 0;
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *hnext = nullptr, *bnorm = nullptr, *scal = nullptr;
+  double *part = nullptr, *part2 = nullptr, *part3 = nullptr, *sc = nullptr;
+  double *rhs = nullptr, *x = nullptr, *r = nullptr, *x0 = nullptr;
+  DevStatus* stat = nullptr;
+  DevStatus* h_stat = nullptr;
+  double* h_scal = nullptr;
+  std::vector<void*> allocs;
+
+  template <typename T>
+  T* alloc(int64_t count) {
+    void* p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) throw Error{WC4D_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    allocs.push_back(p);
+    return (T*)p;
+  }
+  ~wc4d_problem() {
+    plan_free(plan_A);
+    plan_free(plan_pd1);
+    plan_free(plan_pd2);
+    plan_free(plan_pi1);
+    plan_free(plan_pi2);
+    for (void* p : allocs) cudaFree(p);
+    if (h_stat) cudaFreeHost(h_stat);
+    if (h_scal) cudaFreeHost(h_scal);
+  }
+};
+
+namespace wc4d {
+
+static int max_gemm_ctas() { return gemm_resident_ctas(); }
+
+// ------------------------------------------------------------ A v (Sec. 6.2)
+template <typename T>
+static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T* v, T* out, const int* done) {
+  const int s = P->s, N = P->N, p = P->p;
+  const T* v1 = v;
+  const T* v2 = v + P->ns;
+  const T* v3 = v + P->ns + P->np;
+  T* c1 = out;
+  T* c2 = out + P->ns;
+  T* c3 = out + P->ns + P->np;
+  saddle_c3<T>(P->md, v1, v2, P->d_inv, p, c3, done, P->st);
+  GemmOpsT<T> ops{};
+  EpisT<T> ep{};
+  ops.nops = 3;
+  ops.op[0] = {os.B, s, v1, s, s, s, 1, TRI_FULL};
+  ops.op[1] = {os.Q, s, v1 + s, s, s, s, N, TRI_FULL};
+  ops.op[2] = {os.R, p, v2, p, p, p, N + 1, TRI_FULL};
+  ep.e[0] = {EPI_SADDLE_C1, c1, s, 0, v3, nullptr};
+  ep.e[1] = {EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr};
+  ep.e[2] = {EPI_SADDLE_C2, c2, p, 0, v3, nullptr};
+  gemm_run<T>(plan, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+}
+
+// P_D^{-1} v = (Dhat^{-1} v1, Rhat^{-1} v2, Shat^{-1} v3); Dhat^{-1} = W^T W with
+// W the inverse Cholesky factor, Shat^{-1} = Lhat^{-1} D Lhat^{-T} (paper) or
+// W_S^T W_S (exact S).
+template <typename T>
+static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const GemmPlan& p2, const T* v, T* out,
+                     const int* done) {
+  const int s = P->s, N = P->N, p = P->p, k = P->o.k;
+  const bool ident = false;
+  const T* v1 = v;
+  const T* v2 = v + P->ns;
+  const T* v3 = v + P->ns + P->np;
+  T* o1 = out;
+  T* o2 = out + P->ns;
+  T* o3 = out + P->ns + P->np;
+  T* y1 = os.t1;             // W v1
+  T* y2 = os.t1 + P->ns;     // W_R v2
+  T* y3 = os.t2;             // Lhat^{-T} v3
+  T* u3 = os.t3;             // D y3 (or W_S v3)
+  const bool exactS = (P->o.shat == WC4D_SHAT_EXACT);
+  if (!exactS) lhat_sweep<T>(P->md, k, v3, y3, true, ident, done, P->st);
+  GemmOpsT<T> ops{};
+  EpisT<T> ep{};
+  ops.op[0] = {os.WBt, s, v1, s, s, s, 1, TRI_LOWER};
+  ops.op[1] = {os.WQt, s, v1 + s, s, s, s, N, TRI_LOWER};
+  ops.op[2] = {os.WRt, p, v2, p, p, p, N + 1, TRI_LOWER};
+  ep.e[0] = {EPI_STORE, y1, s, 0, nullptr, nullptr};
+  ep.e[1] = {EPI_STORE, y1 + s, s, 0, nullptr, nullptr};
+  ep.e[2] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
+  if (exactS) {
+    ops.nops = 4;
+    ops.op[3] = {os.WSt, P->nS, v3, P->nS, P->nS, P->nS, 1, TRI_LOWER};
+    ep.e[3] = {EPI_STORE, u3, P->nS, 0, nullptr, nullptr};
+  } else {
+    ops.nops = 4;
+    // D y3 = [B y3_0 | Q y3_1..N]: two ops packed as one B-column op and one Q op
+    // exceed GEMM_MAX_OPS together with the three factors, so B's column rides
+    // in a second launch below.
+    ops.op[3] = {os.Q, s, y3 + s, s, s, s, N, TRI_FULL};
+    ep.e[3] = {EPI_STORE, u3 + s, s, 0, nullptr, nullptr};
+  }
+  gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+  GemmOpsT<T> ops2{};
+  EpisT<T> ep2{};
+  ops2.op[0] = {os.WB, s, y1, s, s, s, 1, TRI_UPPER};
+  ops2.op[1] = {os.WQ, s, y1 + s, s, s, s, N, TRI_UPPER};
+  ops2.op[2] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
+  ep2.e[0] = {EPI_STORE, o1, s, 0, nullptr, nullptr};
+  ep2.e[1] = {EPI_STORE, o1 + s, s, 0, nullptr, nullptr};
+  ep2.e[2] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
+  if (exactS) {
+    ops2.nops = 4;
+    ops2.op[3] = {os.WS, P->nS, u3, P->nS, P->nS, P->nS, 1, TRI_UPPER};
+    ep2.e[3] = {EPI_STORE, o3, P->nS, 0, nullptr, nullptr};
+    gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
+  } else {
+    ops2.nops = 4;
+    ops2.op[3] = {os.B, s, y3, s, s, s, 1, TRI_FULL};
+    ep2.e[3] = {EPI_STORE, u3, s, 0, nullptr, nullptr};
+    gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
+    lhat_sweep<T>(P->md, k, u3, o3, false, ident, done, P->st);
+  }
+}
+
+// P_I^{-1} v: c1 = Lhat^{-T} v3, c2 = Rhat^{-1} v2, c3 = Lhat^{-1}(v1 - D c1).
+template <typename T>
+static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const GemmPlan& p2, const T* v, T* out,
+                     const int* done) {
+  const int s = P->s, N = P->N, p = P->p, k = P->o.k;
+  const T* v1 = v;
+  const T* v2 = v + P->ns;
+  const T* v3 = v + P->ns + P->np;
+  T* o1 = out;
+  T* o2 = out + P->ns;
+  T* o3 = out + P->ns + P->np;
+  T* y2 = os.t1;  // W_R v2
+  T* u = os.t2;   // v1 - D c1
+  lhat_sweep<T>(P->md, k, v3, o1, true, false, done, P->st);
+  GemmOpsT<T> ops{};
+  EpisT<T> ep{};
+  ops.nops = 3;
+  ops.op[0] = {os.WRt, p, v2, p, p, p, N + 1, TRI_LOWER};
+  ops.op[1] = {os.B, s, o1, s, s, s, 1, TRI_FULL};
+  ops.op[2] = {os.Q, s, o1 + s, s, s, s, N, TRI_FULL};
+  ep.e[0] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
+  ep.e[1] = {EPI_SUB_FROM, u, s, 0, nullptr, v1};
+  ep.e[2] = {EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s};
+  gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+  GemmOpsT<T> ops2{};
+  EpisT<T> ep2{};
+  ops2.nops = 1;
+  ops2.op[0] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
+  ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
+  gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
+  lhat_sweep<T>(P->md, k, u, o3, false, false, done, P->st);
+}
+
+template <typename T>
+static void apply_P(wc4d_problem* P, int which, OpSet<T>& os, const T* v, T* out, const int* done) {
+  if (which == WC4D_PRECOND_PD)
+    apply_PD<T>(P, os, P->plan_pd1, P->plan_pd2, v, out, done);
+  else
+    apply_PI<T>(P, os, P->plan_pi1, P->plan_pi2, v, out, done);
+}
+
+// ------------------------------------------------------------------ setup
+static void copy_in(void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t st) {
+  WC4D_CUDA(cudaMemcpyAsync(dst, src, bytes, mem_kind == WC4D_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                         : cudaMemcpyHostToDevice, st));
+}
+
+static int read_flag(int* d_flag, cudaStream_t st) {
+  int h = 0;
+  WC4D_CUDA(cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  WC4D_CUDA(cudaStreamSynchronize(st));
+  return h;
+}
+
+// Cholesky + inverse factor of an SPD matrix given in A (overwritten by L).
+static void factor_inverse(wc4d_problem* P, double* A, int m, double* W, double* Wt, int* d_info, double* scratch,
+                           const char* what) {
+  WC4D_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), P->st));
+  cholesky(A, m, d_info, P->st, scratch);
+  const int info = read_flag(d_info, P->st);
+  if (info != 0) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "Cholesky of %s failed: non-positive pivot %d of %d", what, info, m);
+    throw Error{WC4D_ERR_NOT_SPD, buf};
+  }
+  tri_inverse(A, W, Wt, m, P->st, scratch);
+}
+
+// single-op GEMM C = op(At) X with a throwaway plan
+static void gemm_once(wc4d_problem* P, const double* At, int64_t lda, const double* X, int64_t ldx, int m, int kdim,
+                      int ncols, double* C, int64_t ldc, int mode) {
+  GemmPlan plan;
+  plan_build(plan, {OpShape{m, kdim, ncols, TRI_FULL}}, max_gemm_ctas());
+  double* partial = nullptr;
+  WC4D_CUDA(cudaMalloc(&partial, sizeof(double) * (size_t)std::max(1, plan.nslots) * GEMM_BM * GEMM_BN));
+  GemmOps ops{};
+  Epis ep{};
+  ops.nops = 1;
+  ops.op[0] = {At, lda, X, ldx, m, kdim, ncols, TRI_FULL};
+  ep.e[0] = {mode, C, ldc, 0, nullptr, nullptr};
+  gemm_run<double>(plan, ops, ep, partial, P->md, P->d_obs, nullptr, P->st);
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+  cudaFree(partial);
+  plan_free(plan);
+}
+
+__global__ void dense_model_kernel(ModelDev md, int t, double* M) {
+  const int s = md.s;
+  const int64_t total = (int64_t)s * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % s), j = (int)(e / s);
+    double v = 0.0;
+    if (md.kind == WC4D_MODEL_STENCIL3) {
+      if (j == (i + s - 1) % s) v += md.c0;
+      if (j == i) v += md.c1;
+      if (j == (i + 1) % s) v += md.c2;
+    } else {
+      const int w = md.lo + md.hi + 1;
+      int o = j - i;
+      if (o > md.hi) o -= s;
+      if (o < -md.lo) o += s;
+      if (o >= -md.lo && o <= md.hi) v = md.bands[((int64_t)(t - 1) * s + i) * w + o + md.lo];
+    }
+    M[e] = v;
+  }
+}
+
+// S[(r0 + i) + (c0 + j) * nS] (+)= alpha * blk[i + j * s] (or its transpose)
+__global__ void place_block_kernel(double* S, int nS, int r0, int c0, const double* blk, int s, double alpha,
+                                   int accumulate, int transpose) {
+  const int64_t total = (int64_t)s * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % s), j = (int)(e / s);
+    const double v = alpha * (transpose ? blk[j + (int64_t)i * s] : blk[e]);
+    double* d = S + (r0 + i) + (int64_t)(c0 + j) * nS;
+    *d = accumulate ? *d + v : v;
+  }
+}
+
+// S[t s + obs[a], t s + obs[b]] += Rinv[a][b] for every time t
+__global__ void place_obs_kernel(double* S, int nS, int s, int N, const int* obs, int p, const double* Rinv) {
+  const int64_t total = (int64_t)(N + 1) * p * p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % p), b = (int)((e / p) % p), t = (int)(e / ((int64_t)p * p));
+    S[(t * s + obs[a]) + (int64_t)(t * s + obs[b]) * nS] += Rinv[a + (int64_t)b * p];
+  }
+}
+
+// Exact negative Schur complement S = L^T D^{-1} L + H^T R^{-1} H (Sec. 2.2),
+// assembled densely: diagonal blocks D_t^{-1} + M_{t+1}^T D_{t+1}^{-1} M_{t+1}
+// + H^T R^{-1} H, off-diagonal blocks -M_{t+1}^T D_{t+1}^{-1} and transpose.
+static void build_exact_schur(wc4d_problem* P, double* S, const double* WB, const double* WQ, const double* WR) {
+  const int s = P->s, N = P->N, p = P->p, nS = P->nS;
+  const int nbk = std::min<int64_t>(((int64_t)nS * nS + 255) / 256, 152 * 16);
+  double* Binv = P->alloc<double>((int64_t)s * s);
+  double* Qinv = P->alloc<double>((int64_t)s * s);
+  double* Rinv = P->alloc<double>((int64_t)p * p);
+  double* M = P->alloc<double>((int64_t)s * s);
+  double* G = P->alloc<double>((int64_t)s * s);
+  double* MG = P->alloc<double>((int64_t)s * s);
+  gemm_once(P, WB, s, WB, s, s, s, s, Binv, s, EPI_STORE);   // W^T W = B^{-1}
+  gemm_once(P, WQ, s, WQ, s, s, s, s, Qinv, s, EPI_STORE);
+  gemm_once(P, WR, p, WR, p, p, p, p, Rinv, p, EPI_STORE);
+  launch_fill_d(S, 0.0, (int64_t)nS * nS, P->st);
+  for (int t = 0; t <= N; ++t) {
+    const double* Dinv = (t == 0) ? Binv : Qinv;
+    place_block_kernel<<<nbk, 256, 0, P->st>>>(S, nS, t * s, t * s, Dinv, s, 1.0, 1, 0);
+    WC4D_LAUNCH_CHECK();
+  }
+  for (int t = 1; t <= N; ++t) {
+    dense_model_kernel<<<nbk, 256, 0, P->st>>>(P->md, t, M);
+    WC4D_LAUNCH_CHECK();
+    gemm_once(P, Qinv, s, M, s, s, s, s, G, s, EPI_STORE);   // G = D_t^{-1} M_t
+    gemm_once(P, M, s, G, s, s, s, s, MG, s, EPI_STORE);     // M_t^T D_t^{-1} M_t
+    place_block_kernel<<<nbk, 256, 0, P->st>>>(S, nS, (t - 1) * s, (t - 1) * s, MG, s, 1.0, 1, 0);
+    WC4D_LAUNCH_CHECK();
+    place_block_kernel<<<nbk, 256, 0, P->st>>>(S, nS, t * s, (t - 1) * s, G, s, -1.0, 0, 0);
+    WC4D_LAUNCH_CHECK();
+    place_block_kernel<<<nbk, 256, 0, P->st>>>(S, nS, (t - 1) * s, t * s, G, s, -1.0, 0, 1);
+    WC4D_LAUNCH_CHECK();
+  }
+  place_obs_kernel<<<nbk, 256, 0, P->st>>>(S, nS, s, N, P->d_obs, p, Rinv);
+  WC4D_LAUNCH_CHECK();
+  launch_symmetrize(S, nS, P->st);
+}
+
+static void read_diag_minmax(const double* A, int m, int lim, cudaStream_t st, double& lo, double& hi) {
+  std::vector<double> h((size_t)m * m);
+  WC4D_CUDA(cudaMemcpyAsync(h.data(), A, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  WC4D_CUDA(cudaStreamSynchronize(st));
+  lo = INFINITY;
+  hi = -INFINITY;
+  for (int i = 0; i < lim; ++i) {
+    lo = std::min(lo, h[(size_t)i * m + i]);
+    hi = std::max(hi, h[(size_t)i * m + i]);
+  }
+}
+
+// Rhat (Sec. 5): copy of R, its diagonal, Alg. 1 or Alg. 2.
+static void build_rhat(wc4d_problem* P, double* scratch, int* d_count) {
+  const int p = P->p;
+  double* Rh = P->d_Rhat;
+  launch_copy_d(Rh, P->f64.R, (int64_t)p * p, P->st);
+  const int rh = P->o.rhat;
+  if (rh == WC4D_RHAT_EXACT) return;
+  if (rh == WC4D_RHAT_DIAG) {
+    launch_keep_diag(Rh, p, P->st);
+    return;
+  }
+  // eigen-decomposition of R by cyclic Jacobi on an even-sized copy; an odd p
+  // is padded with one decoupled diagonal entry inside the spectrum (the mean
+  // eigenvalue), which neither changes lambda_min/lambda_max nor R_ME's block.
+  const int m = (p % 2 == 0) ? p : p + 1;
+  double* A = P->alloc<double>((int64_t)m * m);
+  double* Vv = P->alloc<double>((int64_t)m * m);
+  double* rot = P->alloc<double>((int64_t)2 * m);
+  launch_fill_d(A, 0.0, (int64_t)m * m, P->st);
+  WC4D_CUDA(cudaMemcpy2DAsync(A, sizeof(double) * m, P->f64.R, sizeof(double) * p, sizeof(double) * p, p,
+                              cudaMemcpyDeviceToDevice, P->st));
+  if (m != p) {
+    std::vector<double> h((size_t)p * p);
+    WC4D_CUDA(cudaMemcpyAsync(h.data(), P->f64.R, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, P->st));
+    WC4D_CUDA(cudaStreamSynchronize(P->st));
+    double tr = 0;
+    for (int i = 0; i < p; ++i) tr += h[(size_t)i * p + i];
+    launch_add_diag(A + (int64_t)p * m + p, 1, m, nullptr, tr / p, P->st);
+  }
+  jacobi_eigh(A, Vv, m, P->st, rot, d_count, 40);
+  double lmin, lmax;
+  read_diag_minmax(A, m, p, P->st, lmin, lmax);
+  const double kap = P->o.kappa_max;
+  if (rh == WC4D_RHAT_RR) {
+    // Alg. 1: gamma = (lambda_max - lambda_min kappa_max) / (kappa_max - 1), >= 0
+    double gamma = (lmax - lmin * kap) / (kap - 1.0);
+    if (gamma < 0.0) gamma = 0.0;
+    P->rhat_param = gamma;
+    launch_add_diag(Rh, p, p, nullptr, gamma, P->st);
+    return;
+  }
+  // Alg. 2: T = lambda_max / kappa_max; eigenvalues <= T are raised to T
+  const double T = lmax / kap;
+  P->rhat_param = T;
+  if (T <= lmin) return;
+  double* U = P->alloc<double>((int64_t)m * m);
+  launch_me_scale(A, Vv, m, T, U, nullptr, P->st);
+  double* C = P->alloc<double>((int64_t)m * m);
+  gemm_once(P, U, m, U, m, m, m, m, C, m, EPI_STORE);  // U^T U = V diag(max(lambda,T)) V^T
+  WC4D_CUDA(cudaMemcpy2DAsync(Rh, sizeof(double) * p, C, sizeof(double) * m, sizeof(double) * p, p,
+                              cudaMemcpyDeviceToDevice, P->st));
+  launch_symmetrize(Rh, p, P->st);
+  (void)scratch;
+}
+
+static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
+  WC4D_CHECK(d && o, WC4D_ERR_ARG, "null descriptor or options");
+  WC4D_CHECK(d->s >= 2 && d->N >= 0 && d->p >= 1 && d->p <= d->s, WC4D_ERR_ARG, "need s >= 2, N >= 0, 1 <= p <= s");
+  WC4D_CHECK(d->mem_kind == WC4D_MEM_HOST || d->mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
+  WC4D_CHECK(d->obs_idx != nullptr, WC4D_ERR_ARG, "obs_idx is null");
+  WC4D_CHECK(d->model_kind == WC4D_MODEL_STENCIL3 || d->model_kind == WC4D_MODEL_BANDED, WC4D_ERR_ARG,
+             "bad model_kind");
+  if (d->model_kind == WC4D_MODEL_BANDED) {
+    WC4D_CHECK(d->band_lo >= 0 && d->band_hi >= 0 && d->band_lo + d->band_hi + 1 <= d->s, WC4D_ERR_ARG,
+               "band offsets must satisfy lo, hi >= 0 and lo + hi + 1 <= s");
+    WC4D_CHECK(d->N == 0 || d->bands != nullptr, WC4D_ERR_ARG, "bands is null");
+  }
+  WC4D_CHECK(d->cov_kind == WC4D_COV_DENSE || d->cov_kind == WC4D_COV_SOAR, WC4D_ERR_ARG, "bad cov_kind");
+  if (d->cov_kind == WC4D_COV_DENSE)
+    WC4D_CHECK(d->B && d->Q && d->R, WC4D_ERR_ARG, "dense covariances missing");
+  else
+    WC4D_CHECK(d->soar_b[1] > 0 && d->soar_q[1] > 0 && d->soar_r[1] > 0 && d->soar_b[0] > 0 && d->soar_q[0] > 0 &&
+                   d->soar_r[0] > 0,
+               WC4D_ERR_ARG, "SOAR variances and lengths must be positive");
+  WC4D_CHECK(o->precond == WC4D_PRECOND_PD || o->precond == WC4D_PRECOND_PI, WC4D_ERR_ARG, "bad precond");
+  WC4D_CHECK(o->k >= 1 && o->k <= d->N + 1, WC4D_ERR_ARG, "k must lie in [1, N+1]");
+  WC4D_CHECK(o->rhat >= WC4D_RHAT_EXACT && o->rhat <= WC4D_RHAT_DIAG, WC4D_ERR_ARG, "bad rhat");
+  WC4D_CHECK(o->rhat == WC4D_RHAT_EXACT || o->rhat == WC4D_RHAT_DIAG || o->kappa_max > 1.0, WC4D_ERR_ARG,
+             "kappa_max must exceed 1");
+  WC4D_CHECK(o->shat == WC4D_SHAT_PAPER || o->shat == WC4D_SHAT_EXACT, WC4D_ERR_ARG, "bad shat");
+  WC4D_CHECK(o->shat == WC4D_SHAT_PAPER || (int64_t)d->s * (d->N + 1) <= 8192, WC4D_ERR_ARG,
+             "exact Schur complement limited to s(N+1) <= 8192");
+  WC4D_CHECK(o->dhat == WC4D_DHAT_EXACT || o->dhat == WC4D_DHAT_SHIFT, WC4D_ERR_ARG, "bad dhat");
+  WC4D_CHECK(o->krylov >= WC4D_KRYLOV_MINRES && o->krylov <= WC4D_KRYLOV_FGMRES, WC4D_ERR_ARG, "bad krylov");
+  WC4D_CHECK(!(o->krylov == WC4D_KRYLOV_MINRES && o->precond != WC4D_PRECOND_PD), WC4D_ERR_ARG,
+             "MINRES needs the SPD block-diagonal preconditioner P_D");
+  WC4D_CHECK(o->tol > 0 && o->maxit >= 1 && o->maxit <= 100000, WC4D_ERR_ARG, "need tol > 0, 1 <= maxit <= 1e5");
+  WC4D_CHECK(o->krylov == WC4D_KRYLOV_MINRES || o->maxit <= 2000, WC4D_ERR_ARG,
+             "GMRES/FGMRES without restarts keep maxit <= 2000 (Hessenberg column in shared memory)");
+  WC4D_CHECK(o->precision == WC4D_PREC_FP64, WC4D_ERR_ARG, "precision mode not available in this build");
+}
+
+static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
+  validate(d, o);
+  P->o = *o;
+  if (P->o.check_every <= 0) P->o.check_every = 4;
+  const int s = d->s, N = d->N, p = d->p;
+  P->s = s;
+  P->N = N;
+  P->p = p;
+  P->ns = (int64_t)(N + 1) * s;
+  P->np = (int64_t)(N + 1) * p;
+  P->n = 2 * P->ns + P->np;
+  cudaStream_t st = P->st;
+  int* d_flag = P->alloc<int>(4);
+  WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * 4, st));
+  // observation operator
+  P->d_obs = P->alloc<int>(p);
+  P->d_inv = P->alloc<int>(s);
+  copy_in(P->d_obs, d->obs_idx, sizeof(int) * p, d->mem_kind, st);
+  launch_check_obs(P->d_obs, p, s, d_flag, st);
+  WC4D_CHECK(read_flag(d_flag, st) == 0, WC4D_ERR_ARG, "obs_idx must be strictly increasing in [0, s)");
+  launch_inv_map(P->d_obs, p, P->d_inv, s, st);
+  // model
+  P->md.kind = d->model_kind;
+  P->md.s = s;
+  P->md.N = N;
+  P->md.c0 = d->stencil[0];
+  P->md.c1 = d->stencil[1];
+  P->md.c2 = d->stencil[2];
+  if (d->model_kind == WC4D_MODEL_BANDED) {
+    const int w = d->band_lo + d->band_hi + 1;
+    P->d_bands = P->alloc<double>((int64_t)N * s * w);
+    if (N > 0) copy_in(P->d_bands, d->bands, sizeof(double) * (size_t)N * s * w, d->mem_kind, st);
+    P->md.bands = P->d_bands;
+    P->md.lo = d->band_lo;
+    P->md.hi = d->band_hi;
+    launch_check_finite(P->d_bands, (int64_t)N * s * w, d_flag + 1, st);
+  }
+  // covariances
+  OpSet<double>& f = P->f64;
+  f.B = P->alloc<double>((int64_t)s * s);
+  f.Q = P->alloc<double>((int64_t)s * s);
+  f.R = P->alloc<double>((int64_t)p * p);
+  if (d->cov_kind == WC4D_COV_DENSE) {
+    copy_in(f.B, d->B, sizeof(double) * (size_t)s * s, d->mem_kind, st);
+    copy_in(f.Q, d->Q, sizeof(double) * (size_t)s * s, d->mem_kind, st);
+    copy_in(f.R, d->R, sizeof(double) * (size_t)p * p, d->mem_kind, st);
+  } else {
+    launch_soar_fill(f.B, s, nullptr, s, d->soar_b[0], d->soar_b[1], st);
+    launch_soar_fill(f.Q, s, nullptr, s, d->soar_q[0], d->soar_q[1], st);
+    launch_soar_fill(f.R, p, P->d_obs, s, d->soar_r[0], d->soar_r[1], st);
+  }
+  launch_check_finite(f.B, (int64_t)s * s, d_flag + 1, st);
+  launch_check_finite(f.Q, (int64_t)s * s, d_flag + 1, st);
+  launch_check_finite(f.R, (int64_t)p * p, d_flag + 1, st);
+  {
+    int h[2];
+    WC4D_CUDA(cudaMemcpyAsync(h, d_flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    WC4D_CUDA(cudaStreamSynchronize(st));
+    WC4D_CHECK(h[1] == 0, WC4D_ERR_NONFINITE, "non-finite entries in the model or covariance inputs");
+  }
+  const int mmax = std::max(s, p);
+  double* scratch = P->alloc<double>((int64_t)mmax * 64 + 64 * 64 * 2);
+  double* work = P->alloc<double>((int64_t)mmax * mmax);
+  // Rhat and its inverse factor
+  P->d_Rhat = P->alloc<double>((int64_t)p * p);
+  build_rhat(P, scratch, d_flag + 2);
+  f.WR = P->alloc<double>((int64_t)p * p);
+  f.WRt = P->alloc<double>((int64_t)p * p);
+  launch_copy_d(work, P->d_Rhat, (int64_t)p * p, st);
+  factor_inverse(P, work, p, f.WR, f.WRt, d_flag + 3, scratch, "Rhat");
+  // Dhat factors (P_D only)
+  P->have_pd = (o->precond == WC4D_PRECOND_PD);
+  if (P->have_pd) {
+    const double delta = (o->dhat == WC4D_DHAT_SHIFT) ? o->dhat_delta : 0.0;
+    f.WB = P->alloc<double>((int64_t)s * s);
+    f.WBt = P->alloc<double>((int64_t)s * s);
+    f.WQ = P->alloc<double>((int64_t)s * s);
+    f.WQt = P->alloc<double>((int64_t)s * s);
+    launch_copy_d(work, f.B, (int64_t)s * s, st);
+    if (delta != 0.0) launch_add_diag(work, s, s, nullptr, delta, st);
+    factor_inverse(P, work, s, f.WB, f.WBt, d_flag + 3, scratch, "Bhat");
+    launch_copy_d(work, f.Q, (int64_t)s * s, st);
+    if (delta != 0.0) launch_add_diag(work, s, s, nullptr, delta, st);
+    factor_inverse(P, work, s, f.WQ, f.WQt, d_flag + 3, scratch, "Qhat");
+    if (o->shat == WC4D_SHAT_EXACT) {
+      // S uses the exact D and R (Sec. 2.2): factors of B, Q, R themselves
+      double *eB = f.WB, *eQ = f.WQ, *eR = f.WR;
+      if (delta != 0.0 || o->rhat != WC4D_RHAT_EXACT) {
+        double* tmpt = P->alloc<double>((int64_t)mmax * mmax);
+        eB = P->alloc<double>((int64_t)s * s);
+        eQ = P->alloc<double>((int64_t)s * s);
+        eR = P->alloc<double>((int64_t)p * p);
+        launch_copy_d(work, f.B, (int64_t)s * s, st);
+        factor_inverse(P, work, s, eB, tmpt, d_flag + 3, scratch, "B");
+        launch_copy_d(work, f.Q, (int64_t)s * s, st);
+        factor_inverse(P, work, s, eQ, tmpt, d_flag + 3, scratch, "Q");
+        launch_copy_d(work, f.R, (int64_t)p * p, st);
+        factor_inverse(P, work, p, eR, tmpt, d_flag + 3, scratch, "R");
+      }
+      P->nS = s * (N + 1);
+      const int nS = P->nS;
+      double* S = P->alloc<double>((int64_t)nS * nS);
+      build_exact_schur(P, S, eB, eQ, eR);
+      f.WS = P->alloc<double>((int64_t)nS * nS);
+      f.WSt = P->alloc<double>((int64_t)nS * nS);
+      double* sscr = P->alloc<double>((int64_t)nS * 64 + 64 * 64 * 2);
+      factor_inverse(P, S, nS, f.WS, f.WSt, d_flag + 3, sscr, "S");
+    }
+  }
+  // GEMM schedules
+  const int C = max_gemm_ctas();
+  plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}, {p, p, N + 1, TRI_FULL}}, C);
+  if (P->have_pd) {
+    if (o->shat == WC4D_SHAT_EXACT) {
+      plan_build(P->plan_pd1, {{s, s, 1, TRI_LOWER}, {s, s, N, TRI_LOWER}, {p, p, N + 1, TRI_LOWER},
+                               {P->nS, P->nS, 1, TRI_LOWER}}, C);
+      plan_build(P->plan_pd2, {{s, s, 1, TRI_UPPER}, {s, s, N, TRI_UPPER}, {p, p, N + 1, TRI_UPPER},
+                               {P->nS, P->nS, 1, TRI_UPPER}}, C);
+    } else {
+      plan_build(P->plan_pd1, {{s, s, 1, TRI_LOWER}, {s, s, N, TRI_LOWER}, {p, p, N + 1, TRI_LOWER},
+                               {s, s, N, TRI_FULL}}, C);
+      plan_build(P->plan_pd2, {{s, s, 1, TRI_UPPER}, {s, s, N, TRI_UPPER}, {p, p, N + 1, TRI_UPPER},
+                               {s, s, 1, TRI_FULL}}, C);
+    }
+  }
+  plan_build(P->plan_pi1, {{p, p, N + 1, TRI_LOWER}, {s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C);
+  plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C);
+  int slots = std::max({P->plan_A.nslots, P->plan_pd1.nslots, P->plan_pd2.nslots, P->plan_pi1.nslots,
+                        P->plan_pi2.nslots, 1});
+  f.partial = P->alloc<double>((int64_t)slots * GEMM_BM * GEMM_BN);
+  f.t1 = P->alloc<double>(P->n);
+  f.t2 = P->alloc<double>(P->n);
+  f.t3 = P->alloc<double>(P->n);
+  // Krylov workspace
+  const int64_t n = P->n;
+  P->maxit = o->maxit;
+  const int64_t nvec = (o->krylov == WC4D_KRYLOV_MINRES) ? 12 : (int64_t)o->maxit + 1;
+  P->V = P->alloc<double>(nvec * n);
+  if (o->krylov != WC4D_KRYLOV_MINRES) P->Z = P->alloc<double>((int64_t)o->maxit * n);
+  const int ldh = o->maxit + 1;
+  P->H = P->alloc<double>((int64_t)ldh * o->maxit);
+  P->cs = P->alloc<double>(o->maxit + 1);
+  P->sn = P->alloc<double>(o->maxit + 1);
+  P->g = P->alloc<double>(o->maxit + 2);
+  P->y = P->alloc<double>(o->maxit + 1);
+  P->h1 = P->alloc<double>(o->maxit + 2);
+  P->h2 = P->alloc<double>(o->maxit + 2);
+  P->hnext = P->alloc<double>(2);
+  P->bnorm = P->alloc<double>(2);
+  P->scal = P->alloc<double>(8);
+  P->part = P->alloc<double>((int64_t)DOT_BLOCKS * (o->maxit + 2));
+  P->part2 = P->alloc<double>(DOT_BLOCKS);
+  P->part3 = P->alloc<double>(DOT_BLOCKS);
+  P->sc = P->alloc<double>(2 * MS_COUNT);
+  P->rhs = P->alloc<double>(n);
+  P->x = P->alloc<double>(n);
+  P->r = P->alloc<double>(n);
+  P->x0 = P->alloc<double>(n);
+  P->stat = P->alloc<DevStatus>(1);
+  WC4D_CUDA(cudaMallocHost(&P->h_stat, sizeof(DevStatus)));
+  WC4D_CUDA(cudaMallocHost(&P->h_scal, sizeof(double) * 8));
+  WC4D_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------ solves
+static void fetch_stat(wc4d_problem* P) {
+  WC4D_CUDA(cudaMemcpyAsync(P->h_stat, P->stat, sizeof(DevStatus), cudaMemcpyDeviceToHost, P->st));
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+}
+
+// ||rhs - A x|| / ||rhs|| in FP64, read back to the host
+static double true_relres(wc4d_problem* P, const double* rhs, const double* x) {
+  apply_A<double>(P, P->f64, P->plan_A, x, P->r, nullptr);
+  vec_sub(rhs, P->r, P->r, P->n, P->st);
+  dot_partial<double>(P->r, P->r, P->n, P->part3, nullptr, P->st);
+  dot_finish(P->part3, P->scal + 1, 1, P->st);
+  WC4D_CUDA(cudaMemcpyAsync(P->h_scal, P->scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, P->st));
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+  const double bn = P->h_scal[0];
+  return P->h_scal[1] / (bn > 0 ? bn : 1.0);
+}
+
+static void resume_after_false_stop(wc4d_problem* P, double est, double relres) {
+  P->h_stat->done = 0;
+  P->h_stat->tol_est = est * (P->o.tol / relres) * 0.5;
+  WC4D_CUDA(cudaMemcpyAsync(P->stat, P->h_stat, sizeof(DevStatus), cudaMemcpyHostToDevice, P->st));
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+}
+
+static int solve_minres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
+  const int64_t n = P->n;
+  double* Vb[3] = {P->V, P->V + n, P->V + 2 * n};
+  double* Zb[2] = {P->V + 3 * n, P->V + 4 * n};
+  double* Wb[3] = {P->V + 5 * n, P->V + 6 * n, P->V + 7 * n};
+  double* Az = P->V + 8 * n;
+  const int* done = &P->stat->done;
+  cudaStream_t st = P->st;
+  // rhs norm
+  dot_partial<double>(P->rhs, P->rhs, n, P->part3, nullptr, st);
+  dot_finish(P->part3, P->scal, 1, st);
+  WC4D_CUDA(cudaMemsetAsync(Vb[0], 0, sizeof(double) * n, st));
+  WC4D_CUDA(cudaMemsetAsync(Wb[0], 0, sizeof(double) * n, st));
+  WC4D_CUDA(cudaMemsetAsync(Wb[1], 0, sizeof(double) * n, st));
+  int64_t nA = 0, nP = 0;
+  if (use_x0) {
+    apply_A<double>(P, P->f64, P->plan_A, P->x, Az, nullptr);
+    vec_sub(P->rhs, Az, Vb[1], n, st);
+    ++nA;
+  } else {
+    WC4D_CUDA(cudaMemsetAsync(P->x, 0, sizeof(double) * n, st));
+    launch_copy_d(Vb[1], P->rhs, n, st);
+  }
+  apply_P<double>(P, WC4D_PRECOND_PD, P->f64, Vb[1], Zb[0], nullptr);
+  ++nP;
+  dot_partial<double>(Zb[0], Vb[1], n, P->part2, nullptr, st);
+  minres_init(P->part2, P->sc, P->stat, P->o.tol, st);
+  int it = 0;  // completed iterations
+  int status = WC4D_OK;
+  double relres = 1.0;
+  bool converged = false;
+  fetch_stat(P);
+  if (P->h_stat->done) {
+    status = P->h_stat->status;
+    converged = (status == 0);
+  }
+  while (!converged && status == WC4D_OK) {
+    const int batch = std::min(P->o.check_every, P->maxit - it);
+    if (batch <= 0) break;
+    for (int b = 0; b < batch; ++b) {
+      const int j = it + b;
+      double* v_old = Vb[j % 3];
+      double* v = Vb[(j + 1) % 3];
+      double* v_new = Vb[(j + 2) % 3];
+      double* z = Zb[j % 2];
+      double* z_new = Zb[(j + 1) % 2];
+      double* w_old = Wb[j % 3];
+      double* w = Wb[(j + 1) % 3];
+      double* w_new = Wb[(j + 2) % 3];
+      double* sc_in = P->sc + (j % 2) * MS_COUNT;
+      double* sc_out = P->sc + ((j + 1) % 2) * MS_COUNT;
+      apply_A<double>(P, P->f64, P->plan_A, z, Az, done);
+      dot_partial<double>(Az, z, n, P->part, done, st);
+      minres_v_update(P->part, sc_in, Az, v, v_old, v_new, n, done, st);
+      apply_P<double>(P, WC4D_PRECOND_PD, P->f64, v_new, z_new, done);
+      dot_partial<double>(z_new, v_new, n, P->part2, done, st);
+      minres_update(P->part, P->part2, sc_in, sc_out, z, w_old, w, w_new, P->x, n, P->stat, st);
+    }
+    fetch_stat(P);
+    it = P->h_stat->iters;
+    if (P->h_stat->status != 0) {
+      status = P->h_stat->status;
+      break;
+    }
+    if (P->h_stat->done) {
+      relres = true_relres(P, P->rhs, P->x);
+      ++nA;
+      if (relres <= P->o.tol || P->h_stat->est == 0.0) {
+        converged = true;
+        break;
+      }
+      // C12: the recurrence estimate met the tolerance but the true FP64
+      // residual did not; tighten the estimate threshold and continue.
+      resume_after_false_stop(P, P->h_stat->est, relres);
+    } else if (it >= P->maxit) {
+      break;
+    }
+  }
+  nA += it;
+  nP += it;
+  if (!converged) {
+    relres = true_relres(P, P->rhs, P->x);
+    ++nA;
+    if (status == WC4D_OK) status = (relres <= P->o.tol) ? WC4D_OK : WC4D_ERR_MAXIT;
+  }
+  if (info) {
+    info->iters = it;
+    info->relres_true = relres;
+    info->relres_est = P->h_stat->est;
+    info->n_apply_A = nA;
+    info->n_apply_P = nP;
+  }
+  return status;
+}
+
+static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
+  const int64_t n = P->n;
+  const int ldh = P->maxit + 1;
+  cudaStream_t st = P->st;
+  const int* done = &P->stat->done;
+  const int which = P->o.precond;
+  double* x0 = use_x0 ? P->x0 : nullptr;  // kept for the final combination
+  int64_t nA = 0, nP = 0;
+  dot_partial<double>(P->rhs, P->rhs, n, P->part3, nullptr, st);
+  dot_finish(P->part3, P->scal, 1, st);
+  WC4D_CUDA(cudaMemcpyAsync(P->bnorm, P->scal, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double* r0 = P->V + n;  // V[1] is free until the first Arnoldi step
+  if (use_x0) {
+    launch_copy_d(x0, P->x, n, st);
+    apply_A<double>(P, P->f64, P->plan_A, x0, r0, nullptr);
+    vec_sub(P->rhs, r0, r0, n, st);
+    ++nA;
+  } else {
+    launch_copy_d(r0, P->rhs, n, st);
+  }
+  dot_partial<double>(r0, r0, n, P->part2, nullptr, st);
+  gm_init<double>(r0, P->part2, P->V, P->g, P->stat, P->o.tol, n, st);
+  WC4D_CUDA(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)ldh * P->maxit, st));
+  int it = 0;
+  int status = WC4D_OK;
+  double relres = 1.0;
+  bool converged = false;
+  fetch_stat(P);
+  if (P->h_stat->done) {
+    status = P->h_stat->status;
+    if (status == 0) {
+      converged = true;
+      relres = 0.0;
+      launch_copy_d(P->x, use_x0 ? x0 : P->x, n, st);
+      if (!use_x0) WC4D_CUDA(cudaMemsetAsync(P->x, 0, sizeof(double) * n, st));
+    }
+  }
+  bool need_normalize = false;
+  while (!converged && status == WC4D_OK) {
+    const int batch = std::min(P->o.check_every, P->maxit - it);
+    if (batch <= 0) break;
+    if (need_normalize) {
+      gm_normalize<double>(P->V + (int64_t)it * n, P->hnext, P->V + (int64_t)it * n, n, nullptr, st);
+      need_normalize = false;
+    }
+    for (int b = 0; b < batch; ++b) {
+      const int j = it + b;
+      double* vj = P->V + (int64_t)j * n;
+      double* zj = P->Z + (int64_t)j * n;
+      double* w = P->V + (int64_t)(j + 1) * n;
+      apply_P<double>(P, which, P->f64, vj, zj, done);
+      apply_A<double>(P, P->f64, P->plan_A, zj, w, done);
+      gm_mdot<double>(P->V, n, j + 1, w, n, P->part, done, st);
+      gm_mdot_reduce(P->part, j + 1, P->h1, done, st);
+      gm_mupdate<double>(P->V, n, j + 1, P->h1, w, n, done, st);
+      gm_mdot<double>(P->V, n, j + 1, w, n, P->part, done, st);
+      gm_mdot_reduce(P->part, j + 1, P->h2, done, st);
+      gm_mupdate<double>(P->V, n, j + 1, P->h2, w, n, done, st);
+      dot_partial<double>(w, w, n, P->part2, done, st);
+      gm_hessenberg(j, P->h1, P->h2, P->part2, P->H, ldh, P->cs, P->sn, P->g, P->hnext, P->stat, P->bnorm, st);
+      gm_normalize<double>(w, P->hnext, w, n, done, st);
+    }
+    fetch_stat(P);
+    it = P->h_stat->iters;
+    if (P->h_stat->status != 0) {
+      status = P->h_stat->status;
+      break;
+    }
+    if (P->h_stat->done || it >= P->maxit) {
+      gm_solve_y(P->H, ldh, P->g, it, P->y, st);
+      gm_combine<double, double>(P->Z, n, it, P->y, x0, P->x, n, st);
+      relres = true_relres(P, P->rhs, P->x);
+      ++nA;
+      if (relres <= P->o.tol) {
+        converged = true;
+        break;
+      }
+      if (it >= P->maxit) break;
+      double hn = 0;
+      WC4D_CUDA(cudaMemcpy(&hn, P->hnext, sizeof(double), cudaMemcpyDeviceToHost));
+      if (hn == 0.0) {
+        status = WC4D_ERR_BREAKDOWN;
+        break;
+      }
+      resume_after_false_stop(P, P->h_stat->est, relres);
+      need_normalize = true;
+    }
+  }
+  nA += it;
+  nP += it;
+  if (!converged && status == WC4D_OK) status = WC4D_ERR_MAXIT;
+  if (info) {
+    info->iters = it;
+    info->relres_true = relres;
+    info->relres_est = P->h_stat->est;
+    info->n_apply_A = nA;
+    info->n_apply_P = nP;
+  }
+  return status;
+}
+
+// d_t[r] = traj_t[obs[r]] + E[r + t p]
+__global__ void obs_rhs_kernel(const double* traj, const double* E, const int* obs, int s, int p, int N, double* d) {
+  const int64_t total = (int64_t)(N + 1) * p;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / p), r = (int)(e % p);
+    d[e] = traj[(int64_t)t * s + obs[r]] + E[e];
+  }
+}
+
+static void synthesize_rhs(wc4d_problem* P, const double* zb_in, const double* zr_in, int mem_kind, double* rhs_out) {
+  WC4D_CHECK(P->md.kind == WC4D_MODEL_STENCIL3, WC4D_ERR_ARG, "synthesize_rhs needs a linear (STENCIL3) model");
+  const int s = P->s, p = P->p, N = P->N;
+  cudaStream_t st = P->st;
+  const int mmax = std::max(s, p);
+  std::vector<void*> tmp;
+  auto dalloc = [&](int64_t cnt) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(double) * (size_t)std::max<int64_t>(cnt, 1)) != cudaSuccess)
+      throw Error{WC4D_ERR_NOMEM, "cudaMalloc failed in synthesize_rhs"};
+    tmp.push_back(q);
+    return (double*)q;
+  };
+  try {
+    double* zb = dalloc(s);
+    double* zr = dalloc(P->np);
+    copy_in(zb, zb_in, sizeof(double) * s, mem_kind, st);
+    copy_in(zr, zr_in, sizeof(double) * P->np, mem_kind, st);
+    double* work = dalloc((int64_t)mmax * mmax);
+    double* Lt = dalloc((int64_t)mmax * mmax);
+    double* scratch = dalloc((int64_t)mmax * 64 + 64 * 64 * 2);
+    int* info = (int*)dalloc(1);
+    double* rhs = dalloc(P->n);
+    WC4D_CUDA(cudaMemsetAsync(rhs, 0, sizeof(double) * P->n, st));
+    // u = chol(B) z_b, then the background-minus-truth trajectory M^t (-u)
+    launch_copy_d(work, P->f64.B, (int64_t)s * s, st);
+    WC4D_CUDA(cudaMemsetAsync(info, 0, sizeof(int), st));
+    cholesky(work, s, info, st, scratch);
+    WC4D_CHECK(read_flag(info, st) == 0, WC4D_ERR_NOT_SPD, "Cholesky of B failed");
+    launch_transpose(work, Lt, s, st);
+    double* traj = dalloc(P->ns);
+    WC4D_CUDA(cudaMemsetAsync(traj, 0, sizeof(double) * P->ns, st));
+    gemm_once(P, Lt, s, zb, s, s, s, 1, traj, s, EPI_NEG_STORE);
+    lhat_sweep<double>(P->md, N + 1, traj, traj, false, false, nullptr, st);
+    // E = chol(R) Z_r
+    launch_copy_d(work, P->f64.R, (int64_t)p * p, st);
+    WC4D_CUDA(cudaMemsetAsync(info, 0, sizeof(int), st));
+    cholesky(work, p, info, st, scratch);
+    WC4D_CHECK(read_flag(info, st) == 0, WC4D_ERR_NOT_SPD, "Cholesky of R failed");
+    launch_transpose(work, Lt, p, st);
+    double* E = dalloc(P->np);
+    gemm_once(P, Lt, p, zr, p, p, p, N + 1, E, p, EPI_STORE);
+    const int nb = (int)std::min<int64_t>((P->np + 255) / 256, 152 * 8);
+    obs_rhs_kernel<<<nb, 256, 0, st>>>(traj, E, P->d_obs, s, p, N, rhs + P->ns);
+    WC4D_LAUNCH_CHECK();
+    WC4D_CUDA(cudaMemcpyAsync(rhs_out, rhs, sizeof(double) * P->n,
+                              mem_kind == WC4D_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    WC4D_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    for (void* q : tmp) cudaFree(q);
+    throw;
+  }
+  for (void* q : tmp) cudaFree(q);
+}
+
+}  // namespace wc4d
+
+// ================================================================ C ABI
+#define WC4D_API_BEGIN try {
+#define WC4D_API_END                                   \
+  }                                                    \
+  catch (const wc4d::Error& e) {                       \
+    wc4d::set_error(e.msg);                            \
+    return e.code;                                     \
+  }                                                    \
+  catch (const std::exception& e) {                    \
+    wc4d::set_error(std::string("exception: ") + e.what()); \
+    return WC4D_ERR_CUDA;                              \
+  }                                                    \
+  catch (...) {                                        \
+    wc4d::set_error("unknown exception");              \
+    return WC4D_ERR_CUDA;                              \
+  }
+
+extern "C" {
+
+void wc4d_default_opts(wc4d_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precond = WC4D_PRECOND_PI;
+  o->k = 1;
+  o->rhat = WC4D_RHAT_EXACT;
+  o->kappa_max = 100.0;
+  o->shat = WC4D_SHAT_PAPER;
+  o->dhat = WC4D_DHAT_EXACT;
+  o->dhat_delta = 0.01;
+  o->krylov = WC4D_KRYLOV_GMRES;
+  o->tol = 1e-6;
+  o->maxit = 1000;
+  o->precision = WC4D_PREC_FP64;
+  o->inner_iters = 20;
+  o->check_every = 4;
+}
+
+int wc4d_setup_problem(const wc4d_problem_desc* desc, const wc4d_solve_opts* opts, void* cuda_stream,
+                       wc4d_problem** out) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(out != nullptr, WC4D_ERR_ARG, "out is null");
+  *out = nullptr;
+  wc4d_problem* P = new wc4d_problem();
+  P->st = (cudaStream_t)cuda_stream;
+  try {
+    setup(P, desc, opts);
+  } catch (...) {
+    cudaStreamSynchronize(P->st);
+    delete P;
+    throw;
+  }
+  *out = P;
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+int wc4d_apply_saddle(wc4d_problem* P, const double* v, double* out) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && v && out, WC4D_ERR_ARG, "null argument");
+  apply_A<double>(P, P->f64, P->plan_A, v, out, nullptr);
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+int wc4d_apply_precond(wc4d_problem* P, int32_t which, const double* v, double* out) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && v && out, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(which == WC4D_PRECOND_PD || which == WC4D_PRECOND_PI, WC4D_ERR_ARG, "bad preconditioner");
+  WC4D_CHECK(which == WC4D_PRECOND_PI || P->have_pd, WC4D_ERR_ARG,
+             "P_D needs a problem set up with precond = PD (Dhat factors)");
+  apply_P<double>(P, which, P->f64, v, out, nullptr);
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, int32_t mem_kind, wc4d_info* info) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && rhs && x, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(mem_kind == WC4D_MEM_HOST || mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t bytes = sizeof(double) * (size_t)P->n;
+  const cudaMemcpyKind kin = mem_kind == WC4D_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = mem_kind == WC4D_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  WC4D_CUDA(cudaMemcpyAsync(P->rhs, rhs, bytes, kin, P->st));
+  if (use_x0) WC4D_CUDA(cudaMemcpyAsync(P->x, x, bytes, kin, P->st));
+  wc4d_info loc{};
+  int status;
+  if (P->o.krylov == WC4D_KRYLOV_MINRES)
+    status = solve_minres(P, &loc, use_x0 != 0);
+  else
+    status = solve_gmres(P, &loc, use_x0 != 0);
+  WC4D_CUDA(cudaMemcpyAsync(x, P->x, bytes, kout, P->st));
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+  loc.status = status;
+  loc.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = loc;
+  if (status != WC4D_OK) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "solve ended with status %d after %d iterations (true relres %.3e)", status, loc.iters,
+             loc.relres_true);
+    wc4d::set_error(buf);
+  }
+  return status;
+  WC4D_API_END
+}
+
+int wc4d_synthesize_rhs(wc4d_problem* P, const double* z_b, const double* z_r, int32_t mem_kind, double* rhs) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && z_b && z_r && rhs, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(mem_kind == WC4D_MEM_HOST || mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
+  wc4d::synthesize_rhs(P, z_b, z_r, mem_kind, rhs);
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+int wc4d_problem_dims(const wc4d_problem* P, int64_t* n, int32_t* s, int32_t* N, int32_t* p) {
+  if (!P) return WC4D_ERR_ARG;
+  if (n) *n = P->n;
+  if (s) *s = P->s;
+  if (N) *N = P->N;
+  if (p) *p = P->p;
+  return WC4D_OK;
+}
+
+int wc4d_get_matrix(wc4d_problem* P, int32_t which, double* dst) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && dst, WC4D_ERR_ARG, "null argument");
+  const double* src = nullptr;
+  int64_t cnt = 0;
+  switch (which) {
+    case 0: src = P->f64.B; cnt = (int64_t)P->s * P->s; break;
+    case 1: src = P->f64.Q; cnt = (int64_t)P->s * P->s; break;
+    case 2: src = P->f64.R; cnt = (int64_t)P->p * P->p; break;
+    case 3: src = P->d_Rhat; cnt = (int64_t)P->p * P->p; break;
+    default: throw wc4d::Error{WC4D_ERR_ARG, "which must be 0..3"};
+  }
+  WC4D_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, P->st));
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+double wc4d_rhat_param(const wc4d_problem* P) { return P ? P->rhat_param : 0.0; }
+
+void wc4d_destroy(wc4d_problem* P) {
+  if (!P) return;
+  cudaStreamSynchronize(P->st);
+  delete P;
+}
+
+const char* wc4d_last_error(void) { return wc4d::g_last_error.c_str(); }
+
+}  // extern "C"

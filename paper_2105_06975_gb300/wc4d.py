@@ -1,0 +1,357 @@
+"""Python binding of the wc4d C ABI (``include/wc4d.h``).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+The library must be built (``paper_2105_06975_gb300.build.build()``); loading
+fails loudly when it is missing -- there is no CPU fallback.
+
+Functions keep the C names (``wc4d_setup_problem``, ``wc4d_apply_saddle``,
+``wc4d_apply_precond``, ``wc4d_solve`` ...).  ``Problem`` is a small helper
+that builds the descriptor from numpy arrays or workload parameters and
+passes torch tensors' device pointers and the current torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------- constants
+WC4D_OK = 0
+WC4D_ERR_ARG = 1
+WC4D_ERR_NOT_SPD = 2
+WC4D_ERR_NONFINITE = 3
+WC4D_ERR_BREAKDOWN = 4
+WC4D_ERR_MAXIT = 5
+WC4D_ERR_TIMEOUT = 6
+WC4D_ERR_CUDA = 7
+WC4D_ERR_NOMEM = 8
+
+WC4D_MODEL_STENCIL3 = 0
+WC4D_MODEL_BANDED = 1
+WC4D_COV_DENSE = 0
+WC4D_COV_SOAR = 1
+WC4D_MEM_HOST = 0
+WC4D_MEM_DEVICE = 1
+WC4D_PRECOND_PD = 0
+WC4D_PRECOND_PI = 1
+WC4D_RHAT_EXACT = 0
+WC4D_RHAT_RR = 1
+WC4D_RHAT_ME = 2
+WC4D_RHAT_DIAG = 3
+WC4D_SHAT_PAPER = 0
+WC4D_SHAT_EXACT = 1
+WC4D_DHAT_EXACT = 0
+WC4D_DHAT_SHIFT = 1
+WC4D_KRYLOV_MINRES = 0
+WC4D_KRYLOV_GMRES = 1
+WC4D_KRYLOV_FGMRES = 2
+WC4D_PREC_FP64 = 0
+WC4D_PREC_MIXED = 1
+
+RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG}
+PRECOND = {"PD": WC4D_PRECOND_PD, "PI": WC4D_PRECOND_PI}
+KRYLOV = {"minres": WC4D_KRYLOV_MINRES, "gmres": WC4D_KRYLOV_GMRES, "fgmres": WC4D_KRYLOV_FGMRES}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32), ("N", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("model_kind", ctypes.c_int32), ("stencil", ctypes.c_double * 3),
+                ("band_lo", ctypes.c_int32), ("band_hi", ctypes.c_int32), ("bands", ctypes.c_void_p),
+                ("obs_idx", ctypes.c_void_p), ("cov_kind", ctypes.c_int32),
+                ("B", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("soar_b", ctypes.c_double * 2), ("soar_q", ctypes.c_double * 2), ("soar_r", ctypes.c_double * 2),
+                ("mem_kind", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int32), ("k", ctypes.c_int32), ("rhat", ctypes.c_int32),
+                ("kappa_max", ctypes.c_double), ("shat", ctypes.c_int32), ("dhat", ctypes.c_int32),
+                ("dhat_delta", ctypes.c_double), ("krylov", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int32), ("precision", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("check_every", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double), ("ms", ctypes.c_double),
+                ("n_apply_A", ctypes.c_int64), ("n_apply_P", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("gemm_launches", ctypes.c_int64), ("orth_ms", ctypes.c_double), ("orth_bytes", ctypes.c_double),
+                ("orth_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# names and signatures of every entry point declared in include/wc4d.h
+SIGNATURES = {
+    "wc4d_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
+    "wc4d_setup_problem": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolveOpts), ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "wc4d_apply_saddle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "wc4d_apply_precond": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "wc4d_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.POINTER(Info)]),
+    "wc4d_synthesize_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_void_p]),
+    "wc4d_problem_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), _ip, _ip, _ip]),
+    "wc4d_get_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "wc4d_rhat_param": (ctypes.c_double, [ctypes.c_void_p]),
+    "wc4d_set_profiling": (None, [ctypes.c_int32]),
+    "wc4d_reset_stats": (None, []),
+    "wc4d_get_stats": (ctypes.c_int, [ctypes.POINTER(Stats)]),
+    "wc4d_destroy": (None, [ctypes.c_void_p]),
+    "wc4d_last_error": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libwc4d.so (building it first if allowed).  Raises if it cannot."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"wc4d CUDA library not built: {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class WC4DError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"wc4d error {code}: {msg}")
+        self.code = code
+
+
+def _check(code):
+    if code != WC4D_OK:
+        raise WC4DError(code, load().wc4d_last_error().decode())
+    return code
+
+
+# ------------------------------------------------------------ thin wrappers
+def wc4d_default_opts() -> SolveOpts:
+    o = SolveOpts()
+    load().wc4d_default_opts(ctypes.byref(o))
+    return o
+
+
+def wc4d_setup_problem(desc: ProblemDesc, opts: SolveOpts, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().wc4d_setup_problem(ctypes.byref(desc), ctypes.byref(opts), ctypes.c_void_p(stream),
+                                     ctypes.byref(h)))
+    return h
+
+
+def wc4d_apply_saddle(h, v_ptr: int, out_ptr: int) -> None:
+    _check(load().wc4d_apply_saddle(h, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)))
+
+
+def wc4d_apply_precond(h, which: int, v_ptr: int, out_ptr: int) -> None:
+    _check(load().wc4d_apply_precond(h, which, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)))
+
+
+def wc4d_solve(h, rhs_ptr: int, x_ptr: int, use_x0: bool, mem_kind: int, raise_on_error=True) -> Info:
+    info = Info()
+    code = load().wc4d_solve(h, ctypes.c_void_p(rhs_ptr), ctypes.c_void_p(x_ptr), int(use_x0), mem_kind,
+                             ctypes.byref(info))
+    if raise_on_error and code not in (WC4D_OK, WC4D_ERR_MAXIT):
+        _check(code)
+    info.status = code
+    return info
+
+
+def wc4d_synthesize_rhs(h, zb_ptr: int, zr_ptr: int, mem_kind: int, rhs_ptr: int) -> None:
+    _check(load().wc4d_synthesize_rhs(h, ctypes.c_void_p(zb_ptr), ctypes.c_void_p(zr_ptr), mem_kind,
+                                      ctypes.c_void_p(rhs_ptr)))
+
+
+def wc4d_problem_dims(h):
+    n = ctypes.c_int64()
+    s, N, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().wc4d_problem_dims(h, ctypes.byref(n), ctypes.byref(s), ctypes.byref(N), ctypes.byref(p)))
+    return n.value, s.value, N.value, p.value
+
+
+def wc4d_get_matrix(h, which: int, dst_ptr: int) -> None:
+    _check(load().wc4d_get_matrix(h, which, ctypes.c_void_p(dst_ptr)))
+
+
+def wc4d_rhat_param(h) -> float:
+    return load().wc4d_rhat_param(h)
+
+
+def wc4d_set_profiling(enable: bool) -> None:
+    load().wc4d_set_profiling(int(bool(enable)))
+
+
+def wc4d_reset_stats() -> None:
+    load().wc4d_reset_stats()
+
+
+def wc4d_get_stats() -> Stats:
+    st = Stats()
+    _check(load().wc4d_get_stats(ctypes.byref(st)))
+    return st
+
+
+def wc4d_destroy(h) -> None:
+    load().wc4d_destroy(h)
+
+
+def wc4d_last_error() -> str:
+    return load().wc4d_last_error().decode()
+
+
+# -------------------------------------------------------------- convenience
+def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dhat="exact", dhat_delta=0.01,
+              krylov=None, tol=1e-6, maxit=1000, precision="fp64", inner_iters=20, check_every=4) -> SolveOpts:
+    o = wc4d_default_opts()
+    o.precond = PRECOND[precond]
+    o.k = int(k)
+    o.rhat = RHAT[rhat]
+    o.kappa_max = float(kappa_max)
+    o.shat = WC4D_SHAT_EXACT if shat == "exact" else WC4D_SHAT_PAPER
+    o.dhat = WC4D_DHAT_SHIFT if dhat in ("rr", "shift") else WC4D_DHAT_EXACT
+    o.dhat_delta = float(dhat_delta)
+    if krylov is None:
+        krylov = "minres" if precond == "PD" else "gmres"
+    o.krylov = KRYLOV[krylov]
+    o.tol = float(tol)
+    o.maxit = int(maxit)
+    o.precision = WC4D_PREC_MIXED if precision == "mixed" else WC4D_PREC_FP64
+    o.inner_iters = int(inner_iters)
+    o.check_every = int(check_every)
+    return o
+
+
+class Problem:
+    """Owns a wc4d problem handle.  Host arrays are passed with mem_kind=HOST
+    and copied by the library; the handle is freed by ``close()``/``__del__``."""
+
+    def __init__(self, s, N, p, obs_idx, opts: SolveOpts, *, stencil=None, bands=None, band_lo=0, band_hi=0,
+                 B=None, Q=None, R=None, soar_b=None, soar_q=None, soar_r=None, stream: Optional[int] = None):
+        import torch
+        d = ProblemDesc()
+        d.s, d.N, d.p = int(s), int(N), int(p)
+        keep = []
+
+        def host(a, dtype):
+            a = np.ascontiguousarray(a, dtype=dtype)
+            keep.append(a)
+            return a.ctypes.data
+        d.obs_idx = host(obs_idx, np.int32)
+        if bands is not None:
+            d.model_kind = WC4D_MODEL_BANDED
+            d.bands = host(bands, np.float64)
+            d.band_lo, d.band_hi = int(band_lo), int(band_hi)
+        else:
+            d.model_kind = WC4D_MODEL_STENCIL3
+            d.stencil[:] = [float(c) for c in stencil]
+        if B is not None:
+            d.cov_kind = WC4D_COV_DENSE
+            # column-major == row-major for the symmetric covariances
+            d.B, d.Q, d.R = host(B, np.float64), host(Q, np.float64), host(R, np.float64)
+        else:
+            d.cov_kind = WC4D_COV_SOAR
+            d.soar_b[:] = list(soar_b)
+            d.soar_q[:] = list(soar_q)
+            d.soar_r[:] = list(soar_r)
+        d.mem_kind = WC4D_MEM_HOST
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.opts = opts
+        self.h = wc4d_setup_problem(d, opts, stream)
+        self.n, self.s, self.N, self.p = wc4d_problem_dims(self.h)
+
+    @classmethod
+    def from_workload(cls, w, dr, opts: SolveOpts, dense=False, **kw):
+        """Build from a ``workload.Workload`` and its draws; SOAR covariances
+        are generated by the library unless ``dense`` arrays are given in kw."""
+        c = w.stencil()
+        if dense:
+            return cls(w.s, w.N, w.p, dr.obs_idx, opts, stencil=c, **kw)
+        return cls(w.s, w.N, w.p, dr.obs_idx, opts, stencil=kw.pop("stencil", c), soar_b=w.soar_b,
+                   soar_q=w.soar_q, soar_r=w.soar_r, **kw)
+
+    def apply_saddle(self, v, out=None):
+        import torch
+        out = torch.empty_like(v) if out is None else out
+        wc4d_apply_saddle(self.h, v.data_ptr(), out.data_ptr())
+        return out
+
+    def apply_precond(self, which, v, out=None):
+        import torch
+        out = torch.empty_like(v) if out is None else out
+        wc4d_apply_precond(self.h, PRECOND[which] if isinstance(which, str) else which, v.data_ptr(),
+                           out.data_ptr())
+        return out
+
+    def solve(self, rhs, x=None, use_x0=False):
+        """rhs/x: torch CUDA tensors (device path) or numpy arrays (host path)."""
+        if isinstance(rhs, np.ndarray):
+            rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+            x = np.zeros_like(rhs) if x is None else x
+            info = wc4d_solve(self.h, rhs.ctypes.data, x.ctypes.data, use_x0, WC4D_MEM_HOST)
+            return x, info
+        import torch
+        x = torch.zeros_like(rhs) if x is None else x
+        info = wc4d_solve(self.h, rhs.data_ptr(), x.data_ptr(), use_x0, WC4D_MEM_DEVICE)
+        return x, info
+
+    def synthesize_rhs(self, dr):
+        """Device-built (b, d, 0) from the draws' z_b, z_r (linear models)."""
+        import torch
+        zb = torch.from_numpy(np.ascontiguousarray(dr.z_b, dtype=np.float64)).cuda()
+        zr = torch.from_numpy(np.ascontiguousarray(dr.z_r, dtype=np.float64)).cuda()
+        rhs = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        wc4d_synthesize_rhs(self.h, zb.data_ptr(), zr.data_ptr(), WC4D_MEM_DEVICE, rhs.data_ptr())
+        return rhs
+
+    def matrix(self, which):
+        import torch
+        m = self.s if which in (0, 1) else self.p
+        out = torch.empty((m, m), dtype=torch.float64, device="cuda")
+        wc4d_get_matrix(self.h, which, out.data_ptr())
+        return out
+
+    def rhat_param(self):
+        return wc4d_rhat_param(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            wc4d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,307 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Every case feeds both sides the same seeded inputs.  Tolerances (FP64 mode):
+  * covariances, A v:                      1e-12 relative (2-norm)
+  * P_I^{-1} v, P_D^{-1} v:                1e-9 relative (the library applies
+    Dhat^{-1}, Rhat^{-1} through explicit inverse Cholesky factors; their error
+    grows like kappa(L) eps, with kappa(L) = kappa(B)^{1/2} ~ 1e3 here)
+  * solves:                                x within 1e-8 of dense LU when both
+    are driven to 1e-12; true residual <= tol with the oracle's operator.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2105_06975_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2105_06975_gb300 import wc4d as L  # noqa: E402
+from oracle import covariance as cov, model as mdl, problem as prb, saddle as sd  # noqa: E402
+
+DEV = "cuda"
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def case(s, N, p=None, obs="random", seed=0, base=W.TINY):
+    w = W.small(base, s=s, N=N, p=p).with_(obs=obs)
+    return w, W.draws(w, seed)
+
+
+def popts(kind="PI", k=1, rhat="exact", shat="paper", dhat="exact", kappa=100.0):
+    return sd.PrecondOptions(kind=kind, k=k, rhat=rhat, shat=shat, dhat=dhat, kappa_max=kappa)
+
+
+def gpu_problem(w, dr, prob=None, precond="PI", k=1, rhat="exact", shat="paper", dhat="exact", kappa=100.0,
+                krylov=None, tol=1e-6, maxit=1000, dense=False, banded=None):
+    o = L.make_opts(precond=precond, k=k, rhat=rhat, kappa_max=kappa, shat=shat, dhat=dhat, krylov=krylov, tol=tol,
+                    maxit=maxit)
+    kw = {}
+    if dense:
+        kw.update(B=prob.B, Q=prob.Q, R=prob.R)
+    if banded is not None:
+        bands, lo, hi = banded
+        kw.update(bands=bands, band_lo=lo, band_hi=hi)
+        return L.Problem(w.s, w.N, w.p, dr.obs_idx, o, B=prob.B, Q=prob.Q, R=prob.R, **kw)
+    return L.Problem.from_workload(w, dr, o, dense=dense, **kw)
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+# ------------------------------------------------------------ covariances
+@pytest.mark.parametrize("s,N,p", [(100, 3, 50), (203, 2, 77)])
+def test_soar_matrices(s, N, p):
+    w, dr = case(s, N, p)
+    prob = prb.linear_problem(w, dr)
+    G = gpu_problem(w, dr)
+    for which, ref in ((0, prob.B), (1, prob.Q), (2, prob.R)):
+        got = G.matrix(which).cpu().numpy()
+        assert rel(got, ref) < 1e-13, which
+    G.close()
+
+
+# ------------------------------------------------------------------- A v
+@pytest.mark.parametrize("s,N,p,obs", [(100, 10, 50, "even"), (203, 5, 77, "random"), (64, 0, 64, "even"),
+                                       (70, 3, 1, "random"), (130, 7, 130, "even")])
+def test_apply_saddle(s, N, p, obs):
+    w, dr = case(s, N, p, obs)
+    prob = prb.linear_problem(w, dr)
+    G = gpu_problem(w, dr)
+    for seed in (1, 2):
+        v = W.random_vector(prob.n, seed)
+        got = G.apply_saddle(to_dev(v)).cpu().numpy()
+        ref = prob.A_apply(v)
+        assert rel(got, ref) < 1e-12
+    G.close()
+
+
+def banded_case(s=90, N=4, p=45, lo=5, hi=3, seed=3, scale=0.3):
+    w, dr = case(s, N, p, "random", seed=seed)
+    g = np.random.default_rng(seed)
+    bands = scale * g.standard_normal((N, s, lo + hi + 1))
+    B, Q, R = prb.covariances(w, dr.obs_idx)
+    prob = sd.Problem(s, N, p, mdl.BandedModel(bands, lo, hi), np.asarray(dr.obs_idx), B, Q, R)
+    return w, dr, prob, (bands, lo, hi)
+
+
+def test_apply_saddle_banded_model():
+    w, dr, prob, bd = banded_case()
+    G = gpu_problem(w, dr, prob, banded=bd)
+    v = W.random_vector(prob.n, 5)
+    assert rel(G.apply_saddle(to_dev(v)).cpu().numpy(), prob.A_apply(v)) < 1e-12
+    for kind in ("PI",):
+        for k in (1, 2, 5):
+            G2 = gpu_problem(w, dr, prob, precond=kind, k=k, banded=bd)
+            P = sd.Preconditioner(prob, popts(kind, k))
+            assert rel(G2.apply_precond(kind, to_dev(v)).cpu().numpy(), P.apply(v)) < 1e-9
+            G2.close()
+    G.close()
+
+
+# ----------------------------------------------------------------- P^{-1} v
+@pytest.mark.parametrize("kind", ["PD", "PI"])
+@pytest.mark.parametrize("rhat", ["exact", "rr", "me", "diag"])
+def test_apply_precond(kind, rhat):
+    w, dr = case(120, 5, 61, "random")
+    prob = prb.linear_problem(w, dr)
+    v = W.random_vector(prob.n, 7)
+    for k in (1, 2, 6):
+        G = gpu_problem(w, dr, precond=kind, k=k, rhat=rhat)
+        P = sd.Preconditioner(prob, popts(kind, k, rhat))
+        got = G.apply_precond(kind, to_dev(v)).cpu().numpy()
+        ref = P.apply(v)
+        assert rel(got, ref) < 1e-9, (kind, rhat, k, rel(got, ref))
+        if rhat in ("rr", "me"):
+            Rh = G.matrix(3).cpu().numpy()
+            assert rel(Rh, P.Rhat) < 1e-10
+            lam = np.linalg.eigvalsh(prob.R)
+            if rhat == "rr":
+                assert G.rhat_param() == pytest.approx(cov.ridge_gamma(lam[0], lam[-1], 100.0), rel=1e-9)
+            else:
+                assert G.rhat_param() == pytest.approx(lam[-1] / 100.0, rel=1e-10)
+        G.close()
+
+
+def test_apply_precond_exact_schur_and_shifted_dhat():
+    w, dr = case(40, 3, 20, "even")
+    prob = prb.linear_problem(w, dr)
+    v = W.random_vector(prob.n, 9)
+    for kw in (dict(shat="exact"), dict(dhat="rr"), dict(shat="exact", rhat="rr")):
+        G = gpu_problem(w, dr, precond="PD", k=2, **kw)
+        P = sd.Preconditioner(prob, popts("PD", 2, kw.get("rhat", "exact"), kw.get("shat", "paper"),
+                                          kw.get("dhat", "exact")))
+        got = G.apply_precond("PD", to_dev(v)).cpu().numpy()
+        assert rel(got, P.apply(v)) < 1e-8, kw
+        G.close()
+
+
+def test_synthesize_rhs_matches_oracle():
+    """The device-built first-loop right-hand side (b, d, 0) equals the
+    oracle's (truth, background and observations of the linear workload)."""
+    for w, seed in ((W.TINY, 0), (W.small(W.SCALE, s=256, N=12, p=100), 3)):
+        dr = W.draws(w, seed)
+        prob, obs, rhs = prb.linear_case(w, dr)
+        G = gpu_problem(w, dr)
+        got = G.synthesize_rhs(dr).cpu().numpy()
+        assert rel(got, rhs) < 1e-11
+        assert np.all(got[:prob.s * (prob.N + 1)] == 0) and np.all(got[-prob.s * (prob.N + 1):] == 0)
+        G.close()
+
+
+# -------------------------------------------------------------------- solves
+def test_tiny_config_mgw_minres_vs_lu():
+    """Plain method on the tiny advection-diffusion workload: P_D with exact
+    D, R and Schur complement; MINRES stops within a handful of iterations and
+    matches dense LU."""
+    w = W.TINY
+    dr = W.draws(w, 0)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    x_lu = sd.dense_solve(prob, rhs)
+    G = gpu_problem(w, dr, precond="PD", shat="exact", krylov="minres", tol=1e-12, maxit=50)
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == 0 and info.iters <= 5
+    assert rel(x.cpu().numpy(), x_lu) < 1e-8
+    G.close()
+
+
+@pytest.mark.parametrize("kind,krylov,k,rhat", [("PD", "minres", 3, "exact"), ("PI", "gmres", 3, "rr"),
+                                               ("PI", "gmres", 1, "exact"), ("PD", "gmres", 7, "me")])
+def test_small_solves_match_lu_and_oracle_iterations(kind, krylov, k, rhat):
+    w, dr = case(64, 6, 32, "random", seed=4)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    x_lu = sd.dense_solve(prob, rhs)
+    G = gpu_problem(w, dr, precond=kind, k=k, rhat=rhat, krylov=krylov, tol=1e-11, maxit=2000)
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == 0, L.wc4d_last_error()
+    assert rel(x.cpu().numpy(), x_lu) < 1e-6
+    G.close()
+    # at the paper's tolerance the iteration counts agree with the oracle's
+    G = gpu_problem(w, dr, precond=kind, k=k, rhat=rhat, krylov=krylov, tol=1e-6, maxit=1000)
+    x, info = G.solve(to_dev(rhs))
+    P = sd.Preconditioner(prob, popts(kind, k, rhat))
+    from oracle import krylov as kr
+    ref = (kr.minres if krylov == "minres" else kr.gmres)(prob.A_apply, P.apply, rhs, tol=1e-6)
+    # the true-residual acceptance near 1e-6 may add a few iterations on
+    # either side (rounding differs; the GPU re-checks on a tightened estimate)
+    assert abs(info.iters - ref.iters) <= 2 + 0.05 * ref.iters, (info.iters, ref.iters)
+    r = rhs - prob.A_apply(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-6
+    G.close()
+
+
+def test_host_and_device_paths_agree_and_x0():
+    w, dr = case(96, 4, 48, "random", seed=5)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    G = gpu_problem(w, dr, precond="PI", k=5)
+    xd, i1 = G.solve(to_dev(rhs))
+    xh, i2 = G.solve(rhs.copy())
+    assert np.array_equal(xd.cpu().numpy(), xh)
+    assert i1.iters == i2.iters
+    # restarting from the converged solution stops immediately
+    x2, i3 = G.solve(to_dev(rhs), x=xd.clone(), use_x0=True)
+    assert i3.iters <= 2 and i3.relres_true <= 1e-6
+    G.close()
+
+
+def test_banded_model_solve():
+    w, dr, prob, bd = banded_case(s=80, N=5, p=40, lo=3, hi=2, seed=8, scale=0.12)
+    rhs = W.random_vector(prob.n, 11)
+    x_lu = sd.dense_solve(prob, rhs)
+    G = gpu_problem(w, dr, prob, precond="PI", k=3, banded=bd, tol=1e-10, maxit=1000)
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == 0
+    assert rel(x.cpu().numpy(), x_lu) < 1e-6
+    G.close()
+
+
+# -------------------------------------------------------------------- errors
+def test_argument_and_numerical_errors():
+    w, dr = case(40, 3, 20, "even")
+    prob = prb.linear_problem(w, dr)
+    with pytest.raises(L.WC4DError) as e:
+        gpu_problem(w, dr, k=0)
+    assert e.value.code == L.WC4D_ERR_ARG
+    bad = W.Draws(**{**dr.__dict__, "obs_idx": dr.obs_idx[::-1].copy()})
+    with pytest.raises(L.WC4DError) as e:
+        gpu_problem(w, bad)
+    assert e.value.code == L.WC4D_ERR_ARG
+    o = L.make_opts(precond="PD")
+    Bneg = prob.B.copy()
+    Bneg[0, 0] = -1.0
+    with pytest.raises(L.WC4DError) as e:
+        L.Problem(w.s, w.N, w.p, dr.obs_idx, o, stencil=w.stencil(), B=Bneg, Q=prob.Q, R=prob.R)
+    assert e.value.code == L.WC4D_ERR_NOT_SPD
+    Bnan = prob.B.copy()
+    Bnan[3, 4] = np.nan
+    with pytest.raises(L.WC4DError) as e:
+        L.Problem(w.s, w.N, w.p, dr.obs_idx, o, stencil=w.stencil(), B=Bnan, Q=prob.Q, R=prob.R)
+    assert e.value.code == L.WC4D_ERR_NONFINITE
+    G = gpu_problem(w, dr, precond="PI")
+    v = to_dev(W.random_vector(prob.n, 1))
+    with pytest.raises(L.WC4DError) as e:
+        G.apply_precond("PD", v)
+    assert e.value.code == L.WC4D_ERR_ARG
+    with pytest.raises(L.WC4DError):
+        L.make_opts(precond="PI", krylov="minres") and gpu_problem(w, dr, precond="PI", krylov="minres")
+    G.close()
+
+
+def test_maxit_reports_status_and_last_iterate():
+    w, dr = case(64, 6, 32, "random")
+    prob, obs, rhs = prb.linear_case(w, dr)
+    G = gpu_problem(w, dr, precond="PI", k=1, maxit=5)
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == L.WC4D_ERR_MAXIT and info.iters == 5
+    r = rhs - prob.A_apply(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(rhs) == pytest.approx(info.relres_true, rel=1e-9)
+    G.close()
+
+
+# ------------------------------------------------------ full-size workload
+@pytest.mark.slow
+def test_scale_workload_operators_and_solve():
+    """s=2048, N=64, p=1024 (n = 332,800), in the launch configuration the
+    benchmark uses.
+
+    * SOAR matrices built on the GPU agree with the oracle's entry by entry.
+    * A v agrees to 1e-12 (with the oracle's own matrices passed in, and with
+      the GPU-built ones).
+    * P_I^{-1} v agrees to 1e-7.  kappa(R) = 2.6e9 and kappa(Q) = 5.6e9 here:
+      two backward-stable FP64 Cholesky factorisations of the same R (the
+      library's blocked one and LAPACK's) give R^{-1} v that differ by up to
+      kappa(R) eps ~ 3e-7, and a 1e-16 relative perturbation of R's entries
+      alone moves R^{-1} v by 1.5e-8 (measured with the oracle).  With the same
+      factor, explicit inverse factors and triangular solves agree to 6e-14.
+    * A solve meets the 1e-6 relative residual with the oracle's operator.
+    """
+    w = W.SCALE
+    dr = W.draws(w, 0)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    v = W.random_vector(prob.n, 3)
+    P = sd.Preconditioner(prob, popts("PI", 4))
+    Av, Pv = prob.A_apply(v), P.apply(v)
+    Gd = gpu_problem(w, dr, prob, precond="PI", k=4, dense=True)
+    assert rel(Gd.apply_saddle(to_dev(v)).cpu().numpy(), Av) < 1e-12
+    assert rel(Gd.apply_precond("PI", to_dev(v)).cpu().numpy(), Pv) < 1e-7
+    Gd.close()
+    G = gpu_problem(w, dr, precond="PI", k=4)
+    for which, ref in ((0, prob.B), (1, prob.Q), (2, prob.R)):
+        assert rel(G.matrix(which).cpu().numpy(), ref) < 1e-13
+    assert rel(G.apply_saddle(to_dev(v)).cpu().numpy(), Av) < 1e-12
+    assert rel(G.apply_precond("PI", to_dev(v)).cpu().numpy(), Pv) < 1e-7
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == 0
+    r = rhs - prob.A_apply(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-6
+    G.close()
