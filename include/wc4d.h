@@ -214,6 +214,37 @@ void wc4d_set_profiling(int32_t enable);
 void wc4d_reset_stats(void);
 int wc4d_get_stats(wc4d_stats* out);
 
+/* A v without any device allocation.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc -- a thread sharing the GPU with a
+ * framework whose caching allocator already holds nearly all device memory,
+ * or a latency-critical loop that cannot pay for cudaMalloc/cudaFree, which may
+ * synchronise the device.  It computes the same product as wc4d_apply_saddle
+ * for a STENCIL3 model (c1 = D v1 + L v3, c2 = R v2 + H v3,
+ * c3 = L^T v1 + H^T v2) from caller-owned device arrays and needs no problem
+ * handle.
+ *   stencil: host, 3 doubles (c0, c1, c2) of the periodic model step;
+ *   obs_idx: device, p strictly increasing indices in [0, s);
+ *   B, Q: device, s x s; R: device, p x p (symmetric, column-major);
+ *   v, out: device, n = (2s+p)(N+1) doubles each, not overlapping;
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream); the call is
+ *   stream-ordered and returns after enqueueing.
+ * Scratch (split-K partial tiles and the inverse observation map) lives in
+ * one 8 MiB file-scope device array that every GPU loading the library keeps
+ * until the process exits.  Limits: s <= 131072 and at most 240 partial
+ * 64x64 tiles, i.e. ceil(s/64)*(1 + ceil(N/64)) + ceil(p/64)*ceil((N+1)/64)
+ * <= 240 (s = 2048, N = 64, p = 1024 needs 96); larger problems return
+ * WC4D_ERR_ARG with a message and launch nothing.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call reuses
+ * the same array and overwrites it (nothing in it needs to start at zero), so
+ * calls that overlap on the GPU -- on different streams, or from different
+ * host threads -- race and must be serialised by the caller.  Observation
+ * indices outside [0, s) are skipped (their c2 rows become NaN); other input
+ * errors are not detected. */
+int wc4d_apply_saddle_noalloc(int32_t s, int32_t N, int32_t p, const double* stencil, const int32_t* obs_idx,
+                              const double* B, const double* Q, const double* R, const double* v, double* out,
+                              void* cuda_stream);
+
 void wc4d_destroy(wc4d_problem* prob);
 const char* wc4d_last_error(void);
 

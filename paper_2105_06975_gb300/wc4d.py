@@ -113,6 +113,10 @@ SIGNATURES = {
     "wc4d_set_profiling": (None, [ctypes.c_int32]),
     "wc4d_reset_stats": (None, []),
     "wc4d_get_stats": (ctypes.c_int, [ctypes.POINTER(Stats)]),
+    "wc4d_apply_saddle_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
     "wc4d_destroy": (None, [ctypes.c_void_p]),
     "wc4d_last_error": (ctypes.c_char_p, []),
 }
@@ -219,6 +223,16 @@ def wc4d_get_stats() -> Stats:
     st = Stats()
     _check(load().wc4d_get_stats(ctypes.byref(st)))
     return st
+
+
+def wc4d_apply_saddle_noalloc(s, N, p, stencil, obs_ptr, B_ptr, Q_ptr, R_ptr, v_ptr, out_ptr, stream=0) -> None:
+    """A v from caller-owned device arrays without any device allocation
+    (see the header for the limits and the shared scratch array)."""
+    c = (ctypes.c_double * 3)(*[float(x) for x in stencil])
+    _check(load().wc4d_apply_saddle_noalloc(int(s), int(N), int(p), c, ctypes.c_void_p(obs_ptr),
+                                            ctypes.c_void_p(B_ptr), ctypes.c_void_p(Q_ptr), ctypes.c_void_p(R_ptr),
+                                            ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr),
+                                            ctypes.c_void_p(stream)))
 
 
 def wc4d_destroy(h) -> None:
