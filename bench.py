@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=20)
     ap.add_argument("--maxit", type=int, default=1000, help="Krylov iteration cap (workspace size)")
+    ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
+    ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
+    ap.add_argument("--chosen", default="df32", choices=["fp64", "df32", "mixed"])
     return ap.parse_args()
 
 
@@ -141,7 +144,7 @@ def oracle_sample(args, w, dr, iters_full, sample_iters):
     return {"value": 1.0 / proj, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"problem build + Rhat factor ({t1 - t0:.2f} s) + {sample_iters} "
                        f"{'MINRES' if args.precond == 'PD' else 'GMRES'} iterations ({t2 - t1:.2f} s) of the same "
-                       f"window; projected to {iters_full} iterations (the GPU solve's count), numpy FP64 on "
+                       f"window; projected to {iters_full} iterations (the FP64 GPU solve's count), numpy FP64 on "
                        f"{os.cpu_count()} host cores"),
             "projected_s_per_solve": proj}
 
@@ -180,6 +183,58 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- GPU
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA: 128/clk/SM (measured 74.4 TF at 1.995 GHz)
+# double-float multiply-add = 13 FP32 instructions (1 FMUL, 3 FFMA, 9 FADD):
+# FP64-equivalent peak of the FP32 pipe = 2 flop x 152 SM x 128 lanes x 2.07 GHz / 13
+DF32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 13 / 1e12
+MODE_DTYPE = {"fp64": "f64", "df32": "df32 products (2 x f32, ~48-bit) / f64 recurrences",
+              "mixed": "f32 inner / df32-f64 outer"}
+MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
+             "df32": "FP64 GMRES; covariance / factor products in double-float on the FP32 pipe",
+             "mixed": "FGMRES outer (double-float A, FP64 true residual) around FP32 inner GMRES({inner}) "
+                      "preconditioned by FP32 {pc}"}
+
+
+def kernel_rows(st, step_ms, hbm):
+    rows = {}
+    if st.gemm_launches:
+        a = st.gemm_flops / (st.gemm_ms * 1e-3) / 1e12
+        rows["gemm_fp64"] = {"kernel": "gemm_streamk_kernel<double> (FP64 covariance / factor products)",
+                             "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": a / FP64_PEAK_TFLOPS, "launches": st.gemm_launches,
+                             "ms_per_launch": st.gemm_ms / st.gemm_launches,
+                             "flops_per_launch": st.gemm_flops / st.gemm_launches,
+                             "share_of_step": st.gemm_ms / step_ms,
+                             "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz"}
+    if st.gemmdf_launches:
+        a = st.gemmdf_flops / (st.gemmdf_ms * 1e-3) / 1e12
+        rows["gemm_df32"] = {"kernel": "gemm_streamk_df32_kernel (double-float covariance / factor products)",
+                             "bound": "alu", "achieved": a, "peak": DF32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": a / DF32_PEAK_TFLOPS, "launches": st.gemmdf_launches,
+                             "ms_per_launch": st.gemmdf_ms / st.gemmdf_launches,
+                             "flops_per_launch": st.gemmdf_flops / st.gemmdf_launches,
+                             "share_of_step": st.gemmdf_ms / step_ms,
+                             "peak_source": "derived: FP32 pipe (152 SM x 128 FMA/clk x 2.07 GHz) / 13 "
+                                            "instructions per double-float multiply-add"}
+    if st.gemm32_launches:
+        a = st.gemm32_flops / (st.gemm32_ms * 1e-3) / 1e12
+        rows["gemm_fp32"] = {"kernel": "gemm_streamk_kernel<float> (FP32 inner-solve products)",
+                             "bound": "alu", "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": a / FP32_PEAK_TFLOPS, "launches": st.gemm32_launches,
+                             "ms_per_launch": st.gemm32_ms / st.gemm32_launches,
+                             "flops_per_launch": st.gemm32_flops / st.gemm32_launches,
+                             "share_of_step": st.gemm32_ms / step_ms,
+                             "peak_source": "derived: 152 SM x 256 FP32 flop/clk x 2.07 GHz"}
+    if st.orth_launches:
+        a = st.orth_bytes / (st.orth_ms * 1e-3) / 1e9
+        rows["orth"] = {"kernel": "gm_mdot/gm_mupdate (Arnoldi CGS2 passes)", "bound": "hbm", "achieved": a,
+                        "peak": hbm, "unit": "GB/s", "frac": (a / hbm) if hbm else None,
+                        "launches": st.orth_launches, "ms_per_launch": st.orth_ms / st.orth_launches,
+                        "bytes_per_launch": st.orth_bytes / st.orth_launches, "share_of_step": st.orth_ms / step_ms,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    return rows
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -196,72 +251,77 @@ def run_gpu(args):
     w = W.SCALE
     seed = args.seed * 1000 + rank
     dr = W.draws(w, seed)
-    opts = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit)
-
-    def build():
-        return wc4d.Problem.from_workload(w, dr, opts, stream=stream.cuda_stream)
-
-    G = build()
+    modes = {
+        "fp64": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit),
+        "df32": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
+                               precision="df32"),
+    }
+    if args.mixed:
+        modes["mixed"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
+                                        maxit=min(args.maxit, 200), precision="mixed", inner_iters=args.inner)
+    G = wc4d.Problem.from_workload(w, dr, modes["fp64"], stream=stream.cuda_stream)
     rhs = G.synthesize_rhs(dr)
     G.close()
     x = torch.zeros(w.n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hbm = peaks().get("hbm_gbs")
 
-    def step():
-        G = build()
+    def step(opts):
+        G = wc4d.Problem.from_workload(w, dr, opts, stream=stream.cuda_stream)
         _, info = G.solve(rhs, x)
         G.close()
         return info
 
-    infos = []
-    for _ in range(args.warmup):
-        infos.append(step())
-    wc4d.wc4d_reset_stats()
-    wc4d.wc4d_set_profiling(True)
+    results = {}
     clk = ClockSampler(local)
     clk.start()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ev = []
-    t_wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        infos.append(step())
-        e1.record(stream)
-        ev.append((e0, e1))
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall0
-    if world > 1:
-        torch.distributed.barrier()
+    for mode, opts in modes.items():
+        for _ in range(args.warmup):
+            step(opts)
+        wc4d.wc4d_reset_stats()
+        wc4d.wc4d_set_profiling(True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev, infos = [], []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(opts))
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wc4d.wc4d_set_profiling(False)
+        st = wc4d.wc4d_get_stats()
+        step_ms = sum(a.elapsed_time(b) for a, b in ev)
+        ms = step_ms / args.steps
+        if world > 1:
+            tt = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
+        results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
+                         "kernels": kernel_rows(st, step_ms, hbm)}
     clocks = clk.stop()
-    wc4d.wc4d_set_profiling(False)
-    st = wc4d.wc4d_get_stats()
-    step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    ms_local = step_ms / args.steps
-    ms = ms_local
-    if world > 1:
-        t = torch.tensor([ms_local], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    timed = infos[args.warmup:]
-    assert all(i.status == 0 for i in timed), [i.as_dict() for i in timed]
-    iters = [i.iters for i in timed]
-    value = world * 1e3 / ms
+    chosen = results[args.chosen]
+    fp64 = results["fp64"]
+    iters = [i.iters for i in chosen["infos"]]
+    inner = [i.inner_iters for i in chosen["infos"]]
 
-    # end to end through the C ABI with host buffers (H2D of the draws and the
-    # right-hand side, D2H of the solution inside the timed region)
+    # end to end through the C ABI with host buffers: H2D of the observation
+    # indices and the right-hand side, D2H of the solution, inside the timing
     rhs_h = rhs.cpu().numpy()
     x_h = np.zeros_like(rhs_h)
     obs_h = np.ascontiguousarray(dr.obs_idx, dtype=np.int32)
-    torch.cuda.synchronize()
     e2e_t = []
     for i in range(max(2, args.steps // 2) + 1):
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Gh = wc4d.Problem(w.s, w.N, w.p, obs_h, opts, stencil=w.stencil(), soar_b=w.soar_b, soar_q=w.soar_q,
-                          soar_r=w.soar_r, stream=stream.cuda_stream)
+        Gh = wc4d.Problem(w.s, w.N, w.p, obs_h, modes[args.chosen], stencil=w.stencil(), soar_b=w.soar_b,
+                          soar_q=w.soar_q, soar_r=w.soar_r, stream=stream.cuda_stream)
         _, info = Gh.solve(rhs_h, x_h)
         Gh.close()
         if i > 0:
@@ -269,39 +329,37 @@ def run_gpu(args):
         assert info.status == 0
     e2e_val = world / statistics.mean(e2e_t)
 
-    gemm_per_launch_ms = st.gemm_ms / max(st.gemm_launches, 1)
-    gemm_flops_per_launch = st.gemm_flops / max(st.gemm_launches, 1)
-    achieved = gemm_flops_per_launch / (gemm_per_launch_ms * 1e-3) / 1e12 if st.gemm_launches else None
-    orth_gbs = (st.orth_bytes / (st.orth_ms * 1e-3) / 1e9) if st.orth_launches else None
-    pk = peaks()
-    hbm = pk.get("hbm_gbs")
+    ks = chosen["kernels"]
+    dom = max(ks.values(), key=lambda r: r["share_of_step"]) if ks else None
+    roof = None
+    if dom is not None:
+        roof = {k: dom[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "peak_source",
+                                    "share_of_step")}
+        roof["traffic"] = None
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "gpu",
-        "config": {**workload_config(args, w), "mode": "FP64 (plain)", "parallelism": f"windows x{world}"},
-        "iterations": {"mean": statistics.mean(iters), "min": min(iters), "max": max(iters)},
-        "relres_true_max": max(i.relres_true for i in timed),
-        "fp64_solves_per_s": value,
-        "roofline": {"kernel": "gemm_streamk_kernel (FP64 covariance products)", "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
-                     "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz",
-                     "launches": st.gemm_launches, "ms_per_launch": gemm_per_launch_ms,
-                     "flops_per_launch": gemm_flops_per_launch,
-                     "share_of_step": st.gemm_ms / step_ms if step_ms else None},
-        "roofline_orth": {"kernel": "gm_mdot/gm_mupdate (Arnoldi CGS2)", "bound": "hbm", "achieved": orth_gbs,
-                          "peak": hbm, "unit": "GB/s", "frac": (orth_gbs / hbm) if (orth_gbs and hbm) else None,
-                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                          "share_of_step": st.orth_ms / step_ms if step_ms else None},
-        "gpu_launches": int(st.launches),
+        "metric": METRIC, "value": chosen["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": chosen["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": MODE_DTYPE[args.chosen], "data": "synthetic", "impl": "gpu",
+        "config": {**workload_config(args, w), "mode": MODE_DESC[args.chosen].format(inner=args.inner, pc=args.precond),
+                   "parallelism": f"windows x{world}"},
+        "iterations": {"mean": statistics.mean(iters), "inner_total_mean": statistics.mean(inner)},
+        "modes": {m: {"solves_per_s": r["value"], "ms_per_step": r["ms"],
+                      "iterations": statistics.mean(i.iters for i in r["infos"])} for m, r in results.items()},
+        "relres_true_max": max(i.relres_true for i in chosen["infos"]),
+        "fp64_solves_per_s": fp64["value"],
+        "chosen_over_fp64": chosen["value"] / fp64["value"],
+        "roofline": roof,
+        "kernels": ks,
+        "kernels_fp64_mode": results["fp64"]["kernels"],
+        "gpu_launches": int(chosen["stats"].launches),
+        "gpu_launches_fp64_mode": int(results["fp64"]["stats"].launches),
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(w.n * 8 + w.p * 4),
                 "d2h_bytes_per_step": int(w.n * 8)},
-        "wall_s_timed": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(args, w, dr, int(round(statistics.mean(iters))), args.cpu_iters)
+        fp64_iters = int(round(line["modes"]["fp64"]["iterations"]))
+        line["cpu_baseline"] = oracle_sample(args, w, dr, fp64_iters, args.cpu_iters)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -79,9 +79,15 @@ enum { WC4D_RHAT_EXACT = 0, WC4D_RHAT_RR = 1,               /* Rhat = R; Alg. 1 
 enum { WC4D_SHAT_PAPER = 0, WC4D_SHAT_EXACT = 1 };          /* Lhat^T D^-1 Lhat ; S (Sec 2.2) */
 enum { WC4D_DHAT_EXACT = 0, WC4D_DHAT_SHIFT = 1 };          /* D ; D + delta I (Sec. 6.1)   */
 enum { WC4D_KRYLOV_MINRES = 0, WC4D_KRYLOV_GMRES = 1, WC4D_KRYLOV_FGMRES = 2 };
-enum { WC4D_PREC_FP64 = 0,        /* every product in FP64                                   */
-       WC4D_PREC_MIXED = 1 };     /* FGMRES(FP64 A) outer, FP32 inner GMRES preconditioned by
-                                     an FP32 copy of the chosen preconditioner (not in the paper) */
+enum { WC4D_PREC_FP64 = 0,        /* every product in native FP64 (DFMA)                       */
+       WC4D_PREC_MIXED = 1,       /* FGMRES outer (FP64-accurate A) around an FP32 inner GMRES
+                                     preconditioned by an FP32 copy of the chosen preconditioner
+                                     (not in the paper)                                         */
+       WC4D_PREC_DF32 = 2 };      /* every covariance / factor product in double-float on the
+                                     FP32 pipe (operands split into two FP32 parts, exact
+                                     product errors, TwoSum accumulation: ~48-bit products);
+                                     recurrences, dots, factorisations and the true residual
+                                     stay FP64 (not in the paper)                               */
 
 typedef struct {
   int32_t s;                 /* state size per time level, >= 2                         */
@@ -170,6 +176,14 @@ int wc4d_apply_precond(wc4d_problem* prob, int32_t which, const double* v, doubl
 int wc4d_solve(wc4d_problem* prob, const double* rhs, double* x, int32_t use_x0,
                int32_t mem_kind, wc4d_info* info);
 
+/* FP32 operators of the mixed-precision mode (not in the paper): out = A v
+ * (which = 0), P_D^{-1} v (which = WC4D_PRECOND_PD + 1) or P_I^{-1} v
+ * (which = WC4D_PRECOND_PI + 1), computed from FP32 copies of the covariances
+ * and inverse factors with FP32 arithmetic (dot products in FP64).  v, out:
+ * device, n floats each, not overlapping.  Needs a problem set up with
+ * precision = WC4D_PREC_MIXED (ARG otherwise).  Stream-ordered, async. */
+int wc4d_apply_fp32(wc4d_problem* prob, int32_t which, const float* v, float* out);
+
 /* Synthetic right-hand side (b, d, 0) of the first outer loop for a
  * STENCIL3 (linear) model, built on the device from standard-normal draws.
  * Follows the data-assimilation setting of Sec. 1 / Sec. 2.1: background
@@ -199,7 +213,8 @@ double wc4d_rhat_param(const wc4d_problem* prob);
  * profiling enabled the library also brackets every launch of its two
  * dominant kernel classes with CUDA events on the launching stream: the
  * stream-K covariance GEMM (work = algorithmic FLOPs: 2 x multiply-adds over
- * the non-zero triangle) and the Arnoldi orthogonalisation passes (work =
+ * the non-zero triangle; FP64 and FP32 instances counted apart) and the
+ * Arnoldi orthogonalisation passes (work =
  * bytes the pass must read and write); launches that exit early on a solve
  * that has already converged are not counted.  wc4d_get_stats synchronises
  * the device.  Not thread-safe across concurrent solves. */
@@ -209,6 +224,10 @@ typedef struct {
   int64_t gemm_launches;
   double orth_ms, orth_bytes;
   int64_t orth_launches;
+  double gemm32_ms, gemm32_flops;
+  int64_t gemm32_launches;
+  double gemmdf_ms, gemmdf_flops;   /* double-float (WC4D_PREC_DF32) products */
+  int64_t gemmdf_launches;
 } wc4d_stats;
 void wc4d_set_profiling(int32_t enable);
 void wc4d_reset_stats(void);

@@ -60,6 +60,8 @@ constexpr int GEMM_MAX_OPS = 4;
 
 enum { TRI_FULL = 0, TRI_LOWER = 1, TRI_UPPER = 2 };  // op(At) lower: k <= i; upper: k >= i
 
+// Ah/Al: the operator split into FP32 high and low parts (At = Ah + Al to
+// 48 bits), used by the double-float ("df32") variant of the FP64 product.
 template <typename T>
 struct GemmOpT {
   const T* At;
@@ -67,11 +69,16 @@ struct GemmOpT {
   const T* X;
   int64_t ldx;
   int m, kdim, ncols, tri;
+  const float* Ah = nullptr;
+  const float* Al = nullptr;
+  const float* Xh = nullptr;  // X split the same way (one pass per launch)
+  const float* Xl = nullptr;
 };
 template <typename T>
 struct GemmOpsT {
   GemmOpT<T> op[GEMM_MAX_OPS];
   int nops;
+  int df32 = 0;  // T = double only: run the products in double-float on the FP32 pipe
 };
 using GemmOp = GemmOpT<double>;
 using GemmOps = GemmOpsT<double>;
@@ -129,14 +136,16 @@ struct GemmPlan {
   double flops = 0;               // 2 * useful multiply-adds
 };
 
-void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas);
+// cost model of the schedule: which product kernel the plan will mostly run
+enum { COST_FP64 = 0, COST_DF32 = 1 };
+void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas, int cost_model = COST_FP64);
 // persistent CTAs for the stream-K GEMM: SMs x resident CTAs per SM
-int gemm_resident_ctas();
+int gemm_resident_ctas(bool df32);
 
 // Opt-in kernel profile: CUDA events around the timed kernel classes on the
 // launching stream; the kernel itself marks whether it did work (launches that
 // exit early on a converged solve do not count).
-enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_CLASSES = 2 };
+enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_GEMM32 = 2, PROF_GEMMDF = 3, PROF_CLASSES = 4 };
 bool prof_enabled();
 // returns a device int* the kernel sets to 1 when it runs (nullptr when off)
 int* prof_begin(int cls, double work, cudaStream_t st);
@@ -156,6 +165,10 @@ void launch_keep_diag(double* A, int m, cudaStream_t st);
 void launch_transpose(const double* A, double* At, int m, cudaStream_t st);
 void launch_symmetrize(double* A, int m, cudaStream_t st);
 void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t st);
+// hi = fl32(a), lo = fl32(a - hi): a = hi + lo to about 48 bits
+void launch_split_df(const double* a, float* hi, float* lo, int64_t n, cudaStream_t st);
+// the same for an m x ncols block with leading dimension ld, written densely (ld = m)
+void launch_split_df_block(const double* a, int64_t ld, int m, int ncols, float* hi, float* lo, cudaStream_t st);
 void launch_inv_map(const int* obs, int p, int* inv, int s, cudaStream_t st);
 void launch_check_obs(const int* obs, int p, int s, int* flag, cudaStream_t st);
 void launch_check_finite(const double* a, int64_t n, int* flag, cudaStream_t st);

@@ -27,7 +27,7 @@ void plan_free(GemmPlan& plan) {
   plan = GemmPlan();
 }
 
-void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas) {
+void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas, int cost_model) {
   plan_free(plan);
   WC4D_CHECK((int)shapes.size() <= GEMM_MAX_OPS, WC4D_ERR_ARG, "too many GEMM ops in one launch");
   plan.nops = (int)shapes.size();
@@ -43,8 +43,9 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
     plan.shape[o] = sh;
     const int rt = (sh.m + GEMM_BM - 1) / GEMM_BM;
     const int ct = std::max(1, (sh.ncols + GEMM_BN - 1) / GEMM_BN);
-    // equal-width column tiles (65 time columns -> 33 + 32, not 64 + 1)
-    const int cw = std::max(1, (sh.ncols + ct - 1) / ct);
+    // full 64-column tiles plus a remainder tile; a one-column remainder (the
+    // 65th time level) runs on the GEMV mapping
+    const int cw = std::min(GEMM_BN, std::max(1, sh.ncols));
     plan.tile_base[o] = (int)tiles.size();
     plan.col_tiles[o] = ct;
     plan.col_width[o] = cw;
@@ -59,9 +60,14 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
         if (sh.tri == TRI_UPPER) klo = std::min(sh.kdim, row0);
         const int cols = std::min(cw, sh.ncols - c * cw);
         const int rows = std::min(GEMM_BM, sh.m - row0);
-        // clocks per k-block: multiply-adds at 2 DFMA/clk/SM plus the tile
-        // load and barriers; a one-column (GEMV) tile is latency-bound
-        const double cost = (cols == 1) ? 2048.0 : 0.5 * GEMM_BM * cols * GEMM_BK + 512.0;
+        // SM clocks per k-block.  FP64: 2 DFMA/clk/SM; double-float: 13 FP32
+        // instructions per multiply-add at 128 lanes/clk/SM.  A one-column
+        // (GEMV) tile is bound by its tile load and barriers; a partial tile
+        // of 2..48 columns runs the predicated path at about full-tile cost.
+        const double per_col = (cost_model == COST_DF32) ? GEMM_BM * GEMM_BK * 13.0 / 128.0 : 0.5 * GEMM_BM * GEMM_BK;
+        const double load = (cost_model == COST_DF32) ? 600.0 : 512.0;
+        const int eff_cols = (cols == 1) ? 1 : (cols >= GEMM_BN - 15 ? cols : GEMM_BN);
+        const double cost = (cols == 1) ? per_col + 1500.0 : per_col * eff_cols + load;
         Tile t{o, row0, c * cw, klo / GEMM_BK, (khi + GEMM_BK - 1) / GEMM_BK, cost};
         tiles.push_back(t);
         flops += 2.0 * rows * cols * (double)(khi - klo);
@@ -252,6 +258,151 @@ __global__ void __launch_bounds__(256) gemm_streamk_kernel(GemmOpsT<T> ops, cons
   }
 }
 
+// ------------------------------------------------- double-float products
+// FP64-class products on the FP32 pipe (GB300 runs FP32 FMA at 64x the FP64
+// rate).  Operators are stored split, A = Ah + Al (two FP32 values, ~48
+// significant bits); vector entries are split on load.  Each multiply-add
+// takes the exact product error of Ah*xh from an FMA, adds the cross terms
+// Ah*xl + Al*xh (Al*xl, of relative size 2^-48, is dropped), and accumulates
+// into an (s, c) pair with Knuth's TwoSum, so the FP32 rounding of the running
+// sum is carried exactly into c.  About 13 FP32 instructions per
+// multiply-add; relative error of a length-K product ~ sqrt(K) 2^-48.
+__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float xh, float xl) {
+  const float p = ah * xh;
+  float e = fmaf(ah, xh, -p);
+  e = fmaf(ah, xl, e);
+  e = fmaf(al, xh, e);
+  const float t = s + p;
+  const float z = t - s;
+  const float err = (s - (t - z)) + (p - z);
+  s = t;
+  c += err + e;
+}
+
+__global__ void __launch_bounds__(256) gemm_streamk_df32_kernel(GemmOpsT<double> ops,
+                                                                const GemmSeg* __restrict__ segs,
+                                                                const int* __restrict__ seg_start,
+                                                                double* __restrict__ partial,
+                                                                const int* __restrict__ done, int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  __shared__ float Ah[GEMM_BK][GEMM_BM + 1];
+  __shared__ float Al[GEMM_BK][GEMM_BM + 1];
+  __shared__ float Xh[GEMM_BK][GEMM_BN + 1];
+  __shared__ float Xl[GEMM_BK][GEMM_BN + 1];
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  constexpr int LA = (GEMM_BM * GEMM_BK) / 256;
+  constexpr int LX = (GEMM_BN * GEMM_BK) / 256;
+  const int sbeg = seg_start[blockIdx.x], send = seg_start[blockIdx.x + 1];
+  for (int si = sbeg; si < send; ++si) {
+    const GemmSeg sg = segs[si];
+    const GemmOpT<double> op = ops.op[sg.op];
+    const int ncv = min(sg.colw, op.ncols - sg.col0);
+    float rah[LA], ral[LA], rxh[LX], rxl[LX];
+    auto fetch = [&](int k) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = tid + 256 * q;
+        const int kk = e % GEMM_BK, ii = e / GEMM_BK;
+        const int gi = sg.row0 + ii, gk = k + kk;
+        const bool in = (gi < op.m && gk < sg.k1);
+        const int64_t idx = gk + (int64_t)gi * op.lda;
+        rah[q] = in ? op.Ah[idx] : 0.f;
+        ral[q] = in ? op.Al[idx] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < LX; ++q) {
+        const int e = tid + 256 * q;
+        const int kk = e % GEMM_BK, cc = e / GEMM_BK;
+        const int gk = k + kk;
+        const bool in = (cc < ncv && gk < sg.k1);
+        const int64_t idx = gk + (int64_t)(sg.col0 + cc) * op.m;  // split X is dense, ld = m
+        rxh[q] = in ? op.Xh[idx] : 0.f;
+        rxl[q] = in ? op.Xl[idx] : 0.f;
+      }
+    };
+    float s[4][4], c[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s[i][j] = c[i][j] = 0.f;
+    fetch(sg.k0);
+    for (int k = sg.k0; k < sg.k1; k += GEMM_BK) {
+#pragma unroll
+      for (int q = 0; q < LA; ++q) {
+        const int e = tid + 256 * q;
+        Ah[e % GEMM_BK][e / GEMM_BK] = rah[q];
+        Al[e % GEMM_BK][e / GEMM_BK] = ral[q];
+      }
+#pragma unroll
+      for (int q = 0; q < LX; ++q) {
+        const int e = tid + 256 * q;
+        Xh[e % GEMM_BK][e / GEMM_BK] = rxh[q];
+        Xl[e % GEMM_BK][e / GEMM_BK] = rxl[q];
+      }
+      __syncthreads();
+      if (k + GEMM_BK < sg.k1) fetch(k + GEMM_BK);
+      if (ncv == 1) {
+        const int r = tid & 63, q0 = tid >> 6;
+#pragma unroll
+        for (int kk = q0; kk < GEMM_BK; kk += 4) df_mac(s[0][0], c[0][0], Ah[kk][r], Al[kk][r], Xh[kk][0], Xl[kk][0]);
+      } else if (ncv >= GEMM_BN - 15) {
+#pragma unroll 4
+        for (int kk = 0; kk < GEMM_BK; ++kk) {
+          float ah[4], al[4], xh[4], xl[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            ah[i] = Ah[kk][tx + 16 * i];
+            al[i] = Al[kk][tx + 16 * i];
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            xh[j] = Xh[kk][ty + 16 * j];
+            xl[j] = Xl[kk][ty + 16 * j];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) df_mac(s[i][j], c[i][j], ah[i], al[i], xh[j], xl[j]);
+        }
+      } else if (ty < ncv) {
+        for (int kk = 0; kk < GEMM_BK; ++kk) {
+          float ah[4], al[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            ah[i] = Ah[kk][tx + 16 * i];
+            al[i] = Al[kk][tx + 16 * i];
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (ty + 16 * j < ncv) {
+              const float xh = Xh[kk][ty + 16 * j], xl = Xl[kk][ty + 16 * j];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) df_mac(s[i][j], c[i][j], ah[i], al[i], xh, xl);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    double* dst = partial + (int64_t)sg.slot * (GEMM_BM * GEMM_BN);
+    if (ncv == 1) {
+      red[tid] = (double)s[0][0] + (double)c[0][0];
+      __syncthreads();
+      if (tid < GEMM_BM) dst[tid] = (red[tid] + red[tid + 64]) + (red[tid + 128] + red[tid + 192]);
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          dst[(ty + 16 * j) * GEMM_BM + tx + 16 * i] = (double)s[i][j] + (double)c[i][j];
+    }
+  }
+}
+
 struct ReduceMeta {
   int nops;
   int tile_base[GEMM_MAX_OPS];
@@ -312,15 +463,31 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
 }
 
 template <typename T>
+static void launch_products(const GemmPlan& plan, const GemmOpsT<T>& ops, T* partial, const int* done,
+                            cudaStream_t st) {
+  int* ran = prof_begin(sizeof(T) == 8 ? PROF_GEMM : PROF_GEMM32, plan.flops, st);
+  gemm_streamk_kernel<T><<<plan.nctas, 256, 0, st>>>(ops, plan.d_segs, plan.d_seg_start, partial, done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+template <>
+void launch_products<double>(const GemmPlan& plan, const GemmOpsT<double>& ops, double* partial, const int* done,
+                             cudaStream_t st) {
+  const bool df = ops.df32 != 0;
+  int* ran = prof_begin(df ? PROF_GEMMDF : PROF_GEMM, plan.flops, st);
+  if (df)
+    gemm_streamk_df32_kernel<<<plan.nctas, 256, 0, st>>>(ops, plan.d_segs, plan.d_seg_start, partial, done, ran);
+  else
+    gemm_streamk_kernel<double><<<plan.nctas, 256, 0, st>>>(ops, plan.d_segs, plan.d_seg_start, partial, done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+
+template <typename T>
 void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis, T* partial, const ModelDev& model,
               const int* obs, const int* done, cudaStream_t st) {
   if (plan.total_out == 0) return;
-  if (plan.nslots > 0) {
-    int* ran = prof_begin(PROF_GEMM, plan.flops, st);
-    gemm_streamk_kernel<T><<<plan.nctas, 256, 0, st>>>(ops, plan.d_segs, plan.d_seg_start, partial, done, ran);
-    WC4D_LAUNCH_CHECK();
-    if (ran) prof_end(st);
-  }
+  if (plan.nslots > 0) launch_products<T>(plan, ops, partial, done, st);
   ReduceMeta meta;
   meta.nops = plan.nops;
   for (int o = 0; o < GEMM_MAX_OPS; ++o) {
@@ -338,15 +505,20 @@ void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis
   WC4D_LAUNCH_CHECK();
 }
 
-int gemm_resident_ctas() {
-  static int cached = 0;
-  if (cached) return cached;
-  int dev = 0, sms = 0, per = 0;
+int gemm_resident_ctas(bool df32) {
+  static int cached[2] = {0, 0};
+  if (cached[df32]) return cached[df32];
+  int dev = 0, sms = 0, per = 0, per32 = 0;
   WC4D_CUDA(cudaGetDevice(&dev));
   WC4D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gemm_streamk_kernel<double>, 256, 0));
-  cached = std::max(1, sms * std::max(1, per));
-  return cached;
+  if (df32)
+    WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gemm_streamk_df32_kernel, 256, 0));
+  else
+    WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gemm_streamk_kernel<double>, 256, 0));
+  // the FP32 instance shares the schedule; use the smaller residency of the two
+  WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, gemm_streamk_kernel<float>, 256, 0));
+  cached[df32] = std::max(1, sms * std::max(1, std::min(per, per32)));
+  return cached[df32];
 }
 
 template void gemm_run<double>(const GemmPlan&, const GemmOpsT<double>&, const EpisT<double>&, double*,

@@ -403,6 +403,50 @@ void gm_solve_y(const double* H, int ldh, const double* g, int k, double* y, cud
   WC4D_LAUNCH_CHECK();
 }
 
+__global__ void gm_solve_y_dev_kernel(const double* H, int ldh, const double* g, const DevStatus* stat, int kmax,
+                                      double* y) {
+  extern __shared__ double rhs[];
+  const int k = min(stat->iters, kmax);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = g[i];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    const double yi = rhs[i] / H[i + (int64_t)i * ldh];
+    __syncthreads();
+    for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] -= H[r + (int64_t)i * ldh] * yi;
+    if (threadIdx.x == 0) y[i] = yi;
+    __syncthreads();
+  }
+}
+void gm_solve_y_dev(const double* H, int ldh, const double* g, const DevStatus* stat, int kmax, double* y,
+                    cudaStream_t st) {
+  gm_solve_y_dev_kernel<<<1, 256, sizeof(double) * (size_t)std::max(kmax, 1), st>>>(H, ldh, g, stat, kmax, y);
+  WC4D_LAUNCH_CHECK();
+}
+
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(256) gm_combine_dev_kernel(const TZ* __restrict__ Z, int64_t ldz,
+                                                             const DevStatus* stat, int kmax,
+                                                             const double* __restrict__ y, T* x, int64_t n) {
+  extern __shared__ double ys[];
+  const int k = min(stat->iters, kmax);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += ys[i] * (double)Z[(int64_t)i * ldz + e];
+    x[e] = (T)acc;
+  }
+}
+template <typename T, typename TZ>
+void gm_combine_dev(const TZ* Z, int64_t ldz, const DevStatus* stat, int kmax, const double* y, T* x, int64_t n,
+                    cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  gm_combine_dev_kernel<T, TZ><<<nb, 256, sizeof(double) * std::max(kmax, 1), st>>>(Z, ldz, stat, kmax, y, x, n);
+  WC4D_LAUNCH_CHECK();
+}
+template void gm_combine_dev<double, float>(const float*, int64_t, const DevStatus*, int, const double*, double*,
+                                            int64_t, cudaStream_t);
+
 // x = x0 + sum_i y_i Z_i
 template <typename T, typename TZ>
 __global__ void __launch_bounds__(256) gm_combine_kernel(const TZ* __restrict__ Z, int64_t ldz, int k,

@@ -47,6 +47,13 @@ void gm_hessenberg(int j, const double* h1, const double* h2, const double* part
 template <typename T>
 void gm_normalize(const T* w, const double* hnext, T* v, int64_t n, const int* done, cudaStream_t st);
 void gm_solve_y(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t st);
+// as gm_solve_y with k = min(stat->iters, kmax) read on the device
+void gm_solve_y_dev(const double* H, int ldh, const double* g, const DevStatus* stat, int kmax, double* y,
+                    cudaStream_t st);
+// x = sum_{i < min(stat->iters, kmax)} y_i Z_i  (FP64 accumulation)
+template <typename T, typename TZ>
+void gm_combine_dev(const TZ* Z, int64_t ldz, const DevStatus* stat, int kmax, const double* y, T* x, int64_t n,
+                    cudaStream_t st);
 template <typename T, typename TZ>
 void gm_combine(const TZ* Z, int64_t ldz, int k, const double* y, const T* x0, T* x, int64_t n, cudaStream_t st);
 

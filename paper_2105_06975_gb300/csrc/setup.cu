@@ -104,6 +104,33 @@ void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t st) {
   if (n > 0) to_float_kernel<<<nblk(n), 256, 0, st>>>(a, b, n);
   WC4D_LAUNCH_CHECK();
 }
+__global__ void split_df_kernel(const double* a, float* hi, float* lo, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[e];
+    const float h = __double2float_rn(v);
+    hi[e] = h;
+    lo[e] = __double2float_rn(v - (double)h);
+  }
+}
+void launch_split_df(const double* a, float* hi, float* lo, int64_t n, cudaStream_t st) {
+  if (n > 0) split_df_kernel<<<nblk(n), 256, 0, st>>>(a, hi, lo, n);
+  WC4D_LAUNCH_CHECK();
+}
+__global__ void split_df_block_kernel(const double* a, int64_t ld, int m, int ncols, float* hi, float* lo) {
+  const int64_t total = (int64_t)m * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), c = (int)(e / m);
+    const double v = a[i + (int64_t)c * ld];
+    const float h = __double2float_rn(v);
+    hi[e] = h;
+    lo[e] = __double2float_rn(v - (double)h);
+  }
+}
+void launch_split_df_block(const double* a, int64_t ld, int m, int ncols, float* hi, float* lo, cudaStream_t st) {
+  const int64_t n = (int64_t)m * ncols;
+  if (n > 0) split_df_block_kernel<<<nblk(n), 256, 0, st>>>(a, ld, m, ncols, hi, lo);
+  WC4D_LAUNCH_CHECK();
+}
 // inverse observation map: inv[j] = r if obs[r] == j, else -1
 __global__ void inv_map_kernel(const int* obs, int p, int* inv, int s) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < p; r += gridDim.x * blockDim.x) inv[obs[r]] = r;

@@ -114,6 +114,14 @@ int wc4d_get_stats(wc4d_stats* out) {
       out->gemm_ms += ms;
       out->gemm_flops += p.recs[i].work;
       out->gemm_launches += 1;
+    } else if (p.recs[i].cls == PROF_GEMMDF) {
+      out->gemmdf_ms += ms;
+      out->gemmdf_flops += p.recs[i].work;
+      out->gemmdf_launches += 1;
+    } else if (p.recs[i].cls == PROF_GEMM32) {
+      out->gemm32_ms += ms;
+      out->gemm32_flops += p.recs[i].work;
+      out->gemm32_launches += 1;
     } else {
       out->orth_ms += ms;
       out->orth_bytes += p.recs[i].work;

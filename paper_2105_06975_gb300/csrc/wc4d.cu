@@ -26,6 +26,10 @@ void saddle_c3(const ModelDev& md, const T* v1, const T* v2, const int* inv, int
 
 // Operator data in one precision: covariances, inverse Cholesky factors and
 // the GEMM partial buffer.
+struct Split {
+  const float* h = nullptr;
+  const float* l = nullptr;
+};
 template <typename T>
 struct OpSet {
   T *B = nullptr, *Q = nullptr, *R = nullptr;
@@ -33,6 +37,36 @@ struct OpSet {
   T *WS = nullptr, *WSt = nullptr;
   T* partial = nullptr;
   T *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;  // n-length scratch
+  // double-float splits of the operators above (DF32 / MIXED outer products)
+  int df32 = 0;
+  std::vector<std::pair<const T*, Split>> splits;
+  Split split_of(const T* m) const {
+    for (auto& s : splits)
+      if (s.first == m) return s.second;
+    return Split{};
+  }
+  float *xh = nullptr, *xl = nullptr;  // split X operands of one launch (2 n floats each)
+  int64_t xcap = 0;
+  // route every product of a launch through the double-float kernel: attach
+  // the operator splits and split each op's X block once
+  void attach(GemmOpsT<T>& ops, cudaStream_t st) const {
+    if (!df32) return;
+    ops.df32 = 1;
+    int64_t off = 0;
+    for (int o = 0; o < ops.nops; ++o) {
+      GemmOpT<T>& op = ops.op[o];
+      const Split sp = split_of(op.At);
+      op.Ah = sp.h;
+      op.Al = sp.l;
+      const int64_t cnt = (int64_t)op.m * op.ncols;
+      if (cnt <= 0) continue;
+      if (off + cnt > xcap) throw Error{WC4D_ERR_ARG, "internal: double-float operand buffer too small"};
+      if constexpr (sizeof(T) == 8) launch_split_df_block(op.X, op.ldx, op.m, op.ncols, xh + off, xl + off, st);
+      op.Xh = xh + off;
+      op.Xl = xl + off;
+      off += cnt;
+    }
+  }
 };
 
 }  // namespace wc4d
@@ -52,7 +86,15 @@ struct wc4d_problem {
   int nS = 0;
   bool have_pd = false;
   OpSet<double> f64;
+  OpSet<float> f32;  // MIXED: FP32 copies for the inner solve
   GemmPlan plan_A, plan_pd1, plan_pd2, plan_pi1, plan_pi2;
+  // MIXED inner GMRES(m) workspace (FP32 basis, FP64 Hessenberg/rotations)
+  int mi = 0;
+  float *Vi = nullptr, *Zi = nullptr, *stage = nullptr;
+  double *Hi = nullptr, *csi = nullptr, *sni = nullptr, *gi = nullptr, *yi = nullptr;
+  double *h1i = nullptr, *h2i = nullptr, *hnexti = nullptr, *bnormi = nullptr, *parti = nullptr, *part2i = nullptr;
+  DevStatus* stat_in = nullptr;
+  int64_t inner_total = 0;
   // Krylov workspace
   int maxit = 0;
   double *V = nullptr, *Z = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
@@ -87,7 +129,7 @@ struct wc4d_problem {
 
 namespace wc4d {
 
-static int max_gemm_ctas() { return gemm_resident_ctas(); }
+static int max_gemm_ctas(bool df32 = false) { return gemm_resident_ctas(df32); }
 
 // ------------------------------------------------------------ A v (Sec. 6.2)
 template <typename T>
@@ -109,6 +151,7 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
   ep.e[0] = {EPI_SADDLE_C1, c1, s, 0, v3, nullptr};
   ep.e[1] = {EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr};
   ep.e[2] = {EPI_SADDLE_C2, c2, p, 0, v3, nullptr};
+  os.attach(ops, P->st);
   gemm_run<T>(plan, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
 }
 
@@ -152,6 +195,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
     ops.op[3] = {os.Q, s, y3 + s, s, s, s, N, TRI_FULL};
     ep.e[3] = {EPI_STORE, u3 + s, s, 0, nullptr, nullptr};
   }
+  os.attach(ops, P->st);
   gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
   GemmOpsT<T> ops2{};
   EpisT<T> ep2{};
@@ -165,11 +209,13 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
     ops2.nops = 4;
     ops2.op[3] = {os.WS, P->nS, u3, P->nS, P->nS, P->nS, 1, TRI_UPPER};
     ep2.e[3] = {EPI_STORE, o3, P->nS, 0, nullptr, nullptr};
+    os.attach(ops2, P->st);
     gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
   } else {
     ops2.nops = 4;
     ops2.op[3] = {os.B, s, y3, s, s, s, 1, TRI_FULL};
     ep2.e[3] = {EPI_STORE, u3, s, 0, nullptr, nullptr};
+    os.attach(ops2, P->st);
     gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
     lhat_sweep<T>(P->md, k, u3, o3, false, ident, done, P->st);
   }
@@ -198,12 +244,14 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   ep.e[0] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
   ep.e[1] = {EPI_SUB_FROM, u, s, 0, nullptr, v1};
   ep.e[2] = {EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s};
+  os.attach(ops, P->st);
   gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
   GemmOpsT<T> ops2{};
   EpisT<T> ep2{};
   ops2.nops = 1;
   ops2.op[0] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
   ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
+  os.attach(ops2, P->st);
   gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
   lhat_sweep<T>(P->md, k, u, o3, false, false, done, P->st);
 }
@@ -442,13 +490,21 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(o->tol > 0 && o->maxit >= 1 && o->maxit <= 100000, WC4D_ERR_ARG, "need tol > 0, 1 <= maxit <= 1e5");
   WC4D_CHECK(o->krylov == WC4D_KRYLOV_MINRES || o->maxit <= 2000, WC4D_ERR_ARG,
              "GMRES/FGMRES without restarts keep maxit <= 2000 (Hessenberg column in shared memory)");
-  WC4D_CHECK(o->precision == WC4D_PREC_FP64, WC4D_ERR_ARG, "precision mode not available in this build");
+  WC4D_CHECK(o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_MIXED || o->precision == WC4D_PREC_DF32,
+             WC4D_ERR_ARG, "bad precision");
+  WC4D_CHECK((o->precision == WC4D_PREC_MIXED) == (o->krylov == WC4D_KRYLOV_FGMRES), WC4D_ERR_ARG,
+             "the mixed-precision mode is FGMRES (flexible outer FP64 iteration around an FP32 inner solve), "
+             "and FGMRES is only used by it");
+  WC4D_CHECK(o->precision != WC4D_PREC_MIXED || (o->inner_iters >= 1 && o->inner_iters <= 200), WC4D_ERR_ARG,
+             "inner_iters must lie in [1, 200]");
 }
 
 static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   validate(d, o);
   P->o = *o;
   if (P->o.check_every <= 0) P->o.check_every = 4;
+  // each outer step of the mixed mode is a whole inner solve: poll every step
+  if (o->precision == WC4D_PREC_MIXED) P->o.check_every = 1;
   const int s = d->s, N = d->N, p = d->p;
   P->s = s;
   P->N = N;
@@ -555,29 +611,100 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     }
   }
   // GEMM schedules
-  const int C = max_gemm_ctas();
-  plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}, {p, p, N + 1, TRI_FULL}}, C);
+  const bool dfm = (o->precision != WC4D_PREC_FP64);
+  const int C = max_gemm_ctas(dfm);
+  const int cm = dfm ? COST_DF32 : COST_FP64;
+  plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}, {p, p, N + 1, TRI_FULL}}, C, cm);
   if (P->have_pd) {
     if (o->shat == WC4D_SHAT_EXACT) {
       plan_build(P->plan_pd1, {{s, s, 1, TRI_LOWER}, {s, s, N, TRI_LOWER}, {p, p, N + 1, TRI_LOWER},
-                               {P->nS, P->nS, 1, TRI_LOWER}}, C);
+                               {P->nS, P->nS, 1, TRI_LOWER}}, C, cm);
       plan_build(P->plan_pd2, {{s, s, 1, TRI_UPPER}, {s, s, N, TRI_UPPER}, {p, p, N + 1, TRI_UPPER},
-                               {P->nS, P->nS, 1, TRI_UPPER}}, C);
+                               {P->nS, P->nS, 1, TRI_UPPER}}, C, cm);
     } else {
       plan_build(P->plan_pd1, {{s, s, 1, TRI_LOWER}, {s, s, N, TRI_LOWER}, {p, p, N + 1, TRI_LOWER},
-                               {s, s, N, TRI_FULL}}, C);
+                               {s, s, N, TRI_FULL}}, C, cm);
       plan_build(P->plan_pd2, {{s, s, 1, TRI_UPPER}, {s, s, N, TRI_UPPER}, {p, p, N + 1, TRI_UPPER},
-                               {s, s, 1, TRI_FULL}}, C);
+                               {s, s, 1, TRI_FULL}}, C, cm);
     }
   }
-  plan_build(P->plan_pi1, {{p, p, N + 1, TRI_LOWER}, {s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C);
-  plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C);
+  plan_build(P->plan_pi1, {{p, p, N + 1, TRI_LOWER}, {s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C, cm);
+  plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
   int slots = std::max({P->plan_A.nslots, P->plan_pd1.nslots, P->plan_pd2.nslots, P->plan_pi1.nslots,
                         P->plan_pi2.nslots, 1});
   f.partial = P->alloc<double>((int64_t)slots * GEMM_BM * GEMM_BN);
   f.t1 = P->alloc<double>(P->n);
   f.t2 = P->alloc<double>(P->n);
   f.t3 = P->alloc<double>(P->n);
+  if (o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_MIXED) {
+    f.df32 = 1;
+    f.xcap = 2 * P->n;
+    f.xh = P->alloc<float>(f.xcap);
+    f.xl = P->alloc<float>(f.xcap);
+    auto add = [&](const double* m, int64_t cnt) {
+      if (!m) return;
+      float* h = P->alloc<float>(cnt);
+      float* l = P->alloc<float>(cnt);
+      launch_split_df(m, h, l, cnt, st);
+      f.splits.push_back({m, Split{h, l}});
+    };
+    add(f.B, (int64_t)s * s);
+    add(f.Q, (int64_t)s * s);
+    add(f.R, (int64_t)p * p);
+    add(f.WR, (int64_t)p * p);
+    add(f.WRt, (int64_t)p * p);
+    add(f.WB, (int64_t)s * s);
+    add(f.WBt, (int64_t)s * s);
+    add(f.WQ, (int64_t)s * s);
+    add(f.WQt, (int64_t)s * s);
+    if (f.WS) {
+      add(f.WS, (int64_t)P->nS * P->nS);
+      add(f.WSt, (int64_t)P->nS * P->nS);
+    }
+  }
+  if (o->precision == WC4D_PREC_MIXED) {
+    OpSet<float>& g = P->f32;
+    auto to32 = [&](const double* src, int64_t cnt) {
+      if (!src) return (float*)nullptr;
+      float* d = P->alloc<float>(cnt);
+      launch_to_float(src, d, cnt, st);
+      return d;
+    };
+    g.B = to32(f.B, (int64_t)s * s);
+    g.Q = to32(f.Q, (int64_t)s * s);
+    g.R = to32(f.R, (int64_t)p * p);
+    g.WR = to32(f.WR, (int64_t)p * p);
+    g.WRt = to32(f.WRt, (int64_t)p * p);
+    g.WB = to32(f.WB, (int64_t)s * s);
+    g.WBt = to32(f.WBt, (int64_t)s * s);
+    g.WQ = to32(f.WQ, (int64_t)s * s);
+    g.WQt = to32(f.WQt, (int64_t)s * s);
+    if (f.WS) {
+      g.WS = to32(f.WS, (int64_t)P->nS * P->nS);
+      g.WSt = to32(f.WSt, (int64_t)P->nS * P->nS);
+    }
+    g.partial = P->alloc<float>((int64_t)slots * GEMM_BM * GEMM_BN);
+    g.t1 = P->alloc<float>(P->n);
+    g.t2 = P->alloc<float>(P->n);
+    g.t3 = P->alloc<float>(P->n);
+    const int mi = o->inner_iters;
+    P->mi = mi;
+    P->Vi = P->alloc<float>((int64_t)(mi + 1) * P->n);
+    P->Zi = P->alloc<float>((int64_t)mi * P->n);
+    P->stage = P->alloc<float>(P->n);
+    P->Hi = P->alloc<double>((int64_t)(mi + 1) * mi);
+    P->csi = P->alloc<double>(mi + 1);
+    P->sni = P->alloc<double>(mi + 1);
+    P->gi = P->alloc<double>(mi + 2);
+    P->yi = P->alloc<double>(mi + 1);
+    P->h1i = P->alloc<double>(mi + 2);
+    P->h2i = P->alloc<double>(mi + 2);
+    P->hnexti = P->alloc<double>(2);
+    P->bnormi = P->alloc<double>(2);
+    P->parti = P->alloc<double>((int64_t)DOT_BLOCKS * (mi + 2));
+    P->part2i = P->alloc<double>(DOT_BLOCKS);
+    P->stat_in = P->alloc<DevStatus>(1);
+  }
   // Krylov workspace
   const int64_t n = P->n;
   P->maxit = o->maxit;
@@ -729,6 +856,44 @@ static int solve_minres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   return status;
 }
 
+// MIXED preconditioner of the outer FGMRES: m steps of right-preconditioned
+// GMRES on the FP32 copy of A with the FP32 copy of the chosen P, from a zero
+// initial guess, on the outer Arnoldi vector v; z (FP64) = the inner iterate.
+// Fixed step count (no inner convergence test), so every outer step applies
+// the same amount of work; a lucky breakdown ends the inner loop early through
+// the inner status flag.
+static void inner_solve(wc4d_problem* P, const double* v, double* z) {
+  const int64_t n = P->n;
+  const int mi = P->mi, ldh = mi + 1;
+  cudaStream_t st = P->st;
+  const int* done = &P->stat_in->done;
+  const int which = P->o.precond;
+  vec_convert<float, double>(v, P->stage, n, 1.0, st);
+  dot_partial<float>(P->stage, P->stage, n, P->part2i, nullptr, st);
+  dot_finish(P->part2i, P->bnormi, 1, st);
+  gm_init<float>(P->stage, P->part2i, P->Vi, P->gi, P->stat_in, 0.0, n, st);
+  for (int j = 0; j < mi; ++j) {
+    float* vj = P->Vi + (int64_t)j * n;
+    float* zj = P->Zi + (int64_t)j * n;
+    float* w = P->Vi + (int64_t)(j + 1) * n;
+    apply_P<float>(P, which, P->f32, vj, zj, done);
+    apply_A<float>(P, P->f32, P->plan_A, zj, w, done);
+    gm_mdot<float>(P->Vi, n, j + 1, w, n, P->parti, done, st);
+    gm_mdot_reduce(P->parti, j + 1, P->h1i, done, st);
+    gm_mupdate<float>(P->Vi, n, j + 1, P->h1i, w, n, done, st);
+    gm_mdot<float>(P->Vi, n, j + 1, w, n, P->parti, done, st);
+    gm_mdot_reduce(P->parti, j + 1, P->h2i, done, st);
+    gm_mupdate<float>(P->Vi, n, j + 1, P->h2i, w, n, done, st);
+    dot_partial<float>(w, w, n, P->part2i, done, st);
+    gm_hessenberg(j, P->h1i, P->h2i, P->part2i, P->Hi, ldh, P->csi, P->sni, P->gi, P->hnexti, P->stat_in, P->bnormi,
+                  st);
+    gm_normalize<float>(w, P->hnexti, w, n, done, st);
+  }
+  gm_solve_y_dev(P->Hi, ldh, P->gi, P->stat_in, mi, P->yi, st);
+  gm_combine_dev<double, float>(P->Zi, n, P->stat_in, mi, P->yi, z, n, st);
+  P->inner_total += mi;
+}
+
 static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   const int64_t n = P->n;
   const int ldh = P->maxit + 1;
@@ -779,7 +944,10 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       double* vj = P->V + (int64_t)j * n;
       double* zj = P->Z + (int64_t)j * n;
       double* w = P->V + (int64_t)(j + 1) * n;
-      apply_P<double>(P, which, P->f64, vj, zj, done);
+      if (P->o.precision == WC4D_PREC_MIXED)
+        inner_solve(P, vj, zj);
+      else
+        apply_P<double>(P, which, P->f64, vj, zj, done);
       apply_A<double>(P, P->f64, P->plan_A, zj, w, done);
       gm_mdot<double>(P->V, n, j + 1, w, n, P->part, done, st);
       gm_mdot_reduce(P->part, j + 1, P->h1, done, st);
@@ -826,6 +994,7 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
     info->relres_est = P->h_stat->est;
     info->n_apply_A = nA;
     info->n_apply_P = nP;
+    info->inner_iters = (int)P->inner_total;
   }
   return status;
 }
@@ -983,6 +1152,7 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
   WC4D_CUDA(cudaMemcpyAsync(P->rhs, rhs, bytes, kin, P->st));
   if (use_x0) WC4D_CUDA(cudaMemcpyAsync(P->x, x, bytes, kin, P->st));
   wc4d_info loc{};
+  P->inner_total = 0;
   int status;
   if (P->o.krylov == WC4D_KRYLOV_MINRES)
     status = solve_minres(P, &loc, use_x0 != 0);
@@ -1000,6 +1170,20 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
     wc4d::set_error(buf);
   }
   return status;
+  WC4D_API_END
+}
+
+int wc4d_apply_fp32(wc4d_problem* P, int32_t which, const float* v, float* out) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && v && out, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(P->o.precision == WC4D_PREC_MIXED, WC4D_ERR_ARG, "FP32 operators need precision = MIXED at setup");
+  WC4D_CHECK(which >= 0 && which <= 2, WC4D_ERR_ARG, "which must be 0 (A), 1 (P_D) or 2 (P_I)");
+  WC4D_CHECK(which != 1 || P->have_pd, WC4D_ERR_ARG, "P_D needs a problem set up with precond = PD");
+  if (which == 0)
+    apply_A<float>(P, P->f32, P->plan_A, v, out, nullptr);
+  else
+    apply_P<float>(P, which - 1, P->f32, v, out, nullptr);
+  return WC4D_OK;
   WC4D_API_END
 }
 

@@ -51,6 +51,7 @@ WC4D_KRYLOV_GMRES = 1
 WC4D_KRYLOV_FGMRES = 2
 WC4D_PREC_FP64 = 0
 WC4D_PREC_MIXED = 1
+WC4D_PREC_DF32 = 2
 
 RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG}
 PRECOND = {"PD": WC4D_PRECOND_PD, "PI": WC4D_PRECOND_PI}
@@ -90,7 +91,9 @@ class Info(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
                 ("gemm_launches", ctypes.c_int64), ("orth_ms", ctypes.c_double), ("orth_bytes", ctypes.c_double),
-                ("orth_launches", ctypes.c_int64)]
+                ("orth_launches", ctypes.c_int64), ("gemm32_ms", ctypes.c_double), ("gemm32_flops", ctypes.c_double),
+                ("gemm32_launches", ctypes.c_int64), ("gemmdf_ms", ctypes.c_double),
+                ("gemmdf_flops", ctypes.c_double), ("gemmdf_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -105,6 +108,7 @@ SIGNATURES = {
     "wc4d_apply_precond": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "wc4d_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.POINTER(Info)]),
+    "wc4d_apply_fp32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "wc4d_synthesize_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_void_p]),
     "wc4d_problem_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), _ip, _ip, _ip]),
@@ -191,6 +195,10 @@ def wc4d_solve(h, rhs_ptr: int, x_ptr: int, use_x0: bool, mem_kind: int, raise_o
     return info
 
 
+def wc4d_apply_fp32(h, which: int, v_ptr: int, out_ptr: int) -> None:
+    _check(load().wc4d_apply_fp32(h, which, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)))
+
+
 def wc4d_synthesize_rhs(h, zb_ptr: int, zr_ptr: int, mem_kind: int, rhs_ptr: int) -> None:
     _check(load().wc4d_synthesize_rhs(h, ctypes.c_void_p(zb_ptr), ctypes.c_void_p(zr_ptr), mem_kind,
                                       ctypes.c_void_p(rhs_ptr)))
@@ -255,11 +263,11 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
     o.dhat = WC4D_DHAT_SHIFT if dhat in ("rr", "shift") else WC4D_DHAT_EXACT
     o.dhat_delta = float(dhat_delta)
     if krylov is None:
-        krylov = "minres" if precond == "PD" else "gmres"
+        krylov = "fgmres" if precision == "mixed" else ("minres" if precond == "PD" else "gmres")
     o.krylov = KRYLOV[krylov]
     o.tol = float(tol)
     o.maxit = int(maxit)
-    o.precision = WC4D_PREC_MIXED if precision == "mixed" else WC4D_PREC_FP64
+    o.precision = {"fp64": WC4D_PREC_FP64, "mixed": WC4D_PREC_MIXED, "df32": WC4D_PREC_DF32}[precision]
     o.inner_iters = int(inner_iters)
     o.check_every = int(check_every)
     return o
@@ -339,6 +347,13 @@ class Problem:
         x = torch.zeros_like(rhs) if x is None else x
         info = wc4d_solve(self.h, rhs.data_ptr(), x.data_ptr(), use_x0, WC4D_MEM_DEVICE)
         return x, info
+
+    def apply_fp32(self, which, v):
+        """which: "A", "PD" or "PI"; v: float32 CUDA tensor."""
+        import torch
+        out = torch.empty_like(v)
+        wc4d_apply_fp32(self.h, {"A": 0, "PD": 1, "PI": 2}[which], v.data_ptr(), out.data_ptr())
+        return out
 
     def synthesize_rhs(self, dr):
         """Device-built (b, d, 0) from the draws' z_b, z_r (linear models)."""

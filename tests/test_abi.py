@@ -14,7 +14,7 @@ HEADER = os.path.join(os.path.dirname(B.HERE), "include", "wc4d.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(wc4d_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(wc4d_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
