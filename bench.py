@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
     ap.add_argument("--chosen", default="df32", choices=["fp64", "df32", "mixed"])
+    ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
     return ap.parse_args()
 
 
@@ -256,9 +259,12 @@ def run_gpu(args):
         "df32": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
                                precision="df32"),
     }
-    if args.mixed:
+    if args.mixed or args.chosen == "mixed":
         modes["mixed"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
                                         maxit=min(args.maxit, 200), precision="mixed", inner_iters=args.inner)
+    if args.modes:
+        keep = args.modes.split(",")
+        modes = {m: o for m, o in modes.items() if m in keep}
     G = wc4d.Problem.from_workload(w, dr, modes["fp64"], stream=stream.cuda_stream)
     rhs = G.synthesize_rhs(dr)
     G.close()
@@ -266,15 +272,22 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     hbm = peaks().get("hbm_gbs")
 
+    split = []   # host-side (setup ms, solve ms) per step: setup synchronises, so this is a clean cut
+
     def step(opts):
+        t0 = time.perf_counter()
         G = wc4d.Problem.from_workload(w, dr, opts, stream=stream.cuda_stream)
+        t1 = time.perf_counter()
         _, info = G.solve(rhs, x)
+        t2 = time.perf_counter()
         G.close()
+        split.append(((t1 - t0) * 1e3, (t2 - t1) * 1e3))
         return info
 
     results = {}
     clk = ClockSampler(local)
-    clk.start()
+    if not args.no_clocks:
+        clk.start()
     for mode, opts in modes.items():
         for _ in range(args.warmup):
             step(opts)
@@ -284,6 +297,7 @@ def run_gpu(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         ev, infos = [], []
+        split.clear()
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -304,10 +318,12 @@ def run_gpu(args):
             ms = float(tt.item())
         assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
         results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
-                         "kernels": kernel_rows(st, step_ms, hbm)}
+                         "kernels": kernel_rows(st, step_ms, hbm),
+                         "setup_ms": statistics.mean(a for a, _ in split),
+                         "solve_ms": statistics.mean(b for _, b in split)}
     clocks = clk.stop()
-    chosen = results[args.chosen]
-    fp64 = results["fp64"]
+    chosen = results[args.chosen] if args.chosen in results else next(iter(results.values()))
+    fp64 = results.get("fp64", chosen)
     iters = [i.iters for i in chosen["infos"]]
     inner = [i.inner_iters for i in chosen["infos"]]
 
@@ -317,7 +333,7 @@ def run_gpu(args):
     x_h = np.zeros_like(rhs_h)
     obs_h = np.ascontiguousarray(dr.obs_idx, dtype=np.int32)
     e2e_t = []
-    for i in range(max(2, args.steps // 2) + 1):
+    for i in range(0 if args.no_e2e else max(2, args.steps // 2) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Gh = wc4d.Problem(w.s, w.N, w.p, obs_h, modes[args.chosen], stencil=w.stencil(), soar_b=w.soar_b,
@@ -327,7 +343,7 @@ def run_gpu(args):
         if i > 0:
             e2e_t.append(time.perf_counter() - t0)
         assert info.status == 0
-    e2e_val = world / statistics.mean(e2e_t)
+    e2e_val = world / statistics.mean(e2e_t) if e2e_t else None
 
     ks = chosen["kernels"]
     dom = max(ks.values(), key=lambda r: r["share_of_step"]) if ks else None
@@ -344,15 +360,16 @@ def run_gpu(args):
                    "parallelism": f"windows x{world}"},
         "iterations": {"mean": statistics.mean(iters), "inner_total_mean": statistics.mean(inner)},
         "modes": {m: {"solves_per_s": r["value"], "ms_per_step": r["ms"],
-                      "iterations": statistics.mean(i.iters for i in r["infos"])} for m, r in results.items()},
+                      "iterations": statistics.mean(i.iters for i in r["infos"]),
+                      "setup_ms_host": r["setup_ms"], "solve_ms_host": r["solve_ms"]} for m, r in results.items()},
         "relres_true_max": max(i.relres_true for i in chosen["infos"]),
         "fp64_solves_per_s": fp64["value"],
         "chosen_over_fp64": chosen["value"] / fp64["value"],
         "roofline": roof,
         "kernels": ks,
-        "kernels_fp64_mode": results["fp64"]["kernels"],
+        "kernels_fp64_mode": fp64["kernels"],
         "gpu_launches": int(chosen["stats"].launches),
-        "gpu_launches_fp64_mode": int(results["fp64"]["stats"].launches),
+        "gpu_launches_fp64_mode": int(fp64["stats"].launches),
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(w.n * 8 + w.p * 4),
                 "d2h_bytes_per_step": int(w.n * 8)},

@@ -203,48 +203,80 @@ void minres_update(const double* part_delta, const double* part_gamma, const dou
 }
 
 // ------------------------------------------------------------------- GMRES
-// part[i * DOT_BLOCKS + b] = sum over block b's slice of V_i . w
+// part[i * nchunks + c] = sum over chunk c (ORTH_CHUNK elements) of V_i . w.
+// Grid (chunks, vector groups of ORTH_G): every thread holds ORTH_U elements of
+// w and issues ORTH_G x ORTH_U independent loads of the basis, enough bytes in
+// flight to stream V at HBM rate.
 template <typename T>
 __global__ void __launch_bounds__(DOT_THREADS) gm_mdot_kernel(const T* __restrict__ V, int64_t ldv, int cnt,
                                                               const T* __restrict__ w, int64_t n,
                                                               double* __restrict__ part, const int* done,
                                                               int* ran) {
   if (done != nullptr && *(volatile const int*)done) return;
-  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t e0 = blockIdx.x * chunk;
-  const int64_t e1 = min(n, e0 + chunk);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < cnt; i += nw) {
-    const T* vi = V + (int64_t)i * ldv;
-    double acc = 0.0;
-    for (int64_t e = e0 + lane; e < e1; e += 32) acc += (double)vi[e] * (double)w[e];
-    acc = warp_sum(acc);
-    if (lane == 0) part[(int64_t)i * DOT_BLOCKS + blockIdx.x] = acc;
+  if (ran != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ran = 1;
+  __shared__ double sh[DOT_THREADS / 32][ORTH_G];
+  const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
+  const int64_t e0 = (int64_t)chunk * ORTH_CHUNK + threadIdx.x;
+  double wv[ORTH_U];
+#pragma unroll
+  for (int u = 0; u < ORTH_U; ++u) {
+    const int64_t e = e0 + (int64_t)u * DOT_THREADS;
+    wv[u] = e < n ? (double)w[e] : 0.0;
+  }
+  double acc[ORTH_G];
+#pragma unroll
+  for (int g = 0; g < ORTH_G; ++g) {
+    acc[g] = 0.0;
+    if (i0 + g < cnt) {
+      const T* vi = V + (int64_t)(i0 + g) * ldv;
+#pragma unroll
+      for (int u = 0; u < ORTH_U; ++u) {
+        const int64_t e = e0 + (int64_t)u * DOT_THREADS;
+        if (e < n) acc[g] += (double)vi[e] * wv[u];
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < ORTH_G; ++g) {
+    const double v = warp_sum(acc[g]);
+    if (lane == 0) sh[wid][g] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < ORTH_G && i0 + threadIdx.x < cnt) {
+    double s = 0.0;
+    for (int k = 0; k < DOT_THREADS / 32; ++k) s += sh[k][threadIdx.x];
+    part[(int64_t)(i0 + threadIdx.x) * gridDim.x + chunk] = s;
   }
 }
 template <typename T>
 void gm_mdot(const T* V, int64_t ldv, int cnt, const T* w, int64_t n, double* part, const int* done,
              cudaStream_t st) {
   int* ran = prof_begin(PROF_ORTH, (double)(cnt + 1) * n * sizeof(T), st);
-  gm_mdot_kernel<T><<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(V, ldv, cnt, w, n, part, done, ran);
+  dim3 grid(orth_chunks(n), (cnt + ORTH_G - 1) / ORTH_G);
+  gm_mdot_kernel<T><<<grid, DOT_THREADS, 0, st>>>(V, ldv, cnt, w, n, part, done, ran);
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
 }
 template void gm_mdot<double>(const double*, int64_t, int, const double*, int64_t, double*, const int*, cudaStream_t);
 template void gm_mdot<float>(const float*, int64_t, int, const float*, int64_t, double*, const int*, cudaStream_t);
 
-__global__ void gm_mdot_reduce_kernel(const double* part, double* h, const int* done) {
+// h[i] = sum over chunks of part[i * nchunks + c], fixed order
+__global__ void gm_mdot_reduce_kernel(const double* part, int nchunks, double* h, const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
   __shared__ double sh[32];
-  const double v = sum_partials(part + (int64_t)blockIdx.x * DOT_BLOCKS, sh);
+  const double* p = part + (int64_t)blockIdx.x * nchunks;
+  double v = 0.0;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) v += p[c];
+  v = block_sum(v, sh);
   if (threadIdx.x == 0) h[blockIdx.x] = v;
 }
-void gm_mdot_reduce(const double* part, int cnt, double* h, const int* done, cudaStream_t st) {
-  gm_mdot_reduce_kernel<<<cnt, DOT_THREADS, 0, st>>>(part, h, done);
+void gm_mdot_reduce(const double* part, int cnt, int nchunks, double* h, const int* done, cudaStream_t st) {
+  gm_mdot_reduce_kernel<<<cnt, DOT_THREADS, 0, st>>>(part, nchunks, h, done);
   WC4D_LAUNCH_CHECK();
 }
 
+// w -= V h over cnt basis vectors, eight independent loads in flight per thread
 template <typename T>
 __global__ void __launch_bounds__(DOT_THREADS) gm_mupdate_kernel(const T* __restrict__ V, int64_t ldv, int cnt,
                                                                  const double* __restrict__ h, T* __restrict__ w,
@@ -255,16 +287,26 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_mupdate_kernel(const T* __rest
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) hs[i] = h[i];
   __syncthreads();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < cnt; ++i) acc += hs[i] * (double)V[(int64_t)i * ldv + e];
-    w[e] = (T)((double)w[e] - acc);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = 0;
+    for (; i + 8 <= cnt; i += 8) {
+      const T* p = V + (int64_t)i * ldv + e;
+      const double x0 = (double)p[0], x1 = (double)p[ldv], x2 = (double)p[2 * ldv], x3 = (double)p[3 * ldv];
+      const double x4 = (double)p[4 * ldv], x5 = (double)p[5 * ldv], x6 = (double)p[6 * ldv], x7 = (double)p[7 * ldv];
+      a0 += hs[i] * x0 + hs[i + 4] * x4;
+      a1 += hs[i + 1] * x1 + hs[i + 5] * x5;
+      a2 += hs[i + 2] * x2 + hs[i + 6] * x6;
+      a3 += hs[i + 3] * x3 + hs[i + 7] * x7;
+    }
+    for (; i < cnt; ++i) a0 += hs[i] * (double)V[(int64_t)i * ldv + e];
+    w[e] = (T)((double)w[e] - ((a0 + a1) + (a2 + a3)));
   }
 }
 template <typename T>
 void gm_mupdate(const T* V, int64_t ldv, int cnt, const double* h, T* w, int64_t n, const int* done,
                 cudaStream_t st) {
-  const int nb = (int)std::min<int64_t>((n + DOT_THREADS - 1) / DOT_THREADS, 152 * 8);
   int* ran = prof_begin(PROF_ORTH, (double)(cnt + 2) * n * sizeof(T), st);
+  const int nb = (int)std::min<int64_t>((n + DOT_THREADS - 1) / DOT_THREADS, 152 * 16);
   gm_mupdate_kernel<T><<<nb, DOT_THREADS, sizeof(double) * cnt, st>>>(V, ldv, cnt, h, w, n, done, ran);
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
@@ -472,6 +514,185 @@ template void gm_combine<float, float>(const float*, int64_t, int, const double*
                                        cudaStream_t);
 template void gm_combine<double, float>(const float*, int64_t, int, const double*, const double*, double*, int64_t,
                                         cudaStream_t);
+
+// ------------------------------------------------ double-float Arnoldi passes
+// The same error-free multiply-add as the double-float GEMM: product error by
+// FMA, cross terms, Knuth TwoSum into (s, c).
+__device__ __forceinline__ void dfk_mac(float& s, float& c, float ah, float al, float xh, float xl) {
+  const float p = ah * xh;
+  float e = fmaf(ah, xh, -p);
+  e = fmaf(ah, xl, e);
+  e = fmaf(al, xh, e);
+  const float t = s + p;
+  const float z = t - s;
+  const float err = (s - (t - z)) + (p - z);
+  s = t;
+  c += err + e;
+}
+
+// Block dots V^T w over the split basis.  Grid (chunks of 1024 elements,
+// groups of ORTH_G vectors); each thread takes 4 consecutive elements, so every
+// basis access is a 16-byte load (the many-stream read pattern reaches HBM
+// rate only with wide per-thread loads).  ldv and the buffers are padded to a
+// multiple of 4 elements with zeros.
+__global__ void __launch_bounds__(DOT_THREADS) gm_mdot_df_kernel(const float* __restrict__ Vh,
+                                                                 const float* __restrict__ Vl, int64_t ldv, int cnt,
+                                                                 const float* __restrict__ wh,
+                                                                 const float* __restrict__ wl, int64_t n4,
+                                                                 double* __restrict__ part, const int* done,
+                                                                 int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ran = 1;
+  __shared__ double sh[DOT_THREADS / 32][ORTH_G];
+  const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
+  const int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x;  // float4 index
+  const bool in = q < n4;
+  const float4 xh = in ? reinterpret_cast<const float4*>(wh)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 xl = in ? reinterpret_cast<const float4*>(wl)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+  double acc[ORTH_G];
+#pragma unroll
+  for (int g = 0; g < ORTH_G; ++g) {
+    float s = 0.f, c = 0.f;
+    if (in && i0 + g < cnt) {
+      const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
+      const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
+      dfk_mac(s, c, a.x, b.x, xh.x, xl.x);
+      dfk_mac(s, c, a.y, b.y, xh.y, xl.y);
+      dfk_mac(s, c, a.z, b.z, xh.z, xl.z);
+      dfk_mac(s, c, a.w, b.w, xh.w, xl.w);
+    }
+    acc[g] = (double)s + (double)c;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < ORTH_G; ++g) {
+    const double v = warp_sum(acc[g]);
+    if (lane == 0) sh[wid][g] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < ORTH_G && i0 + threadIdx.x < cnt) {
+    double s = 0.0;
+    for (int k = 0; k < DOT_THREADS / 32; ++k) s += sh[k][threadIdx.x];
+    part[(int64_t)(i0 + threadIdx.x) * gridDim.x + chunk] = s;
+  }
+}
+void gm_mdot_df(const float* Vh, const float* Vl, int64_t ldv, int cnt, const float* wh, const float* wl, int64_t n,
+                double* part, const int* done, cudaStream_t st) {
+  int* ran = prof_begin(PROF_ORTH, (double)(cnt + 1) * n * 8.0, st);
+  const int64_t n4 = (n + 3) / 4;
+  dim3 grid((unsigned)((n4 + DOT_THREADS - 1) / DOT_THREADS), (cnt + ORTH_G - 1) / ORTH_G);
+  gm_mdot_df_kernel<<<grid, DOT_THREADS, 0, st>>>(Vh, Vl, ldv, cnt, wh, wl, n4, part, done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+
+// w -= V h with double-float accumulation of V h (4 elements per thread,
+// 16-byte basis loads), then w is re-split for the next pass
+__global__ void __launch_bounds__(DOT_THREADS) gm_mupdate_df_kernel(const float* __restrict__ Vh,
+                                                                    const float* __restrict__ Vl, int64_t ldv,
+                                                                    int cnt, const double* __restrict__ h,
+                                                                    double* __restrict__ w, float* __restrict__ wh,
+                                                                    float* __restrict__ wl, int64_t n,
+                                                                    const int* done, int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  extern __shared__ float hsh[];  // [cnt] hi, [cnt] lo
+  float* hsl = hsh + cnt;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const float hi = __double2float_rn(h[i]);
+    hsh[i] = hi;
+    hsl[i] = __double2float_rn(h[i] - (double)hi);
+  }
+  __syncthreads();
+  const int64_t n4 = (n + 3) / 4;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    int i = 0;
+    // four basis vectors per step: eight 16-byte loads in flight per thread
+    for (; i + 4 <= cnt; i += 4) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = reinterpret_cast<const float4*>(Vh + (int64_t)(i + u) * ldv)[q];
+        b[u] = reinterpret_cast<const float4*>(Vl + (int64_t)(i + u) * ldv)[q];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float hh = hsh[i + u], hl = hsl[i + u];
+        dfk_mac(s[0], c[0], hh, hl, a[u].x, b[u].x);
+        dfk_mac(s[1], c[1], hh, hl, a[u].y, b[u].y);
+        dfk_mac(s[2], c[2], hh, hl, a[u].z, b[u].z);
+        dfk_mac(s[3], c[3], hh, hl, a[u].w, b[u].w);
+      }
+    }
+    for (; i < cnt; ++i) {
+      const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)i * ldv)[q];
+      const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)i * ldv)[q];
+      const float hh = hsh[i], hl = hsl[i];
+      dfk_mac(s[0], c[0], hh, hl, a.x, b.x);
+      dfk_mac(s[1], c[1], hh, hl, a.y, b.y);
+      dfk_mac(s[2], c[2], hh, hl, a.z, b.z);
+      dfk_mac(s[3], c[3], hh, hl, a.w, b.w);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t e = 4 * q + u;
+      if (e < n) {
+        const double v = w[e] - ((double)s[u] + (double)c[u]);
+        w[e] = v;
+        const float vh = __double2float_rn(v);
+        wh[e] = vh;
+        wl[e] = __double2float_rn(v - (double)vh);
+      }
+    }
+  }
+}
+void gm_mupdate_df(const float* Vh, const float* Vl, int64_t ldv, int cnt, const double* h, double* w, float* wh,
+                   float* wl, int64_t n, const int* done, cudaStream_t st) {
+  int* ran = prof_begin(PROF_ORTH, (double)cnt * n * 8.0 + 3.0 * n * 8.0, st);
+  const int64_t n4 = (n + 3) / 4;
+  const int nb = (int)std::min<int64_t>((n4 + DOT_THREADS - 1) / DOT_THREADS, 152 * 16);
+  gm_mupdate_df_kernel<<<nb, DOT_THREADS, sizeof(float) * 2 * std::max(cnt, 1), st>>>(Vh, Vl, ldv, cnt, h, w, wh, wl,
+                                                                                    n, done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+
+__global__ void gm_normalize_df_kernel(const double* __restrict__ w, const double* hnext, double* __restrict__ v,
+                                       float* __restrict__ vh, float* __restrict__ vl, int64_t n, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  const double hh = *hnext;
+  const double ih = hh > 0.0 ? 1.0 / hh : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[e] * ih;
+    v[e] = x;
+    const float xh = __double2float_rn(x);
+    vh[e] = xh;
+    vl[e] = __double2float_rn(x - (double)xh);
+  }
+}
+void gm_normalize_df(const double* w, const double* hnext, double* v, float* vh, float* vl, int64_t n,
+                     const int* done, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  gm_normalize_df_kernel<<<nb, 256, 0, st>>>(w, hnext, v, vh, vl, n, done);
+  WC4D_LAUNCH_CHECK();
+}
+
+__global__ void gm_split_kernel(const double* __restrict__ w, float* __restrict__ wh, float* __restrict__ wl, int64_t n,
+                                const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[e];
+    const float xh = __double2float_rn(x);
+    wh[e] = xh;
+    wl[e] = __double2float_rn(x - (double)xh);
+  }
+}
+void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  gm_split_kernel<<<nb, 256, 0, st>>>(w, wh, wl, n, done);
+  WC4D_LAUNCH_CHECK();
+}
 
 // ---------------------------------------------------------------- vectors
 template <typename T>

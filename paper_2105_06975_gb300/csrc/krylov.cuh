@@ -6,6 +6,11 @@ namespace wc4d {
 
 constexpr int DOT_BLOCKS = 304;  // 2 per SM on a 152-SM GB300; fixed for deterministic sums
 constexpr int DOT_THREADS = 256;
+// block-dot partials of the Arnoldi passes: one partial per 1024-element chunk
+constexpr int ORTH_U = 4;                         // elements per thread
+constexpr int ORTH_G = 8;                         // basis vectors per block
+constexpr int ORTH_CHUNK = DOT_THREADS * ORTH_U;  // elements per block
+inline int orth_chunks(int64_t n) { return (int)((n + ORTH_CHUNK - 1) / ORTH_CHUNK); }
 
 struct DevStatus {
   int done;
@@ -34,7 +39,7 @@ void minres_update(const double* part_delta, const double* part_gamma, const dou
 template <typename T>
 void gm_mdot(const T* V, int64_t ldv, int cnt, const T* w, int64_t n, double* part, const int* done,
              cudaStream_t st);
-void gm_mdot_reduce(const double* part, int cnt, double* h, const int* done, cudaStream_t st);
+void gm_mdot_reduce(const double* part, int cnt, int nchunks, double* h, const int* done, cudaStream_t st);
 template <typename T>
 void gm_mupdate(const T* V, int64_t ldv, int cnt, const double* h, T* w, int64_t n, const int* done,
                 cudaStream_t st);
@@ -56,6 +61,17 @@ void gm_combine_dev(const TZ* Z, int64_t ldz, const DevStatus* stat, int kmax, c
                     cudaStream_t st);
 template <typename T, typename TZ>
 void gm_combine(const TZ* Z, int64_t ldz, int k, const double* y, const T* x0, T* x, int64_t n, cudaStream_t st);
+
+// double-float Arnoldi basis (DF32 mode): basis vectors stored as FP32 hi/lo
+// pairs; dots and updates run on the FP32 pipe with exact-error accumulation
+void gm_mdot_df(const float* Vh, const float* Vl, int64_t ldv, int cnt, const float* wh, const float* wl, int64_t n,
+                double* part, const int* done, cudaStream_t st);
+void gm_mupdate_df(const float* Vh, const float* Vl, int64_t ldv, int cnt, const double* h, double* w, float* wh,
+                   float* wl, int64_t n, const int* done, cudaStream_t st);
+// v = w / hnext as a double vector and as its split into the basis slot
+void gm_normalize_df(const double* w, const double* hnext, double* v, float* vh, float* vl, int64_t n,
+                     const int* done, cudaStream_t st);
+void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done, cudaStream_t st);
 
 // small vector ops
 template <typename T>

@@ -101,6 +101,11 @@ struct wc4d_problem {
   double *h1 = nullptr, *h2 = nullptr, *hnext = nullptr, *bnorm = nullptr, *scal = nullptr;
   double *part = nullptr, *part2 = nullptr, *part3 = nullptr, *sc = nullptr;
   double *rhs = nullptr, *x = nullptr, *r = nullptr, *x0 = nullptr;
+  // DF32 GMRES: Arnoldi basis stored split (hi/lo FP32), current vector and w in FP64
+  bool split_basis = false;
+  int64_t ldb = 0;  // leading dimension of the split basis
+  float *Vh = nullptr, *Vl = nullptr, *wh = nullptr, *wl = nullptr;
+  double *vcur = nullptr, *wbuf = nullptr;
   DevStatus* stat = nullptr;
   DevStatus* h_stat = nullptr;
   double* h_scal = nullptr;
@@ -701,7 +706,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     P->h2i = P->alloc<double>(mi + 2);
     P->hnexti = P->alloc<double>(2);
     P->bnormi = P->alloc<double>(2);
-    P->parti = P->alloc<double>((int64_t)DOT_BLOCKS * (mi + 2));
+    P->parti = P->alloc<double>((int64_t)std::max(DOT_BLOCKS, orth_chunks(P->n)) * (mi + 2));
     P->part2i = P->alloc<double>(DOT_BLOCKS);
     P->stat_in = P->alloc<DevStatus>(1);
   }
@@ -709,7 +714,24 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   const int64_t n = P->n;
   P->maxit = o->maxit;
   const int64_t nvec = (o->krylov == WC4D_KRYLOV_MINRES) ? 12 : (int64_t)o->maxit + 1;
-  P->V = P->alloc<double>(nvec * n);
+  P->split_basis = (o->krylov != WC4D_KRYLOV_MINRES) && (o->precision != WC4D_PREC_FP64);
+  if (P->split_basis) {
+    // leading dimension padded to 4 floats (16-byte loads); padding stays zero
+    P->ldb = (n + 3) / 4 * 4;
+    P->Vh = P->alloc<float>(nvec * P->ldb);
+    P->Vl = P->alloc<float>(nvec * P->ldb);
+    P->wh = P->alloc<float>(P->ldb);
+    P->wl = P->alloc<float>(P->ldb);
+    WC4D_CUDA(cudaMemsetAsync(P->Vh, 0, sizeof(float) * nvec * P->ldb, st));
+    WC4D_CUDA(cudaMemsetAsync(P->Vl, 0, sizeof(float) * nvec * P->ldb, st));
+    WC4D_CUDA(cudaMemsetAsync(P->wh, 0, sizeof(float) * P->ldb, st));
+    WC4D_CUDA(cudaMemsetAsync(P->wl, 0, sizeof(float) * P->ldb, st));
+    P->vcur = P->alloc<double>(n);
+    P->wbuf = P->alloc<double>(n);
+    P->V = P->alloc<double>(n);  // r0 staging only
+  } else {
+    P->V = P->alloc<double>(nvec * n);
+  }
   if (o->krylov != WC4D_KRYLOV_MINRES) P->Z = P->alloc<double>((int64_t)o->maxit * n);
   const int ldh = o->maxit + 1;
   P->H = P->alloc<double>((int64_t)ldh * o->maxit);
@@ -722,7 +744,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->hnext = P->alloc<double>(2);
   P->bnorm = P->alloc<double>(2);
   P->scal = P->alloc<double>(8);
-  P->part = P->alloc<double>((int64_t)DOT_BLOCKS * (o->maxit + 2));
+  P->part = P->alloc<double>((int64_t)std::max(DOT_BLOCKS, orth_chunks(P->n)) * (o->maxit + 2));
   P->part2 = P->alloc<double>(DOT_BLOCKS);
   P->part3 = P->alloc<double>(DOT_BLOCKS);
   P->sc = P->alloc<double>(2 * MS_COUNT);
@@ -879,10 +901,10 @@ static void inner_solve(wc4d_problem* P, const double* v, double* z) {
     apply_P<float>(P, which, P->f32, vj, zj, done);
     apply_A<float>(P, P->f32, P->plan_A, zj, w, done);
     gm_mdot<float>(P->Vi, n, j + 1, w, n, P->parti, done, st);
-    gm_mdot_reduce(P->parti, j + 1, P->h1i, done, st);
+    gm_mdot_reduce(P->parti, j + 1, orth_chunks(n), P->h1i, done, st);
     gm_mupdate<float>(P->Vi, n, j + 1, P->h1i, w, n, done, st);
     gm_mdot<float>(P->Vi, n, j + 1, w, n, P->parti, done, st);
-    gm_mdot_reduce(P->parti, j + 1, P->h2i, done, st);
+    gm_mdot_reduce(P->parti, j + 1, orth_chunks(n), P->h2i, done, st);
     gm_mupdate<float>(P->Vi, n, j + 1, P->h2i, w, n, done, st);
     dot_partial<float>(w, w, n, P->part2i, done, st);
     gm_hessenberg(j, P->h1i, P->h2i, P->part2i, P->Hi, ldh, P->csi, P->sni, P->gi, P->hnexti, P->stat_in, P->bnormi,
@@ -905,7 +927,8 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   dot_partial<double>(P->rhs, P->rhs, n, P->part3, nullptr, st);
   dot_finish(P->part3, P->scal, 1, st);
   WC4D_CUDA(cudaMemcpyAsync(P->bnorm, P->scal, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double* r0 = P->V + n;  // V[1] is free until the first Arnoldi step
+  const bool sb = P->split_basis;
+  double* r0 = sb ? P->V : P->V + n;  // V[1] is free until the first Arnoldi step
   if (use_x0) {
     launch_copy_d(x0, P->x, n, st);
     apply_A<double>(P, P->f64, P->plan_A, x0, r0, nullptr);
@@ -915,7 +938,8 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
     launch_copy_d(r0, P->rhs, n, st);
   }
   dot_partial<double>(r0, r0, n, P->part2, nullptr, st);
-  gm_init<double>(r0, P->part2, P->V, P->g, P->stat, P->o.tol, n, st);
+  gm_init<double>(r0, P->part2, sb ? P->vcur : P->V, P->g, P->stat, P->o.tol, n, st);
+  if (sb) gm_split(P->vcur, P->Vh, P->Vl, n, nullptr, st);
   WC4D_CUDA(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)ldh * P->maxit, st));
   int it = 0;
   int status = WC4D_OK;
@@ -936,24 +960,49 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
     const int batch = std::min(P->o.check_every, P->maxit - it);
     if (batch <= 0) break;
     if (need_normalize) {
-      gm_normalize<double>(P->V + (int64_t)it * n, P->hnext, P->V + (int64_t)it * n, n, nullptr, st);
+      if (sb)
+        gm_normalize_df(P->wbuf, P->hnext, P->vcur, P->Vh + (int64_t)it * P->ldb, P->Vl + (int64_t)it * P->ldb, n,
+                        nullptr, st);
+      else
+        gm_normalize<double>(P->V + (int64_t)it * n, P->hnext, P->V + (int64_t)it * n, n, nullptr, st);
       need_normalize = false;
     }
     for (int b = 0; b < batch; ++b) {
       const int j = it + b;
-      double* vj = P->V + (int64_t)j * n;
+      double* vj = sb ? P->vcur : P->V + (int64_t)j * n;
       double* zj = P->Z + (int64_t)j * n;
-      double* w = P->V + (int64_t)(j + 1) * n;
+      double* w = sb ? P->wbuf : P->V + (int64_t)(j + 1) * n;
+      if (sb) {
+        if (P->o.precision == WC4D_PREC_MIXED)
+          inner_solve(P, vj, zj);
+        else
+          apply_P<double>(P, which, P->f64, vj, zj, done);
+        apply_A<double>(P, P->f64, P->plan_A, zj, w, done);
+        const int nc = orth_chunks(n);
+        gm_split(w, P->wh, P->wl, n, done, st);
+        const int64_t lb = P->ldb;
+        gm_mdot_df(P->Vh, P->Vl, lb, j + 1, P->wh, P->wl, n, P->part, done, st);
+        gm_mdot_reduce(P->part, j + 1, nc, P->h1, done, st);
+        gm_mupdate_df(P->Vh, P->Vl, lb, j + 1, P->h1, w, P->wh, P->wl, n, done, st);
+        gm_mdot_df(P->Vh, P->Vl, lb, j + 1, P->wh, P->wl, n, P->part, done, st);
+        gm_mdot_reduce(P->part, j + 1, nc, P->h2, done, st);
+        gm_mupdate_df(P->Vh, P->Vl, lb, j + 1, P->h2, w, P->wh, P->wl, n, done, st);
+        dot_partial<double>(w, w, n, P->part2, done, st);
+        gm_hessenberg(j, P->h1, P->h2, P->part2, P->H, ldh, P->cs, P->sn, P->g, P->hnext, P->stat, P->bnorm, st);
+        gm_normalize_df(w, P->hnext, P->vcur, P->Vh + (int64_t)(j + 1) * P->ldb, P->Vl + (int64_t)(j + 1) * P->ldb, n,
+                        done, st);
+        continue;
+      }
       if (P->o.precision == WC4D_PREC_MIXED)
         inner_solve(P, vj, zj);
       else
         apply_P<double>(P, which, P->f64, vj, zj, done);
       apply_A<double>(P, P->f64, P->plan_A, zj, w, done);
       gm_mdot<double>(P->V, n, j + 1, w, n, P->part, done, st);
-      gm_mdot_reduce(P->part, j + 1, P->h1, done, st);
+      gm_mdot_reduce(P->part, j + 1, orth_chunks(n), P->h1, done, st);
       gm_mupdate<double>(P->V, n, j + 1, P->h1, w, n, done, st);
       gm_mdot<double>(P->V, n, j + 1, w, n, P->part, done, st);
-      gm_mdot_reduce(P->part, j + 1, P->h2, done, st);
+      gm_mdot_reduce(P->part, j + 1, orth_chunks(n), P->h2, done, st);
       gm_mupdate<double>(P->V, n, j + 1, P->h2, w, n, done, st);
       dot_partial<double>(w, w, n, P->part2, done, st);
       gm_hessenberg(j, P->h1, P->h2, P->part2, P->H, ldh, P->cs, P->sn, P->g, P->hnext, P->stat, P->bnorm, st);
