@@ -265,7 +265,8 @@ def run_gpu(args):
     if args.modes:
         keep = args.modes.split(",")
         modes = {m: o for m, o in modes.items() if m in keep}
-    G = wc4d.Problem.from_workload(w, dr, modes["fp64"], stream=stream.cuda_stream)
+    G = wc4d.Problem.from_workload(w, dr, wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat),
+                                   stream=stream.cuda_stream)
     rhs = G.synthesize_rhs(dr)
     G.close()
     x = torch.zeros(w.n, dtype=torch.float64, device=dev)

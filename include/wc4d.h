@@ -97,7 +97,8 @@ typedef struct {
   double stencil[3];         /* STENCIL3 coefficients (c0, c1, c2)                      */
   int32_t band_lo, band_hi;  /* BANDED: offsets; band_lo + band_hi + 1 <= s             */
   const double* bands;       /* BANDED: [N][s][band_lo+band_hi+1],
-                                bands[i-1][j][o+band_lo] = (M_i)[j][(j+o) mod s]        */
+                                bands[i-1][j][o+band_lo] = (M_i)[j][(j+o) mod s];
+                                may be NULL (all zero) when wc4d_l96_gauss_newton fills it */
   const int32_t* obs_idx;    /* [p] strictly increasing indices in [0, s)               */
   int32_t cov_kind;          /* WC4D_COV_*                                              */
   const double* B;           /* DENSE: s x s                                            */
@@ -197,6 +198,41 @@ int wc4d_apply_fp32(wc4d_problem* prob, int32_t which, const float* v, float* ou
  * B and R (not Rhat).  Synchronises the stream.  Errors: ARG (banded model),
  * NOT_SPD, NOMEM, CUDA. */
 int wc4d_synthesize_rhs(wc4d_problem* prob, const double* z_b, const double* z_r, int32_t mem_kind, double* rhs);
+
+/* Lorenz-96 incremental weak-constraint 4D-Var (Sec. 2.1, Sec. 7.1).
+ * The problem must be set up with model_kind = WC4D_MODEL_BANDED,
+ * band_lo = 8 * steps_per_obs and band_hi = 4 * steps_per_obs (the reach of
+ * steps_per_obs RK4 steps of dx_j/dt = (x_{j+1} - x_{j-2}) x_{j-1} - x_j + F);
+ * its bands may be NULL at setup (they are rebuilt here).  Each outer loop l:
+ * M_t = exact Jacobian of the RK4 steps about x^(l)_{t-1} (banded),
+ * b_0 = x_b - x^(l)_0, b_t = M_t(x^(l)_{t-1}) - x^(l)_t (nonlinear forecast),
+ * d_t = y_t - H x^(l)_t, solve the saddle-point system with the set-up
+ * Krylov method / preconditioner, x^(l+1) = x^(l) + dx.  B, Q, R and their
+ * factors are reused across loops.
+ *   xb: s doubles; y: (N+1) p doubles (time-major); traj: (N+1) s doubles,
+ *   in: the initial trajectory when init_background = 0 (else ignored and
+ *   replaced by the background forecast from xb), out: the final trajectory;
+ *   all three host or all device per mem_kind.
+ *   loop_info: NULL or outer_loops entries, one per inner solve.
+ * Limits: s <= 4096 (the state and its tangent live in shared memory).
+ * Returns the first failing inner solve's status (the loop stops there).
+ * Synchronises the stream. */
+typedef struct {
+  double forcing;            /* F (8 in Sec. 7.1)                    */
+  double dt;                 /* RK4 step                             */
+  int32_t steps_per_obs;     /* RK4 steps between observation times  */
+  int32_t outer_loops;       /* Gauss-Newton iterations              */
+} wc4d_l96_params;
+int wc4d_l96_gauss_newton(wc4d_problem* prob, const wc4d_l96_params* prm, const double* xb, const double* y,
+                          double* traj, int32_t init_background, int32_t mem_kind, wc4d_info* loop_info);
+
+/* The linearisation half of one Gauss-Newton outer loop: rebuild the
+ * problem's banded M_t about traj (Jacobians of the RK4 steps) and write the
+ * right-hand side (b, d, 0) about traj into rhs (n doubles).  Same
+ * requirements and layouts as wc4d_l96_gauss_newton; xb, y, traj, rhs all host
+ * or all device per mem_kind.  Synchronises the stream. */
+int wc4d_l96_linearize(wc4d_problem* prob, const wc4d_l96_params* prm, const double* xb, const double* y,
+                       const double* traj, int32_t mem_kind, double* rhs);
 
 /* Problem sizes: n (vector length), s, N, p. */
 int wc4d_problem_dims(const wc4d_problem* prob, int64_t* n, int32_t* s, int32_t* N, int32_t* p);

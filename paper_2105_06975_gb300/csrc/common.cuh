@@ -18,11 +18,18 @@ struct Error {
 };
 
 void set_error(const std::string& msg);
+inline const char* src_name(const char* path) {
+  const char* b = path;
+  for (const char* q = path; *q; ++q)
+    if (*q == '/') b = q + 1;
+  return b;
+}
 #define WC4D_CUDA(call)                                                              \
   do {                                                                               \
     cudaError_t e_ = (call);                                                         \
     if (e_ != cudaSuccess)                                                           \
-      throw ::wc4d::Error{WC4D_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+      throw ::wc4d::Error{WC4D_ERR_CUDA, std::string(#call) + " at " + ::wc4d::src_name(__FILE__) + ":" + \
+                                             std::to_string(__LINE__) + ": " + cudaGetErrorString(e_)};     \
   } while (0)
 // every kernel launch of the library is followed by this: it counts the
 // launch (wc4d_get_stats) and turns a launch error into an exception

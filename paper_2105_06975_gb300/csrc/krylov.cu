@@ -545,42 +545,43 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_mdot_df_kernel(const float* __
   if (ran != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ran = 1;
   __shared__ double sh[DOT_THREADS / 32][ORTH_G];
   const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
-  const int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x;  // float4 index
-  const bool in = q < n4;
-  const float4 xh = in ? reinterpret_cast<const float4*>(wh)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 xl = in ? reinterpret_cast<const float4*>(wl)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-  double acc[ORTH_G];
+  const int gn = min(ORTH_G, cnt - i0);
+  float s[ORTH_G], c[ORTH_G];
 #pragma unroll
-  for (int g = 0; g < ORTH_G; ++g) {
-    float s = 0.f, c = 0.f;
-    if (in && i0 + g < cnt) {
-      const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
-      const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
-      dfk_mac(s, c, a.x, b.x, xh.x, xl.x);
-      dfk_mac(s, c, a.y, b.y, xh.y, xl.y);
-      dfk_mac(s, c, a.z, b.z, xh.z, xl.z);
-      dfk_mac(s, c, a.w, b.w, xh.w, xl.w);
+  for (int g = 0; g < ORTH_G; ++g) s[g] = c[g] = 0.f;
+  for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
+    const float4 xh = reinterpret_cast<const float4*>(wh)[q];
+    const float4 xl = reinterpret_cast<const float4*>(wl)[q];
+#pragma unroll
+    for (int g = 0; g < ORTH_G; ++g) {
+      if (g < gn) {
+        const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
+        const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
+        dfk_mac(s[g], c[g], a.x, b.x, xh.x, xl.x);
+        dfk_mac(s[g], c[g], a.y, b.y, xh.y, xl.y);
+        dfk_mac(s[g], c[g], a.z, b.z, xh.z, xl.z);
+        dfk_mac(s[g], c[g], a.w, b.w, xh.w, xl.w);
+      }
     }
-    acc[g] = (double)s + (double)c;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g < ORTH_G; ++g) {
-    const double v = warp_sum(acc[g]);
+    const double v = warp_sum((double)s[g] + (double)c[g]);
     if (lane == 0) sh[wid][g] = v;
   }
   __syncthreads();
   if (threadIdx.x < ORTH_G && i0 + threadIdx.x < cnt) {
-    double s = 0.0;
-    for (int k = 0; k < DOT_THREADS / 32; ++k) s += sh[k][threadIdx.x];
-    part[(int64_t)(i0 + threadIdx.x) * gridDim.x + chunk] = s;
+    double v = 0.0;
+    for (int k = 0; k < DOT_THREADS / 32; ++k) v += sh[k][threadIdx.x];
+    part[(int64_t)(i0 + threadIdx.x) * gridDim.x + chunk] = v;
   }
 }
 void gm_mdot_df(const float* Vh, const float* Vl, int64_t ldv, int cnt, const float* wh, const float* wl, int64_t n,
                 double* part, const int* done, cudaStream_t st) {
   int* ran = prof_begin(PROF_ORTH, (double)(cnt + 1) * n * 8.0, st);
   const int64_t n4 = (n + 3) / 4;
-  dim3 grid((unsigned)((n4 + DOT_THREADS - 1) / DOT_THREADS), (cnt + ORTH_G - 1) / ORTH_G);
+  dim3 grid((unsigned)dot_chunks(n, cnt), (cnt + ORTH_G - 1) / ORTH_G);
   gm_mdot_df_kernel<<<grid, DOT_THREADS, 0, st>>>(Vh, Vl, ldv, cnt, wh, wl, n4, part, done, ran);
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
@@ -608,16 +609,16 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_mupdate_df_kernel(const float*
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
     float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
     int i = 0;
-    // four basis vectors per step: eight 16-byte loads in flight per thread
-    for (; i + 4 <= cnt; i += 4) {
-      float4 a[4], b[4];
+    // eight basis vectors per step: sixteen 16-byte loads in flight per thread
+    for (; i + 8 <= cnt; i += 8) {
+      float4 a[8], b[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         a[u] = reinterpret_cast<const float4*>(Vh + (int64_t)(i + u) * ldv)[q];
         b[u] = reinterpret_cast<const float4*>(Vl + (int64_t)(i + u) * ldv)[q];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const float hh = hsh[i + u], hl = hsl[i + u];
         dfk_mac(s[0], c[0], hh, hl, a[u].x, b[u].x);
         dfk_mac(s[1], c[1], hh, hl, a[u].y, b[u].y);
@@ -692,6 +693,349 @@ void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done,
   const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
   gm_split_kernel<<<nb, 256, 0, st>>>(w, wh, wl, n, done);
   WC4D_LAUNCH_CHECK();
+}
+
+// ------------------------------------------- delayed CGS2 Arnoldi (DF32 GMRES)
+// Classical Gram-Schmidt with the reorthogonalisation of each basis vector
+// delayed by one step (low-synchronisation CGS2, Bielich, Langou, Thomas,
+// Swirydowicz, Yamazaki and Boman, Parallel Computing 2022).  Step j applies the
+// operator to the candidate u_j (one projection done, not yet reorthogonalised)
+// and reads the basis twice instead of four times:
+//   dot pass:    a = [Q_j u_j]^T w,  c = [Q_j u_j]^T u_j,  w^T w
+//   coefficients: gamma = |u_j - Q_j c| (Pythagoras), q_j = (u_j - Q_j c)/gamma,
+//                b = Q_{j+1}^T w, Hessenberg column j-1 completed (see below)
+//   update pass: q_j and the next candidate u_{j+1} = (w - Q_{j+1} b) / alpha
+// The operator was applied to u_j, not q_j, so column j-1 of the Hessenberg
+// matrix is completed one step late from the identity
+//   A P^-1 q_{j-1} = Q_j (b_{j-1} - Hbar c_{j-1} + alpha_j c_j) / gamma_{j-1}
+//                    + (alpha_j gamma_j / gamma_{j-1}) q_j,
+// Hbar being the unrotated Hessenberg columns 0..j-2.  The preconditioned
+// candidates Z~_j = P^-1 u_j are stored as computed; with U = Q T (T upper
+// triangular, columns [c_j; gamma_j]) the solution is x0 + Z~ T^-1 y, so the
+// rounding of the preconditioner never enters the residual (as in CGS2 GMRES,
+// where Z holds the computed P^-1 q_j).
+
+// part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w
+__global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __restrict__ Vh,
+                                                                const float* __restrict__ Vl, int64_t ldv, int j,
+                                                                const float* __restrict__ wh,
+                                                                const float* __restrict__ wl, int64_t n4,
+                                                                double* __restrict__ part, const int* done,
+                                                                int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ran = 1;
+  __shared__ double sh[DOT_THREADS / 32][2 * ORTH_G + 1];
+  const int cnt = j + 1;
+  const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
+  const int gn = min(ORTH_G, cnt - i0);
+  const bool first = blockIdx.y == 0;
+  float s[2 * ORTH_G + 1], c[2 * ORTH_G + 1];
+#pragma unroll
+  for (int g = 0; g < 2 * ORTH_G + 1; ++g) s[g] = c[g] = 0.f;
+  const float* uhp = Vh + (int64_t)j * ldv;
+  const float* ulp = Vl + (int64_t)j * ldv;
+  for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
+    const float4 xh = reinterpret_cast<const float4*>(wh)[q];
+    const float4 xl = reinterpret_cast<const float4*>(wl)[q];
+    const float4 uh = reinterpret_cast<const float4*>(uhp)[q];
+    const float4 ul = reinterpret_cast<const float4*>(ulp)[q];
+#pragma unroll
+    for (int g = 0; g < ORTH_G; ++g) {
+      if (g < gn) {
+        const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
+        const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
+        dfk_mac(s[g], c[g], a.x, b.x, xh.x, xl.x);
+        dfk_mac(s[g], c[g], a.y, b.y, xh.y, xl.y);
+        dfk_mac(s[g], c[g], a.z, b.z, xh.z, xl.z);
+        dfk_mac(s[g], c[g], a.w, b.w, xh.w, xl.w);
+        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.x, b.x, uh.x, ul.x);
+        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.y, b.y, uh.y, ul.y);
+        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.z, b.z, uh.z, ul.z);
+        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.w, b.w, uh.w, ul.w);
+      }
+    }
+    if (first) {
+      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.x, xl.x, xh.x, xl.x);
+      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.y, xl.y, xh.y, xl.y);
+      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.z, xl.z, xh.z, xl.z);
+      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.w, xl.w, xh.w, xl.w);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < 2 * ORTH_G + 1; ++g) {
+    const double v = warp_sum((double)s[g] + (double)c[g]);
+    if (lane == 0) sh[wid][g] = v;
+  }
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < 2 * ORTH_G + 1) {
+    double v = 0.0;
+    for (int k = 0; k < DOT_THREADS / 32; ++k) v += sh[k][r];
+    int row = -1;
+    if (r < ORTH_G) {
+      if (r < gn) row = i0 + r;
+    } else if (r < 2 * ORTH_G) {
+      if (r - ORTH_G < gn) row = cnt + i0 + r - ORTH_G;
+    } else if (first) {
+      row = 2 * cnt;
+    }
+    if (row >= 0) part[(int64_t)row * gridDim.x + chunk] = v;
+  }
+}
+void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float* wh, const float* wl, int64_t n,
+               double* part, const int* done, cudaStream_t st) {
+  int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st);
+  const int64_t n4 = (n + 3) / 4;
+  dim3 grid((unsigned)dot_chunks(n, j + 1), (j + 1 + ORTH_G - 1) / ORTH_G);
+  gm_dc_dot_kernel<<<grid, DOT_THREADS, 0, st>>>(Vh, Vl, ldv, j, wh, wl, n4, part, done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+
+// One CTA.  red: the reduced dot rows (a, c, w^T w).  dc: scalar state
+// (DC_* slots), bprev / cprev: b and c of the previous step, e: the update
+// coefficients.  Completes Hessenberg column j-1 (raw into Hraw, rotated into
+// H), updates the Givens rotations, g and the status, and writes column j of
+// the triangular T with u_j = Q_j c_j + gamma_j q_j (T = [c_j; gamma_j]), so
+// that P^-1 Q = Z~ T^-1 for the stored Z~_j = P^-1 u_j.  Shared memory: the
+// column and the rotations (3j + 2 doubles, as the CGS2 Hessenberg kernel).
+__global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* __restrict__ red, double* dc,
+                                                          double* bprev, double* cprev, double* e, double* Hraw,
+                                                          double* H, double* T, int ldh, double* cs, double* sn,
+                                                          double* g, double* hnext, DevStatus* stat,
+                                                          const double* bnorm) {
+  extern __shared__ double sm[];
+  __shared__ double sh[32];
+  if (*(volatile const int*)&stat->done) return;
+  const int cnt = j + 1;
+  const double* a = red;        // a_0..a_j
+  const double* c = red + cnt;  // c_0..c_{j-1}, c_j = u_j^T u_j
+  double* col = sm;             // [j + 2]
+  double* rc = col + j + 2;     // [j]
+  double* rs = rc + j;          // [j]
+  for (int i = threadIdx.x; i + 1 < j; i += blockDim.x) {
+    rc[i] = cs[i];
+    rs[i] = sn[i];
+  }
+  const double ww = red[2 * cnt];
+  const double uu = c[j];
+  double cc = 0.0, ca = 0.0;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cc += c[i] * c[i];
+    ca += c[i] * a[i];
+  }
+  cc = block_sum(cc, sh);
+  ca = block_sum(ca, sh);
+  const double gam = sqrt(fmax(uu - cc, 0.0));
+  const double igam = gam > 0.0 ? 1.0 / gam : 0.0;
+  const double bj = (a[j] - ca) * igam;  // q_j^T w
+  const double alpha = dc[DC_ALPHA];     // scale of u_j
+  const double gprev = dc[DC_GAMMA];
+  // column j-1: (b_{j-1} - Hbar c_{j-1} + alpha c_j) / gamma_{j-1}, sub-diagonal alpha gamma / gamma_{j-1}
+  if (j >= 1) {
+    const double ig = 1.0 / gprev;
+    for (int r = threadIdx.x; r < j; r += blockDim.x) {
+      double t0 = 0.0, t1 = 0.0;
+      int k = (r > 0 ? r - 1 : 0);
+      for (; k + 2 < j; k += 2) {
+        t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
+        t1 += Hraw[r + (int64_t)(k + 1) * ldh] * cprev[k + 1];
+      }
+      if (k + 1 < j) t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
+      col[r] = (bprev[r] - (t0 + t1) + alpha * c[r]) * ig;
+    }
+    if (threadIdx.x == 0) col[j] = alpha * gam * ig;
+  }
+  __syncthreads();
+  if (j >= 1) {
+    double* raw = Hraw + (int64_t)(j - 1) * ldh;
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) raw[r] = col[r];
+  }
+  {
+    double* tc = T + (int64_t)j * ldh;
+    for (int r = threadIdx.x; r < j; r += blockDim.x) tc[r] = c[r];
+    if (threadIdx.x == 0) tc[j] = gam;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (j == 0) {
+      g[0] = dc[DC_BETA] * gam;  // r0 = ||r0|| u_0 = (||r0|| gamma_0) q_0
+      stat->iters = 0;
+      if (!(gam > 0.0) || !isfinite(gam)) {
+        stat->status = isfinite(gam) ? WC4D_ERR_BREAKDOWN : WC4D_ERR_NONFINITE;
+        stat->done = 1;
+      }
+    } else {
+      const int jc = j - 1;  // column being completed
+      *hnext = col[j];
+      for (int i = 0; i < jc; ++i) {
+        const double x = col[i], y = col[i + 1];
+        col[i] = rc[i] * x + rs[i] * y;
+        col[i + 1] = -rs[i] * x + rc[i] * y;
+      }
+      double cr = 1.0, sr = 0.0;
+      if (col[jc + 1] != 0.0) {
+        const double rr = hypot(col[jc], col[jc + 1]);
+        cr = col[jc] / rr;
+        sr = col[jc + 1] / rr;
+      }
+      cs[jc] = cr;
+      sn[jc] = sr;
+      col[jc] = cr * col[jc] + sr * col[jc + 1];
+      col[jc + 1] = 0.0;
+      const double gj = g[jc];
+      g[jc + 1] = -sr * gj;
+      g[jc] = cr * gj;
+      const double est = fabs(g[jc + 1]) / *bnorm;
+      stat->iters = j;
+      stat->est = est;
+      if (!isfinite(est) || !isfinite(gam)) {
+        stat->status = WC4D_ERR_NONFINITE;
+        stat->done = 1;
+      } else if (est <= stat->tol_est || !(gam > 0.0)) {
+        stat->done = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (j >= 1) {
+    double* out = H + (int64_t)(j - 1) * ldh;
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) out[r] = col[r];
+  }
+  // b = (a_0..a_{j-1}, bj); next candidate scale by Pythagoras: |w - Q b|^2 = w^T w - b^T b
+  double bb = 0.0;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) bb += a[i] * a[i];
+  bb = block_sum(bb, sh) + bj * bj;  // block_sum ends with a barrier: bprev / cprev reads are done
+  const double ratio = bj * igam;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    bprev[i] = a[i];
+    cprev[i] = c[i];
+    e[i] = a[i] - ratio * c[i];
+  }
+  if (threadIdx.x == 0) {
+    bprev[j] = bj;
+    e[j] = ratio;
+    const double a2 = fmax(ww - bb, ww * 1e-30);
+    const double an = a2 > 0.0 ? sqrt(a2) : 1.0;
+    dc[DC_GAMMA] = gam;
+    dc[DC_ALPHA] = an;
+    dc[DC_IGAMMA] = igam;
+    dc[DC_IALPHA] = a2 > 0.0 ? 1.0 / an : 0.0;
+  }
+}
+void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
+                double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
+                const double* bnorm, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (3 * (size_t)j + 2);
+  gm_dc_coef_kernel<<<1, 1024, smem, st>>>(j, red, dc, bprev, cprev, e, Hraw, H, T, ldh, cs, sn, g, hnext, stat,
+                                           bnorm);
+  WC4D_LAUNCH_CHECK();
+}
+
+// q_j = (u_j - Q_j c) / gamma into slot j (in place), u_{j+1} = (w - Q_j e' - e_j u_j) / alpha
+// into slot j+1 and into v (double, the next operator input).  Both sums in
+// double-float; 4 elements per thread, 16-byte loads.
+__global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, float* Vl, int64_t ldv, int j,
+                                                                   const double* __restrict__ e,
+                                                                   const double* __restrict__ cv,
+                                                                   const double* __restrict__ dc,
+                                                                   const double* __restrict__ w,
+                                                                   double* __restrict__ v, int64_t n,
+                                                                   const int* done, int* ran) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  extern __shared__ float cf[];  // e hi/lo [j], c hi/lo [j]
+  float* eh = cf;
+  float* el = eh + j;
+  float* ch = el + j;
+  float* cl = ch + j;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    const float x = __double2float_rn(e[i]);
+    eh[i] = x;
+    el[i] = __double2float_rn(e[i] - (double)x);
+    const float y = __double2float_rn(cv[i]);
+    ch[i] = y;
+    cl[i] = __double2float_rn(cv[i] - (double)y);
+  }
+  __syncthreads();
+  const double ej = e[j], igam = dc[DC_IGAMMA], ialpha = dc[DC_IALPHA];
+  const int64_t n4 = (n + 3) / 4;
+  float* qh = Vh + (int64_t)j * ldv;
+  float* ql = Vl + (int64_t)j * ldv;
+  float* nh = Vh + (int64_t)(j + 1) * ldv;
+  float* nl = Vl + (int64_t)(j + 1) * ldv;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+    float se[4] = {0.f, 0.f, 0.f, 0.f}, ce[4] = {0.f, 0.f, 0.f, 0.f};
+    float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    int i = 0;
+    for (; i + 4 <= j; i += 4) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = reinterpret_cast<const float4*>(Vh + (int64_t)(i + u) * ldv)[q];
+        b[u] = reinterpret_cast<const float4*>(Vl + (int64_t)(i + u) * ldv)[q];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float h1 = eh[i + u], l1 = el[i + u], h2 = ch[i + u], l2 = cl[i + u];
+        dfk_mac(se[0], ce[0], h1, l1, a[u].x, b[u].x);
+        dfk_mac(se[1], ce[1], h1, l1, a[u].y, b[u].y);
+        dfk_mac(se[2], ce[2], h1, l1, a[u].z, b[u].z);
+        dfk_mac(se[3], ce[3], h1, l1, a[u].w, b[u].w);
+        dfk_mac(sc[0], cc[0], h2, l2, a[u].x, b[u].x);
+        dfk_mac(sc[1], cc[1], h2, l2, a[u].y, b[u].y);
+        dfk_mac(sc[2], cc[2], h2, l2, a[u].z, b[u].z);
+        dfk_mac(sc[3], cc[3], h2, l2, a[u].w, b[u].w);
+      }
+    }
+    for (; i < j; ++i) {
+      const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)i * ldv)[q];
+      const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)i * ldv)[q];
+      const float h1 = eh[i], l1 = el[i], h2 = ch[i], l2 = cl[i];
+      dfk_mac(se[0], ce[0], h1, l1, a.x, b.x);
+      dfk_mac(se[1], ce[1], h1, l1, a.y, b.y);
+      dfk_mac(se[2], ce[2], h1, l1, a.z, b.z);
+      dfk_mac(se[3], ce[3], h1, l1, a.w, b.w);
+      dfk_mac(sc[0], cc[0], h2, l2, a.x, b.x);
+      dfk_mac(sc[1], cc[1], h2, l2, a.y, b.y);
+      dfk_mac(sc[2], cc[2], h2, l2, a.z, b.z);
+      dfk_mac(sc[3], cc[3], h2, l2, a.w, b.w);
+    }
+    const float4 uh = reinterpret_cast<const float4*>(qh)[q];
+    const float4 ul = reinterpret_cast<const float4*>(ql)[q];
+    const float uhs[4] = {uh.x, uh.y, uh.z, uh.w}, uls[4] = {ul.x, ul.y, ul.z, ul.w};
+    float oqh[4], oql[4], onh[4], onl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t el_ = 4 * q + u;
+      const double uj = (double)uhs[u] + (double)uls[u];
+      const double qv = (uj - ((double)sc[u] + (double)cc[u])) * igam;
+      double nv = 0.0;
+      if (el_ < n) {
+        nv = (w[el_] - ((double)se[u] + (double)ce[u]) - ej * uj) * ialpha;
+        v[el_] = nv;
+      }
+      oqh[u] = __double2float_rn(qv);
+      oql[u] = __double2float_rn(qv - (double)oqh[u]);
+      onh[u] = __double2float_rn(nv);
+      onl[u] = __double2float_rn(nv - (double)onh[u]);
+    }
+    reinterpret_cast<float4*>(qh)[q] = make_float4(oqh[0], oqh[1], oqh[2], oqh[3]);
+    reinterpret_cast<float4*>(ql)[q] = make_float4(oql[0], oql[1], oql[2], oql[3]);
+    reinterpret_cast<float4*>(nh)[q] = make_float4(onh[0], onh[1], onh[2], onh[3]);
+    reinterpret_cast<float4*>(nl)[q] = make_float4(onl[0], onl[1], onl[2], onl[3]);
+  }
+}
+void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
+                  const double* w, double* v, int64_t n, const int* done, cudaStream_t st) {
+  int* ran = prof_begin(PROF_ORTH, (double)(j + 1) * n * 8.0 + 4.0 * n * 8.0, st);
+  const int64_t n4 = (n + 3) / 4;
+  const int nb = (int)std::min<int64_t>((n4 + DOT_THREADS - 1) / DOT_THREADS, 152 * 16);
+  gm_dc_update_kernel<<<nb, DOT_THREADS, sizeof(float) * 4 * std::max(j, 1), st>>>(Vh, Vl, ldv, j, e, c, dc, w, v, n,
+                                                                                  done, ran);
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
 }
 
 // ---------------------------------------------------------------- vectors

@@ -11,6 +11,16 @@ constexpr int ORTH_U = 4;                         // elements per thread
 constexpr int ORTH_G = 8;                         // basis vectors per block
 constexpr int ORTH_CHUNK = DOT_THREADS * ORTH_U;  // elements per block
 inline int orth_chunks(int64_t n) { return (int)((n + ORTH_CHUNK - 1) / ORTH_CHUNK); }
+// Chunk count of the split-basis dot kernels for cnt basis vectors: enough CTAs
+// (chunks x vector groups) to fill the GPU about eight deep, each thread
+// striding over several float4 so the block reduction is amortised.  The
+// partial buffer holds orth_chunks(n) >= this many partials per row.
+inline int dot_chunks(int64_t n, int cnt) {
+  const int maxc = orth_chunks(n);
+  const int groups = (cnt + ORTH_G - 1) / ORTH_G;
+  int c = (152 * 8 + groups - 1) / groups;
+  return c < 1 ? 1 : (c > maxc ? maxc : c);
+}
 
 struct DevStatus {
   int done;
@@ -72,6 +82,16 @@ void gm_mupdate_df(const float* Vh, const float* Vl, int64_t ldv, int cnt, const
 void gm_normalize_df(const double* w, const double* hnext, double* v, float* vh, float* vl, int64_t n,
                      const int* done, cudaStream_t st);
 void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done, cudaStream_t st);
+
+// delayed CGS2 Arnoldi on the split basis (DF32 GMRES): scalar state slots
+enum { DC_GAMMA = 0, DC_ALPHA, DC_IGAMMA, DC_IALPHA, DC_BETA, DC_COUNT };
+void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float* wh, const float* wl, int64_t n,
+               double* part, const int* done, cudaStream_t st);
+void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
+                double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
+                const double* bnorm, cudaStream_t st);
+void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
+                  const double* w, double* v, int64_t n, const int* done, cudaStream_t st);
 
 // small vector ops
 template <typename T>

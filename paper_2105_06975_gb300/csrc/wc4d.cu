@@ -106,6 +106,11 @@ struct wc4d_problem {
   int64_t ldb = 0;  // leading dimension of the split basis
   float *Vh = nullptr, *Vl = nullptr, *wh = nullptr, *wl = nullptr;
   double *vcur = nullptr, *wbuf = nullptr;
+  // DF32 GMRES with delayed reorthogonalisation: raw Hessenberg, scalar state,
+  // previous b and c, update coefficients, reduced dot rows, operator scratch
+  bool dcgs = false;
+  double *Hraw = nullptr, *Tm = nullptr, *dcst = nullptr, *bprev = nullptr, *cprev = nullptr, *ecoef = nullptr;
+  double *red = nullptr, *yhat = nullptr;
   DevStatus* stat = nullptr;
   DevStatus* h_stat = nullptr;
   double* h_scal = nullptr;
@@ -471,7 +476,6 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   if (d->model_kind == WC4D_MODEL_BANDED) {
     WC4D_CHECK(d->band_lo >= 0 && d->band_hi >= 0 && d->band_lo + d->band_hi + 1 <= d->s, WC4D_ERR_ARG,
                "band offsets must satisfy lo, hi >= 0 and lo + hi + 1 <= s");
-    WC4D_CHECK(d->N == 0 || d->bands != nullptr, WC4D_ERR_ARG, "bands is null");
   }
   WC4D_CHECK(d->cov_kind == WC4D_COV_DENSE || d->cov_kind == WC4D_COV_SOAR, WC4D_ERR_ARG, "bad cov_kind");
   if (d->cov_kind == WC4D_COV_DENSE)
@@ -537,7 +541,8 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   if (d->model_kind == WC4D_MODEL_BANDED) {
     const int w = d->band_lo + d->band_hi + 1;
     P->d_bands = P->alloc<double>((int64_t)N * s * w);
-    if (N > 0) copy_in(P->d_bands, d->bands, sizeof(double) * (size_t)N * s * w, d->mem_kind, st);
+    if (N > 0 && d->bands) copy_in(P->d_bands, d->bands, sizeof(double) * (size_t)N * s * w, d->mem_kind, st);
+    if (N > 0 && !d->bands) WC4D_CUDA(cudaMemsetAsync(P->d_bands, 0, sizeof(double) * (size_t)N * s * w, st));
     P->md.bands = P->d_bands;
     P->md.lo = d->band_lo;
     P->md.hi = d->band_hi;
@@ -715,6 +720,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->maxit = o->maxit;
   const int64_t nvec = (o->krylov == WC4D_KRYLOV_MINRES) ? 12 : (int64_t)o->maxit + 1;
   P->split_basis = (o->krylov != WC4D_KRYLOV_MINRES) && (o->precision != WC4D_PREC_FP64);
+  P->dcgs = (o->krylov == WC4D_KRYLOV_GMRES) && (o->precision == WC4D_PREC_DF32);
   if (P->split_basis) {
     // leading dimension padded to 4 floats (16-byte loads); padding stays zero
     P->ldb = (n + 3) / 4 * 4;
@@ -732,9 +738,19 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   } else {
     P->V = P->alloc<double>(nvec * n);
   }
-  if (o->krylov != WC4D_KRYLOV_MINRES) P->Z = P->alloc<double>((int64_t)o->maxit * n);
+  if (o->krylov != WC4D_KRYLOV_MINRES) P->Z = P->alloc<double>((int64_t)(o->maxit + (P->dcgs ? 1 : 0)) * n);
   const int ldh = o->maxit + 1;
   P->H = P->alloc<double>((int64_t)ldh * o->maxit);
+  if (P->dcgs) {
+    P->Hraw = P->alloc<double>((int64_t)ldh * o->maxit);
+    P->Tm = P->alloc<double>((int64_t)ldh * (o->maxit + 1));
+    P->dcst = P->alloc<double>(DC_COUNT);
+    P->bprev = P->alloc<double>(o->maxit + 2);
+    P->cprev = P->alloc<double>(o->maxit + 2);
+    P->ecoef = P->alloc<double>(o->maxit + 2);
+    P->red = P->alloc<double>(2 * (int64_t)o->maxit + 4);
+    P->yhat = P->alloc<double>(o->maxit + 1);
+  }
   P->cs = P->alloc<double>(o->maxit + 1);
   P->sn = P->alloc<double>(o->maxit + 1);
   P->g = P->alloc<double>(o->maxit + 2);
@@ -744,7 +760,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->hnext = P->alloc<double>(2);
   P->bnorm = P->alloc<double>(2);
   P->scal = P->alloc<double>(8);
-  P->part = P->alloc<double>((int64_t)std::max(DOT_BLOCKS, orth_chunks(P->n)) * (o->maxit + 2));
+  P->part = P->alloc<double>((int64_t)std::max(DOT_BLOCKS, orth_chunks(P->n)) * (2 * (int64_t)o->maxit + 4));
   P->part2 = P->alloc<double>(DOT_BLOCKS);
   P->part3 = P->alloc<double>(DOT_BLOCKS);
   P->sc = P->alloc<double>(2 * MS_COUNT);
@@ -916,7 +932,122 @@ static void inner_solve(wc4d_problem* P, const double* v, double* z) {
   P->inner_total += mi;
 }
 
+// GMRES with the delayed-reorthogonalisation Arnoldi on the split basis (DF32
+// mode).  Step j: Z~_j = P^-1 u_j, w = A Z~_j, one dot pass, the coefficient
+// kernel (completes Hessenberg column j-1, Givens, status, column j of T), one
+// update pass (q_j and u_{j+1}).  The solution is x0 + Z~ T^-1 y.
+static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
+  const int64_t n = P->n;
+  const int ldh = P->maxit + 1;
+  cudaStream_t st = P->st;
+  const int* done = &P->stat->done;
+  const int which = P->o.precond;
+  const int64_t lb = P->ldb;
+  int64_t nA = 0, nP = 0;
+  dot_partial<double>(P->rhs, P->rhs, n, P->part3, nullptr, st);
+  dot_finish(P->part3, P->scal, 1, st);
+  WC4D_CUDA(cudaMemcpyAsync(P->bnorm, P->scal, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double* r0 = P->V;
+  if (use_x0) {
+    launch_copy_d(P->x0, P->x, n, st);
+    apply_A<double>(P, P->f64, P->plan_A, P->x0, r0, nullptr);
+    vec_sub(P->rhs, r0, r0, n, st);
+    ++nA;
+  } else {
+    launch_copy_d(r0, P->rhs, n, st);
+  }
+  dot_partial<double>(r0, r0, n, P->part2, nullptr, st);
+  gm_init<double>(r0, P->part2, P->vcur, P->g, P->stat, P->o.tol, n, st);
+  WC4D_CUDA(cudaMemcpyAsync(P->dcst + DC_BETA, P->g, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  gm_split(P->vcur, P->Vh, P->Vl, n, nullptr, st);
+  WC4D_CUDA(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)ldh * P->maxit, st));
+  WC4D_CUDA(cudaMemsetAsync(P->Hraw, 0, sizeof(double) * (size_t)ldh * P->maxit, st));
+  int status = WC4D_OK;
+  double relres = 1.0;
+  bool converged = false;
+  int it = 0;           // columns completed
+  int next = 0;         // next Arnoldi step to run
+  bool pending_update = false;
+  fetch_stat(P);
+  if (P->h_stat->done) {
+    status = P->h_stat->status;
+    if (status == 0) {
+      converged = true;
+      relres = 0.0;
+      if (use_x0)
+        launch_copy_d(P->x, P->x0, n, st);
+      else
+        WC4D_CUDA(cudaMemsetAsync(P->x, 0, sizeof(double) * n, st));
+    }
+  }
+  while (!converged && status == WC4D_OK) {
+    if (pending_update) {  // the step that stopped on a false convergence still owes its update pass
+      gm_dc_update(P->Vh, P->Vl, lb, next - 1, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, nullptr, st);
+      pending_update = false;
+    }
+    const int batch = std::min(P->o.check_every, P->maxit + 1 - next);
+    if (batch <= 0) break;
+    for (int b = 0; b < batch; ++b) {
+      const int j = next + b;
+      double* zj = P->Z + (int64_t)j * n;
+      apply_P<double>(P, which, P->f64, P->vcur, zj, done);
+      apply_A<double>(P, P->f64, P->plan_A, zj, P->wbuf, done);
+      gm_split(P->wbuf, P->wh, P->wl, n, done, st);
+      gm_dc_dot(P->Vh, P->Vl, lb, j, P->wh, P->wl, n, P->part, done, st);
+      gm_mdot_reduce(P->part, 2 * (j + 1) + 1, dot_chunks(n, j + 1), P->red, done, st);
+      gm_dc_coef(j, P->red, P->dcst, P->bprev, P->cprev, P->ecoef, P->Hraw, P->H, P->Tm, ldh, P->cs, P->sn, P->g,
+                 P->hnext, P->stat, P->bnorm, st);
+      if (j < P->maxit)
+        gm_dc_update(P->Vh, P->Vl, lb, j, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, done, st);
+    }
+    fetch_stat(P);
+    it = P->h_stat->iters;
+    if (P->h_stat->status != 0) {
+      status = P->h_stat->status;
+      break;
+    }
+    const int ran_to = next + batch;  // steps next..ran_to-1 were issued
+    if (P->h_stat->done || ran_to > P->maxit) {
+      const int k = std::min(it, P->maxit);
+      gm_solve_y(P->H, ldh, P->g, k, P->y, st);
+      gm_solve_y(P->Tm, ldh, P->y, k, P->yhat, st);  // T yhat = y
+      gm_combine<double, double>(P->Z, n, k, P->yhat, use_x0 ? P->x0 : nullptr, P->x, n, st);
+      relres = true_relres(P, P->rhs, P->x);
+      ++nA;
+      if (relres <= P->o.tol) {
+        converged = true;
+        break;
+      }
+      if (!P->h_stat->done) break;  // maxit
+      double hn = 0;
+      WC4D_CUDA(cudaMemcpy(&hn, P->hnext, sizeof(double), cudaMemcpyDeviceToHost));
+      if (hn == 0.0 || it >= P->maxit) {
+        status = (it >= P->maxit) ? WC4D_OK : WC4D_ERR_BREAKDOWN;
+        break;
+      }
+      resume_after_false_stop(P, P->h_stat->est, relres);
+      next = it + 1;  // step `it` completed its coefficients; its update pass is pending
+      pending_update = true;
+    } else {
+      next = ran_to;
+    }
+  }
+  nA += it + 1;
+  nP += it + 1;
+  if (!converged && status == WC4D_OK) status = WC4D_ERR_MAXIT;
+  if (info) {
+    info->iters = it;
+    info->relres_true = relres;
+    info->relres_est = P->h_stat->est;
+    info->n_apply_A = nA;
+    info->n_apply_P = nP;
+    info->inner_iters = 0;
+  }
+  return status;
+}
+
 static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
+  if (P->dcgs) return solve_gmres_dc(P, info, use_x0);
   const int64_t n = P->n;
   const int ldh = P->maxit + 1;
   cudaStream_t st = P->st;
@@ -978,7 +1109,7 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
         else
           apply_P<double>(P, which, P->f64, vj, zj, done);
         apply_A<double>(P, P->f64, P->plan_A, zj, w, done);
-        const int nc = orth_chunks(n);
+        const int nc = dot_chunks(n, j + 1);
         gm_split(w, P->wh, P->wl, n, done, st);
         const int64_t lb = P->ldb;
         gm_mdot_df(P->Vh, P->Vl, lb, j + 1, P->wh, P->wl, n, P->part, done, st);
@@ -1045,6 +1176,112 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
     info->n_apply_P = nP;
     info->inner_iters = (int)P->inner_total;
   }
+  return status;
+}
+
+void l96_forecast(const double* in, double* out, int count, int s, double F, double dt, int steps, cudaStream_t st);
+void l96_background(const double* xb, double* traj, int N, int s, double F, double dt, int steps, cudaStream_t st);
+void l96_tlm_bands(const double* traj, double* bands, int N, int s, int lo, int hi, double F, double dt, int steps,
+                   cudaStream_t st);
+void gn_rhs(const double* xb, const double* traj, const double* fc, const double* y, const int* obs, int s, int N,
+            int p, double* rhs, cudaStream_t st);
+
+static void l96_check(wc4d_problem* P, const wc4d_l96_params* prm) {
+  WC4D_CHECK(prm != nullptr, WC4D_ERR_ARG, "null parameters");
+  WC4D_CHECK(P->md.kind == WC4D_MODEL_BANDED, WC4D_ERR_ARG, "Gauss-Newton for Lorenz-96 needs a BANDED problem");
+  WC4D_CHECK(prm->steps_per_obs >= 1 && prm->outer_loops >= 0 && prm->dt > 0, WC4D_ERR_ARG, "bad L96 parameters");
+  WC4D_CHECK(P->md.lo == 8 * prm->steps_per_obs && P->md.hi == 4 * prm->steps_per_obs, WC4D_ERR_ARG,
+             "band offsets must be lo = 8 steps, hi = 4 steps");
+  WC4D_CHECK(P->s <= 4096, WC4D_ERR_ARG, "Lorenz-96 kernels keep the state in shared memory: s <= 4096");
+  WC4D_CHECK(P->md.lo + P->md.hi + 1 <= P->s, WC4D_ERR_ARG, "band wider than the state: colours would alias");
+}
+
+static void l96_linearize(wc4d_problem* P, const wc4d_l96_params* prm, const double* xb_in, const double* y_in,
+                          const double* traj_in, int mem_kind, double* rhs_out) {
+  l96_check(P, prm);
+  const int s = P->s, N = P->N, p = P->p;
+  cudaStream_t st = P->st;
+  double *xb = nullptr, *y = nullptr, *traj = nullptr, *fc = nullptr;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(xb);
+    cudaFree(y);
+    cudaFree(traj);
+    cudaFree(fc);
+  };
+  try {
+    WC4D_CUDA(cudaMalloc(&xb, sizeof(double) * s));
+    WC4D_CUDA(cudaMalloc(&y, sizeof(double) * P->np));
+    WC4D_CUDA(cudaMalloc(&traj, sizeof(double) * P->ns));
+    WC4D_CUDA(cudaMalloc(&fc, sizeof(double) * std::max<int64_t>(1, (int64_t)N * s)));
+    copy_in(xb, xb_in, sizeof(double) * s, mem_kind, st);
+    copy_in(y, y_in, sizeof(double) * P->np, mem_kind, st);
+    copy_in(traj, traj_in, sizeof(double) * P->ns, mem_kind, st);
+    l96_tlm_bands(traj, P->d_bands, N, s, P->md.lo, P->md.hi, prm->forcing, prm->dt, prm->steps_per_obs, st);
+    if (N > 0) l96_forecast(traj, fc, N, s, prm->forcing, prm->dt, prm->steps_per_obs, st);
+    gn_rhs(xb, traj, fc, y, P->d_obs, s, N, p, P->rhs, st);
+    WC4D_CUDA(cudaMemcpyAsync(rhs_out, P->rhs, sizeof(double) * P->n,
+                              mem_kind == WC4D_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    WC4D_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
+}
+
+static int l96_gauss_newton(wc4d_problem* P, const wc4d_l96_params* prm, const double* xb_in, const double* y_in,
+                            double* traj_io, bool init_bg, int mem_kind, wc4d_info* infos) {
+  l96_check(P, prm);
+  const int s = P->s, N = P->N, p = P->p;
+  cudaStream_t st = P->st;
+  std::vector<void*> tmp;
+  auto dalloc = [&](int64_t cnt) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(double) * (size_t)std::max<int64_t>(cnt, 1)) != cudaSuccess)
+      throw Error{WC4D_ERR_NOMEM, "cudaMalloc failed in Gauss-Newton"};
+    tmp.push_back(q);
+    return (double*)q;
+  };
+  int status = WC4D_OK;
+  try {
+    double* xb = dalloc(s);
+    double* y = dalloc(P->np);
+    double* traj = dalloc(P->ns);
+    double* fc = dalloc((int64_t)N * s);
+    copy_in(xb, xb_in, sizeof(double) * s, mem_kind, st);
+    copy_in(y, y_in, sizeof(double) * P->np, mem_kind, st);
+    if (init_bg)
+      l96_background(xb, traj, N, s, prm->forcing, prm->dt, prm->steps_per_obs, st);
+    else
+      copy_in(traj, traj_io, sizeof(double) * P->ns, mem_kind, st);
+    for (int l = 0; l < prm->outer_loops; ++l) {
+      l96_tlm_bands(traj, P->d_bands, N, s, P->md.lo, P->md.hi, prm->forcing, prm->dt, prm->steps_per_obs, st);
+      if (N > 0) l96_forecast(traj, fc, N, s, prm->forcing, prm->dt, prm->steps_per_obs, st);
+      gn_rhs(xb, traj, fc, y, P->d_obs, s, N, p, P->rhs, st);
+      wc4d_info loc{};
+      P->inner_total = 0;
+      const auto t0 = std::chrono::steady_clock::now();
+      const int rc = (P->o.krylov == WC4D_KRYLOV_MINRES) ? solve_minres(P, &loc, false) : solve_gmres(P, &loc, false);
+      loc.status = rc;
+      loc.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (infos) infos[l] = loc;
+      // x^(l+1) = x^(l) + dx  (dx = third block of the solution)
+      vec_axpby<double>(traj, P->x + P->ns + P->np, 1.0, 1.0, P->ns, st);
+      if (rc != WC4D_OK) {
+        status = rc;
+        break;
+      }
+    }
+    WC4D_CUDA(cudaMemcpyAsync(traj_io, traj, sizeof(double) * P->ns,
+                              mem_kind == WC4D_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    WC4D_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    for (void* q : tmp) cudaFree(q);
+    throw;
+  }
+  for (void* q : tmp) cudaFree(q);
   return status;
 }
 
@@ -1241,6 +1478,27 @@ int wc4d_synthesize_rhs(wc4d_problem* P, const double* z_b, const double* z_r, i
   WC4D_CHECK(P && z_b && z_r && rhs, WC4D_ERR_ARG, "null argument");
   WC4D_CHECK(mem_kind == WC4D_MEM_HOST || mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
   wc4d::synthesize_rhs(P, z_b, z_r, mem_kind, rhs);
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+int wc4d_l96_gauss_newton(wc4d_problem* P, const wc4d_l96_params* prm, const double* xb, const double* y,
+                          double* traj, int32_t init_background, int32_t mem_kind, wc4d_info* loop_info) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && xb && y && traj, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(mem_kind == WC4D_MEM_HOST || mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
+  const int rc = wc4d::l96_gauss_newton(P, prm, xb, y, traj, init_background != 0, mem_kind, loop_info);
+  if (rc != WC4D_OK) wc4d::set_error("an inner solve of the Gauss-Newton loop failed");
+  return rc;
+  WC4D_API_END
+}
+
+int wc4d_l96_linearize(wc4d_problem* P, const wc4d_l96_params* prm, const double* xb, const double* y,
+                       const double* traj, int32_t mem_kind, double* rhs) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && xb && y && traj && rhs, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(mem_kind == WC4D_MEM_HOST || mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
+  wc4d::l96_linearize(P, prm, xb, y, traj, mem_kind, rhs);
   return WC4D_OK;
   WC4D_API_END
 }

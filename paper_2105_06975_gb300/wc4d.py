@@ -99,6 +99,11 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class L96Params(ctypes.Structure):
+    _fields_ = [("forcing", ctypes.c_double), ("dt", ctypes.c_double), ("steps_per_obs", ctypes.c_int32),
+                ("outer_loops", ctypes.c_int32)]
+
+
 # names and signatures of every entry point declared in include/wc4d.h
 SIGNATURES = {
     "wc4d_default_opts": (None, [ctypes.POINTER(SolveOpts)]),
@@ -111,6 +116,11 @@ SIGNATURES = {
     "wc4d_apply_fp32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "wc4d_synthesize_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_void_p]),
+    "wc4d_l96_gauss_newton": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(L96Params), ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(Info)]),
+    "wc4d_l96_linearize": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(L96Params), ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "wc4d_problem_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), _ip, _ip, _ip]),
     "wc4d_get_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "wc4d_rhat_param": (ctypes.c_double, [ctypes.c_void_p]),
@@ -204,6 +214,16 @@ def wc4d_synthesize_rhs(h, zb_ptr: int, zr_ptr: int, mem_kind: int, rhs_ptr: int
                                       ctypes.c_void_p(rhs_ptr)))
 
 
+def wc4d_l96_gauss_newton(h, forcing, dt, steps, loops, xb_ptr, y_ptr, traj_ptr, init_background, mem_kind):
+    prm = L96Params(float(forcing), float(dt), int(steps), int(loops))
+    infos = (Info * int(loops))()
+    code = load().wc4d_l96_gauss_newton(h, ctypes.byref(prm), ctypes.c_void_p(xb_ptr), ctypes.c_void_p(y_ptr),
+                                        ctypes.c_void_p(traj_ptr), int(init_background), mem_kind, infos)
+    if code not in (WC4D_OK, WC4D_ERR_MAXIT):
+        _check(code)
+    return code, [infos[i] for i in range(int(loops))]
+
+
 def wc4d_problem_dims(h):
     n = ctypes.c_int64()
     s, N, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -278,7 +298,8 @@ class Problem:
     and copied by the library; the handle is freed by ``close()``/``__del__``."""
 
     def __init__(self, s, N, p, obs_idx, opts: SolveOpts, *, stencil=None, bands=None, band_lo=0, band_hi=0,
-                 B=None, Q=None, R=None, soar_b=None, soar_q=None, soar_r=None, stream: Optional[int] = None):
+                 banded=False, B=None, Q=None, R=None, soar_b=None, soar_q=None, soar_r=None,
+                 stream: Optional[int] = None):
         import torch
         d = ProblemDesc()
         d.s, d.N, d.p = int(s), int(N), int(p)
@@ -289,9 +310,9 @@ class Problem:
             keep.append(a)
             return a.ctypes.data
         d.obs_idx = host(obs_idx, np.int32)
-        if bands is not None:
+        if bands is not None or banded:
             d.model_kind = WC4D_MODEL_BANDED
-            d.bands = host(bands, np.float64)
+            d.bands = host(bands, np.float64) if bands is not None else None
             d.band_lo, d.band_hi = int(band_lo), int(band_hi)
         else:
             d.model_kind = WC4D_MODEL_STENCIL3
@@ -362,6 +383,25 @@ class Problem:
         zr = torch.from_numpy(np.ascontiguousarray(dr.z_r, dtype=np.float64)).cuda()
         rhs = torch.empty(self.n, dtype=torch.float64, device="cuda")
         wc4d_synthesize_rhs(self.h, zb.data_ptr(), zr.data_ptr(), WC4D_MEM_DEVICE, rhs.data_ptr())
+        return rhs
+
+    def l96_gauss_newton(self, forcing, dt, steps, loops, xb, y, traj=None):
+        """Host arrays in, final trajectory (N+1, s) and per-loop Info out."""
+        xb = np.ascontiguousarray(xb, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        out = np.zeros((self.N + 1, self.s)) if traj is None else np.ascontiguousarray(traj, dtype=np.float64).copy()
+        code, infos = wc4d_l96_gauss_newton(self.h, forcing, dt, steps, loops, xb.ctypes.data, y.ctypes.data,
+                                            out.ctypes.data, traj is None, WC4D_MEM_HOST)
+        return out, infos, code
+
+    def l96_linearize(self, forcing, dt, steps, xb, y, traj):
+        """Rebuild the banded M_t about traj; return the right-hand side (host)."""
+        xb, y, traj = (np.ascontiguousarray(a, dtype=np.float64) for a in (xb, y, traj))
+        rhs = np.zeros(self.n)
+        prm = L96Params(float(forcing), float(dt), int(steps), 0)
+        _check(load().wc4d_l96_linearize(self.h, ctypes.byref(prm), ctypes.c_void_p(xb.ctypes.data),
+                                         ctypes.c_void_p(y.ctypes.data), ctypes.c_void_p(traj.ctypes.data),
+                                         WC4D_MEM_HOST, ctypes.c_void_p(rhs.ctypes.data)))
         return rhs
 
     def matrix(self, which):
