@@ -83,11 +83,17 @@ enum { WC4D_PREC_FP64 = 0,        /* every product in native FP64 (DFMA)        
        WC4D_PREC_MIXED = 1,       /* FGMRES outer (FP64-accurate A) around an FP32 inner GMRES
                                      preconditioned by an FP32 copy of the chosen preconditioner
                                      (not in the paper)                                         */
-       WC4D_PREC_DF32 = 2 };      /* every covariance / factor product in double-float on the
+       WC4D_PREC_DF32 = 2,        /* every covariance / factor product in double-float on the
                                      FP32 pipe (operands split into two FP32 parts, exact
                                      product errors, TwoSum accumulation: ~48-bit products);
                                      recurrences, dots, factorisations and the true residual
                                      stay FP64 (not in the paper)                               */
+       WC4D_PREC_DF32_P32 = 3 };  /* GMRES only: A and the Arnoldi process as in DF32, the
+                                     preconditioner applied in FP32 (FP32 copies of the
+                                     operators and factors).  The DF32 Arnoldi keeps the
+                                     computed preconditioned vectors, so GMRES is flexible and
+                                     the FP32 rounding of P^-1 costs iterations, not accuracy
+                                     (not in the paper)                                         */
 
 typedef struct {
   int32_t s;                 /* state size per time level, >= 2                         */
@@ -177,12 +183,29 @@ int wc4d_apply_precond(wc4d_problem* prob, int32_t which, const double* v, doubl
 int wc4d_solve(wc4d_problem* prob, const double* rhs, double* x, int32_t use_x0,
                int32_t mem_kind, wc4d_info* info);
 
+/* Batched solve of count independent problems (assimilation windows of any
+ * s, N, p, model and precision, each set up by wc4d_setup_problem); not in the
+ * paper, whose experiments solve one window at a time.  Equivalent to calling
+ * wc4d_solve(probs[i], rhs[i], x[i], use_x0, mem_kind, &infos[i]) for every i,
+ * but windows run concurrently: `workers` host threads (0 = min(count, 8),
+ * at most 64) each own a non-blocking CUDA stream and take windows
+ * largest-first by (s^2 + p^2)(N+1).  Each problem's own stream is
+ * synchronised on entry (inputs produced on it are complete) and is restored
+ * on return.  probs: distinct problems on the current device; rhs[i], x[i]:
+ * n_i doubles each, all host or all device per mem_kind.  infos: NULL or
+ * count entries.  Blocks until every window has finished.  Returns the status
+ * of the lowest-indexed window that failed (its message names it), else OK.
+ * Not for concurrent use with wc4d_set_profiling (single-stream profile). */
+int wc4d_solve_batch(wc4d_problem* const* probs, int32_t count, const double* const* rhs, double* const* x,
+                     int32_t use_x0, int32_t mem_kind, int32_t workers, wc4d_info* infos);
+
 /* FP32 operators of the mixed-precision mode (not in the paper): out = A v
  * (which = 0), P_D^{-1} v (which = WC4D_PRECOND_PD + 1) or P_I^{-1} v
  * (which = WC4D_PRECOND_PI + 1), computed from FP32 copies of the covariances
  * and inverse factors with FP32 arithmetic (dot products in FP64).  v, out:
  * device, n floats each, not overlapping.  Needs a problem set up with
- * precision = WC4D_PREC_MIXED (ARG otherwise).  Stream-ordered, async. */
+ * precision = WC4D_PREC_MIXED or WC4D_PREC_DF32_P32 (ARG otherwise).
+ * Stream-ordered, async. */
 int wc4d_apply_fp32(wc4d_problem* prob, int32_t which, const float* v, float* out);
 
 /* Synthetic right-hand side (b, d, 0) of the first outer loop for a

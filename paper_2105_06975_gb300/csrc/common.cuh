@@ -44,6 +44,44 @@ void note_launch();
     if (!(cond)) throw ::wc4d::Error{(code), (msg)};       \
   } while (0)
 
+// ------------------------------------------------- double-float arithmetic
+// FP64-class products on the FP32 pipe (GB300 runs FP32 FMA at 64x the FP64
+// rate).  Operators are stored split, A = Ah + Al (two FP32 values, ~48
+// significant bits); vector entries are split on load.  Each multiply-add
+// takes the exact product error of Ah*xh from an FMA, adds the cross terms
+// Ah*xl + Al*xh (Al*xl, of relative size 2^-48, is dropped), and accumulates
+// into an (s, c) pair with Knuth's TwoSum, so the FP32 rounding of the running
+// sum is carried exactly into c.  About 13 FP32 instructions per
+// multiply-add; relative error of a length-K product ~ sqrt(K) 2^-48.
+__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float xh, float xl) {
+  const float p = ah * xh;
+  float e = fmaf(ah, xh, -p);
+  e = fmaf(ah, xl, e);
+  e = fmaf(al, xh, e);
+  const float t = s + p;
+  const float z = t - s;
+  const float err = (s - (t - z)) + (p - z);
+  s = t;
+  c += err + e;
+}
+
+// The same multiply-add on two independent accumulators at once with the
+// paired FP32 instructions of sm_100+ (FFMA2 / FADD2 / FMUL2 round each lane
+// to nearest like their scalar forms, so the error-free steps are unchanged);
+// half the issue slots of two scalar df_mac calls.
+__device__ __forceinline__ void df_mac2(float2& s, float2& c, float2 ah, float2 al, float2 xh, float2 xl) {
+  const float2 p = __fmul2_rn(ah, xh);
+  float2 e = __ffma2_rn(ah, xh, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(ah, xl, e);
+  e = __ffma2_rn(al, xh, e);
+  const float2 t = __fadd2_rn(s, p);
+  const float2 z = __fadd2_rn(t, make_float2(-s.x, -s.y));
+  const float2 tz = __fadd2_rn(t, make_float2(-z.x, -z.y));
+  const float2 err = __fadd2_rn(__fadd2_rn(s, make_float2(-tz.x, -tz.y)), __fadd2_rn(p, make_float2(-z.x, -z.y)));
+  s = t;
+  c = __fadd2_rn(c, __fadd2_rn(err, e));
+}
+
 // ------------------------------------------------------------ model on device
 // M_t for t = 1..N (maps time t-1 to t).  STENCIL3: same 3-point periodic
 // stencil for all t.  BANDED: bands[(t-1)*s*w + j*w + (o+lo)] = M_t[j][(j+o) mod s].

@@ -259,25 +259,7 @@ __global__ void __launch_bounds__(256) gemm_streamk_kernel(GemmOpsT<T> ops, cons
 }
 
 // ------------------------------------------------- double-float products
-// FP64-class products on the FP32 pipe (GB300 runs FP32 FMA at 64x the FP64
-// rate).  Operators are stored split, A = Ah + Al (two FP32 values, ~48
-// significant bits); vector entries are split on load.  Each multiply-add
-// takes the exact product error of Ah*xh from an FMA, adds the cross terms
-// Ah*xl + Al*xh (Al*xl, of relative size 2^-48, is dropped), and accumulates
-// into an (s, c) pair with Knuth's TwoSum, so the FP32 rounding of the running
-// sum is carried exactly into c.  About 13 FP32 instructions per
-// multiply-add; relative error of a length-K product ~ sqrt(K) 2^-48.
-__device__ __forceinline__ void df_mac(float& s, float& c, float ah, float al, float xh, float xl) {
-  const float p = ah * xh;
-  float e = fmaf(ah, xh, -p);
-  e = fmaf(ah, xl, e);
-  e = fmaf(al, xh, e);
-  const float t = s + p;
-  const float z = t - s;
-  const float err = (s - (t - z)) + (p - z);
-  s = t;
-  c += err + e;
-}
+// df_mac / df_mac2 (common.cuh): FP64-class multiply-add on the FP32 pipe.
 
 __global__ void __launch_bounds__(256) gemm_streamk_df32_kernel(GemmOpsT<double> ops,
                                                                 const GemmSeg* __restrict__ segs,
@@ -349,24 +331,44 @@ __global__ void __launch_bounds__(256) gemm_streamk_df32_kernel(GemmOpsT<double>
 #pragma unroll
         for (int kk = q0; kk < GEMM_BK; kk += 4) df_mac(s[0][0], c[0][0], Ah[kk][r], Al[kk][r], Xh[kk][0], Xl[kk][0]);
       } else if (ncv >= GEMM_BN - 15) {
+        // output pairs (j, j+1) share one paired instruction stream
+        float2 s2[4][2], c2[4][2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            s2[i][q] = make_float2(s[i][2 * q], s[i][2 * q + 1]);
+            c2[i][q] = make_float2(c[i][2 * q], c[i][2 * q + 1]);
+          }
 #pragma unroll 4
         for (int kk = 0; kk < GEMM_BK; ++kk) {
-          float ah[4], al[4], xh[4], xl[4];
+          float ah[4], al[4];
+          float2 xh[2], xl[2];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             ah[i] = Ah[kk][tx + 16 * i];
             al[i] = Al[kk][tx + 16 * i];
           }
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            xh[j] = Xh[kk][ty + 16 * j];
-            xl[j] = Xl[kk][ty + 16 * j];
+          for (int q = 0; q < 2; ++q) {
+            xh[q] = make_float2(Xh[kk][ty + 32 * q], Xh[kk][ty + 32 * q + 16]);
+            xl[q] = make_float2(Xl[kk][ty + 32 * q], Xl[kk][ty + 32 * q + 16]);
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) df_mac(s[i][j], c[i][j], ah[i], al[i], xh[j], xl[j]);
+            for (int q = 0; q < 2; ++q)
+              df_mac2(s2[i][q], c2[i][q], make_float2(ah[i], ah[i]), make_float2(al[i], al[i]), xh[q], xl[q]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            s[i][2 * q] = s2[i][q].x;
+            s[i][2 * q + 1] = s2[i][q].y;
+            c[i][2 * q] = c2[i][q].x;
+            c[i][2 * q + 1] = c2[i][q].y;
+          }
       } else if (ty < ncv) {
         for (int kk = 0; kk < GEMM_BK; ++kk) {
           float ah[4], al[4];

@@ -716,7 +716,7 @@ void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done,
 // where Z holds the computed P^-1 q_j).
 
 // part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w
-__global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __restrict__ Vh,
+__global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* __restrict__ Vh,
                                                                 const float* __restrict__ Vl, int64_t ldv, int j,
                                                                 const float* __restrict__ wh,
                                                                 const float* __restrict__ wl, int64_t n4,
@@ -729,9 +729,10 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
   const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
   const int gn = min(ORTH_G, cnt - i0);
   const bool first = blockIdx.y == 0;
-  float s[2 * ORTH_G + 1], c[2 * ORTH_G + 1];
+  // paired double-float accumulators: lane x sums elements 0, 2 of each float4, lane y elements 1, 3
+  float2 s[2 * ORTH_G + 1], c[2 * ORTH_G + 1];
 #pragma unroll
-  for (int g = 0; g < 2 * ORTH_G + 1; ++g) s[g] = c[g] = 0.f;
+  for (int g = 0; g < 2 * ORTH_G + 1; ++g) s[g] = c[g] = make_float2(0.f, 0.f);
   const float* uhp = Vh + (int64_t)j * ldv;
   const float* ulp = Vl + (int64_t)j * ldv;
   for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
@@ -739,32 +740,32 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
     const float4 xl = reinterpret_cast<const float4*>(wl)[q];
     const float4 uh = reinterpret_cast<const float4*>(uhp)[q];
     const float4 ul = reinterpret_cast<const float4*>(ulp)[q];
+    const float2 xh0 = make_float2(xh.x, xh.y), xh1 = make_float2(xh.z, xh.w);
+    const float2 xl0 = make_float2(xl.x, xl.y), xl1 = make_float2(xl.z, xl.w);
+    const float2 uh0 = make_float2(uh.x, uh.y), uh1 = make_float2(uh.z, uh.w);
+    const float2 ul0 = make_float2(ul.x, ul.y), ul1 = make_float2(ul.z, ul.w);
 #pragma unroll
     for (int g = 0; g < ORTH_G; ++g) {
       if (g < gn) {
         const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
         const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
-        dfk_mac(s[g], c[g], a.x, b.x, xh.x, xl.x);
-        dfk_mac(s[g], c[g], a.y, b.y, xh.y, xl.y);
-        dfk_mac(s[g], c[g], a.z, b.z, xh.z, xl.z);
-        dfk_mac(s[g], c[g], a.w, b.w, xh.w, xl.w);
-        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.x, b.x, uh.x, ul.x);
-        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.y, b.y, uh.y, ul.y);
-        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.z, b.z, uh.z, ul.z);
-        dfk_mac(s[ORTH_G + g], c[ORTH_G + g], a.w, b.w, uh.w, ul.w);
+        const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+        const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
+        df_mac2(s[g], c[g], a0, b0, xh0, xl0);
+        df_mac2(s[g], c[g], a1, b1, xh1, xl1);
+        df_mac2(s[ORTH_G + g], c[ORTH_G + g], a0, b0, uh0, ul0);
+        df_mac2(s[ORTH_G + g], c[ORTH_G + g], a1, b1, uh1, ul1);
       }
     }
     if (first) {
-      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.x, xl.x, xh.x, xl.x);
-      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.y, xl.y, xh.y, xl.y);
-      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.z, xl.z, xh.z, xl.z);
-      dfk_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.w, xl.w, xh.w, xl.w);
+      df_mac2(s[2 * ORTH_G], c[2 * ORTH_G], xh0, xl0, xh0, xl0);
+      df_mac2(s[2 * ORTH_G], c[2 * ORTH_G], xh1, xl1, xh1, xl1);
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g < 2 * ORTH_G + 1; ++g) {
-    const double v = warp_sum((double)s[g] + (double)c[g]);
+    const double v = warp_sum(((double)s[g].x + (double)c[g].x) + ((double)s[g].y + (double)c[g].y));
     if (lane == 0) sh[wid][g] = v;
   }
   __syncthreads();
@@ -793,6 +794,85 @@ void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float
   if (ran) prof_end(st);
 }
 
+// Applies the Givens rotations 0..m-1 (cosines rc, sines rs) to a new
+// Hessenberg column col[0..m] in place.  Rotation i maps the pair
+// (a_i, col[i+1]) to (rc_i a_i + rs_i col[i+1], -rs_i a_i + rc_i col[i+1]),
+// where a_0 = col[0] and a_{i+1} is the second component: an affine recurrence
+// a_{i+1} = alpha_i a_i + beta_i with alpha_i = -rs_i, beta_i = rc_i col[i+1].
+// Affine maps compose associatively, so the chain is a block-wide inclusive
+// scan of (A, B) pairs (a -> A a + B) instead of m dependent steps: on GB300 a
+// serial FP64 chain in one thread costs tens of cycles per operation.  Ends
+// with col[0..m-1] rotated and col[m] = a_m; col[m+1] is untouched.  Needs
+// m <= 2 * blockDim.x; sh: 64 doubles of shared scratch (two per warp).
+__device__ void rotate_column_scan(double* col, const double* rc, const double* rs, int m, double* sh) {
+  const int per = (m + blockDim.x - 1) / blockDim.x;  // 1 or 2 rotations per thread
+  const int i0 = threadIdx.x * per;
+  const int i1 = min(i0 + per, m);
+  double LA = 1.0, LB = 0.0;  // this thread's rotations composed, in order
+  for (int i = i0; i < i1; ++i) {
+    const double al = -rs[i], be = rc[i] * col[i + 1];
+    LB = al * LB + be;
+    LA = al * LA;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  double A = LA, B = LB;  // inclusive scan within the warp: later o earlier
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double Ap = __shfl_up_sync(0xffffffffu, A, off), Bp = __shfl_up_sync(0xffffffffu, B, off);
+    if (lane >= off) {
+      B = A * Bp + B;
+      A = A * Ap;
+    }
+  }
+  double* wa = sh;
+  double* wb = sh + 32;
+  __syncthreads();  // sh may hold a previous reduction's partials
+  if (lane == 31) {
+    wa[wid] = A;
+    wb[wid] = B;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double X = lane < nw ? wa[lane] : 1.0, Y = lane < nw ? wb[lane] : 0.0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double Xp = __shfl_up_sync(0xffffffffu, X, off), Yp = __shfl_up_sync(0xffffffffu, Y, off);
+      if (lane >= off) {
+        Y = X * Yp + Y;
+        X = X * Xp;
+      }
+    }
+    if (lane < nw) {
+      wa[lane] = X;
+      wb[lane] = Y;
+    }
+  }
+  __syncthreads();
+  // exclusive prefix of this thread = (lane-exclusive within the warp) o (warps before)
+  double eA = __shfl_up_sync(0xffffffffu, A, 1), eB = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) {
+    eA = 1.0;
+    eB = 0.0;
+  }
+  if (wid > 0) {
+    const double PA = wa[wid - 1], PB = wb[wid - 1];
+    eB = eA * PB + eB;
+    eA = eA * PA;
+  }
+  const double a0 = col[0];
+  double av = eA * a0 + eB;  // a_{i0}
+  double outv[2] = {0.0, 0.0};
+  for (int i = i0; i < i1; ++i) {
+    const double y = col[i + 1];
+    outv[i - i0] = rc[i] * av + rs[i] * y;
+    av = -rs[i] * av + rc[i] * y;
+  }
+  __syncthreads();  // every thread has read the unrotated column
+  for (int i = i0; i < i1; ++i) col[i] = outv[i - i0];
+  if (i0 < m && i1 == m) col[m] = av;
+  __syncthreads();
+}
+
 // One CTA.  red: the reduced dot rows (a, c, w^T w).  dc: scalar state
 // (DC_* slots), bprev / cprev: b and c of the previous step, e: the update
 // coefficients.  Completes Hessenberg column j-1 (raw into Hraw, rotated into
@@ -806,7 +886,7 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
                                                           double* g, double* hnext, DevStatus* stat,
                                                           const double* bnorm) {
   extern __shared__ double sm[];
-  __shared__ double sh[32];
+  __shared__ double sh[64];
   if (*(volatile const int*)&stat->done) return;
   const int cnt = j + 1;
   const double* a = red;        // a_0..a_j
@@ -814,6 +894,7 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
   double* col = sm;             // [j + 2]
   double* rc = col + j + 2;     // [j]
   double* rs = rc + j;          // [j]
+  double* tp = rs + j;          // [nseg * j] partial sums of Hbar c (nseg > 1 only)
   for (int i = threadIdx.x; i + 1 < j; i += blockDim.x) {
     rc[i] = cs[i];
     rs[i] = sn[i];
@@ -832,18 +913,43 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
   const double bj = (a[j] - ca) * igam;  // q_j^T w
   const double alpha = dc[DC_ALPHA];     // scale of u_j
   const double gprev = dc[DC_GAMMA];
+  // Hbar c_{j-1} (rows 0..j-1, columns 0..j-2 of the raw Hessenberg): the
+  // column range is cut into nseg segments so every thread has a short run of
+  // independent loads; the segments are summed in a fixed order.
+  const int nseg = (j >= 1) ? max(1, min((int)blockDim.x / j, 32)) : 1;
+  if (j >= 1) {
+    const int ncol = j - 1;
+    const int seg = (ncol + nseg - 1) / nseg;
+    for (int idx = threadIdx.x; idx < nseg * j; idx += blockDim.x) {
+      const int r = idx % j, sgi = idx / j;
+      const int k0 = max(sgi * seg, r > 0 ? r - 1 : 0), k1 = min((sgi + 1) * seg, ncol);
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      int k = k0;
+      for (; k + 4 <= k1; k += 4) {
+        t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
+        t1 += Hraw[r + (int64_t)(k + 1) * ldh] * cprev[k + 1];
+        t2 += Hraw[r + (int64_t)(k + 2) * ldh] * cprev[k + 2];
+        t3 += Hraw[r + (int64_t)(k + 3) * ldh] * cprev[k + 3];
+      }
+      for (; k < k1; ++k) t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
+      const double tsum = (t0 + t1) + (t2 + t3);
+      if (nseg > 1)
+        tp[sgi * j + r] = tsum;
+      else
+        col[r] = tsum;
+    }
+  }
+  __syncthreads();
   // column j-1: (b_{j-1} - Hbar c_{j-1} + alpha c_j) / gamma_{j-1}, sub-diagonal alpha gamma / gamma_{j-1}
   if (j >= 1) {
     const double ig = 1.0 / gprev;
     for (int r = threadIdx.x; r < j; r += blockDim.x) {
-      double t0 = 0.0, t1 = 0.0;
-      int k = (r > 0 ? r - 1 : 0);
-      for (; k + 2 < j; k += 2) {
-        t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
-        t1 += Hraw[r + (int64_t)(k + 1) * ldh] * cprev[k + 1];
-      }
-      if (k + 1 < j) t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
-      col[r] = (bprev[r] - (t0 + t1) + alpha * c[r]) * ig;
+      double tsum = 0.0;
+      if (nseg > 1)
+        for (int q = 0; q < nseg; ++q) tsum += tp[q * j + r];
+      else
+        tsum = col[r];
+      col[r] = (bprev[r] - tsum + alpha * c[r]) * ig;
     }
     if (threadIdx.x == 0) col[j] = alpha * gam * ig;
   }
@@ -858,6 +964,7 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
     if (threadIdx.x == 0) tc[j] = gam;
   }
   __syncthreads();
+  if (j >= 2) rotate_column_scan(col, rc, rs, j - 1, sh);
   if (threadIdx.x == 0) {
     if (j == 0) {
       g[0] = dc[DC_BETA] * gam;  // r0 = ||r0|| u_0 = (||r0|| gamma_0) q_0
@@ -867,13 +974,8 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
         stat->done = 1;
       }
     } else {
-      const int jc = j - 1;  // column being completed
+      const int jc = j - 1;  // column being completed (rows 0..jc already rotated)
       *hnext = col[j];
-      for (int i = 0; i < jc; ++i) {
-        const double x = col[i], y = col[i + 1];
-        col[i] = rc[i] * x + rs[i] * y;
-        col[i + 1] = -rs[i] * x + rc[i] * y;
-      }
       double cr = 1.0, sr = 0.0;
       if (col[jc + 1] != 0.0) {
         const double rr = hypot(col[jc], col[jc + 1]);
@@ -927,7 +1029,9 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
 void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
                 double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
                 const double* bnorm, cudaStream_t st) {
-  const size_t smem = sizeof(double) * (3 * (size_t)j + 2);
+  // column + rotations (3j + 2) and, when j <= 512, nseg * j <= 1024 segment partials
+  const int nseg = (j >= 1) ? std::max(1, std::min(1024 / j, 32)) : 1;
+  const size_t smem = sizeof(double) * (3 * (size_t)j + 2 + (nseg > 1 ? (size_t)nseg * j : 0));
   gm_dc_coef_kernel<<<1, 1024, smem, st>>>(j, red, dc, bprev, cprev, e, Hraw, H, T, ldh, cs, sn, g, hnext, stat,
                                            bnorm);
   WC4D_LAUNCH_CHECK();
@@ -966,8 +1070,10 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
   float* nh = Vh + (int64_t)(j + 1) * ldv;
   float* nl = Vl + (int64_t)(j + 1) * ldv;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
-    float se[4] = {0.f, 0.f, 0.f, 0.f}, ce[4] = {0.f, 0.f, 0.f, 0.f};
-    float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    // paired accumulators: [0] elements 0, 1 of the float4, [1] elements 2, 3
+    float2 se[2], ce[2], sc[2], cc[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) se[u] = ce[u] = sc[u] = cc[u] = make_float2(0.f, 0.f);
     int i = 0;
     for (; i + 4 <= j; i += 4) {
       float4 a[4], b[4];
@@ -978,30 +1084,30 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float h1 = eh[i + u], l1 = el[i + u], h2 = ch[i + u], l2 = cl[i + u];
-        dfk_mac(se[0], ce[0], h1, l1, a[u].x, b[u].x);
-        dfk_mac(se[1], ce[1], h1, l1, a[u].y, b[u].y);
-        dfk_mac(se[2], ce[2], h1, l1, a[u].z, b[u].z);
-        dfk_mac(se[3], ce[3], h1, l1, a[u].w, b[u].w);
-        dfk_mac(sc[0], cc[0], h2, l2, a[u].x, b[u].x);
-        dfk_mac(sc[1], cc[1], h2, l2, a[u].y, b[u].y);
-        dfk_mac(sc[2], cc[2], h2, l2, a[u].z, b[u].z);
-        dfk_mac(sc[3], cc[3], h2, l2, a[u].w, b[u].w);
+        const float2 h1 = make_float2(eh[i + u], eh[i + u]), l1 = make_float2(el[i + u], el[i + u]);
+        const float2 h2 = make_float2(ch[i + u], ch[i + u]), l2 = make_float2(cl[i + u], cl[i + u]);
+        const float2 a0 = make_float2(a[u].x, a[u].y), a1 = make_float2(a[u].z, a[u].w);
+        const float2 b0 = make_float2(b[u].x, b[u].y), b1 = make_float2(b[u].z, b[u].w);
+        df_mac2(se[0], ce[0], h1, l1, a0, b0);
+        df_mac2(se[1], ce[1], h1, l1, a1, b1);
+        df_mac2(sc[0], cc[0], h2, l2, a0, b0);
+        df_mac2(sc[1], cc[1], h2, l2, a1, b1);
       }
     }
     for (; i < j; ++i) {
       const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)i * ldv)[q];
       const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)i * ldv)[q];
-      const float h1 = eh[i], l1 = el[i], h2 = ch[i], l2 = cl[i];
-      dfk_mac(se[0], ce[0], h1, l1, a.x, b.x);
-      dfk_mac(se[1], ce[1], h1, l1, a.y, b.y);
-      dfk_mac(se[2], ce[2], h1, l1, a.z, b.z);
-      dfk_mac(se[3], ce[3], h1, l1, a.w, b.w);
-      dfk_mac(sc[0], cc[0], h2, l2, a.x, b.x);
-      dfk_mac(sc[1], cc[1], h2, l2, a.y, b.y);
-      dfk_mac(sc[2], cc[2], h2, l2, a.z, b.z);
-      dfk_mac(sc[3], cc[3], h2, l2, a.w, b.w);
+      const float2 h1 = make_float2(eh[i], eh[i]), l1 = make_float2(el[i], el[i]);
+      const float2 h2 = make_float2(ch[i], ch[i]), l2 = make_float2(cl[i], cl[i]);
+      const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+      const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
+      df_mac2(se[0], ce[0], h1, l1, a0, b0);
+      df_mac2(se[1], ce[1], h1, l1, a1, b1);
+      df_mac2(sc[0], cc[0], h2, l2, a0, b0);
+      df_mac2(sc[1], cc[1], h2, l2, a1, b1);
     }
+    const float se_s[4] = {se[0].x, se[0].y, se[1].x, se[1].y}, ce_s[4] = {ce[0].x, ce[0].y, ce[1].x, ce[1].y};
+    const float sc_s[4] = {sc[0].x, sc[0].y, sc[1].x, sc[1].y}, cc_s[4] = {cc[0].x, cc[0].y, cc[1].x, cc[1].y};
     const float4 uh = reinterpret_cast<const float4*>(qh)[q];
     const float4 ul = reinterpret_cast<const float4*>(ql)[q];
     const float uhs[4] = {uh.x, uh.y, uh.z, uh.w}, uls[4] = {ul.x, ul.y, ul.z, ul.w};
@@ -1010,10 +1116,10 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
     for (int u = 0; u < 4; ++u) {
       const int64_t el_ = 4 * q + u;
       const double uj = (double)uhs[u] + (double)uls[u];
-      const double qv = (uj - ((double)sc[u] + (double)cc[u])) * igam;
+      const double qv = (uj - ((double)sc_s[u] + (double)cc_s[u])) * igam;
       double nv = 0.0;
       if (el_ < n) {
-        nv = (w[el_] - ((double)se[u] + (double)ce[u]) - ej * uj) * ialpha;
+        nv = (w[el_] - ((double)se_s[u] + (double)ce_s[u]) - ej * uj) * ialpha;
         v[el_] = nv;
       }
       oqh[u] = __double2float_rn(qv);

@@ -6,7 +6,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -90,7 +93,7 @@ struct wc4d_problem {
   GemmPlan plan_A, plan_pd1, plan_pd2, plan_pi1, plan_pi2;
   // MIXED inner GMRES(m) workspace (FP32 basis, FP64 Hessenberg/rotations)
   int mi = 0;
-  float *Vi = nullptr, *Zi = nullptr, *stage = nullptr;
+  float *Vi = nullptr, *Zi = nullptr, *stage = nullptr, *zf = nullptr;
   double *Hi = nullptr, *csi = nullptr, *sni = nullptr, *gi = nullptr, *yi = nullptr;
   double *h1i = nullptr, *h2i = nullptr, *hnexti = nullptr, *bnormi = nullptr, *parti = nullptr, *part2i = nullptr;
   DevStatus* stat_in = nullptr;
@@ -499,8 +502,11 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(o->tol > 0 && o->maxit >= 1 && o->maxit <= 100000, WC4D_ERR_ARG, "need tol > 0, 1 <= maxit <= 1e5");
   WC4D_CHECK(o->krylov == WC4D_KRYLOV_MINRES || o->maxit <= 2000, WC4D_ERR_ARG,
              "GMRES/FGMRES without restarts keep maxit <= 2000 (Hessenberg column in shared memory)");
-  WC4D_CHECK(o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_MIXED || o->precision == WC4D_PREC_DF32,
+  WC4D_CHECK(o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_MIXED || o->precision == WC4D_PREC_DF32 ||
+                 o->precision == WC4D_PREC_DF32_P32,
              WC4D_ERR_ARG, "bad precision");
+  WC4D_CHECK(o->precision != WC4D_PREC_DF32_P32 || o->krylov == WC4D_KRYLOV_GMRES, WC4D_ERR_ARG,
+             "the FP32-preconditioner mode runs the (flexible) DF32 GMRES");
   WC4D_CHECK((o->precision == WC4D_PREC_MIXED) == (o->krylov == WC4D_KRYLOV_FGMRES), WC4D_ERR_ARG,
              "the mixed-precision mode is FGMRES (flexible outer FP64 iteration around an FP32 inner solve), "
              "and FGMRES is only used by it");
@@ -646,7 +652,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   f.t1 = P->alloc<double>(P->n);
   f.t2 = P->alloc<double>(P->n);
   f.t3 = P->alloc<double>(P->n);
-  if (o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_MIXED) {
+  if (o->precision != WC4D_PREC_FP64) {
     f.df32 = 1;
     f.xcap = 2 * P->n;
     f.xh = P->alloc<float>(f.xcap);
@@ -672,7 +678,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       add(f.WSt, (int64_t)P->nS * P->nS);
     }
   }
-  if (o->precision == WC4D_PREC_MIXED) {
+  if (o->precision == WC4D_PREC_MIXED || o->precision == WC4D_PREC_DF32_P32) {
     OpSet<float>& g = P->f32;
     auto to32 = [&](const double* src, int64_t cnt) {
       if (!src) return (float*)nullptr;
@@ -697,11 +703,14 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     g.t1 = P->alloc<float>(P->n);
     g.t2 = P->alloc<float>(P->n);
     g.t3 = P->alloc<float>(P->n);
+    P->stage = P->alloc<float>(P->n);
+  }
+  if (o->precision == WC4D_PREC_DF32_P32) P->zf = P->alloc<float>(P->n);
+  if (o->precision == WC4D_PREC_MIXED) {
     const int mi = o->inner_iters;
     P->mi = mi;
     P->Vi = P->alloc<float>((int64_t)(mi + 1) * P->n);
     P->Zi = P->alloc<float>((int64_t)mi * P->n);
-    P->stage = P->alloc<float>(P->n);
     P->Hi = P->alloc<double>((int64_t)(mi + 1) * mi);
     P->csi = P->alloc<double>(mi + 1);
     P->sni = P->alloc<double>(mi + 1);
@@ -720,7 +729,8 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->maxit = o->maxit;
   const int64_t nvec = (o->krylov == WC4D_KRYLOV_MINRES) ? 12 : (int64_t)o->maxit + 1;
   P->split_basis = (o->krylov != WC4D_KRYLOV_MINRES) && (o->precision != WC4D_PREC_FP64);
-  P->dcgs = (o->krylov == WC4D_KRYLOV_GMRES) && (o->precision == WC4D_PREC_DF32);
+  P->dcgs = (o->krylov == WC4D_KRYLOV_GMRES) &&
+            (o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_DF32_P32);
   if (P->split_basis) {
     // leading dimension padded to 4 floats (16-byte loads); padding stays zero
     P->ldb = (n + 3) / 4 * 4;
@@ -943,6 +953,7 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   const int* done = &P->stat->done;
   const int which = P->o.precond;
   const int64_t lb = P->ldb;
+  const bool p32 = (P->o.precision == WC4D_PREC_DF32_P32);
   int64_t nA = 0, nP = 0;
   dot_partial<double>(P->rhs, P->rhs, n, P->part3, nullptr, st);
   dot_finish(P->part3, P->scal, 1, st);
@@ -990,7 +1001,13 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
     for (int b = 0; b < batch; ++b) {
       const int j = next + b;
       double* zj = P->Z + (int64_t)j * n;
-      apply_P<double>(P, which, P->f64, P->vcur, zj, done);
+      if (p32) {  // FP32 preconditioner: the stored Z~_j is whatever it computed
+        vec_convert<float, double>(P->vcur, P->stage, n, 1.0, st);
+        apply_P<float>(P, which, P->f32, P->stage, P->zf, done);
+        vec_convert<double, float>(P->zf, zj, n, 1.0, st);
+      } else {
+        apply_P<double>(P, which, P->f64, P->vcur, zj, done);
+      }
       apply_A<double>(P, P->f64, P->plan_A, zj, P->wbuf, done);
       gm_split(P->wbuf, P->wh, P->wl, n, done, st);
       gm_dc_dot(P->Vh, P->Vl, lb, j, P->wh, P->wl, n, P->part, done, st);
@@ -1459,10 +1476,77 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
   WC4D_API_END
 }
 
+// Batched solve of independent windows: a pool of host workers, each with its
+// own non-blocking CUDA stream, takes windows largest-first (longest
+// processing time first) and runs the window's own solver on its stream, so
+// the kernels of small windows overlap on the GPU while other workers wait on
+// their convergence polls.
+int wc4d_solve_batch(wc4d_problem* const* probs, int32_t count, const double* const* rhs, double* const* x,
+                     int32_t use_x0, int32_t mem_kind, int32_t workers, wc4d_info* infos) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(count >= 0, WC4D_ERR_ARG, "count must be >= 0");
+  if (count == 0) return WC4D_OK;
+  WC4D_CHECK(probs && rhs && x, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(mem_kind == WC4D_MEM_HOST || mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
+  WC4D_CHECK(workers >= 0 && workers <= 64, WC4D_ERR_ARG, "workers must lie in [0, 64]");
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) {
+    WC4D_CHECK(probs[i] && rhs[i] && x[i], WC4D_ERR_ARG, "null problem, rhs or x in the batch");
+    for (int k = 0; k < i; ++k) WC4D_CHECK(probs[k] != probs[i], WC4D_ERR_ARG, "a problem appears twice in the batch");
+    order[i] = i;
+  }
+  auto cost = [&](int i) {
+    const wc4d_problem* P = probs[i];
+    return ((double)P->s * P->s + (double)P->p * P->p) * (P->N + 1);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  const int nw = workers > 0 ? std::min<int>(workers, count) : std::min(count, 8);
+  int dev = 0;
+  WC4D_CUDA(cudaGetDevice(&dev));
+  for (int i = 0; i < count; ++i) WC4D_CUDA(cudaStreamSynchronize(probs[i]->st));
+  std::atomic<int> next{0};
+  std::vector<int> status(count, WC4D_OK);
+  std::vector<std::string> msg(count);
+  std::vector<wc4d_info> loc(count);
+  auto work = [&]() {
+    cudaStream_t ws = nullptr;
+    if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+      for (int k = next++; k < count; k = next++) {
+        status[order[k]] = WC4D_ERR_CUDA;
+        msg[order[k]] = "worker stream creation failed";
+      }
+      return;
+    }
+    for (int k = next++; k < count; k = next++) {
+      const int i = order[k];
+      wc4d_problem* P = probs[i];
+      cudaStream_t own = P->st;
+      P->st = ws;
+      status[i] = wc4d_solve(P, rhs[i], x[i], use_x0, mem_kind, &loc[i]);
+      if (status[i] != WC4D_OK) msg[i] = wc4d_last_error();
+      P->st = own;
+    }
+    cudaStreamDestroy(ws);
+  };
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nw; ++w) pool.emplace_back(work);
+  for (auto& th : pool) th.join();
+  if (infos)
+    for (int i = 0; i < count; ++i) infos[i] = loc[i];
+  for (int i = 0; i < count; ++i)
+    if (status[i] != WC4D_OK) {
+      wc4d::set_error("window " + std::to_string(i) + ": " + msg[i]);
+      return status[i];
+    }
+  return WC4D_OK;
+  WC4D_API_END
+}
+
 int wc4d_apply_fp32(wc4d_problem* P, int32_t which, const float* v, float* out) {
   WC4D_API_BEGIN
   WC4D_CHECK(P && v && out, WC4D_ERR_ARG, "null argument");
-  WC4D_CHECK(P->o.precision == WC4D_PREC_MIXED, WC4D_ERR_ARG, "FP32 operators need precision = MIXED at setup");
+  WC4D_CHECK(P->o.precision == WC4D_PREC_MIXED || P->o.precision == WC4D_PREC_DF32_P32, WC4D_ERR_ARG,
+             "FP32 operators need precision = MIXED or DF32_P32 at setup");
   WC4D_CHECK(which >= 0 && which <= 2, WC4D_ERR_ARG, "which must be 0 (A), 1 (P_D) or 2 (P_I)");
   WC4D_CHECK(which != 1 || P->have_pd, WC4D_ERR_ARG, "P_D needs a problem set up with precond = PD");
   if (which == 0)

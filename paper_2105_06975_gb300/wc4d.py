@@ -52,6 +52,7 @@ WC4D_KRYLOV_FGMRES = 2
 WC4D_PREC_FP64 = 0
 WC4D_PREC_MIXED = 1
 WC4D_PREC_DF32 = 2
+WC4D_PREC_DF32_P32 = 3
 
 RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG}
 PRECOND = {"PD": WC4D_PRECOND_PD, "PI": WC4D_PRECOND_PI}
@@ -114,6 +115,9 @@ SIGNATURES = {
     "wc4d_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.POINTER(Info)]),
     "wc4d_apply_fp32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "wc4d_solve_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Info)]),
     "wc4d_synthesize_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                            ctypes.c_void_p]),
     "wc4d_l96_gauss_newton": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(L96Params), ctypes.c_void_p,
@@ -205,6 +209,42 @@ def wc4d_solve(h, rhs_ptr: int, x_ptr: int, use_x0: bool, mem_kind: int, raise_o
     return info
 
 
+def wc4d_solve_batch(handles, rhs_ptrs, x_ptrs, use_x0: bool, mem_kind: int, workers: int = 0,
+                     raise_on_error=True):
+    """Solve len(handles) independent problems concurrently; returns (code, [Info])."""
+    cnt = len(handles)
+    H = (ctypes.c_void_p * max(cnt, 1))(*handles)
+    R = (ctypes.c_void_p * max(cnt, 1))(*rhs_ptrs)
+    X = (ctypes.c_void_p * max(cnt, 1))(*x_ptrs)
+    infos = (Info * max(cnt, 1))()
+    code = load().wc4d_solve_batch(H, cnt, R, X, int(use_x0), mem_kind, int(workers), infos)
+    if raise_on_error and code not in (WC4D_OK, WC4D_ERR_MAXIT):
+        _check(code)
+    return code, [infos[i] for i in range(cnt)]
+
+
+def solve_batch(problems, rhs_list, x_list=None, use_x0=False, workers=0):
+    """Batched solve of Problem objects: rhs_list entries are numpy arrays (host
+    path) or CUDA tensors (device path), all of one kind."""
+    import numpy as _np
+    host = isinstance(rhs_list[0], _np.ndarray)
+    if host:
+        rhs_list = [_np.ascontiguousarray(r, dtype=_np.float64) for r in rhs_list]
+        if x_list is None:
+            x_list = [_np.zeros_like(r) for r in rhs_list]
+        rp = [r.ctypes.data for r in rhs_list]
+        xp = [x.ctypes.data for x in x_list]
+    else:
+        import torch as _torch
+        if x_list is None:
+            x_list = [_torch.zeros_like(r) for r in rhs_list]
+        rp = [r.data_ptr() for r in rhs_list]
+        xp = [x.data_ptr() for x in x_list]
+    code, infos = wc4d_solve_batch([p.h for p in problems], rp, xp, use_x0,
+                                   WC4D_MEM_HOST if host else WC4D_MEM_DEVICE, workers)
+    return x_list, infos, code
+
+
 def wc4d_apply_fp32(h, which: int, v_ptr: int, out_ptr: int) -> None:
     _check(load().wc4d_apply_fp32(h, which, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)))
 
@@ -287,7 +327,8 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
     o.krylov = KRYLOV[krylov]
     o.tol = float(tol)
     o.maxit = int(maxit)
-    o.precision = {"fp64": WC4D_PREC_FP64, "mixed": WC4D_PREC_MIXED, "df32": WC4D_PREC_DF32}[precision]
+    o.precision = {"fp64": WC4D_PREC_FP64, "mixed": WC4D_PREC_MIXED, "df32": WC4D_PREC_DF32,
+                   "df32p32": WC4D_PREC_DF32_P32}[precision]
     o.inner_iters = int(inner_iters)
     o.check_every = int(check_every)
     return o

@@ -16,6 +16,10 @@ available, so these stand in for its experiments with the shapes below):
   drawn without replacement and sorted.  n = 332,800.
 * ``l96``   -- Lorenz-96, s=1000, F=8, RK4 dt=0.025 with 5 steps per
   observation time, N=50, every 2nd variable observed, 3 Gauss-Newton loops.
+* ``batch`` -- ``batch_windows``: independent windows of uneven size,
+  s = 4 U{32..512}, N = U{8..96}, p = s/2 or s/4, advection-diffusion (the
+  scale workload's covariances) or Lorenz-96 (its covariances, lengths in grid
+  points, and the paper's time step 1e-4 of Sec. 7.1) by a fair coin each.
 
 Seeds: master seed m in {0, 1, 2}; window w of a batch uses m*1000 + w.
 """
@@ -81,6 +85,23 @@ L96 = Workload(name="l96", s=1000, N=50, p=500, obs="even", model="l96",
                soar_r=(0.5, 4.0 / 1000), outer_loops=3)
 
 WORKLOADS = {w.name: w for w in (TINY, SCALE, L96)}
+
+
+def batch_windows(count: int = 256, seed: int = 0) -> list:
+    """The windows of the batched workload with their draw seeds: a list of
+    (Workload, seed) with seed = 1000 * seed + window index."""
+    g = rng(1000 * int(seed) + 999)
+    out = []
+    for i in range(int(count)):
+        s = 4 * int(g.integers(32, 513))
+        N = int(g.integers(8, 97))
+        p = s // 2 if g.random() < 0.5 else s // 4
+        if g.random() < 0.5:
+            w = SCALE.with_(name=f"batch{i}-advdiff", s=s, N=N, p=p)
+        else:
+            w = small(L96, s=s, N=N, p=p).with_(name=f"batch{i}-l96", dt=1e-4, outer_loops=1)
+        out.append((w, 1000 * int(seed) + i))
+    return out
 
 
 def rng(seed: int) -> np.random.Generator:
