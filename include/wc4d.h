@@ -55,7 +55,8 @@ enum {
   WC4D_ERR_MAXIT = 5,      /* tolerance not reached within maxit iterations    */
   WC4D_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                    */
   WC4D_ERR_CUDA = 7,       /* CUDA runtime error                               */
-  WC4D_ERR_NOMEM = 8       /* device allocation failed                         */
+  WC4D_ERR_NOMEM = 8,      /* device allocation failed                         */
+  WC4D_ERR_IO = 9          /* checkpoint file could not be read or written     */
 };
 
 /* model operator M_i (Eq. def:L) */
@@ -76,7 +77,9 @@ enum { WC4D_MEM_HOST = 0, WC4D_MEM_DEVICE = 1 };
 enum { WC4D_PRECOND_PD = 0, WC4D_PRECOND_PI = 1 };          /* Eq. prec                     */
 enum { WC4D_RHAT_EXACT = 0, WC4D_RHAT_RR = 1,               /* Rhat = R; Alg. 1 ridge       */
        WC4D_RHAT_ME = 2, WC4D_RHAT_DIAG = 3 };              /* Alg. 2 min-eig; Sec. 5.1     */
-enum { WC4D_SHAT_PAPER = 0, WC4D_SHAT_EXACT = 1 };          /* Lhat^T D^-1 Lhat ; S (Sec 2.2) */
+enum { WC4D_SHAT_PAPER = 0, WC4D_SHAT_EXACT = 1,           /* Lhat^T D^-1 Lhat ; S (Sec 2.2) */
+       WC4D_SHAT_LEARNED = 2 };   /* PAPER plus a learned correction of its inverse (not in the
+                                     paper; wc4d_precond_train / _load), GMRES only          */
 enum { WC4D_DHAT_EXACT = 0, WC4D_DHAT_SHIFT = 1 };          /* D ; D + delta I (Sec. 6.1)   */
 enum { WC4D_KRYLOV_MINRES = 0, WC4D_KRYLOV_GMRES = 1, WC4D_KRYLOV_FGMRES = 2 };
 enum { WC4D_PREC_FP64 = 0,        /* every product in native FP64 (DFMA)                       */
@@ -136,6 +139,9 @@ typedef struct {
   int32_t status;            /* WC4D_OK or the failure code                              */
   int32_t iters;             /* outer Krylov iterations                                  */
   int32_t inner_iters;       /* MIXED: total inner iterations                            */
+  int32_t precond_fallback;  /* SHAT_LEARNED: 1 if the solve with the learned Schur block
+                                failed and was repeated with the plain one (the reported
+                                fields are the repeated solve's)                         */
   double relres_true;        /* ||rhs - A x||_2 / ||rhs||_2 recomputed in FP64 at exit   */
   double relres_est;         /* recurrence estimate at exit                              */
   double ms;                 /* wall time of the solve call                              */
@@ -198,6 +204,62 @@ int wc4d_solve(wc4d_problem* prob, const double* rhs, double* x, int32_t use_x0,
  * Not for concurrent use with wc4d_set_profiling (single-stream profile). */
 int wc4d_solve_batch(wc4d_problem* const* probs, int32_t count, const double* const* rhs, double* const* x,
                      int32_t use_x0, int32_t mem_kind, int32_t workers, wc4d_info* infos);
+
+/* ---------------------------------------------------------------- learned
+ * Learned Schur-block preconditioner (not in the paper).  P_D's third block
+ * S_hat^{-1} = Lhat^{-1} D Lhat^{-T} (Sec. 2.2, Definition 1) gives y; the
+ * learned block returns z = |y| (y/|y| + f(y/|y|)), f a 1D convolutional net
+ * over the grid with the N+1 time levels as channels: conv(N+1 -> H) ReLU
+ * conv(H -> H) ReLU conv(H -> H) ReLU conv(H -> N+1), kernel 5, periodic
+ * 'same' padding, FP32.  It is trained to map y = S_hat^{-1} r to S^{-1} r,
+ * S = L^T D^-1 L + H^T R^-1 H (the exact Schur complement): pairs are made
+ * exactly by drawing v (white, or S_hat^{-1} of white noise, alternately),
+ * forming r = S v with the problem's own operators, and t = v = S^{-1} r.
+ * Needs a problem set up with precond = PD, shat = LEARNED, rhat = EXACT,
+ * dhat = EXACT, krylov = GMRES (the net is nonlinear; the library's GMRES
+ * keeps the preconditioned vectors and is therefore flexible), N + 1 <= 64.
+ * The plain block (shat = PAPER) is the fallback and the judge: training
+ * compares both on held-out pairs and activates the net only if its relative
+ * error is smaller; a solve that fails with the net is repeated without it
+ * (wc4d_info.precond_fallback). */
+typedef struct {
+  int32_t pairs;             /* training + validation pairs generated (50000)       */
+  int32_t hidden;            /* hidden channels H, <= 64 (32)                       */
+  int32_t batch;             /* minibatch (64)                                      */
+  int32_t epochs;            /* passes over the training pairs (4)                  */
+  double lr;                 /* Adam step size (1e-3)                               */
+  double val_frac;           /* held-out fraction (0.05)                            */
+  uint64_t seed;             /* draws, initialisation and shuffling                 */
+} wc4d_train_opts;
+typedef struct {
+  double loss_first;         /* mean training loss |z - t|^2/|t|^2, first epoch     */
+  double loss_last;          /* ... last epoch                                      */
+  double val_err_learned;    /* held-out RMS of |z - t| / |t| with the net          */
+  double val_err_plain;      /* ... with the plain S_hat^{-1} (z = y)               */
+  int32_t kept;              /* 1 if the net is active (learned error < plain)      */
+  int32_t pairs_train;       /* pairs used for training                             */
+  double gen_ms, train_ms;   /* pair generation / training wall time                */
+} wc4d_train_report;
+void wc4d_default_train_opts(wc4d_train_opts* opts);
+/* Generate pairs, train on the device, validate, and (ckpt_path != NULL) save
+ * the weights.  report may be NULL.  Device memory: 8 (N+1) s bytes per pair
+ * plus the problem's own.  Synchronises the stream.  Errors: ARG (problem not
+ * set up as above, bad options), NOMEM, CUDA, IO (checkpoint file). */
+int wc4d_precond_train(wc4d_problem* prob, const wc4d_train_opts* opts, const char* ckpt_path,
+                       wc4d_train_report* report);
+/* Load weights saved by wc4d_precond_train (same N+1 and s); the net is
+ * activated if its saved validation error beat the plain block's. */
+int wc4d_precond_load(wc4d_problem* prob, const char* ckpt_path);
+/* Set the net's weights directly (host array, layout: for each layer l,
+ * W[co][ci][5] then b[co]) and whether it is active. */
+int wc4d_precond_set_net(wc4d_problem* prob, int32_t hidden, const float* params, int32_t active);
+/* Mean loss and parameter gradients of the net on B host samples yn, tn
+ * ([B][C][s] each, tn2 = |tn|^2 per sample), computed by the library's device
+ * kernels; for checking them against a reference.  params, grads: host,
+ * nparams floats. */
+int wc4d_net_grad(int32_t C, int32_t hidden, int32_t s, int32_t B, const float* params, const float* yn,
+                  const float* tn, double* loss, float* grads);
+int64_t wc4d_net_nparams(int32_t C, int32_t hidden);
 
 /* FP32 operators of the mixed-precision mode (not in the paper): out = A v
  * (which = 0), P_D^{-1} v (which = WC4D_PRECOND_PD + 1) or P_I^{-1} v

@@ -44,6 +44,30 @@ void note_launch();
     if (!(cond)) throw ::wc4d::Error{(code), (msg)};       \
   } while (0)
 
+// sqrt of a sum of squares that rounding may push slightly below zero: negative
+// values give 0, NaN stays NaN (fmax(NaN, 0) would return 0 and hide a
+// non-finite input from every check downstream)
+__device__ __forceinline__ double sqrt_clamped(double v) { return v > 0.0 ? sqrt(v) : (v == v ? 0.0 : v); }
+
+// ------------------------------------------------------ block reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum, result valid in every thread (sh: one double per warp)
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += sh[i];
+  return t;
+}
+
 // ------------------------------------------------- double-float arithmetic
 // FP64-class products on the FP32 pipe (GB300 runs FP32 FMA at 64x the FP64
 // rate).  Operators are stored split, A = Ah + Al (two FP32 values, ~48

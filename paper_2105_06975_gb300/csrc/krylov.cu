@@ -10,24 +10,6 @@
 
 namespace wc4d {
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// block-wide sum, result valid in every thread
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < nw; ++i) t += sh[i];
-  return t;
-}
-
 // sum of DOT_BLOCKS partials in fixed order (whole block cooperates, same result everywhere)
 __device__ __forceinline__ double sum_partials(const double* __restrict__ part, double* sh) {
   double v = 0.0;
@@ -58,7 +40,7 @@ template void dot_partial<float>(const float*, const float*, int64_t, double*, c
 __global__ void dot_finish_kernel(const double* part, double* out, int sqrt_it) {
   __shared__ double sh[32];
   const double v = sum_partials(part, sh);
-  if (threadIdx.x == 0) *out = sqrt_it ? sqrt(fmax(v, 0.0)) : v;
+  if (threadIdx.x == 0) *out = sqrt_it ? sqrt_clamped(v) : v;
 }
 void dot_finish(const double* part, double* out, int sqrt_it, cudaStream_t st) {
   dot_finish_kernel<<<1, DOT_THREADS, 0, st>>>(part, out, sqrt_it);
@@ -70,7 +52,7 @@ __global__ void minres_init_kernel(const double* part_gamma, double* sc, DevStat
   __shared__ double sh[32];
   const double g2 = sum_partials(part_gamma, sh);
   if (threadIdx.x == 0) {
-    const double g = sqrt(fmax(g2, 0.0));
+    const double g = sqrt_clamped(g2);
     sc[MS_GAMMA] = g;
     sc[MS_GAMMA_OLD] = 1.0;
     sc[MS_ETA] = g;
@@ -131,7 +113,7 @@ __device__ __forceinline__ MinresStep minres_scalars(const double* part_delta, c
   m.g = sc[MS_GAMMA];
   m.delta = sum_partials(part_delta, sh) / (m.g * m.g);
   m.gn2 = sum_partials(part_gamma, sh);
-  m.gn = sqrt(fmax(m.gn2, 0.0));
+  m.gn = sqrt_clamped(m.gn2);
   m.c = sc[MS_C];
   m.s = sc[MS_S];
   m.eta = sc[MS_ETA];
@@ -320,7 +302,7 @@ template <typename T>
 __global__ void gm_init_kernel(const T* __restrict__ r0, const double* part_beta, T* __restrict__ v0, double* g,
                                DevStatus* stat, double tol, int64_t n) {
   __shared__ double sh[32];
-  const double beta = sqrt(fmax(sum_partials(part_beta, sh), 0.0));
+  const double beta = sqrt_clamped(sum_partials(part_beta, sh));
   const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     v0[e] = (T)((double)r0[e] * ib);
@@ -365,7 +347,7 @@ __global__ void gm_hessenberg_kernel(int j, const double* h1, const double* h2, 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const double hn = sqrt(fmax(nrm2, 0.0));
+    const double hn = sqrt_clamped(nrm2);
     col[j + 1] = hn;
     *hnext = hn;
     for (int i = 0; i < j; ++i) {
@@ -908,7 +890,7 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
   }
   cc = block_sum(cc, sh);
   ca = block_sum(ca, sh);
-  const double gam = sqrt(fmax(uu - cc, 0.0));
+  const double gam = sqrt_clamped(uu - cc);
   const double igam = gam > 0.0 ? 1.0 / gam : 0.0;
   const double bj = (a[j] - ca) * igam;  // q_j^T w
   const double alpha = dc[DC_ALPHA];     // scale of u_j
@@ -969,8 +951,11 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
     if (j == 0) {
       g[0] = dc[DC_BETA] * gam;  // r0 = ||r0|| u_0 = (||r0|| gamma_0) q_0
       stat->iters = 0;
-      if (!(gam > 0.0) || !isfinite(gam)) {
-        stat->status = isfinite(gam) ? WC4D_ERR_BREAKDOWN : WC4D_ERR_NONFINITE;
+      if (!isfinite(gam) || !isfinite(ww) || !isfinite(bj)) {
+        stat->status = WC4D_ERR_NONFINITE;
+        stat->done = 1;
+      } else if (!(gam > 0.0)) {
+        stat->status = WC4D_ERR_BREAKDOWN;
         stat->done = 1;
       }
     } else {
@@ -992,7 +977,7 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
       const double est = fabs(g[jc + 1]) / *bnorm;
       stat->iters = j;
       stat->est = est;
-      if (!isfinite(est) || !isfinite(gam)) {
+      if (!isfinite(est) || !isfinite(gam) || !isfinite(ww) || !isfinite(bj)) {
         stat->status = WC4D_ERR_NONFINITE;
         stat->done = 1;
       } else if (est <= stat->tol_est || !(gam > 0.0)) {

@@ -9,11 +9,15 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <fstream>
+#include <random>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
 #include "krylov.cuh"
+#include "learned.cuh"
 
 namespace wc4d {
 
@@ -114,6 +118,12 @@ struct wc4d_problem {
   bool dcgs = false;
   double *Hraw = nullptr, *Tm = nullptr, *dcst = nullptr, *bprev = nullptr, *cprev = nullptr, *ecoef = nullptr;
   double *red = nullptr, *yhat = nullptr;
+  // learned Schur-block correction (shat = LEARNED): weights, inference scratch
+  NetShape net_sh;
+  float* net_params = nullptr;
+  bool net_on = false;
+  float *net_in = nullptr, *net_out = nullptr, *net_act[3] = {nullptr, nullptr, nullptr};
+  double *net_nrm2 = nullptr, *net_part = nullptr;
   DevStatus* stat = nullptr;
   DevStatus* h_stat = nullptr;
   double* h_scal = nullptr;
@@ -166,6 +176,17 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
   ep.e[2] = {EPI_SADDLE_C2, c2, p, 0, v3, nullptr};
   os.attach(ops, P->st);
   gemm_run<T>(plan, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+}
+
+// Learned correction of the third block, in place: y <- |y| (y/|y| + f(y/|y|)).
+static void learned_block(wc4d_problem* P, double* y) {
+  const int64_t len = (int64_t)(P->N + 1) * P->s;
+  dot_partial<double>(y, y, len, P->net_part, nullptr, P->st);
+  dot_finish(P->net_part, P->net_nrm2, 0, P->st);
+  net_in_from(y, P->net_nrm2, P->net_in, len, P->st);
+  float* acts[3] = {P->net_act[0], P->net_act[1], P->net_act[2]};
+  net_forward(P->net_sh, P->net_params, 1, P->net_in, acts, P->net_out, P->st);
+  net_out_to(P->net_in, P->net_out, P->net_nrm2, y, len, P->st);
 }
 
 // P_D^{-1} v = (Dhat^{-1} v1, Rhat^{-1} v2, Shat^{-1} v3); Dhat^{-1} = W^T W with
@@ -231,6 +252,9 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
     os.attach(ops2, P->st);
     gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
     lhat_sweep<T>(P->md, k, u3, o3, false, ident, done, P->st);
+    if constexpr (std::is_same<T, double>::value) {
+      if (P->net_on) learned_block(P, o3);
+    }
   }
 }
 
@@ -492,7 +516,11 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(o->rhat >= WC4D_RHAT_EXACT && o->rhat <= WC4D_RHAT_DIAG, WC4D_ERR_ARG, "bad rhat");
   WC4D_CHECK(o->rhat == WC4D_RHAT_EXACT || o->rhat == WC4D_RHAT_DIAG || o->kappa_max > 1.0, WC4D_ERR_ARG,
              "kappa_max must exceed 1");
-  WC4D_CHECK(o->shat == WC4D_SHAT_PAPER || o->shat == WC4D_SHAT_EXACT, WC4D_ERR_ARG, "bad shat");
+  WC4D_CHECK(o->shat == WC4D_SHAT_PAPER || o->shat == WC4D_SHAT_EXACT || o->shat == WC4D_SHAT_LEARNED, WC4D_ERR_ARG,
+             "bad shat");
+  WC4D_CHECK(o->shat != WC4D_SHAT_LEARNED ||
+                 (o->precond == WC4D_PRECOND_PD && o->krylov == WC4D_KRYLOV_GMRES && d->N + 1 <= 64),
+             WC4D_ERR_ARG, "the learned Schur block needs precond = PD, krylov = GMRES (flexible) and N + 1 <= 64");
   WC4D_CHECK(o->shat == WC4D_SHAT_PAPER || (int64_t)d->s * (d->N + 1) <= 8192, WC4D_ERR_ARG,
              "exact Schur complement limited to s(N+1) <= 8192");
   WC4D_CHECK(o->dhat == WC4D_DHAT_EXACT || o->dhat == WC4D_DHAT_SHIFT, WC4D_ERR_ARG, "bad dhat");
@@ -779,6 +807,15 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->r = P->alloc<double>(n);
   P->x0 = P->alloc<double>(n);
   P->stat = P->alloc<DevStatus>(1);
+  if (o->shat == WC4D_SHAT_LEARNED) {
+    const int64_t len = (int64_t)(N + 1) * s;
+    P->net_in = P->alloc<float>(len);
+    P->net_out = P->alloc<float>(len);
+    for (int l = 0; l < 3; ++l) P->net_act[l] = P->alloc<float>(64 * (int64_t)s);
+    P->net_nrm2 = P->alloc<double>(1);
+    P->net_part = P->alloc<double>(DOT_BLOCKS);
+    P->net_params = P->alloc<float>(NetShape{N + 1, 64, s}.nparams());
+  }
   WC4D_CUDA(cudaMallocHost(&P->h_stat, sizeof(DevStatus)));
   WC4D_CUDA(cudaMallocHost(&P->h_scal, sizeof(double) * 8));
   WC4D_CUDA(cudaStreamSynchronize(st));
@@ -876,6 +913,10 @@ static int solve_minres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
     if (P->h_stat->done) {
       relres = true_relres(P, P->rhs, P->x);
       ++nA;
+      if (!std::isfinite(relres)) {
+        status = WC4D_ERR_NONFINITE;
+        break;
+      }
       if (relres <= P->o.tol || P->h_stat->est == 0.0) {
         converged = true;
         break;
@@ -892,7 +933,8 @@ static int solve_minres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   if (!converged) {
     relres = true_relres(P, P->rhs, P->x);
     ++nA;
-    if (status == WC4D_OK) status = (relres <= P->o.tol) ? WC4D_OK : WC4D_ERR_MAXIT;
+    if (status == WC4D_OK)
+      status = !std::isfinite(relres) ? WC4D_ERR_NONFINITE : (relres <= P->o.tol ? WC4D_OK : WC4D_ERR_MAXIT);
   }
   if (info) {
     info->iters = it;
@@ -1031,6 +1073,10 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       gm_combine<double, double>(P->Z, n, k, P->yhat, use_x0 ? P->x0 : nullptr, P->x, n, st);
       relres = true_relres(P, P->rhs, P->x);
       ++nA;
+      if (!std::isfinite(relres)) {
+        status = WC4D_ERR_NONFINITE;
+        break;
+      }
       if (relres <= P->o.tol) {
         converged = true;
         break;
@@ -1167,6 +1213,10 @@ static int solve_gmres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       gm_combine<double, double>(P->Z, n, it, P->y, x0, P->x, n, st);
       relres = true_relres(P, P->rhs, P->x);
       ++nA;
+      if (!std::isfinite(relres)) {
+        status = WC4D_ERR_NONFINITE;
+        break;
+      }
       if (relres <= P->o.tol) {
         converged = true;
         break;
@@ -1461,6 +1511,20 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
     status = solve_minres(P, &loc, use_x0 != 0);
   else
     status = solve_gmres(P, &loc, use_x0 != 0);
+  if (status != WC4D_OK && P->net_on) {
+    // the plain Schur block is the fallback of the learned one
+    P->net_on = false;
+    if (use_x0) WC4D_CUDA(cudaMemcpyAsync(P->x, x, bytes, kin, P->st));
+    loc = wc4d_info{};
+    try {
+      status = solve_gmres(P, &loc, use_x0 != 0);
+    } catch (...) {
+      P->net_on = true;
+      throw;
+    }
+    P->net_on = true;
+    loc.precond_fallback = 1;
+  }
   WC4D_CUDA(cudaMemcpyAsync(x, P->x, bytes, kout, P->st));
   WC4D_CUDA(cudaStreamSynchronize(P->st));
   loc.status = status;
@@ -1473,6 +1537,335 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
     wc4d::set_error(buf);
   }
   return status;
+  WC4D_API_END
+}
+
+// ------------------------------------------------------------ learned block
+static const char kNetMagic[8] = {'W', 'C', '4', 'D', 'N', 'E', 'T', '1'};
+
+void wc4d_default_train_opts(wc4d_train_opts* o) {
+  if (!o) return;
+  o->pairs = 50000;
+  o->hidden = 32;
+  o->batch = 64;
+  o->epochs = 4;
+  o->lr = 1e-3;
+  o->val_frac = 0.05;
+  o->seed = 1;
+}
+
+int64_t wc4d_net_nparams(int32_t C, int32_t hidden) { return NetShape{C, hidden, 1}.nparams(); }
+
+// Initial weights: uniform in +-1/sqrt(fan_in) from SplitMix64 of the seed
+// (host), biases zero, the last layer scaled by 0.1 (a small first correction).
+static std::vector<float> net_init(const NetShape& sh, uint64_t seed) {
+  std::vector<float> w((size_t)sh.nparams(), 0.f);
+  uint64_t z = seed * 0x9E3779B97F4A7C15ull + 12345;
+  auto next = [&]() {
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t x = z;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+  };
+  for (int l = 0; l < NET_LAYERS; ++l) {
+    const double a = 1.0 / std::sqrt((double)sh.ci(l) * NET_KW) * (l == NET_LAYERS - 1 ? 0.1 : 1.0);
+    const int64_t nw = (int64_t)sh.co(l) * sh.ci(l) * NET_KW;
+    for (int64_t i = 0; i < nw; ++i) w[(size_t)(sh.w_off(l) + i)] = (float)((2.0 * next() - 1.0) * a);
+  }
+  return w;
+}
+
+// Mean of |yn + f - tn|^2 / |tn|^2 over samples [i0, i1) of the pair store
+// (with_net = 0: f = 0, the plain block), forward passes in batches of B.
+static double net_val_error(wc4d_problem* P, const NetShape& sh, const float* params, const float* yn, const float* tn,
+                            const double* tn2, int i0, int i1, int B, float* xb, float* acts[3], float* outb,
+                            float* gout, int* d_idx, double* d_loss, bool with_net) {
+  cudaStream_t st = P->st;
+  const int64_t len = (int64_t)sh.C * sh.s;
+  WC4D_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(double), st));
+  std::vector<int> idx(B);
+  for (int b0 = i0; b0 < i1; b0 += B) {
+    const int nb = std::min(B, i1 - b0);
+    for (int b = 0; b < nb; ++b) idx[b] = b0 + b;
+    WC4D_CUDA(cudaMemcpy(d_idx, idx.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+    net_gather(yn, d_idx, nb, len, xb, st);
+    net_gather(tn, d_idx, nb, len, gout, st);  // targets into the gradient buffer (scratch here)
+    if (with_net)
+      net_forward(sh, params, nb, xb, acts, outb, st);
+    else
+      WC4D_CUDA(cudaMemsetAsync(outb, 0, sizeof(float) * nb * len, st));
+    // loss kernel overwrites its gradient argument: give it acts[0] as scratch (>= nb * len floats)
+    net_loss_grad(sh, nb, xb, outb, gout, tn2, d_idx, acts[0], d_loss, st);
+  }
+  double h = 0;
+  WC4D_CUDA(cudaMemcpy(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost));
+  return h / std::max(1, i1 - i0);
+}
+
+static void save_net(const char* path, const NetShape& sh, const std::vector<float>& w, double ve, double vp) {
+  std::ofstream f(path, std::ios::binary);
+  WC4D_CHECK(f.good(), WC4D_ERR_IO, std::string("cannot write ") + path);
+  const int32_t hdr[3] = {sh.C, sh.H, sh.s};
+  const int64_t np = sh.nparams();
+  f.write(kNetMagic, 8);
+  f.write((const char*)hdr, sizeof hdr);
+  f.write((const char*)&np, sizeof np);
+  f.write((const char*)w.data(), sizeof(float) * w.size());
+  f.write((const char*)&ve, sizeof ve);
+  f.write((const char*)&vp, sizeof vp);
+  WC4D_CHECK(f.good(), WC4D_ERR_IO, std::string("write failed: ") + path);
+}
+
+int wc4d_precond_set_net(wc4d_problem* P, int32_t hidden, const float* params, int32_t active) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && params, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(P->o.shat == WC4D_SHAT_LEARNED && P->net_params, WC4D_ERR_ARG,
+             "the problem was not set up with shat = LEARNED");
+  WC4D_CHECK(hidden >= 1 && hidden <= 64, WC4D_ERR_ARG, "hidden must lie in [1, 64]");
+  P->net_sh = NetShape{P->N + 1, hidden, P->s};
+  WC4D_CUDA(cudaMemcpyAsync(P->net_params, params, sizeof(float) * P->net_sh.nparams(), cudaMemcpyHostToDevice, P->st));
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+  P->net_on = active != 0;
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+int wc4d_precond_load(wc4d_problem* P, const char* path) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P && path, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(P->o.shat == WC4D_SHAT_LEARNED && P->net_params, WC4D_ERR_ARG,
+             "the problem was not set up with shat = LEARNED");
+  std::ifstream f(path, std::ios::binary);
+  WC4D_CHECK(f.good(), WC4D_ERR_IO, std::string("cannot read ") + path);
+  char mg[8];
+  int32_t hdr[3];
+  int64_t np = 0;
+  f.read(mg, 8);
+  f.read((char*)hdr, sizeof hdr);
+  f.read((char*)&np, sizeof np);
+  WC4D_CHECK(f.good() && std::memcmp(mg, kNetMagic, 8) == 0, WC4D_ERR_IO, "not a wc4d network checkpoint");
+  WC4D_CHECK(hdr[0] == P->N + 1 && hdr[2] == P->s && hdr[1] >= 1 && hdr[1] <= 64, WC4D_ERR_ARG,
+             "checkpoint was trained for another (N+1, s)");
+  const NetShape sh{hdr[0], hdr[1], hdr[2]};
+  WC4D_CHECK(np == sh.nparams(), WC4D_ERR_IO, "checkpoint parameter count mismatch");
+  std::vector<float> w((size_t)np);
+  double ve = 0, vp = 0;
+  f.read((char*)w.data(), sizeof(float) * np);
+  f.read((char*)&ve, sizeof ve);
+  f.read((char*)&vp, sizeof vp);
+  WC4D_CHECK(f.good(), WC4D_ERR_IO, "truncated checkpoint");
+  return wc4d_precond_set_net(P, sh.H, w.data(), ve < vp ? 1 : 0);
+  WC4D_API_END
+}
+
+int wc4d_precond_train(wc4d_problem* P, const wc4d_train_opts* o_in, const char* ckpt_path, wc4d_train_report* rep) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P, WC4D_ERR_ARG, "null problem");
+  wc4d_train_opts o;
+  if (o_in)
+    o = *o_in;
+  else
+    wc4d_default_train_opts(&o);
+  WC4D_CHECK(P->o.shat == WC4D_SHAT_LEARNED && P->have_pd && P->o.rhat == WC4D_RHAT_EXACT &&
+                 P->o.dhat == WC4D_DHAT_EXACT,
+             WC4D_ERR_ARG, "training needs a problem set up with precond = PD, shat = LEARNED, rhat = dhat = EXACT");
+  WC4D_CHECK(o.pairs >= 2 && o.hidden >= 1 && o.hidden <= 64 && o.batch >= 1 && o.batch <= 4096 && o.epochs >= 1 &&
+                 o.lr > 0 && o.val_frac > 0 && o.val_frac < 1,
+             WC4D_ERR_ARG, "bad training options");
+  cudaStream_t st = P->st;
+  const int C = P->N + 1, s = P->s;
+  const NetShape sh{C, o.hidden, s};
+  const int64_t len = (int64_t)C * s, n = P->n;
+  const int nval = std::max(1, (int)std::lround(o.pairs * o.val_frac));
+  const int ntr = o.pairs - nval;
+  WC4D_CHECK(ntr >= 1, WC4D_ERR_ARG, "no training pairs left after the validation split");
+  std::vector<void*> owned;
+  auto dalloc = [&](size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) throw wc4d::Error{WC4D_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    owned.push_back(p);
+    return p;
+  };
+  const bool was_on = P->net_on;
+  try {
+    P->net_on = false;  // pairs use the plain operators
+    float* yn = (float*)dalloc(sizeof(float) * len * o.pairs);
+    float* tn = (float*)dalloc(sizeof(float) * len * o.pairs);
+    double* tn2 = (double*)dalloc(sizeof(double) * o.pairs);
+    double* va = (double*)dalloc(sizeof(double) * n);
+    double* vb = (double*)dalloc(sizeof(double) * n);
+    double* vc = (double*)dalloc(sizeof(double) * n);
+    double* nrm2 = (double*)dalloc(sizeof(double));
+    double* part = (double*)dalloc(sizeof(double) * DOT_BLOCKS);
+    WC4D_CUDA(cudaMemsetAsync(tn2, 0, sizeof(double) * o.pairs, st));
+    const int64_t off3 = P->ns + P->np;  // the x block (Schur block) of a saddle vector
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < o.pairs; ++i) {
+      // v: white noise, or S_hat^{-1} of white noise (alternately)
+      WC4D_CUDA(cudaMemsetAsync(va, 0, sizeof(double) * n, st));
+      normal_fill(va + off3, len, o.seed, (uint64_t)i * (uint64_t)len, st);
+      if (i & 1) {
+        apply_P<double>(P, WC4D_PRECOND_PD, P->f64, va, vb, nullptr);  // (0, 0, S_hat^{-1} xi)
+      } else {
+        launch_copy_d(vb, va, n, st);
+      }
+      // r = S v: A (0,0,v) = (L v, H v, 0); P_D of that = (D^-1 L v, R^-1 H v, 0); A of that: x block = S v
+      apply_A<double>(P, P->f64, P->plan_A, vb, vc, nullptr);
+      WC4D_CUDA(cudaMemsetAsync(vc + off3, 0, sizeof(double) * len, st));
+      apply_P<double>(P, WC4D_PRECOND_PD, P->f64, vc, va, nullptr);
+      WC4D_CUDA(cudaMemsetAsync(va + off3, 0, sizeof(double) * len, st));
+      apply_A<double>(P, P->f64, P->plan_A, va, vc, nullptr);
+      // y = S_hat^{-1} r
+      WC4D_CUDA(cudaMemsetAsync(va, 0, sizeof(double) * off3, st));
+      launch_copy_d(va + off3, vc + off3, len, st);
+      apply_P<double>(P, WC4D_PRECOND_PD, P->f64, va, vc, nullptr);
+      dot_partial<double>(vc + off3, vc + off3, len, part, nullptr, st);
+      dot_finish(part, nrm2, 0, st);
+      net_store_pair(vc + off3, vb + off3, nrm2, yn + (int64_t)i * len, tn + (int64_t)i * len, tn2 + i, len, st);
+    }
+    WC4D_CUDA(cudaStreamSynchronize(st));
+    const auto t1 = std::chrono::steady_clock::now();
+    // training buffers
+    const int B = o.batch;
+    const int Hm = std::max(C, sh.H);
+    float* params = (float*)dalloc(sizeof(float) * sh.nparams());
+    float* grads = (float*)dalloc(sizeof(float) * sh.nparams());
+    float* am = (float*)dalloc(sizeof(float) * sh.nparams());
+    float* av = (float*)dalloc(sizeof(float) * sh.nparams());
+    float* xb = (float*)dalloc(sizeof(float) * B * len);
+    float* tb = (float*)dalloc(sizeof(float) * B * len);
+    float* outb = (float*)dalloc(sizeof(float) * B * len);
+    float* gout = (float*)dalloc(sizeof(float) * B * len);
+    float* acts[3];
+    for (int l = 0; l < 3; ++l) acts[l] = (float*)dalloc(sizeof(float) * B * (int64_t)Hm * s);
+    float* sc0 = (float*)dalloc(sizeof(float) * B * (int64_t)Hm * s);
+    float* sc1 = (float*)dalloc(sizeof(float) * B * (int64_t)Hm * s);
+    const int64_t wcap = net_wpart_elems(sh, B);
+    float* wpart = (float*)dalloc(sizeof(float) * wcap);
+    int* d_idx = (int*)dalloc(sizeof(int) * B);
+    double* d_loss = (double*)dalloc(sizeof(double));
+    std::vector<float> w0 = net_init(sh, o.seed);
+    WC4D_CUDA(cudaMemcpy(params, w0.data(), sizeof(float) * w0.size(), cudaMemcpyHostToDevice));
+    WC4D_CUDA(cudaMemsetAsync(am, 0, sizeof(float) * sh.nparams(), st));
+    WC4D_CUDA(cudaMemsetAsync(av, 0, sizeof(float) * sh.nparams(), st));
+    std::mt19937_64 rng(o.seed);
+    std::vector<int> order(ntr), idx(B);
+    for (int i = 0; i < ntr; ++i) order[i] = i;
+    double loss_first = 0, loss_last = 0;
+    int step = 0;
+    for (int ep = 0; ep < o.epochs; ++ep) {
+      std::shuffle(order.begin(), order.end(), rng);
+      WC4D_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(double), st));
+      int seen = 0;
+      for (int b0 = 0; b0 + B <= ntr || (b0 < ntr && b0 == 0); b0 += B) {
+        const int nb = std::min(B, ntr - b0);
+        for (int b = 0; b < nb; ++b) idx[b] = order[b0 + b];
+        WC4D_CUDA(cudaMemcpy(d_idx, idx.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+        net_gather(yn, d_idx, nb, len, xb, st);
+        net_gather(tn, d_idx, nb, len, tb, st);
+        net_forward(sh, params, nb, xb, acts, outb, st);
+        net_loss_grad(sh, nb, xb, outb, tb, tn2, d_idx, gout, d_loss, st);
+        net_backward(sh, params, nb, xb, acts, gout, grads, sc0, sc1, wpart, wcap, st);
+        net_adam(params, grads, am, av, sh.nparams(), (float)o.lr, ++step, st);
+        seen += nb;
+      }
+      double h = 0;
+      WC4D_CUDA(cudaMemcpy(&h, d_loss, sizeof(double), cudaMemcpyDeviceToHost));
+      const double mean = h / std::max(1, seen);
+      if (ep == 0) loss_first = mean;
+      loss_last = mean;
+    }
+    // the plain block judges the net on the held-out pairs
+    const double el = net_val_error(P, sh, params, yn, tn, tn2, ntr, o.pairs, B, xb, acts, outb, tb, d_idx, d_loss, true);
+    const double ep_ = net_val_error(P, sh, params, yn, tn, tn2, ntr, o.pairs, B, xb, acts, outb, tb, d_idx, d_loss,
+                                     false);
+    const auto t2 = std::chrono::steady_clock::now();
+    std::vector<float> w((size_t)sh.nparams());
+    WC4D_CUDA(cudaMemcpy(w.data(), params, sizeof(float) * w.size(), cudaMemcpyDeviceToHost));
+    const bool keep = std::sqrt(el) < std::sqrt(ep_);
+    P->net_sh = sh;
+    WC4D_CUDA(cudaMemcpy(P->net_params, params, sizeof(float) * w.size(), cudaMemcpyDeviceToDevice));
+    P->net_on = keep;
+    if (ckpt_path) save_net(ckpt_path, sh, w, std::sqrt(el), std::sqrt(ep_));
+    if (rep) {
+      rep->loss_first = loss_first;
+      rep->loss_last = loss_last;
+      rep->val_err_learned = std::sqrt(el);
+      rep->val_err_plain = std::sqrt(ep_);
+      rep->kept = keep ? 1 : 0;
+      rep->pairs_train = ntr;
+      rep->gen_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+      rep->train_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    }
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    for (void* p : owned) cudaFree(p);
+    P->net_on = was_on;
+    throw;
+  }
+  WC4D_CUDA(cudaStreamSynchronize(st));
+  for (void* p : owned) cudaFree(p);
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+int wc4d_net_grad(int32_t C, int32_t hidden, int32_t s, int32_t B, const float* params, const float* yn,
+                  const float* tn, double* loss, float* grads) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(params && yn && tn && loss && grads, WC4D_ERR_ARG, "null argument");
+  WC4D_CHECK(C >= 1 && C <= 64 && hidden >= 1 && hidden <= 64 && s >= 1 && B >= 1 && B <= 4096, WC4D_ERR_ARG,
+             "bad network sizes");
+  const NetShape sh{C, hidden, s};
+  const int64_t len = (int64_t)C * s, np = sh.nparams(), Hm = std::max(C, hidden);
+  cudaStream_t st = nullptr;
+  std::vector<void*> owned;
+  auto dalloc = [&](size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) throw wc4d::Error{WC4D_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    owned.push_back(p);
+    return p;
+  };
+  try {
+    float* dp = (float*)dalloc(sizeof(float) * np);
+    float* dg = (float*)dalloc(sizeof(float) * np);
+    float* dy = (float*)dalloc(sizeof(float) * B * len);
+    float* dt = (float*)dalloc(sizeof(float) * B * len);
+    float* out = (float*)dalloc(sizeof(float) * B * len);
+    float* gout = (float*)dalloc(sizeof(float) * B * len);
+    float* acts[3];
+    for (int l = 0; l < 3; ++l) acts[l] = (float*)dalloc(sizeof(float) * B * Hm * s);
+    float* sc0 = (float*)dalloc(sizeof(float) * B * Hm * s);
+    float* sc1 = (float*)dalloc(sizeof(float) * B * Hm * s);
+    const int64_t wcap = net_wpart_elems(sh, B);
+    float* wpart = (float*)dalloc(sizeof(float) * wcap);
+    double* tn2 = (double*)dalloc(sizeof(double) * B);
+    double* dl = (double*)dalloc(sizeof(double));
+    WC4D_CUDA(cudaMemcpy(dp, params, sizeof(float) * np, cudaMemcpyHostToDevice));
+    WC4D_CUDA(cudaMemcpy(dy, yn, sizeof(float) * B * len, cudaMemcpyHostToDevice));
+    WC4D_CUDA(cudaMemcpy(dt, tn, sizeof(float) * B * len, cudaMemcpyHostToDevice));
+    std::vector<double> h2(B, 0.0);
+    for (int b = 0; b < B; ++b)
+      for (int64_t e = 0; e < len; ++e) h2[b] += (double)tn[b * len + e] * tn[b * len + e];
+    WC4D_CUDA(cudaMemcpy(tn2, h2.data(), sizeof(double) * B, cudaMemcpyHostToDevice));
+    WC4D_CUDA(cudaMemset(dl, 0, sizeof(double)));
+    net_forward(sh, dp, B, dy, acts, out, st);
+    net_loss_grad(sh, B, dy, out, dt, tn2, nullptr, gout, dl, st);
+    net_backward(sh, dp, B, dy, acts, gout, dg, sc0, sc1, wpart, wcap, st);
+    WC4D_CUDA(cudaMemcpy(grads, dg, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    double h = 0;
+    WC4D_CUDA(cudaMemcpy(&h, dl, sizeof(double), cudaMemcpyDeviceToHost));
+    *loss = h / B;
+  } catch (...) {
+    cudaDeviceSynchronize();
+    for (void* p : owned) cudaFree(p);
+    throw;
+  }
+  for (void* p : owned) cudaFree(p);
+  return WC4D_OK;
   WC4D_API_END
 }
 

@@ -29,6 +29,7 @@ WC4D_ERR_MAXIT = 5
 WC4D_ERR_TIMEOUT = 6
 WC4D_ERR_CUDA = 7
 WC4D_ERR_NOMEM = 8
+WC4D_ERR_IO = 9
 
 WC4D_MODEL_STENCIL3 = 0
 WC4D_MODEL_BANDED = 1
@@ -44,6 +45,7 @@ WC4D_RHAT_ME = 2
 WC4D_RHAT_DIAG = 3
 WC4D_SHAT_PAPER = 0
 WC4D_SHAT_EXACT = 1
+WC4D_SHAT_LEARNED = 2
 WC4D_DHAT_EXACT = 0
 WC4D_DHAT_SHIFT = 1
 WC4D_KRYLOV_MINRES = 0
@@ -82,6 +84,7 @@ class SolveOpts(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("precond_fallback", ctypes.c_int32),
                 ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double), ("ms", ctypes.c_double),
                 ("n_apply_A", ctypes.c_int64), ("n_apply_P", ctypes.c_int64)]
 
@@ -95,6 +98,22 @@ class Stats(ctypes.Structure):
                 ("orth_launches", ctypes.c_int64), ("gemm32_ms", ctypes.c_double), ("gemm32_flops", ctypes.c_double),
                 ("gemm32_launches", ctypes.c_int64), ("gemmdf_ms", ctypes.c_double),
                 ("gemmdf_flops", ctypes.c_double), ("gemmdf_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int32), ("hidden", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("epochs", ctypes.c_int32), ("lr", ctypes.c_double), ("val_frac", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class TrainReport(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("val_err_learned", ctypes.c_double), ("val_err_plain", ctypes.c_double),
+                ("kept", ctypes.c_int32), ("pairs_train", ctypes.c_int32),
+                ("gen_ms", ctypes.c_double), ("train_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -135,6 +154,15 @@ SIGNATURES = {
                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
+    "wc4d_default_train_opts": (None, [ctypes.POINTER(TrainOpts)]),
+    "wc4d_precond_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TrainOpts), ctypes.c_char_p,
+                                          ctypes.POINTER(TrainReport)]),
+    "wc4d_precond_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "wc4d_precond_set_net": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32]),
+    "wc4d_net_grad": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.c_void_p]),
+    "wc4d_net_nparams": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32]),
     "wc4d_destroy": (None, [ctypes.c_void_p]),
     "wc4d_last_error": (ctypes.c_char_p, []),
 }
@@ -245,6 +273,25 @@ def solve_batch(problems, rhs_list, x_list=None, use_x0=False, workers=0):
     return x_list, infos, code
 
 
+def net_nparams(C: int, hidden: int) -> int:
+    return int(load().wc4d_net_nparams(int(C), int(hidden)))
+
+
+def net_grad(C, hidden, s, params, yn, tn):
+    """Library (device) mean loss and parameter gradients of the learned net on
+    host samples yn, tn of shape [B, C, s]."""
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    yn = np.ascontiguousarray(yn, dtype=np.float32)
+    tn = np.ascontiguousarray(tn, dtype=np.float32)
+    B = yn.shape[0]
+    grads = np.zeros_like(params)
+    loss = ctypes.c_double(0.0)
+    _check(load().wc4d_net_grad(int(C), int(hidden), int(s), int(B), ctypes.c_void_p(params.ctypes.data),
+                                ctypes.c_void_p(yn.ctypes.data), ctypes.c_void_p(tn.ctypes.data),
+                                ctypes.byref(loss), ctypes.c_void_p(grads.ctypes.data)))
+    return loss.value, grads
+
+
 def wc4d_apply_fp32(h, which: int, v_ptr: int, out_ptr: int) -> None:
     _check(load().wc4d_apply_fp32(h, which, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)))
 
@@ -319,7 +366,7 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
     o.k = int(k)
     o.rhat = RHAT[rhat]
     o.kappa_max = float(kappa_max)
-    o.shat = WC4D_SHAT_EXACT if shat == "exact" else WC4D_SHAT_PAPER
+    o.shat = {"paper": WC4D_SHAT_PAPER, "exact": WC4D_SHAT_EXACT, "learned": WC4D_SHAT_LEARNED}[shat]
     o.dhat = WC4D_DHAT_SHIFT if dhat in ("rr", "shift") else WC4D_DHAT_EXACT
     o.dhat_delta = float(dhat_delta)
     if krylov is None:
@@ -444,6 +491,25 @@ class Problem:
                                          ctypes.c_void_p(y.ctypes.data), ctypes.c_void_p(traj.ctypes.data),
                                          WC4D_MEM_HOST, ctypes.c_void_p(rhs.ctypes.data)))
         return rhs
+
+    def precond_train(self, pairs=50000, hidden=32, batch=64, epochs=4, lr=1e-3, val_frac=0.05, seed=1,
+                      ckpt_path=None):
+        """Train the learned Schur block on the device; returns the TrainReport."""
+        o = TrainOpts()
+        load().wc4d_default_train_opts(ctypes.byref(o))
+        o.pairs, o.hidden, o.batch, o.epochs = int(pairs), int(hidden), int(batch), int(epochs)
+        o.lr, o.val_frac, o.seed = float(lr), float(val_frac), int(seed)
+        rep = TrainReport()
+        path = ckpt_path.encode() if ckpt_path else None
+        _check(load().wc4d_precond_train(self.h, ctypes.byref(o), path, ctypes.byref(rep)))
+        return rep
+
+    def precond_load(self, ckpt_path):
+        _check(load().wc4d_precond_load(self.h, ckpt_path.encode()))
+
+    def precond_set_net(self, hidden, params, active=True):
+        w = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().wc4d_precond_set_net(self.h, int(hidden), ctypes.c_void_p(w.ctypes.data), int(active)))
 
     def matrix(self, which):
         import torch

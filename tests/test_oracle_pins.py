@@ -481,3 +481,57 @@ def test_gauss_newton_l96_rhs_and_convergence():
         lin = sd.linearised_cost(prob, b.ravel(), d.ravel(), eps * e) - costs[0]
         non = J(traj + eps * e.reshape(traj.shape)) - costs[0]
         assert lin == pytest.approx(non, rel=10 * eps)
+
+
+# ------------------------------------------------------ learned Schur block
+def test_learned_conv_matches_dense_definition():
+    """The periodic conv equals the dense matrix built entry by entry from
+    out[co, x] = b[co] + sum W[co, ci, k] in[ci, (x + k - 2) mod s]."""
+    from oracle import learned as ln
+    g = np.random.default_rng(3)
+    W = g.standard_normal((4, 3, ln.KW))
+    b = g.standard_normal(4)
+    x = g.standard_normal((3, 11))
+    ref = (ln.conv_matrix(W, 11) @ x.ravel()).reshape(4, 11) + b[:, None]
+    assert np.max(np.abs(ln.conv1d(x, W, b) - ref)) < 1e-13
+
+
+def test_learned_backward_matches_finite_differences():
+    """Every weight and bias gradient of |z - t|^2/|t|^2 against central
+    differences in FP64 (step 1e-6): relative error below 1e-6."""
+    from oracle import learned as ln
+    g = np.random.default_rng(4)
+    params = ln.init_params(3, 5, seed=7)
+    params = [(W + 0.05 * g.standard_normal(W.shape), b + 0.05 * g.standard_normal(b.shape)) for W, b in params]
+    y = g.standard_normal((3, 13))
+    t = y + 0.3 * g.standard_normal((3, 13))
+    _, grads = ln.backward(params, y, t)
+    h = 1e-6
+    worst = 0.0
+    for li in range(4):
+        for which in (0, 1):
+            arr = params[li][which]
+            gref = grads[li][which]
+            for idx in np.ndindex(arr.shape):
+                old = arr[idx]
+                arr[idx] = old + h
+                lp = ln.loss(params, y, t)
+                arr[idx] = old - h
+                lm = ln.loss(params, y, t)
+                arr[idx] = old
+                fd = (lp - lm) / (2 * h)
+                worst = max(worst, abs(fd - gref[idx]) / max(1e-8, abs(fd) + abs(gref[idx])))
+    assert worst < 1e-6, worst
+
+
+def test_learned_preconditioner_is_scale_equivariant():
+    """z(alpha y) = alpha z(y) for alpha > 0: the input is normalised before the
+    network and the output rescaled, so the preconditioner commutes with the
+    residual's scale (as a Krylov preconditioner must, up to rounding)."""
+    from oracle import learned as ln
+    g = np.random.default_rng(5)
+    params = ln.init_params(3, 4, seed=2)
+    y = g.standard_normal((3, 9))
+    z1, _ = ln.forward(params, y)
+    z2, _ = ln.forward(params, 1e5 * y)
+    assert np.max(np.abs(z2 - 1e5 * z1)) <= 1e-9 * np.max(np.abs(z2))
