@@ -56,8 +56,11 @@ def parse():
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "batch"],
-                    help="scale: one s=2048 N=64 window (default line); batch: independent uneven windows")
+    ap.add_argument("--workload", default="scale", choices=["scale", "batch", "learned"],
+                    help="scale: one s=2048 N=64 window (default line); batch: independent uneven windows; "
+                         "learned: learned Schur block vs the plain P_D (s=1024 N=32)")
+    ap.add_argument("--pairs", type=int, default=50000, help="training pairs of the learned workload")
+    ap.add_argument("--epochs", type=int, default=4, help="training epochs of the learned workload")
     ap.add_argument("--batch", type=int, default=256, help="windows in the batched workload")
     ap.add_argument("--batch-maxit", type=int, default=250, help="Krylov cap per batched window")
     ap.add_argument("--workers", type=int, default=8, help="host workers / CUDA streams of the batched solve")
@@ -478,12 +481,77 @@ def run_batch(args):
         G.close()
 
 
+def run_learned(args):
+    """Learned Schur block (trained on the device, outside the timed region)
+    against the plain block-diagonal preconditioner: advection-diffusion
+    s=1024, N=32, p=512, P_D with L_M(k), solves to true relres 1e-6."""
+    import numpy as np
+    import torch
+
+    from paper_2105_06975_gb300 import wc4d, workload as W
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    w = W.SCALE.with_(name="learned-advdiff", s=1024, N=32, p=512)
+    dr = W.draws(w, args.seed * 1000 + rank)
+    k = min(args.k, w.N + 1)
+    arms = {
+        "learned_gmres": wc4d.make_opts(precond="PD", k=k, shat="learned", krylov="gmres", tol=1e-6,
+                                        maxit=args.maxit, precision="df32"),
+        "plain_gmres": wc4d.make_opts(precond="PD", k=k, krylov="gmres", tol=1e-6, maxit=args.maxit,
+                                      precision="df32"),
+        "plain_minres": wc4d.make_opts(precond="PD", k=k, krylov="minres", tol=1e-6, maxit=20000,
+                                       precision="df32"),
+    }
+    probs = {a: wc4d.Problem.from_workload(w, dr, o) for a, o in arms.items()}
+    rhs = probs["plain_gmres"].synthesize_rhs(dr)
+    t0 = time.perf_counter()
+    rep = probs["learned_gmres"].precond_train(pairs=args.pairs, hidden=32, batch=64, epochs=args.epochs,
+                                               lr=1e-3, seed=args.seed + 1)
+    train_s = time.perf_counter() - t0
+    out_arms = {}
+    for a, G in probs.items():
+        x = torch.zeros_like(rhs)
+        for _ in range(args.warmup):
+            G.solve(rhs, x)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [G.solve(rhs, x)[1] for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out_arms[a] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iterations": infos[-1].iters,
+                       "status": infos[-1].status, "relres_true": infos[-1].relres_true,
+                       "precond_fallback": infos[-1].precond_fallback}
+    best = out_arms["learned_gmres"]
+    line = {"metric": METRIC, "value": best["solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": best["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "df32 products / f64 recurrences; learned block FP32", "data": "synthetic",
+            "impl": "gpu",
+            "config": {"workload": f"advection-diffusion window s={w.s} N={w.N} p={w.p} (n={w.n}), SOAR B/Q/R; "
+                                   "learned Schur block in GMRES vs plain P_D",
+                       "precond": "PD", "lhat": f"L_M({k})", "tol": 1e-6, "pairs": args.pairs,
+                       "epochs": args.epochs, "hidden": 32,
+                       "step": "one solve with the problem set up and the net trained (outside the timed region)",
+                       "l2": "operators (3 x 8 MB B/Q/R plus factors) and the n-vectors exceed L2 only in part"},
+            "arms": out_arms, "training": {k_: (round(v, 5) if isinstance(v, float) else v)
+                                           for k_, v in rep.as_dict().items()},
+            "train_wall_s": train_s}
+    print(json.dumps(line))
+    for G in probs.values():
+        G.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_gpu(args)
 

@@ -56,6 +56,29 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// two block-wide sums at once (sh: two doubles per warp), results in every thread
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[wid] = a;
+    sh[32 + wid] = b;
+  }
+  __syncthreads();
+  double ta = 0.0, tb = 0.0;
+  for (int i = 0; i < nw; ++i) {
+    ta += sh[i];
+    tb += sh[32 + i];
+  }
+  a = ta;
+  b = tb;
+}
+
 // block-wide sum, result valid in every thread (sh: one double per warp)
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;

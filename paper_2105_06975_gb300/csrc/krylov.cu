@@ -785,9 +785,10 @@ void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float
 // scan of (A, B) pairs (a -> A a + B) instead of m dependent steps: on GB300 a
 // serial FP64 chain in one thread costs tens of cycles per operation.  Ends
 // with col[0..m-1] rotated and col[m] = a_m; col[m+1] is untouched.  Needs
-// m <= 2 * blockDim.x; sh: 64 doubles of shared scratch (two per warp).
+// m <= SCAN_PER * blockDim.x; sh: 64 doubles of shared scratch (two per warp).
+constexpr int SCAN_PER = 8;
 __device__ void rotate_column_scan(double* col, const double* rc, const double* rs, int m, double* sh) {
-  const int per = (m + blockDim.x - 1) / blockDim.x;  // 1 or 2 rotations per thread
+  const int per = (m + blockDim.x - 1) / blockDim.x;  // at most SCAN_PER rotations per thread
   const int i0 = threadIdx.x * per;
   const int i1 = min(i0 + per, m);
   double LA = 1.0, LB = 0.0;  // this thread's rotations composed, in order
@@ -843,7 +844,7 @@ __device__ void rotate_column_scan(double* col, const double* rc, const double* 
   }
   const double a0 = col[0];
   double av = eA * a0 + eB;  // a_{i0}
-  double outv[2] = {0.0, 0.0};
+  double outv[SCAN_PER];
   for (int i = i0; i < i1; ++i) {
     const double y = col[i + 1];
     outv[i - i0] = rc[i] * av + rs[i] * y;
@@ -862,11 +863,11 @@ __device__ void rotate_column_scan(double* col, const double* rc, const double* 
 // the triangular T with u_j = Q_j c_j + gamma_j q_j (T = [c_j; gamma_j]), so
 // that P^-1 Q = Z~ T^-1 for the stored Z~_j = P^-1 u_j.  Shared memory: the
 // column and the rotations (3j + 2 doubles, as the CGS2 Hessenberg kernel).
-__global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* __restrict__ red, double* dc,
-                                                          double* bprev, double* cprev, double* e, double* Hraw,
-                                                          double* H, double* T, int ldh, double* cs, double* sn,
-                                                          double* g, double* hnext, DevStatus* stat,
-                                                          const double* bnorm) {
+__global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const double* __restrict__ red, double* dc,
+                                                         double* bprev, double* cprev, double* e, double* Hraw,
+                                                         double* H, double* T, int ldh, double* cs, double* sn,
+                                                         double* g, double* hnext, DevStatus* stat,
+                                                         const double* bnorm, const double* __restrict__ hc) {
   extern __shared__ double sm[];
   __shared__ double sh[64];
   if (*(volatile const int*)&stat->done) return;
@@ -876,7 +877,6 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
   double* col = sm;             // [j + 2]
   double* rc = col + j + 2;     // [j]
   double* rs = rc + j;          // [j]
-  double* tp = rs + j;          // [nseg * j] partial sums of Hbar c (nseg > 1 only)
   for (int i = threadIdx.x; i + 1 < j; i += blockDim.x) {
     rc[i] = cs[i];
     rs[i] = sn[i];
@@ -888,51 +888,19 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
     cc += c[i] * c[i];
     ca += c[i] * a[i];
   }
-  cc = block_sum(cc, sh);
-  ca = block_sum(ca, sh);
+  block_sum2(cc, ca, sh);
   const double gam = sqrt_clamped(uu - cc);
   const double igam = gam > 0.0 ? 1.0 / gam : 0.0;
   const double bj = (a[j] - ca) * igam;  // q_j^T w
   const double alpha = dc[DC_ALPHA];     // scale of u_j
   const double gprev = dc[DC_GAMMA];
-  // Hbar c_{j-1} (rows 0..j-1, columns 0..j-2 of the raw Hessenberg): the
-  // column range is cut into nseg segments so every thread has a short run of
-  // independent loads; the segments are summed in a fixed order.
-  const int nseg = (j >= 1) ? max(1, min((int)blockDim.x / j, 32)) : 1;
-  if (j >= 1) {
-    const int ncol = j - 1;
-    const int seg = (ncol + nseg - 1) / nseg;
-    for (int idx = threadIdx.x; idx < nseg * j; idx += blockDim.x) {
-      const int r = idx % j, sgi = idx / j;
-      const int k0 = max(sgi * seg, r > 0 ? r - 1 : 0), k1 = min((sgi + 1) * seg, ncol);
-      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-      int k = k0;
-      for (; k + 4 <= k1; k += 4) {
-        t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
-        t1 += Hraw[r + (int64_t)(k + 1) * ldh] * cprev[k + 1];
-        t2 += Hraw[r + (int64_t)(k + 2) * ldh] * cprev[k + 2];
-        t3 += Hraw[r + (int64_t)(k + 3) * ldh] * cprev[k + 3];
-      }
-      for (; k < k1; ++k) t0 += Hraw[r + (int64_t)k * ldh] * cprev[k];
-      const double tsum = (t0 + t1) + (t2 + t3);
-      if (nseg > 1)
-        tp[sgi * j + r] = tsum;
-      else
-        col[r] = tsum;
-    }
-  }
-  __syncthreads();
-  // column j-1: (b_{j-1} - Hbar c_{j-1} + alpha c_j) / gamma_{j-1}, sub-diagonal alpha gamma / gamma_{j-1}
+  // column j-1: (b_{j-1} - Hbar c_{j-1} + alpha c_j) / gamma_{j-1}, sub-diagonal alpha gamma / gamma_{j-1};
+  // hc = Hbar c_{j-1} was formed by the previous step's update kernel
   if (j >= 1) {
     const double ig = 1.0 / gprev;
-    for (int r = threadIdx.x; r < j; r += blockDim.x) {
-      double tsum = 0.0;
-      if (nseg > 1)
-        for (int q = 0; q < nseg; ++q) tsum += tp[q * j + r];
-      else
-        tsum = col[r];
-      col[r] = (bprev[r] - tsum + alpha * c[r]) * ig;
-    }
+    // Hbar_{j-1} has columns 0..j-2: none at j = 1
+    for (int r = threadIdx.x; r < j; r += blockDim.x)
+      col[r] = (bprev[r] - (j >= 2 ? hc[r] : 0.0) + alpha * c[r]) * ig;
     if (threadIdx.x == 0) col[j] = alpha * gam * ig;
   }
   __syncthreads();
@@ -1013,12 +981,10 @@ __global__ void __launch_bounds__(1024) gm_dc_coef_kernel(int j, const double* _
 }
 void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
                 double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
-                const double* bnorm, cudaStream_t st) {
-  // column + rotations (3j + 2) and, when j <= 512, nseg * j <= 1024 segment partials
-  const int nseg = (j >= 1) ? std::max(1, std::min(1024 / j, 32)) : 1;
-  const size_t smem = sizeof(double) * (3 * (size_t)j + 2 + (nseg > 1 ? (size_t)nseg * j : 0));
-  gm_dc_coef_kernel<<<1, 1024, smem, st>>>(j, red, dc, bprev, cprev, e, Hraw, H, T, ldh, cs, sn, g, hnext, stat,
-                                           bnorm);
+                const double* bnorm, const double* hc, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (3 * (size_t)j + 2);  // column + rotations
+  gm_dc_coef_kernel<<<1, 256, smem, st>>>(j, red, dc, bprev, cprev, e, Hraw, H, T, ldh, cs, sn, g, hnext, stat,
+                                          bnorm, hc);
   WC4D_LAUNCH_CHECK();
 }
 
@@ -1031,9 +997,20 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
                                                                    const double* __restrict__ dc,
                                                                    const double* __restrict__ w,
                                                                    double* __restrict__ v, int64_t n,
-                                                                   const int* done, int* ran) {
+                                                                   const double* __restrict__ Hraw, int ldh,
+                                                                   double* __restrict__ hc, const int* done,
+                                                                   int* ran) {
   if (done != nullptr && *(volatile const int*)done) return;
   if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  // hc = Hbar_j c_j for the next step's coefficient kernel: raw Hessenberg
+  // columns 0..j-1 (rows 0..j) times c_j, one row per block, spread over the grid
+  for (int r = blockIdx.x; r <= j && j >= 1; r += gridDim.x) {
+    __shared__ double shr[32];
+    double t = 0.0;
+    for (int k = (r > 0 ? r - 1 : 0) + threadIdx.x; k < j; k += blockDim.x) t += Hraw[r + (int64_t)k * ldh] * cv[k];
+    t = block_sum(t, shr);
+    if (threadIdx.x == 0) hc[r] = t;
+  }
   extern __shared__ float cf[];  // e hi/lo [j], c hi/lo [j]
   float* eh = cf;
   float* el = eh + j;
@@ -1119,12 +1096,13 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
   }
 }
 void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
-                  const double* w, double* v, int64_t n, const int* done, cudaStream_t st) {
+                  const double* w, double* v, int64_t n, const double* Hraw, int ldh, double* hc, const int* done,
+                  cudaStream_t st) {
   int* ran = prof_begin(PROF_ORTH, (double)(j + 1) * n * 8.0 + 4.0 * n * 8.0, st);
   const int64_t n4 = (n + 3) / 4;
   const int nb = (int)std::min<int64_t>((n4 + DOT_THREADS - 1) / DOT_THREADS, 152 * 16);
   gm_dc_update_kernel<<<nb, DOT_THREADS, sizeof(float) * 4 * std::max(j, 1), st>>>(Vh, Vl, ldv, j, e, c, dc, w, v, n,
-                                                                                  done, ran);
+                                                                                  Hraw, ldh, hc, done, ran);
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
 }

@@ -87,11 +87,13 @@ void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done,
 enum { DC_GAMMA = 0, DC_ALPHA, DC_IGAMMA, DC_IALPHA, DC_BETA, DC_COUNT };
 void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float* wh, const float* wl, int64_t n,
                double* part, const int* done, cudaStream_t st);
+// hc: Hbar c of the previous step (j rows), written by gm_dc_update
 void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
                 double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
-                const double* bnorm, cudaStream_t st);
+                const double* bnorm, const double* hc, cudaStream_t st);
 void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
-                  const double* w, double* v, int64_t n, const int* done, cudaStream_t st);
+                  const double* w, double* v, int64_t n, const double* Hraw, int ldh, double* hc, const int* done,
+                  cudaStream_t st);
 
 // small vector ops
 template <typename T>

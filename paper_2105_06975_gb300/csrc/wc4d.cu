@@ -117,7 +117,7 @@ struct wc4d_problem {
   // previous b and c, update coefficients, reduced dot rows, operator scratch
   bool dcgs = false;
   double *Hraw = nullptr, *Tm = nullptr, *dcst = nullptr, *bprev = nullptr, *cprev = nullptr, *ecoef = nullptr;
-  double *red = nullptr, *yhat = nullptr;
+  double *red = nullptr, *yhat = nullptr, *hcbuf = nullptr;
   // learned Schur-block correction (shat = LEARNED): weights, inference scratch
   NetShape net_sh;
   float* net_params = nullptr;
@@ -521,7 +521,7 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(o->shat != WC4D_SHAT_LEARNED ||
                  (o->precond == WC4D_PRECOND_PD && o->krylov == WC4D_KRYLOV_GMRES && d->N + 1 <= 64),
              WC4D_ERR_ARG, "the learned Schur block needs precond = PD, krylov = GMRES (flexible) and N + 1 <= 64");
-  WC4D_CHECK(o->shat == WC4D_SHAT_PAPER || (int64_t)d->s * (d->N + 1) <= 8192, WC4D_ERR_ARG,
+  WC4D_CHECK(o->shat != WC4D_SHAT_EXACT || (int64_t)d->s * (d->N + 1) <= 8192, WC4D_ERR_ARG,
              "exact Schur complement limited to s(N+1) <= 8192");
   WC4D_CHECK(o->dhat == WC4D_DHAT_EXACT || o->dhat == WC4D_DHAT_SHIFT, WC4D_ERR_ARG, "bad dhat");
   WC4D_CHECK(o->krylov >= WC4D_KRYLOV_MINRES && o->krylov <= WC4D_KRYLOV_FGMRES, WC4D_ERR_ARG, "bad krylov");
@@ -788,6 +788,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     P->ecoef = P->alloc<double>(o->maxit + 2);
     P->red = P->alloc<double>(2 * (int64_t)o->maxit + 4);
     P->yhat = P->alloc<double>(o->maxit + 1);
+    P->hcbuf = P->alloc<double>(o->maxit + 2);
   }
   P->cs = P->alloc<double>(o->maxit + 1);
   P->sn = P->alloc<double>(o->maxit + 1);
@@ -1035,7 +1036,8 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   }
   while (!converged && status == WC4D_OK) {
     if (pending_update) {  // the step that stopped on a false convergence still owes its update pass
-      gm_dc_update(P->Vh, P->Vl, lb, next - 1, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, nullptr, st);
+      gm_dc_update(P->Vh, P->Vl, lb, next - 1, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, P->Hraw, ldh,
+                   P->hcbuf, nullptr, st);
       pending_update = false;
     }
     const int batch = std::min(P->o.check_every, P->maxit + 1 - next);
@@ -1055,9 +1057,10 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       gm_dc_dot(P->Vh, P->Vl, lb, j, P->wh, P->wl, n, P->part, done, st);
       gm_mdot_reduce(P->part, 2 * (j + 1) + 1, dot_chunks(n, j + 1), P->red, done, st);
       gm_dc_coef(j, P->red, P->dcst, P->bprev, P->cprev, P->ecoef, P->Hraw, P->H, P->Tm, ldh, P->cs, P->sn, P->g,
-                 P->hnext, P->stat, P->bnorm, st);
+                 P->hnext, P->stat, P->bnorm, P->hcbuf, st);
       if (j < P->maxit)
-        gm_dc_update(P->Vh, P->Vl, lb, j, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, done, st);
+        gm_dc_update(P->Vh, P->Vl, lb, j, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, P->Hraw, ldh, P->hcbuf,
+                     done, st);
     }
     fetch_stat(P);
     it = P->h_stat->iters;
