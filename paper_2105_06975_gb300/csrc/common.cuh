@@ -129,6 +129,53 @@ __device__ __forceinline__ void df_mac2(float2& s, float2& c, float2 ah, float2 
   c = __fadd2_rn(c, __fadd2_rn(err, e));
 }
 
+// Double-float arithmetic on (hi, lo) FP32 pairs (Dekker / Knuth error-free
+// transformations): sums and products to ~2^-48 relative without the FP64 pipe.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e += a.y + b.y;
+  float h, l;
+  fast_two_sum(s, e, h, l);
+  return make_float2(h, l);
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+// a double as a normalised pair (FP64 pipe: one conversion, one add, one conversion)
+__device__ __forceinline__ float2 df_from(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+// warp-wide sum of double-float accumulators (s, c) as a pair, valid in every lane
+__device__ __forceinline__ float2 df_warp_sum(float s, float c) {
+  float h, l;
+  two_sum(s, c, h, l);
+  float2 v = make_float2(h, l);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+    v = df_add(v, w);
+  }
+  return v;
+}
+
 // ------------------------------------------------------------ model on device
 // M_t for t = 1..N (maps time t-1 to t).  STENCIL3: same 3-point periodic
 // stencil for all t.  BANDED: bands[(t-1)*s*w + j*w + (o+lo)] = M_t[j][(j+o) mod s].

@@ -498,19 +498,11 @@ template void gm_combine<double, float>(const float*, int64_t, int, const double
                                         cudaStream_t);
 
 // ------------------------------------------------ double-float Arnoldi passes
+// The same error-free multiply-add as the double-float GEMM (df_mac /
+// df_mac2 in common.cuh): product error by FMA, cross terms, TwoSum into (s, c).
 // The same error-free multiply-add as the double-float GEMM: product error by
 // FMA, cross terms, Knuth TwoSum into (s, c).
-__device__ __forceinline__ void dfk_mac(float& s, float& c, float ah, float al, float xh, float xl) {
-  const float p = ah * xh;
-  float e = fmaf(ah, xh, -p);
-  e = fmaf(ah, xl, e);
-  e = fmaf(al, xh, e);
-  const float t = s + p;
-  const float z = t - s;
-  const float err = (s - (t - z)) + (p - z);
-  s = t;
-  c += err + e;
-}
+
 
 // Block dots V^T w over the split basis.  Grid (chunks of 1024 elements,
 // groups of ORTH_G vectors); each thread takes 4 consecutive elements, so every
@@ -539,18 +531,18 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_mdot_df_kernel(const float* __
       if (g < gn) {
         const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
         const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
-        dfk_mac(s[g], c[g], a.x, b.x, xh.x, xl.x);
-        dfk_mac(s[g], c[g], a.y, b.y, xh.y, xl.y);
-        dfk_mac(s[g], c[g], a.z, b.z, xh.z, xl.z);
-        dfk_mac(s[g], c[g], a.w, b.w, xh.w, xl.w);
+        df_mac(s[g], c[g], a.x, b.x, xh.x, xl.x);
+        df_mac(s[g], c[g], a.y, b.y, xh.y, xl.y);
+        df_mac(s[g], c[g], a.z, b.z, xh.z, xl.z);
+        df_mac(s[g], c[g], a.w, b.w, xh.w, xl.w);
       }
     }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g < ORTH_G; ++g) {
-    const double v = warp_sum((double)s[g] + (double)c[g]);
-    if (lane == 0) sh[wid][g] = v;
+    const float2 v = df_warp_sum(s[g], c[g]);
+    if (lane == 0) sh[wid][g] = (double)v.x + (double)v.y;
   }
   __syncthreads();
   if (threadIdx.x < ORTH_G && i0 + threadIdx.x < cnt) {
@@ -602,20 +594,20 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_mupdate_df_kernel(const float*
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const float hh = hsh[i + u], hl = hsl[i + u];
-        dfk_mac(s[0], c[0], hh, hl, a[u].x, b[u].x);
-        dfk_mac(s[1], c[1], hh, hl, a[u].y, b[u].y);
-        dfk_mac(s[2], c[2], hh, hl, a[u].z, b[u].z);
-        dfk_mac(s[3], c[3], hh, hl, a[u].w, b[u].w);
+        df_mac(s[0], c[0], hh, hl, a[u].x, b[u].x);
+        df_mac(s[1], c[1], hh, hl, a[u].y, b[u].y);
+        df_mac(s[2], c[2], hh, hl, a[u].z, b[u].z);
+        df_mac(s[3], c[3], hh, hl, a[u].w, b[u].w);
       }
     }
     for (; i < cnt; ++i) {
       const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)i * ldv)[q];
       const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)i * ldv)[q];
       const float hh = hsh[i], hl = hsl[i];
-      dfk_mac(s[0], c[0], hh, hl, a.x, b.x);
-      dfk_mac(s[1], c[1], hh, hl, a.y, b.y);
-      dfk_mac(s[2], c[2], hh, hl, a.z, b.z);
-      dfk_mac(s[3], c[3], hh, hl, a.w, b.w);
+      df_mac(s[0], c[0], hh, hl, a.x, b.x);
+      df_mac(s[1], c[1], hh, hl, a.y, b.y);
+      df_mac(s[2], c[2], hh, hl, a.z, b.z);
+      df_mac(s[3], c[3], hh, hl, a.w, b.w);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -698,7 +690,7 @@ void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done,
 // where Z holds the computed P^-1 q_j).
 
 // part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w
-__global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* __restrict__ Vh,
+__global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __restrict__ Vh,
                                                                 const float* __restrict__ Vl, int64_t ldv, int j,
                                                                 const float* __restrict__ wh,
                                                                 const float* __restrict__ wl, int64_t n4,
@@ -711,10 +703,11 @@ __global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* 
   const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
   const int gn = min(ORTH_G, cnt - i0);
   const bool first = blockIdx.y == 0;
-  // paired double-float accumulators: lane x sums elements 0, 2 of each float4, lane y elements 1, 3
-  float2 s[2 * ORTH_G + 1], c[2 * ORTH_G + 1];
+  // scalar double-float accumulators (the paired form needs more registers than
+  // three resident CTAs per SM allow, and the kernel is latency-bound)
+  float s[2 * ORTH_G + 1], c[2 * ORTH_G + 1];
 #pragma unroll
-  for (int g = 0; g < 2 * ORTH_G + 1; ++g) s[g] = c[g] = make_float2(0.f, 0.f);
+  for (int g = 0; g < 2 * ORTH_G + 1; ++g) s[g] = c[g] = 0.f;
   const float* uhp = Vh + (int64_t)j * ldv;
   const float* ulp = Vl + (int64_t)j * ldv;
   for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
@@ -722,33 +715,36 @@ __global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* 
     const float4 xl = reinterpret_cast<const float4*>(wl)[q];
     const float4 uh = reinterpret_cast<const float4*>(uhp)[q];
     const float4 ul = reinterpret_cast<const float4*>(ulp)[q];
-    const float2 xh0 = make_float2(xh.x, xh.y), xh1 = make_float2(xh.z, xh.w);
-    const float2 xl0 = make_float2(xl.x, xl.y), xl1 = make_float2(xl.z, xl.w);
-    const float2 uh0 = make_float2(uh.x, uh.y), uh1 = make_float2(uh.z, uh.w);
-    const float2 ul0 = make_float2(ul.x, ul.y), ul1 = make_float2(ul.z, ul.w);
 #pragma unroll
     for (int g = 0; g < ORTH_G; ++g) {
       if (g < gn) {
         const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
         const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
-        const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
-        const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
-        df_mac2(s[g], c[g], a0, b0, xh0, xl0);
-        df_mac2(s[g], c[g], a1, b1, xh1, xl1);
-        df_mac2(s[ORTH_G + g], c[ORTH_G + g], a0, b0, uh0, ul0);
-        df_mac2(s[ORTH_G + g], c[ORTH_G + g], a1, b1, uh1, ul1);
+        df_mac(s[g], c[g], a.x, b.x, xh.x, xl.x);
+        df_mac(s[g], c[g], a.y, b.y, xh.y, xl.y);
+        df_mac(s[g], c[g], a.z, b.z, xh.z, xl.z);
+        df_mac(s[g], c[g], a.w, b.w, xh.w, xl.w);
+        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.x, b.x, uh.x, ul.x);
+        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.y, b.y, uh.y, ul.y);
+        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.z, b.z, uh.z, ul.z);
+        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.w, b.w, uh.w, ul.w);
       }
     }
     if (first) {
-      df_mac2(s[2 * ORTH_G], c[2 * ORTH_G], xh0, xl0, xh0, xl0);
-      df_mac2(s[2 * ORTH_G], c[2 * ORTH_G], xh1, xl1, xh1, xl1);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.x, xl.x, xh.x, xl.x);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.y, xl.y, xh.y, xl.y);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.z, xl.z, xh.z, xl.z);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.w, xl.w, xh.w, xl.w);
     }
   }
+  // warp reduction in double-float on the FP32 pipe (an FP64 shuffle tree per
+  // vector would occupy GB300's 1/64-rate FP64 pipe for a large part of the
+  // kernel); one FP64 conversion per warp and vector
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int g = 0; g < 2 * ORTH_G + 1; ++g) {
-    const double v = warp_sum(((double)s[g].x + (double)c[g].x) + ((double)s[g].y + (double)c[g].y));
-    if (lane == 0) sh[wid][g] = v;
+    const float2 v = df_warp_sum(s[g], c[g]);
+    if (lane == 0) sh[wid][g] = (double)v.x + (double)v.y;
   }
   __syncthreads();
   const int r = threadIdx.x;
@@ -989,8 +985,8 @@ void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cpr
 }
 
 // q_j = (u_j - Q_j c) / gamma into slot j (in place), u_{j+1} = (w - Q_j e' - e_j u_j) / alpha
-// into slot j+1 and into v (double, the next operator input).  Both sums in
-// double-float; 4 elements per thread, 16-byte loads.
+// into slot j+1 and into v (double, the next operator input).  Both sums and
+// the q_j epilogue in double-float; 4 elements per thread, 16-byte loads.
 __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, float* Vl, int64_t ldv, int j,
                                                                    const double* __restrict__ e,
                                                                    const double* __restrict__ cv,
@@ -1025,7 +1021,9 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
     cl[i] = __double2float_rn(cv[i] - (double)y);
   }
   __syncthreads();
-  const double ej = e[j], igam = dc[DC_IGAMMA], ialpha = dc[DC_IALPHA];
+  // scalars as double-float pairs: the per-element epilogue stays on the FP32 pipe
+  const float2 eJ = df_from(e[j]), gI = df_from(dc[DC_IGAMMA]);
+  const double ialpha = dc[DC_IALPHA];
   const int64_t n4 = (n + 3) / 4;
   float* qh = Vh + (int64_t)j * ldv;
   float* ql = Vl + (int64_t)j * ldv;
@@ -1077,17 +1075,25 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int64_t el_ = 4 * q + u;
-      const double uj = (double)uhs[u] + (double)uls[u];
-      const double qv = (uj - ((double)sc_s[u] + (double)cc_s[u])) * igam;
-      double nv = 0.0;
+      const float2 uj = make_float2(uhs[u], uls[u]);
+      float2 scs, ses;
+      two_sum(sc_s[u], cc_s[u], scs.x, scs.y);
+      two_sum(se_s[u], ce_s[u], ses.x, ses.y);
+      const float2 qd = df_mul(df_add(uj, df_neg(scs)), gI);  // (u_j - Q_j c) / gamma
+      float2 nd = make_float2(0.f, 0.f);
       if (el_ < n) {
-        nv = (w[el_] - ((double)se_s[u] + (double)ce_s[u]) - ej * uj) * ialpha;
+        // (w - (Q_j e' + e_j u_j)) / alpha: the projection in double-float, the
+        // subtraction from w in FP64 (it cancels when w is nearly in span Q, and
+        // w's low bits would be lost in a double-float copy of w)
+        const float2 pr = df_add(ses, df_mul(eJ, uj));
+        const double nv = (w[el_] - ((double)pr.x + (double)pr.y)) * ialpha;
         v[el_] = nv;
+        nd = df_from(nv);
       }
-      oqh[u] = __double2float_rn(qv);
-      oql[u] = __double2float_rn(qv - (double)oqh[u]);
-      onh[u] = __double2float_rn(nv);
-      onl[u] = __double2float_rn(nv - (double)onh[u]);
+      oqh[u] = qd.x;
+      oql[u] = qd.y;
+      onh[u] = nd.x;
+      onl[u] = nd.y;
     }
     reinterpret_cast<float4*>(qh)[q] = make_float4(oqh[0], oqh[1], oqh[2], oqh[3]);
     reinterpret_cast<float4*>(ql)[q] = make_float4(oql[0], oql[1], oql[2], oql[3]);

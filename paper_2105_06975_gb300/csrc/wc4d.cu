@@ -1059,8 +1059,8 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       gm_dc_coef(j, P->red, P->dcst, P->bprev, P->cprev, P->ecoef, P->Hraw, P->H, P->Tm, ldh, P->cs, P->sn, P->g,
                  P->hnext, P->stat, P->bnorm, P->hcbuf, st);
       if (j < P->maxit)
-        gm_dc_update(P->Vh, P->Vl, lb, j, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, P->Hraw, ldh, P->hcbuf,
-                     done, st);
+        gm_dc_update(P->Vh, P->Vl, lb, j, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, P->Hraw, ldh,
+                     P->hcbuf, done, st);
     }
     fetch_stat(P);
     it = P->h_stat->iters;
