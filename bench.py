@@ -207,7 +207,14 @@ MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
                       "preconditioned by FP32 {pc}"}
 
 
-def kernel_rows(st, step_ms, hbm):
+# DRAM bytes per launch of gemm_streamk_df32_kernel, ncu dram__bytes_read.sum + dram__bytes_write.sum,
+# mean over the three product launches of one GMRES step (P_I level 1, P_I level 2, A v) at the scale
+# workload; captured on a GB300 (summary and command in profiles/gemm_streamk_df32__advdiff_s2048_N64.md).
+# Valid while that kernel is unchanged; the other kernels report no traffic.
+GEMM_DF32_TRAFFIC_BYTES = 53.3e6
+
+
+def kernel_rows(st, step_ms, hbm, dcgs=False):
     rows = {}
     if st.gemm_launches:
         a = st.gemm_flops / (st.gemm_ms * 1e-3) / 1e12
@@ -239,7 +246,9 @@ def kernel_rows(st, step_ms, hbm):
                              "peak_source": "derived: 152 SM x 256 FP32 flop/clk x 2.07 GHz"}
     if st.orth_launches:
         a = st.orth_bytes / (st.orth_ms * 1e-3) / 1e9
-        rows["orth"] = {"kernel": "gm_mdot/gm_mupdate (Arnoldi CGS2 passes)", "bound": "hbm", "achieved": a,
+        name = ("gm_dc_dot/gm_dc_update (delayed-CGS2 Arnoldi passes)" if dcgs
+                else "gm_mdot/gm_mupdate (Arnoldi CGS2 passes)")
+        rows["orth"] = {"kernel": name, "bound": "hbm", "achieved": a,
                         "peak": hbm, "unit": "GB/s", "frac": (a / hbm) if hbm else None,
                         "launches": st.orth_launches, "ms_per_launch": st.orth_ms / st.orth_launches,
                         "bytes_per_launch": st.orth_bytes / st.orth_launches, "share_of_step": st.orth_ms / step_ms,
@@ -332,7 +341,7 @@ def run_gpu(args):
             ms = float(tt.item())
         assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
         results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
-                         "kernels": kernel_rows(st, step_ms, hbm),
+                         "kernels": kernel_rows(st, step_ms, hbm, dcgs=mode in ("df32", "df32p32")),
                          "setup_ms": statistics.mean(a for a, _ in split),
                          "solve_ms": statistics.mean(b for _, b in split)}
     clocks = clk.stop()
@@ -365,7 +374,22 @@ def run_gpu(args):
     if dom is not None:
         roof = {k: dom[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "peak_source",
                                     "share_of_step")}
-        roof["traffic"] = None
+        roof["traffic"] = GEMM_DF32_TRAFFIC_BYTES if dom["kernel"].startswith("gemm_streamk_df32") else None
+        if roof["traffic"] is not None:
+            roof["traffic_source"] = ("ncu dram bytes read+write per launch, mean of one GMRES step's three "
+                                      "product launches (profiles/gemm_streamk_df32__advdiff_s2048_N64.md)")
+    # whole-solve bound: the FP64-class products at the DF32 peak vs the Arnoldi and operator bytes at HBM
+    st_c = chosen["stats"]
+    solve_roof = None
+    if st_c.gemmdf_launches and hbm:
+        steps_n = max(args.steps, 1)
+        t_alu = st_c.gemmdf_flops / steps_n / (DF32_PEAK_TFLOPS * 1e12) * 1e3
+        t_hbm = (st_c.orth_bytes + st_c.gemmdf_launches * GEMM_DF32_TRAFFIC_BYTES) / steps_n / (hbm * 1e9) * 1e3
+        t_roof = max(t_alu, t_hbm)
+        solve_roof = {"bound": "alu" if t_alu >= t_hbm else "hbm", "t_alu_ms": t_alu, "t_hbm_ms": t_hbm,
+                      "t_roof_ms": t_roof, "ms_per_step": chosen["ms"], "frac": t_roof / chosen["ms"],
+                      "note": "lower bound of one step from the product FLOPs (DF32 peak) and the Arnoldi + "
+                              "operator bytes (measured HBM); setup and small kernels count as time only"}
     line = {
         "metric": METRIC, "value": chosen["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["ms"], "higher_is_better": True, "scaling": "weak",
@@ -380,6 +404,7 @@ def run_gpu(args):
         "fp64_solves_per_s": fp64["value"],
         "chosen_over_fp64": chosen["value"] / fp64["value"],
         "roofline": roof,
+        "roofline_step": solve_roof,
         "kernels": ks,
         "kernels_fp64_mode": fp64["kernels"],
         "gpu_launches": int(chosen["stats"].launches),
