@@ -296,7 +296,9 @@ void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis
               const ModelDev& model, const int* obs, const int* done, cudaStream_t st);
 
 // ---------------------------------------------------------------- kernels
-void launch_soar_fill(double* M, int m, const int* idx, int s, double sigma2, double ell, cudaStream_t st);
+// tab: s doubles of scratch (the correlation by grid distance), stream-ordered
+void launch_soar_fill(double* M, int m, const int* idx, int s, double sigma2, double ell, double* tab,
+                      cudaStream_t st);
 void launch_copy_d(double* dst, const double* src, int64_t n, cudaStream_t st);
 void launch_fill_d(double* dst, double v, int64_t n, cudaStream_t st);
 void launch_add_diag(double* A, int m, int64_t lda, const double* shift_dev, double shift, cudaStream_t st);

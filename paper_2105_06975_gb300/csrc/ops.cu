@@ -44,10 +44,96 @@ __global__ void __launch_bounds__(1024) lhat_sweep_kernel(ModelDev md, int k, co
   }
 }
 
+// The same sweep with each chunk's grid cut into segments of W points, one CTA
+// per (chunk, segment): a CTA starts from the chunk's first level on its
+// segment widened by R (k-1) points on each side (R = the model's reach, 1 for
+// the 3-point stencil, max(lo, hi) for bands; periodic), keeps the running level
+// in shared memory and narrows the valid range by R per step, so no CTA needs
+// another's values.  Every output element is computed with the same operations
+// in the same order as lhat_sweep_kernel.  Needs v and z not to overlap.
+template <typename T>
+__device__ __forceinline__ T local_apply(const ModelDev& md, int t, const T* cur, int e, int x, bool transpose) {
+  const int s = md.s;
+  if (md.kind == WC4D_MODEL_STENCIL3) {
+    return transpose ? T(md.c0) * cur[e + 1] + T(md.c1) * cur[e] + T(md.c2) * cur[e - 1]
+                     : T(md.c0) * cur[e - 1] + T(md.c1) * cur[e] + T(md.c2) * cur[e + 1];
+  }
+  const int w = md.lo + md.hi + 1;
+  T acc = T(0);
+  if (!transpose) {
+    const double* b = md.bands + ((int64_t)(t - 1) * s + x) * w;
+    for (int o = -md.lo; o <= md.hi; ++o) acc += T(b[o + md.lo]) * cur[e + o];
+  } else {
+    const double* b = md.bands + (int64_t)(t - 1) * s * w;
+    for (int o = -md.lo; o <= md.hi; ++o) {
+      const int i = wrap_idx(x - o, s);
+      acc += T(b[(int64_t)i * w + o + md.lo]) * cur[e - o];
+    }
+  }
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lhat_sweep_seg_kernel(ModelDev md, int k, const T* __restrict__ v,
+                                                             T* __restrict__ z, int transpose, int identity_model,
+                                                             int W, int R, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  extern __shared__ unsigned char smraw[];
+  T* bufA = reinterpret_cast<T*>(smraw);
+  const int s = md.s, T1 = md.N + 1;
+  const int t0 = blockIdx.x * k, t1 = min(t0 + k, T1) - 1, steps = t1 - t0;
+  const int x0 = blockIdx.y * W, x1 = min(x0 + W, s);
+  const int H = R * steps, E = (x1 - x0) + 2 * H;
+  T* bufB = bufA + E;
+  auto gx = [&](int e) { return wrap_idx(x0 - H + e, s); };
+  const int ts = transpose ? t1 : t0;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    const T val = v[(int64_t)ts * s + gx(e)];
+    bufA[e] = val;
+    if (e >= H && e < H + (x1 - x0)) z[(int64_t)ts * s + gx(e)] = val;
+  }
+  __syncthreads();
+  T* cur = bufA;
+  T* nxt = bufB;
+  for (int m = 1; m <= steps; ++m) {
+    const int t = transpose ? t1 - m : t0 + m;   // level being formed
+    const int tm = transpose ? t + 1 : t;        // forward uses M_t on z_{t-1}; transpose M_{t+1}^T on z_{t+1}
+    const int lo_e = R * m, hi_e = E - R * m;
+    for (int e = lo_e + threadIdx.x; e < hi_e; e += blockDim.x) {
+      const int x = gx(e);
+      const T mz = identity_model ? cur[e] : local_apply<T>(md, tm, cur, e, x, transpose != 0);
+      const T val = v[(int64_t)t * s + x] + mz;
+      nxt[e] = val;
+      if (e >= H && e < H + (x1 - x0)) z[(int64_t)t * s + x] = val;
+    }
+    __syncthreads();
+    T* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+}
+
 template <typename T>
 void lhat_sweep(const ModelDev& md, int k, const T* v, T* z, bool transpose, bool identity_model, const int* done,
                 cudaStream_t st) {
   const int nchunks = (md.N + 1 + k - 1) / k;
+  const int s = md.s;
+  const int R = identity_model ? 0 : (md.kind == WC4D_MODEL_STENCIL3 ? 1 : std::max(md.lo, md.hi));
+  const int steps = std::min(k, md.N + 1) - 1;
+  // about two CTAs per SM over (chunks x segments); segments of >= 128 points
+  int nseg = std::max(1, (152 * 2) / nchunks);
+  int W = ((s + nseg - 1) / nseg + 31) / 32 * 32;
+  W = std::max(W, 128);
+  nseg = (s + W - 1) / W;
+  const int E = W + 2 * R * steps;
+  const bool alias = (const void*)v == (const void*)z;
+  if (nseg > 1 && !alias && steps > 0 && 2 * R * steps <= W && E <= s &&
+      (size_t)E * 2 * sizeof(T) <= 48 * 1024) {
+    lhat_sweep_seg_kernel<T><<<dim3(nchunks, nseg), 256, (size_t)E * 2 * sizeof(T), st>>>(
+        md, k, v, z, transpose ? 1 : 0, identity_model ? 1 : 0, W, R, done);
+    WC4D_LAUNCH_CHECK();
+    return;
+  }
   const int threads = std::min(1024, ((md.s + 31) / 32) * 32);
   lhat_sweep_kernel<T><<<nchunks, threads, 0, st>>>(md, k, v, z, transpose ? 1 : 0, identity_model ? 1 : 0, done);
   WC4D_LAUNCH_CHECK();

@@ -14,19 +14,29 @@ static inline int nblk(int64_t n, int t = 256) { return (int)std::min<int64_t>((
 // ------------------------------------------------------------------ SOAR
 // c(r) = sigma2 (1 + r/ell) exp(-r/ell), r = chordal distance on the circle of
 // circumference 1 between x_i = idx_i/s and x_j = idx_j/s: sin(pi |dx|)/pi.
-__global__ void soar_fill_kernel(double* M, int m, const int* idx, int s, double sigma2, double ell) {
+// Entries depend only on the grid distance d = |idx_i - idx_j| in [0, s): the
+// s correlations are evaluated once into a table (the exponential and sine
+// run on GB300's 1/64-rate FP64 pipe) and the matrix is filled by lookup.
+__global__ void soar_table_kernel(double* tab, int s, double sigma2, double ell) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < s; d += gridDim.x * blockDim.x) {
+    const double r = sin(M_PI * ((double)d / s)) / M_PI;
+    const double q = r / ell;
+    tab[d] = sigma2 * (1.0 + q) * exp(-q);
+  }
+}
+__global__ void soar_fill_kernel(double* M, int m, const int* idx, const double* __restrict__ tab) {
   const int64_t total = (int64_t)m * m;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % m), j = (int)(e / m);
-    const double xi = (double)(idx ? idx[i] : i) / s;
-    const double xj = (double)(idx ? idx[j] : j) / s;
-    const double r = sin(M_PI * fabs(xi - xj)) / M_PI;
-    const double q = r / ell;
-    M[e] = sigma2 * (1.0 + q) * exp(-q);
+    const int a = idx ? idx[i] : i, b = idx ? idx[j] : j;
+    M[e] = tab[a > b ? a - b : b - a];
   }
 }
-void launch_soar_fill(double* M, int m, const int* idx, int s, double sigma2, double ell, cudaStream_t st) {
-  soar_fill_kernel<<<nblk((int64_t)m * m), 256, 0, st>>>(M, m, idx, s, sigma2, ell);
+void launch_soar_fill(double* M, int m, const int* idx, int s, double sigma2, double ell, double* tab,
+                      cudaStream_t st) {
+  soar_table_kernel<<<nblk(s), 256, 0, st>>>(tab, s, sigma2, ell);
+  WC4D_LAUNCH_CHECK();
+  soar_fill_kernel<<<nblk((int64_t)m * m), 256, 0, st>>>(M, m, idx, tab);
   WC4D_LAUNCH_CHECK();
 }
 

@@ -592,9 +592,10 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     copy_in(f.Q, d->Q, sizeof(double) * (size_t)s * s, d->mem_kind, st);
     copy_in(f.R, d->R, sizeof(double) * (size_t)p * p, d->mem_kind, st);
   } else {
-    launch_soar_fill(f.B, s, nullptr, s, d->soar_b[0], d->soar_b[1], st);
-    launch_soar_fill(f.Q, s, nullptr, s, d->soar_q[0], d->soar_q[1], st);
-    launch_soar_fill(f.R, p, P->d_obs, s, d->soar_r[0], d->soar_r[1], st);
+    double* tab = P->alloc<double>(s);
+    launch_soar_fill(f.B, s, nullptr, s, d->soar_b[0], d->soar_b[1], tab, st);
+    launch_soar_fill(f.Q, s, nullptr, s, d->soar_q[0], d->soar_q[1], tab, st);
+    launch_soar_fill(f.R, p, P->d_obs, s, d->soar_r[0], d->soar_r[1], tab, st);
   }
   launch_check_finite(f.B, (int64_t)s * s, d_flag + 1, st);
   launch_check_finite(f.Q, (int64_t)s * s, d_flag + 1, st);
@@ -766,8 +767,11 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     P->Vl = P->alloc<float>(nvec * P->ldb);
     P->wh = P->alloc<float>(P->ldb);
     P->wl = P->alloc<float>(P->ldb);
-    WC4D_CUDA(cudaMemsetAsync(P->Vh, 0, sizeof(float) * nvec * P->ldb, st));
-    WC4D_CUDA(cudaMemsetAsync(P->Vl, 0, sizeof(float) * nvec * P->ldb, st));
+    if (P->ldb != n) {  // only the padding of each basis vector must read zero
+      const size_t pitch = sizeof(float) * P->ldb, width = sizeof(float) * (P->ldb - n);
+      WC4D_CUDA(cudaMemset2DAsync(P->Vh + n, pitch, 0, width, nvec, st));
+      WC4D_CUDA(cudaMemset2DAsync(P->Vl + n, pitch, 0, width, nvec, st));
+    }
     WC4D_CUDA(cudaMemsetAsync(P->wh, 0, sizeof(float) * P->ldb, st));
     WC4D_CUDA(cudaMemsetAsync(P->wl, 0, sizeof(float) * P->ldb, st));
     P->vcur = P->alloc<double>(n);
