@@ -49,6 +49,19 @@ void note_launch();
 // non-finite input from every check downstream)
 __device__ __forceinline__ double sqrt_clamped(double v) { return v > 0.0 ? sqrt(v) : (v == v ? 0.0 : v); }
 
+// q = e / m, r = e % m for a grid-stride index: 32-bit arithmetic when the
+// whole range fits (a 64-bit division is a long emulated instruction sequence)
+__device__ __forceinline__ void idx_divmod(int64_t e, int m, bool fits32, int& q, int& r) {
+  if (fits32) {
+    const int ee = (int)e;
+    q = ee / m;
+    r = ee - q * m;
+  } else {
+    q = (int)(e / m);
+    r = (int)(e - (int64_t)q * m);
+  }
+}
+
 // ------------------------------------------------------ block reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

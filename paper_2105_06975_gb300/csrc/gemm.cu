@@ -40,6 +40,7 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
   double flops = 0;
   for (int o = 0; o < plan.nops; ++o) {
     const OpShape& sh = shapes[o];
+    WC4D_CHECK((int64_t)sh.m * sh.ncols < ((int64_t)1 << 31), WC4D_ERR_ARG, "GEMM output too large (2^31 entries)");
     plan.shape[o] = sh;
     const int rt = (sh.m + GEMM_BM - 1) / GEMM_BM;
     const int ct = std::max(1, (sh.ncols + GEMM_BN - 1) / GEMM_BN);
@@ -389,18 +390,23 @@ __global__ void __launch_bounds__(256) gemm_streamk_df32_kernel(GemmOpsT<double>
       }
       __syncthreads();
     }
-    double* dst = partial + (int64_t)sg.slot * (GEMM_BM * GEMM_BN);
+    // partial tiles stay double-float pairs (s, c): the FP64 conversion is done
+    // once per output by the reduce kernel, off GB300's 1/64-rate FP64 pipe here
+    float2* dst = reinterpret_cast<float2*>(partial) + (int64_t)sg.slot * (GEMM_BM * GEMM_BN);
     if (ncv == 1) {
-      red[tid] = (double)s[0][0] + (double)c[0][0];
+      float2* red2 = reinterpret_cast<float2*>(red);
+      float h, l;
+      two_sum(s[0][0], c[0][0], h, l);
+      red2[tid] = make_float2(h, l);
       __syncthreads();
-      if (tid < GEMM_BM) dst[tid] = (red[tid] + red[tid + 64]) + (red[tid + 128] + red[tid + 192]);
+      if (tid < GEMM_BM)
+        dst[tid] = df_add(df_add(red2[tid], red2[tid + 64]), df_add(red2[tid + 128], red2[tid + 192]));
       __syncthreads();
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          dst[(ty + 16 * j) * GEMM_BM + tx + 16 * i] = (double)s[i][j] + (double)c[i][j];
+        for (int i = 0; i < 4; ++i) dst[(ty + 16 * j) * GEMM_BM + tx + 16 * i] = make_float2(s[i][j], c[i][j]);
     }
   }
 }
@@ -414,6 +420,7 @@ struct ReduceMeta {
   int ncols[GEMM_MAX_OPS];
   int64_t out_base[GEMM_MAX_OPS];
   int64_t total;
+  int pairs;  // partials are double-float pairs (s, c) written by the DF32 kernel
 };
 
 template <typename T>
@@ -426,15 +433,29 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
        g += (int64_t)gridDim.x * blockDim.x) {
     int o = 0;
     while (o + 1 < meta.nops && g >= meta.out_base[o + 1]) ++o;
-    const int64_t e = g - meta.out_base[o];
+    // 32-bit index arithmetic: one op's outputs m * ncols < 2^31 (checked by the
+    // plan); 64-bit division per element is a long emulated sequence
+    const int e = (int)(g - meta.out_base[o]);
     const int m = meta.m[o];
-    const int r = (int)(e % m), c = (int)(e / m);
+    const int r = e % m, c = e / m;
     const int cw = meta.col_width[o];
     const int tile = meta.tile_base[o] + (r / GEMM_BM) * meta.col_tiles[o] + c / cw;
     const int off = (c % cw) * GEMM_BM + (r % GEMM_BM);
     T acc = T(0);
-    for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q)
-      acc += partial[(int64_t)tile_slots[q] * (GEMM_BM * GEMM_BN) + off];
+    if (sizeof(T) == 8 && meta.pairs) {
+      const float2* pp = reinterpret_cast<const float2*>(partial);
+      float2 a2 = make_float2(0.f, 0.f);
+      for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q) {
+        const float2 v = pp[(int64_t)tile_slots[q] * (GEMM_BM * GEMM_BN) + off];
+        float h, l;
+        two_sum(v.x, v.y, h, l);
+        a2 = df_add(a2, make_float2(h, l));
+      }
+      acc = T((double)a2.x + (double)a2.y);
+    } else {
+      for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q)
+        acc += partial[(int64_t)tile_slots[q] * (GEMM_BM * GEMM_BN) + off];
+    }
     const EpiT<T>& ep = epis.e[o];
     T val;
     switch (ep.mode) {
@@ -501,6 +522,7 @@ void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis
     meta.out_base[o] = o < plan.nops ? plan.out_base[o] : plan.total_out;
   }
   meta.total = plan.total_out;
+  meta.pairs = (sizeof(T) == 8 && ops.df32 != 0) ? 1 : 0;
   const int64_t nb = std::min<int64_t>((plan.total_out + 255) / 256, 152 * 8);
   gemm_reduce_kernel<T><<<(int)nb, 256, 0, st>>>(meta, epis, partial, plan.d_tile_start, plan.d_tile_slots, model,
                                                  obs, done);

@@ -155,7 +155,8 @@ __global__ void saddle_c3_kernel(ModelDev md, const T* __restrict__ v1, const T*
   const int s = md.s, N = md.N;
   const int64_t total = (int64_t)(N + 1) * s;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(e / s), j = (int)(e % s);
+    int t, j;
+    idx_divmod(e, s, total < ((int64_t)1 << 31), t, j);
     T val = v1[e];
     if (t < N) val -= model_apply_T<T>(md, t + 1, v1 + (int64_t)(t + 1) * s, j);
     const int r = inv[j];

@@ -27,7 +27,8 @@ __global__ void soar_table_kernel(double* tab, int s, double sigma2, double ell)
 __global__ void soar_fill_kernel(double* M, int m, const int* idx, const double* __restrict__ tab) {
   const int64_t total = (int64_t)m * m;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
+    int i, j;
+    idx_divmod(e, m, total < ((int64_t)1 << 31), j, i);
     const int a = idx ? idx[i] : i, b = idx ? idx[j] : j;
     M[e] = tab[a > b ? a - b : b - a];
   }
@@ -126,10 +127,12 @@ void launch_split_df(const double* a, float* hi, float* lo, int64_t n, cudaStrea
   if (n > 0) split_df_kernel<<<nblk(n), 256, 0, st>>>(a, hi, lo, n);
   WC4D_LAUNCH_CHECK();
 }
+// 32-bit index arithmetic (m * ncols < 2^31 is checked by the launcher): a
+// 64-bit division per element is a long emulated sequence on the GPU
 __global__ void split_df_block_kernel(const double* a, int64_t ld, int m, int ncols, float* hi, float* lo) {
-  const int64_t total = (int64_t)m * ncols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % m), c = (int)(e / m);
+  const int total = m * ncols;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e % m, c = e / m;
     const double v = a[i + (int64_t)c * ld];
     const float h = __double2float_rn(v);
     hi[e] = h;
@@ -138,6 +141,7 @@ __global__ void split_df_block_kernel(const double* a, int64_t ld, int m, int nc
 }
 void launch_split_df_block(const double* a, int64_t ld, int m, int ncols, float* hi, float* lo, cudaStream_t st) {
   const int64_t n = (int64_t)m * ncols;
+  WC4D_CHECK(n < ((int64_t)1 << 31), WC4D_ERR_ARG, "operand block too large for the split kernel");
   if (n > 0) split_df_block_kernel<<<nblk(n), 256, 0, st>>>(a, ld, m, ncols, hi, lo);
   WC4D_LAUNCH_CHECK();
 }
@@ -312,8 +316,11 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(double* A, int64_t lda
 
 __global__ void zero_upper_kernel(double* A, int m) {
   const int64_t total = (int64_t)m * m;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    if (e % m < e / m) A[e] = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int c, r;
+    idx_divmod(e, m, total < ((int64_t)1 << 31), c, r);
+    if (r < c) A[e] = 0.0;
+  }
 }
 
 void cholesky(double* A, int m, int* info, cudaStream_t st, double* /*scratch*/) {
@@ -410,8 +417,11 @@ __global__ void __launch_bounds__(256) trinv_update_kernel(const double* L, doub
 
 __global__ void identity_kernel(double* W, int m) {
   const int64_t total = (int64_t)m * m;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    W[e] = (e % m == e / m) ? 1.0 : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int c, r;
+    idx_divmod(e, m, total < ((int64_t)1 << 31), c, r);
+    W[e] = (r == c) ? 1.0 : 0.0;
+  }
 }
 
 // W = L^{-1} by blocked forward substitution on the identity (right-looking).
