@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--pairs", type=int, default=50000, help="training pairs of the learned workload")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of the learned workload")
     ap.add_argument("--batch", type=int, default=256, help="windows in the batched workload")
-    ap.add_argument("--batch-maxit", type=int, default=250, help="Krylov cap per batched window")
+    ap.add_argument("--batch-maxit", type=int, default=300, help="Krylov cap per batched window")
     ap.add_argument("--workers", type=int, default=8, help="host workers / CUDA streams of the batched solve")
     return ap.parse_args()
 

@@ -80,6 +80,25 @@ struct OpSet {
 
 using namespace wc4d;
 
+namespace wc4d {
+// The default memory pool of the current device retains freed blocks up to
+// this many bytes (set once per device; process-local, not a GPU setting).
+inline void retain_default_pool() {
+  static std::mutex mu;
+  static bool set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (set[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = 32ull << 30;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  set[dev] = true;
+}
+}  // namespace wc4d
+
 struct wc4d_problem {
   int s = 0, N = 0, p = 0;
   int64_t n = 0, ns = 0, np = 0;
@@ -129,11 +148,15 @@ struct wc4d_problem {
   double* h_scal = nullptr;
   std::vector<void*> allocs;
 
+  // Stream-ordered allocation from the device's default pool, which keeps up to
+  // 32 GB of freed memory for reuse: building a problem again (a new window, or
+  // a benchmark step) then costs no driver allocation of its workspace.
   template <typename T>
   T* alloc(int64_t count) {
     void* p = nullptr;
     if (count <= 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)count);
+    wc4d::retain_default_pool();
+    cudaError_t e = cudaMallocAsync(&p, sizeof(T) * (size_t)count, st);
     if (e != cudaSuccess) throw Error{WC4D_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
     allocs.push_back(p);
     return (T*)p;
@@ -144,7 +167,8 @@ struct wc4d_problem {
     plan_free(plan_pd2);
     plan_free(plan_pi1);
     plan_free(plan_pi2);
-    for (void* p : allocs) cudaFree(p);
+    for (void* p : allocs) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
     if (h_stat) cudaFreeHost(h_stat);
     if (h_scal) cudaFreeHost(h_scal);
   }
