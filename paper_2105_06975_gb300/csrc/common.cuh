@@ -322,6 +322,14 @@ void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t st);
 // hi = fl32(a), lo = fl32(a - hi): a = hi + lo to about 48 bits
 void launch_split_df(const double* a, float* hi, float* lo, int64_t n, cudaStream_t st);
 // the same for an m x ncols block with leading dimension ld, written densely (ld = m)
+struct SplitBlocks {
+  const double* a[4];
+  int64_t ld[4];
+  int m[4];
+  int off[5];  // dense offsets of each block; off[n] = total
+  int n = 0, total = 0;
+};
+void launch_split_df_multi(const SplitBlocks& sb, float* hi, float* lo, cudaStream_t st);
 void launch_split_df_block(const double* a, int64_t ld, int m, int ncols, float* hi, float* lo, cudaStream_t st);
 void launch_inv_map(const int* obs, int p, int* inv, int s, cudaStream_t st);
 void launch_check_obs(const int* obs, int p, int s, int* flag, cudaStream_t st);

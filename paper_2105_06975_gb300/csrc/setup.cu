@@ -145,6 +145,27 @@ void launch_split_df_block(const double* a, int64_t ld, int m, int ncols, float*
   if (n > 0) split_df_block_kernel<<<nblk(n), 256, 0, st>>>(a, ld, m, ncols, hi, lo);
   WC4D_LAUNCH_CHECK();
 }
+// All operand blocks of one product launch split in one kernel: block o is
+// an m_o x ncols_o column-major slice (leading dimension ld_o) written densely
+// from offset off_o of hi / lo.
+__global__ void split_df_multi_kernel(SplitBlocks sb, float* hi, float* lo) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < sb.total; g += gridDim.x * blockDim.x) {
+    int o = 0;
+    while (o + 1 < sb.n && g >= sb.off[o + 1]) ++o;
+    const int e = g - sb.off[o];
+    const int c = e / sb.m[o], i = e - c * sb.m[o];
+    const double v = sb.a[o][i + (int64_t)c * sb.ld[o]];
+    const float h = __double2float_rn(v);
+    hi[g] = h;
+    lo[g] = __double2float_rn(v - (double)h);
+  }
+}
+void launch_split_df_multi(const SplitBlocks& sb, float* hi, float* lo, cudaStream_t st) {
+  WC4D_CHECK(sb.total >= 0 && sb.total < (1 << 30), WC4D_ERR_ARG, "operand blocks too large for the split kernel");
+  if (sb.total > 0) split_df_multi_kernel<<<nblk(sb.total), 256, 0, st>>>(sb, hi, lo);
+  WC4D_LAUNCH_CHECK();
+}
+
 // inverse observation map: inv[j] = r if obs[r] == j, else -1
 __global__ void inv_map_kernel(const int* obs, int p, int* inv, int s) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < p; r += gridDim.x * blockDim.x) inv[obs[r]] = r;

@@ -60,6 +60,7 @@ struct OpSet {
     if (!df32) return;
     ops.df32 = 1;
     int64_t off = 0;
+    SplitBlocks sb{};
     for (int o = 0; o < ops.nops; ++o) {
       GemmOpT<T>& op = ops.op[o];
       const Split sp = split_of(op.At);
@@ -68,10 +69,21 @@ struct OpSet {
       const int64_t cnt = (int64_t)op.m * op.ncols;
       if (cnt <= 0) continue;
       if (off + cnt > xcap) throw Error{WC4D_ERR_ARG, "internal: double-float operand buffer too small"};
-      if constexpr (sizeof(T) == 8) launch_split_df_block(op.X, op.ldx, op.m, op.ncols, xh + off, xl + off, st);
+      if constexpr (sizeof(T) == 8) {
+        sb.a[sb.n] = op.X;
+        sb.ld[sb.n] = op.ldx;
+        sb.m[sb.n] = op.m;
+        sb.off[sb.n] = (int)off;
+        ++sb.n;
+      }
       op.Xh = xh + off;
       op.Xl = xl + off;
       off += cnt;
+    }
+    if constexpr (sizeof(T) == 8) {  // one split launch for all operand blocks
+      sb.off[sb.n] = (int)off;
+      sb.total = (int)off;
+      launch_split_df_multi(sb, xh, xl, st);
     }
   }
 };
