@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
                                                                 int* ran) {
   if (done != nullptr && *(volatile const int*)done) return;
   if (ran != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ran = 1;
-  __shared__ double sh[DOT_THREADS / 32][2 * ORTH_G + 1];
+  __shared__ float2 sh[DOT_THREADS / 32][2 * ORTH_G + 1];
   const int cnt = j + 1;
   const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
   const int gn = min(ORTH_G, cnt - i0);
@@ -744,13 +744,14 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
 #pragma unroll
   for (int g = 0; g < 2 * ORTH_G + 1; ++g) {
     const float2 v = df_warp_sum(s[g], c[g]);
-    if (lane == 0) sh[wid][g] = (double)v.x + (double)v.y;
+    if (lane == 0) sh[wid][g] = v;
   }
   __syncthreads();
-  const int r = threadIdx.x;
+  const int r = threadIdx.x;  // threads 0..2*ORTH_G of warp 0: one FP64 conversion each
   if (r < 2 * ORTH_G + 1) {
-    double v = 0.0;
-    for (int k = 0; k < DOT_THREADS / 32; ++k) v += sh[k][r];
+    float2 a2 = sh[0][r];
+    for (int k = 1; k < DOT_THREADS / 32; ++k) a2 = df_add(a2, sh[k][r]);
+    const double v = (double)a2.x + (double)a2.y;
     int row = -1;
     if (r < ORTH_G) {
       if (r < gn) row = i0 + r;
