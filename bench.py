@@ -61,6 +61,8 @@ def parse():
                          "learned: learned Schur block vs the plain P_D (s=1024 N=32)")
     ap.add_argument("--pairs", type=int, default=50000, help="training pairs of the learned workload")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of the learned workload")
+    ap.add_argument("--loss", default="error", choices=["error", "residual"],
+                    help="learned workload: train on the Schur-solve error or the preconditioned residual")
     ap.add_argument("--batch", type=int, default=256, help="windows in the batched workload")
     ap.add_argument("--batch-maxit", type=int, default=300, help="Krylov cap per batched window")
     ap.add_argument("--workers", type=int, default=8, help="host workers / CUDA streams of the batched solve")
@@ -548,7 +550,7 @@ def run_learned(args):
     rhs = probs["plain_gmres"].synthesize_rhs(dr)
     t0 = time.perf_counter()
     rep = probs["learned_gmres"].precond_train(pairs=args.pairs, hidden=32, batch=64, epochs=args.epochs,
-                                               lr=1e-3, seed=args.seed + 1)
+                                               lr=1e-3, seed=args.seed + 1, loss=args.loss)
     train_s = time.perf_counter() - t0
     out_arms = {}
     for a, G in probs.items():
@@ -574,7 +576,7 @@ def run_learned(args):
             "config": {"workload": f"advection-diffusion window s={w.s} N={w.N} p={w.p} (n={w.n}), SOAR B/Q/R; "
                                    "learned Schur block in GMRES vs plain P_D",
                        "precond": "PD", "lhat": f"L_M({k})", "tol": 1e-6, "pairs": args.pairs,
-                       "epochs": args.epochs, "hidden": 32,
+                       "epochs": args.epochs, "hidden": 32, "loss": args.loss,
                        "step": "one solve with the problem set up and the net trained (outside the timed region)",
                        "l2": "operators (3 x 8 MB B/Q/R plus factors) and the n-vectors exceed L2 only in part"},
             "arms": out_arms, "training": {k_: (round(v, 5) if isinstance(v, float) else v)

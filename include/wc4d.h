@@ -219,9 +219,9 @@ int wc4d_solve_batch(wc4d_problem* const* probs, int32_t count, const double* co
  * dhat = EXACT, krylov = GMRES (the net is nonlinear; the library's GMRES
  * keeps the preconditioned vectors and is therefore flexible), N + 1 <= 64.
  * The plain block (shat = PAPER) is the fallback and the judge: training
- * compares both on held-out pairs and activates the net only if its relative
- * error is smaller; a solve that fails with the net is repeated without it
- * (wc4d_info.precond_fallback). */
+ * compares both on held-out pairs in the metric of the loss and activates the
+ * net only if it is smaller; a solve that fails with the net is repeated
+ * without it (wc4d_info.precond_fallback). */
 typedef struct {
   int32_t pairs;             /* training + validation pairs generated (50000)       */
   int32_t hidden;            /* hidden channels H, <= 64 (32)                       */
@@ -230,11 +230,17 @@ typedef struct {
   double lr;                 /* Adam step size (1e-3)                               */
   double val_frac;           /* held-out fraction (0.05)                            */
   uint64_t seed;             /* draws, initialisation and shuffling                 */
+  int32_t loss;              /* WC4D_LOSS_*: what training minimises and the judge
+                                compares (WC4D_LOSS_ERROR)                          */
 } wc4d_train_opts;
+enum { WC4D_LOSS_ERROR = 0,     /* |z - S^-1 r|^2 / |S^-1 r|^2: the error of the Schur solve */
+       WC4D_LOSS_RESIDUAL = 1   /* |S z - r|^2 / |r|^2: the preconditioned residual, the
+                                   quantity GMRES sees (two S applies per pair and step) */
+};
 typedef struct {
   double loss_first;         /* mean training loss |z - t|^2/|t|^2, first epoch     */
   double loss_last;          /* ... last epoch                                      */
-  double val_err_learned;    /* held-out RMS of |z - t| / |t| with the net          */
+  double val_err_learned;    /* held-out RMS of the loss's relative error, with the net */
   double val_err_plain;      /* ... with the plain S_hat^{-1} (z = y)               */
   int32_t kept;              /* 1 if the net is active (learned error < plain)      */
   int32_t pairs_train;       /* pairs used for training                             */

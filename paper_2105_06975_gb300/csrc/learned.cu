@@ -295,6 +295,16 @@ void net_out_to(const float* yn, const float* f, const double* nrm2, double* z, 
   WC4D_LAUNCH_CHECK();
 }
 
+// d = yn + f - tn (f may be NULL: the plain block) as doubles
+__global__ void resid_kernel(const float* yn, const float* f, const float* tn, double* d, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (double)yn[e] + (f ? (double)f[e] : 0.0) - (double)tn[e];
+}
+void net_resid(const float* yn, const float* f, const float* tn, double* d, int64_t n, cudaStream_t st) {
+  resid_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(yn, f, tn, d, n);
+  WC4D_LAUNCH_CHECK();
+}
+
 __global__ void store_pair_kernel(const double* y, const double* t, const double* nrm2, float* yn, float* tn,
                                   double* tn2_acc, int64_t n) {
   __shared__ double sh[32];

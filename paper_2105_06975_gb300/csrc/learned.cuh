@@ -52,6 +52,8 @@ void normal_fill(double* out, int64_t n, uint64_t seed, uint64_t base, cudaStrea
 // and back: z = |y| (yn + f) as double.
 void net_in_from(const double* y, const double* nrm2, float* yn, int64_t n, cudaStream_t st);
 void net_out_to(const float* yn, const float* f, const double* nrm2, double* z, int64_t n, cudaStream_t st);
+// d = yn + f - tn in double (f NULL: yn - tn)
+void net_resid(const float* yn, const float* f, const float* tn, double* d, int64_t n, cudaStream_t st);
 // Training pair store: yn = y / |y|, tn = t / |y| (float), tn2 = |tn|^2.
 void net_store_pair(const double* y, const double* t, const double* nrm2, float* yn, float* tn, double* tn2_acc,
                     int64_t n, cudaStream_t st);

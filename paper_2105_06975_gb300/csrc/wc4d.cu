@@ -1595,6 +1595,7 @@ void wc4d_default_train_opts(wc4d_train_opts* o) {
   o->lr = 1e-3;
   o->val_frac = 0.05;
   o->seed = 1;
+  o->loss = WC4D_LOSS_ERROR;
 }
 
 int64_t wc4d_net_nparams(int32_t C, int32_t hidden) { return NetShape{C, hidden, 1}.nparams(); }
@@ -1715,7 +1716,8 @@ int wc4d_precond_train(wc4d_problem* P, const wc4d_train_opts* o_in, const char*
                  P->o.dhat == WC4D_DHAT_EXACT,
              WC4D_ERR_ARG, "training needs a problem set up with precond = PD, shat = LEARNED, rhat = dhat = EXACT");
   WC4D_CHECK(o.pairs >= 2 && o.hidden >= 1 && o.hidden <= 64 && o.batch >= 1 && o.batch <= 4096 && o.epochs >= 1 &&
-                 o.lr > 0 && o.val_frac > 0 && o.val_frac < 1,
+                 o.lr > 0 && o.val_frac > 0 && o.val_frac < 1 &&
+                 (o.loss == WC4D_LOSS_ERROR || o.loss == WC4D_LOSS_RESIDUAL),
              WC4D_ERR_ARG, "bad training options");
   cudaStream_t st = P->st;
   const int C = P->N + 1, s = P->s;
@@ -1743,6 +1745,8 @@ int wc4d_precond_train(wc4d_problem* P, const wc4d_train_opts* o_in, const char*
     double* vc = (double*)dalloc(sizeof(double) * n);
     double* nrm2 = (double*)dalloc(sizeof(double));
     double* part = (double*)dalloc(sizeof(double) * DOT_BLOCKS);
+    double* r2 = (double*)dalloc(sizeof(double) * o.pairs);   // |r|^2 per pair
+    double* nu2 = (double*)dalloc(sizeof(double) * o.pairs);  // |y|^2 per pair
     WC4D_CUDA(cudaMemsetAsync(tn2, 0, sizeof(double) * o.pairs, st));
     const int64_t off3 = P->ns + P->np;  // the x block (Schur block) of a saddle vector
     const auto t0 = std::chrono::steady_clock::now();
@@ -1762,15 +1766,53 @@ int wc4d_precond_train(wc4d_problem* P, const wc4d_train_opts* o_in, const char*
       WC4D_CUDA(cudaMemsetAsync(va + off3, 0, sizeof(double) * len, st));
       apply_A<double>(P, P->f64, P->plan_A, va, vc, nullptr);
       // y = S_hat^{-1} r
+      dot_partial<double>(vc + off3, vc + off3, len, part, nullptr, st);
+      dot_finish(part, r2 + i, 0, st);
       WC4D_CUDA(cudaMemsetAsync(va, 0, sizeof(double) * off3, st));
       launch_copy_d(va + off3, vc + off3, len, st);
       apply_P<double>(P, WC4D_PRECOND_PD, P->f64, va, vc, nullptr);
       dot_partial<double>(vc + off3, vc + off3, len, part, nullptr, st);
       dot_finish(part, nrm2, 0, st);
+      WC4D_CUDA(cudaMemcpyAsync(nu2 + i, nrm2, sizeof(double), cudaMemcpyDeviceToDevice, st));
       net_store_pair(vc + off3, vb + off3, nrm2, yn + (int64_t)i * len, tn + (int64_t)i * len, tn2 + i, len, st);
     }
     WC4D_CUDA(cudaStreamSynchronize(st));
     const auto t1 = std::chrono::steady_clock::now();
+    // |S tn|^2 = |r|^2 / |y|^2 per pair (the residual loss's normaliser)
+    std::vector<double> hr2(o.pairs), hnu2(o.pairs), rn2(o.pairs);
+    WC4D_CUDA(cudaMemcpy(hr2.data(), r2, sizeof(double) * o.pairs, cudaMemcpyDeviceToHost));
+    WC4D_CUDA(cudaMemcpy(hnu2.data(), nu2, sizeof(double) * o.pairs, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < o.pairs; ++i) rn2[i] = hr2[i] / std::max(hnu2[i], 1e-300);
+    const bool resid_loss = (o.loss == WC4D_LOSS_RESIDUAL);
+    double* sd = (double*)dalloc(sizeof(double) * len);   // S d
+    double* ssd = (double*)dalloc(sizeof(double) * len);  // S S d
+    double* dd = (double*)dalloc(sizeof(double) * len);   // d
+    double* lossv = (double*)dalloc(sizeof(double) * std::max(2, o.batch));
+    // S x for an x block (time levels x grid): A (0,0,x) = (L x, H x, 0), P_D of
+    // that = (D^-1 L x, R^-1 H x, 0), A again: its x block is S x
+    auto applyS = [&](const double* x, double* out) {
+      WC4D_CUDA(cudaMemsetAsync(va, 0, sizeof(double) * off3, st));
+      launch_copy_d(va + off3, x, len, st);
+      apply_A<double>(P, P->f64, P->plan_A, va, vc, nullptr);
+      WC4D_CUDA(cudaMemsetAsync(vc + off3, 0, sizeof(double) * len, st));
+      apply_P<double>(P, WC4D_PRECOND_PD, P->f64, vc, va, nullptr);
+      WC4D_CUDA(cudaMemsetAsync(va + off3, 0, sizeof(double) * len, st));
+      apply_A<double>(P, P->f64, P->plan_A, va, vc, nullptr);
+      launch_copy_d(out, vc + off3, len, st);
+    };
+    // residual-loss value and gradient of sample b of a batch (yb, fb, tb: its rows):
+    // loss |S d|^2 / rn2, d = yn + f - tn; gradient 2 S S d / (rn2 nb) into gb
+    auto resid_sample = [&](const float* yb, const float* fb, const float* tb, double rn, int nb, float* gb,
+                            double* loss_out) {
+      net_resid(yb, fb, tb, dd, len, st);
+      applyS(dd, sd);
+      dot_partial<double>(sd, sd, len, part, nullptr, st);
+      dot_finish(part, loss_out, 0, st);
+      if (gb) {
+        applyS(sd, ssd);
+        vec_convert<float, double>(ssd, gb, len, 2.0 / (rn * nb), st);
+      }
+    };
     // training buffers
     const int B = o.batch;
     const int Hm = std::max(C, sh.H);
@@ -1810,7 +1852,21 @@ int wc4d_precond_train(wc4d_problem* P, const wc4d_train_opts* o_in, const char*
         net_gather(yn, d_idx, nb, len, xb, st);
         net_gather(tn, d_idx, nb, len, tb, st);
         net_forward(sh, params, nb, xb, acts, outb, st);
-        net_loss_grad(sh, nb, xb, outb, tb, tn2, d_idx, gout, d_loss, st);
+        if (resid_loss) {
+          for (int b = 0; b < nb; ++b)
+            resid_sample(xb + (int64_t)b * len, outb + (int64_t)b * len, tb + (int64_t)b * len, rn2[idx[b]], nb,
+                         gout + (int64_t)b * len, lossv + b);
+          std::vector<double> hl(nb);
+          WC4D_CUDA(cudaMemcpy(hl.data(), lossv, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+          double add = 0;
+          for (int b = 0; b < nb; ++b) add += hl[b] / rn2[idx[b]];
+          double cur = 0;
+          WC4D_CUDA(cudaMemcpy(&cur, d_loss, sizeof(double), cudaMemcpyDeviceToHost));
+          cur += add;
+          WC4D_CUDA(cudaMemcpy(d_loss, &cur, sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+          net_loss_grad(sh, nb, xb, outb, tb, tn2, d_idx, gout, d_loss, st);
+        }
         net_backward(sh, params, nb, xb, acts, gout, grads, sc0, sc1, wpart, wcap, st);
         net_adam(params, grads, am, av, sh.nparams(), (float)o.lr, ++step, st);
         seen += nb;
@@ -1821,10 +1877,26 @@ int wc4d_precond_train(wc4d_problem* P, const wc4d_train_opts* o_in, const char*
       if (ep == 0) loss_first = mean;
       loss_last = mean;
     }
-    // the plain block judges the net on the held-out pairs
-    const double el = net_val_error(P, sh, params, yn, tn, tn2, ntr, o.pairs, B, xb, acts, outb, tb, d_idx, d_loss, true);
-    const double ep_ = net_val_error(P, sh, params, yn, tn, tn2, ntr, o.pairs, B, xb, acts, outb, tb, d_idx, d_loss,
-                                     false);
+    // the plain block judges the net on the held-out pairs, in the loss's metric
+    double el = 0, ep_ = 0;
+    if (!resid_loss) {
+      el = net_val_error(P, sh, params, yn, tn, tn2, ntr, o.pairs, B, xb, acts, outb, tb, d_idx, d_loss, true);
+      ep_ = net_val_error(P, sh, params, yn, tn, tn2, ntr, o.pairs, B, xb, acts, outb, tb, d_idx, d_loss, false);
+    } else {
+      for (int i = ntr; i < o.pairs; ++i) {
+        const float* yi = yn + (int64_t)i * len;
+        const float* ti = tn + (int64_t)i * len;
+        net_forward(sh, params, 1, yi, acts, outb, st);
+        resid_sample(yi, outb, ti, rn2[i], 1, nullptr, lossv);
+        resid_sample(yi, nullptr, ti, rn2[i], 1, nullptr, lossv + 1);
+        double hl[2];
+        WC4D_CUDA(cudaMemcpy(hl, lossv, sizeof(double) * 2, cudaMemcpyDeviceToHost));
+        el += hl[0] / rn2[i];
+        ep_ += hl[1] / rn2[i];
+      }
+      el /= nval;
+      ep_ /= nval;
+    }
     const auto t2 = std::chrono::steady_clock::now();
     std::vector<float> w((size_t)sh.nparams());
     WC4D_CUDA(cudaMemcpy(w.data(), params, sizeof(float) * w.size(), cudaMemcpyDeviceToHost));

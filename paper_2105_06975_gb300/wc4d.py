@@ -106,7 +106,11 @@ class Stats(ctypes.Structure):
 class TrainOpts(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int32), ("hidden", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("epochs", ctypes.c_int32), ("lr", ctypes.c_double), ("val_frac", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("loss", ctypes.c_int32)]
+
+
+WC4D_LOSS_ERROR = 0
+WC4D_LOSS_RESIDUAL = 1
 
 
 class TrainReport(ctypes.Structure):
@@ -493,12 +497,14 @@ class Problem:
         return rhs
 
     def precond_train(self, pairs=50000, hidden=32, batch=64, epochs=4, lr=1e-3, val_frac=0.05, seed=1,
-                      ckpt_path=None):
-        """Train the learned Schur block on the device; returns the TrainReport."""
+                      ckpt_path=None, loss="error"):
+        """Train the learned Schur block on the device; returns the TrainReport.
+        loss: "error" (|z - S^-1 r| / |S^-1 r|) or "residual" (|S z - r| / |r|)."""
         o = TrainOpts()
         load().wc4d_default_train_opts(ctypes.byref(o))
         o.pairs, o.hidden, o.batch, o.epochs = int(pairs), int(hidden), int(batch), int(epochs)
         o.lr, o.val_frac, o.seed = float(lr), float(val_frac), int(seed)
+        o.loss = {"error": WC4D_LOSS_ERROR, "residual": WC4D_LOSS_RESIDUAL}[loss]
         rep = TrainReport()
         path = ckpt_path.encode() if ckpt_path else None
         _check(load().wc4d_precond_train(self.h, ctypes.byref(o), path, ctypes.byref(rep)))

@@ -71,18 +71,21 @@ def learned_case(seed=3):
     return w, dr, prob, rhs
 
 
-def test_training_gain_over_plain_block():
+@pytest.mark.parametrize("loss", ["error", "residual"])
+def test_training_gain_over_plain_block(loss):
     """Pairs from the method, training on the device: the loss falls, and on
-    held-out pairs the learned block approximates S^{-1} r far better than the
-    plain S_hat^{-1} (the plain block judges the net and it is kept).  Inside
+    held-out pairs the learned block beats the plain S_hat^{-1} in the loss's
+    metric (the error of S^{-1} r, or the preconditioned residual |S z - r|)
+    by a wide margin (the plain block judges the net and it is kept).  Inside
     GMRES the learned block still reaches the tolerance (true residual with the
     oracle's operator).  It does not cut GMRES iterations on this workload
-    (measured: 161 with it vs 143 without at k=2), which the solve's info
-    reports; that is the gain it does not give."""
+    (measured at k=2: 161 or 177 with it vs 143 without for the error loss,
+    147 for the residual loss); that is the gain it does not give."""
     w, dr, prob, rhs = learned_case()
     kw = dict(precond="PD", k=2, krylov="gmres", tol=1e-8, maxit=600, precision="df32")
     G = L.Problem.from_workload(w, dr, L.make_opts(shat="learned", **kw))
-    rep = G.precond_train(pairs=3000, hidden=16, batch=32, epochs=6, lr=2e-3, seed=5)
+    pairs, epochs = (3000, 6) if loss == "error" else (1500, 3)
+    rep = G.precond_train(pairs=pairs, hidden=16, batch=32, epochs=epochs, lr=2e-3, seed=5, loss=loss)
     assert rep.loss_last < 0.1 * rep.loss_first, rep.as_dict()
     assert rep.kept == 1 and rep.val_err_learned < 0.2 * rep.val_err_plain, rep.as_dict()
     r = torch.from_numpy(rhs).to(DEV)
