@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="windows in the batched workload")
     ap.add_argument("--batch-maxit", type=int, default=300, help="Krylov cap per batched window")
     ap.add_argument("--workers", type=int, default=8, help="host workers / CUDA streams of the batched solve")
+    ap.add_argument("--check-every", type=int, default=4, help="Krylov steps between convergence polls")
     return ap.parse_args()
 
 
@@ -467,7 +468,7 @@ def run_batch(args):
     if world > 1:
         torch.distributed.init_process_group("nccl")
     opts = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.batch_maxit,
-                          precision="df32")
+                          precision="df32", check_every=args.check_every)
     t0 = time.perf_counter()
     probs, rhs, meta = build_batch(args, wc4d, W, opts)
     torch.cuda.synchronize()
@@ -511,6 +512,7 @@ def run_batch(args):
                                   "advection-diffusion | Lorenz-96 (dt 1e-4), SOAR covariances",
                       "precond": args.precond, "lhat": f"L_M({args.k})", "rhat": args.rhat, "tol": 1e-6,
                       "maxit_per_window": args.batch_maxit, "workers": args.workers,
+                      "check_every": args.check_every,
                       "step": "wc4d_solve_batch over all windows (set up once, outside the timed region)",
                       "l2": "inputs larger than L2 (the windows' operators total tens of GB)"},
            "windows_converged": ok, "windows_per_rank_rank0": len(probs),
