@@ -218,7 +218,7 @@ int wc4d_solve_batch(wc4d_problem* const* probs, int32_t count, const double* co
  * Needs a problem set up with precond = PD, shat = LEARNED, rhat = EXACT,
  * dhat = EXACT, krylov = GMRES (the net is nonlinear; the library's GMRES
  * keeps the preconditioned vectors and is therefore flexible), N + 1 <= 64.
- * The plain block (shat = PAPER) is the fallback and the judge: training
+ * The plain block (shat = PAPER) is the fallback and the yardstick: training
  * compares both on held-out pairs in the metric of the loss and activates the
  * net only if it is smaller; a solve that fails with the net is repeated
  * without it (wc4d_info.precond_fallback). */
@@ -230,8 +230,8 @@ typedef struct {
   double lr;                 /* Adam step size (1e-3)                               */
   double val_frac;           /* held-out fraction (0.05)                            */
   uint64_t seed;             /* draws, initialisation and shuffling                 */
-  int32_t loss;              /* WC4D_LOSS_*: what training minimises and the judge
-                                compares (WC4D_LOSS_ERROR)                          */
+  int32_t loss;              /* WC4D_LOSS_*: what training minimises and the held-out
+                                comparison uses (WC4D_LOSS_ERROR)                   */
 } wc4d_train_opts;
 enum { WC4D_LOSS_ERROR = 0,     /* |z - S^-1 r|^2 / |S^-1 r|^2: the error of the Schur solve */
        WC4D_LOSS_RESIDUAL = 1   /* |S z - r|^2 / |r|^2: the preconditioned residual, the

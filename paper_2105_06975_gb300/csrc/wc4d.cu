@@ -1877,7 +1877,7 @@ int wc4d_precond_train(wc4d_problem* P, const wc4d_train_opts* o_in, const char*
       if (ep == 0) loss_first = mean;
       loss_last = mean;
     }
-    // the plain block judges the net on the held-out pairs, in the loss's metric
+    // the net is kept only if it beats the plain block on the held-out pairs, in the loss's metric
     double el = 0, ep_ = 0;
     if (!resid_loss) {
       el = net_val_error(P, sh, params, yn, tn, tn2, ntr, o.pairs, B, xb, acts, outb, tb, d_idx, d_loss, true);

@@ -76,7 +76,7 @@ def test_training_gain_over_plain_block(loss):
     """Pairs from the method, training on the device: the loss falls, and on
     held-out pairs the learned block beats the plain S_hat^{-1} in the loss's
     metric (the error of S^{-1} r, or the preconditioned residual |S z - r|)
-    by a wide margin (the plain block judges the net and it is kept).  Inside
+    by a wide margin (so the net is kept, not replaced by the plain block).  Inside
     GMRES the learned block still reaches the tolerance (true residual with the
     oracle's operator).  It does not cut GMRES iterations on this workload
     (measured at k=2: 161 or 177 with it vs 143 without for the error loss,
