@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--maxit", type=int, default=1000, help="Krylov iteration cap (workspace size)")
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
-    ap.add_argument("--chosen", default="df32", choices=["fp64", "df32", "df32p32", "mixed"])
+    ap.add_argument("--chosen", default="df32", choices=["fp64", "df32", "df32p32", "mixed", "ozaki"])
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
@@ -201,9 +201,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA: 128/clk/SM (measu
 # FP64-equivalent peak of the FP32 pipe = 2 flop x 152 SM x 128 lanes x 2.07 GHz / 12
 DF32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 12 / 1e12
 MODE_DTYPE = {"fp64": "f64", "df32": "df32 products (2 x f32, ~48-bit) / f64 recurrences",
-              "mixed": "f32 inner / df32-f64 outer"}
+              "mixed": "f32 inner / df32-f64 outer",
+              "ozaki": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / df32 / f64 recurrences"}
 MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
              "df32": "FP64 GMRES; covariance / factor products in double-float on the FP32 pipe",
+             "ozaki": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
+                      "on the tensor cores (tcgen05, TMEM accumulators), one-column products in double-float",
              "mixed": "FGMRES outer (double-float A, FP64 true residual) around FP32 inner GMRES({inner}) "
                       "preconditioned by FP32 {pc}"}
 
@@ -236,6 +239,30 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                              "share_of_step": st.gemmdf_ms / step_ms,
                              "peak_source": "derived: FP32 pipe (152 SM x 128 lanes x 2.07 GHz) / 12 "
                                             "FP32 lane operations per double-float multiply-add"}
+    if st.gemmtc_launches:
+        ms1 = st.gemmtc_ms / st.gemmtc_launches
+        a_hbm = st.gemmtc_bytes / (st.gemmtc_ms * 1e-3) / 1e9
+        a_tc = st.gemmtc_mma_flops / (st.gemmtc_ms * 1e-3) / 1e12
+        bf16 = peaks().get("bf16_tflops")
+        f_hbm = (a_hbm / hbm) if hbm else None
+        f_tc = (a_tc / bf16) if bf16 else None
+        tensor_bound = f_tc is not None and (f_hbm is None or f_tc >= f_hbm)
+        rows["gemm_tc"] = {"kernel": "gemm_tc_kernel (Ozaki digit products on tcgen05; one-column products "
+                                     "in double-float)",
+                           "bound": "tensor" if tensor_bound else "hbm",
+                           "achieved": a_tc if tensor_bound else a_hbm,
+                           "peak": bf16 if tensor_bound else hbm,
+                           "unit": "TFLOP/s" if tensor_bound else "GB/s",
+                           "frac": f_tc if tensor_bound else f_hbm,
+                           "hbm": {"achieved_gbs": a_hbm, "frac": f_hbm},
+                           "tensor": {"achieved_tflops_bf16": a_tc, "frac": f_tc},
+                           "fp64_class_tflops": st.gemmtc_flops / (st.gemmtc_ms * 1e-3) / 1e12,
+                           "launches": st.gemmtc_launches, "ms_per_launch": ms1,
+                           "flops_per_launch": st.gemmtc_flops / st.gemmtc_launches,
+                           "bytes_per_launch": st.gemmtc_bytes / st.gemmtc_launches,
+                           "mma_flops_per_launch": st.gemmtc_mma_flops / st.gemmtc_launches,
+                           "share_of_step": st.gemmtc_ms / step_ms,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) / hbm_gbs (measured)"}
     if st.gemm32_launches:
         a = st.gemm32_flops / (st.gemm32_ms * 1e-3) / 1e12
         rows["gemm_fp32"] = {"kernel": "gemm_streamk_kernel<float> (FP32 inner-solve products)",
@@ -278,6 +305,8 @@ def run_gpu(args):
         "fp64": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit),
         "df32": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
                                precision="df32"),
+        "ozaki": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
+                                precision="ozaki"),
     }
     if args.chosen == "df32p32" or (args.modes and "df32p32" in args.modes.split(",")):
         # FP32 preconditioner: only for covariances with kappa * eps32 << 1 (not this workload's R)
@@ -343,7 +372,7 @@ def run_gpu(args):
             ms = float(tt.item())
         assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
         results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
-                         "kernels": kernel_rows(st, step_ms, hbm, dcgs=mode in ("df32", "df32p32")),
+                         "kernels": kernel_rows(st, step_ms, hbm, dcgs=mode in ("df32", "df32p32", "ozaki")),
                          "setup_ms": statistics.mean(a for a, _ in split),
                          "solve_ms": statistics.mean(b for _, b in split)}
     clocks = clk.stop()

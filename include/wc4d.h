@@ -91,12 +91,21 @@ enum { WC4D_PREC_FP64 = 0,        /* every product in native FP64 (DFMA)        
                                      product errors, TwoSum accumulation: ~48-bit products);
                                      recurrences, dots, factorisations and the true residual
                                      stay FP64 (not in the paper)                               */
-       WC4D_PREC_DF32_P32 = 3 };  /* GMRES only: A and the Arnoldi process as in DF32, the
+       WC4D_PREC_DF32_P32 = 3,    /* GMRES only: A and the Arnoldi process as in DF32, the
                                      preconditioner applied in FP32 (FP32 copies of the
                                      operators and factors).  The DF32 Arnoldi keeps the
                                      computed preconditioned vectors, so GMRES is flexible and
                                      the FP32 rounding of P^-1 costs iterations, not accuracy
                                      (not in the paper)                                         */
+       WC4D_PREC_OZAKI = 4 };     /* as DF32, but every covariance / factor product with two or
+                                     more right-hand sides runs on the tensor cores: operator
+                                     rows and vector columns are cut into 7 balanced base-128
+                                     digits (47 bits below a power-of-two scale per row /
+                                     column), the 28 digit products of significance levels
+                                     0..6 accumulate exactly in FP32 (K-ranges of at most 512)
+                                     and are combined in double-float; one-column products run
+                                     in double-float (Ozaki, Ogita, Oishi and Rump 2012; not in
+                                     the paper)                                                 */
 
 typedef struct {
   int32_t s;                 /* state size per time level, >= 2                         */
@@ -355,6 +364,12 @@ typedef struct {
   int64_t gemm32_launches;
   double gemmdf_ms, gemmdf_flops;   /* double-float (WC4D_PREC_DF32) products */
   int64_t gemmdf_launches;
+  double gemmtc_ms, gemmtc_flops;   /* Ozaki tensor-core (WC4D_PREC_OZAKI) products; flops as above */
+  double gemmtc_bytes;              /* bytes those launches must move: operator digit tiles and GEMV
+                                       operands read once, vector digit tiles once per product,
+                                       partial tiles written                                       */
+  double gemmtc_mma_flops;          /* BF16 tensor-core flops of the digit products issued         */
+  int64_t gemmtc_launches;
 } wc4d_stats;
 void wc4d_set_profiling(int32_t enable);
 void wc4d_reset_stats(void);

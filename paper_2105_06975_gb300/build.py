@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwc4d.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["gemm.cu", "setup.cu", "ops.cu", "krylov.cu", "wc4d.cu", "stats.cu", "noalloc.cu", "l96.cu", "learned.cu"]
+SOURCES = ["gemm.cu", "setup.cu", "ops.cu", "krylov.cu", "wc4d.cu", "stats.cu", "noalloc.cu", "l96.cu", "learned.cu",
+           "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

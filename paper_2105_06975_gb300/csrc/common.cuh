@@ -225,12 +225,21 @@ struct GemmOpT {
   const float* Al = nullptr;
   const float* Xh = nullptr;  // X split the same way (one pass per launch)
   const float* Xl = nullptr;
+  // Ozaki digit form (tensor-core products): the operator's rows and X's
+  // columns as 7 balanced base-128 digits in BF16, pre-tiled for tcgen05, and
+  // one power-of-two scale per row / column (ozaki.cu)
+  const uint16_t* Ad = nullptr;
+  const float* As = nullptr;
+  uint16_t* Xd = nullptr;
+  float* Xs = nullptr;
 };
 template <typename T>
 struct GemmOpsT {
   GemmOpT<T> op[GEMM_MAX_OPS];
   int nops;
   int df32 = 0;  // T = double only: run the products in double-float on the FP32 pipe
+  int tc = 0;    // T = double only: wide tiles by Ozaki digit products on the tensor cores
+  int* err = nullptr;  // tc: device flag set if a wait of the kernel gave up
 };
 using GemmOp = GemmOpT<double>;
 using GemmOps = GemmOpsT<double>;
@@ -272,6 +281,7 @@ struct OpShape {
 // the reduction sums the slots of each output tile in k order.
 struct GemmPlan {
   int nops = 0;
+  int bm = GEMM_BM;  // rows per output tile (and per partial slot): 128 for the tensor-core plan
   OpShape shape[GEMM_MAX_OPS];
   int nctas = 0;
   int nslots = 0;
@@ -286,10 +296,13 @@ struct GemmPlan {
   int64_t total_out = 0;          // sum over ops of m * ncols
   int64_t out_base[GEMM_MAX_OPS];  // prefix of m * ncols
   double flops = 0;               // 2 * useful multiply-adds
+  double tc_bytes = 0;            // tensor-core plan: operator digit tiles and GEMV operands read once,
+                                  // X digit tiles once per op, partial tiles written
+  double tc_mma_flops = 0;        // tensor-core plan: BF16 flops of the issued digit products
 };
 
 // cost model of the schedule: which product kernel the plan will mostly run
-enum { COST_FP64 = 0, COST_DF32 = 1 };
+enum { COST_FP64 = 0, COST_DF32 = 1, COST_TC = 2 };
 void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas, int cost_model = COST_FP64);
 // persistent CTAs for the stream-K GEMM: SMs x resident CTAs per SM
 int gemm_resident_ctas(bool df32);
@@ -297,10 +310,10 @@ int gemm_resident_ctas(bool df32);
 // Opt-in kernel profile: CUDA events around the timed kernel classes on the
 // launching stream; the kernel itself marks whether it did work (launches that
 // exit early on a converged solve do not count).
-enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_GEMM32 = 2, PROF_GEMMDF = 3, PROF_CLASSES = 4 };
+enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_GEMM32 = 2, PROF_GEMMDF = 3, PROF_GEMMTC = 4, PROF_CLASSES = 5 };
 bool prof_enabled();
 // returns a device int* the kernel sets to 1 when it runs (nullptr when off)
-int* prof_begin(int cls, double work, cudaStream_t st);
+int* prof_begin(int cls, double work, cudaStream_t st, double work2 = 0.0, double work3 = 0.0);
 void prof_end(cudaStream_t st);
 void plan_free(GemmPlan& plan);
 

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "model_dev.cuh"
+#include "ozaki.cuh"
 
 namespace wc4d {
 
@@ -31,9 +32,15 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
   plan_free(plan);
   WC4D_CHECK((int)shapes.size() <= GEMM_MAX_OPS, WC4D_ERR_ARG, "too many GEMM ops in one launch");
   plan.nops = (int)shapes.size();
+  // the tensor-core plan: 128-row tiles, segments of at most OZ_KMAX k (exact
+  // FP32 accumulation of the digit products)
+  const bool tc = (cost_model == COST_TC);
+  const int bm = tc ? OZ_BM : GEMM_BM;
+  plan.bm = bm;
   struct Tile {
     int op, row0, col0, kb0, kb1;
     double cost_per_kb;
+    bool gemv;
   };
   std::vector<Tile> tiles;
   int64_t outpos = 0;
@@ -42,7 +49,7 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
     const OpShape& sh = shapes[o];
     WC4D_CHECK((int64_t)sh.m * sh.ncols < ((int64_t)1 << 31), WC4D_ERR_ARG, "GEMM output too large (2^31 entries)");
     plan.shape[o] = sh;
-    const int rt = (sh.m + GEMM_BM - 1) / GEMM_BM;
+    const int rt = (sh.m + bm - 1) / bm;
     const int ct = std::max(1, (sh.ncols + GEMM_BN - 1) / GEMM_BN);
     // full 64-column tiles plus a remainder tile; a one-column remainder (the
     // 65th time level) runs on the GEMV mapping
@@ -55,12 +62,12 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
     if (sh.m <= 0 || sh.ncols <= 0) continue;
     for (int r = 0; r < rt; ++r) {
       for (int c = 0; c < ct; ++c) {
-        const int row0 = r * GEMM_BM;
+        const int row0 = r * bm;
         int klo = 0, khi = sh.kdim;
-        if (sh.tri == TRI_LOWER) khi = std::min(sh.kdim, row0 + GEMM_BM);
+        if (sh.tri == TRI_LOWER) khi = std::min(sh.kdim, row0 + bm);
         if (sh.tri == TRI_UPPER) klo = std::min(sh.kdim, row0);
         const int cols = std::min(cw, sh.ncols - c * cw);
-        const int rows = std::min(GEMM_BM, sh.m - row0);
+        const int rows = std::min(bm, sh.m - row0);
         // SM clocks per k-block.  FP64: 2 DFMA/clk/SM; double-float: 13 FP32
         // instructions per multiply-add at 128 lanes/clk/SM.  A one-column
         // (GEMV) tile is bound by its tile load and barriers; a partial tile
@@ -68,8 +75,11 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
         const double per_col = (cost_model == COST_DF32) ? GEMM_BM * GEMM_BK * 13.0 / 128.0 : 0.5 * GEMM_BM * GEMM_BK;
         const double load = (cost_model == COST_DF32) ? 600.0 : 512.0;
         const int eff_cols = (cols == 1) ? 1 : (cols >= GEMM_BN - 15 ? cols : GEMM_BN);
-        const double cost = (cols == 1) ? per_col + 1500.0 : per_col * eff_cols + load;
-        Tile t{o, row0, c * cw, klo / GEMM_BK, (khi + GEMM_BK - 1) / GEMM_BK, cost};
+        double cost = (cols == 1) ? per_col + 1500.0 : per_col * eff_cols + load;
+        // tensor-core plan, per 16 k: 28 MMAs of 128 x 64 x 16 (~25 ns each on
+        // one SM) against 42 KB of digit tiles; a GEMV k-block reads 16 KB
+        if (tc) cost = (cols == 1) ? 300.0 : 1000.0;
+        Tile t{o, row0, c * cw, klo / GEMM_BK, (khi + GEMM_BK - 1) / GEMM_BK, cost, cols == 1};
         tiles.push_back(t);
         flops += 2.0 * rows * cols * (double)(khi - klo);
       }
@@ -90,30 +100,43 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
   std::vector<int> seg_start(C + 1, 0);
   std::vector<std::vector<int>> tile_slots(tiles.size());
   // walk the linearised (tile, k-block) list; the CTA of an item is fixed by
-  // the midpoint of its cost interval
-  double cum = 0;
-  int cur_cta = -1;
+  // the midpoint of its cost interval.  The tensor-core plan balances its
+  // one-column (double-float GEMV) work and its tensor-core work as two
+  // separate partitions and lists a CTA's GEMV segments first: its epilogue
+  // warps run them while the copy and MMA warps stream the tensor-core tiles.
   std::vector<std::vector<GemmSeg>> per_cta(C);
-  for (int ti = 0; ti < (int)tiles.size(); ++ti) {
-    const Tile& t = tiles[ti];
-    for (int kb = t.kb0; kb < t.kb1; ++kb) {
-      const double mid = cum + 0.5 * t.cost_per_kb;
-      cum += t.cost_per_kb;
-      int cta = (int)std::floor(mid / W * C);
-      cta = std::min(std::max(cta, 0), C - 1);
-      auto& lst = per_cta[cta];
-      const int k0 = kb * GEMM_BK;
-      const int k1 = std::min(shapes[t.op].kdim, (kb + 1) * GEMM_BK);
-      if (!lst.empty() && lst.back().op == t.op && lst.back().row0 == t.row0 && lst.back().col0 == t.col0 &&
-          lst.back().k1 == k0 && cur_cta == cta) {
-        lst.back().k1 = k1;
-      } else {
-        lst.push_back(GemmSeg{t.op, t.row0, t.col0, k0, k1, ti /* tile id, slot assigned below */,
-                              plan.col_width[t.op]});
+  auto assign = [&](int pass) {
+    double Wp = 0;
+    for (auto& t : tiles)
+      if (!tc || (pass == 0) == t.gemv) Wp += t.cost_per_kb * (t.kb1 - t.kb0);
+    if (Wp <= 0) return;
+    double cum = 0;
+    int cur_cta = -1;
+    for (int ti = 0; ti < (int)tiles.size(); ++ti) {
+      const Tile& t = tiles[ti];
+      if (tc && (pass == 0) != t.gemv) continue;
+      for (int kb = t.kb0; kb < t.kb1; ++kb) {
+        const double mid = cum + 0.5 * t.cost_per_kb;
+        cum += t.cost_per_kb;
+        int cta = (int)std::floor(mid / Wp * C);
+        cta = std::min(std::max(cta, 0), C - 1);
+        auto& lst = per_cta[cta];
+        const int k0 = kb * GEMM_BK;
+        const int k1 = std::min(shapes[t.op].kdim, (kb + 1) * GEMM_BK);
+        if (!lst.empty() && lst.back().op == t.op && lst.back().row0 == t.row0 && lst.back().col0 == t.col0 &&
+            lst.back().k1 == k0 && cur_cta == cta && (!tc || k1 - lst.back().k0 <= OZ_KMAX)) {
+          lst.back().k1 = k1;
+        } else {
+          lst.push_back(GemmSeg{t.op, t.row0, t.col0, k0, k1, ti /* tile id, slot assigned below */,
+                                plan.col_width[t.op]});
+        }
+        cur_cta = cta;
       }
-      cur_cta = cta;
     }
-  }
+  };
+  assign(0);
+  if (tc) assign(1);
+  (void)W;
   int slot = 0;
   for (int c = 0; c < C; ++c) {
     seg_start[c] = (int)segs.size();
@@ -126,6 +149,26 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
   }
   seg_start[C] = (int)segs.size();
   plan.nslots = slot;
+  if (tc) {
+    double bytes = 0, mma = 0;
+    for (int o = 0; o < plan.nops; ++o)  // X digits (once per op; the row tiles re-read them from L2)
+      bytes += 2.0 * (double)oz_x_elems(shapes[o].kdim, shapes[o].ncols);
+    for (const GemmSeg& sg : segs) {
+      const OpShape& sh = shapes[sg.op];
+      const int cols = std::min(sg.colw, sh.ncols - sg.col0);
+      const int rows = std::min(bm, sh.m - sg.row0);
+      WC4D_CHECK(sg.k1 - sg.k0 <= OZ_KMAX, WC4D_ERR_ARG, "internal: tensor-core segment longer than 512");
+      const int kbs = (sg.k1 + OZ_BK - 1) / OZ_BK - sg.k0 / OZ_BK;
+      if (cols >= 2) {
+        bytes += (double)kbs * 2.0 * OZ_DIGITS * OZ_A_TILE + 8.0 * rows * cols;
+        mma += (double)kbs * (OZ_DIGITS * (OZ_DIGITS + 1) / 2) * 2.0 * OZ_BM * OZ_BN * OZ_BK;
+      } else {
+        bytes += 8.0 * rows * (double)(sg.k1 - sg.k0) + 8.0 * (sg.k1 - sg.k0) + 8.0 * rows;
+      }
+    }
+    plan.tc_bytes = bytes;
+    plan.tc_mma_flops = mma;
+  }
   // slots of a tile in k order (segments were appended in k order per CTA and
   // CTAs in increasing order, which is also increasing k within a tile)
   std::vector<int> tstart(tiles.size() + 1, 0), tslots;
@@ -421,6 +464,7 @@ struct ReduceMeta {
   int64_t out_base[GEMM_MAX_OPS];
   int64_t total;
   int pairs;  // partials are double-float pairs (s, c) written by the DF32 kernel
+  int bm;     // rows per tile / partial slot
 };
 
 template <typename T>
@@ -439,14 +483,16 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
     const int m = meta.m[o];
     const int r = e % m, c = e / m;
     const int cw = meta.col_width[o];
-    const int tile = meta.tile_base[o] + (r / GEMM_BM) * meta.col_tiles[o] + c / cw;
-    const int off = (c % cw) * GEMM_BM + (r % GEMM_BM);
+    const int bm = meta.bm;
+    const int tile = meta.tile_base[o] + (r / bm) * meta.col_tiles[o] + c / cw;
+    const int off = (c % cw) * bm + (r % bm);
+    const int64_t slot_elems = (int64_t)bm * GEMM_BN;
     T acc = T(0);
     if (sizeof(T) == 8 && meta.pairs) {
       const float2* pp = reinterpret_cast<const float2*>(partial);
       float2 a2 = make_float2(0.f, 0.f);
       for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q) {
-        const float2 v = pp[(int64_t)tile_slots[q] * (GEMM_BM * GEMM_BN) + off];
+        const float2 v = pp[(int64_t)tile_slots[q] * slot_elems + off];
         float h, l;
         two_sum(v.x, v.y, h, l);
         a2 = df_add(a2, make_float2(h, l));
@@ -454,7 +500,7 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
       acc = T((double)a2.x + (double)a2.y);
     } else {
       for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q)
-        acc += partial[(int64_t)tile_slots[q] * (GEMM_BM * GEMM_BN) + off];
+        acc += partial[(int64_t)tile_slots[q] * slot_elems + off];
     }
     const EpiT<T>& ep = epis.e[o];
     T val;
@@ -496,6 +542,12 @@ static void launch_products(const GemmPlan& plan, const GemmOpsT<T>& ops, T* par
 template <>
 void launch_products<double>(const GemmPlan& plan, const GemmOpsT<double>& ops, double* partial, const int* done,
                              cudaStream_t st) {
+  if (ops.tc) {
+    int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, plan.tc_bytes, plan.tc_mma_flops);
+    launch_gemm_tc(ops, plan.d_segs, plan.d_seg_start, plan.nctas, partial, done, ran, ops.err, st);
+    if (ran) prof_end(st);
+    return;
+  }
   const bool df = ops.df32 != 0;
   int* ran = prof_begin(df ? PROF_GEMMDF : PROF_GEMM, plan.flops, st);
   if (df)
@@ -522,7 +574,10 @@ void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis
     meta.out_base[o] = o < plan.nops ? plan.out_base[o] : plan.total_out;
   }
   meta.total = plan.total_out;
-  meta.pairs = (sizeof(T) == 8 && ops.df32 != 0) ? 1 : 0;
+  meta.pairs = (sizeof(T) == 8 && (ops.df32 != 0 || ops.tc != 0)) ? 1 : 0;
+  meta.bm = plan.bm;
+  WC4D_CHECK(plan.bm == GEMM_BM || (sizeof(T) == 8 && ops.tc), WC4D_ERR_ARG,
+             "internal: tensor-core plan run without the tensor-core operands");
   const int64_t nb = std::min<int64_t>((plan.total_out + 255) / 256, 152 * 8);
   gemm_reduce_kernel<T><<<(int)nb, 256, 0, st>>>(meta, epis, partial, plan.d_tile_start, plan.d_tile_slots, model,
                                                  obs, done);

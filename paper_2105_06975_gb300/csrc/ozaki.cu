@@ -1,0 +1,522 @@
+// Ozaki-scheme covariance products on the tensor cores (tcgen05, sm_100+).
+//
+// A product y = op(At) X in the TN form of the stream-K GEMM (k contiguous in
+// both operands) is evaluated as a sum of exact BF16 digit products.  Every
+// row i of op(At) and every column c of X is cut below a power-of-two scale
+// (2^E above the row / column maximum, E from the largest exponent) into an
+// integer F < 2^47 (47 bits), written as seven balanced base-128 digits:
+//   a_ik = sigma_i sum_t D_t 2^(-5-7t),   x_kc = tau_c sum_u E_u 2^(-5-7u),
+// t, u = 0..6 (t = 0 most significant), |D|, |E| <= 64, each exact in BF16.
+// (F + 64 sum_j 128^j < 2^49 keeps the balanced digits within seven 7-bit
+// fields; with 48 bits a magnitude within 0.8 % of the scale would carry out.)
+// The digit products of significance level l = t + u <= 6 (28 of the 49) are
+// accumulated in FP32 in tensor memory, one accumulator per level.  A level
+// has at most 7 digit pairs, a segment at most 512 k and |D E| <= 2^12, so
+// every partial sum is an integer below 2^24 and the accumulation is exact.
+// The epilogue combines the seven levels in double-float and scales by
+// sigma_i tau_c 2^-10.  The truncation of each operand (2^-47 of its row or
+// column maximum) and the dropped levels 7..12 bound the error of an output by
+// about 2^-44 K max_k|a_ik| max_k|x_kc|.  (Error-free splitting of a matrix
+// product into products that a lower precision evaluates exactly: Ozaki,
+// Ogita, Oishi and Rump, Numer. Algorithms 59, 2012.)
+//
+// Layout of a digit tile (what one bulk copy moves into shared memory): for a
+// block of 16 k, the 7 digit matrices of 128 rows (operator) or 64 columns (X)
+// follow each other; each is K-major in 8 x 8 core matrices (8 rows of 16
+// bytes), the two k-halves of an 8-row group adjacent (128 bytes apart), the
+// 8-row groups 256 bytes apart -- the no-swizzle canonical layout of a
+// tcgen05 shared-memory operand.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "ozaki.cuh"
+
+namespace wc4d {
+
+namespace {
+
+constexpr uint64_t OZ_BIAS = 64ull * (1ull + (1ull << 7) + (1ull << 14) + (1ull << 21) + (1ull << 28) +
+                                      (1ull << 35) + (1ull << 42));
+
+__device__ __forceinline__ uint64_t mag_bits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// the seven balanced digits of x below 2^(emax - 1022), emax the largest
+// biased exponent of its row / column (integer operations only)
+__device__ __forceinline__ void digits7(double x, int emax, int d[OZ_DIGITS]) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  uint64_t F = 0;  // floor(|x| 2^(47 - E)) < 2^47
+  if (e != 0 && e != 0x7FF) {
+    const int sh = 6 + emax - e;
+    if (sh < 64) F = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> sh;
+  }
+  const uint64_t G = F + OZ_BIAS;  // base-128 digits of G minus 64 are the balanced digits of F
+  const bool neg = (b >> 63) != 0;
+#pragma unroll
+  for (int t = 0; t < OZ_DIGITS; ++t) {
+    const int v = (int)((G >> (7 * (OZ_DIGITS - 1 - t))) & 127) - 64;
+    d[t] = neg ? -v : v;
+  }
+}
+
+// 2^(emax - 1022) as a float; NaN marks a row / column with a non-finite entry
+__device__ __forceinline__ float scale_of(int emax) {
+  if (emax == 0x7FF) return __int_as_float(0x7FC00000);
+  const int E = emax - 1022;
+  if (E < -126) return 0.f;
+  if (E > 127) return __int_as_float(0x7F800000);
+  return __int_as_float((E + 127) << 23);
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
+  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn((float)lo));
+  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn((float)hi));
+  return a | (b << 16);
+}
+
+__device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[warp] = v;
+  __syncthreads();
+  uint64_t m = 0;
+  for (int w = 0; w < nw; ++w) m = red[w] > m ? red[w] : m;
+  __syncthreads();
+  return m;
+}
+
+// Digits of one row (operator) or column (X) of length kdim, padded to nkb
+// blocks of 16, into tile rt/ct at position r of its 128 (64) rows.
+// src == nullptr or a padding row writes zero digits.
+__device__ __forceinline__ void write_digits(const double* src, int kdim, int nkb, int emax, uint16_t* tiles,
+                                             int64_t tile_elems, int rows, int r) {
+  for (int g = threadIdx.x; g < 2 * nkb; g += blockDim.x) {
+    const int k0 = 8 * g, kb = k0 >> 4, kh = (k0 >> 3) & 1;
+    int dg[8][OZ_DIGITS];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + q;
+      const double a = (src != nullptr && k < kdim) ? src[k] : 0.0;
+      digits7(a, emax, dg[q]);
+    }
+    uint16_t* base = tiles + (int64_t)kb * OZ_DIGITS * tile_elems + (r >> 3) * 128 + kh * 64 + (r & 7) * 8;
+#pragma unroll
+    for (int t = 0; t < OZ_DIGITS; ++t) {
+      uint4 v;
+      v.x = bf16_pair(dg[0][t], dg[1][t]);
+      v.y = bf16_pair(dg[2][t], dg[3][t]);
+      v.z = bf16_pair(dg[4][t], dg[5][t]);
+      v.w = bf16_pair(dg[6][t], dg[7][t]);
+      *reinterpret_cast<uint4*>(base + t * tile_elems) = v;
+    }
+  }
+  (void)rows;
+}
+
+// one CTA per padded row i of op(At)
+__global__ void __launch_bounds__(128) oz_rows_kernel(const double* __restrict__ At, int64_t lda, int m, int kdim,
+                                                      int nkb, uint16_t* __restrict__ Ad, float* __restrict__ As) {
+  __shared__ uint64_t red[4];
+  const int i = blockIdx.x;
+  const double* row = (i < m) ? At + (int64_t)i * lda : nullptr;
+  uint64_t mx = 0;
+  if (row)
+    for (int k = threadIdx.x; k < kdim; k += blockDim.x) {
+      const uint64_t v = mag_bits(row[k]);
+      mx = v > mx ? v : mx;
+    }
+  mx = block_max_u64(mx, red);
+  const int emax = (int)(mx >> 52);
+  if (threadIdx.x == 0) As[i] = row ? scale_of(emax) : 0.f;
+  const int rt = i / OZ_BM, r = i % OZ_BM;
+  write_digits(row, kdim, nkb, emax, Ad + (int64_t)rt * nkb * OZ_DIGITS * OZ_A_TILE, OZ_A_TILE, OZ_BM, r);
+}
+
+// one CTA per (op, wide column tile, column of the tile)
+__global__ void __launch_bounds__(128) oz_cols_kernel(OzColJobs jobs) {
+  __shared__ uint64_t red[4];
+  int o = 0;
+  while (o + 1 < jobs.n && (int)blockIdx.x >= jobs.cta_base[o + 1]) ++o;
+  const OzColJob& jb = jobs.j[o];
+  const int local = (int)blockIdx.x - jobs.cta_base[o];
+  const int ct = local / OZ_BN, cl = local % OZ_BN;
+  const int c = ct * OZ_BN + cl;
+  const double* col = (c < jb.ncols) ? jb.X + (int64_t)c * jb.ldx : nullptr;
+  uint64_t mx = 0;
+  if (col)
+    for (int k = threadIdx.x; k < jb.kdim; k += blockDim.x) {
+      const uint64_t v = mag_bits(col[k]);
+      mx = v > mx ? v : mx;
+    }
+  mx = block_max_u64(mx, red);
+  const int emax = (int)(mx >> 52);
+  if (threadIdx.x == 0) jb.Xs[c] = col ? scale_of(emax) : 0.f;
+  write_digits(col, jb.kdim, jb.nkb, emax, jb.Xd + (int64_t)ct * jb.nkb * OZ_DIGITS * OZ_X_TILE, OZ_X_TILE, OZ_BN,
+               cl);
+}
+
+// ----------------------------------------------------------- tcgen05 kernel
+constexpr int OZ_STAGES = 4;
+constexpr uint32_t OZ_A_BYTES = OZ_DIGITS * OZ_A_TILE * 2;  // 28672
+constexpr uint32_t OZ_X_BYTES = OZ_DIGITS * OZ_X_TILE * 2;  // 14336
+constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_X_BYTES;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES;  // 172032
+constexpr int OZ_THREADS = 192;                      // warps 0-3 epilogue, 4 copies, 5 MMA
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, N = 64, M = 128
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(OZ_BM >> 4) << 24);
+constexpr unsigned long long OZ_WAIT_NS = 1000000000ull;  // a wait gives up after 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// no-swizzle shared-memory matrix descriptor: start, leading (next core matrix
+// along k) and stride (next 8-row group) byte offsets, descriptor version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity; false after the time limit
+// or once another role has given up
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if ((it & 63) == 0 && (*abort_flag || now_ns() - t0 > OZ_WAIT_NS)) return false;
+  }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void give_up(volatile int* abort_flag, int* err, int code) {
+  *abort_flag = 1;
+  if (err) atomicCAS(err, 0, code);
+}
+
+// double-float GEMV segment (one output column): warp w takes rows w, w+4, ...,
+// two rows per pass (rows r and r + 4) so that 64 loads per lane are in
+// flight; lanes stride k, the X values of the segment stay in registers
+__device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float2* __restrict__ dst) {
+  constexpr int Q = OZ_KMAX / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float xh[Q], xl[Q];
+  const double* xc = op.X + (int64_t)sg.col0 * op.ldx;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int k = sg.k0 + lane + 32 * q;
+    const double x = (k < sg.k1) ? xc[k] : 0.0;
+    xh[q] = __double2float_rn(x);
+    xl[q] = __double2float_rn(x - (double)xh[q]);
+  }
+  for (int r = warp; r < OZ_BM; r += 8) {
+    const int row0 = sg.row0 + r;
+    if (row0 >= op.m) break;
+    const bool has1 = row0 + 4 < op.m;  // r = warp + 8j <= 123, so row r + 4 is in the tile
+    const int row1 = has1 ? row0 + 4 : row0;
+    const float* ah0 = op.Ah + (int64_t)row0 * op.lda;
+    const float* al0 = op.Al + (int64_t)row0 * op.lda;
+    const float* ah1 = op.Ah + (int64_t)row1 * op.lda;
+    const float* al1 = op.Al + (int64_t)row1 * op.lda;
+    float a0h[Q], a0l[Q], a1h[Q], a1l[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k = sg.k0 + lane + 32 * q;
+      const bool in = k < sg.k1;
+      a0h[q] = in ? ah0[k] : 0.f;
+      a0l[q] = in ? al0[k] : 0.f;
+      a1h[q] = in ? ah1[k] : 0.f;
+      a1l[q] = in ? al1[k] : 0.f;
+    }
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      df_mac(s0, c0, a0h[q], a0l[q], xh[q], xl[q]);
+      df_mac(s1, c1, a1h[q], a1l[q], xh[q], xl[q]);
+    }
+    const float2 v0 = df_warp_sum(s0, c0);
+    const float2 v1 = df_warp_sum(s1, c1);
+    if (lane == 0) {
+      dst[r] = v0;
+      if (has1) dst[r + 4] = v1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    gemm_tc_kernel(GemmOpsT<double> ops, const GemmSeg* __restrict__ segs, const int* __restrict__ seg_start,
+                   float2* __restrict__ partial, const int* __restrict__ done, int* ran, int* err) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  extern __shared__ __align__(1024) unsigned char oz_smem[];
+  __shared__ __align__(8) uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar, tfree_bar, fin_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sbeg = seg_start[blockIdx.x], send = seg_start[blockIdx.x + 1];
+  if (tid == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&tfull_bar, 1);
+    mbar_init(&tfree_bar, 128);
+    mbar_init(&fin_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    // 7 level accumulators of 64 columns: 448 of the 512 columns (one CTA per SM)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t sbase = smem_u32(oz_smem);
+
+  if (warp == 4) {
+    // ---- bulk-copy producer: one stage = the 7 operator and 7 X digit tiles of 16 k
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int si = sbeg; si < send && ok; ++si) {
+        const GemmSeg sg = segs[si];
+        const GemmOpT<double>& op = ops.op[sg.op];
+        if (min(sg.colw, op.ncols - sg.col0) < 2) continue;
+        const int nkb = (op.kdim + OZ_BK - 1) / OZ_BK;
+        const uint16_t* asrc = op.Ad + (int64_t)(sg.row0 / OZ_BM) * nkb * OZ_DIGITS * OZ_A_TILE;
+        const uint16_t* xsrc = op.Xd + (int64_t)(sg.col0 / OZ_BN) * nkb * OZ_DIGITS * OZ_X_TILE;
+        for (int kb = sg.k0 / OZ_BK; kb < (sg.k1 + OZ_BK - 1) / OZ_BK; ++kb, ++it) {
+          const int s = it % OZ_STAGES;
+          if (it >= OZ_STAGES && !mbar_wait(&empty_bar[s], ((it / OZ_STAGES) - 1) & 1, &abort_flag)) {
+            give_up(&abort_flag, err, 1);
+            ok = false;
+            break;
+          }
+          const uint32_t dA = sbase + s * OZ_STAGE_BYTES, dX = dA + OZ_A_BYTES;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full_bar[s])),
+                       "r"(OZ_STAGE_BYTES)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dA),
+              "l"(asrc + (int64_t)kb * OZ_DIGITS * OZ_A_TILE), "r"(OZ_A_BYTES), "r"(smem_u32(&full_bar[s]))
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dX),
+              "l"(xsrc + (int64_t)kb * OZ_DIGITS * OZ_X_TILE), "r"(OZ_X_BYTES), "r"(smem_u32(&full_bar[s]))
+              : "memory");
+        }
+      }
+      // no copy may still be landing when the CTA exits: wait for the last fill
+      // of every stage (already complete unless a wait above gave up)
+      for (int f = max(0, it - OZ_STAGES); f < it; ++f) {
+        uint64_t* b = &full_bar[f % OZ_STAGES];
+        const unsigned long long t0 = now_ns();
+        while (!mbar_test(b, (f / OZ_STAGES) & 1) && now_ns() - t0 < OZ_WAIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer: 28 digit products per 16 k into the 7 level accumulators
+    if (lane == 0) {
+      int it = 0, nseg = 0;
+      bool ok = true;
+      for (int si = sbeg; si < send && ok; ++si) {
+        const GemmSeg sg = segs[si];
+        const GemmOpT<double>& op = ops.op[sg.op];
+        if (min(sg.colw, op.ncols - sg.col0) < 2) continue;
+        if (nseg > 0 && !mbar_wait(&tfree_bar, (nseg - 1) & 1, &abort_flag)) {
+          give_up(&abort_flag, err, 2);
+          break;
+        }
+        tc_fence_after();
+        const int kb0 = sg.k0 / OZ_BK;
+        for (int kb = kb0; kb < (sg.k1 + OZ_BK - 1) / OZ_BK; ++kb, ++it) {
+          const int s = it % OZ_STAGES;
+          if (!mbar_wait(&full_bar[s], (it / OZ_STAGES) & 1, &abort_flag)) {
+            give_up(&abort_flag, err, 3);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aA = sbase + s * OZ_STAGE_BYTES, aX = aA + OZ_A_BYTES;
+#pragma unroll
+          for (int t = 0; t < OZ_DIGITS; ++t) {
+#pragma unroll
+            for (int u = 0; u + t < OZ_DIGITS; ++u) {
+              const uint64_t da = sdesc(aA + t * (OZ_A_TILE * 2));
+              const uint64_t db = sdesc(aX + u * (OZ_X_TILE * 2));
+              const uint32_t acc = (kb > kb0 || t > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tbase + (uint32_t)((t + u) * OZ_BN)),
+                  "l"(da), "l"(db), "r"(OZ_IDESC), "r"(acc));
+            }
+          }
+          tc_commit(&empty_bar[s]);  // the stage is free once these products have read it
+        }
+        if (!ok) break;
+        tc_commit(&tfull_bar);
+        ++nseg;
+      }
+      // every product issued by this thread has completed before TMEM is freed
+      tc_commit(&fin_bar);
+      const unsigned long long t0 = now_ns();
+      while (!mbar_test(&fin_bar, 0) && now_ns() - t0 < OZ_WAIT_NS) {
+      }
+    }
+  } else {
+    // ---- epilogue warps 0-3: TMEM lanes 32w..32w+31 are rows of the tile
+    int nseg = 0;
+    for (int si = sbeg; si < send; ++si) {
+      const GemmSeg sg = segs[si];
+      const GemmOpT<double>& op = ops.op[sg.op];
+      const int ncv = min(sg.colw, op.ncols - sg.col0);
+      float2* dst = partial + (int64_t)sg.slot * (OZ_BM * GEMM_BN);
+      if (ncv < 2) {
+        gemv_segment(op, sg, dst);
+        continue;
+      }
+      if (!mbar_wait(&tfull_bar, nseg & 1, &abort_flag)) {
+        give_up(&abort_flag, err, 4);
+        break;
+      }
+      __syncwarp();
+      tc_fence_after();
+      const int r = 32 * warp + lane, row = sg.row0 + r;
+      const bool rin = row < op.m;
+      const float sig = rin ? op.As[row] : 0.f;
+#pragma unroll 1
+      for (int cc = 0; cc < OZ_BN / 16; ++cc) {
+        uint32_t v[OZ_DIGITS][16];
+#pragma unroll
+        for (int l = 0; l < OZ_DIGITS; ++l) {
+          const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(l * OZ_BN + cc * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]), "=r"(v[l][5]),
+                "=r"(v[l][6]), "=r"(v[l][7]), "=r"(v[l][8]), "=r"(v[l][9]), "=r"(v[l][10]), "=r"(v[l][11]),
+                "=r"(v[l][12]), "=r"(v[l][13]), "=r"(v[l][14]), "=r"(v[l][15])
+              : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = cc * 16 + j;
+          // sum_l acc_l 2^(-7l) in double-float, smallest level first (each term exact)
+          float h = __uint_as_float(v[OZ_DIGITS - 1][j]) * 0x1p-42f, lo = 0.f;
+#pragma unroll
+          for (int l = OZ_DIGITS - 2; l >= 0; --l) {
+            const float tl = __uint_as_float(v[l][j]) * __int_as_float((127 - 7 * l) << 23);
+            float s, e;
+            two_sum(tl, h, s, e);
+            h = s;
+            lo += e;
+          }
+          float hh, ll;
+          fast_two_sum(h, lo, hh, ll);
+          if (rin && c < ncv) {
+            const float f = sig * op.Xs[sg.col0 + c] * 0x1p-10f;
+            dst[c * OZ_BM + r] = make_float2(hh * f, ll * f);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tfree_bar);
+      ++nseg;
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+}
+
+}  // namespace
+
+int oz_wide_tiles(int ncols) {
+  if (ncols < 2) return 0;
+  const int full = ncols / OZ_BN, rem = ncols % OZ_BN;
+  return full + (rem >= 2 ? 1 : 0);
+}
+
+int64_t oz_operator_elems(int m, int kdim) {
+  const int64_t rt = (m + OZ_BM - 1) / OZ_BM, nkb = (kdim + OZ_BK - 1) / OZ_BK;
+  return rt * nkb * OZ_DIGITS * OZ_A_TILE;
+}
+
+int64_t oz_x_elems(int kdim, int ncols) {
+  const int64_t nkb = (kdim + OZ_BK - 1) / OZ_BK;
+  return (int64_t)oz_wide_tiles(ncols) * nkb * OZ_DIGITS * OZ_X_TILE;
+}
+
+void launch_oz_rows(const double* At, int64_t lda, int m, int kdim, uint16_t* Ad, float* As, cudaStream_t st) {
+  const int rt = (m + OZ_BM - 1) / OZ_BM, nkb = (kdim + OZ_BK - 1) / OZ_BK;
+  if (rt == 0 || nkb == 0) return;
+  oz_rows_kernel<<<rt * OZ_BM, 128, 0, st>>>(At, lda, m, kdim, nkb, Ad, As);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_oz_cols(const OzColJobs& jobs, cudaStream_t st) {
+  const int ctas = jobs.cta_base[jobs.n];
+  if (jobs.n == 0 || ctas == 0) return;
+  oz_cols_kernel<<<ctas, 128, 0, st>>>(jobs);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int* seg_start, int nctas,
+                    double* partial, const int* done, int* ran, int* err, cudaStream_t st) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    WC4D_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+  });
+  gemm_tc_kernel<<<nctas, OZ_THREADS, OZ_SMEM, st>>>(ops, segs, seg_start, reinterpret_cast<float2*>(partial), done,
+                                                     ran, err);
+  WC4D_LAUNCH_CHECK();
+}
+
+int oz_resident_ctas() {
+  static int cached = 0;
+  if (cached) return cached;
+  int dev = 0, sms = 0;
+  WC4D_CUDA(cudaGetDevice(&dev));
+  WC4D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cached = std::max(1, sms);
+  return cached;
+}
+
+}  // namespace wc4d

@@ -1,0 +1,48 @@
+// Ozaki-scheme products on the tensor cores: digit forms and the tcgen05
+// stream-K kernel (ozaki.cu).
+#pragma once
+#include "common.cuh"
+
+namespace wc4d {
+
+constexpr int OZ_DIGITS = 7;                 // balanced base-128 digits per operand (47 bits)
+constexpr int OZ_BM = 128;                   // operator rows per tile (MMA M, TMEM lanes)
+constexpr int OZ_BN = 64;                    // X columns per tile (MMA N)
+constexpr int OZ_BK = 16;                    // k per MMA and per digit tile
+constexpr int OZ_KMAX = 512;                 // longest k-range accumulated exactly in FP32
+constexpr int OZ_A_TILE = OZ_BM * OZ_BK;     // elements of one operator digit tile
+constexpr int OZ_X_TILE = OZ_BN * OZ_BK;     // elements of one X digit tile
+
+// Digit form of the X operand of one op of a launch.
+struct OzColJob {
+  const double* X;
+  int64_t ldx;
+  int kdim, ncols, nkb;
+  uint16_t* Xd;  // oz_x_elems(kdim, ncols) BF16 digits
+  float* Xs;     // oz_wide_tiles(ncols) * OZ_BN scales
+};
+struct OzColJobs {
+  OzColJob j[GEMM_MAX_OPS];
+  int cta_base[GEMM_MAX_OPS + 1];  // one CTA per column slot of every wide tile
+  int n;
+};
+
+// column tiles of an op that run on the tensor cores (width >= 2)
+int oz_wide_tiles(int ncols);
+// BF16 elements of an operator's digit tiles (rows padded to 128, k to 16)
+int64_t oz_operator_elems(int m, int kdim);
+// BF16 elements of an X operand's digit tiles
+int64_t oz_x_elems(int kdim, int ncols);
+// operator digits (setup): rows i of op(At) (At[k + i lda], k < kdim);
+// As gets ceil(m/128)*128 scales
+void launch_oz_rows(const double* At, int64_t lda, int m, int kdim, uint16_t* Ad, float* As, cudaStream_t st);
+// X digits of every op of one launch
+void launch_oz_cols(const OzColJobs& jobs, cudaStream_t st);
+// the tensor-core stream-K products of a plan built with COST_TC; err (device
+// int, may be NULL) receives a non-zero code if a wait gave up
+void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int* seg_start, int nctas,
+                    double* partial, const int* done, int* ran, int* err, cudaStream_t st);
+// persistent CTAs of the tensor-core kernel (one per SM)
+int oz_resident_ctas();
+
+}  // namespace wc4d

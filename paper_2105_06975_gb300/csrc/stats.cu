@@ -16,6 +16,7 @@ struct Rec {
   int cls;
   double work;
   int flag;
+  double work2, work3;
 };
 struct Profile {
   std::mutex mu;
@@ -44,11 +45,11 @@ cudaEvent_t get_event(Profile& p) {
 
 bool prof_enabled() { return prof().on; }
 
-int* prof_begin(int cls, double work, cudaStream_t st) {
+int* prof_begin(int cls, double work, cudaStream_t st, double work2, double work3) {
   Profile& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   if (!p.on || (int)p.recs.size() >= p.cap) return nullptr;
-  Rec r{get_event(p), get_event(p), cls, work, (int)p.recs.size()};
+  Rec r{get_event(p), get_event(p), cls, work, (int)p.recs.size(), work2, work3};
   WC4D_CUDA(cudaMemsetAsync(p.d_flags + r.flag, 0, sizeof(int), st));
   WC4D_CUDA(cudaEventRecord(r.e0, st));
   p.recs.push_back(r);
@@ -118,6 +119,12 @@ int wc4d_get_stats(wc4d_stats* out) {
       out->gemmdf_ms += ms;
       out->gemmdf_flops += p.recs[i].work;
       out->gemmdf_launches += 1;
+    } else if (p.recs[i].cls == PROF_GEMMTC) {
+      out->gemmtc_ms += ms;
+      out->gemmtc_flops += p.recs[i].work;
+      out->gemmtc_bytes += p.recs[i].work2;
+      out->gemmtc_mma_flops += p.recs[i].work3;
+      out->gemmtc_launches += 1;
     } else if (p.recs[i].cls == PROF_GEMM32) {
       out->gemm32_ms += ms;
       out->gemm32_flops += p.recs[i].work;

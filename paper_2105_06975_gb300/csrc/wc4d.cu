@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "krylov.cuh"
 #include "learned.cuh"
+#include "ozaki.cuh"
 
 namespace wc4d {
 
@@ -37,6 +38,10 @@ struct Split {
   const float* h = nullptr;
   const float* l = nullptr;
 };
+struct Digits {  // Ozaki digit tiles and row scales of an operator
+  const uint16_t* d = nullptr;
+  const float* s = nullptr;
+};
 template <typename T>
 struct OpSet {
   T *B = nullptr, *Q = nullptr, *R = nullptr;
@@ -54,9 +59,69 @@ struct OpSet {
   }
   float *xh = nullptr, *xl = nullptr;  // split X operands of one launch (2 n floats each)
   int64_t xcap = 0;
+  // OZAKI: wide products on the tensor cores from digit forms of the operators
+  // and of each launch's X blocks; one-column products read the splits above
+  int tc = 0;
+  std::vector<std::pair<const T*, Digits>> digits;
+  Digits digits_of(const T* m) const {
+    for (auto& d : digits)
+      if (d.first == m) return d.second;
+    return Digits{};
+  }
+  uint16_t* xd = nullptr;
+  int64_t xdcap = 0;
+  float* xs = nullptr;
+  int64_t xscap = 0;
+  int* tc_err = nullptr;
+  void attach_tc(GemmOpsT<T>& ops, cudaStream_t st) const {
+    if constexpr (sizeof(T) == 8) {
+      ops.tc = 1;
+      ops.df32 = 1;
+      ops.err = tc_err;
+      OzColJobs jobs{};
+      int64_t xoff = 0, soff = 0;
+      int ctas = 0;
+      for (int o = 0; o < ops.nops; ++o) {
+        GemmOpT<T>& op = ops.op[o];
+        const Split sp = split_of(op.At);
+        op.Ah = sp.h;
+        op.Al = sp.l;
+        const int wide = oz_wide_tiles(op.ncols);
+        if (wide == 0 || op.m <= 0) continue;
+        const Digits dg = digits_of(op.At);
+        if (!dg.d) throw Error{WC4D_ERR_ARG, "internal: no digit form for a tensor-core operator"};
+        op.Ad = dg.d;
+        op.As = dg.s;
+        const int64_t xe = oz_x_elems(op.kdim, op.ncols);
+        if (xoff + xe > xdcap || soff + (int64_t)wide * OZ_BN > xscap)
+          throw Error{WC4D_ERR_ARG, "internal: digit operand buffer too small"};
+        op.Xd = xd + xoff;
+        op.Xs = xs + soff;
+        OzColJob& jb = jobs.j[jobs.n];
+        jb.X = op.X;
+        jb.ldx = op.ldx;
+        jb.kdim = op.kdim;
+        jb.ncols = op.ncols;
+        jb.nkb = (op.kdim + OZ_BK - 1) / OZ_BK;
+        jb.Xd = op.Xd;
+        jb.Xs = op.Xs;
+        jobs.cta_base[jobs.n] = ctas;
+        ++jobs.n;
+        ctas += wide * OZ_BN;
+        xoff += xe;
+        soff += (int64_t)wide * OZ_BN;
+      }
+      jobs.cta_base[jobs.n] = ctas;
+      launch_oz_cols(jobs, st);
+    }
+  }
   // route every product of a launch through the double-float kernel: attach
   // the operator splits and split each op's X block once
   void attach(GemmOpsT<T>& ops, cudaStream_t st) const {
+    if (tc) {
+      attach_tc(ops, st);
+      return;
+    }
     if (!df32) return;
     ops.df32 = 1;
     int64_t off = 0;
@@ -567,7 +632,7 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(o->krylov == WC4D_KRYLOV_MINRES || o->maxit <= 2000, WC4D_ERR_ARG,
              "GMRES/FGMRES without restarts keep maxit <= 2000 (Hessenberg column in shared memory)");
   WC4D_CHECK(o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_MIXED || o->precision == WC4D_PREC_DF32 ||
-                 o->precision == WC4D_PREC_DF32_P32,
+                 o->precision == WC4D_PREC_DF32_P32 || o->precision == WC4D_PREC_OZAKI,
              WC4D_ERR_ARG, "bad precision");
   WC4D_CHECK(o->precision != WC4D_PREC_DF32_P32 || o->krylov == WC4D_KRYLOV_GMRES, WC4D_ERR_ARG,
              "the FP32-preconditioner mode runs the (flexible) DF32 GMRES");
@@ -693,8 +758,9 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   }
   // GEMM schedules
   const bool dfm = (o->precision != WC4D_PREC_FP64);
-  const int C = max_gemm_ctas(dfm);
-  const int cm = dfm ? COST_DF32 : COST_FP64;
+  const bool ozm = (o->precision == WC4D_PREC_OZAKI);
+  const int C = ozm ? oz_resident_ctas() : max_gemm_ctas(dfm);
+  const int cm = ozm ? COST_TC : (dfm ? COST_DF32 : COST_FP64);
   plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}, {p, p, N + 1, TRI_FULL}}, C, cm);
   if (P->have_pd) {
     if (o->shat == WC4D_SHAT_EXACT) {
@@ -713,7 +779,10 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
   int slots = std::max({P->plan_A.nslots, P->plan_pd1.nslots, P->plan_pd2.nslots, P->plan_pi1.nslots,
                         P->plan_pi2.nslots, 1});
-  f.partial = P->alloc<double>((int64_t)slots * GEMM_BM * GEMM_BN);
+  const GemmPlan* plans[5] = {&P->plan_A, &P->plan_pd1, &P->plan_pd2, &P->plan_pi1, &P->plan_pi2};
+  int64_t slot_rows = 0;  // slots x rows per slot over the plans
+  for (const GemmPlan* pl : plans) slot_rows = std::max<int64_t>(slot_rows, (int64_t)pl->nslots * pl->bm);
+  f.partial = P->alloc<double>(std::max<int64_t>(slot_rows, GEMM_BM) * GEMM_BN);
   f.t1 = P->alloc<double>(P->n);
   f.t2 = P->alloc<double>(P->n);
   f.t3 = P->alloc<double>(P->n);
@@ -742,6 +811,45 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       add(f.WS, (int64_t)P->nS * P->nS);
       add(f.WSt, (int64_t)P->nS * P->nS);
     }
+  }
+  if (ozm) {
+    // digit forms of the operators that meet two or more right-hand sides
+    // (the Q family with N >= 2 time levels, the R family with N + 1 >= 2)
+    f.tc = 1;
+    auto dig = [&](const double* m, int rows) {
+      if (!m) return;
+      const int64_t rp = (int64_t)(rows + OZ_BM - 1) / OZ_BM * OZ_BM;
+      uint16_t* d = P->alloc<uint16_t>(oz_operator_elems(rows, rows));
+      float* sc = P->alloc<float>(rp);
+      launch_oz_rows(m, rows, rows, rows, d, sc, st);
+      f.digits.push_back({m, Digits{d, sc}});
+    };
+    if (N >= 2) {
+      dig(f.Q, s);
+      dig(f.WQ, s);
+      dig(f.WQt, s);
+    }
+    if (N + 1 >= 2) {
+      dig(f.R, p);
+      dig(f.WR, p);
+      dig(f.WRt, p);
+    }
+    int64_t xe = 0, xsc = 0;
+    for (const GemmPlan* pl : plans) {
+      int64_t e = 0, c = 0;
+      for (int q = 0; q < pl->nops; ++q) {
+        e += oz_x_elems(pl->shape[q].kdim, pl->shape[q].ncols);
+        c += (int64_t)oz_wide_tiles(pl->shape[q].ncols) * OZ_BN;
+      }
+      xe = std::max(xe, e);
+      xsc = std::max(xsc, c);
+    }
+    f.xdcap = std::max<int64_t>(xe, 8);
+    f.xd = P->alloc<uint16_t>(f.xdcap);
+    f.xscap = std::max<int64_t>(xsc, 1);
+    f.xs = P->alloc<float>(f.xscap);
+    f.tc_err = P->alloc<int>(1);
+    WC4D_CUDA(cudaMemsetAsync(f.tc_err, 0, sizeof(int), st));
   }
   if (o->precision == WC4D_PREC_MIXED || o->precision == WC4D_PREC_DF32_P32) {
     OpSet<float>& g = P->f32;
@@ -795,7 +903,8 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   const int64_t nvec = (o->krylov == WC4D_KRYLOV_MINRES) ? 12 : (int64_t)o->maxit + 1;
   P->split_basis = (o->krylov != WC4D_KRYLOV_MINRES) && (o->precision != WC4D_PREC_FP64);
   P->dcgs = (o->krylov == WC4D_KRYLOV_GMRES) &&
-            (o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_DF32_P32);
+            (o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_DF32_P32 ||
+             o->precision == WC4D_PREC_OZAKI);
   if (P->split_basis) {
     // leading dimension padded to 4 floats (16-byte loads); padding stays zero
     P->ldb = (n + 3) / 4 * 4;
@@ -1570,6 +1679,12 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
   }
   WC4D_CUDA(cudaMemcpyAsync(x, P->x, bytes, kout, P->st));
   WC4D_CUDA(cudaStreamSynchronize(P->st));
+  if (P->f64.tc_err) {
+    // a bounded wait of the tensor-core kernel gave up (its outputs are not valid)
+    int e = 0;
+    WC4D_CUDA(cudaMemcpy(&e, P->f64.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    WC4D_CHECK(e == 0, WC4D_ERR_CUDA, "tensor-core product: a bounded wait gave up (code " + std::to_string(e) + ")");
+  }
   loc.status = status;
   loc.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = loc;

@@ -55,6 +55,7 @@ WC4D_PREC_FP64 = 0
 WC4D_PREC_MIXED = 1
 WC4D_PREC_DF32 = 2
 WC4D_PREC_DF32_P32 = 3
+WC4D_PREC_OZAKI = 4
 
 RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG}
 PRECOND = {"PD": WC4D_PRECOND_PD, "PI": WC4D_PRECOND_PI}
@@ -97,7 +98,10 @@ class Stats(ctypes.Structure):
                 ("gemm_launches", ctypes.c_int64), ("orth_ms", ctypes.c_double), ("orth_bytes", ctypes.c_double),
                 ("orth_launches", ctypes.c_int64), ("gemm32_ms", ctypes.c_double), ("gemm32_flops", ctypes.c_double),
                 ("gemm32_launches", ctypes.c_int64), ("gemmdf_ms", ctypes.c_double),
-                ("gemmdf_flops", ctypes.c_double), ("gemmdf_launches", ctypes.c_int64)]
+                ("gemmdf_flops", ctypes.c_double), ("gemmdf_launches", ctypes.c_int64),
+                ("gemmtc_ms", ctypes.c_double), ("gemmtc_flops", ctypes.c_double),
+                ("gemmtc_bytes", ctypes.c_double), ("gemmtc_mma_flops", ctypes.c_double),
+                ("gemmtc_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -379,7 +383,7 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
     o.tol = float(tol)
     o.maxit = int(maxit)
     o.precision = {"fp64": WC4D_PREC_FP64, "mixed": WC4D_PREC_MIXED, "df32": WC4D_PREC_DF32,
-                   "df32p32": WC4D_PREC_DF32_P32}[precision]
+                   "df32p32": WC4D_PREC_DF32_P32, "ozaki": WC4D_PREC_OZAKI}[precision]
     o.inner_iters = int(inner_iters)
     o.check_every = int(check_every)
     return o

@@ -1,0 +1,180 @@
+"""OZAKI mode (not in the paper): the covariance / factor products with two or
+more right-hand sides on the tensor cores, by exact BF16 digit products
+(7 balanced base-128 digits per operand below a power-of-two scale per row /
+column, the 28 products of significance levels 0..6 accumulated exactly in
+FP32, combined in double-float).  One-column products run in double-float.
+
+Parity with the FP64 oracle on the same seeded inputs:
+  * A v within 1e-11 (2-norm, relative) -- each operand keeps 47 bits below
+    its row / column scale and a product's error is ~2^-44 K max|a_i.| max|x_.c|,
+    close to the DF32 mode's ~48-bit products;
+  * P^{-1} v within 1e-9 (as DF32 mode);
+  * the solve meets the true FP64 residual with the oracle's operator, in the
+    same number of iterations as DF32 mode (+-2, 5 %).
+Shapes cover ragged tiles: rows and k not multiples of 128 / 16, one-column
+time levels, column tiles of 2..64 columns and a 65th column, k-ranges longer
+than one exact segment (512).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2105_06975_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2105_06975_gb300 import wc4d as L  # noqa: E402
+from oracle import problem as prb, saddle as sd  # noqa: E402
+
+DEV = "cuda"
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def case(s, N, p, obs="random", seed=0):
+    w = W.small(W.TINY, s=s, N=N, p=p).with_(obs=obs)
+    return w, W.draws(w, seed)
+
+
+def popts(kind, k):
+    return sd.PrecondOptions(kind=kind, k=k, rhat="exact", shat="paper", dhat="exact", kappa_max=100.0)
+
+
+@pytest.mark.parametrize("s,N,p", [
+    (203, 6, 77),     # rows / k ragged; Q: one 6-column tile; R: 7 columns
+    (256, 64, 128),   # Q: one full 64-column tile; R: 64 + a one-column remainder
+    (300, 70, 130),   # Q: 64 + 6 columns; R: 64 + 7
+    (130, 1, 40),     # Q: one column (double-float only); R: a 2-column tile
+    (600, 3, 520),    # k = 600 and 520: several exact segments per tile
+])
+def test_ozaki_products_match_oracle_and_df32(s, N, p):
+    w, dr = case(s, N, p, seed=3)
+    prob = prb.linear_problem(w, dr)
+    k = min(3, N + 1)
+    o = L.make_opts(precond="PI", k=k, precision="ozaki")
+    Z = L.Problem.from_workload(w, dr, o)
+    D = L.Problem.from_workload(w, dr, L.make_opts(precond="PI", k=k, precision="df32"))
+    v = W.random_vector(prob.n, 11)
+    az = Z.apply_saddle(to_dev(v)).cpu().numpy()
+    assert np.all(np.isfinite(az))
+    assert rel(az, prob.A_apply(v)) < 1e-11
+    assert rel(az, D.apply_saddle(to_dev(v)).cpu().numpy()) < 1e-11
+    P = sd.Preconditioner(prob, popts("PI", k))
+    pz = Z.apply_precond("PI", to_dev(v)).cpu().numpy()
+    assert rel(pz, P.apply(v)) < 1e-9
+    # a zero vector gives exactly zero
+    zero = Z.apply_saddle(torch.zeros(prob.n, dtype=torch.float64, device=DEV))
+    assert float(zero.abs().max()) == 0.0
+    Z.close()
+    D.close()
+
+
+def test_ozaki_column_maxima_next_to_a_power_of_two():
+    """A column whose largest magnitude lies just below its power-of-two scale
+    is the edge of the digit split (the balanced digits of a 47-bit integer
+    fill all seven 7-bit fields); signs, exact zeros and entries 2^-60 below
+    the maximum ride along."""
+    w, dr = case(203, 6, 77, seed=5)
+    prob = prb.linear_problem(w, dr)
+    Z = L.Problem.from_workload(w, dr, L.make_opts(precond="PI", k=3, precision="ozaki"))
+    v = W.random_vector(prob.n, 21)
+    s, N, p = w.s, w.N, w.p
+    ns = s * (N + 1)
+    rng = np.random.default_rng(7)
+    for off, m in ((0, s), (ns, p)):
+        blk = v[off:off + m * (N + 1)].reshape(N + 1, m)   # one time level per row of blk (a view)
+        for c in range(N + 1):
+            col = blk[c]
+            j = int(np.argmax(np.abs(col)))
+            col *= (1.0 - 2.0 ** -45) * 2.0 ** (c - 3) / abs(col[j])
+            col[j] = (-1.0 if c % 2 else 1.0) * abs(col[j])
+            col[rng.integers(0, m, 3)] = 0.0
+            col[(j + 1) % m] = 2.0 ** -60
+    az = Z.apply_saddle(to_dev(v)).cpu().numpy()
+    assert rel(az, prob.A_apply(v)) < 1e-11
+    P = sd.Preconditioner(prob, popts("PI", 3))
+    assert rel(Z.apply_precond("PI", to_dev(v)).cpu().numpy(), P.apply(v)) < 1e-9
+    Z.close()
+
+
+def test_ozaki_block_diagonal_preconditioner():
+    w, dr = case(203, 6, 77, seed=2)
+    prob = prb.linear_problem(w, dr)
+    Z = L.Problem.from_workload(w, dr, L.make_opts(precond="PD", k=3, precision="ozaki"))
+    v = W.random_vector(prob.n, 8)
+    P = sd.Preconditioner(prob, popts("PD", 3))
+    assert rel(Z.apply_precond("PD", to_dev(v)).cpu().numpy(), P.apply(v)) < 1e-9
+    Z.close()
+
+
+@pytest.mark.parametrize("kind,krylov", [("PI", "gmres"), ("PD", "gmres"), ("PD", "minres")])
+def test_ozaki_solve_matches_df32_and_lu(kind, krylov):
+    w, dr = case(203, 6, 77, seed=2)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    x_lu = sd.dense_solve(prob, rhs)
+    res = {}
+    for prec in ("df32", "ozaki"):
+        o = L.make_opts(precond=kind, k=3, precision=prec, krylov=krylov, tol=1e-10, maxit=1500)
+        G = L.Problem.from_workload(w, dr, o)
+        x, info = G.solve(to_dev(rhs))
+        assert info.status == 0, (prec, info.as_dict())
+        xg = x.cpu().numpy()
+        r = rhs - prob.A_apply(xg)
+        assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-10
+        assert rel(xg, x_lu) < 1e-6
+        res[prec] = info.iters
+        G.close()
+    assert abs(res["ozaki"] - res["df32"]) <= 2 + 0.05 * res["df32"], res
+
+
+def test_ozaki_nonfinite_input_is_reported():
+    w, dr = case(203, 6, 77, seed=2)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    G = L.Problem.from_workload(w, dr, L.make_opts(precond="PI", k=3, precision="ozaki", maxit=50))
+    bad = rhs.copy()
+    bad[5] = np.nan
+    v = W.random_vector(prob.n, 4)
+    v[prob.n // 2] = np.inf
+    av = G.apply_saddle(to_dev(v)).cpu().numpy()
+    assert not np.all(np.isfinite(av))
+    with pytest.raises(L.WC4DError) as e:
+        G.solve(to_dev(bad))
+    assert e.value.code == L.WC4D_ERR_NONFINITE
+    # the problem stays usable
+    x, info = G.solve(to_dev(rhs))
+    assert info.status in (0, L.WC4D_ERR_MAXIT)
+    G.close()
+
+
+@pytest.mark.slow
+def test_ozaki_scale_workload():
+    """s=2048, N=64, p=1024 (n = 332,800): the benchmark's launch configuration.
+    A v within 1e-11 of the oracle, P_I^{-1} v within 1e-7 (the bound of the
+    FP64 mode at this size: kappa(R) = 2.6e9), and the solve meets the 1e-6
+    relative residual with the oracle's operator."""
+    w = W.SCALE
+    dr = W.draws(w, 0)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    v = W.random_vector(prob.n, 3)
+    P = sd.Preconditioner(prob, popts("PI", 4))
+    o = L.make_opts(precond="PI", k=4, precision="ozaki", tol=1e-6, maxit=1000)
+    G = L.Problem.from_workload(w, dr, o)
+    assert rel(G.apply_saddle(to_dev(v)).cpu().numpy(), prob.A_apply(v)) < 1e-11
+    assert rel(G.apply_precond("PI", to_dev(v)).cpu().numpy(), P.apply(v)) < 1e-7
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == 0, info.as_dict()
+    r = rhs - prob.A_apply(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-6
+    G.close()
