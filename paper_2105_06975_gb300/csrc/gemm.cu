@@ -123,8 +123,11 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
         auto& lst = per_cta[cta];
         const int k0 = kb * GEMM_BK;
         const int k1 = std::min(shapes[t.op].kdim, (kb + 1) * GEMM_BK);
+        // tensor-core plan: exact segments of at most OZ_KMAX k; GEMV segments of
+        // at most OZ_GEMV_K k (fine grains to interleave with the MMA segments)
+        const int kcap = t.gemv ? OZ_GEMV_K : OZ_KMAX;
         if (!lst.empty() && lst.back().op == t.op && lst.back().row0 == t.row0 && lst.back().col0 == t.col0 &&
-            lst.back().k1 == k0 && cur_cta == cta && (!tc || k1 - lst.back().k0 <= OZ_KMAX)) {
+            lst.back().k1 == k0 && cur_cta == cta && (!tc || k1 - lst.back().k0 <= kcap)) {
           lst.back().k1 = k1;
         } else {
           lst.push_back(GemmSeg{t.op, t.row0, t.col0, k0, k1, ti /* tile id, slot assigned below */,
@@ -135,7 +138,36 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
     }
   };
   assign(0);
-  if (tc) assign(1);
+  if (tc) {
+    assign(1);
+    // order of a CTA's list: g_0, T_0, g_1, T_1, ..., g_{n-1}, T_{n-1}, with the
+    // GEMV segments g_i sized like the tensor-core segment T_i.  The epilogue
+    // warps run g_i while the MMAs of T_i proceed, then drain T_i just before
+    // T_{i+1} needs the accumulators.
+    for (auto& lst : per_cta) {
+      std::vector<GemmSeg> G, T;
+      for (auto& sg : lst) (tiles[sg.slot].gemv ? G : T).push_back(sg);
+      if (T.empty() || G.empty()) continue;
+      double tkb = 0;
+      for (auto& sg : T) tkb += sg.k1 - sg.k0;
+      double gk = 0;
+      for (auto& sg : G) gk += sg.k1 - sg.k0;
+      std::vector<GemmSeg> out;
+      size_t gi = 0;
+      double done_t = 0, done_g = 0;
+      for (auto& sg : T) {
+        done_t += sg.k1 - sg.k0;
+        const double target = gk * done_t / tkb;  // GEMV k to have been issued by the end of this gap
+        while (gi < G.size() && done_g + 0.5 * (G[gi].k1 - G[gi].k0) <= target) {
+          done_g += G[gi].k1 - G[gi].k0;
+          out.push_back(G[gi++]);
+        }
+        out.push_back(sg);
+      }
+      while (gi < G.size()) out.push_back(G[gi++]);
+      lst.swap(out);
+    }
+  }
   (void)W;
   int slot = 0;
   for (int c = 0; c < C; ++c) {
@@ -157,7 +189,8 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
       const OpShape& sh = shapes[sg.op];
       const int cols = std::min(sg.colw, sh.ncols - sg.col0);
       const int rows = std::min(bm, sh.m - sg.row0);
-      WC4D_CHECK(sg.k1 - sg.k0 <= OZ_KMAX, WC4D_ERR_ARG, "internal: tensor-core segment longer than 512");
+      WC4D_CHECK(sg.k1 - sg.k0 <= (cols >= 2 ? OZ_KMAX : OZ_GEMV_K), WC4D_ERR_ARG,
+                 "internal: tensor-core plan segment longer than its exact / GEMV limit");
       const int kbs = (sg.k1 + OZ_BK - 1) / OZ_BK - sg.k0 / OZ_BK;
       if (cols >= 2) {
         bytes += (double)kbs * 2.0 * OZ_DIGITS * OZ_A_TILE + 8.0 * rows * cols;

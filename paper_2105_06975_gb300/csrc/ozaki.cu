@@ -93,6 +93,22 @@ __device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t* red) {
   return m;
 }
 
+// largest magnitude bit pattern of src[0..n) (8 independent loads in flight per thread)
+__device__ __forceinline__ uint64_t max_mag_bits(const double* __restrict__ src, int n) {
+  uint64_t mx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k0 = threadIdx.x; k0 < n; k0 += 8 * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + j * blockDim.x;
+      const uint64_t v = (k < n) ? mag_bits(src[k]) : 0ull;
+      mx[j] = v > mx[j] ? v : mx[j];
+    }
+  }
+#pragma unroll
+  for (int j = 1; j < 8; ++j) mx[0] = mx[j] > mx[0] ? mx[j] : mx[0];
+  return mx[0];
+}
+
 // Digits of one row (operator) or column (X) of length kdim, padded to nkb
 // blocks of 16, into tile rt/ct at position r of its 128 (64) rows.
 // src == nullptr or a padding row writes zero digits.
@@ -127,12 +143,7 @@ __global__ void __launch_bounds__(128) oz_rows_kernel(const double* __restrict__
   __shared__ uint64_t red[4];
   const int i = blockIdx.x;
   const double* row = (i < m) ? At + (int64_t)i * lda : nullptr;
-  uint64_t mx = 0;
-  if (row)
-    for (int k = threadIdx.x; k < kdim; k += blockDim.x) {
-      const uint64_t v = mag_bits(row[k]);
-      mx = v > mx ? v : mx;
-    }
+  uint64_t mx = row ? max_mag_bits(row, kdim) : 0ull;
   mx = block_max_u64(mx, red);
   const int emax = (int)(mx >> 52);
   if (threadIdx.x == 0) As[i] = row ? scale_of(emax) : 0.f;
@@ -140,22 +151,28 @@ __global__ void __launch_bounds__(128) oz_rows_kernel(const double* __restrict__
   write_digits(row, kdim, nkb, emax, Ad + (int64_t)rt * nkb * OZ_DIGITS * OZ_A_TILE, OZ_A_TILE, OZ_BM, r);
 }
 
-// one CTA per (op, wide column tile, column of the tile)
+// one CTA per (op, wide column tile, column of the tile), and one per op for
+// the double-float split of its one-column (GEMV) column
 __global__ void __launch_bounds__(128) oz_cols_kernel(OzColJobs jobs) {
   __shared__ uint64_t red[4];
   int o = 0;
   while (o + 1 < jobs.n && (int)blockIdx.x >= jobs.cta_base[o + 1]) ++o;
   const OzColJob& jb = jobs.j[o];
   const int local = (int)blockIdx.x - jobs.cta_base[o];
+  if (local >= jb.wide * OZ_BN) {
+    const double* xc = jb.X + (int64_t)jb.gemv_col * jb.ldx;
+    for (int k = threadIdx.x; k < jb.kdim; k += blockDim.x) {
+      const double x = xc[k];
+      const float h = __double2float_rn(x);
+      jb.Xgh[k] = h;
+      jb.Xgl[k] = __double2float_rn(x - (double)h);
+    }
+    return;
+  }
   const int ct = local / OZ_BN, cl = local % OZ_BN;
   const int c = ct * OZ_BN + cl;
   const double* col = (c < jb.ncols) ? jb.X + (int64_t)c * jb.ldx : nullptr;
-  uint64_t mx = 0;
-  if (col)
-    for (int k = threadIdx.x; k < jb.kdim; k += blockDim.x) {
-      const uint64_t v = mag_bits(col[k]);
-      mx = v > mx ? v : mx;
-    }
+  uint64_t mx = col ? max_mag_bits(col, jb.kdim) : 0ull;
   mx = block_max_u64(mx, red);
   const int emax = (int)(mx >> 52);
   if (threadIdx.x == 0) jb.Xs[c] = col ? scale_of(emax) : 0.f;
@@ -171,9 +188,8 @@ constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_X_BYTES;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES;  // 172032
 constexpr int OZ_THREADS = 192;                      // warps 0-3 epilogue, 4 copies, 5 MMA
 // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
-// K-major, N = 64, M = 128
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                              ((uint32_t)(OZ_BM >> 4) << 24);
+// K-major, M = 128; N / 8 goes in at bit 17
+constexpr uint32_t OZ_IDESC_MK = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
 constexpr unsigned long long OZ_WAIT_NS = 1000000000ull;  // a wait gives up after 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -225,51 +241,65 @@ __device__ __forceinline__ void give_up(volatile int* abort_flag, int* err, int 
   if (err) atomicCAS(err, 0, code);
 }
 
-// double-float GEMV segment (one output column): warp w takes rows w, w+4, ...,
-// two rows per pass (rows r and r + 4) so that 64 loads per lane are in
-// flight; lanes stride k, the X values of the segment stay in registers
-__device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float2* __restrict__ dst) {
-  constexpr int Q = OZ_KMAX / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float xh[Q], xl[Q];
-  const double* xc = op.X + (int64_t)sg.col0 * op.ldx;
+// 16 consecutive operator entries (hi, lo) from k = kb on: 16-byte loads when
+// the row is 16-byte aligned and all 16 lie below k1
+__device__ __forceinline__ void load16(const float* __restrict__ h, const float* __restrict__ l, int kb, int k1,
+                                       bool vec, float* oh, float* ol) {
+  if (vec && kb + 16 <= k1) {
 #pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int k = sg.k0 + lane + 32 * q;
-    const double x = (k < sg.k1) ? xc[k] : 0.0;
-    xh[q] = __double2float_rn(x);
-    xl[q] = __double2float_rn(x - (double)xh[q]);
-  }
-  for (int r = warp; r < OZ_BM; r += 8) {
-    const int row0 = sg.row0 + r;
-    if (row0 >= op.m) break;
-    const bool has1 = row0 + 4 < op.m;  // r = warp + 8j <= 123, so row r + 4 is in the tile
-    const int row1 = has1 ? row0 + 4 : row0;
-    const float* ah0 = op.Ah + (int64_t)row0 * op.lda;
-    const float* al0 = op.Al + (int64_t)row0 * op.lda;
-    const float* ah1 = op.Ah + (int64_t)row1 * op.lda;
-    const float* al1 = op.Al + (int64_t)row1 * op.lda;
-    float a0h[Q], a0l[Q], a1h[Q], a1l[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int k = sg.k0 + lane + 32 * q;
-      const bool in = k < sg.k1;
-      a0h[q] = in ? ah0[k] : 0.f;
-      a0l[q] = in ? al0[k] : 0.f;
-      a1h[q] = in ? ah1[k] : 0.f;
-      a1l[q] = in ? al1[k] : 0.f;
+    for (int q = 0; q < 4; ++q) {
+      const float4 a = *reinterpret_cast<const float4*>(h + kb + 4 * q);
+      const float4 b = *reinterpret_cast<const float4*>(l + kb + 4 * q);
+      oh[4 * q] = a.x, oh[4 * q + 1] = a.y, oh[4 * q + 2] = a.z, oh[4 * q + 3] = a.w;
+      ol[4 * q] = b.x, ol[4 * q + 1] = b.y, ol[4 * q + 2] = b.z, ol[4 * q + 3] = b.w;
     }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const bool in = kb + q < k1;
+      oh[q] = in ? h[kb + q] : 0.f;
+      ol[q] = in ? l[kb + q] : 0.f;
+    }
+  }
+}
+
+// Double-float GEMV segment (one output column, k-range <= OZ_GEMV_K = 128):
+// eight lanes per row, each over 16 consecutive k; a warp takes rows
+// 32 p + 8 w + g and that + 4 in pass p (g = lane / 8), so 64 operand floats
+// per lane are in flight.  X comes split (hi, lo) from the digit kernel.
+__device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float2* __restrict__ dst) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 3, j = lane & 7;
+  const int kb = sg.k0 + 16 * j;
+  const bool vec = (op.lda & 3) == 0;  // the split arrays start 16-byte aligned
+  float xh[16], xl[16];
+  load16(op.Xh, op.Xl, kb, sg.k1, true, xh, xl);
+#pragma unroll 1
+  for (int pass = 0; pass < OZ_BM / 32; ++pass) {
+    const int ra = 32 * pass + 8 * warp + g, rb = ra + 4;
+    const int rowa = sg.row0 + ra, rowb = sg.row0 + rb;
+    if (!__any_sync(0xffffffffu, rowa < op.m)) break;
+    float ah[16], al[16], bh[16], bl[16];
+    const int64_t oa = (int64_t)min(rowa, op.m - 1) * op.lda, ob = (int64_t)min(rowb, op.m - 1) * op.lda;
+    load16(op.Ah + oa, op.Al + oa, kb, rowa < op.m ? sg.k1 : kb, vec, ah, al);
+    load16(op.Ah + ob, op.Al + ob, kb, rowb < op.m ? sg.k1 : kb, vec, bh, bl);
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      df_mac(s0, c0, a0h[q], a0l[q], xh[q], xl[q]);
-      df_mac(s1, c1, a1h[q], a1l[q], xh[q], xl[q]);
+    for (int q = 0; q < 16; ++q) {
+      df_mac(s0, c0, ah[q], al[q], xh[q], xl[q]);
+      df_mac(s1, c1, bh[q], bl[q], xh[q], xl[q]);
     }
-    const float2 v0 = df_warp_sum(s0, c0);
-    const float2 v1 = df_warp_sum(s1, c1);
-    if (lane == 0) {
-      dst[r] = v0;
-      if (has1) dst[r + 4] = v1;
+    float2 va, vb;
+    two_sum(s0, c0, va.x, va.y);
+    two_sum(s1, c1, vb.x, vb.y);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      va = df_add(va, make_float2(__shfl_xor_sync(0xffffffffu, va.x, o), __shfl_xor_sync(0xffffffffu, va.y, o)));
+      vb = df_add(vb, make_float2(__shfl_xor_sync(0xffffffffu, vb.x, o), __shfl_xor_sync(0xffffffffu, vb.y, o)));
+    }
+    if (j == 0) {
+      if (rowa < op.m) dst[ra] = va;
+      if (rowb < op.m) dst[rb] = vb;
     }
   }
 }
@@ -374,17 +404,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t aA = sbase + s * OZ_STAGE_BYTES, aX = aA + OZ_A_BYTES;
+          // For digit t of the operator the X digit tiles u = 0..6-t lie stacked in
+          // shared memory and their level accumulators t+u are adjacent in TMEM,
+          // so one MMA of N = 64 (7-t) columns (split at N <= 256) does them all:
+          // 10 MMAs per 16 k instead of 28, and each operator digit tile is read
+          // from shared memory once or twice instead of 7-t times.
 #pragma unroll
           for (int t = 0; t < OZ_DIGITS; ++t) {
 #pragma unroll
-            for (int u = 0; u + t < OZ_DIGITS; ++u) {
+            for (int u0 = 0; u0 < OZ_DIGITS - t; u0 += 4) {
+              const int cnt = min(4, OZ_DIGITS - t - u0);
               const uint64_t da = sdesc(aA + t * (OZ_A_TILE * 2));
-              const uint64_t db = sdesc(aX + u * (OZ_X_TILE * 2));
+              const uint64_t db = sdesc(aX + u0 * (OZ_X_TILE * 2));
+              const uint32_t idesc = OZ_IDESC_MK | ((uint32_t)((cnt * OZ_BN) >> 3) << 17);
               const uint32_t acc = (kb > kb0 || t > 0) ? 1u : 0u;
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tbase + (uint32_t)((t + u) * OZ_BN)),
-                  "l"(da), "l"(db), "r"(OZ_IDESC), "r"(acc));
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tbase + (uint32_t)((t + u0) * OZ_BN)),
+                  "l"(da), "l"(db), "r"(idesc), "r"(acc));
             }
           }
           tc_commit(&empty_bar[s]);  // the stage is free once these products have read it

@@ -10,22 +10,36 @@ constexpr int OZ_BM = 128;                   // operator rows per tile (MMA M, T
 constexpr int OZ_BN = 64;                    // X columns per tile (MMA N)
 constexpr int OZ_BK = 16;                    // k per MMA and per digit tile
 constexpr int OZ_KMAX = 512;                 // longest k-range accumulated exactly in FP32
+constexpr int OZ_GEMV_K = 128;               // longest k-range of a one-column (GEMV) segment
 constexpr int OZ_A_TILE = OZ_BM * OZ_BK;     // elements of one operator digit tile
 constexpr int OZ_X_TILE = OZ_BN * OZ_BK;     // elements of one X digit tile
 
-// Digit form of the X operand of one op of a launch.
+// Digit form of the X operand of one op of a launch, and the double-float
+// split of its one-column (GEMV) column if it has one.
 struct OzColJob {
   const double* X;
   int64_t ldx;
   int kdim, ncols, nkb;
   uint16_t* Xd;  // oz_x_elems(kdim, ncols) BF16 digits
   float* Xs;     // oz_wide_tiles(ncols) * OZ_BN scales
+  int wide;      // oz_wide_tiles(ncols)
+  int gemv_col;  // oz_gemv_col(ncols), -1 if none
+  float* Xgh;    // kdim floats each: hi / lo parts of column gemv_col
+  float* Xgl;
 };
 struct OzColJobs {
   OzColJob j[GEMM_MAX_OPS];
-  int cta_base[GEMM_MAX_OPS + 1];  // one CTA per column slot of every wide tile
+  int cta_base[GEMM_MAX_OPS + 1];  // wide * 64 CTAs per op, + 1 with a GEMV column
   int n;
 };
+
+// the column a plan runs as a one-column (GEMV) tile: column 0 of a
+// one-column op, the last column when ncols = 64 q + 1 (q >= 1); else -1
+inline int oz_gemv_col(int ncols) {
+  if (ncols == 1) return 0;
+  if (ncols > OZ_BN && ncols % OZ_BN == 1) return ncols - 1;
+  return -1;
+}
 
 // column tiles of an op that run on the tensor cores (width >= 2)
 int oz_wide_tiles(int ncols);

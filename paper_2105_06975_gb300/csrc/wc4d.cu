@@ -72,6 +72,8 @@ struct OpSet {
   int64_t xdcap = 0;
   float* xs = nullptr;
   int64_t xscap = 0;
+  float* xg = nullptr;  // double-float split of each op's GEMV column
+  int64_t xgcap = 0;
   int* tc_err = nullptr;
   void attach_tc(GemmOpsT<T>& ops, cudaStream_t st) const {
     if constexpr (sizeof(T) == 8) {
@@ -81,35 +83,52 @@ struct OpSet {
       OzColJobs jobs{};
       int64_t xoff = 0, soff = 0;
       int ctas = 0;
+      int64_t goff = 0;
       for (int o = 0; o < ops.nops; ++o) {
         GemmOpT<T>& op = ops.op[o];
         const Split sp = split_of(op.At);
         op.Ah = sp.h;
         op.Al = sp.l;
         const int wide = oz_wide_tiles(op.ncols);
-        if (wide == 0 || op.m <= 0) continue;
-        const Digits dg = digits_of(op.At);
-        if (!dg.d) throw Error{WC4D_ERR_ARG, "internal: no digit form for a tensor-core operator"};
-        op.Ad = dg.d;
-        op.As = dg.s;
-        const int64_t xe = oz_x_elems(op.kdim, op.ncols);
-        if (xoff + xe > xdcap || soff + (int64_t)wide * OZ_BN > xscap)
-          throw Error{WC4D_ERR_ARG, "internal: digit operand buffer too small"};
-        op.Xd = xd + xoff;
-        op.Xs = xs + soff;
+        const int gcol = oz_gemv_col(op.ncols);
+        if ((wide == 0 && gcol < 0) || op.m <= 0 || op.kdim <= 0) continue;
         OzColJob& jb = jobs.j[jobs.n];
+        jb = OzColJob{};
         jb.X = op.X;
         jb.ldx = op.ldx;
         jb.kdim = op.kdim;
         jb.ncols = op.ncols;
         jb.nkb = (op.kdim + OZ_BK - 1) / OZ_BK;
-        jb.Xd = op.Xd;
-        jb.Xs = op.Xs;
+        jb.wide = wide;
+        jb.gemv_col = gcol;
+        if (wide > 0) {
+          const Digits dg = digits_of(op.At);
+          if (!dg.d) throw Error{WC4D_ERR_ARG, "internal: no digit form for a tensor-core operator"};
+          op.Ad = dg.d;
+          op.As = dg.s;
+          const int64_t xe = oz_x_elems(op.kdim, op.ncols);
+          if (xoff + xe > xdcap || soff + (int64_t)wide * OZ_BN > xscap)
+            throw Error{WC4D_ERR_ARG, "internal: digit operand buffer too small"};
+          op.Xd = xd + xoff;
+          op.Xs = xs + soff;
+          jb.Xd = op.Xd;
+          jb.Xs = op.Xs;
+          xoff += xe;
+          soff += (int64_t)wide * OZ_BN;
+        }
+        if (gcol >= 0) {
+          if (!sp.h) throw Error{WC4D_ERR_ARG, "internal: no double-float split for a GEMV operator"};
+          const int64_t ge = (op.kdim + 3) / 4 * 4;  // keep each part 16-byte aligned
+          if (goff + 2 * ge > xgcap) throw Error{WC4D_ERR_ARG, "internal: GEMV operand buffer too small"};
+          jb.Xgh = xg + goff;
+          jb.Xgl = xg + goff + ge;
+          op.Xh = jb.Xgh;
+          op.Xl = jb.Xgl;
+          goff += 2 * ge;
+        }
         jobs.cta_base[jobs.n] = ctas;
         ++jobs.n;
-        ctas += wide * OZ_BN;
-        xoff += xe;
-        soff += (int64_t)wide * OZ_BN;
+        ctas += wide * OZ_BN + (gcol >= 0 ? 1 : 0);
       }
       jobs.cta_base[jobs.n] = ctas;
       launch_oz_cols(jobs, st);
@@ -834,16 +853,20 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       dig(f.WR, p);
       dig(f.WRt, p);
     }
-    int64_t xe = 0, xsc = 0;
+    int64_t xe = 0, xsc = 0, xgc = 0;
     for (const GemmPlan* pl : plans) {
-      int64_t e = 0, c = 0;
+      int64_t e = 0, c = 0, gg = 0;
       for (int q = 0; q < pl->nops; ++q) {
         e += oz_x_elems(pl->shape[q].kdim, pl->shape[q].ncols);
         c += (int64_t)oz_wide_tiles(pl->shape[q].ncols) * OZ_BN;
+        if (oz_gemv_col(pl->shape[q].ncols) >= 0) gg += 2 * ((pl->shape[q].kdim + 3) / 4 * 4);
       }
       xe = std::max(xe, e);
       xsc = std::max(xsc, c);
+      xgc = std::max(xgc, gg);
     }
+    f.xgcap = std::max<int64_t>(xgc, 4);
+    f.xg = P->alloc<float>(f.xgcap);
     f.xdcap = std::max<int64_t>(xe, 8);
     f.xd = P->alloc<uint16_t>(f.xdcap);
     f.xscap = std::max<int64_t>(xsc, 1);
