@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--maxit", type=int, default=1000, help="Krylov iteration cap (workspace size)")
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
-    ap.add_argument("--chosen", default="df32", choices=["fp64", "df32", "df32p32", "mixed", "ozaki"])
+    ap.add_argument("--chosen", default="ozaki", choices=["fp64", "df32", "df32p32", "mixed", "ozaki"])
+    ap.add_argument("--precision", default="ozaki", choices=["df32", "ozaki"],
+                    help="product precision of the batched and learned workloads")
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
@@ -412,7 +414,19 @@ def run_gpu(args):
     # whole-solve bound: the FP64-class products at the DF32 peak vs the Arnoldi and operator bytes at HBM
     st_c = chosen["stats"]
     solve_roof = None
-    if st_c.gemmdf_launches and hbm:
+    bf16 = peaks().get("bf16_tflops")
+    if st_c.gemmtc_launches and hbm and bf16:
+        # tensor-core mode: digit products at the BF16 peak vs the Arnoldi, digit-tile and GEMV bytes at HBM
+        steps_n = max(args.steps, 1)
+        t_tc = st_c.gemmtc_mma_flops / steps_n / (bf16 * 1e12) * 1e3
+        t_hbm = (st_c.orth_bytes + st_c.gemmtc_bytes) / steps_n / (hbm * 1e9) * 1e3
+        t_roof = max(t_tc, t_hbm)
+        solve_roof = {"bound": "tensor" if t_tc >= t_hbm else "hbm", "t_tensor_ms": t_tc, "t_hbm_ms": t_hbm,
+                      "t_roof_ms": t_roof, "ms_per_step": chosen["ms"], "frac": t_roof / chosen["ms"],
+                      "note": "lower bound of one step from the digit-product FLOPs (measured BF16 peak) and the "
+                              "Arnoldi + operator-digit + GEMV bytes (measured HBM); setup and small kernels "
+                              "count as time only"}
+    elif st_c.gemmdf_launches and hbm:
         steps_n = max(args.steps, 1)
         t_alu = st_c.gemmdf_flops / steps_n / (DF32_PEAK_TFLOPS * 1e12) * 1e3
         t_hbm = (st_c.orth_bytes + st_c.gemmdf_launches * GEMM_DF32_TRAFFIC_BYTES) / steps_n / (hbm * 1e9) * 1e3
@@ -497,7 +511,7 @@ def run_batch(args):
     if world > 1:
         torch.distributed.init_process_group("nccl")
     opts = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.batch_maxit,
-                          precision="df32", check_every=args.check_every)
+                          precision=args.precision, check_every=args.check_every)
     t0 = time.perf_counter()
     probs, rhs, meta = build_batch(args, wc4d, W, opts)
     torch.cuda.synchronize()
@@ -571,11 +585,11 @@ def run_learned(args):
     k = min(args.k, w.N + 1)
     arms = {
         "learned_gmres": wc4d.make_opts(precond="PD", k=k, shat="learned", krylov="gmres", tol=1e-6,
-                                        maxit=args.maxit, precision="df32"),
+                                        maxit=args.maxit, precision=args.precision),
         "plain_gmres": wc4d.make_opts(precond="PD", k=k, krylov="gmres", tol=1e-6, maxit=args.maxit,
-                                      precision="df32"),
+                                      precision=args.precision),
         "plain_minres": wc4d.make_opts(precond="PD", k=k, krylov="minres", tol=1e-6, maxit=20000,
-                                       precision="df32"),
+                                       precision=args.precision),
     }
     probs = {a: wc4d.Problem.from_workload(w, dr, o) for a, o in arms.items()}
     rhs = probs["plain_gmres"].synthesize_rhs(dr)

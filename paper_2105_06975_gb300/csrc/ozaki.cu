@@ -181,12 +181,14 @@ __global__ void __launch_bounds__(128) oz_cols_kernel(OzColJobs jobs) {
 }
 
 // ----------------------------------------------------------- tcgen05 kernel
-constexpr int OZ_STAGES = 4;
+constexpr int OZ_STAGES = 5;
 constexpr uint32_t OZ_A_BYTES = OZ_DIGITS * OZ_A_TILE * 2;  // 28672
 constexpr uint32_t OZ_X_BYTES = OZ_DIGITS * OZ_X_TILE * 2;  // 14336
 constexpr uint32_t OZ_STAGE_BYTES = OZ_A_BYTES + OZ_X_BYTES;
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES;  // 172032
-constexpr int OZ_THREADS = 192;                      // warps 0-3 epilogue, 4 copies, 5 MMA
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES;  // 215040
+constexpr int OZ_EPI_WARPS = 8;                      // two per TMEM lane quarter (column halves)
+constexpr int OZ_THREADS = 32 * (OZ_EPI_WARPS + 2);  // + one copy warp and one MMA warp
+constexpr int OZ_COPY_WARP = OZ_EPI_WARPS, OZ_MMA_WARP = OZ_EPI_WARPS + 1;
 // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
 // K-major, M = 128; N / 8 goes in at bit 17
 constexpr uint32_t OZ_IDESC_MK = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BM >> 4) << 24);
@@ -263,10 +265,13 @@ __device__ __forceinline__ void load16(const float* __restrict__ h, const float*
   }
 }
 
-// Double-float GEMV segment (one output column, k-range <= OZ_GEMV_K = 128):
-// eight lanes per row, each over 16 consecutive k; a warp takes rows
-// 32 p + 8 w + g and that + 4 in pass p (g = lane / 8), so 64 operand floats
-// per lane are in flight.  X comes split (hi, lo) from the digit kernel.
+// Double-float GEMV segment (one output column, k-range <= OZ_GEMV_K = 128),
+// run by the epilogue warps: eight lanes per row, each over 16 consecutive k;
+// in pass p warp w takes rows 4 R (W p + w) + g + 4 i, i < R (g = lane / 8,
+// W = OZ_EPI_WARPS, R = OZ_GEMV_ROWS), so 32 R operand floats per lane are in
+// flight.  X comes split (hi, lo) from the digit kernel.
+constexpr int OZ_GEMV_ROWS = 2;
+static_assert(OZ_BM % (4 * OZ_GEMV_ROWS * OZ_EPI_WARPS) == 0, "GEMV passes must tile the 128 rows");
 __device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float2* __restrict__ dst) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 3, j = lane & 7;
@@ -275,31 +280,31 @@ __device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float
   float xh[16], xl[16];
   load16(op.Xh, op.Xl, kb, sg.k1, true, xh, xl);
 #pragma unroll 1
-  for (int pass = 0; pass < OZ_BM / 32; ++pass) {
-    const int ra = 32 * pass + 8 * warp + g, rb = ra + 4;
-    const int rowa = sg.row0 + ra, rowb = sg.row0 + rb;
-    if (!__any_sync(0xffffffffu, rowa < op.m)) break;
-    float ah[16], al[16], bh[16], bl[16];
-    const int64_t oa = (int64_t)min(rowa, op.m - 1) * op.lda, ob = (int64_t)min(rowb, op.m - 1) * op.lda;
-    load16(op.Ah + oa, op.Al + oa, kb, rowa < op.m ? sg.k1 : kb, vec, ah, al);
-    load16(op.Ah + ob, op.Al + ob, kb, rowb < op.m ? sg.k1 : kb, vec, bh, bl);
-    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+  for (int pass = 0; pass < OZ_BM / (4 * OZ_GEMV_ROWS * OZ_EPI_WARPS); ++pass) {
+    const int base = 4 * OZ_GEMV_ROWS * (OZ_EPI_WARPS * pass + warp) + g;
+    if (!__any_sync(0xffffffffu, sg.row0 + base < op.m)) break;
+    float ah[OZ_GEMV_ROWS][16], al[OZ_GEMV_ROWS][16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      df_mac(s0, c0, ah[q], al[q], xh[q], xl[q]);
-      df_mac(s1, c1, bh[q], bl[q], xh[q], xl[q]);
+    for (int i = 0; i < OZ_GEMV_ROWS; ++i) {
+      const int row = sg.row0 + base + 4 * i;
+      const int64_t o = (int64_t)min(row, op.m - 1) * op.lda;
+      load16(op.Ah + o, op.Al + o, kb, row < op.m ? sg.k1 : kb, vec, ah[i], al[i]);
     }
-    float2 va, vb;
-    two_sum(s0, c0, va.x, va.y);
-    two_sum(s1, c1, vb.x, vb.y);
+    float sv[OZ_GEMV_ROWS], cv[OZ_GEMV_ROWS];
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      va = df_add(va, make_float2(__shfl_xor_sync(0xffffffffu, va.x, o), __shfl_xor_sync(0xffffffffu, va.y, o)));
-      vb = df_add(vb, make_float2(__shfl_xor_sync(0xffffffffu, vb.x, o), __shfl_xor_sync(0xffffffffu, vb.y, o)));
-    }
-    if (j == 0) {
-      if (rowa < op.m) dst[ra] = va;
-      if (rowb < op.m) dst[rb] = vb;
+    for (int i = 0; i < OZ_GEMV_ROWS; ++i) sv[i] = cv[i] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+#pragma unroll
+      for (int i = 0; i < OZ_GEMV_ROWS; ++i) df_mac(sv[i], cv[i], ah[i][q], al[i][q], xh[q], xl[q]);
+#pragma unroll
+    for (int i = 0; i < OZ_GEMV_ROWS; ++i) {
+      float2 v;
+      two_sum(sv[i], cv[i], v.x, v.y);
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1)
+        v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+      if (j == 0 && sg.row0 + base + 4 * i < op.m) dst[base + 4 * i] = v;
     }
   }
 }
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&tfull_bar, 1);
-    mbar_init(&tfree_bar, 128);
+    mbar_init(&tfree_bar, 32 * OZ_EPI_WARPS);
     mbar_init(&fin_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -338,7 +343,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t tbase = tmem_base;
   const uint32_t sbase = smem_u32(oz_smem);
 
-  if (warp == 4) {
+  if (warp == OZ_COPY_WARP) {
     // ---- bulk-copy producer: one stage = the 7 operator and 7 X digit tiles of 16 k
     if (lane == 0) {
       int it = 0;
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == OZ_MMA_WARP) {
     // ---- MMA issuer: 28 digit products per 16 k into the 7 level accumulators
     if (lane == 0) {
       int it = 0, nseg = 0;
@@ -437,7 +442,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
     }
   } else {
-    // ---- epilogue warps 0-3: TMEM lanes 32w..32w+31 are rows of the tile
+    // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of
+    // the tile) and columns 32 (w / 4) .. + 31 of every level
+    const int quarter = warp & 3, half = warp >> 2;
     int nseg = 0;
     for (int si = sbeg; si < send; ++si) {
       const GemmSeg sg = segs[si];
@@ -454,15 +461,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       __syncwarp();
       tc_fence_after();
-      const int r = 32 * warp + lane, row = sg.row0 + r;
+      const int r = 32 * quarter + lane, row = sg.row0 + r;
       const bool rin = row < op.m;
       const float sig = rin ? op.As[row] : 0.f;
 #pragma unroll 1
-      for (int cc = 0; cc < OZ_BN / 16; ++cc) {
+      for (int cc = 2 * half; cc < 2 * half + 2; ++cc) {
         uint32_t v[OZ_DIGITS][16];
 #pragma unroll
         for (int l = 0; l < OZ_DIGITS; ++l) {
-          const uint32_t ta = tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(l * OZ_BN + cc * 16);
+          const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(l * OZ_BN + cc * 16);
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
               : "=r"(v[l][0]), "=r"(v[l][1]), "=r"(v[l][2]), "=r"(v[l][3]), "=r"(v[l][4]), "=r"(v[l][5]),
