@@ -1036,15 +1036,18 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, fl
 #pragma unroll
     for (int u = 0; u < 2; ++u) se[u] = ce[u] = sc[u] = cc[u] = make_float2(0.f, 0.f);
     int i = 0;
-    for (; i + 4 <= j; i += 4) {
-      float4 a[4], b[4];
+    // groups of UPD_G basis vectors: 2 UPD_G 16-byte loads in flight per thread
+    // (about two CTAs per SM, so registers are not the limit)
+    constexpr int UPD_G = 8;
+    for (; i + UPD_G <= j; i += UPD_G) {
+      float4 a[UPD_G], b[UPD_G];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < UPD_G; ++u) {
         a[u] = reinterpret_cast<const float4*>(Vh + (int64_t)(i + u) * ldv)[q];
         b[u] = reinterpret_cast<const float4*>(Vl + (int64_t)(i + u) * ldv)[q];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < UPD_G; ++u) {
         const float2 h1 = make_float2(eh[i + u], eh[i + u]), l1 = make_float2(el[i + u], el[i + u]);
         const float2 h2 = make_float2(ch[i + u], ch[i + u]), l2 = make_float2(cl[i + u], cl[i + u]);
         const float2 a0 = make_float2(a[u].x, a[u].y), a1 = make_float2(a[u].z, a[u].w);

@@ -8,7 +8,7 @@ constexpr int DOT_BLOCKS = 304;  // 2 per SM on a 152-SM GB300; fixed for determ
 constexpr int DOT_THREADS = 256;
 // block-dot partials of the Arnoldi passes: one partial per 1024-element chunk
 constexpr int ORTH_U = 4;                         // elements per thread
-constexpr int ORTH_G = 8;                         // basis vectors per block
+constexpr int ORTH_G = 4;                         // basis vectors per block
 constexpr int ORTH_CHUNK = DOT_THREADS * ORTH_U;  // elements per block
 inline int orth_chunks(int64_t n) { return (int)((n + ORTH_CHUNK - 1) / ORTH_CHUNK); }
 // Chunk count of the split-basis dot kernels for cnt basis vectors: about three
