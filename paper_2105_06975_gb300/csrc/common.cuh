@@ -264,6 +264,8 @@ struct EpiT {
   int t0;          // time index of output column 0
   const T* v3;     // EPI_SADDLE_*: x part of the input vector (time-major, s per time)
   const T* Y;      // EPI_SUB_FROM: minuend, same layout as C
+  float* Ch = nullptr;  // T = double, optional: the double-float split of C (same layout)
+  float* Cl = nullptr;
 };
 template <typename T>
 struct EpisT {

@@ -521,19 +521,43 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
     const int off = (c % cw) * bm + (r % bm);
     const int64_t slot_elems = (int64_t)bm * GEMM_BN;
     T acc = T(0);
+    // slots in batches of 8: the slot indices, then the partials, are loaded
+    // together (independent loads in flight) and summed in slot order
+    constexpr int RB = 8;
+    const int q0 = tile_start[tile], q1 = tile_start[tile + 1];
     if (sizeof(T) == 8 && meta.pairs) {
       const float2* pp = reinterpret_cast<const float2*>(partial);
       float2 a2 = make_float2(0.f, 0.f);
-      for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q) {
-        const float2 v = pp[(int64_t)tile_slots[q] * slot_elems + off];
-        float h, l;
-        two_sum(v.x, v.y, h, l);
-        a2 = df_add(a2, make_float2(h, l));
+      for (int qb = q0; qb < q1; qb += RB) {
+        int sl[RB];
+        float2 v[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) sl[u] = (qb + u < q1) ? tile_slots[qb + u] : -1;
+#pragma unroll
+        for (int u = 0; u < RB; ++u) v[u] = sl[u] >= 0 ? pp[(int64_t)sl[u] * slot_elems + off] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          if (sl[u] < 0) break;
+          float h, l;
+          two_sum(v[u].x, v[u].y, h, l);
+          a2 = df_add(a2, make_float2(h, l));
+        }
       }
       acc = T((double)a2.x + (double)a2.y);
     } else {
-      for (int q = tile_start[tile]; q < tile_start[tile + 1]; ++q)
-        acc += partial[(int64_t)tile_slots[q] * slot_elems + off];
+      for (int qb = q0; qb < q1; qb += RB) {
+        int sl[RB];
+        T v[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) sl[u] = (qb + u < q1) ? tile_slots[qb + u] : -1;
+#pragma unroll
+        for (int u = 0; u < RB; ++u) v[u] = sl[u] >= 0 ? partial[(int64_t)sl[u] * slot_elems + off] : T(0);
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          if (sl[u] < 0) break;
+          acc += v[u];
+        }
+      }
     }
     const EpiT<T>& ep = epis.e[o];
     T val;
@@ -561,6 +585,11 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
         val = acc;
     }
     ep.C[r + (int64_t)c * ep.ldc] = val;
+    if (sizeof(T) == 8 && ep.Ch != nullptr) {
+      const float h = (float)val;
+      ep.Ch[r + (int64_t)c * ep.ldc] = h;
+      ep.Cl[r + (int64_t)c * ep.ldc] = (float)((double)val - (double)h);
+    }
   }
 }
 

@@ -148,9 +148,11 @@ void launch_lhat_sweep(const ModelDev& md, int k, const double* v, double* z, bo
 
 // c3_t[j] = v1_t[j] - [t < N] (M_{t+1}^T v1_{t+1})[j] + (H^T v2_t)[j],
 // H^T scatters nu_t[r] to grid point obs[r]; inv[j] = r or -1.
+// c3h / c3l (optional): the double-float split of c3 (hi = round(c3), lo = round(c3 - hi))
 template <typename T>
 __global__ void saddle_c3_kernel(ModelDev md, const T* __restrict__ v1, const T* __restrict__ v2,
-                                 const int* __restrict__ inv, int p, T* __restrict__ c3, const int* done) {
+                                 const int* __restrict__ inv, int p, T* __restrict__ c3, float* __restrict__ c3h,
+                                 float* __restrict__ c3l, const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
   const int s = md.s, N = md.N;
   const int64_t total = (int64_t)(N + 1) * s;
@@ -162,6 +164,11 @@ __global__ void saddle_c3_kernel(ModelDev md, const T* __restrict__ v1, const T*
     const int r = inv[j];
     if (r >= 0) val += v2[(int64_t)t * p + r];
     c3[e] = val;
+    if (c3h != nullptr) {
+      const float h = (float)val;
+      c3h[e] = h;
+      c3l[e] = (float)((double)val - (double)h);
+    }
   }
 }
 
@@ -170,7 +177,14 @@ void saddle_c3(const ModelDev& md, const T* v1, const T* v2, const int* inv, int
                cudaStream_t st) {
   const int64_t total = (int64_t)(md.N + 1) * md.s;
   const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-  saddle_c3_kernel<T><<<nb, 256, 0, st>>>(md, v1, v2, inv, p, c3, done);
+  saddle_c3_kernel<T><<<nb, 256, 0, st>>>(md, v1, v2, inv, p, c3, nullptr, nullptr, done);
+  WC4D_LAUNCH_CHECK();
+}
+void saddle_c3_split(const ModelDev& md, const double* v1, const double* v2, const int* inv, int p, double* c3,
+                     float* c3h, float* c3l, const int* done, cudaStream_t st) {
+  const int64_t total = (int64_t)(md.N + 1) * md.s;
+  const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  saddle_c3_kernel<double><<<nb, 256, 0, st>>>(md, v1, v2, inv, p, c3, c3h, c3l, done);
   WC4D_LAUNCH_CHECK();
 }
 template void saddle_c3<double>(const ModelDev&, const double*, const double*, const int*, int, double*, const int*,

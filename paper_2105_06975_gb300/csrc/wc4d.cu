@@ -31,6 +31,8 @@ void lhat_sweep(const ModelDev& md, int k, const T* v, T* z, bool transpose, boo
 template <typename T>
 void saddle_c3(const ModelDev& md, const T* v1, const T* v2, const int* inv, int p, T* c3, const int* done,
                cudaStream_t st);
+void saddle_c3_split(const ModelDev& md, const double* v1, const double* v2, const int* inv, int p, double* c3,
+                     float* c3h, float* c3l, const int* done, cudaStream_t st);
 
 // Operator data in one precision: covariances, inverse Cholesky factors and
 // the GEMM partial buffer.
@@ -275,8 +277,10 @@ namespace wc4d {
 static int max_gemm_ctas(bool df32 = false) { return gemm_resident_ctas(df32); }
 
 // ------------------------------------------------------------ A v (Sec. 6.2)
+// wh / wl (T = double, optional): also write the double-float split of out
 template <typename T>
-static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T* v, T* out, const int* done) {
+static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T* v, T* out, const int* done,
+                    float* wh = nullptr, float* wl = nullptr) {
   const int s = P->s, N = P->N, p = P->p;
   const T* v1 = v;
   const T* v2 = v + P->ns;
@@ -284,7 +288,15 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
   T* c1 = out;
   T* c2 = out + P->ns;
   T* c3 = out + P->ns + P->np;
-  saddle_c3<T>(P->md, v1, v2, P->d_inv, p, c3, done, P->st);
+  const bool split = (sizeof(T) == 8) && wh != nullptr;
+  if constexpr (sizeof(T) == 8) {
+    if (split)
+      saddle_c3_split(P->md, v1, v2, P->d_inv, p, c3, wh + P->ns + P->np, wl + P->ns + P->np, done, P->st);
+    else
+      saddle_c3<T>(P->md, v1, v2, P->d_inv, p, c3, done, P->st);
+  } else {
+    saddle_c3<T>(P->md, v1, v2, P->d_inv, p, c3, done, P->st);
+  }
   GemmOpsT<T> ops{};
   EpisT<T> ep{};
   ops.nops = 3;
@@ -294,6 +306,14 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
   ep.e[0] = {EPI_SADDLE_C1, c1, s, 0, v3, nullptr};
   ep.e[1] = {EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr};
   ep.e[2] = {EPI_SADDLE_C2, c2, p, 0, v3, nullptr};
+  if (split) {
+    ep.e[0].Ch = wh;
+    ep.e[0].Cl = wl;
+    ep.e[1].Ch = wh + s;
+    ep.e[1].Cl = wl + s;
+    ep.e[2].Ch = wh + P->ns;
+    ep.e[2].Cl = wl + P->ns;
+  }
   os.attach(ops, P->st);
   gemm_run<T>(plan, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
 }
@@ -1224,8 +1244,8 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       } else {
         apply_P<double>(P, which, P->f64, P->vcur, zj, done);
       }
-      apply_A<double>(P, P->f64, P->plan_A, zj, P->wbuf, done);
-      gm_split(P->wbuf, P->wh, P->wl, n, done, st);
+      // w = A z_j, written with its double-float split for the dot pass
+      apply_A<double>(P, P->f64, P->plan_A, zj, P->wbuf, done, P->wh, P->wl);
       gm_dc_dot(P->Vh, P->Vl, lb, j, P->wh, P->wl, n, P->part, done, st);
       gm_mdot_reduce(P->part, 2 * (j + 1) + 1, dot_chunks(n, j + 1), P->red, done, st);
       gm_dc_coef(j, P->red, P->dcst, P->bprev, P->cprev, P->ecoef, P->Hraw, P->H, P->Tm, ldh, P->cs, P->sn, P->g,
