@@ -58,9 +58,11 @@ def parse():
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "batch", "learned"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "batch", "learned", "profile"],
                     help="scale: one s=2048 N=64 window (default line); batch: independent uneven windows; "
-                         "learned: learned Schur block vs the plain P_D (s=1024 N=32)")
+                         "learned: learned Schur block vs the plain P_D (s=1024 N=32); profile: a small fixed "
+                         "run of the hot kernels at the scale sizes for ncu captures (products, then one "
+                         "solve of --maxit GMRES steps)")
     ap.add_argument("--pairs", type=int, default=50000, help="training pairs of the learned workload")
     ap.add_argument("--epochs", type=int, default=4, help="training epochs of the learned workload")
     ap.add_argument("--loss", default="error", choices=["error", "residual"],
@@ -632,10 +634,52 @@ def run_learned(args):
         G.close()
 
 
+def run_profile(args):
+    """The hot kernels at the scale workload's sizes, for ncu captures: 4 x
+    (A v, P_I^-1 v) through the C ABI, then one GMRES solve capped at --maxit
+    steps (tolerance unreachable, so the Arnoldi passes run up to j = maxit-1).
+    About 1 GB on the device at --maxit 110.  Prints one JSON line of CUDA-event
+    timings (not a benchmark line)."""
+    import torch
+
+    from paper_2105_06975_gb300 import wc4d, workload as W
+    torch.cuda.set_device(0)
+    w = W.SCALE
+    dr = W.draws(w, args.seed)
+    o = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-30, maxit=args.maxit,
+                       precision=args.chosen if args.chosen in ("df32", "ozaki") else "ozaki")
+    G = wc4d.Problem.from_workload(w, dr, o)
+    v = torch.from_numpy(W.random_vector(w.n, 3)).cuda()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(4):
+        G.apply_saddle(v)
+        G.apply_precond(args.precond, v)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(4):
+        G.apply_saddle(v)
+    ev[1].record()
+    for _ in range(4):
+        G.apply_precond(args.precond, v)
+    ev[2].record()
+    torch.cuda.synchronize()
+    rhs = G.synthesize_rhs(dr)
+    x = torch.zeros_like(rhs)
+    t0 = time.perf_counter()
+    wc4d.wc4d_solve(G.h, rhs.data_ptr(), x.data_ptr(), False, wc4d.WC4D_MEM_DEVICE, raise_on_error=False)
+    torch.cuda.synchronize()
+    G.close()
+    print(json.dumps({"workload": "profile", "precision": o.precision, "apply_saddle_ms": ev[0].elapsed_time(ev[1]) / 4,
+                      "apply_precond_ms": ev[1].elapsed_time(ev[2]) / 4, "solve_steps": args.maxit,
+                      "solve_ms": (time.perf_counter() - t0) * 1e3}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "profile":
+        run_profile(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "learned":

@@ -988,7 +988,10 @@ void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cpr
 // q_j = (u_j - Q_j c) / gamma into slot j (in place), u_{j+1} = (w - Q_j e' - e_j u_j) / alpha
 // into slot j+1 and into v (double, the next operator input).  Both sums and
 // the q_j epilogue in double-float; 4 elements per thread, 16-byte loads.
-__global__ void __launch_bounds__(DOT_THREADS) gm_dc_update_kernel(float* Vh, float* Vl, int64_t ldv, int j,
+// 64-thread CTAs: one float4 row per thread, so the grid is n/256 small CTAs
+// that spread evenly over the SMs (256-thread CTAs left 2 or 3 per SM)
+constexpr int UPD_THREADS = 64;
+__global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, float* Vl, int64_t ldv, int j,
                                                                    const double* __restrict__ e,
                                                                    const double* __restrict__ cv,
                                                                    const double* __restrict__ dc,
@@ -1110,8 +1113,8 @@ void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, con
                   cudaStream_t st) {
   int* ran = prof_begin(PROF_ORTH, (double)(j + 1) * n * 8.0 + 4.0 * n * 8.0, st);
   const int64_t n4 = (n + 3) / 4;
-  const int nb = (int)std::min<int64_t>((n4 + DOT_THREADS - 1) / DOT_THREADS, 152 * 16);
-  gm_dc_update_kernel<<<nb, DOT_THREADS, sizeof(float) * 4 * std::max(j, 1), st>>>(Vh, Vl, ldv, j, e, c, dc, w, v, n,
+  const int nb = (int)std::min<int64_t>((n4 + UPD_THREADS - 1) / UPD_THREADS, 152 * 64);
+  gm_dc_update_kernel<<<nb, UPD_THREADS, sizeof(float) * 4 * std::max(j, 1), st>>>(Vh, Vl, ldv, j, e, c, dc, w, v, n,
                                                                                   Hraw, ldh, hc, done, ran);
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);

@@ -11,15 +11,16 @@ constexpr int ORTH_U = 4;                         // elements per thread
 constexpr int ORTH_G = 4;                         // basis vectors per block
 constexpr int ORTH_CHUNK = DOT_THREADS * ORTH_U;  // elements per block
 inline int orth_chunks(int64_t n) { return (int)((n + ORTH_CHUNK - 1) / ORTH_CHUNK); }
-// Chunk count of the split-basis dot kernels for cnt basis vectors: about three
-// CTAs (chunks x vector groups) per SM (all resident at 80 registers), so each
-// thread strides over several float4 and the closing block reduction (a
-// shuffle tree per vector) is amortised.  The
+// Chunk count of the split-basis dot kernels for cnt basis vectors: at most
+// three CTAs (chunks x vector groups) per SM, all resident at 80 registers
+// (rounded down: a few CTAs beyond one wave would run as a second wave and
+// nearly double the pass), so each thread strides over several float4 and the
+// closing block reduction (a shuffle tree per vector) is amortised.  The
 // partial buffer holds orth_chunks(n) >= this many partials per row.
 inline int dot_chunks(int64_t n, int cnt) {
   const int maxc = orth_chunks(n);
   const int groups = (cnt + ORTH_G - 1) / ORTH_G;
-  int c = (152 * 3 + groups - 1) / groups;
+  int c = (152 * 3) / groups;
   return c < 1 ? 1 : (c > maxc ? maxc : c);
 }
 
