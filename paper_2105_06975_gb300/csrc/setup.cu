@@ -195,38 +195,42 @@ void launch_check_finite(const double* a, int64_t n, int* flag, cudaStream_t st)
   WC4D_LAUNCH_CHECK();
 }
 
-// ---------------------------------------------------- 64x64 tile products
-// acc[i][j] (thread (tx,ty) owns rows tx+16i, cols ty+16j) += sum_l A(r,l) B(l,c)
-// with A(r,l) = a[(ar0+r) + (ac0+l)*lda] (column-major, rows contiguous) and
-// B(l,c) either b[(br0+l) + (bc0+c)*ldb] (BT = false) or b[(br0+c) + (bc0+l)*ldb]
-// (BT = true: B given through its transpose).  Rows >= ar_lim / cols >= bc_lim read 0.
+// --------------------------------------------------------------- tile products
+// acc[i][j] += sum_l A(r,l) B(l,c) over a tile, with A(r,l) = a[(ar0+r) +
+// (ac0+l)*lda] (column-major, rows contiguous) and B(l,c) either
+// b[(br0+l) + (bc0+c)*ldb] (BT = false) or b[(br0+c) + (bc0+l)*ldb] (BT = true:
+// B given through its transpose).  Rows >= rlim / cols >= clim read 0.
 struct TileMat {
   const double* p;
   int64_t ld;
   int r0, c0;
   int rlim, clim;  // valid extent in the (row, col) of the stored matrix
 };
+// 32x32 tiles with 64 threads (thread (tx, ty) = (tid % 8, tid / 8) owns rows
+// tx + 8i and columns ty + 8j, i, j < 4): four times the CTAs of the 64x64 form
+// for the same product, so small trailing matrices still spread over all SMs
+// (GB300's FP64 pipe makes one 64x64x64 tile about 60 us on one SM).
 template <bool BT>
-__device__ void tile_mm(double acc[4][4], const TileMat& A, const TileMat& B, int K, double (*As)[65],
-                        double (*Bs)[65]) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+__device__ void tile_mm32(double acc[4][4], const TileMat& A, const TileMat& B, int K, double (*As)[33],
+                          double (*Bs)[33]) {
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   for (int l0 = 0; l0 < K; l0 += 16) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q;
-      const int r = e % 64, kk = e / 64;
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 64 * q;
+      const int r = e & 31, kk = e >> 5;
       const int gr = A.r0 + r, gc = A.c0 + l0 + kk;
       As[kk][r] = (l0 + kk < K && gr < A.rlim && gc < A.clim) ? A.p[gr + (int64_t)gc * A.ld] : 0.0;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + 256 * q;
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + 64 * q;
       if (!BT) {
-        const int kk = e % 16, c = e / 16;
+        const int kk = e & 15, c = e >> 4;
         const int gr = B.r0 + l0 + kk, gc = B.c0 + c;
         Bs[kk][c] = (l0 + kk < K && gr < B.rlim && gc < B.clim) ? B.p[gr + (int64_t)gc * B.ld] : 0.0;
       } else {
-        const int c = e % 64, kk = e / 64;
+        const int c = e & 31, kk = e >> 5;
         const int gr = B.r0 + c, gc = B.c0 + l0 + kk;
         Bs[kk][c] = (l0 + kk < K && gr < B.rlim && gc < B.clim) ? B.p[gr + (int64_t)gc * B.ld] : 0.0;
       }
@@ -236,9 +240,9 @@ __device__ void tile_mm(double acc[4][4], const TileMat& A, const TileMat& B, in
     for (int kk = 0; kk < 16; ++kk) {
       double a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 8 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 8 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -253,13 +257,24 @@ constexpr int NB = 64;
 
 // Factor the nb x nb diagonal block at (j0, j0) in shared memory (unblocked,
 // right-looking).  A non-positive or non-finite pivot records its 1-based
-// index in *info (first one wins) and continues with pivot 1.
+// index in *info (first one wins) and continues with pivot 1.  Step c updates
+// only the active triangle i >= j > c, walked densely through a packed
+// (row, column) table so every FP64 instruction of the step has work (GB300's
+// FP64 pipe charges a warp instruction whether or not its lanes are active).
+constexpr int TRI63 = (NB - 1) * NB / 2;  // entries of a size-63 lower triangle
 __global__ void __launch_bounds__(256) potrf_diag_kernel(double* A, int64_t lda, int j0, int nb, int* info) {
   __shared__ double S[NB][NB + 1];
+  __shared__ unsigned short tri[TRI63];  // e -> (i' << 8) | j', rows i' in order, 0 <= j' <= i'
   const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += 256) {
     const int i = e % NB, j = e / NB;
     S[i][j] = (i < nb && j < nb && i >= j) ? A[(j0 + i) + (int64_t)(j0 + j) * lda] : 0.0;
+  }
+  for (int e = tid; e < TRI63; e += 256) {
+    int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    while (r * (r + 1) / 2 > e) --r;
+    tri[e] = (unsigned short)((r << 8) | (e - r * (r + 1) / 2));
   }
   __syncthreads();
   for (int c = 0; c < nb; ++c) {
@@ -275,10 +290,11 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* A, int64_t lda,
     const double piv = S[c][c];
     for (int i = c + 1 + tid; i < nb; i += 256) S[i][c] /= piv;
     __syncthreads();
-    const int rem = nb - c - 1;
-    for (int e = tid; e < rem * rem; e += 256) {
-      const int i = c + 1 + e % rem, j = c + 1 + e / rem;
-      if (i >= j) S[i][j] -= S[i][c] * S[j][c];
+    const int rem = nb - c - 1, cnt = rem * (rem + 1) / 2;
+    for (int e = tid; e < cnt; e += 256) {
+      const int ij = tri[e];
+      const int i = c + 1 + (ij >> 8), j = c + 1 + (ij & 255);
+      S[i][j] = fma(-S[i][c], S[j][c], S[i][j]);
     }
     __syncthreads();
   }
@@ -313,24 +329,25 @@ __global__ void __launch_bounds__(128) trsm_panel_kernel(double* A, int64_t lda,
     if (c < nb) A[row + (int64_t)(j0 + c) * lda] = x[c];
 }
 
-// Trailing update A[i][j] -= sum_l L[i][j0+l] L[j][j0+l] on lower-triangle tiles.
-__global__ void __launch_bounds__(256) syrk_update_kernel(double* A, int64_t lda, int m, int j0, int nb) {
+// Trailing update A[i][j] -= sum_l L[i][j0+l] L[j][j0+l] on lower-triangle
+// 32x32 tiles (64 threads each).
+__global__ void __launch_bounds__(64) syrk_update_kernel(double* A, int64_t lda, int m, int j0, int nb) {
   const int bi = blockIdx.x, bj = blockIdx.y;
   if (bj > bi) return;
-  __shared__ double As[16][65];
-  __shared__ double Bs[16][65];
+  __shared__ double As[16][33];
+  __shared__ double Bs[16][33];
   const int start = j0 + nb;
-  const int r0 = start + bi * 64, c0 = start + bj * 64;
+  const int r0 = start + bi * 32, c0 = start + bj * 32;
   double acc[4][4] = {};
   TileMat Am{A, lda, r0, j0, m, j0 + nb};
   TileMat Bm{A, lda, c0, j0, m, j0 + nb};
-  tile_mm<true>(acc, Am, Bm, nb, As, Bs);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  tile_mm32<true>(acc, Am, Bm, nb, As, Bs);
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int r = r0 + tx + 16 * i, c = c0 + ty + 16 * j;
+      const int r = r0 + tx + 8 * i, c = c0 + ty + 8 * j;
       if (r < m && c < m && r >= c) A[r + (int64_t)c * lda] -= acc[i][j];
     }
 }
@@ -353,8 +370,8 @@ void cholesky(double* A, int m, int* info, cudaStream_t st, double* /*scratch*/)
     if (rem > 0) {
       trsm_panel_kernel<<<(rem + 127) / 128, 128, 0, st>>>(A, m, m, j0, nb);
       WC4D_LAUNCH_CHECK();
-      const int T = (rem + 63) / 64;
-      syrk_update_kernel<<<dim3(T, T), 256, 0, st>>>(A, m, m, j0, nb);
+      const int T = (rem + 31) / 32;
+      syrk_update_kernel<<<dim3(T, T), 64, 0, st>>>(A, m, m, j0, nb);
       WC4D_LAUNCH_CHECK();
     }
   }
@@ -393,46 +410,104 @@ __global__ void __launch_bounds__(64) trtri_diag_kernel(const double* L, int64_t
   }
 }
 
-// Block row i of W: W[i, cb] = Dinv_i * E[i, cb] for cb < i (cb == i is Dinv_i).
-__global__ void __launch_bounds__(256) trinv_rowapply_kernel(double* W, int m, int i, const double* Dinv) {
-  const int cb = blockIdx.x;
-  __shared__ double As[16][65];
-  __shared__ double Bs[16][65];
-  const int r0 = i * NB, c0 = cb * NB;
-  const int nb = min(NB, m - r0);
+// Blocked inverse W = L^{-1} (NB-row blocks, Dinv_i = L_ii^{-1}).  Forward
+// substitution on the identity E: for each block row i in turn,
+//   E[j, cb] -= (L_ji Dinv_i) E[i, cb]   for j > i, cb <= i,
+// and at the end W[i, cb] = Dinv_i E[i, cb] for all i, cb <= i at once (the
+// same products as scaling block row i before it is used, regrouped so that
+// only the updates form a serial chain).  All products on 32x32 tiles.
+
+// M_ji = L_ji Dinv_i for every block pair j > i (one launch; M in the layout of L)
+__global__ void __launch_bounds__(64) trinv_scale_kernel(const double* L, double* M, int m, const double* Dinv) {
+  const int nbk = (m + NB - 1) / NB;
+  int pair = blockIdx.x >> 2;  // (j, i) with j > i, enumerated row by row: j = 1.., i = 0..j-1
+  int j = 1;
+  while (pair >= j) {
+    pair -= j;
+    ++j;
+  }
+  const int i = pair, sub = blockIdx.x & 3;
+  if (j >= nbk) return;
+  __shared__ double As[16][33];
+  __shared__ double Bs[16][33];
+  const int r0 = j * NB + 32 * (sub & 1), cs = 32 * (sub >> 1);
   double acc[4][4] = {};
-  TileMat Am{Dinv + (int64_t)i * NB * NB, NB, 0, 0, NB, NB};
-  TileMat Bm{W, m, r0, c0, m, m};
-  tile_mm<false>(acc, Am, Bm, nb, As, Bs);
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  TileMat Am{L, m, r0, i * NB, m, m};
+  TileMat Bm{Dinv + (int64_t)i * NB * NB, NB, 0, cs, NB, NB};
+  tile_mm32<false>(acc, Am, Bm, NB, As, Bs);
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int bq = 0; bq < 4; ++bq) {
-      const int r = r0 + tx + 16 * a, c = c0 + ty + 16 * bq;
-      if (r < m && c < m) W[r + (int64_t)c * m] = acc[a][bq];
+    for (int b = 0; b < 4; ++b) {
+      const int r = r0 + tx + 8 * a, c = i * NB + cs + ty + 8 * b;
+      if (r < m) M[r + (int64_t)c * m] = acc[a][b];
     }
 }
 
-// Rows below: E[j, cb] -= L[j, i] * W[i, cb] for block rows j > i, cb <= i.
-__global__ void __launch_bounds__(256) trinv_update_kernel(const double* L, double* W, int m, int i) {
-  const int jb = i + 1 + blockIdx.x, cb = blockIdx.y;
-  __shared__ double As[16][65];
-  __shared__ double Bs[16][65];
-  const int r0 = jb * NB, c0 = cb * NB, k0 = i * NB;
-  const int K = min(NB, m - k0);
+// Step i: E[j, cb] -= M_ji E[i, cb] for block rows j > i, block columns cb <= i
+// (reads block row i, writes the rows below it: no overlap).
+__global__ void __launch_bounds__(64) trinv_update_kernel(const double* M, double* W, int m, int i) {
+  const int nsub = 4 * (i + 1);  // 32x32 sub-tiles per block row
+  const int jb = i + 1 + blockIdx.x / nsub, t = blockIdx.x % nsub;
+  const int cb = t >> 2, sub = t & 3;
+  __shared__ double As[16][33];
+  __shared__ double Bs[16][33];
+  const int r0 = jb * NB + 32 * (sub & 1), c0 = cb * NB + 32 * (sub >> 1), k0 = i * NB;
   double acc[4][4] = {};
-  TileMat Am{L, m, r0, k0, m, m};
+  TileMat Am{M, m, r0, k0, m, m};
   TileMat Bm{W, m, k0, c0, m, m};
-  tile_mm<false>(acc, Am, Bm, K, As, Bs);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  tile_mm32<false>(acc, Am, Bm, NB, As, Bs);
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int bq = 0; bq < 4; ++bq) {
-      const int r = r0 + tx + 16 * a, c = c0 + ty + 16 * bq;
-      if (r < m && c < m) W[r + (int64_t)c * m] -= acc[a][bq];
+    for (int b = 0; b < 4; ++b) {
+      const int r = r0 + tx + 8 * a, c = c0 + ty + 8 * b;
+      if (r < m && c < m) W[r + (int64_t)c * m] -= acc[a][b];
+    }
+}
+
+// W[i, cb] = Dinv_i E[i, cb] in place for every i and cb <= i: one CTA per
+// (block row, 32-column stripe) reads its whole 64 x 32 input before writing.
+__global__ void __launch_bounds__(128) trinv_finish_kernel(double* W, int m, const double* Dinv) {
+  int t = blockIdx.x >> 1;  // (i, cb) with cb <= i, row by row
+  int i = 0;
+  while (t > i) {
+    t -= i + 1;
+    ++i;
+  }
+  const int cb = t, half = blockIdx.x & 1;
+  const int r0 = i * NB, c0 = cb * NB + 32 * half;
+  const int nb = min(NB, m - r0);
+  __shared__ double Dt[NB][NB];  // Dt[k][r] = Dinv_i(r, k): lanes of a warp read consecutive r
+  __shared__ double E[NB][32];   // E[i, stripe]  (48 KB together)
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += 128) Dt[e / NB][e % NB] = Dinv[(int64_t)i * NB * NB + e];
+  for (int e = tid; e < NB * 32; e += 128) {
+    const int r = e % NB, c = e / NB;
+    E[r][c] = (r < nb && c0 + c < m) ? W[(r0 + r) + (int64_t)(c0 + c) * m] : 0.0;
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16 a, columns ty + 8 b
+  double acc[4][4] = {};
+  for (int k = 0; k < nb; ++k) {
+    double d[4], e[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) d[a] = Dt[k][tx + 16 * a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) e[b] = E[k][ty + 8 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(d[a], e[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = tx + 16 * a, c = c0 + ty + 8 * b;
+      if (r < nb && c < m) W[(r0 + r) + (int64_t)c * m] = acc[a][b];
     }
 }
 
@@ -445,21 +520,24 @@ __global__ void identity_kernel(double* W, int m) {
   }
 }
 
-// W = L^{-1} by blocked forward substitution on the identity (right-looking).
+// W = L^{-1} (the scheme above); Wt = W^T.  Wt serves as the M_ji buffer
+// until the final transpose overwrites it.
 void tri_inverse(const double* L, double* W, double* Wt, int m, cudaStream_t st, double* scratch) {
   const int nbk = (m + NB - 1) / NB;
   identity_kernel<<<nblk((int64_t)m * m), 256, 0, st>>>(W, m);
   note_launch();
   trtri_diag_kernel<<<nbk, 64, 0, st>>>(L, m, m, scratch);
   WC4D_LAUNCH_CHECK();
-  for (int i = 0; i < nbk; ++i) {
-    trinv_rowapply_kernel<<<i + 1, 256, 0, st>>>(W, m, i, scratch);
+  if (nbk > 1) {
+    trinv_scale_kernel<<<4 * (nbk * (nbk - 1) / 2), 64, 0, st>>>(L, Wt, m, scratch);
     WC4D_LAUNCH_CHECK();
-    if (i + 1 < nbk) {
-      trinv_update_kernel<<<dim3(nbk - i - 1, i + 1), 256, 0, st>>>(L, W, m, i);
+    for (int i = 0; i + 1 < nbk; ++i) {
+      trinv_update_kernel<<<(nbk - i - 1) * 4 * (i + 1), 64, 0, st>>>(Wt, W, m, i);
       WC4D_LAUNCH_CHECK();
     }
   }
+  trinv_finish_kernel<<<2 * (nbk * (nbk + 1) / 2), 128, 0, st>>>(W, m, scratch);
+  WC4D_LAUNCH_CHECK();
   launch_transpose(W, Wt, m, st);
 }
 
