@@ -304,29 +304,56 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(double* A, int64_t lda,
   }
 }
 
-// Panel: rows i >= j0+nb solve x L11^T = a (one thread per row).
-__global__ void __launch_bounds__(128) trsm_panel_kernel(double* A, int64_t lda, int m, int j0, int nb) {
-  __shared__ double L11[NB][NB + 1];
-  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+// Panel: rows i >= j0+nb solve x L11^T = a.  One CTA per 32 rows (lane =
+// row), eight warps: warp w owns columns 8w..8w+7.  For column block b, warp b
+// finishes its eight columns by substitution and publishes them; warps w > b
+// subtract their contribution.  Every x_c accumulates its terms in increasing
+// l with the same FMAs and division as a one-thread-per-row substitution (the
+// results are identical), but the FP64 work of a row spreads over the four
+// SM sub-partitions instead of one lane's serial chain.
+__global__ void __launch_bounds__(256) trsm_panel_kernel(double* A, int64_t lda, int m, int j0, int nb) {
+  __shared__ double L11[NB][NB];  // 32 KB
+  __shared__ double X[NB][32];    // solved x_c of the CTA's 32 rows (16 KB)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
     const int i = e % NB, j = e / NB;
     L11[i][j] = (i < nb && j < nb) ? A[(j0 + i) + (int64_t)(j0 + j) * lda] : (i == j ? 1.0 : 0.0);
   }
+  const int row = j0 + nb + blockIdx.x * 32 + lane;
+  const bool valid = row < m;
+  double a[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = 8 * warp + q;
+    a[q] = (valid && c < nb) ? A[row + (int64_t)(j0 + c) * lda] : 0.0;
+  }
   __syncthreads();
-  const int row = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= m) return;
-  double x[NB];
+  for (int b = 0; b < NB / 8; ++b) {
+    if (warp == b) {
 #pragma unroll
-  for (int c = 0; c < NB; ++c) x[c] = (c < nb) ? A[row + (int64_t)(j0 + c) * lda] : 0.0;
+      for (int q = 0; q < 8; ++q) {
+        const int c = 8 * b + q;
+        double v = a[q];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    double v = x[c];
+        for (int l = 0; l < q; ++l) v -= X[8 * b + l][lane] * L11[c][8 * b + l];
+        X[c][lane] = v / L11[c][c];
+      }
+    }
+    __syncthreads();
+    if (warp > b) {
 #pragma unroll
-    for (int l = 0; l < c; ++l) v -= x[l] * L11[c][l];
-    x[c] = v / L11[c][c];
+      for (int q = 0; q < 8; ++q) {
+        const int c = 8 * warp + q;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) a[q] -= X[8 * b + l][lane] * L11[c][8 * b + l];
+      }
+    }
   }
 #pragma unroll
-  for (int c = 0; c < NB; ++c)
-    if (c < nb) A[row + (int64_t)(j0 + c) * lda] = x[c];
+  for (int q = 0; q < 8; ++q) {
+    const int c = 8 * warp + q;
+    if (valid && c < nb) A[row + (int64_t)(j0 + c) * lda] = X[c][lane];
+  }
 }
 
 // Trailing update A[i][j] -= sum_l L[i][j0+l] L[j][j0+l] on lower-triangle
@@ -368,7 +395,7 @@ void cholesky(double* A, int m, int* info, cudaStream_t st, double* /*scratch*/)
     WC4D_LAUNCH_CHECK();
     const int rem = m - j0 - nb;
     if (rem > 0) {
-      trsm_panel_kernel<<<(rem + 127) / 128, 128, 0, st>>>(A, m, m, j0, nb);
+      trsm_panel_kernel<<<(rem + 31) / 32, 256, 0, st>>>(A, m, m, j0, nb);
       WC4D_LAUNCH_CHECK();
       const int T = (rem + 31) / 32;
       syrk_update_kernel<<<dim3(T, T), 64, 0, st>>>(A, m, m, j0, nb);
