@@ -663,6 +663,17 @@ def run_profile(args):
         G.apply_precond(args.precond, v)
     ev[2].record()
     torch.cuda.synchronize()
+    # the library's own accounting of one A v launch and one P^-1 v (two launches)
+    acct = {}
+    for name, fn in (("apply_saddle", lambda: G.apply_saddle(v)), ("apply_precond", lambda: G.apply_precond(args.precond, v))):
+        wc4d.wc4d_set_profiling(1)
+        wc4d.wc4d_reset_stats()
+        fn()
+        st = wc4d.wc4d_get_stats()
+        wc4d.wc4d_set_profiling(0)
+        acct[name] = {"product_launches": st.gemmtc_launches + st.gemmdf_launches,
+                      "bytes": st.gemmtc_bytes, "fp64_class_flops": st.gemmtc_flops + st.gemmdf_flops,
+                      "bf16_mma_flops": st.gemmtc_mma_flops, "ms": st.gemmtc_ms + st.gemmdf_ms}
     rhs = G.synthesize_rhs(dr)
     x = torch.zeros_like(rhs)
     t0 = time.perf_counter()
@@ -670,8 +681,8 @@ def run_profile(args):
     torch.cuda.synchronize()
     G.close()
     print(json.dumps({"workload": "profile", "precision": o.precision, "apply_saddle_ms": ev[0].elapsed_time(ev[1]) / 4,
-                      "apply_precond_ms": ev[1].elapsed_time(ev[2]) / 4, "solve_steps": args.maxit,
-                      "solve_ms": (time.perf_counter() - t0) * 1e3}))
+                      "apply_precond_ms": ev[1].elapsed_time(ev[2]) / 4, "product_accounting": acct,
+                      "solve_steps": args.maxit, "solve_ms": (time.perf_counter() - t0) * 1e3}))
 
 
 def main():

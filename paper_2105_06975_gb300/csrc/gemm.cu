@@ -521,6 +521,27 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
     const int off = (c % cw) * bm + (r % bm);
     const int64_t slot_elems = (int64_t)bm * GEMM_BN;
     T acc = T(0);
+    // the epilogue operands do not depend on the partials: load them first so
+    // their latency overlaps the slot-index / partial chain below
+    const EpiT<T>& ep = epis.e[o];
+    T pre = T(0);
+    switch (ep.mode) {
+      case EPI_SADDLE_C1: {
+        const int t = c + ep.t0;
+        const int s = md.s;
+        pre = ep.v3[(int64_t)t * s + r];
+        if (t >= 1) pre -= model_apply<T>(md, t, ep.v3 + (int64_t)(t - 1) * s, r);
+        break;
+      }
+      case EPI_SADDLE_C2:
+        pre = ep.v3[(int64_t)(c + ep.t0) * md.s + obs[r]];
+        break;
+      case EPI_SUB_FROM:
+        pre = ep.Y[r + (int64_t)c * ep.ldc];
+        break;
+      default:
+        break;
+    }
     // slots in batches of 8: the slot indices, then the partials, are loaded
     // together (independent loads in flight) and summed in slot order
     constexpr int RB = 8;
@@ -559,24 +580,14 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
         }
       }
     }
-    const EpiT<T>& ep = epis.e[o];
     T val;
     switch (ep.mode) {
-      case EPI_SADDLE_C1: {
-        const int t = c + ep.t0;
-        const int s = md.s;
-        T lv = ep.v3[(int64_t)t * s + r];
-        if (t >= 1) lv -= model_apply<T>(md, t, ep.v3 + (int64_t)(t - 1) * s, r);
-        val = acc + lv;
+      case EPI_SADDLE_C1:
+      case EPI_SADDLE_C2:
+        val = acc + pre;
         break;
-      }
-      case EPI_SADDLE_C2: {
-        const int t = c + ep.t0;
-        val = acc + ep.v3[(int64_t)t * md.s + obs[r]];
-        break;
-      }
       case EPI_SUB_FROM:
-        val = ep.Y[r + (int64_t)c * ep.ldc] - acc;
+        val = pre - acc;
         break;
       case EPI_NEG_STORE:
         val = -acc;

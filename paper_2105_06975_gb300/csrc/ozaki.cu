@@ -109,32 +109,40 @@ __device__ __forceinline__ uint64_t max_mag_bits(const double* __restrict__ src,
   return mx[0];
 }
 
+// The digits of the 8 consecutive entries x[0..8) = k 8g..8g+7 of a row /
+// column into its tiles (position r of the tile's 128 (64) rows).
+__device__ __forceinline__ void store_group_digits(const double x[8], int g, int emax, uint16_t* tiles,
+                                                   int64_t tile_elems, int r) {
+  const int k0 = 8 * g, kb = k0 >> 4, kh = (k0 >> 3) & 1;
+  int dg[8][OZ_DIGITS];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) digits7(x[q], emax, dg[q]);
+  uint16_t* base = tiles + (int64_t)kb * OZ_DIGITS * tile_elems + (r >> 3) * 128 + kh * 64 + (r & 7) * 8;
+#pragma unroll
+  for (int t = 0; t < OZ_DIGITS; ++t) {
+    uint4 v;
+    v.x = bf16_pair(dg[0][t], dg[1][t]);
+    v.y = bf16_pair(dg[2][t], dg[3][t]);
+    v.z = bf16_pair(dg[4][t], dg[5][t]);
+    v.w = bf16_pair(dg[6][t], dg[7][t]);
+    *reinterpret_cast<uint4*>(base + t * tile_elems) = v;
+  }
+}
+
 // Digits of one row (operator) or column (X) of length kdim, padded to nkb
 // blocks of 16, into tile rt/ct at position r of its 128 (64) rows.
 // src == nullptr or a padding row writes zero digits.
 __device__ __forceinline__ void write_digits(const double* src, int kdim, int nkb, int emax, uint16_t* tiles,
-                                             int64_t tile_elems, int rows, int r) {
+                                             int64_t tile_elems, int r) {
   for (int g = threadIdx.x; g < 2 * nkb; g += blockDim.x) {
-    const int k0 = 8 * g, kb = k0 >> 4, kh = (k0 >> 3) & 1;
-    int dg[8][OZ_DIGITS];
+    double x[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int k = k0 + q;
-      const double a = (src != nullptr && k < kdim) ? src[k] : 0.0;
-      digits7(a, emax, dg[q]);
+      const int k = 8 * g + q;
+      x[q] = (src != nullptr && k < kdim) ? src[k] : 0.0;
     }
-    uint16_t* base = tiles + (int64_t)kb * OZ_DIGITS * tile_elems + (r >> 3) * 128 + kh * 64 + (r & 7) * 8;
-#pragma unroll
-    for (int t = 0; t < OZ_DIGITS; ++t) {
-      uint4 v;
-      v.x = bf16_pair(dg[0][t], dg[1][t]);
-      v.y = bf16_pair(dg[2][t], dg[3][t]);
-      v.z = bf16_pair(dg[4][t], dg[5][t]);
-      v.w = bf16_pair(dg[6][t], dg[7][t]);
-      *reinterpret_cast<uint4*>(base + t * tile_elems) = v;
-    }
+    store_group_digits(x, g, emax, tiles, tile_elems, r);
   }
-  (void)rows;
 }
 
 // one CTA per padded row i of op(At)
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(128) oz_rows_kernel(const double* __restrict__
   const int emax = (int)(mx >> 52);
   if (threadIdx.x == 0) As[i] = row ? scale_of(emax) : 0.f;
   const int rt = i / OZ_BM, r = i % OZ_BM;
-  write_digits(row, kdim, nkb, emax, Ad + (int64_t)rt * nkb * OZ_DIGITS * OZ_A_TILE, OZ_A_TILE, OZ_BM, r);
+  write_digits(row, kdim, nkb, emax, Ad + (int64_t)rt * nkb * OZ_DIGITS * OZ_A_TILE, OZ_A_TILE, r);
 }
 
 // one CTA per (op, wide column tile, column of the tile), and one per op for
@@ -172,12 +180,39 @@ __global__ void __launch_bounds__(128) oz_cols_kernel(OzColJobs jobs) {
   const int ct = local / OZ_BN, cl = local % OZ_BN;
   const int c = ct * OZ_BN + cl;
   const double* col = (c < jb.ncols) ? jb.X + (int64_t)c * jb.ldx : nullptr;
+  uint16_t* tiles = jb.Xd + (int64_t)ct * jb.nkb * OZ_DIGITS * OZ_X_TILE;
+  const int ngroups = 2 * jb.nkb;
+  constexpr int GR = 2;  // groups of 8 entries a thread keeps in registers (k <= 2048 with 128 threads)
+  if (ngroups <= GR * (int)blockDim.x) {
+    // one read of the column: the maximum and the digits from the same registers
+    double x[GR][8];
+    uint64_t mx = 0;
+#pragma unroll
+    for (int gi = 0; gi < GR; ++gi) {
+      const int g = threadIdx.x + gi * blockDim.x;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = 8 * g + q;
+        x[gi][q] = (col != nullptr && g < ngroups && k < jb.kdim) ? col[k] : 0.0;
+        const uint64_t v = mag_bits(x[gi][q]);
+        mx = v > mx ? v : mx;
+      }
+    }
+    mx = block_max_u64(mx, red);
+    const int emax = (int)(mx >> 52);
+    if (threadIdx.x == 0) jb.Xs[c] = col ? scale_of(emax) : 0.f;
+#pragma unroll
+    for (int gi = 0; gi < GR; ++gi) {
+      const int g = threadIdx.x + gi * blockDim.x;
+      if (g < ngroups) store_group_digits(x[gi], g, emax, tiles, OZ_X_TILE, cl);
+    }
+    return;
+  }
   uint64_t mx = col ? max_mag_bits(col, jb.kdim) : 0ull;
   mx = block_max_u64(mx, red);
   const int emax = (int)(mx >> 52);
   if (threadIdx.x == 0) jb.Xs[c] = col ? scale_of(emax) : 0.f;
-  write_digits(col, jb.kdim, jb.nkb, emax, jb.Xd + (int64_t)ct * jb.nkb * OZ_DIGITS * OZ_X_TILE, OZ_X_TILE, OZ_BN,
-               cl);
+  write_digits(col, jb.kdim, jb.nkb, emax, tiles, OZ_X_TILE, cl);
 }
 
 // ----------------------------------------------------------- tcgen05 kernel
