@@ -218,8 +218,18 @@ MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
 # DRAM bytes per launch of gemm_streamk_df32_kernel, ncu dram__bytes_read.sum + dram__bytes_write.sum,
 # mean over the three product launches of one GMRES step (P_I level 1, P_I level 2, A v) at the scale
 # workload; captured on a GB300 (summary and command in profiles/gemm_streamk_df32__advdiff_s2048_N64.md).
-# Valid while that kernel is unchanged; the other kernels report no traffic.
+# Valid while that kernel is unchanged.
 GEMM_DF32_TRAFFIC_BYTES = 53.3e6
+# DRAM bytes (read + write) over algorithmic bytes of one captured launch, for kernels whose
+# bytes per launch vary with the launch (Arnoldi step j, product type): traffic per launch =
+# ratio x the live algorithmic bytes per launch.  Captured on a GB300 with
+# `bench.py --workload profile --maxit 110` (summaries and commands in profiles/).
+TRAFFIC_RATIO = {
+    "orth": (0.9934, "ncu dram bytes of gm_dc_dot + gm_dc_update at Arnoldi step j = 99 (544.8 MB) over their "
+                     "algorithmic bytes (548.5 MB), profiles/gm_dc_arnoldi__advdiff_s2048_N64.md"),
+    "gemm_tc": (0.947, "ncu dram bytes of one A v launch of gemm_tc_kernel (123.2 MB) over its algorithmic "
+                       "bytes (130.1 MB), profiles/gemm_tc__advdiff_s2048_N64.md"),
+}
 
 
 def kernel_rows(st, step_ms, hbm, dcgs=False):
@@ -413,6 +423,11 @@ def run_gpu(args):
         if roof["traffic"] is not None:
             roof["traffic_source"] = ("ncu dram bytes read+write per launch, mean of one GMRES step's three "
                                       "product launches (profiles/gemm_streamk_df32__advdiff_s2048_N64.md)")
+        dom_key = next(k for k, r in ks.items() if r is dom)
+        if dom_key in TRAFFIC_RATIO and dom.get("bytes_per_launch"):
+            ratio, src = TRAFFIC_RATIO[dom_key]
+            roof["traffic"] = ratio * dom["bytes_per_launch"]
+            roof["traffic_source"] = src + "; scaled to this run's mean algorithmic bytes per launch"
     # whole-solve bound: the FP64-class products at the DF32 peak vs the Arnoldi and operator bytes at HBM
     st_c = chosen["stats"]
     solve_roof = None
