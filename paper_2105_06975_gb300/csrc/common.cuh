@@ -39,6 +39,29 @@ void note_launch();
     ::wc4d::note_launch();                 \
     WC4D_CUDA(cudaGetLastError());         \
   } while (0)
+// Programmatic dependent launch (the kernels of a GMRES step): each such
+// kernel starts with pdl_wait() -- it returns once the preceding grid has
+// completed and its writes are visible (immediately for a plain launch) --
+// and then pdl_trigger(), which lets the next grid launch and reach its own
+// pdl_wait() while this one runs.  Nothing is read before pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 #define WC4D_CHECK(cond, code, msg)                        \
   do {                                                     \
     if (!(cond)) throw ::wc4d::Error{(code), (msg)};       \

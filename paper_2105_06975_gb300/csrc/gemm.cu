@@ -505,6 +505,8 @@ __global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT
                                                           const int* __restrict__ tile_start,
                                                           const int* __restrict__ tile_slots, ModelDev md,
                                                           const int* __restrict__ obs, const int* __restrict__ done) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < meta.total;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -652,8 +654,8 @@ void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis
   WC4D_CHECK(plan.bm == GEMM_BM || (sizeof(T) == 8 && ops.tc), WC4D_ERR_ARG,
              "internal: tensor-core plan run without the tensor-core operands");
   const int64_t nb = std::min<int64_t>((plan.total_out + 255) / 256, 152 * 8);
-  gemm_reduce_kernel<T><<<(int)nb, 256, 0, st>>>(meta, epis, partial, plan.d_tile_start, plan.d_tile_slots, model,
-                                                 obs, done);
+  WC4D_CUDA(launch_pdl(gemm_reduce_kernel<T>, dim3((unsigned)nb), dim3(256), 0, st, meta, epis, (const T*)partial,
+                       (const int*)plan.d_tile_start, (const int*)plan.d_tile_slots, model, obs, done));
   WC4D_LAUNCH_CHECK();
 }
 

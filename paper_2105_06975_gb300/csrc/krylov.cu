@@ -245,6 +245,8 @@ template void gm_mdot<float>(const float*, int64_t, int, const float*, int64_t, 
 
 // h[i] = sum over chunks of part[i * nchunks + c], fixed order
 __global__ void gm_mdot_reduce_kernel(const double* part, int nchunks, double* h, const int* done) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   __shared__ double sh[32];
   const double* p = part + (int64_t)blockIdx.x * nchunks;
@@ -254,7 +256,7 @@ __global__ void gm_mdot_reduce_kernel(const double* part, int nchunks, double* h
   if (threadIdx.x == 0) h[blockIdx.x] = v;
 }
 void gm_mdot_reduce(const double* part, int cnt, int nchunks, double* h, const int* done, cudaStream_t st) {
-  gm_mdot_reduce_kernel<<<cnt, DOT_THREADS, 0, st>>>(part, nchunks, h, done);
+  WC4D_CUDA(launch_pdl(gm_mdot_reduce_kernel, dim3(cnt), dim3(DOT_THREADS), 0, st, part, nchunks, h, done));
   WC4D_LAUNCH_CHECK();
 }
 
@@ -696,6 +698,8 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
                                                                 const float* __restrict__ wl, int64_t n4,
                                                                 double* __restrict__ part, const int* done,
                                                                 int* ran) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   if (ran != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ran = 1;
   __shared__ float2 sh[DOT_THREADS / 32][2 * ORTH_G + 1];
@@ -768,7 +772,7 @@ void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float
   int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st);
   const int64_t n4 = (n + 3) / 4;
   dim3 grid((unsigned)dot_chunks(n, j + 1), (j + 1 + ORTH_G - 1) / ORTH_G);
-  gm_dc_dot_kernel<<<grid, DOT_THREADS, 0, st>>>(Vh, Vl, ldv, j, wh, wl, n4, part, done, ran);
+  WC4D_CUDA(launch_pdl(gm_dc_dot_kernel, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done, ran));
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
 }
@@ -867,6 +871,8 @@ __global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const double* __
                                                          const double* bnorm, const double* __restrict__ hc) {
   extern __shared__ double sm[];
   __shared__ double sh[64];
+  pdl_wait();
+  pdl_trigger();
   if (*(volatile const int*)&stat->done) return;
   const int cnt = j + 1;
   const double* a = red;        // a_0..a_j
@@ -980,8 +986,8 @@ void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cpr
                 double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
                 const double* bnorm, const double* hc, cudaStream_t st) {
   const size_t smem = sizeof(double) * (3 * (size_t)j + 2);  // column + rotations
-  gm_dc_coef_kernel<<<1, 256, smem, st>>>(j, red, dc, bprev, cprev, e, Hraw, H, T, ldh, cs, sn, g, hnext, stat,
-                                          bnorm, hc);
+  WC4D_CUDA(launch_pdl(gm_dc_coef_kernel, dim3(1), dim3(256), smem, st, j, red, dc, bprev, cprev, e, Hraw, H, T, ldh,
+                       cs, sn, g, hnext, stat, bnorm, hc));
   WC4D_LAUNCH_CHECK();
 }
 
@@ -1000,6 +1006,8 @@ __global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, fl
                                                                    const double* __restrict__ Hraw, int ldh,
                                                                    double* __restrict__ hc, const int* done,
                                                                    int* ran) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
   // hc = Hbar_j c_j for the next step's coefficient kernel: raw Hessenberg
@@ -1114,8 +1122,8 @@ void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, con
   int* ran = prof_begin(PROF_ORTH, (double)(j + 1) * n * 8.0 + 4.0 * n * 8.0, st);
   const int64_t n4 = (n + 3) / 4;
   const int nb = (int)std::min<int64_t>((n4 + UPD_THREADS - 1) / UPD_THREADS, 152 * 64);
-  gm_dc_update_kernel<<<nb, UPD_THREADS, sizeof(float) * 4 * std::max(j, 1), st>>>(Vh, Vl, ldv, j, e, c, dc, w, v, n,
-                                                                                  Hraw, ldh, hc, done, ran);
+  WC4D_CUDA(launch_pdl(gm_dc_update_kernel, dim3(nb), dim3(UPD_THREADS), sizeof(float) * 4 * std::max(j, 1), st, Vh, Vl,
+                       ldv, j, e, c, dc, w, v, n, Hraw, ldh, hc, done, ran));
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
 }

@@ -15,6 +15,8 @@ namespace wc4d {
 template <typename T>
 __global__ void __launch_bounds__(1024) lhat_sweep_kernel(ModelDev md, int k, const T* v, T* z, int transpose,
                                                           int identity_model, const int* done) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   const int s = md.s, T1 = md.N + 1;
   const int t0 = blockIdx.x * k;
@@ -77,6 +79,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) lhat_sweep_seg_kernel(ModelDev md, int k, const T* __restrict__ v,
                                                              T* __restrict__ z, int transpose, int identity_model,
                                                              int W, int R, const int* done) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   extern __shared__ unsigned char smraw[];
   T* bufA = reinterpret_cast<T*>(smraw);
@@ -129,13 +133,14 @@ void lhat_sweep(const ModelDev& md, int k, const T* v, T* z, bool transpose, boo
   const bool alias = (const void*)v == (const void*)z;
   if (nseg > 1 && !alias && steps > 0 && 2 * R * steps <= W && E <= s &&
       (size_t)E * 2 * sizeof(T) <= 48 * 1024) {
-    lhat_sweep_seg_kernel<T><<<dim3(nchunks, nseg), 256, (size_t)E * 2 * sizeof(T), st>>>(
-        md, k, v, z, transpose ? 1 : 0, identity_model ? 1 : 0, W, R, done);
+    WC4D_CUDA(launch_pdl(lhat_sweep_seg_kernel<T>, dim3(nchunks, nseg), dim3(256), (size_t)E * 2 * sizeof(T), st, md, k,
+                         v, z, transpose ? 1 : 0, identity_model ? 1 : 0, W, R, done));
     WC4D_LAUNCH_CHECK();
     return;
   }
   const int threads = std::min(1024, ((md.s + 31) / 32) * 32);
-  lhat_sweep_kernel<T><<<nchunks, threads, 0, st>>>(md, k, v, z, transpose ? 1 : 0, identity_model ? 1 : 0, done);
+  WC4D_CUDA(launch_pdl(lhat_sweep_kernel<T>, dim3(nchunks), dim3(threads), 0, st, md, k, v, z, transpose ? 1 : 0,
+                       identity_model ? 1 : 0, done));
   WC4D_LAUNCH_CHECK();
 }
 template void lhat_sweep<double>(const ModelDev&, int, const double*, double*, bool, bool, const int*, cudaStream_t);
@@ -153,6 +158,8 @@ template <typename T>
 __global__ void saddle_c3_kernel(ModelDev md, const T* __restrict__ v1, const T* __restrict__ v2,
                                  const int* __restrict__ inv, int p, T* __restrict__ c3, float* __restrict__ c3h,
                                  float* __restrict__ c3l, const int* done) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   const int s = md.s, N = md.N;
   const int64_t total = (int64_t)(N + 1) * s;
@@ -177,14 +184,15 @@ void saddle_c3(const ModelDev& md, const T* v1, const T* v2, const int* inv, int
                cudaStream_t st) {
   const int64_t total = (int64_t)(md.N + 1) * md.s;
   const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-  saddle_c3_kernel<T><<<nb, 256, 0, st>>>(md, v1, v2, inv, p, c3, nullptr, nullptr, done);
+  WC4D_CUDA(launch_pdl(saddle_c3_kernel<T>, dim3(nb), dim3(256), 0, st, md, v1, v2, inv, p, c3, (float*)nullptr,
+                       (float*)nullptr, done));
   WC4D_LAUNCH_CHECK();
 }
 void saddle_c3_split(const ModelDev& md, const double* v1, const double* v2, const int* inv, int p, double* c3,
                      float* c3h, float* c3l, const int* done, cudaStream_t st) {
   const int64_t total = (int64_t)(md.N + 1) * md.s;
   const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-  saddle_c3_kernel<double><<<nb, 256, 0, st>>>(md, v1, v2, inv, p, c3, c3h, c3l, done);
+  WC4D_CUDA(launch_pdl(saddle_c3_kernel<double>, dim3(nb), dim3(256), 0, st, md, v1, v2, inv, p, c3, c3h, c3l, done));
   WC4D_LAUNCH_CHECK();
 }
 template void saddle_c3<double>(const ModelDev&, const double*, const double*, const int*, int, double*, const int*,

@@ -163,6 +163,8 @@ __global__ void __launch_bounds__(128) oz_rows_kernel(const double* __restrict__
 // the double-float split of its one-column (GEMV) column
 __global__ void __launch_bounds__(128) oz_cols_kernel(OzColJobs jobs) {
   __shared__ uint64_t red[4];
+  pdl_wait();
+  pdl_trigger();
   int o = 0;
   while (o + 1 < jobs.n && (int)blockIdx.x >= jobs.cta_base[o + 1]) ++o;
   const OzColJob& jb = jobs.j[o];
@@ -347,6 +349,8 @@ __device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_tc_kernel(GemmOpsT<double> ops, const GemmSeg* __restrict__ segs, const int* __restrict__ seg_start,
                    float2* __restrict__ partial, const int* __restrict__ done, int* ran, int* err) {
+  pdl_wait();
+  pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
   extern __shared__ __align__(1024) unsigned char oz_smem[];
@@ -573,7 +577,7 @@ void launch_oz_rows(const double* At, int64_t lda, int m, int kdim, uint16_t* Ad
 void launch_oz_cols(const OzColJobs& jobs, cudaStream_t st) {
   const int ctas = jobs.cta_base[jobs.n];
   if (jobs.n == 0 || ctas == 0) return;
-  oz_cols_kernel<<<ctas, 128, 0, st>>>(jobs);
+  WC4D_CUDA(launch_pdl(oz_cols_kernel, dim3(ctas), dim3(128), 0, st, jobs));
   WC4D_LAUNCH_CHECK();
 }
 
@@ -583,8 +587,8 @@ void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int*
   std::call_once(once, [] {
     WC4D_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   });
-  gemm_tc_kernel<<<nctas, OZ_THREADS, OZ_SMEM, st>>>(ops, segs, seg_start, reinterpret_cast<float2*>(partial), done,
-                                                     ran, err);
+  WC4D_CUDA(launch_pdl(gemm_tc_kernel, dim3(nctas), dim3(OZ_THREADS), OZ_SMEM, st, ops, segs, seg_start,
+                       reinterpret_cast<float2*>(partial), done, ran, err));
   WC4D_LAUNCH_CHECK();
 }
 

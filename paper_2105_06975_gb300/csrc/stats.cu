@@ -49,8 +49,8 @@ int* prof_begin(int cls, double work, cudaStream_t st, double work2, double work
   Profile& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   if (!p.on || (int)p.recs.size() >= p.cap) return nullptr;
+  // the flag slot is zero: slots are cleared when allocated and on every reset
   Rec r{get_event(p), get_event(p), cls, work, (int)p.recs.size(), work2, work3};
-  WC4D_CUDA(cudaMemsetAsync(p.d_flags + r.flag, 0, sizeof(int), st));
   WC4D_CUDA(cudaEventRecord(r.e0, st));
   p.recs.push_back(r);
   return p.d_flags + r.flag;
@@ -73,7 +73,9 @@ void wc4d_set_profiling(int32_t enable) {
   std::lock_guard<std::mutex> lk(p.mu);
   if (enable && !p.d_flags) {
     p.cap = 1 << 20;
-    if (cudaMalloc(&p.d_flags, sizeof(int) * p.cap) != cudaSuccess) {
+    if (cudaMalloc(&p.d_flags, sizeof(int) * p.cap) != cudaSuccess ||
+        cudaMemset(p.d_flags, 0, sizeof(int) * p.cap) != cudaSuccess) {
+      cudaFree(p.d_flags);
       p.d_flags = nullptr;
       p.cap = 0;
       return;
@@ -87,6 +89,7 @@ void wc4d_reset_stats(void) {
   Profile& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   cudaDeviceSynchronize();
+  if (p.d_flags && !p.recs.empty()) cudaMemset(p.d_flags, 0, sizeof(int) * p.recs.size());
   for (auto& r : p.recs) {
     p.pool.push_back(r.e0);
     p.pool.push_back(r.e1);
