@@ -1,5 +1,6 @@
 // Internal declarations shared by the wc4d translation units.
 #pragma once
+#include <memory>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -324,6 +325,7 @@ struct GemmPlan {
   double tc_bytes = 0;            // tensor-core plan: operator digit tiles and GEMV operands read once,
                                   // X digit tiles once per op, partial tiles written
   double tc_mma_flops = 0;        // tensor-core plan: BF16 flops of the issued digit products
+  std::shared_ptr<void> owner;    // keeps the device arrays alive (plans are shared through a cache)
 };
 
 // cost model of the schedule: which product kernel the plan will mostly run

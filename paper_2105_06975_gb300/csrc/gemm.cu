@@ -12,6 +12,10 @@
 // A v, the v1 - D c1 of P_I).
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
 
 #include "common.cuh"
 #include "model_dev.cuh"
@@ -20,17 +24,45 @@
 namespace wc4d {
 
 // --------------------------------------------------------------- planning
-void plan_free(GemmPlan& plan) {
-  cudaFree(plan.d_seg_start);
-  cudaFree(plan.d_segs);
-  cudaFree(plan.d_tile_start);
-  cudaFree(plan.d_tile_slots);
-  plan = GemmPlan();
+// A plan is a pure function of (device, op shapes, CTA count, cost model) and
+// read-only on the device once built, so built plans are kept in a bounded
+// process-wide cache and shared: a problem of the same shapes as an earlier
+// one (the next assimilation window, a benchmark step) reuses its schedule
+// instead of rebuilding it and paying for device allocations and copies.
+namespace {
+struct PlanArrays {
+  void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  ~PlanArrays() {
+    for (void* q : p) cudaFree(q);
+  }
+};
+std::mutex g_plan_mu;
+std::map<std::string, GemmPlan>& plan_cache() {
+  static std::map<std::string, GemmPlan> c;
+  return c;
 }
+constexpr size_t PLAN_CACHE_MAX = 512;
+}  // namespace
+
+void plan_free(GemmPlan& plan) { plan = GemmPlan(); }
 
 void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas, int cost_model) {
   plan_free(plan);
   WC4D_CHECK((int)shapes.size() <= GEMM_MAX_OPS, WC4D_ERR_ARG, "too many GEMM ops in one launch");
+  int dev = 0;
+  WC4D_CUDA(cudaGetDevice(&dev));
+  std::string key = std::to_string(dev) + ":" + std::to_string(max_ctas) + ":" + std::to_string(cost_model);
+  for (const OpShape& sh : shapes)
+    key += ":" + std::to_string(sh.m) + "," + std::to_string(sh.kdim) + "," + std::to_string(sh.ncols) + "," +
+           std::to_string(sh.tri);
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = plan_cache().find(key);
+    if (it != plan_cache().end()) {
+      plan = it->second;
+      return;
+    }
+  }
   plan.nops = (int)shapes.size();
   // the tensor-core plan: 128-row tiles, segments of at most OZ_KMAX k (exact
   // FP32 accumulation of the digit products)
@@ -212,14 +244,23 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
   tstart[tiles.size()] = (int)tslots.size();
   if (tslots.empty()) tslots.push_back(0);
   if (segs.empty()) segs.push_back(GemmSeg{0, 0, 0, 0, 0, 0, 1});
-  WC4D_CUDA(cudaMalloc(&plan.d_seg_start, sizeof(int) * seg_start.size()));
-  WC4D_CUDA(cudaMalloc(&plan.d_segs, sizeof(GemmSeg) * segs.size()));
-  WC4D_CUDA(cudaMalloc(&plan.d_tile_start, sizeof(int) * tstart.size()));
-  WC4D_CUDA(cudaMalloc(&plan.d_tile_slots, sizeof(int) * tslots.size()));
+  auto arrays = std::make_shared<PlanArrays>();
+  plan.owner = arrays;
+  WC4D_CUDA(cudaMalloc(&arrays->p[0], sizeof(int) * seg_start.size()));
+  WC4D_CUDA(cudaMalloc(&arrays->p[1], sizeof(GemmSeg) * segs.size()));
+  WC4D_CUDA(cudaMalloc(&arrays->p[2], sizeof(int) * tstart.size()));
+  WC4D_CUDA(cudaMalloc(&arrays->p[3], sizeof(int) * tslots.size()));
+  plan.d_seg_start = (int*)arrays->p[0];
+  plan.d_segs = (GemmSeg*)arrays->p[1];
+  plan.d_tile_start = (int*)arrays->p[2];
+  plan.d_tile_slots = (int*)arrays->p[3];
   WC4D_CUDA(cudaMemcpy(plan.d_seg_start, seg_start.data(), sizeof(int) * seg_start.size(), cudaMemcpyHostToDevice));
   WC4D_CUDA(cudaMemcpy(plan.d_segs, segs.data(), sizeof(GemmSeg) * segs.size(), cudaMemcpyHostToDevice));
   WC4D_CUDA(cudaMemcpy(plan.d_tile_start, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice));
   WC4D_CUDA(cudaMemcpy(plan.d_tile_slots, tslots.data(), sizeof(int) * tslots.size(), cudaMemcpyHostToDevice));
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (plan_cache().size() >= PLAN_CACHE_MAX) plan_cache().clear();  // live problems keep their plans
+  plan_cache().emplace(key, plan);
 }
 
 // ---------------------------------------------------------------- kernels

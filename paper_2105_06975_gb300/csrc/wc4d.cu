@@ -179,6 +179,37 @@ struct OpSet {
 using namespace wc4d;
 
 namespace wc4d {
+// Small pinned host blocks (status words, scalars) from a process-wide free
+// list: cudaMallocHost / cudaFreeHost per problem cost more than a setup's
+// kernels and cudaFreeHost synchronises the device.
+constexpr size_t PINNED_BLOCK = 256;
+inline std::mutex& pinned_mu() {
+  static std::mutex m;
+  return m;
+}
+inline std::vector<void*>& pinned_free_list() {
+  static std::vector<void*> v;
+  return v;
+}
+inline void* pinned_get() {
+  {
+    std::lock_guard<std::mutex> lk(pinned_mu());
+    auto& v = pinned_free_list();
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  WC4D_CUDA(cudaMallocHost(&p, PINNED_BLOCK));
+  return p;
+}
+inline void pinned_put(void* p) {
+  std::lock_guard<std::mutex> lk(pinned_mu());
+  pinned_free_list().push_back(p);
+}
+
 // The default memory pool of the current device retains freed blocks up to
 // this many bytes (set once per device; process-local, not a GPU setting).
 inline void retain_default_pool() {
@@ -244,6 +275,13 @@ struct wc4d_problem {
   DevStatus* stat = nullptr;
   DevStatus* h_stat = nullptr;
   double* h_scal = nullptr;
+  int* d_flags = nullptr;  // setup flag slots (see setup)
+  struct CholCheck {
+    int64_t slot;
+    const char* what;
+    int m;
+  };
+  std::vector<CholCheck> chol_checks;
   std::vector<void*> allocs;
 
   // Stream-ordered allocation from the device's default pool, which keeps up to
@@ -267,8 +305,8 @@ struct wc4d_problem {
     plan_free(plan_pi2);
     for (void* p : allocs) cudaFreeAsync(p, st);
     cudaStreamSynchronize(st);
-    if (h_stat) cudaFreeHost(h_stat);
-    if (h_scal) cudaFreeHost(h_scal);
+    if (h_stat) pinned_put(h_stat);
+    if (h_scal) pinned_put(h_scal);
   }
 };
 
@@ -455,16 +493,15 @@ static int read_flag(int* d_flag, cudaStream_t st) {
 }
 
 // Cholesky + inverse factor of an SPD matrix given in A (overwritten by L).
-static void factor_inverse(wc4d_problem* P, double* A, int m, double* W, double* Wt, int* d_info, double* scratch,
+// The pivot check is read once at the end of setup (a failed factorisation
+// only produces non-finite factors meanwhile); each factorisation has its own
+// flag slot so the error names the matrix.
+static void factor_inverse(wc4d_problem* P, double* A, int m, double* W, double* Wt, double* scratch,
                            const char* what) {
-  WC4D_CUDA(cudaMemsetAsync(d_info, 0, sizeof(int), P->st));
+  WC4D_CHECK(P->chol_checks.size() < 12, WC4D_ERR_ARG, "internal: too many factorisations in one setup");
+  int* d_info = P->d_flags + 4 + (int)P->chol_checks.size();
+  P->chol_checks.push_back({d_info - P->d_flags, what, m});
   cholesky(A, m, d_info, P->st, scratch);
-  const int info = read_flag(d_info, P->st);
-  if (info != 0) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "Cholesky of %s failed: non-positive pivot %d of %d", what, info, m);
-    throw Error{WC4D_ERR_NOT_SPD, buf};
-  }
   tri_inverse(A, W, Wt, m, P->st, scratch);
 }
 
@@ -696,14 +733,24 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->np = (int64_t)(N + 1) * p;
   P->n = 2 * P->ns + P->np;
   cudaStream_t st = P->st;
-  int* d_flag = P->alloc<int>(4);
-  WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * 4, st));
-  // observation operator
+  // flag slots: 0 observation indices, 1 non-finite inputs, 2 R reconditioning,
+  // 4.. one per Cholesky factorisation (read once at the end of setup)
+  int* d_flag = P->alloc<int>(16);
+  P->d_flags = d_flag;
+  WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * 16, st));
+  // observation operator (the inverse map indexes by obs_idx: checked before it runs)
   P->d_obs = P->alloc<int>(p);
   P->d_inv = P->alloc<int>(s);
-  copy_in(P->d_obs, d->obs_idx, sizeof(int) * p, d->mem_kind, st);
-  launch_check_obs(P->d_obs, p, s, d_flag, st);
-  WC4D_CHECK(read_flag(d_flag, st) == 0, WC4D_ERR_ARG, "obs_idx must be strictly increasing in [0, s)");
+  if (d->mem_kind == WC4D_MEM_HOST) {
+    for (int r = 0; r < p; ++r)
+      WC4D_CHECK(d->obs_idx[r] >= 0 && d->obs_idx[r] < s && (r == 0 || d->obs_idx[r] > d->obs_idx[r - 1]),
+                 WC4D_ERR_ARG, "obs_idx must be strictly increasing in [0, s)");
+    copy_in(P->d_obs, d->obs_idx, sizeof(int) * p, d->mem_kind, st);
+  } else {
+    copy_in(P->d_obs, d->obs_idx, sizeof(int) * p, d->mem_kind, st);
+    launch_check_obs(P->d_obs, p, s, d_flag, st);
+    WC4D_CHECK(read_flag(d_flag, st) == 0, WC4D_ERR_ARG, "obs_idx must be strictly increasing in [0, s)");
+  }
   launch_inv_map(P->d_obs, p, P->d_inv, s, st);
   // model
   P->md.kind = d->model_kind;
@@ -740,12 +787,6 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   launch_check_finite(f.B, (int64_t)s * s, d_flag + 1, st);
   launch_check_finite(f.Q, (int64_t)s * s, d_flag + 1, st);
   launch_check_finite(f.R, (int64_t)p * p, d_flag + 1, st);
-  {
-    int h[2];
-    WC4D_CUDA(cudaMemcpyAsync(h, d_flag, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
-    WC4D_CUDA(cudaStreamSynchronize(st));
-    WC4D_CHECK(h[1] == 0, WC4D_ERR_NONFINITE, "non-finite entries in the model or covariance inputs");
-  }
   const int mmax = std::max(s, p);
   double* scratch = P->alloc<double>((int64_t)mmax * 64 + 64 * 64 * 2);
   double* work = P->alloc<double>((int64_t)mmax * mmax);
@@ -755,7 +796,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   f.WR = P->alloc<double>((int64_t)p * p);
   f.WRt = P->alloc<double>((int64_t)p * p);
   launch_copy_d(work, P->d_Rhat, (int64_t)p * p, st);
-  factor_inverse(P, work, p, f.WR, f.WRt, d_flag + 3, scratch, "Rhat");
+  factor_inverse(P, work, p, f.WR, f.WRt, scratch, "Rhat");
   // Dhat factors (P_D only)
   P->have_pd = (o->precond == WC4D_PRECOND_PD);
   if (P->have_pd) {
@@ -766,10 +807,10 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     f.WQt = P->alloc<double>((int64_t)s * s);
     launch_copy_d(work, f.B, (int64_t)s * s, st);
     if (delta != 0.0) launch_add_diag(work, s, s, nullptr, delta, st);
-    factor_inverse(P, work, s, f.WB, f.WBt, d_flag + 3, scratch, "Bhat");
+    factor_inverse(P, work, s, f.WB, f.WBt, scratch, "Bhat");
     launch_copy_d(work, f.Q, (int64_t)s * s, st);
     if (delta != 0.0) launch_add_diag(work, s, s, nullptr, delta, st);
-    factor_inverse(P, work, s, f.WQ, f.WQt, d_flag + 3, scratch, "Qhat");
+    factor_inverse(P, work, s, f.WQ, f.WQt, scratch, "Qhat");
     if (o->shat == WC4D_SHAT_EXACT) {
       // S uses the exact D and R (Sec. 2.2): factors of B, Q, R themselves
       double *eB = f.WB, *eQ = f.WQ, *eR = f.WR;
@@ -779,11 +820,11 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
         eQ = P->alloc<double>((int64_t)s * s);
         eR = P->alloc<double>((int64_t)p * p);
         launch_copy_d(work, f.B, (int64_t)s * s, st);
-        factor_inverse(P, work, s, eB, tmpt, d_flag + 3, scratch, "B");
+        factor_inverse(P, work, s, eB, tmpt, scratch, "B");
         launch_copy_d(work, f.Q, (int64_t)s * s, st);
-        factor_inverse(P, work, s, eQ, tmpt, d_flag + 3, scratch, "Q");
+        factor_inverse(P, work, s, eQ, tmpt, scratch, "Q");
         launch_copy_d(work, f.R, (int64_t)p * p, st);
-        factor_inverse(P, work, p, eR, tmpt, d_flag + 3, scratch, "R");
+        factor_inverse(P, work, p, eR, tmpt, scratch, "R");
       }
       P->nS = s * (N + 1);
       const int nS = P->nS;
@@ -792,7 +833,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       f.WS = P->alloc<double>((int64_t)nS * nS);
       f.WSt = P->alloc<double>((int64_t)nS * nS);
       double* sscr = P->alloc<double>((int64_t)nS * 64 + 64 * 64 * 2);
-      factor_inverse(P, S, nS, f.WS, f.WSt, d_flag + 3, sscr, "S");
+      factor_inverse(P, S, nS, f.WS, f.WSt, sscr, "S");
     }
   }
   // GEMM schedules
@@ -1009,9 +1050,23 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     P->net_part = P->alloc<double>(DOT_BLOCKS);
     P->net_params = P->alloc<float>(NetShape{N + 1, 64, s}.nparams());
   }
-  WC4D_CUDA(cudaMallocHost(&P->h_stat, sizeof(DevStatus)));
-  WC4D_CUDA(cudaMallocHost(&P->h_scal, sizeof(double) * 8));
+  P->h_stat = (DevStatus*)pinned_get();
+  P->h_scal = (double*)pinned_get();
+  // the deferred checks: non-finite inputs, then each factorisation's pivots
+  int* hf = (int*)pinned_get();
+  WC4D_CUDA(cudaMemcpyAsync(hf, d_flag, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
   WC4D_CUDA(cudaStreamSynchronize(st));
+  int hflags[16];
+  std::memcpy(hflags, hf, sizeof hflags);
+  pinned_put(hf);
+  WC4D_CHECK(hflags[1] == 0, WC4D_ERR_NONFINITE, "non-finite entries in the model or covariance inputs");
+  for (const auto& ck : P->chol_checks) {
+    if (hflags[ck.slot] != 0) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "Cholesky of %s failed: non-positive pivot %d of %d", ck.what, hflags[ck.slot], ck.m);
+      throw Error{WC4D_ERR_NOT_SPD, buf};
+    }
+  }
 }
 
 // ------------------------------------------------------------------ solves
