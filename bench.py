@@ -315,12 +315,14 @@ def run_gpu(args):
     w = W.SCALE
     seed = window_seed(args.seed, rank)
     dr = W.draws(w, seed)
+    ce = args.check_every
     modes = {
-        "fp64": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit),
+        "fp64": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
+                               check_every=ce),
         "df32": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
-                               precision="df32"),
+                               precision="df32", check_every=ce),
         "ozaki": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
-                                precision="ozaki"),
+                                precision="ozaki", check_every=ce),
     }
     if args.chosen == "df32p32" or (args.modes and "df32p32" in args.modes.split(",")):
         # FP32 preconditioner: only for covariances with kappa * eps32 << 1 (not this workload's R)

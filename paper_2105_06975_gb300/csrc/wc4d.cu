@@ -276,6 +276,7 @@ struct wc4d_problem {
   DevStatus* h_stat = nullptr;
   double* h_scal = nullptr;
   int* d_flags = nullptr;  // setup flag slots (see setup)
+  int* d_kerr = nullptr;   // set by the tensor-core kernel if a bounded wait gave up (read after each solve)
   struct CholCheck {
     int64_t slot;
     const char* what;
@@ -735,9 +736,10 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   cudaStream_t st = P->st;
   // flag slots: 0 observation indices, 1 non-finite inputs, 2 R reconditioning,
   // 4.. one per Cholesky factorisation (read once at the end of setup)
-  int* d_flag = P->alloc<int>(16);
+  int* d_flag = P->alloc<int>(17);
   P->d_flags = d_flag;
-  WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * 16, st));
+  P->d_kerr = d_flag + 16;
+  WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * 17, st));
   // observation operator (the inverse map indexes by obs_idx: checked before it runs)
   P->d_obs = P->alloc<int>(p);
   P->d_inv = P->alloc<int>(s);
@@ -932,8 +934,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     f.xd = P->alloc<uint16_t>(f.xdcap);
     f.xscap = std::max<int64_t>(xsc, 1);
     f.xs = P->alloc<float>(f.xscap);
-    f.tc_err = P->alloc<int>(1);
-    WC4D_CUDA(cudaMemsetAsync(f.tc_err, 0, sizeof(int), st));
+    f.tc_err = P->d_kerr;
   }
   if (o->precision == WC4D_PREC_MIXED || o->precision == WC4D_PREC_DF32_P32) {
     OpSet<float>& g = P->f32;
@@ -1777,11 +1778,12 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
   }
   WC4D_CUDA(cudaMemcpyAsync(x, P->x, bytes, kout, P->st));
   WC4D_CUDA(cudaStreamSynchronize(P->st));
-  if (P->f64.tc_err) {
-    // a bounded wait of the tensor-core kernel gave up (its outputs are not valid)
+  if (P->d_kerr) {
+    // a bounded wait of the tensor-core product kernel gave up: its outputs
+    // are not valid
     int e = 0;
-    WC4D_CUDA(cudaMemcpy(&e, P->f64.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    WC4D_CHECK(e == 0, WC4D_ERR_CUDA, "tensor-core product: a bounded wait gave up (code " + std::to_string(e) + ")");
+    WC4D_CUDA(cudaMemcpy(&e, P->d_kerr, sizeof(int), cudaMemcpyDeviceToHost));
+    WC4D_CHECK(e == 0, WC4D_ERR_CUDA, "pipelined kernel: a bounded wait gave up (code " + std::to_string(e) + ")");
   }
   loc.status = status;
   loc.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
