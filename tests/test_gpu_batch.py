@@ -51,7 +51,8 @@ def batch():
     specs = [linear_window(96, 4, 48, 11, "PI", "df32"), linear_window(160, 2, 40, 12, "PD", "fp64"),
              linear_window(128, 7, 64, 13, "PI", "fp64"), linear_window(64, 3, 16, 14, "PI", "df32"),
              l96_window(80, 3, 15, "df32"), linear_window(200, 5, 100, 16, "PD", "fp64"),
-             l96_window(96, 2, 17, "fp64"), linear_window(72, 9, 36, 18, "PI", "df32")]
+             l96_window(96, 2, 17, "fp64"), linear_window(72, 9, 36, 18, "PI", "df32"),
+             linear_window(144, 6, 70, 19, "PI", "ozaki"), l96_window(80, 4, 20, "ozaki")]
     return specs
 
 

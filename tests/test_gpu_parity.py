@@ -394,6 +394,26 @@ def test_l96_gauss_newton_small(loops):
     assert rel(traj, trajs[0]) > 1e-3          # the loop did move the trajectory
 
 
+def test_l96_gauss_newton_small_ozaki():
+    """The same outer loop with the covariance / factor products as exact BF16
+    digit products on the tensor cores (OZAKI mode, not in the paper): the
+    trajectory still follows the oracle's.  The inner solves run to 1e-8 (the
+    batched path's tolerance): at 1e-11 the Pythagorean norm of the Arnoldi
+    candidate reaches zero (reported as a breakdown) before the residual
+    estimate does, the products carrying ~2^-44 of max|a| max|x| against
+    FP64's 2^-53; the oracle's trajectory is taken at 1e-11."""
+    w = W.small(W.L96, s=80, N=4, p=40).with_(spinup_steps=300)
+    dr = W.draws(w, 1)
+    B, Q, R = prb.covariances(w, dr.obs_idx)
+    obs = prb.l96_truth(w, dr, B, Q, R, dr.obs_idx)
+    trajs, results, _ = prb.gauss_newton_l96(w, dr, popts("PI", 3), "gmres", tol=1e-11, maxit=3000, loops=1,
+                                             obs=obs)
+    traj, infos, code = l96_gpu_gn(w, dr, obs, 1, 1e-8, precision="ozaki")
+    assert code == 0 and all(i.status == 0 for i in infos)
+    assert rel(traj, trajs[-1]) < 1e-6
+    assert rel(traj, trajs[0]) > 1e-3
+
+
 def l96_cost(w, obs, B, Q, R, obs_idx, traj):
     """Nonlinear weak-constraint cost (Eq. CostFn) of a trajectory."""
     e0 = traj[0] - obs.xb
