@@ -346,14 +346,19 @@ double wc4d_rhat_param(const wc4d_problem* prob);
 
 /* Process-wide counters for measurement (no counterpart in the paper).
  * launches: kernels the library launched since the last reset.  With
- * profiling enabled the library also brackets every launch of its two
- * dominant kernel classes with CUDA events on the launching stream: the
- * stream-K covariance GEMM (work = algorithmic FLOPs: 2 x multiply-adds over
- * the non-zero triangle; FP64 and FP32 instances counted apart) and the
- * Arnoldi orthogonalisation passes (work =
- * bytes the pass must read and write); launches that exit early on a solve
- * that has already converged are not counted.  wc4d_get_stats synchronises
- * the device.  Not thread-safe across concurrent solves. */
+ * profiling enabled the library also brackets every launch of its dominant
+ * kernel classes with CUDA events on the launching stream: the covariance /
+ * factor products (stream-K GEMM in FP64, FP32 and double-float, and the
+ * tensor-core Ozaki products; work = algorithmic FLOPs: 2 x multiply-adds
+ * over the non-zero triangle, plus bytes and BF16 MMA flops for the
+ * tensor-core class) and the Arnoldi orthogonalisation passes (work = bytes
+ * the pass must read and write); launches that exit early on a solve that has
+ * already converged are not counted.  The events add stream operations
+ * between launches (they also stop consecutive kernels from overlapping their
+ * launch), so a timing of whole solves should be taken with profiling off.
+ * wc4d_set_profiling(1) allocates and clears the flag buffer (synchronous);
+ * wc4d_reset_stats and wc4d_get_stats synchronise the device.  Not
+ * thread-safe across concurrent solves. */
 typedef struct {
   int64_t launches;
   double gemm_ms, gemm_flops;
