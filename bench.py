@@ -11,8 +11,8 @@ built on the device before timing (inputs resident in HBM).
 
 Launch: ``python bench.py --gpus N --steps K --warmup W`` (N > 1 under
 torch.distributed.run, one window per rank, weak scaling, no data-path
-collective).  ``--impl reference`` times the FP64 CPU oracle on a bounded
-sample of the same workload.  Prints one JSON line on rank 0.
+collective).  ``--impl reference`` times the FP64 CPU oracle: each step one
+full solve of the same window on the host cores.  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -48,7 +48,6 @@ def parse():
     ap.add_argument("--rhat", default="exact")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=20)
     ap.add_argument("--maxit", type=int, default=1000, help="Krylov iteration cap (workspace size)")
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
@@ -140,29 +139,42 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_sample(args, w, dr, iters_full, sample_iters):
-    """Time the FP64 oracle on a bounded sample: problem build + Rhat factor +
-    ``sample_iters`` preconditioned GMRES iterations; project to one full
-    solve of ``iters_full`` iterations."""
-    import numpy as np
+def host_threads():
+    """Threads the oracle's numpy/BLAS work runs on: the BLAS thread-count
+    variables when set, else the cores this process may run on."""
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        try:
+            return max(1, int(os.environ[var]))
+        except (KeyError, ValueError):
+            pass
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def oracle_solve(args, w, dr, maxit=1000, tol=1e-6):
+    """One full solve by the FP64 oracle, timed on the host cores: problem
+    build + Rhat factor + the Krylov solve to ``tol`` (the GPU solve's
+    stopping rule).  With ``tol=0`` and a small ``maxit`` it is a short
+    untimed warm-up (BLAS thread pool, page-in)."""
     from oracle import krylov, problem as prb, saddle as sd
     t0 = time.perf_counter()
     prob, obs, rhs = prb.linear_case(w, dr)
     P = sd.Preconditioner(prob, sd.PrecondOptions(kind=args.precond, k=args.k, rhat=args.rhat))
     t1 = time.perf_counter()
     if args.precond == "PD":
-        krylov.minres(prob.A_apply, P.apply, rhs, tol=0.0, maxit=sample_iters, check_true=False)
+        r = krylov.minres(prob.A_apply, P.apply, rhs, tol=tol, maxit=maxit)
     else:
-        krylov.gmres(prob.A_apply, P.apply, rhs, tol=0.0, maxit=sample_iters)
+        r = krylov.gmres(prob.A_apply, P.apply, rhs, tol=tol, maxit=maxit)
     t2 = time.perf_counter()
-    per_iter = (t2 - t1) / sample_iters
-    proj = (t1 - t0) + per_iter * iters_full
-    return {"value": 1.0 / proj, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"problem build + Rhat factor ({t1 - t0:.2f} s) + {sample_iters} "
-                       f"{'MINRES' if args.precond == 'PD' else 'GMRES'} iterations ({t2 - t1:.2f} s) of the same "
-                       f"window; projected to {iters_full} iterations (the FP64 GPU solve's count), numpy FP64 on "
-                       f"{os.cpu_count()} host cores"),
-            "projected_s_per_solve": proj}
+    name = "MINRES" if args.precond == "PD" else "GMRES"
+    cores = host_threads()
+    return {"value": 1.0 / (t2 - t0), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one full solve of the same window: problem build + Rhat factor ({t1 - t0:.2f} s) + "
+                       f"{r.iters} {name} iterations to true relative residual {r.relres_true:.3g} "
+                       f"({t2 - t1:.2f} s); numpy FP64 on {cores} host threads"),
+            "iterations": r.iters, "relres_true": r.relres_true, "converged": bool(r.converged)}
 
 
 def workload_config(args, w):
@@ -180,20 +192,19 @@ def run_reference(args):
     from paper_2105_06975_gb300 import workload as W
     w = W.SCALE
     dr = W.draws(w, args.seed)
-    # the oracle's own iteration count is not known without a full (minutes
-    # long) run; the GPU arm's count for this window is 1 full solve's worth
-    iters_full = int(os.environ.get("WC4D_REF_ITERS", "150"))
-    vals = []
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample(args, w, dr, iters_full, max(4, args.cpu_iters // 2))
-        if i >= args.warmup:
-            vals.append(r)
-    v = statistics.mean(x["value"] for x in vals)
+    # warm-up steps are short untimed oracle runs (imports, BLAS threads,
+    # page-in); every timed step is one full oracle solve (~15-30 s on 8-16
+    # host cores at this size)
+    for _ in range(args.warmup):
+        oracle_solve(args, w, dr, maxit=2, tol=0.0)
+    vals = [oracle_solve(args, w, dr) for _ in range(args.steps)]
+    v = len(vals) / sum(1.0 / x["value"] for x in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, w),
-            "cpu_baseline": {**vals[-1], "value": v},
+            "cpu_baseline": {**vals[-1], "value": v,
+                             "sample": f"{len(vals)} timed steps, each " + vals[-1]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -493,8 +504,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(w.n * 8)},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        fp64_iters = int(round(line["modes"]["fp64"]["iterations"]))
-        line["cpu_baseline"] = oracle_sample(args, w, dr, fp64_iters, args.cpu_iters)
+        line["cpu_baseline"] = oracle_solve(args, w, dr)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
