@@ -308,6 +308,71 @@ def test_theorem1_intervals_contain_spectrum(k, rhat, dhat):
     assert bounds.in_intervals(ev.real, iv).all()
 
 
+def test_r_diag_is_the_diagonal():
+    """Sec. 5.1: R_diag keeps R's diagonal only.  A SOAR R has the constant
+    diagonal sigma^2, so R_diag = sigma^2 I and eig(R_diag^{-1} R) = eig(R)/sigma^2."""
+    w, dr = tiny(s=40, N=2, p=20)
+    R = cov.soar_obs(w.s, dr.obs_idx, 0.1, 0.2)
+    Rd = cov.r_diag(R)
+    assert np.array_equal(Rd, 0.1 * np.eye(R.shape[0]))
+    assert np.array_equal(cov.rhat(R, "diag"), Rd)
+    got = np.sort(sla.eigh(R, Rd, eigvals_only=True))
+    assert np.allclose(got, np.linalg.eigvalsh(R) / 0.1, rtol=1e-12)
+    M = np.array([[4.0, 1.0, 2.0], [1.0, 3.0, 0.5], [2.0, 0.5, 5.0]])
+    assert np.array_equal(cov.r_diag(M), np.diag([4.0, 3.0, 5.0]))
+
+
+def test_bd_intervals_attained_on_decoupled_blocks():
+    """Eq. BDPrecBounds against saddle points small enough to solve by hand.
+    One block each (Phi = [a], B = [b], preconditioner diag(ah, sh)):
+    eig = roots of lambda^2 - d lambda - d mu (d = a/ah, mu = (b^2/a)/sh),
+    and with delta = Delta = d, phi = Phi = mu all four outer ends are those
+    roots.  Phi = diag(a1, a2) with B = [b, 0]: the eigenvalues are d2 and the
+    roots for d1; the positive root is the positive interval's lower end when
+    d1 is the smaller ratio and its upper end when d1 is the larger.  Exact
+    blocks give the MGW values."""
+    for a, ah, b, sh in [(2.0, 4.0, 1.3, 0.7), (5.0, 2.0, 0.4, 2.5)]:
+        ev = np.sort(sla.eigvals(np.array([[a, b], [b, 0.0]]), np.diag([ah, sh])).real)
+        d, mu = a / ah, b * b / a / sh
+        lm, lp = (d - math.sqrt(d * d + 4 * d * mu)) / 2, (d + math.sqrt(d * d + 4 * d * mu)) / 2
+        assert np.allclose(ev, [lm, lp], rtol=1e-12)
+        neg, mid, pos = bounds.bd_intervals(d, d, mu, mu)
+        assert neg == pytest.approx((lm, lm), rel=1e-12) and pos == pytest.approx((lp, lp), rel=1e-12)
+        assert mid == (d, d)
+    for a1, a2, a1h, a2h, b, sh in [(2.0, 3.0, 4.0, 1.5, 1.3, 0.7), (5.0, 1.0, 2.0, 4.0, 0.4, 2.5)]:
+        A = np.array([[a1, 0, b], [0, a2, 0], [b, 0, 0]])
+        ev = np.sort(sla.eigvals(A, np.diag([a1h, a2h, sh])).real)
+        d1, d2 = a1 / a1h, a2 / a2h
+        mu = b * b / a1 / sh
+        lm, lp = (d1 - math.sqrt(d1 * d1 + 4 * d1 * mu)) / 2, (d1 + math.sqrt(d1 * d1 + 4 * d1 * mu)) / 2
+        assert np.allclose(ev, np.sort([lm, d2, lp]), rtol=1e-12)
+        neg, mid, pos = bounds.bd_intervals(min(d1, d2), max(d1, d2), mu, mu)
+        assert bounds.in_intervals(ev, (neg, mid, pos), rtol=1e-12).all()
+        assert neg[0] <= lm <= neg[1] and mid[0] <= d2 <= mid[1]
+        assert lp == pytest.approx(pos[0] if d1 < d2 else pos[1], rel=1e-12)
+    mgw = bounds.bd_intervals(1.0, 1.0, 1.0, 1.0)
+    for (lo, hi), v in zip(mgw, [(1 - 5 ** 0.5) / 2, 1.0, (1 + 5 ** 0.5) / 2]):
+        assert lo == pytest.approx(v, rel=1e-15) and hi == pytest.approx(v, rel=1e-15)
+
+
+def test_remark1_symmetric_closed_form_and_iteration_count():
+    """For [-b, -a] U [a, b] the factor per two MINRES steps is the
+    Chebyshev one on [a^2, b^2]: (b - a)/(b + a).  Unequal widths are
+    stretched to the wider one, which can only raise the factor.  The
+    iteration count is the smallest even 2l with 2 rho^l <= tol."""
+    for a, b in [(0.5, 2.0), (1.0, 1.0), (1e-3, 10.0)]:
+        assert bounds.remark1_factor(b, a, a, b) == pytest.approx((b - a) / (b + a), rel=1e-14, abs=1e-15)
+    r_un = bounds.remark1_factor(3.0, 1.0, 0.5, 1.0)           # widths 2 and 0.5
+    assert r_un == pytest.approx(bounds.remark1_factor(3.0, 1.0, 0.5, 2.5), rel=1e-15)
+    assert r_un > bounds.remark1_factor(1.5, 1.0, 0.5, 1.0)
+    for mus, tol in [((2.0, 0.5, 0.5, 2.0), 1e-6), ((4.0, 0.3, 0.7, 3.1), 1e-8), ((1.0, 0.9, 0.9, 1.0), 1e-3)]:
+        rho = bounds.remark1_factor(*mus)
+        it = bounds.remark1_iterations(*mus, tol)
+        l = it // 2
+        assert it % 2 == 0 and 2 * rho ** l <= tol * (1 + 1e-12)
+        assert l == 1 or 2 * rho ** (l - 1) > tol
+
+
 def test_remark1_minres_rate():
     """Remark 1: ||r_2l||_{P^{-1}} <= 2 rho^l ||r_0||_{P^{-1}} with rho from the
     computed eigenvalue intervals; the oracle's |eta| is that norm."""
