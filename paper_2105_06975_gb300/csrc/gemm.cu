@@ -11,6 +11,7 @@
 // reduction, which also applies the fused epilogue (the L v3 / H v3 terms of
 // A v, the v1 - D c1 of P_I).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <memory>
@@ -701,8 +702,9 @@ void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis
 }
 
 int gemm_resident_ctas(bool df32) {
-  static int cached[2] = {0, 0};
-  if (cached[df32]) return cached[df32];
+  // set by whichever host thread (a batched solve's workers) asks first; all compute the same value
+  static std::atomic<int> cached[2]{};
+  if (const int c = cached[df32].load(std::memory_order_relaxed)) return c;
   int dev = 0, sms = 0, per = 0, per32 = 0;
   WC4D_CUDA(cudaGetDevice(&dev));
   WC4D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -712,8 +714,9 @@ int gemm_resident_ctas(bool df32) {
     WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gemm_streamk_kernel<double>, 256, 0));
   // the FP32 instance shares the schedule; use the smaller residency of the two
   WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, gemm_streamk_kernel<float>, 256, 0));
-  cached[df32] = std::max(1, sms * std::max(1, std::min(per, per32)));
-  return cached[df32];
+  const int c = std::max(1, sms * std::max(1, std::min(per, per32)));
+  cached[df32].store(c, std::memory_order_relaxed);
+  return c;
 }
 
 template void gemm_run<double>(const GemmPlan&, const GemmOpsT<double>&, const EpisT<double>&, double*,

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -593,13 +594,15 @@ void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int*
 }
 
 int oz_resident_ctas() {
-  static int cached = 0;
-  if (cached) return cached;
+  // set by whichever host thread (a batched solve's workers) asks first; all compute the same value
+  static std::atomic<int> cached{0};
+  if (const int c = cached.load(std::memory_order_relaxed)) return c;
   int dev = 0, sms = 0;
   WC4D_CUDA(cudaGetDevice(&dev));
   WC4D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  cached = std::max(1, sms);
-  return cached;
+  const int c = std::max(1, sms);
+  cached.store(c, std::memory_order_relaxed);
+  return c;
 }
 
 }  // namespace wc4d
