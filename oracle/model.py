@@ -17,6 +17,7 @@ time t, matching Eq. def:L where block row t carries -M_t in block column t-1.
 Advection-diffusion (linear workloads): one explicit step of periodic upwind
 advection (Courant c) plus central diffusion (number d):
   (M x)_j = (c+d) x_{j-1} + (1-c-2d) x_j + d x_{j+1}.
+Heat equation (Sec. 7.2): Dirichlet boundaries, stored banded (heat_model).
 Lorenz-96 (Sec. 7.1): dx_j/dt = (x_{j+1} - x_{j-2}) x_{j-1} - x_j + F, periodic,
 integrated with classical RK4; M_i is the exact chain-rule Jacobian of the
 ``steps_per_obs`` RK4 steps between two observation times, stored banded.
@@ -102,6 +103,22 @@ class IdentityModel:
 
     def dense(self, t):
         return np.eye(self.s)
+
+
+def heat_model(s: int, N: int, r: float) -> BandedModel:
+    """Sec. 7.2: the heat equation on the unit line, forward Euler in time and
+    centred differences in space, homogeneous Dirichlet boundaries: the two
+    boundary rows and columns of M are zero and interior row j carries
+    (r, 1 - 2r, r) on columns j-1, j, j+1 (the couplings into the boundary
+    columns 0 and s-1 are zero), r = alpha dt / dx^2."""
+    if s < 3:
+        raise ValueError("the heat model needs s >= 3")
+    bands = np.zeros((N, s, 3))
+    j = np.arange(1, s - 1)
+    bands[:, j, 0] = np.where(j - 1 >= 1, r, 0.0)
+    bands[:, j, 1] = 1.0 - 2.0 * r
+    bands[:, j, 2] = np.where(j + 1 <= s - 2, r, 0.0)
+    return BandedModel(bands, 1, 1)
 
 
 def advdiff_coeffs(courant: float, diffusion: float):

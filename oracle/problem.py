@@ -30,17 +30,34 @@ from . import krylov
 from paper_2105_06975_gb300 import workload
 
 
-def covariances(w, obs_idx):
-    B = cov.soar_state(w.s, *w.soar_b)
-    Q = cov.soar_state(w.s, *w.soar_q)
-    R = cov.soar_obs(w.s, obs_idx, *w.soar_r)
+def covariances(w, obs_idx, extra=None):
+    """B, Q and R_i of a workload: chordal SOAR (all but the heat workload) or
+    the modified SOAR B, Q and the channel-block R_i of Sec. 6.1 (their draws
+    in ``extra``)."""
+    if w.cov == "msoar":
+        B = cov.modified_soar(w.s, *w.msoar_b, extra["psi"][0])[0]
+        Q = cov.modified_soar(w.s, *w.msoar_q, extra["psi"][1])[0]
+    else:
+        B = cov.soar_state(w.s, *w.soar_b)
+        Q = cov.soar_state(w.s, *w.soar_q)
+    if w.r_kind == "block":
+        pvec = workload.block_sizes(w.p, w.r_blocks)
+        pcorr = cov.pcorr_factors(extra["pcorr_on"], extra["pcorr_u"], w.r_pcorr_max, w.r_uncorrelated)
+        R = cov.block_r_matrix(pvec, w.r_density, pcorr, extra["r_u"], w.r_msoar, w.r_lmin)
+    else:
+        R = cov.soar_obs(w.s, obs_idx, *w.soar_r)
     return B, Q, R
 
 
+def linear_model(w):
+    if w.model == "heat":
+        return mdl.heat_model(w.s, w.N, w.heat_r)
+    return mdl.StencilModel(w.s, w.N, mdl.advdiff_coeffs(w.courant, w.diffusion))
+
+
 def linear_problem(w, dr) -> Problem:
-    B, Q, R = covariances(w, dr.obs_idx)
-    m = mdl.StencilModel(w.s, w.N, mdl.advdiff_coeffs(w.courant, w.diffusion))
-    return Problem(w.s, w.N, w.p, m, np.asarray(dr.obs_idx), B, Q, R)
+    B, Q, R = covariances(w, dr.obs_idx, dr.extra)
+    return Problem(w.s, w.N, w.p, linear_model(w), np.asarray(dr.obs_idx), B, Q, R)
 
 
 def chol_lower(M):

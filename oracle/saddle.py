@@ -117,7 +117,8 @@ class Problem:
 class PrecondOptions:
     kind: str = "PD"          # "PD" (block diagonal) | "PI" (inexact constraint)
     k: int = 1                # Lhat = L_M(k); 1 -> L_0 = I, N+1 -> L
-    rhat: str = "exact"       # "exact" | "rr" | "me" | "diag"
+    rhat: str = "exact"       # "exact" | "rr" | "me" | "diag" | "block"
+    rblock: tuple = ()        # "block": (pvec, tol, maxsize, numproc) of Alg. 3
     kappa_max: float = 100.0
     shat: str = "paper"       # "paper" (Lhat^T D^{-1} Lhat) | "exact" (S)
     dhat: str = "exact"       # "exact" | "rr"  (D + delta I, Sec. 6.1 delta = 0.01)
@@ -141,7 +142,7 @@ class Preconditioner:
         if not (1 <= opts.k <= N + 1):
             raise ValueError("k must lie in [1, N+1]")
         self.lhat_model = mdl.IdentityModel(prob.s, N) if opts.lhat_identity else prob.model
-        self.Rhat = cov.rhat(prob.R, opts.rhat, opts.kappa_max)
+        self.Rhat = cov.rhat(prob.R, opts.rhat, opts.kappa_max, opts.rblock or None)
         self.Rhat_solve = cov.SPDSolver(self.Rhat)
         if opts.dhat == "exact":
             Bh, Qh = prob.B, prob.Q

@@ -20,6 +20,11 @@ available, so these stand in for its experiments with the shapes below):
   s = 4 U{32..512}, N = U{8..96}, p = s/2 or s/4, advection-diffusion (the
   scale workload's covariances) or Lorenz-96 (its covariances, lengths in grid
   points, and the paper's time step 1e-4 of Sec. 7.1) by a fair coin each.
+* ``heat``  -- the heat equation with homogeneous Dirichlet boundaries
+  (Sec. 7.2, forward Euler, r = 0.4), s=50,000, N=5, p=12,500 random sorted
+  observed points (p/s = 0.25), the banded "modified SOAR" B and Q of
+  Sec. 6.1 (amplitude, length, maxval = 0.4, 0.6, 100 and 0.2, 0.5, 120) and
+  the channel-block R_i of Sec. 6.1.  n = 750,000.
 
 Seeds: master seed m in {0, 1, 2}; window w of a batch uses m*1000 + w.
 """
@@ -43,12 +48,12 @@ class Workload:
     # observation pattern: "even" (every 2nd grid point) or "random" (sorted
     # draw without replacement, shared by all times, Sec. 6.1)
     obs: str
-    # model: "advdiff" (periodic 3-point stencil) or "l96"
+    # model: "advdiff" (periodic 3-point stencil), "l96" or "heat" (Dirichlet)
     model: str
     # SOAR (variance, length as a fraction of the periodic unit domain)
-    soar_b: tuple
-    soar_q: tuple
-    soar_r: tuple
+    soar_b: tuple = ()
+    soar_q: tuple = ()
+    soar_r: tuple = ()
     # advection-diffusion: upwind Courant number c and diffusion number d give
     # x'_j = (c+d) x_{j-1} + (1-c-2d) x_j + d x_{j+1}
     courant: float = 0.5
@@ -61,6 +66,26 @@ class Workload:
     outer_loops: int = 1
     # synthetic truth for the linear model: Gaussian bump of this width
     bump_width: float = 0.05
+    # heat equation: r = alpha dt / dx^2
+    heat_r: float = 0.4
+    # B and Q: "soar" (chordal SOAR above) or "msoar" (the banded circulant
+    # modified SOAR of Sec. 6.1: amplitude, length, maxval)
+    cov: str = "soar"
+    msoar_b: tuple = (0.4, 0.6, 100)
+    msoar_q: tuple = (0.2, 0.5, 120)
+    # R_i: "soar" (chordal SOAR over the observed points) or "block" (the
+    # channel-block matrix of Sec. 6.1): r_blocks equal channel blocks, sparse
+    # random factors of density r_density, off-diagonal factors pcorr drawn in
+    # (0, r_pcorr_max) with probability 1 - r_uncorrelated (else 0), diagonal
+    # blocks weighted by a modified SOAR (amplitude, length, maxval), and the
+    # smallest eigenvalue set to r_lmin
+    r_kind: str = "soar"
+    r_blocks: int = 8
+    r_density: float = 0.2
+    r_pcorr_max: float = 0.5
+    r_uncorrelated: float = 0.5
+    r_msoar: tuple = (1.0, 0.5, 10)
+    r_lmin: float = 0.41
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -84,7 +109,17 @@ L96 = Workload(name="l96", s=1000, N=50, p=500, obs="even", model="l96",
                soar_b=(1.0, 5.0 / 1000), soar_q=(0.1, 5.0 / 1000),
                soar_r=(0.5, 4.0 / 1000), outer_loops=3)
 
-WORKLOADS = {w.name: w for w in (TINY, SCALE, L96)}
+HEAT = Workload(name="heat", s=50000, N=5, p=12500, obs="random", model="heat", cov="msoar", r_kind="block")
+
+WORKLOADS = {w.name: w for w in (TINY, SCALE, L96, HEAT)}
+
+
+def block_sizes(p: int, blocks: int) -> np.ndarray:
+    """pvec of the channel-block R_i: ``blocks`` sizes summing to p, as equal
+    as possible (the first p mod blocks one larger)."""
+    blocks = max(1, min(int(blocks), int(p)))
+    q, r = divmod(int(p), blocks)
+    return np.array([q + 1] * r + [q] * (blocks - r), dtype=np.int64)
 
 
 def batch_windows(count: int = 256, seed: int = 0) -> list:
@@ -141,8 +176,18 @@ def draws(w: Workload, seed: int = 0) -> Draws:
     z_r = g.standard_normal((w.N + 1, w.p))
     x0_pert = g.standard_normal(w.s)
     rhs_probe = g.standard_normal(w.n)
+    extra = {}
+    # drawn after the draws every workload takes, so those do not change
+    if w.cov == "msoar":
+        extra["psi"] = g.uniform(0.0, 0.5, size=2)          # shifts psi of B, Q (Sec. 6.1)
+    if w.r_kind == "block":
+        nb = len(block_sizes(w.p, w.r_blocks))
+        npairs = nb * (nb - 1) // 2
+        extra["pcorr_on"] = g.random(npairs)                 # < 1 - r_uncorrelated: correlated pair
+        extra["pcorr_u"] = g.random(npairs)                  # pcorr = r_pcorr_max * u
+        extra["r_u"] = g.random((w.p, w.p))                  # sparse random factors (mask and value)
     return Draws(obs_idx=obs_idx, bump_center=center, z_b=z_b, z_q=z_q, z_r=z_r,
-                 x0_pert=x0_pert, rhs_probe=rhs_probe)
+                 x0_pert=x0_pert, rhs_probe=rhs_probe, extra=extra)
 
 
 def bump(w: Workload, center: float) -> np.ndarray:
