@@ -224,3 +224,25 @@ def test_heat_problem_lu_equals_primal_minimiser_and_krylov():
         res = krylov.gmres(prob.A_apply, P.apply, rhs, tol=1e-10)
         assert res.converged
         assert np.linalg.norm(res.x - x_lu) <= 1e-7 * np.linalg.norm(x_lu)
+
+
+# ------------------------------------------------------------------- L_I
+def test_l_i_is_the_printed_matrix_and_a_prefix_sum():
+    """Sec. 2.2's L_I: identity blocks on the diagonal, -I below it.  Its
+    inverse is block lower triangular with every block I, so L_I^{-1} v is the
+    running sum over time levels and L_I^{-T} v the sum from the end.  Inside
+    the preconditioner it replaces only L-hat: the saddle matrix keeps M."""
+    s, N = 5, 4
+    im = mdl.IdentityModel(s, N)
+    Ld = mdl.L_dense(im)
+    want = np.eye((N + 1) * s) - np.eye((N + 1) * s, k=-s)
+    assert np.array_equal(Ld, want)
+    v = np.random.default_rng(4).standard_normal((N + 1, s))
+    assert np.allclose(mdl.LM_inv(im, v, N + 1), np.cumsum(v, axis=0), atol=1e-15)
+    assert np.allclose(mdl.LM_inv_T(im, v, N + 1), np.cumsum(v[::-1], axis=0)[::-1], atol=1e-15)
+    w, dr = small_heat(s=24, N=3, p=6)
+    prob = prb.linear_problem(w, dr)
+    P = sd.Preconditioner(prob, sd.PrecondOptions(kind="PI", k=prob.N + 1, lhat_identity=True))
+    ns = prob.s * (prob.N + 1)
+    assert np.array_equal(P.dense()[:ns, -ns:], mdl.L_dense(mdl.IdentityModel(prob.s, prob.N)))
+    assert np.array_equal(prob.A_dense()[:ns, -ns:], mdl.L_dense(prob.model))
