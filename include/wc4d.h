@@ -76,7 +76,21 @@ enum { WC4D_MEM_HOST = 0, WC4D_MEM_DEVICE = 1 };
 
 enum { WC4D_PRECOND_PD = 0, WC4D_PRECOND_PI = 1 };          /* Eq. prec                     */
 enum { WC4D_RHAT_EXACT = 0, WC4D_RHAT_RR = 1,               /* Rhat = R; Alg. 1 ridge       */
-       WC4D_RHAT_ME = 2, WC4D_RHAT_DIAG = 3 };              /* Alg. 2 min-eig; Sec. 5.1     */
+       WC4D_RHAT_ME = 2, WC4D_RHAT_DIAG = 3,                /* Alg. 2 min-eig; Sec. 5.1     */
+       WC4D_RHAT_BLOCK = 4 };     /* Alg. 3 (Sec. 5.1): R's channel blocks (rblock_sizes) are
+                                     decoupled where the first super-diagonal block's Frobenius
+                                     norm over sqrt(size_j size_j+1) is below rblock_tol; Rhat
+                                     keeps R inside each run of coupled blocks (every level) and
+                                     is zero between runs.  Optional size / count rules: a run
+                                     above rblock_maxsize rows is cut at its row midpoint; more
+                                     runs than rblock_numproc joins the adjacent pair with the
+                                     smallest total size, fewer than rblock_numproc - 2 cuts the
+                                     largest run at its midpoint (ties: the first); each rule
+                                     applies once, in this order                                */
+enum { WC4D_LHAT_LM = 0,          /* Lhat = L_M(k) with the model's M_i (Definition 1)          */
+       WC4D_LHAT_I = 1 };         /* Lhat = L_I (Sec. 2.2): every M_i inside Lhat replaced by the
+                                     identity, chunked by k like L_M(k) (k = N+1: the printed
+                                     L_I); the saddle matrix keeps M                            */
 enum { WC4D_SHAT_PAPER = 0, WC4D_SHAT_EXACT = 1,           /* Lhat^T D^-1 Lhat ; S (Sec 2.2) */
        WC4D_SHAT_LEARNED = 2 };   /* PAPER plus a learned correction of its inverse (not in the
                                      paper; wc4d_precond_train / _load), GMRES only          */
@@ -142,6 +156,13 @@ typedef struct {
   int32_t precision;         /* WC4D_PREC_*                                                 */
   int32_t inner_iters;       /* MIXED: inner GMRES steps per outer FGMRES step              */
   int32_t check_every;       /* host polls the device convergence flag every this many steps */
+  int32_t lhat;              /* WC4D_LHAT_*                                                 */
+  int32_t rblock_count;      /* RHAT_BLOCK: number of channel blocks (pvec of Alg. 3), >= 1 */
+  const int32_t* rblock_sizes; /* RHAT_BLOCK: host array [rblock_count] of block sizes, each
+                                  >= 1, summing to p; read during setup only (caller-owned)  */
+  double rblock_tol;         /* RHAT_BLOCK: Alg. 3 tol (>= 0; infinity cuts every coupling)  */
+  int32_t rblock_maxsize;    /* RHAT_BLOCK: Alg. 3 maxsize in rows; 0 = no size rule        */
+  int32_t rblock_numproc;    /* RHAT_BLOCK: Alg. 3 numproc; 0 = no count rule              */
 } wc4d_solve_opts;
 
 typedef struct {
@@ -160,12 +181,13 @@ typedef struct {
 
 typedef struct wc4d_problem wc4d_problem;   /* opaque, library-owned */
 
-/* Fill opts with the defaults of Sec. 7: P_I + GMRES, k = 1, Rhat = R,
- * kappa_max = 100, paper Shat, exact Dhat, tol 1e-6, maxit 1000, FP64. */
+/* Fill opts with the defaults of Sec. 7: P_I + GMRES, k = 1, Lhat = L_M(k),
+ * Rhat = R, kappa_max = 100, paper Shat, exact Dhat, tol 1e-6, maxit 1000,
+ * FP64; the Alg. 3 fields zero (no channel blocks). */
 void wc4d_default_opts(wc4d_solve_opts* opts);
 
 /* Build a problem: copy/generate B, Q, R, M_i and H on the device, build
- * Rhat (Alg. 1/2 or Sec. 5.1), factor Dhat, Rhat (and S when requested) with
+ * Rhat (Alg. 1/2/3 or Sec. 5.1), factor Dhat, Rhat (and S when requested) with
  * FP64 Cholesky, invert the triangular factors, and allocate the Krylov
  * workspace for opts->maxit iterations.  cuda_stream is a cudaStream_t (NULL =
  * legacy default stream).  On success *out owns all device memory it uses;
@@ -341,7 +363,8 @@ int wc4d_problem_dims(const wc4d_problem* prob, int64_t* n, int32_t* s, int32_t*
  * dst (device, col-major, s*s or p*p doubles).  For tests and diagnostics. */
 int wc4d_get_matrix(wc4d_problem* prob, int32_t which, double* dst);
 
-/* Rhat parameter used at setup: gamma (Alg. 1) or T (Alg. 2); 0 otherwise. */
+/* Rhat parameter used at setup: gamma (Alg. 1), T (Alg. 2) or the number of
+ * decoupled runs of channel blocks (Alg. 3); 0 otherwise. */
 double wc4d_rhat_param(const wc4d_problem* prob);
 
 /* Process-wide counters for measurement (no counterpart in the paper).

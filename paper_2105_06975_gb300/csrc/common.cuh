@@ -356,6 +356,8 @@ void launch_copy_d(double* dst, const double* src, int64_t n, cudaStream_t st);
 void launch_fill_d(double* dst, double v, int64_t n, cudaStream_t st);
 void launch_add_diag(double* A, int m, int64_t lda, const double* shift_dev, double shift, cudaStream_t st);
 void launch_keep_diag(double* A, int m, cudaStream_t st);
+void launch_block_sumsq(const double* A, int m, const int* pst, int nblocks, double* out, cudaStream_t st);
+void launch_zero_across_runs(double* A, int m, const int* run, cudaStream_t st);
 void launch_transpose(const double* A, double* At, int m, cudaStream_t st);
 void launch_symmetrize(double* A, int m, cudaStream_t st);
 void launch_to_float(const double* a, float* b, int64_t n, cudaStream_t st);

@@ -73,6 +73,48 @@ void launch_keep_diag(double* A, int m, cudaStream_t st) {
   keep_diag_kernel<<<nblk((int64_t)m * m), 256, 0, st>>>(A, m);
   WC4D_LAUNCH_CHECK();
 }
+
+// Alg. 3: sum of squares of the first super-diagonal block (rows pst[j] ..
+// pst[j+1]-1, columns pst[j+1] .. pst[j+2]-1) of the m x m matrix A, one CTA
+// per block j < nblocks
+__global__ void __launch_bounds__(256) block_sumsq_kernel(const double* __restrict__ A, int m,
+                                                          const int* __restrict__ pst, double* __restrict__ out) {
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  const int r0 = pst[j], r1 = pst[j + 1], c1 = pst[j + 2];
+  const int rows = r1 - r0;
+  const int64_t cnt = (int64_t)rows * (c1 - r1);
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int r = r0 + (int)(e % rows), c = r1 + (int)(e / rows);
+    const double a = A[r + (int64_t)c * m];
+    acc = fma(a, a, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[j] = t;
+  }
+}
+void launch_block_sumsq(const double* A, int m, const int* pst, int nblocks, double* out, cudaStream_t st) {
+  if (nblocks <= 0) return;
+  block_sumsq_kernel<<<nblocks, 256, 0, st>>>(A, m, pst, out);
+  WC4D_LAUNCH_CHECK();
+}
+
+// A[i + j m] = 0 where rows i and j lie in different runs (run[i] != run[j])
+__global__ void zero_across_runs_kernel(double* A, int m, const int* __restrict__ run) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    if (run[e % m] != run[e / m]) A[e] = 0.0;
+}
+void launch_zero_across_runs(double* A, int m, const int* run, cudaStream_t st) {
+  zero_across_runs_kernel<<<nblk((int64_t)m * m), 256, 0, st>>>(A, m, run);
+  WC4D_LAUNCH_CHECK();
+}
 // At[j + i m] = A[i + j m], 32x32 tiles through shared memory
 __global__ void transpose_kernel(const double* A, double* At, int m) {
   __shared__ double tile[32][33];

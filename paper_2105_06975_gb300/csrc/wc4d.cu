@@ -238,6 +238,7 @@ struct wc4d_problem {
   double* d_bands = nullptr;
   double* d_Rhat = nullptr;
   double rhat_param = 0.0;
+  std::vector<int> rblock_sizes;  // RHAT_BLOCK: channel block sizes (Alg. 3 pvec)
   int nS = 0;
   bool have_pd = false;
   OpSet<double> f64;
@@ -375,7 +376,7 @@ template <typename T>
 static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const GemmPlan& p2, const T* v, T* out,
                      const int* done) {
   const int s = P->s, N = P->N, p = P->p, k = P->o.k;
-  const bool ident = false;
+  const bool ident = (P->o.lhat == WC4D_LHAT_I);
   const T* v1 = v;
   const T* v2 = v + P->ns;
   const T* v3 = v + P->ns + P->np;
@@ -450,7 +451,8 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   T* o3 = out + P->ns + P->np;
   T* y2 = os.t1;  // W_R v2
   T* u = os.t2;   // v1 - D c1
-  lhat_sweep<T>(P->md, k, v3, o1, true, false, done, P->st);
+  const bool ident = (P->o.lhat == WC4D_LHAT_I);
+  lhat_sweep<T>(P->md, k, v3, o1, true, ident, done, P->st);
   GemmOpsT<T> ops{};
   EpisT<T> ep{};
   ops.nops = 3;
@@ -469,7 +471,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
   os.attach(ops2, P->st);
   gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
-  lhat_sweep<T>(P->md, k, u, o3, false, false, done, P->st);
+  lhat_sweep<T>(P->md, k, u, o3, false, ident, done, P->st);
 }
 
 template <typename T>
@@ -616,7 +618,91 @@ static void read_diag_minmax(const double* A, int m, int lim, cudaStream_t st, d
   }
 }
 
-// Rhat (Sec. 5): copy of R, its diagonal, Alg. 1 or Alg. 2.
+// Alg. 3 on the host: the rows where R_block decouples.  A cut c separates
+// rows < c from rows >= c; runs are the row ranges between cuts.
+static std::vector<int> rblock_cuts(const std::vector<int>& sizes, const std::vector<double>& normvec, double tol,
+                                    int maxsize, int numproc, int p) {
+  std::vector<int> cuts;
+  int start = 0;
+  for (size_t j = 0; j + 1 < sizes.size(); ++j) {
+    start += sizes[j];
+    if (normvec[j] < tol) cuts.push_back(start);
+  }
+  auto runs = [&]() {
+    std::vector<std::pair<int, int>> r;
+    int a = 0;
+    for (int c : cuts) {
+      r.push_back({a, c});
+      a = c;
+    }
+    r.push_back({a, p});
+    return r;
+  };
+  auto split_largest = [&]() {
+    const auto r = runs();
+    size_t best = 0;
+    for (size_t i = 1; i < r.size(); ++i)
+      if (r[i].second - r[i].first > r[best].second - r[best].first) best = i;
+    const int a = r[best].first, len = r[best].second - r[best].first;
+    if (len >= 2) {
+      cuts.push_back(a + len / 2);
+      std::sort(cuts.begin(), cuts.end());
+    }
+  };
+  if (maxsize > 0) {
+    int largest = 0;
+    for (const auto& q : runs()) largest = std::max(largest, q.second - q.first);
+    if (largest > maxsize) split_largest();
+  }
+  if (numproc > 0) {
+    const auto r = runs();
+    const int nr = (int)r.size();
+    if (nr > numproc) {
+      size_t best = 0;
+      for (size_t i = 1; i + 1 < r.size(); ++i)
+        if (r[i + 1].second - r[i].first < r[best + 1].second - r[best].first) best = i;
+      cuts.erase(std::find(cuts.begin(), cuts.end(), r[best].second));
+    } else if (nr < numproc - 2) {
+      split_largest();
+    }
+  }
+  return cuts;
+}
+
+// R_block (Alg. 3): scaled Frobenius norms of the first super-diagonal channel
+// blocks on the device, the cuts on the host, then R zeroed between runs.
+static void build_rblock(wc4d_problem* P, double* Rh) {
+  const int p = P->p;
+  const std::vector<int>& sz = P->rblock_sizes;
+  const int pn = (int)sz.size();
+  std::vector<double> normvec(pn > 1 ? pn - 1 : 0);
+  if (pn > 1) {
+    std::vector<int> pst(pn + 1, 0);
+    for (int j = 0; j < pn; ++j) pst[j + 1] = pst[j] + sz[j];
+    int* d_pst = P->alloc<int>(pn + 1);
+    double* d_ss = P->alloc<double>(pn - 1);
+    WC4D_CUDA(cudaMemcpyAsync(d_pst, pst.data(), sizeof(int) * (pn + 1), cudaMemcpyHostToDevice, P->st));
+    launch_block_sumsq(Rh, p, d_pst, pn - 1, d_ss, P->st);
+    WC4D_CUDA(cudaMemcpyAsync(normvec.data(), d_ss, sizeof(double) * (pn - 1), cudaMemcpyDeviceToHost, P->st));
+    WC4D_CUDA(cudaStreamSynchronize(P->st));
+    for (int j = 0; j + 1 < pn; ++j) normvec[j] = std::sqrt(normvec[j]) / std::sqrt((double)sz[j] * (double)sz[j + 1]);
+  }
+  const std::vector<int> cuts =
+      rblock_cuts(sz, normvec, P->o.rblock_tol, P->o.rblock_maxsize, P->o.rblock_numproc, p);
+  P->rhat_param = (double)(cuts.size() + 1);
+  if (cuts.empty()) return;
+  std::vector<int> run(p);
+  for (int i = 0, q = 0; i < p; ++i) {
+    while (q < (int)cuts.size() && i >= cuts[q]) ++q;
+    run[i] = q;
+  }
+  int* d_run = P->alloc<int>(p);
+  WC4D_CUDA(cudaMemcpyAsync(d_run, run.data(), sizeof(int) * p, cudaMemcpyHostToDevice, P->st));
+  launch_zero_across_runs(Rh, p, d_run, P->st);
+  WC4D_CUDA(cudaStreamSynchronize(P->st));  // the host label array goes out of scope
+}
+
+// Rhat (Sec. 5): copy of R, its diagonal, Alg. 1, Alg. 2 or Alg. 3.
 static void build_rhat(wc4d_problem* P, double* scratch, int* d_count) {
   const int p = P->p;
   double* Rh = P->d_Rhat;
@@ -625,6 +711,10 @@ static void build_rhat(wc4d_problem* P, double* scratch, int* d_count) {
   if (rh == WC4D_RHAT_EXACT) return;
   if (rh == WC4D_RHAT_DIAG) {
     launch_keep_diag(Rh, p, P->st);
+    return;
+  }
+  if (rh == WC4D_RHAT_BLOCK) {
+    build_rblock(P, Rh);
     return;
   }
   // eigen-decomposition of R by cyclic Jacobi on an even-sized copy; an odd p
@@ -691,9 +781,23 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
                WC4D_ERR_ARG, "SOAR variances and lengths must be positive");
   WC4D_CHECK(o->precond == WC4D_PRECOND_PD || o->precond == WC4D_PRECOND_PI, WC4D_ERR_ARG, "bad precond");
   WC4D_CHECK(o->k >= 1 && o->k <= d->N + 1, WC4D_ERR_ARG, "k must lie in [1, N+1]");
-  WC4D_CHECK(o->rhat >= WC4D_RHAT_EXACT && o->rhat <= WC4D_RHAT_DIAG, WC4D_ERR_ARG, "bad rhat");
-  WC4D_CHECK(o->rhat == WC4D_RHAT_EXACT || o->rhat == WC4D_RHAT_DIAG || o->kappa_max > 1.0, WC4D_ERR_ARG,
-             "kappa_max must exceed 1");
+  WC4D_CHECK(o->rhat >= WC4D_RHAT_EXACT && o->rhat <= WC4D_RHAT_BLOCK, WC4D_ERR_ARG, "bad rhat");
+  WC4D_CHECK(o->rhat == WC4D_RHAT_EXACT || o->rhat == WC4D_RHAT_DIAG || o->rhat == WC4D_RHAT_BLOCK ||
+                 o->kappa_max > 1.0,
+             WC4D_ERR_ARG, "kappa_max must exceed 1");
+  if (o->rhat == WC4D_RHAT_BLOCK) {
+    WC4D_CHECK(o->rblock_count >= 1 && o->rblock_count <= d->p && o->rblock_sizes != nullptr, WC4D_ERR_ARG,
+               "RHAT_BLOCK needs 1 <= rblock_count <= p channel block sizes");
+    int64_t sum = 0;
+    for (int j = 0; j < o->rblock_count; ++j) {
+      WC4D_CHECK(o->rblock_sizes[j] >= 1, WC4D_ERR_ARG, "channel block sizes must be >= 1");
+      sum += o->rblock_sizes[j];
+    }
+    WC4D_CHECK(sum == d->p, WC4D_ERR_ARG, "channel block sizes must sum to p");
+    WC4D_CHECK(o->rblock_tol >= 0.0 && o->rblock_maxsize >= 0 && o->rblock_numproc >= 0, WC4D_ERR_ARG,
+               "need rblock_tol >= 0, rblock_maxsize >= 0, rblock_numproc >= 0");
+  }
+  WC4D_CHECK(o->lhat == WC4D_LHAT_LM || o->lhat == WC4D_LHAT_I, WC4D_ERR_ARG, "bad lhat");
   WC4D_CHECK(o->shat == WC4D_SHAT_PAPER || o->shat == WC4D_SHAT_EXACT || o->shat == WC4D_SHAT_LEARNED, WC4D_ERR_ARG,
              "bad shat");
   WC4D_CHECK(o->shat != WC4D_SHAT_LEARNED ||
@@ -723,6 +827,8 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
 static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   validate(d, o);
   P->o = *o;
+  if (o->rhat == WC4D_RHAT_BLOCK) P->rblock_sizes.assign(o->rblock_sizes, o->rblock_sizes + o->rblock_count);
+  P->o.rblock_sizes = nullptr;  // caller-owned: read during setup only
   if (P->o.check_every <= 0) P->o.check_every = 4;
   // each outer step of the mixed mode is a whole inner solve: poll every step
   if (o->precision == WC4D_PREC_MIXED) P->o.check_every = 1;

@@ -43,6 +43,9 @@ WC4D_RHAT_EXACT = 0
 WC4D_RHAT_RR = 1
 WC4D_RHAT_ME = 2
 WC4D_RHAT_DIAG = 3
+WC4D_RHAT_BLOCK = 4
+WC4D_LHAT_LM = 0
+WC4D_LHAT_I = 1
 WC4D_SHAT_PAPER = 0
 WC4D_SHAT_EXACT = 1
 WC4D_SHAT_LEARNED = 2
@@ -57,7 +60,9 @@ WC4D_PREC_DF32 = 2
 WC4D_PREC_DF32_P32 = 3
 WC4D_PREC_OZAKI = 4
 
-RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG}
+RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG,
+        "block": WC4D_RHAT_BLOCK}
+LHAT = {"lm": WC4D_LHAT_LM, "i": WC4D_LHAT_I}
 PRECOND = {"PD": WC4D_PRECOND_PD, "PI": WC4D_PRECOND_PI}
 KRYLOV = {"minres": WC4D_KRYLOV_MINRES, "gmres": WC4D_KRYLOV_GMRES, "fgmres": WC4D_KRYLOV_FGMRES}
 
@@ -80,7 +85,9 @@ class SolveOpts(ctypes.Structure):
                 ("kappa_max", ctypes.c_double), ("shat", ctypes.c_int32), ("dhat", ctypes.c_int32),
                 ("dhat_delta", ctypes.c_double), ("krylov", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int32), ("precision", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
-                ("check_every", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("lhat", ctypes.c_int32), ("rblock_count", ctypes.c_int32),
+                ("rblock_sizes", ctypes.POINTER(ctypes.c_int32)), ("rblock_tol", ctypes.c_double),
+                ("rblock_maxsize", ctypes.c_int32), ("rblock_numproc", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -368,8 +375,21 @@ def wc4d_last_error() -> str:
 
 # -------------------------------------------------------------- convenience
 def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dhat="exact", dhat_delta=0.01,
-              krylov=None, tol=1e-6, maxit=1000, precision="fp64", inner_iters=20, check_every=4) -> SolveOpts:
+              krylov=None, tol=1e-6, maxit=1000, precision="fp64", inner_iters=20, check_every=4, lhat="lm",
+              rblock=None) -> SolveOpts:
+    """``rblock`` = (channel block sizes, tol, maxsize, numproc) for rhat="block"
+    (Alg. 3; maxsize / numproc None or 0 switch their rule off)."""
     o = wc4d_default_opts()
+    o.lhat = LHAT[lhat]
+    if rblock is not None:
+        sizes, btol, maxsize, numproc = rblock
+        arr = (ctypes.c_int32 * len(sizes))(*[int(x) for x in sizes])
+        o._rblock_keep = arr          # the library reads the sizes during setup
+        o.rblock_count = len(sizes)
+        o.rblock_sizes = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32))
+        o.rblock_tol = float(btol)
+        o.rblock_maxsize = int(maxsize or 0)
+        o.rblock_numproc = int(numproc or 0)
     o.precond = PRECOND[precond]
     o.k = int(k)
     o.rhat = RHAT[rhat]

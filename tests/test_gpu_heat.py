@@ -76,3 +76,70 @@ def test_heat_solve_matches_lu(precision):
     assert info.relres_true <= 1e-10
     assert rel(x.cpu().numpy(), x_lu) < 1e-7
     G.close()
+
+
+# ------------------------------------------------ R_block (Alg. 3) and L_I
+def gpu_opts(w, dr, prob, **kw):
+    o = L.make_opts(maxit=1000, **kw)
+    return L.Problem(w.s, w.N, w.p, dr.obs_idx, o, B=prob.B, Q=prob.Q, R=prob.R,
+                     bands=heat_bands(w.s, w.N, w.heat_r), band_lo=1, band_hi=1)
+
+
+def rblock_cases(R, pvec):
+    """(tol, maxsize, numproc) cases with tol well away from every scaled norm
+    (the two sides sum the norms in different orders)."""
+    from oracle import covariance as cov
+    nv = np.sort(cov.block_normvec(R, pvec))
+    mids = [0.5 * (a + b) for a, b in zip(nv[:-1], nv[1:]) if b - a > 1e-6 * max(b, 1e-300)]
+    cases = [(0.0, None, None), (np.inf, None, None), (0.0, 10, None), (np.inf, None, 3), (0.0, None, 6)]
+    cases += [(m, None, None) for m in mids]
+    return cases
+
+
+def test_rblock_rhat_matches_oracle():
+    from oracle import covariance as cov
+    w, dr, prob, rhs = heat_case()
+    pvec = W.block_sizes(w.p, w.r_blocks)
+    for tol, maxsize, numproc in rblock_cases(prob.R, pvec):
+        G = gpu_opts(w, dr, prob, rhat="block", rblock=(pvec, tol, maxsize, numproc))
+        want = cov.r_block(prob.R, pvec, tol, maxsize, numproc)
+        cuts, _ = cov.r_block_cuts(prob.R, pvec, tol, maxsize, numproc)
+        assert np.array_equal(G.matrix(3).cpu().numpy(), want), (tol, maxsize, numproc)
+        assert G.rhat_param() == len(cuts) + 1
+        G.close()
+
+
+@pytest.mark.parametrize("lhat", ["lm", "i"])
+@pytest.mark.parametrize("kind", ["PI", "PD"])
+def test_rblock_and_l_i_preconditioners_match_oracle(kind, lhat):
+    w, dr, prob, rhs = heat_case()
+    pvec = W.block_sizes(w.p, w.r_blocks)
+    tol = rblock_cases(prob.R, pvec)[-1][0]
+    v = W.random_vector(prob.n, 7)
+    for k in (2, w.N + 1):
+        G = gpu_opts(w, dr, prob, precond=kind, k=k, rhat="block", rblock=(pvec, tol, None, None), lhat=lhat)
+        P = sd.Preconditioner(prob, sd.PrecondOptions(kind=kind, k=k, rhat="block", rblock=(pvec, tol, None, None),
+                                                      lhat_identity=(lhat == "i")))
+        got = G.apply_precond(kind, torch.from_numpy(v).to(DEV)).cpu().numpy()
+        assert rel(got, P.apply(v)) < 1e-9, (k, lhat)
+        G.close()
+
+
+def test_rblock_l_i_solve_matches_lu():
+    w, dr, prob, rhs = heat_case()
+    pvec = W.block_sizes(w.p, w.r_blocks)
+    tol = rblock_cases(prob.R, pvec)[-1][0]
+    x_lu = sd.dense_solve(prob, rhs)
+    G = gpu_opts(w, dr, prob, precond="PI", k=w.N + 1, rhat="block", rblock=(pvec, tol, None, None), lhat="i",
+                 tol=1e-10)
+    x, info = G.solve(torch.from_numpy(rhs).to(DEV))
+    assert info.status == 0 and info.relres_true <= 1e-10
+    assert rel(x.cpu().numpy(), x_lu) < 1e-7
+    G.close()
+
+
+def test_rblock_argument_errors():
+    w, dr, prob, rhs = heat_case()
+    for bad in [([5, 5], 0.1, None, None), ([0, 24], 0.1, None, None), ([12, 12], -1.0, None, None)]:
+        with pytest.raises(L.WC4DError):
+            gpu_opts(w, dr, prob, rhat="block", rblock=bad)
