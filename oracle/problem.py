@@ -25,7 +25,7 @@ import scipy.linalg as sla
 
 from . import covariance as cov
 from . import model as mdl
-from .saddle import Problem, Preconditioner, PrecondOptions
+from .saddle import PerTimeProblem, Problem, Preconditioner, PrecondOptions
 from . import krylov
 from paper_2105_06975_gb300 import workload
 
@@ -58,6 +58,34 @@ def linear_model(w):
 def linear_problem(w, dr) -> Problem:
     B, Q, R = covariances(w, dr.obs_idx, dr.extra)
     return Problem(w.s, w.N, w.p, linear_model(w), np.asarray(dr.obs_idx), B, Q, R)
+
+
+def per_time_problem(w, dr) -> PerTimeProblem:
+    """Distinct H_i, R_i per time: R_i is the workload's R over time i's
+    observed points (chordal SOAR at obs_list[i]/s)."""
+    B, Q, _ = covariances(w, dr.obs_idx, dr.extra)
+    obs_list = dr.extra["obs_list"]
+    R_list = [cov.soar_obs(w.s, o, *w.soar_r) for o in obs_list]
+    return PerTimeProblem(w.s, w.N, linear_model(w), obs_list, B, Q, R_list)
+
+
+def per_time_case(w, dr):
+    """Problem, truth / observations and the first-loop right-hand side (C1,
+    C17) with y_i = H_i x_i^t + chol(R_i) z_i."""
+    prob = per_time_problem(w, dr)
+    x0t = workload.bump(w, dr.bump_center)
+    truth = np.zeros((w.N + 1, w.s))
+    truth[0] = x0t
+    for t in range(1, w.N + 1):
+        truth[t] = prob.model.apply(t, truth[t - 1])
+    xb = x0t + chol_lower(prob.B) @ dr.z_b
+    y = [truth[i, o] + chol_lower(Ri) @ dr.z_r[i] for i, (o, Ri) in enumerate(zip(prob.obs_list, prob.R_list))]
+    traj = background_trajectory_linear(prob, xb)
+    b = np.zeros((w.N + 1, w.s))
+    b[0] = xb - traj[0]
+    d = [y[i] - traj[i, o] for i, o in enumerate(prob.obs_list)]
+    rhs = PerTimeProblem.join(b, d, np.zeros((w.N + 1, w.s)))
+    return prob, Observations(xb, y, truth), rhs
 
 
 def chol_lower(M):

@@ -142,8 +142,7 @@ class Preconditioner:
         if not (1 <= opts.k <= N + 1):
             raise ValueError("k must lie in [1, N+1]")
         self.lhat_model = mdl.IdentityModel(prob.s, N) if opts.lhat_identity else prob.model
-        self.Rhat = cov.rhat(prob.R, opts.rhat, opts.kappa_max, opts.rblock or None)
-        self.Rhat_solve = cov.SPDSolver(self.Rhat)
+        self._build_rhat()
         if opts.dhat == "exact":
             Bh, Qh = prob.B, prob.Q
         elif opts.dhat == "rr":
@@ -154,6 +153,14 @@ class Preconditioner:
         self.Bhat_solve = cov.SPDSolver(Bh) if opts.kind == "PD" else None
         self.Qhat_solve = cov.SPDSolver(Qh) if opts.kind == "PD" else None
         self.S_solve = cov.SPDSolver(prob.S_dense()) if opts.shat == "exact" else None
+
+    def _build_rhat(self):
+        o = self.o
+        self.Rhat = cov.rhat(self.prob.R, o.rhat, o.kappa_max, o.rblock or None)
+        self.Rhat_solve = cov.SPDSolver(self.Rhat)
+
+    def Rhat_dense(self):
+        return np.kron(np.eye(self.prob.N + 1), self.Rhat)
 
     # ---- pieces
     def Lhat_inv(self, v):
@@ -209,8 +216,8 @@ class Preconditioner:
 
     def dense(self) -> np.ndarray:
         p = self.prob
-        Rh = np.kron(np.eye(p.N + 1), self.Rhat)
-        ns, npp = p.s * (p.N + 1), p.p * (p.N + 1)
+        Rh = self.Rhat_dense()
+        ns, npp = p.s * (p.N + 1), Rh.shape[0]
         Z = np.zeros
         if self.o.kind == "PD":
             return sla.block_diag(self.Dhat_dense(), Rh, self.Shat_dense())
@@ -218,6 +225,94 @@ class Preconditioner:
         return np.block([[p.D_dense(), Z((ns, npp)), Lh],
                          [Z((npp, ns)), Rh, Z((npp, ns))],
                          [Lh.T, Z((ns, npp)), Z((ns, ns))]])
+
+
+# ------------------------------------------- per-time observations (H_i, R_i)
+class PerTimeProblem(Problem):
+    """The general blocks of Sec. 2.1: time i observes the p_i grid points
+    obs_list[i] (H_i selects them) with its own error covariance R_list[i];
+    R = blkdiag(R_0..R_N), H = blkdiag(H_0..H_N).  nu is stored as the
+    concatenation of the N+1 blocks of sizes p_i, so ``split`` returns it as a
+    list.  ``p`` is the total number of observations over the window."""
+
+    def __init__(self, s, N, model, obs_list, B, Q, R_list):
+        if len(obs_list) != N + 1 or len(R_list) != N + 1:
+            raise ValueError("need N+1 observation sets and R_i blocks")
+        self.s, self.N, self.model, self.B, self.Q = s, N, model, B, Q
+        self.obs_list = [np.asarray(o) for o in obs_list]
+        self.R_list = [np.asarray(r, dtype=np.float64) for r in R_list]
+        self.p_list = [len(o) for o in self.obs_list]
+        for o, r in zip(self.obs_list, self.R_list):
+            if r.shape != (len(o), len(o)):
+                raise ValueError("R_i must be p_i x p_i")
+        self.p = int(sum(self.p_list))
+        self.obs_idx = None
+        self.R = None
+
+    @property
+    def n(self) -> int:
+        return 2 * self.s * (self.N + 1) + self.p
+
+    def split(self, v: np.ndarray):
+        s, T = self.s, self.N + 1
+        v1 = v[:T * s].reshape(T, s)
+        off = T * s
+        v2 = []
+        for pi in self.p_list:
+            v2.append(v[off:off + pi])
+            off += pi
+        v3 = v[off:].reshape(T, s)
+        return v1, v2, v3
+
+    @staticmethod
+    def join(c1, c2, c3) -> np.ndarray:
+        return np.concatenate([c1.ravel()] + [np.ravel(x) for x in c2] + [c3.ravel()])
+
+    def R_apply(self, v2):
+        return [Ri @ vi for Ri, vi in zip(self.R_list, v2)]
+
+    def A_apply(self, v: np.ndarray) -> np.ndarray:
+        v1, v2, v3 = self.split(v)
+        c1 = self.D_apply(v1) + mdl.L_apply(self.model, v3)
+        c2 = [r + h for r, h in zip(self.R_apply(v2), self.H_apply(v3))]
+        c3 = mdl.LT_apply(self.model, v1) + self.HT_apply(v2)
+        return self.join(c1, c2, c3)
+
+    def H_apply(self, x: np.ndarray):
+        return [x[i, o] for i, o in enumerate(self.obs_list)]
+
+    def HT_apply(self, y) -> np.ndarray:
+        out = np.zeros((self.N + 1, self.s))
+        for i, o in enumerate(self.obs_list):
+            out[i, o] = y[i]
+        return out
+
+    def H_dense(self) -> np.ndarray:
+        blocks = []
+        for o in self.obs_list:
+            Hi = np.zeros((len(o), self.s))
+            Hi[np.arange(len(o)), o] = 1.0
+            blocks.append(Hi)
+        return sla.block_diag(*blocks)
+
+    def R_dense(self) -> np.ndarray:
+        return sla.block_diag(*self.R_list)
+
+
+class PerTimePreconditioner(Preconditioner):
+    """P_D / P_I (Eq. prec) with R-hat_i built from each R_i (Sec. 5 applied
+    blockwise, as the paper's Remark in Sec. 5 states)."""
+
+    def _build_rhat(self):
+        o = self.o
+        self.Rhat_list = [cov.rhat(Ri, o.rhat, o.kappa_max, o.rblock or None) for Ri in self.prob.R_list]
+        self.Rhat_solves = [cov.SPDSolver(Rh) for Rh in self.Rhat_list]
+
+    def Rhat_dense(self):
+        return sla.block_diag(*self.Rhat_list)
+
+    def Rhat_inv(self, v2):
+        return [solve(vi) for solve, vi in zip(self.Rhat_solves, v2)]
 
 
 # ------------------------------------------------------------ direct solves

@@ -86,6 +86,9 @@ class Workload:
     r_uncorrelated: float = 0.5
     r_msoar: tuple = (1.0, 0.5, 10)
     r_lmin: float = 0.41
+    # per-time observation sets: time i observes its own p sorted points drawn
+    # without replacement (H_i and R_i differ between times)
+    obs_per_time: bool = False
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -186,6 +189,9 @@ def draws(w: Workload, seed: int = 0) -> Draws:
         extra["pcorr_on"] = g.random(npairs)                 # < 1 - r_uncorrelated: correlated pair
         extra["pcorr_u"] = g.random(npairs)                  # pcorr = r_pcorr_max * u
         extra["r_u"] = g.random((w.p, w.p))                  # sparse random factors (mask and value)
+    if w.obs_per_time:
+        extra["obs_list"] = [np.sort(g.choice(w.s, size=w.p, replace=False)).astype(np.int32)
+                             for _ in range(w.N + 1)]
     return Draws(obs_idx=obs_idx, bump_center=center, z_b=z_b, z_q=z_q, z_r=z_r,
                  x0_pert=x0_pert, rhs_probe=rhs_probe, extra=extra)
 
