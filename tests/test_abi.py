@@ -61,3 +61,30 @@ int main(){printf("%zu %zu %zu %zu %zu\n", sizeof(wc4d_problem_desc), sizeof(wc4
     assert sizes[2] == ctypes.sizeof(wc4d.Info)
     assert sizes[3] == wc4d.ProblemDesc.mem_kind.offset
     assert sizes[4] == wc4d.SolveOpts.check_every.offset
+
+
+def test_every_field_offset_matches_header():
+    """Each ctypes field of the descriptor, options, info and stats structs
+    sits at the C offset (a field added on one side only shifts the rest)."""
+    import subprocess
+    import tempfile
+    from paper_2105_06975_gb300 import wc4d
+    structs = {"wc4d_problem_desc": wc4d.ProblemDesc, "wc4d_solve_opts": wc4d.SolveOpts, "wc4d_info": wc4d.Info,
+               "wc4d_stats": wc4d.Stats}
+    lines = []
+    for cname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"wc4d.h\"\nint main(){" + "".join(lines) + "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        r = subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.skip("no host C compiler: " + r.stderr[:200])
+        out = subprocess.run([exe], capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for cname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
