@@ -1,0 +1,125 @@
+"""wc4d_setup_problem's argument checks (host logic, no GPU): every invalid
+descriptor or option is refused with WC4D_ERR_ARG and a message naming the
+rule, before any device work, and no handle is returned."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2105_06975_gb300 import build as B
+from paper_2105_06975_gb300 import wc4d as L
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def base(s=16, N=2, p=8):
+    d = L.ProblemDesc()
+    d.s, d.N, d.p = s, N, p
+    d.model_kind = L.WC4D_MODEL_STENCIL3
+    d.stencil[:] = [0.7, 0.1, 0.2]
+    obs = np.arange(0, 2 * p, 2, dtype=np.int32)[:p]
+    d.obs_idx = obs.ctypes.data
+    d.cov_kind = L.WC4D_COV_SOAR
+    d.soar_b[:] = [1.0, 0.1]
+    d.soar_q[:] = [0.05, 0.05]
+    d.soar_r[:] = [0.1, 0.05]
+    d.mem_kind = L.WC4D_MEM_HOST
+    return d, obs
+
+
+def refused(lib, d, o, needle):
+    h = ctypes.c_void_p()
+    rc = lib.wc4d_setup_problem(ctypes.byref(d), ctypes.byref(o), None, ctypes.byref(h))
+    msg = lib.wc4d_last_error().decode()
+    if h.value:
+        lib.wc4d_destroy(h)
+    assert rc == L.WC4D_ERR_ARG, (rc, msg)
+    assert needle in msg, msg
+    assert not h.value
+
+
+DESC_CASES = [
+    ({"s": 1, "p": 1}, "need s >= 2"),
+    ({"p": 17}, "1 <= p <= s"),
+    ({"N": -1}, "N >= 0"),
+    ({"mem_kind": 5}, "bad mem_kind"),
+    ({"obs_idx": None}, "obs_idx is null"),
+    ({"model_kind": 7}, "bad model_kind"),
+    ({"model_kind": L.WC4D_MODEL_BANDED, "band_lo": 10, "band_hi": 6}, "band offsets"),
+    ({"cov_kind": 9}, "bad cov_kind"),
+    ({"cov_kind": L.WC4D_COV_DENSE}, "dense covariances missing"),
+]
+
+
+@pytest.mark.parametrize("edits,needle", DESC_CASES)
+def test_descriptor_checks(lib, edits, needle):
+    d, obs = base()
+    for k, v in edits.items():
+        setattr(d, k, v)
+    refused(lib, d, L.make_opts(), needle)
+
+
+def test_soar_parameters_positive(lib):
+    d, obs = base()
+    d.soar_q[1] = 0.0
+    refused(lib, d, L.make_opts(), "SOAR variances and lengths")
+
+
+OPT_CASES = [
+    ({"precond": 5}, "bad precond"),
+    ({"k": 0}, "k must lie in [1, N+1]"),
+    ({"k": 4}, "k must lie in [1, N+1]"),
+    ({"rhat": 9}, "bad rhat"),
+    ({"rhat": L.WC4D_RHAT_RR, "kappa_max": 1.0}, "kappa_max must exceed 1"),
+    ({"lhat": 3}, "bad lhat"),
+    ({"shat": 7}, "bad shat"),
+    ({"shat": L.WC4D_SHAT_LEARNED}, "learned Schur block"),
+    ({"dhat": 4}, "bad dhat"),
+    ({"krylov": 9}, "bad krylov"),
+    ({"krylov": L.WC4D_KRYLOV_MINRES}, "MINRES needs"),
+    ({"tol": 0.0}, "need tol > 0"),
+    ({"maxit": 0}, "1 <= maxit"),
+    ({"maxit": 3000}, "maxit <= 2000"),
+    ({"precision": 9}, "bad precision"),
+    ({"precision": L.WC4D_PREC_MIXED}, "mixed-precision mode is FGMRES"),
+    ({"krylov": L.WC4D_KRYLOV_FGMRES}, "mixed-precision mode is FGMRES"),
+    ({"precision": L.WC4D_PREC_MIXED, "krylov": L.WC4D_KRYLOV_FGMRES, "inner_iters": 0}, "inner_iters"),
+    ({"precision": L.WC4D_PREC_DF32_P32, "precond": L.WC4D_PRECOND_PD, "krylov": L.WC4D_KRYLOV_MINRES},
+     "FP32-preconditioner mode"),
+]
+
+
+@pytest.mark.parametrize("edits,needle", OPT_CASES)
+def test_option_checks(lib, edits, needle):
+    d, obs = base()
+    o = L.make_opts()
+    for k, v in edits.items():
+        setattr(o, k, v)
+    refused(lib, d, o, needle)
+
+
+def test_exact_schur_size_limit(lib):
+    d, obs = base(s=4096, N=2, p=8)
+    refused(lib, d, L.make_opts(precond="PD", shat="exact"), "exact Schur complement limited")
+
+
+@pytest.mark.parametrize("rblock,needle", [
+    (([4, 3], 0.1, None, None), "sum to p"),
+    (([8, 0], 0.1, None, None), "must be >= 1"),
+    (([4, 4], -1.0, None, None), "need rblock_tol >= 0"),
+    (([4, 4], 0.1, -2, None), "need rblock_tol >= 0"),
+])
+def test_rblock_checks(lib, rblock, needle):
+    d, obs = base()
+    refused(lib, d, L.make_opts(rhat="block", rblock=rblock), needle)
+
+
+def test_rblock_needs_sizes(lib):
+    d, obs = base()
+    o = L.make_opts()
+    o.rhat = L.WC4D_RHAT_BLOCK
+    refused(lib, d, o, "RHAT_BLOCK needs")
