@@ -123,3 +123,31 @@ def test_rblock_needs_sizes(lib):
     o = L.make_opts()
     o.rhat = L.WC4D_RHAT_BLOCK
     refused(lib, d, o, "RHAT_BLOCK needs")
+
+
+def test_null_problem_handles_are_refused(lib):
+    """Entry points that take a problem refuse a null one (no dereference)."""
+    n = None
+    one = ctypes.c_void_p(1)       # never dereferenced: the null problem is checked first
+    for rc in (lib.wc4d_apply_saddle(n, one, one), lib.wc4d_apply_precond(n, 0, one, one),
+               lib.wc4d_solve(n, one, one, 0, L.WC4D_MEM_DEVICE, None), lib.wc4d_apply_fp32(n, 0, one, one),
+               lib.wc4d_synthesize_rhs(n, one, one, L.WC4D_MEM_HOST, one), lib.wc4d_get_matrix(n, 0, one),
+               lib.wc4d_precond_load(n, b"x"), lib.wc4d_precond_set_net(n, 32, one, 1)):
+        assert rc == L.WC4D_ERR_ARG, lib.wc4d_last_error()
+    nn = ctypes.c_int64()
+    i = ctypes.c_int32()
+    assert lib.wc4d_problem_dims(n, ctypes.byref(nn), ctypes.byref(i), ctypes.byref(i), ctypes.byref(i)) == \
+        L.WC4D_ERR_ARG
+    assert lib.wc4d_rhat_param(n) == 0.0
+    lib.wc4d_destroy(n)            # a no-op
+    lib.wc4d_default_opts(None)    # no-ops
+    lib.wc4d_default_train_opts(None)
+
+
+def test_batch_and_stats_arguments(lib):
+    assert lib.wc4d_solve_batch(None, 1, None, None, 0, L.WC4D_MEM_DEVICE, 1, None) == L.WC4D_ERR_ARG
+    assert lib.wc4d_get_stats(None) == L.WC4D_ERR_ARG
+    st = L.Stats()
+    lib.wc4d_reset_stats()
+    assert lib.wc4d_get_stats(ctypes.byref(st)) == L.WC4D_OK
+    assert st.launches == 0 and st.gemm_launches == 0
