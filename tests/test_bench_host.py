@@ -86,24 +86,29 @@ def test_clock_record_parsing():
 
 
 @pytest.mark.slow
-def test_reference_arm_prints_one_full_oracle_solve():
-    """One timed step of the reference arm: a full FP64 oracle solve of the
-    scale window (s=2048, N=64, p=1024) on the host cores, about 30 s here."""
+def test_reference_arm_full_solve_then_calibrated_sample():
+    """The reference arm: a full FP64 oracle solve of the scale window (s=2048,
+    N=64, p=1024) on the host cores (about 30 s here), then, with the time
+    budget spent, a sample calibrated by that solve."""
     env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    # two steps with no time budget left after the first: one full solve, one calibrated sample
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=900,
-                         cwd=ROOT, env=env)
+                          "--steps", "2", "--warmup", "1", "--ref-budget-s", "1"], capture_output=True, text=True,
+                         timeout=900, cwd=ROOT, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["higher_is_better"] is True
-    assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["ms_per_step"] == pytest.approx(1e3 / d["value"])
     assert d["config"]["s"] == 2048 and d["config"]["N"] == 64 and d["config"]["p"] == 1024
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     # the oracle meets the stopping rule the GPU solve uses
     assert cb["converged"] and cb["relres_true"] <= 1e-6 and 1 <= cb["iterations"] <= 1000
+    assert "1 full solves" in cb["sample"] and "1 samples" in cb["sample"]
+    # the calibrated sample lands near the full solve: the line's value is their harmonic mean
+    assert 0.5 * (1.0 / cb["t_total"]) < d["value"] < 2.0 * (1.0 / cb["t_total"])
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
