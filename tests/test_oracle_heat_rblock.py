@@ -246,3 +246,28 @@ def test_l_i_is_the_printed_matrix_and_a_prefix_sum():
     ns = prob.s * (prob.N + 1)
     assert np.array_equal(P.dense()[:ns, -ns:], mdl.L_dense(mdl.IdentityModel(prob.s, prob.N)))
     assert np.array_equal(prob.A_dense()[:ns, -ns:], mdl.L_dense(prob.model))
+
+
+def test_r_block_one_cut_spectrum_pairs_about_one():
+    """With one cut, R = R_block + E with E zero on the two diagonal runs, so
+    R_block^{-1/2} E R_block^{-1/2} has eigenvalues in +- pairs and eig(R_block^{-1}
+    R) = 1 +- mu: lambda_min + lambda_max = 2.  Table 2's R_block columns show
+    that pairing in every row (to the printed 4 digits), and the oracle's
+    R_block on a channel-block R_i with one cut has it exactly.  The same
+    table fixes lambda_min(R_i) = 0.41 in every row."""
+    rows = [list(map(float, ln.split())) for ln in open(os.path.join(ROOT, "tests", "golden", "table2_eigs.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 6
+    for p, rmin, rmax, dmin, dmax, bmin, bmax, *_ in rows:
+        assert bmin + bmax == pytest.approx(2.0, abs=2e-4)
+        assert rmin == 0.41
+    pvec = W.block_sizes(40, 4)
+    u = np.random.default_rng(9).random((40, 40))
+    R = cov.block_r_matrix(pvec, 0.4, np.array([0.3, 0.2, 0.1, 0.4, 0.25, 0.35]), u, (1.0, 0.5, 2), 0.41)
+    nv = cov.block_normvec(R, pvec)
+    tol = 0.5 * (np.sort(nv)[0] + np.sort(nv)[1])      # exactly one first super-diagonal coupling below tol
+    cuts, _ = cov.r_block_cuts(R, pvec, tol)
+    assert len(cuts) == 1
+    ev = np.sort(sla.eigh(R, cov.r_block(R, pvec, tol), eigvals_only=True))
+    assert ev[0] + ev[-1] == pytest.approx(2.0, abs=1e-10)
+    assert np.allclose(ev + ev[::-1], 2.0, atol=1e-10)
