@@ -3,6 +3,7 @@
 #include <memory>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -11,6 +12,16 @@
 #include "wc4d.h"
 
 namespace wc4d {
+
+// An NVTX range over a host scope: setup, factorisation, solve and residual
+// phases show up as named ranges in Nsight tools (header-only, a no-op when
+// no tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------------ errors
 struct Error {

@@ -502,6 +502,7 @@ static int read_flag(int* d_flag, cudaStream_t st) {
 // flag slot so the error names the matrix.
 static void factor_inverse(wc4d_problem* P, double* A, int m, double* W, double* Wt, double* scratch,
                            const char* what) {
+  NvtxRange nvtx_range("wc4d.factor_inverse");
   WC4D_CHECK(P->chol_checks.size() < 12, WC4D_ERR_ARG, "internal: too many factorisations in one setup");
   int* d_info = P->d_flags + 4 + (int)P->chol_checks.size();
   P->chol_checks.push_back({d_info - P->d_flags, what, m});
@@ -654,6 +655,7 @@ static void build_rblock(wc4d_problem* P, double* Rh) {
 
 // Rhat (Sec. 5): copy of R, its diagonal, Alg. 1, Alg. 2 or Alg. 3.
 static void build_rhat(wc4d_problem* P, double* scratch, int* d_count) {
+  NvtxRange nvtx_range("wc4d.build_rhat");
   const int p = P->p;
   double* Rh = P->d_Rhat;
   launch_copy_d(Rh, P->f64.R, (int64_t)p * p, P->st);
@@ -775,6 +777,7 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
 }
 
 static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
+  NvtxRange nvtx_range("wc4d.setup");
   validate(d, o);
   P->o = *o;
   if (o->rhat == WC4D_RHAT_BLOCK) P->rblock_sizes.assign(o->rblock_sizes, o->rblock_sizes + o->rblock_count);
@@ -1134,6 +1137,7 @@ static void fetch_stat(wc4d_problem* P) {
 
 // ||rhs - A x|| / ||rhs|| in FP64, read back to the host
 static double true_relres(wc4d_problem* P, const double* rhs, const double* x) {
+  NvtxRange nvtx_range("wc4d.true_residual");
   apply_A<double>(P, P->f64, P->plan_A, x, P->r, nullptr);
   vec_sub(rhs, P->r, P->r, P->n, P->st);
   dot_partial<double>(P->r, P->r, P->n, P->part3, nullptr, P->st);
@@ -1803,6 +1807,7 @@ int wc4d_apply_precond(wc4d_problem* P, int32_t which, const double* v, double* 
 
 int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, int32_t mem_kind, wc4d_info* info) {
   WC4D_API_BEGIN
+  wc4d::NvtxRange nvtx_range("wc4d.solve");
   WC4D_CHECK(P && rhs && x, WC4D_ERR_ARG, "null argument");
   WC4D_CHECK(mem_kind == WC4D_MEM_HOST || mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
   const auto t0 = std::chrono::steady_clock::now();
