@@ -12,9 +12,9 @@ built on the device before timing (inputs resident in HBM).
 Launch: ``python bench.py --gpus N --steps K --warmup W`` (N > 1 under
 torch.distributed.run, one window per rank, weak scaling, no data-path
 collective).  ``--impl reference`` times the FP64 CPU oracle on the host
-cores: each step one full solve of the same window while the run stays within
-``--ref-budget-s``, later steps a sample (build + 20 iterations) scaled by the
-first full solve's own ratio.  Prints one JSON line on rank 0.
+cores: each timed step is one full solve of the same window; steps stop early
+once the next would overrun ``--ref-budget-s``, and ``steps`` reports the
+solves that ran.  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--ref-budget-s", type=float, default=240.0,
-                    help="reference arm: time for full oracle solves; later steps are calibrated samples")
+                    help="reference arm: time budget for its timed full oracle solves (stops early)")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
     ap.add_argument("--workload", default="scale", choices=["scale", "batch", "learned", "profile"],
                     help="scale: one s=2048 N=64 window (default line); batch: independent uneven windows; "
@@ -157,34 +157,20 @@ def host_threads():
         return os.cpu_count()
 
 
-REF_SAMPLE_ITERS = 20
-
-
 def oracle_solve(args, w, dr, maxit=1000, tol=1e-6):
     """One full solve by the FP64 oracle, timed on the host cores: problem
     build + Rhat factor + the Krylov solve to ``tol`` (the GPU solve's
     stopping rule).  With ``tol=0`` and a small ``maxit`` it is a short
-    untimed warm-up (BLAS thread pool, page-in) or a sample.  Also records
-    ``t_head``: the time from the start to the start of Krylov iteration
-    REF_SAMPLE_ITERS (build + the first iterations), which calibrates samples."""
+    untimed warm-up (BLAS thread pool, page-in)."""
     from oracle import krylov, problem as prb, saddle as sd
     t0 = time.perf_counter()
     prob, obs, rhs = prb.linear_case(w, dr)
     P = sd.Preconditioner(prob, sd.PrecondOptions(kind=args.precond, k=args.k, rhat=args.rhat))
     t1 = time.perf_counter()
-    calls = [0]
-    head = [None]
-
-    def papply(v):
-        # one preconditioner apply per Krylov iteration (MINRES: one more before the loop)
-        if calls[0] == REF_SAMPLE_ITERS + (1 if args.precond == "PD" else 0):
-            head[0] = time.perf_counter() - t0
-        calls[0] += 1
-        return P.apply(v)
     if args.precond == "PD":
-        r = krylov.minres(prob.A_apply, papply, rhs, tol=tol, maxit=maxit)
+        r = krylov.minres(prob.A_apply, P.apply, rhs, tol=tol, maxit=maxit)
     else:
-        r = krylov.gmres(prob.A_apply, papply, rhs, tol=tol, maxit=maxit)
+        r = krylov.gmres(prob.A_apply, P.apply, rhs, tol=tol, maxit=maxit)
     t2 = time.perf_counter()
     name = "MINRES" if args.precond == "PD" else "GMRES"
     cores = host_threads()
@@ -193,24 +179,7 @@ def oracle_solve(args, w, dr, maxit=1000, tol=1e-6):
                        f"{r.iters} {name} iterations to true relative residual {r.relres_true:.3g} "
                        f"({t2 - t1:.2f} s); numpy FP64 on {cores} host threads"),
             "iterations": r.iters, "relres_true": r.relres_true, "converged": bool(r.converged),
-            "t_head": head[0] if head[0] is not None else t2 - t0, "t_total": t2 - t0}
-
-
-def oracle_sample_calibrated(args, w, dr, full):
-    """A bounded sample of one solve: problem build + Rhat factor + the first
-    REF_SAMPLE_ITERS Krylov iterations, scaled to a full solve by the ratio
-    (full solve time / the same head of that solve) measured on ``full``, an
-    earlier full oracle solve of the same window in this run."""
-    t0 = time.perf_counter()
-    oracle_solve(args, w, dr, maxit=REF_SAMPLE_ITERS, tol=0.0)
-    t = time.perf_counter() - t0
-    ratio = full["t_total"] / full["t_head"]
-    out = dict(full)
-    out["value"] = 1.0 / (t * ratio)
-    out["sample"] = (f"problem build + Rhat factor + {REF_SAMPLE_ITERS} iterations ({t:.2f} s), scaled by "
-                     f"{ratio:.2f} = full solve / its first {REF_SAMPLE_ITERS} iterations, both from the full "
-                     f"oracle solve of this run")
-    return out
+            "t_total": t2 - t0}
 
 
 def workload_config(args, w):
@@ -229,30 +198,32 @@ def run_reference(args):
     w = W.SCALE
     dr = W.draws(w, args.seed)
     # warm-up steps are short untimed oracle runs (imports, BLAS threads,
-    # page-in); a timed step is one full oracle solve (~15-30 s on 8-16 host
-    # cores at this size) while the run stays within --ref-budget-s, after
-    # that a sample calibrated by the first full solve
+    # page-in); every timed step is one full oracle solve (~13-30 s on 8-16
+    # host cores at this size).  Steps stop early once the next one would not
+    # fit in --ref-budget-s, and the line reports the solves that ran.
     for _ in range(args.warmup):
         oracle_solve(args, w, dr, maxit=2, tol=0.0)
     t_start = time.perf_counter()
     vals = []
     for _ in range(args.steps):
         elapsed = time.perf_counter() - t_start
-        if not vals or elapsed + vals[0]["t_total"] <= args.ref_budget_s:
-            vals.append(oracle_solve(args, w, dr))
-        else:
-            vals.append(oracle_sample_calibrated(args, w, dr, vals[0]))
-    nfull = sum(1 for x in vals if x["sample"].startswith("one full solve"))
-    v = len(vals) / sum(1.0 / x["value"] for x in vals)
+        if vals and elapsed + vals[0]["t_total"] > args.ref_budget_s:
+            break
+        vals.append(oracle_solve(args, w, dr))
+    wall = time.perf_counter() - t_start
+    v = len(vals) / sum(x["t_total"] for x in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, w),
-            "cpu_baseline": {**vals[0], "value": v,
-                             "sample": (f"{len(vals)} timed steps: {nfull} full solves ("
+            "steps": len(vals), "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, w), "timed_wall_s": wall,
+            "cpu_baseline": {**{k: vals[0][k] for k in ("unit", "cores", "kind", "iterations", "relres_true",
+                                                        "converged")},
+                             "value": v,
+                             "sample": (f"{len(vals)} timed steps, each one full oracle solve ("
                                         + vals[0]["sample"] + ")"
-                                        + (f", {len(vals) - nfull} samples ({vals[-1]['sample']})"
-                                           if nfull < len(vals) else ""))},
+                                        + (f"; stopped after {len(vals)} of {args.steps} requested steps to stay "
+                                           f"within {args.ref_budget_s:.0f} s" if len(vals) < args.steps
+                                           else ""))},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -53,7 +53,7 @@ enum {
   WC4D_ERR_NONFINITE = 3,  /* NaN/Inf in inputs or Krylov scalars              */
   WC4D_ERR_BREAKDOWN = 4,  /* Lanczos/Arnoldi breakdown before convergence     */
   WC4D_ERR_MAXIT = 5,      /* tolerance not reached within maxit iterations    */
-  WC4D_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                    */
+  WC4D_ERR_TIMEOUT = 6,    /* a bounded device wait gave up (wc4d_status)      */
   WC4D_ERR_CUDA = 7,       /* CUDA runtime error                               */
   WC4D_ERR_NOMEM = 8,      /* device allocation failed                         */
   WC4D_ERR_IO = 9          /* checkpoint file could not be read or written     */
@@ -177,6 +177,18 @@ typedef struct {
   double ms;                 /* wall time of the solve call                              */
   int64_t n_apply_A;         /* FP64 applications of A                                   */
   int64_t n_apply_P;         /* applications of the preconditioner (any precision)      */
+  /* Per-component product counts in the convention of Tables 4 and 5 (Sec. 7):
+   * one count per time block a product touches, so a full pass over the
+   * window counts N+1.  Per A v: N+1 R_i, N+1 D_i and 2N model products
+   * (L v3, L^T v1).  Per P_D^{-1} v: N+1 Dhat_i^{-1}, N+1 Rhat_i^{-1}, N+1 D_i
+   * (Shat^{-1} = Lhat^{-1} D Lhat^{-T}) and 2 (N - floor(N/k)) model products
+   * in the two Lhat sweeps (none with the exact S or with Lhat = L_I).  Per
+   * P_I^{-1} v: N+1 Rhat_i^{-1}, N+1 D_i (D c1) and the same sweep products.
+   * The mixed mode counts its inner FP32 A and P applies.                      */
+  int64_t n_cov;             /* covariance products: n_R + n_D                          */
+  int64_t n_M;               /* model products M_i v and M_i^T v                        */
+  int64_t n_trsm;            /* inverse-covariance applies: n_Dhat_inv + n_Rhat_inv    */
+  int64_t n_R, n_D, n_Dhat_inv, n_Rhat_inv;  /* n_cov and n_trsm by operator          */
 } wc4d_info;
 
 typedef struct wc4d_problem wc4d_problem;   /* opaque, library-owned */
@@ -200,6 +212,24 @@ int wc4d_setup_problem(const wc4d_problem_desc* desc, const wc4d_solve_opts* opt
 /* out = A v (Sec. 6.2: c1 = D v1 + L v3, c2 = R v2 + H v3, c3 = L^T v1 + H^T v2).
  * v, out: device, n doubles each, must not overlap.  Stream-ordered, async. */
 int wc4d_apply_saddle(wc4d_problem* prob, const double* v, double* out);
+
+/* Failure detection of the asynchronous calls.  In WC4D_PREC_OZAKI mode the
+ * tensor-core product kernel runs a copy / MMA / epilogue pipeline whose
+ * mbarrier waits are bounded (1 s by default); if one gives up, the kernel
+ * stops writing, waits (again bounded) for its own copies and products, frees
+ * its tensor memory and sets the problem's error word.  wc4d_solve reads and
+ * clears that word after every solve and returns WC4D_ERR_TIMEOUT; after
+ * wc4d_apply_saddle / wc4d_apply_precond (which only enqueue) call
+ * wc4d_status: it synchronises the problem's stream, reads and clears the
+ * word, and returns WC4D_ERR_TIMEOUT if a wait gave up (every output since
+ * the previous check is then invalid), else WC4D_OK.  No counterpart in the
+ * paper. */
+int wc4d_status(wc4d_problem* prob);
+/* Process-wide time limit of those pipeline waits in nanoseconds (0 restores
+ * the default of 1 s), read at each launch.  The drain waits before a CTA
+ * exits always keep the default.  For tests of the failure path: a limit of
+ * a few ns makes a wait give up. */
+void wc4d_set_wait_limit_ns(uint64_t ns);
 
 /* out = P^{-1} v for which = WC4D_PRECOND_PD (Dhat^{-1} v1, Rhat^{-1} v2,
  * Lhat^{-1} D Lhat^{-T} v3, Sec. 6.2) or WC4D_PRECOND_PI (c1 = Lhat^{-T} v3,

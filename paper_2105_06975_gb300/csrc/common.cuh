@@ -275,6 +275,7 @@ struct GemmOpsT {
   int df32 = 0;  // T = double only: run the products in double-float on the FP32 pipe
   int tc = 0;    // T = double only: wide tiles by Ozaki digit products on the tensor cores
   int* err = nullptr;  // tc: device flag set if a wait of the kernel gave up
+  unsigned long long wait_ns = 0;  // tc: time limit of the pipeline waits (0: the default, 1 s)
 };
 using GemmOp = GemmOpT<double>;
 using GemmOps = GemmOpsT<double>;

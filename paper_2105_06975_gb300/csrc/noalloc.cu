@@ -10,6 +10,7 @@
 // partial tiles of the covariance products and the inverse observation map --
 // in one file-scope device array of fixed size (8 MiB), which every GPU that
 // loads the library holds until the process exits.
+#include <atomic>
 #include <algorithm>
 
 #include "common.cuh"
@@ -141,21 +142,22 @@ __global__ void na_inv_fill_kernel(const int* obs, int p, int s, int* inv) {
   }
 }
 
-// device address of the scratch array, looked up once per device
-double* g_scratch_addr[64] = {};
+// device address of the scratch array, looked up once per device; host
+// threads making their first call at the same time may both look it up (the
+// same address) but never read a half-written pointer
+std::atomic<double*> g_scratch_addr[64];
 
 double* scratch_for_current_device() {
   int dev = 0;
   WC4D_CUDA(cudaGetDevice(&dev));
   WC4D_CHECK(dev >= 0 && dev < 64, WC4D_ERR_ARG, "device ordinal out of range");
-  if (g_scratch_addr[dev] == nullptr) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess)
-      throw Error{WC4D_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
-    g_scratch_addr[dev] = (double*)ptr;
-  }
-  return g_scratch_addr[dev];
+  if (double* a = g_scratch_addr[dev].load(std::memory_order_relaxed)) return a;
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess)
+    throw Error{WC4D_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
+  g_scratch_addr[dev].store((double*)ptr, std::memory_order_relaxed);
+  return (double*)ptr;
 }
 
 void fill_op(NaOp& op, const double* At, const double* X, int m, int ncols) {

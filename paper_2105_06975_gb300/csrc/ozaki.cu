@@ -256,14 +256,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait for the phase of the given parity; false after the time limit
-// or once another role has given up
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// bounded wait for the phase of the given parity; false after lim ns or once
+// another role has given up
+__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                       unsigned long long lim) {
   if (mbar_test(bar, parity)) return true;
   const unsigned long long t0 = now_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_test(bar, parity)) return true;
-    if ((it & 63) == 0 && (*abort_flag || now_ns() - t0 > OZ_WAIT_NS)) return false;
+    if ((it & 63) == 0 && (*abort_flag || now_ns() - t0 > lim)) return false;
   }
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -361,6 +362,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sbeg = seg_start[blockIdx.x], send = seg_start[blockIdx.x + 1];
+  // the pipeline waits give up after lim; the drains at the end keep the full
+  // OZ_WAIT_NS so that no copy or product is in flight when the CTA exits
+  const unsigned long long lim = ops.wait_ns ? ops.wait_ns : OZ_WAIT_NS;
   if (tid == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const uint16_t* xsrc = op.Xd + (int64_t)(sg.col0 / OZ_BN) * nkb * OZ_DIGITS * OZ_X_TILE;
         for (int kb = sg.k0 / OZ_BK; kb < (sg.k1 + OZ_BK - 1) / OZ_BK; ++kb, ++it) {
           const int s = it % OZ_STAGES;
-          if (it >= OZ_STAGES && !mbar_wait(&empty_bar[s], ((it / OZ_STAGES) - 1) & 1, &abort_flag)) {
+          if (it >= OZ_STAGES && !mbar_wait(&empty_bar[s], ((it / OZ_STAGES) - 1) & 1, &abort_flag, lim)) {
             give_up(&abort_flag, err, 1);
             ok = false;
             break;
@@ -434,7 +438,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const GemmSeg sg = segs[si];
         const GemmOpT<double>& op = ops.op[sg.op];
         if (min(sg.colw, op.ncols - sg.col0) < 2) continue;
-        if (nseg > 0 && !mbar_wait(&tfree_bar, (nseg - 1) & 1, &abort_flag)) {
+        if (nseg > 0 && !mbar_wait(&tfree_bar, (nseg - 1) & 1, &abort_flag, lim)) {
           give_up(&abort_flag, err, 2);
           break;
         }
@@ -442,7 +446,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int kb0 = sg.k0 / OZ_BK;
         for (int kb = kb0; kb < (sg.k1 + OZ_BK - 1) / OZ_BK; ++kb, ++it) {
           const int s = it % OZ_STAGES;
-          if (!mbar_wait(&full_bar[s], (it / OZ_STAGES) & 1, &abort_flag)) {
+          if (!mbar_wait(&full_bar[s], (it / OZ_STAGES) & 1, &abort_flag, lim)) {
             give_up(&abort_flag, err, 3);
             ok = false;
             break;
@@ -495,7 +499,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         gemv_segment(op, sg, dst);
         continue;
       }
-      if (!mbar_wait(&tfull_bar, nseg & 1, &abort_flag)) {
+      if (!mbar_wait(&tfull_bar, nseg & 1, &abort_flag, lim)) {
         give_up(&abort_flag, err, 4);
         break;
       }
@@ -533,7 +537,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           float hh, ll;
           fast_two_sum(h, lo, hh, ll);
-          if (rin && c < ncv) {
+          // once any role has given up, the launch's outputs are invalid (the
+          // host reports the error): nothing more is written
+          if (rin && c < ncv && !abort_flag) {
             const float f = sig * op.Xs[sg.col0 + c] * 0x1p-10f;
             dst[c * OZ_BM + r] = make_float2(hh * f, ll * f);
           }
@@ -592,6 +598,10 @@ void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int*
                        reinterpret_cast<float2*>(partial), done, ran, err));
   WC4D_LAUNCH_CHECK();
 }
+
+static std::atomic<unsigned long long> g_oz_wait_ns{0};
+void oz_set_wait_limit(unsigned long long ns) { g_oz_wait_ns.store(ns, std::memory_order_relaxed); }
+unsigned long long oz_wait_limit() { return g_oz_wait_ns.load(std::memory_order_relaxed); }
 
 int oz_resident_ctas() {
   // set by whichever host thread (a batched solve's workers) asks first; all compute the same value

@@ -58,5 +58,9 @@ void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int*
                     double* partial, const int* done, int* ran, int* err, cudaStream_t st);
 // persistent CTAs of the tensor-core kernel (one per SM)
 int oz_resident_ctas();
+// process-wide time limit of the kernel's pipeline waits in ns (0: the default
+// of 1 s); the final drain waits always keep the default
+void oz_set_wait_limit(unsigned long long ns);
+unsigned long long oz_wait_limit();
 
 }  // namespace wc4d

@@ -83,6 +83,7 @@ struct OpSet {
       ops.tc = 1;
       ops.df32 = 1;
       ops.err = tc_err;
+      ops.wait_ns = oz_wait_limit();
       OzColJobs jobs{};
       int64_t xoff = 0, soff = 0;
       int ctas = 0;
@@ -1155,6 +1156,46 @@ static void resume_after_false_stop(wc4d_problem* P, double est, double relres) 
   WC4D_CUDA(cudaStreamSynchronize(P->st));
 }
 
+// The tensor-core product kernel sets the problem's error word when one of
+// its bounded waits gives up; every output of that launch (and of what was
+// computed from it) is then invalid.  Reads and clears the word (the stream
+// must be synchronised) and reports WC4D_ERR_TIMEOUT.
+static void check_kernel_waits(wc4d_problem* P) {
+  if (!P->d_kerr) return;
+  int e = 0;
+  WC4D_CUDA(cudaMemcpy(&e, P->d_kerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e == 0) return;
+  WC4D_CUDA(cudaMemset(P->d_kerr, 0, sizeof(int)));
+  throw Error{WC4D_ERR_TIMEOUT, "tensor-core product kernel: a bounded wait gave up (role " + std::to_string(e) +
+                                    "); the outputs of that launch are invalid"};
+}
+
+// Per-component product counts in the convention of Tables 4 and 5: one count
+// per time block touched, from the number of A and P applies of the solve.
+// A v: N+1 R_i and N+1 D_i products, 2N model products (L and L^T).  P_D^{-1}:
+// N+1 Dhat_i^{-1} and N+1 Rhat_i^{-1} applies, N+1 D_i products and
+// 2(N - floor(N/k)) model products in the two Lhat sweeps (paper Shat; none
+// for the exact S or for Lhat = L_I).  P_I^{-1}: N+1 Rhat_i^{-1}, N+1 D_i,
+// the same sweep products.  The mixed mode's inner FP32 steps (one A and one
+// P apply each) are counted, and its outer preconditioner steps (each a whole
+// inner solve) are not.
+static void fill_counts(const wc4d_problem* P, wc4d_info* info) {
+  const int64_t T = P->N + 1, N = P->N, k = P->o.k;
+  const bool mixed = (P->o.precision == WC4D_PREC_MIXED);
+  const int64_t nA = info->n_apply_A + (mixed ? info->inner_iters : 0);
+  const int64_t nP = mixed ? info->inner_iters : info->n_apply_P;
+  const bool pd = (P->o.precond == WC4D_PRECOND_PD);
+  const bool exactS = pd && (P->o.shat == WC4D_SHAT_EXACT);
+  const int64_t sweepM = (P->o.lhat == WC4D_LHAT_LM && !exactS) ? 2 * (N - N / k) : 0;
+  info->n_R = nA * T;
+  info->n_D = nA * T + (exactS ? 0 : nP * T);
+  info->n_Dhat_inv = pd ? nP * T : 0;
+  info->n_Rhat_inv = nP * T;
+  info->n_M = nA * 2 * N + nP * sweepM;
+  info->n_cov = info->n_R + info->n_D;
+  info->n_trsm = info->n_Dhat_inv + info->n_Rhat_inv;
+}
+
 static int solve_minres(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   const int64_t n = P->n;
   double* Vb[3] = {P->V, P->V + n, P->V + 2 * n};
@@ -1794,6 +1835,17 @@ int wc4d_apply_saddle(wc4d_problem* P, const double* v, double* out) {
   WC4D_API_END
 }
 
+int wc4d_status(wc4d_problem* P) {
+  WC4D_API_BEGIN
+  WC4D_CHECK(P, WC4D_ERR_ARG, "null argument");
+  WC4D_CUDA(cudaStreamSynchronize(P->st));
+  check_kernel_waits(P);
+  return WC4D_OK;
+  WC4D_API_END
+}
+
+void wc4d_set_wait_limit_ns(uint64_t ns) { oz_set_wait_limit((unsigned long long)ns); }
+
 int wc4d_apply_precond(wc4d_problem* P, int32_t which, const double* v, double* out) {
   WC4D_API_BEGIN
   WC4D_CHECK(P && v && out, WC4D_ERR_ARG, "null argument");
@@ -1839,13 +1891,8 @@ int wc4d_solve(wc4d_problem* P, const double* rhs, double* x, int32_t use_x0, in
   }
   WC4D_CUDA(cudaMemcpyAsync(x, P->x, bytes, kout, P->st));
   WC4D_CUDA(cudaStreamSynchronize(P->st));
-  if (P->d_kerr) {
-    // a bounded wait of the tensor-core product kernel gave up: its outputs
-    // are not valid
-    int e = 0;
-    WC4D_CUDA(cudaMemcpy(&e, P->d_kerr, sizeof(int), cudaMemcpyDeviceToHost));
-    WC4D_CHECK(e == 0, WC4D_ERR_CUDA, "pipelined kernel: a bounded wait gave up (code " + std::to_string(e) + ")");
-  }
+  check_kernel_waits(P);
+  fill_counts(P, &loc);
   loc.status = status;
   loc.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = loc;

@@ -94,7 +94,10 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
                 ("precond_fallback", ctypes.c_int32),
                 ("relres_true", ctypes.c_double), ("relres_est", ctypes.c_double), ("ms", ctypes.c_double),
-                ("n_apply_A", ctypes.c_int64), ("n_apply_P", ctypes.c_int64)]
+                ("n_apply_A", ctypes.c_int64), ("n_apply_P", ctypes.c_int64),
+                ("n_cov", ctypes.c_int64), ("n_M", ctypes.c_int64), ("n_trsm", ctypes.c_int64),
+                ("n_R", ctypes.c_int64), ("n_D", ctypes.c_int64), ("n_Dhat_inv", ctypes.c_int64),
+                ("n_Rhat_inv", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -148,6 +151,8 @@ SIGNATURES = {
     "wc4d_apply_precond": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "wc4d_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.POINTER(Info)]),
+    "wc4d_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "wc4d_set_wait_limit_ns": (None, [ctypes.c_uint64]),
     "wc4d_apply_fp32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "wc4d_solve_batch": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -240,6 +245,19 @@ def wc4d_apply_saddle(h, v_ptr: int, out_ptr: int) -> None:
 
 def wc4d_apply_precond(h, which: int, v_ptr: int, out_ptr: int) -> None:
     _check(load().wc4d_apply_precond(h, which, ctypes.c_void_p(v_ptr), ctypes.c_void_p(out_ptr)))
+
+
+def wc4d_status(h, raise_on_error=True) -> int:
+    """Synchronise the problem's stream and report (then clear) a bounded
+    device wait that gave up since the last check (WC4D_ERR_TIMEOUT)."""
+    code = load().wc4d_status(h)
+    if raise_on_error:
+        _check(code)
+    return code
+
+
+def wc4d_set_wait_limit_ns(ns: int) -> None:
+    load().wc4d_set_wait_limit_ns(int(ns))
 
 
 def wc4d_solve(h, rhs_ptr: int, x_ptr: int, use_x0: bool, mem_kind: int, raise_on_error=True) -> Info:

@@ -178,3 +178,40 @@ def test_ozaki_scale_workload():
     r = rhs - prob.A_apply(x.cpu().numpy())
     assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-6
     G.close()
+
+
+def test_bounded_wait_gives_up_with_timeout_then_recovers():
+    """Failure detection of the tensor-core kernel's pipeline (not in the
+    paper).  With the pipeline waits limited to 1 ns a wait gives up: the
+    kernel stops writing, drains its own copies and products (full limit),
+    frees its tensor memory and sets the problem's error word, which
+    wc4d_status reports as WC4D_ERR_TIMEOUT (and clears).  With the default
+    limit restored the same problem applies A to 1e-11 of the oracle and
+    solves to the true residual: the context and the problem stay usable."""
+    w, dr = case(512, 40, 256, seed=6)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    G = L.Problem.from_workload(w, dr, L.make_opts(precond="PI", k=3, precision="ozaki", tol=1e-8, maxit=500))
+    v = W.random_vector(prob.n, 9)
+    want = prob.A_apply(v)
+    codes = []
+    try:
+        L.wc4d_set_wait_limit_ns(1)
+        for _ in range(3):
+            G.apply_saddle(to_dev(v))
+            codes.append(L.wc4d_status(G.h, raise_on_error=False))
+            if codes[-1] == L.WC4D_ERR_TIMEOUT:
+                break
+    finally:
+        L.wc4d_set_wait_limit_ns(0)
+    assert L.WC4D_ERR_TIMEOUT in codes, codes
+    assert "bounded wait gave up" in L.wc4d_last_error()
+    # the word was cleared by the read: the next check is clean
+    assert L.wc4d_status(G.h, raise_on_error=False) == L.WC4D_OK
+    got = G.apply_saddle(to_dev(v)).cpu().numpy()
+    assert L.wc4d_status(G.h, raise_on_error=False) == L.WC4D_OK
+    assert rel(got, want) < 1e-11
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == 0
+    r = rhs - prob.A_apply(x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-8
+    G.close()

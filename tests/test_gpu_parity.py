@@ -184,7 +184,9 @@ def test_small_solves_match_lu_and_oracle_iterations(kind, krylov, k, rhat):
     G = gpu_problem(w, dr, precond=kind, k=k, rhat=rhat, krylov=krylov, tol=1e-11, maxit=2000)
     x, info = G.solve(to_dev(rhs))
     assert info.status == 0, L.wc4d_last_error()
-    assert rel(x.cpu().numpy(), x_lu) < 1e-6
+    # kappa(A) = 1.6e5 here; the oracle's own solves to 1e-11 land within
+    # 1.3e-10 of LU, so the FP64 bound of 1e-8 holds with margin
+    assert rel(x.cpu().numpy(), x_lu) < 1e-8
     G.close()
     # at the paper's tolerance the iteration counts agree with the oracle's
     G = gpu_problem(w, dr, precond=kind, k=k, rhat=rhat, krylov=krylov, tol=1e-6, maxit=1000)
@@ -221,7 +223,8 @@ def test_banded_model_solve():
     G = gpu_problem(w, dr, prob, precond="PI", k=3, banded=bd, tol=1e-10, maxit=1000)
     x, info = G.solve(to_dev(rhs))
     assert info.status == 0
-    assert rel(x.cpu().numpy(), x_lu) < 1e-6
+    # kappa(A) = 2.0e5; the oracle's solve to 1e-10 lands within 7e-12 of LU
+    assert rel(x.cpu().numpy(), x_lu) < 1e-8
     G.close()
 
 
@@ -273,7 +276,8 @@ def test_df32_gmres_delayed_reorthogonalisation():
     ref = kr.gmres(prob.A_apply, P.apply, rhs, tol=1e-10, maxit=300)
     assert info.status == 0 and abs(info.iters - ref.iters) <= 1, (info.iters, ref.iters)
     x_lu = sd.dense_solve(prob, rhs)
-    assert rel(x.cpu().numpy(), x_lu) < 1e-6
+    # kappa(A) = 1.3e7; the oracle's GMRES to 1e-10 lands within 1.2e-11 of LU
+    assert rel(x.cpu().numpy(), x_lu) < 1e-8
     x0 = W.random_vector(prob.n, 5)
     x1, info1 = D.solve(to_dev(rhs), to_dev(x0), use_x0=True)
     assert info1.status == 0
@@ -573,4 +577,59 @@ def test_scale_workload_operators_and_solve():
     assert info.status == 0
     r = rhs - prob.A_apply(x.cpu().numpy())
     assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-6
+    G.close()
+
+
+@pytest.mark.parametrize("kind,krylov,k,lhat", [("PD", "minres", 3, "lm"), ("PI", "gmres", 2, "lm"),
+                                                ("PI", "gmres", 4, "i")])
+def test_product_counts_follow_tables_4_5(kind, krylov, k, lhat):
+    """wc4d_info's per-component product counts (Tables 4 and 5 convention: one
+    count per time block a product touches).  The oracle's own operators,
+    wrapped to count, give the products of one A apply and one P apply; the
+    library's totals after 7 iterations must equal those per-apply counts times
+    its own numbers of A and P applies, and those numbers follow the solver
+    (7 preconditioner applies plus MINRES's initial one)."""
+    w, dr = case(48, 5, 24, "random", seed=3)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    o = sd.PrecondOptions(kind=kind, k=k, rhat="exact", lhat_identity=(lhat == "i"))
+    P = sd.Preconditioner(prob, o)
+    cnt = {"D": 0, "R": 0, "Dh": 0, "Rh": 0, "M": 0}
+
+    def wrap(obj, name, key, per):
+        f = getattr(obj, name)
+
+        def g(*a):
+            cnt[key] += per(*a)
+            return f(*a)
+        setattr(obj, name, g)
+    T = prob.N + 1
+    wrap(prob, "D_apply", "D", lambda *a: T)
+    wrap(prob, "R_apply", "R", lambda *a: T)
+    wrap(P, "Dhat_inv", "Dh", lambda *a: T)
+    wrap(P, "Rhat_inv", "Rh", lambda *a: T)
+    wrap(prob.model, "apply", "M", lambda *a: 1)
+    wrap(prob.model, "apply_T", "M", lambda *a: 1)
+    v = W.random_vector(prob.n, 2)
+    prob.A_apply(v)
+    perA = dict(cnt)
+    for key in cnt:
+        cnt[key] = 0
+    P.apply(v)
+    perP = dict(cnt)
+    G = gpu_problem(w, dr, precond=kind, k=k, krylov=krylov, tol=1e-30, maxit=7)
+    if lhat == "i":
+        G.close()
+        G = L.Problem.from_workload(w, dr, L.make_opts(precond=kind, k=k, krylov=krylov, tol=1e-30, maxit=7,
+                                                       lhat="i"))
+    x, info = G.solve(to_dev(rhs))
+    assert info.status == L.WC4D_ERR_MAXIT and info.iters == 7
+    nA, nP = info.n_apply_A, info.n_apply_P
+    assert nP == 7 + (1 if krylov == "minres" else 0)
+    assert info.n_R == nA * perA["R"] and perA["R"] == T
+    assert info.n_D == nA * perA["D"] + nP * perP["D"]
+    assert info.n_Dhat_inv == nP * perP["Dh"] and info.n_Rhat_inv == nP * perP["Rh"]
+    assert info.n_M == nA * perA["M"] + nP * perP["M"]
+    assert info.n_cov == info.n_R + info.n_D and info.n_trsm == info.n_Dhat_inv + info.n_Rhat_inv
+    # the ratios Tables 4 and 5 print: D_i = 2 R_i per iteration, Dhat^-1 = R_i for P_D, none for P_I
+    assert perP["D"] == perA["R"] and (perP["Dh"] == T if kind == "PD" else perP["Dh"] == 0)
     G.close()

@@ -496,6 +496,49 @@ def test_l96_fixed_point_and_tlm():
     assert np.allclose(bm.apply(1, v), M @ v, atol=1e-13)
 
 
+def test_l96_rhs_hand_evaluated_with_periodic_wrap():
+    """Sec. 7.1: dx_j/dt = (x_{j+1} - x_{j-2}) x_{j-1} - x_j + F, periodic.
+    On x_j = j + 1 (s = 8, 0-based j) the interior entries are
+    (3)(j) - (j+1) + F = 2j + 7, and the wrapped ends are worked out by hand:
+      j = 0: (x_1 - x_6) x_7 - x_0 + 8 = (2 - 7) 8 - 1 + 8 = -33
+      j = 1: (x_2 - x_7) x_0 - x_1 + 8 = (3 - 8) 1 - 2 + 8 =   1
+      j = 7: (x_0 - x_5) x_6 - x_7 + 8 = (1 - 6) 7 - 8 + 8 = -35
+    A mirrored stencil (x_{j-1} - x_{j+2}) x_{j+1} or a swapped pair of roll
+    offsets changes these values, which the constant fixed point cannot see."""
+    x = np.arange(1.0, 9.0)
+    f = mdl.l96_rhs(x, 8.0)
+    expected = np.array([-33.0, 1.0, 11.0, 13.0, 15.0, 17.0, 19.0, -35.0])
+    assert np.array_equal(f, expected)
+    # forcing enters additively, once
+    assert np.array_equal(mdl.l96_rhs(x, 0.0), expected - 8.0)
+
+
+def test_rk4_step_is_classical_fourth_order(monkeypatch):
+    """The Runge-Kutta scheme of Sec. 7.1 is the classical fourth-order one.
+    (i) On the linear test equation dx/dt = lam x one classical RK4 step
+    multiplies x by the degree-4 Taylor polynomial of exp(lam dt), exactly (up
+    to rounding); a wrong stage weight or stage point breaks that identity.
+    (ii) On the Lorenz-96 right-hand side itself, the global error at t = 0.5
+    against a fine-step solution falls by 2^4 per halving of dt."""
+    lam = np.array([-0.7, 0.3, -2.0, 1.1])
+    monkeypatch.setattr(mdl, "l96_rhs", lambda x, F: lam * x)
+    x0 = np.array([1.0, -2.0, 0.5, 3.0])
+    for dt in (0.1, 0.37):
+        z = lam * dt
+        taylor = 1.0 + z + z ** 2 / 2.0 + z ** 3 / 6.0 + z ** 4 / 24.0
+        np.testing.assert_allclose(mdl.rk4_step(x0, dt, 0.0), taylor * x0, rtol=1e-15, atol=0)
+    monkeypatch.undo()
+
+    g = np.random.default_rng(3)
+    x = 8.0 + g.standard_normal(40)
+    T = 0.5
+    ref = mdl.l96_forecast(x, T / 4096, 8.0, 4096)
+    errs = [np.linalg.norm(mdl.l96_forecast(x, T / m, 8.0, m) - ref) for m in (32, 64, 128)]
+    ratios = [errs[0] / errs[1], errs[1] / errs[2]]
+    for r in ratios:
+        assert 13.0 < r < 19.0, ratios
+
+
 def test_gauss_newton_linear_converges_in_one_loop():
     """For a linear model the first inner solve is the full answer: the second
     outer loop's increment is zero to solver tolerance (Sec. 2.1)."""

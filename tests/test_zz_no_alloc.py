@@ -4,7 +4,8 @@ wc4d_apply_saddle_noalloc serves callers that cannot call cudaMalloc (a GPU
 shared with a framework whose caching allocator holds the memory, or a loop
 that cannot pay for allocation); it keeps its scratch in a fixed device array
 inside the library.  Two calls in a row must both match wc4d_apply_saddle on
-the same matrices, at the A v tolerance of the parity tests, and an oversized
+the same matrices, at the A v tolerance of the parity tests (1e-12), and the
+FP64 oracle's blockwise A v at the same tolerance; an oversized
 problem must be refused before any launch.  This file is collected last so
 that a failure here does not hide the other GPU tests.
 """
@@ -18,7 +19,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from oracle import problem as prb  # noqa: E402
+from oracle import model as mdl, problem as prb, saddle as sd  # noqa: E402
 from paper_2105_06975_gb300 import wc4d as L, workload as W  # noqa: E402
 
 
@@ -46,6 +47,10 @@ def test_noalloc_matches_apply_saddle_twice(s, N, p):
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert rel(out, ref) < 1e-12
+        prob = sd.Problem(s=w.s, N=w.N, p=w.p, model=mdl.StencilModel(w.s, w.N, w.stencil()),
+                          obs_idx=np.asarray(dr.obs_idx), B=B, Q=Q, R=R)
+        want = torch.from_numpy(prob.A_apply(v.cpu().numpy()))
+        assert rel(out.cpu(), want) < 1e-12
     G.close()
 
 
