@@ -96,6 +96,19 @@ enum { WC4D_SHAT_PAPER = 0, WC4D_SHAT_EXACT = 1,           /* Lhat^T D^-1 Lhat ;
                                      paper; wc4d_precond_train / _load), GMRES only          */
 enum { WC4D_DHAT_EXACT = 0, WC4D_DHAT_SHIFT = 1 };          /* D ; D + delta I (Sec. 6.1)   */
 enum { WC4D_KRYLOV_MINRES = 0, WC4D_KRYLOV_GMRES = 1, WC4D_KRYLOV_FGMRES = 2 };
+enum { WC4D_COVPROD_DENSE = 0,    /* B, Q as dense s x s products; Dhat^-1 through inverse Cholesky
+                                     factors                                                    */
+       WC4D_COVPROD_FFT = 1 };    /* B and Q are circulant (Sec. 6.1: SOAR on the periodic uniform
+                                     grid depends on (i - j) mod s only): B v, Q v, Bhat^-1 v and
+                                     Qhat^-1 v as FP64 FFT, scaling by the real spectrum (or its
+                                     inverse, with the Dhat shift) and inverse FFT; no s x s
+                                     factorisation.  Needs s a power of two in [64, 8192],
+                                     precision FP64, DF32 or OZAKI, shat PAPER or LEARNED; with
+                                     cov_kind DENSE the caller's B and Q must be circulant
+                                     (checked at setup: ARG otherwise), the spectrum being taken
+                                     from their first columns.  A spectrum value <= 0 gives
+                                     NOT_SPD.  R stays a dense product (the observed points are
+                                     not a uniform grid).                                       */
 enum { WC4D_PREC_FP64 = 0,        /* every product in native FP64 (DFMA)                       */
        WC4D_PREC_MIXED = 1,       /* FGMRES outer (FP64-accurate A) around an FP32 inner GMRES
                                      preconditioned by an FP32 copy of the chosen preconditioner
@@ -163,6 +176,7 @@ typedef struct {
   double rblock_tol;         /* RHAT_BLOCK: Alg. 3 tol (>= 0; infinity cuts every coupling)  */
   int32_t rblock_maxsize;    /* RHAT_BLOCK: Alg. 3 maxsize in rows; 0 = no size rule        */
   int32_t rblock_numproc;    /* RHAT_BLOCK: Alg. 3 numproc; 0 = no count rule              */
+  int32_t covprod;           /* WC4D_COVPROD_*: how B, Q (and Bhat^-1, Qhat^-1) are applied */
 } wc4d_solve_opts;
 
 typedef struct {

@@ -1,0 +1,334 @@
+// Circulant covariance products by FFT in FP64 (Sec. 6.1: on the periodic
+// uniform grid the SOAR B and Q depend on (i - j) mod s only, so they are
+// circulant, diagonalised by the DFT: C = F^{-1} diag(lambda) F with lambda
+// real because C is symmetric).  C x, C^{-1} x and (C + delta I)^{-1} x are
+// then two transforms and a scaling per column instead of an s x s product.
+//
+// GB300 runs FP64 at 2 DFMA per clock per SM, so one CTA per column would
+// leave most SMs idle behind a few long FP64 chains.  Each complex transform
+// (two real columns of one operator packed as re + i im: a real spectrum acts
+// on both parts separately) is instead split over a cluster of 8 CTAs with the
+// four-step factorisation s = 8 Q, n = Q n1 + n2, k = k1 + 8 k2:
+//   X[k1 + 8 k2] = sum_n2 w_Q^(n2 k2) w^(n2 k1) sum_n1 w_8^(n1 k1) x[Q n1 + n2]
+// Phase 1: CTA c takes n2 in [c Q/8, (c+1) Q/8): 8-point DFTs over n1 in
+//          registers, twiddle w^(n2 k1), each result sent to CTA k1's shared
+//          memory (distributed shared memory store).
+// Phase 2: CTA k1: length-Q decimation-in-frequency FFT in shared memory
+//          (natural order in, bit-reversed out), scaling by lambda (stored in
+//          the same bit-reversed cluster layout), decimation-in-time inverse
+//          FFT (bit-reversed in, natural out), twiddle w^(-n2 k1), each value
+//          sent back to the CTA owning n2.
+// Phase 3: CTA c: 8-point inverse DFTs over k1, / s, fused epilogue, store.
+// Two cluster barriers separate the phases; both exchanges go through
+// distributed shared memory, so HBM sees each input column read once and
+// each output column written once.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "circulant.cuh"
+#include "model_dev.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace wc4d {
+namespace {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
+  return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 w) {  // a * conj(w)
+  return make_double2(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
+}
+
+// 8-point DFT in registers, natural order in and out.  sign = -1: forward
+// (w_8 = exp(-2 pi i / 8)); +1: inverse without the 1/8.  Radix-2
+// decimation in frequency, then the bit-reversed result put back in order.
+template <int SIGN>
+__device__ __forceinline__ void dft8(double2 (&a)[8]) {
+  constexpr double c = 0.70710678118654752440;  // cos(pi/4)
+  // stage h = 4: twiddles w_8^j, j = 0..3
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double2 u = a[j], v = a[j + 4];
+    a[j] = cadd(u, v);
+    double2 d = csub(u, v);
+    if (j == 1) d = make_double2(c * (d.x - SIGN * d.y), c * (d.y + SIGN * d.x));
+    if (j == 2) d = make_double2(-SIGN * d.y, SIGN * d.x);
+    if (j == 3) d = make_double2(-c * (d.x + SIGN * d.y), c * (SIGN * d.x - d.y));
+    a[j + 4] = d;
+  }
+  // stage h = 2: twiddles w_8^(2j) = w_4^j, j = 0, 1
+#pragma unroll
+  for (int b = 0; b < 8; b += 4) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const double2 u = a[b + j], v = a[b + j + 2];
+      a[b + j] = cadd(u, v);
+      double2 d = csub(u, v);
+      if (j == 1) d = make_double2(-SIGN * d.y, SIGN * d.x);
+      a[b + j + 2] = d;
+    }
+  }
+  // stage h = 1
+#pragma unroll
+  for (int b = 0; b < 8; b += 2) {
+    const double2 u = a[b], v = a[b + 1];
+    a[b] = cadd(u, v);
+    a[b + 1] = csub(u, v);
+  }
+  // bit-reversed positions 1 <-> 4, 3 <-> 6
+  double2 t = a[1];
+  a[1] = a[4];
+  a[4] = t;
+  t = a[3];
+  a[3] = a[6];
+  a[6] = t;
+}
+
+__device__ __forceinline__ void epilogue_store(const CircJob& J, const ModelDev& md, int s, int r, int c, double y) {
+  if (c >= J.ncols) return;
+  double val;
+  switch (J.mode) {
+    case EPI_SADDLE_C1: {
+      const int t = c + J.t0;
+      double pre = J.v3[(int64_t)t * s + r];
+      if (t >= 1) pre -= model_apply<double>(md, t, J.v3 + (int64_t)(t - 1) * s, r);
+      val = y + pre;
+      break;
+    }
+    case EPI_SUB_FROM:
+      val = J.Y[r + (int64_t)c * J.ldc] - y;
+      break;
+    case EPI_NEG_STORE:
+      val = -y;
+      break;
+    default:
+      val = y;
+  }
+  J.C[r + (int64_t)c * J.ldc] = val;
+  if (J.Ch != nullptr) {
+    const float h = (float)val;
+    J.Ch[r + (int64_t)c * J.ldc] = h;
+    J.Cl[r + (int64_t)c * J.ldc] = (float)(val - (double)h);
+  }
+}
+
+__global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s, const double2* __restrict__ tw,
+                                                            ModelDev md, const int* __restrict__ done) {
+  pdl_wait();
+  pdl_trigger();
+  // every CTA of a cluster reads the same flag (written by an earlier grid),
+  // so a cluster exits as a whole or not at all
+  if (done != nullptr && *(volatile const int*)done) return;
+  cg::cluster_group cl = cg::this_cluster();
+  // distributed shared memory may be written only once every CTA of the
+  // cluster runs
+  cl.sync();
+  const int rank = (int)cl.block_rank();
+  const int tr = blockIdx.x / CIRC_P;
+  int jb = 0;
+  while (jb + 1 < jobs.n && tr >= jobs.tr_base[jb + 1]) ++jb;
+  const CircJob& J = jobs.j[jb];
+  const int pr = tr - jobs.tr_base[jb];
+  const int ca = 2 * pr, cb = 2 * pr + 1;
+  const bool hasb = cb < J.ncols;
+  const int Q = s / CIRC_P, QP = Q / CIRC_P;
+  extern __shared__ double2 circ_smem[];
+  double2* buf = circ_smem;       // phase 2 data: Y[rank, n2], n2 < Q
+  double2* buf2 = circ_smem + Q;  // phase 3 data: V[k1, n2] for this CTA's n2, k1-major
+  const double* xa = J.X + (int64_t)ca * J.ldx;
+  const double* xb = J.X + (int64_t)(hasb ? cb : ca) * J.ldx;
+
+  // ---- phase 1: 8-point DFTs over n1 for this CTA's n2
+  for (int t = threadIdx.x; t < QP; t += blockDim.x) {
+    const int n2 = rank * QP + t;
+    double2 u[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) {
+      const int idx = Q * n1 + n2;
+      u[n1] = make_double2(xa[idx], hasb ? xb[idx] : 0.0);
+    }
+    dft8<-1>(u);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+      const double2 v = (k1 == 0) ? u[0] : cmul(u[k1], tw[n2 * k1]);
+      double2* dst = cl.map_shared_rank(buf, k1);
+      dst[n2] = v;
+    }
+  }
+  cl.sync();
+
+  // ---- phase 2: length-Q FFT over n2 (DIF), lambda, inverse FFT (DIT)
+  const int half = Q / 2;
+  for (int h = half; h >= 1; h >>= 1) {
+    const int stride = (Q / (2 * h)) * CIRC_P;  // w_{2h}^j = w^(8 j Q / (2h))
+    for (int b = threadIdx.x; b < half; b += blockDim.x) {
+      const int j = b & (h - 1);
+      const int i = ((b / h) * 2 * h) + j;
+      const double2 u = buf[i], v = buf[i + h];
+      buf[i] = cadd(u, v);
+      buf[i + h] = (j == 0) ? csub(u, v) : cmul(csub(u, v), tw[j * stride]);
+    }
+    __syncthreads();
+  }
+  {
+    const double* lam = J.lam + (int64_t)rank * Q;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+      const double l = lam[i];
+      const double2 u = buf[i];
+      buf[i] = make_double2(u.x * l, u.y * l);
+    }
+  }
+  __syncthreads();
+  for (int h = 1; h <= half; h <<= 1) {
+    const int stride = (Q / (2 * h)) * CIRC_P;
+    for (int b = threadIdx.x; b < half; b += blockDim.x) {
+      const int j = b & (h - 1);
+      const int i = ((b / h) * 2 * h) + j;
+      const double2 u = buf[i];
+      const double2 v = (j == 0) ? buf[i + h] : cmulc(buf[i + h], tw[j * stride]);
+      buf[i] = cadd(u, v);
+      buf[i + h] = csub(u, v);
+    }
+    __syncthreads();
+  }
+  // twiddle w^(-n2 k1) and send W[rank, n2] to the CTA owning n2
+  for (int n2 = threadIdx.x; n2 < Q; n2 += blockDim.x) {
+    const double2 v = (rank == 0) ? buf[n2] : cmulc(buf[n2], tw[n2 * rank]);
+    double2* dst = cl.map_shared_rank(buf2, n2 / QP);
+    dst[rank * QP + (n2 % QP)] = v;
+  }
+  cl.sync();
+
+  // ---- phase 3: 8-point inverse DFTs over k1, / s, epilogue
+  const double inv_s = 1.0 / (double)s;
+  for (int t = threadIdx.x; t < QP; t += blockDim.x) {
+    const int n2 = rank * QP + t;
+    double2 u[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) u[k1] = buf2[k1 * QP + t];
+    dft8<1>(u);
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) {
+      const int r = Q * n1 + n2;
+      epilogue_store(J, md, s, r, ca, u[n1].x * inv_s);
+      if (hasb) epilogue_store(J, md, s, r, cb, u[n1].y * inv_s);
+    }
+  }
+}
+
+__global__ void circ_twiddle_kernel(double2* tw, int s) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < s; j += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)j / (double)s, &sn, &cs);
+    tw[j] = make_double2(cs, -sn);
+  }
+}
+
+// double-double sum (hi, lo) += a * b: exact product error by FMA, TwoSum
+__device__ __forceinline__ void dd_mac(double& hi, double& lo, double a, double b) {
+  const double p = a * b;
+  const double pe = fma(a, b, -p);
+  const double t = hi + p;
+  const double z = t - hi;
+  const double e = (hi - (t - z)) + (p - z);
+  hi = t;
+  lo += e + pe;
+}
+
+__device__ __forceinline__ int bitrev(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
+
+// one warp per frequency k: lambda_k = sum_j col[j] Re(w^(j k))
+__global__ void circ_spectrum_kernel(const double* __restrict__ col, int s, const double2* __restrict__ tw,
+                                     double shift, int invert, double* __restrict__ lam, int* flag) {
+  const int lane = threadIdx.x & 31;
+  const int Q = s / CIRC_P;
+  const int qbits = __ffs(Q) - 1;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < s; k += (gridDim.x * blockDim.x) >> 5) {
+    double hi = 0.0, lo = 0.0;
+    for (int j = lane; j < s; j += 32) {
+      const int m = (int)(((int64_t)j * k) % s);
+      dd_mac(hi, lo, col[j], tw[m].x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      const double t = hi + oh;
+      const double z = t - hi;
+      const double e = (hi - (t - z)) + (oh - z);
+      hi = t;
+      lo += ol + e;
+    }
+    if (lane == 0) {
+      const double v = (hi + lo) + shift;
+      if (!(v > 0.0) || !isfinite(v)) atomicExch(flag, 1);
+      const int k1 = k % CIRC_P, k2 = k / CIRC_P;
+      lam[(int64_t)k1 * Q + bitrev(k2, qbits)] = invert ? 1.0 / v : v;
+    }
+  }
+}
+
+// flag = 1 where |A[i + j s] - A[(i - j) mod s]| > tol A[0] (A SPD: its
+// diagonal bounds every entry)
+__global__ void circ_check_kernel(const double* __restrict__ A, int s, double tol, int* flag) {
+  const double lim = tol * fabs(A[0]);
+  const int64_t total = (int64_t)s * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % s), j = (int)(e / s);
+    int d = i - j;
+    d += (d < 0) ? s : 0;
+    const double a = A[e];
+    if (!(fabs(a - A[d]) <= lim)) atomicExch(flag, 1);
+  }
+}
+
+}  // namespace
+
+void launch_circ_check(const double* A, int s, double tol, int* flag, cudaStream_t st) {
+  const int64_t total = (int64_t)s * s;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  circ_check_kernel<<<blocks, 256, 0, st>>>(A, s, tol, flag);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_circ_twiddles(double2* tw, int s, cudaStream_t st) {
+  circ_twiddle_kernel<<<(s + 255) / 256, 256, 0, st>>>(tw, s);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_circ_spectrum(const double* col, int s, const double2* tw, double shift, int invert, double* lam,
+                          int* flag, cudaStream_t st) {
+  const int warps = 8;
+  const int blocks = std::min((s + warps - 1) / warps, 152 * 8);
+  circ_spectrum_kernel<<<blocks, 32 * warps, 0, st>>>(col, s, tw, shift, invert, lam, flag);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_circ(const CircJobs& jobs, int s, const double2* tw, const ModelDev& md, const int* done,
+                 cudaStream_t st) {
+  if (jobs.n == 0) return;
+  const int transforms = jobs.tr_base[jobs.n];
+  if (transforms == 0) return;
+  WC4D_CHECK(circ_size_ok(s), WC4D_ERR_ARG, "internal: circulant product of an unsupported size");
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(transforms * CIRC_P));
+  cfg.blockDim = dim3(CIRC_THREADS);
+  cfg.dynamicSmemBytes = sizeof(double2) * 2 * (s / CIRC_P);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CIRC_P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  WC4D_CUDA(cudaLaunchKernelEx(&cfg, circ_kernel, jobs, s, tw, md, done));
+  WC4D_LAUNCH_CHECK();
+}
+
+}  // namespace wc4d

@@ -256,10 +256,31 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// non-blocking probe of the phase (test_wait returns at once)
+__device__ __forceinline__ bool mbar_probe(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred q;\nmbarrier.test_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // bounded wait for the phase of the given parity; false after lim ns or once
-// another role has given up
+// another role has given up.  With the default limit the loop uses try_wait,
+// which lets the hardware suspend the thread until the phase completes (the
+// time is checked every 64 polls); a shorter limit (a test of the failure
+// path) polls with test_wait and checks the time on every poll, so that the
+// limit, not the suspension, decides.
 __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                        unsigned long long lim) {
+  if (lim < OZ_WAIT_NS) {
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+      if (mbar_probe(bar, parity)) return true;
+      if (*abort_flag || now_ns() - t0 > lim) return false;
+    }
+  }
   if (mbar_test(bar, parity)) return true;
   const unsigned long long t0 = now_ns();
   for (uint32_t it = 1;; ++it) {

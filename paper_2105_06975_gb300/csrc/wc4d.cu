@@ -15,6 +15,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "circulant.cuh"
 #include "common.cuh"
 #include "krylov.cuh"
 #include "learned.cuh"
@@ -245,6 +246,11 @@ struct wc4d_problem {
   bool have_pd = false;
   OpSet<double> f64;
   OpSet<float> f32;  // MIXED: FP32 copies for the inner solve
+  // WC4D_COVPROD_FFT: B and Q are circulant and applied by FFT (twiddle table,
+  // spectra of B, Q and of Bhat^-1, Qhat^-1 in the FFT kernel's cluster layout)
+  bool circ = false;
+  double2* tw = nullptr;
+  double *lamB = nullptr, *lamQ = nullptr, *lamBi = nullptr, *lamQi = nullptr;
   GemmPlan plan_A, plan_pd1, plan_pd2, plan_pi1, plan_pi2;
   // MIXED inner GMRES(m) workspace (FP32 basis, FP64 Hessenberg/rotations)
   int mi = 0;
@@ -284,6 +290,7 @@ struct wc4d_problem {
     int64_t slot;
     const char* what;
     int m;
+    bool spectrum = false;  // a circulant spectrum check instead of a Cholesky pivot
   };
   std::vector<CholCheck> chol_checks;
   std::vector<void*> allocs;
@@ -339,6 +346,30 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
   } else {
     saddle_c3<T>(P->md, v1, v2, P->d_inv, p, c3, done, P->st);
   }
+  if constexpr (sizeof(T) == 8) {
+    if (P->circ) {
+      // D v1 + L v3 by FFT (circulant B, Q), R v2 + H v3 on the product path
+      CircJobs cj{};
+      circ_add(cj, CircJob{v1, s, 1, P->lamB, EPI_SADDLE_C1, c1, s, 0, v3, nullptr, split ? wh : nullptr,
+                           split ? wl : nullptr});
+      if (N > 0)
+        circ_add(cj, CircJob{v1 + s, s, N, P->lamQ, EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr,
+                             split ? wh + s : nullptr, split ? wl + s : nullptr});
+      launch_circ(cj, s, P->tw, P->md, done, P->st);
+      GemmOpsT<T> ops{};
+      EpisT<T> ep{};
+      ops.nops = 1;
+      ops.op[0] = {os.R, p, v2, p, p, p, N + 1, TRI_FULL};
+      ep.e[0] = {EPI_SADDLE_C2, c2, p, 0, v3, nullptr};
+      if (split) {
+        ep.e[0].Ch = wh + P->ns;
+        ep.e[0].Cl = wl + P->ns;
+      }
+      os.attach(ops, P->st);
+      gemm_run<T>(plan, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+      return;
+    }
+  }
   GemmOpsT<T> ops{};
   EpisT<T> ep{};
   ops.nops = 3;
@@ -391,6 +422,34 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   T* u3 = os.t3;             // D y3 (or W_S v3)
   const bool exactS = (P->o.shat == WC4D_SHAT_EXACT);
   if (!exactS) lhat_sweep<T>(P->md, k, v3, y3, true, ident, done, P->st);
+  if constexpr (sizeof(T) == 8) {
+    if (P->circ) {
+      // Dhat^{-1} v1 and D y3 by FFT in one launch; Rhat^{-1} v2 = W^T (W v2)
+      GemmOpsT<T> ops{};
+      EpisT<T> ep{};
+      ops.nops = 1;
+      ops.op[0] = {os.WRt, p, v2, p, p, p, N + 1, TRI_LOWER};
+      ep.e[0] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
+      os.attach(ops, P->st);
+      gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+      CircJobs cj{};
+      circ_add(cj, CircJob{v1, s, 1, P->lamBi, EPI_STORE, o1, s, 0, nullptr, nullptr});
+      if (N > 0) circ_add(cj, CircJob{v1 + s, s, N, P->lamQi, EPI_STORE, o1 + s, s, 0, nullptr, nullptr});
+      circ_add(cj, CircJob{y3, s, 1, P->lamB, EPI_STORE, u3, s, 0, nullptr, nullptr});
+      if (N > 0) circ_add(cj, CircJob{y3 + s, s, N, P->lamQ, EPI_STORE, u3 + s, s, 0, nullptr, nullptr});
+      launch_circ(cj, s, P->tw, P->md, done, P->st);
+      GemmOpsT<T> ops2{};
+      EpisT<T> ep2{};
+      ops2.nops = 1;
+      ops2.op[0] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
+      ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
+      os.attach(ops2, P->st);
+      gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
+      lhat_sweep<T>(P->md, k, u3, o3, false, ident, done, P->st);
+      if (P->net_on) learned_block(P, o3);
+      return;
+    }
+  }
   GemmOpsT<T> ops{};
   EpisT<T> ep{};
   ops.op[0] = {os.WBt, s, v1, s, s, s, 1, TRI_LOWER};
@@ -455,6 +514,31 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   T* u = os.t2;   // v1 - D c1
   const bool ident = (P->o.lhat == WC4D_LHAT_I);
   lhat_sweep<T>(P->md, k, v3, o1, true, ident, done, P->st);
+  if constexpr (sizeof(T) == 8) {
+    if (P->circ) {
+      GemmOpsT<T> ops{};
+      EpisT<T> ep{};
+      ops.nops = 1;
+      ops.op[0] = {os.WRt, p, v2, p, p, p, N + 1, TRI_LOWER};
+      ep.e[0] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
+      os.attach(ops, P->st);
+      gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+      // u = v1 - D c1 by FFT
+      CircJobs cj{};
+      circ_add(cj, CircJob{o1, s, 1, P->lamB, EPI_SUB_FROM, u, s, 0, nullptr, v1});
+      if (N > 0) circ_add(cj, CircJob{o1 + s, s, N, P->lamQ, EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s});
+      launch_circ(cj, s, P->tw, P->md, done, P->st);
+      GemmOpsT<T> ops2{};
+      EpisT<T> ep2{};
+      ops2.nops = 1;
+      ops2.op[0] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
+      ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
+      os.attach(ops2, P->st);
+      gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
+      lhat_sweep<T>(P->md, k, u, o3, false, ident, done, P->st);
+      return;
+    }
+  }
   GemmOpsT<T> ops{};
   EpisT<T> ep{};
   ops.nops = 3;
@@ -775,6 +859,15 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
              "and FGMRES is only used by it");
   WC4D_CHECK(o->precision != WC4D_PREC_MIXED || (o->inner_iters >= 1 && o->inner_iters <= 200), WC4D_ERR_ARG,
              "inner_iters must lie in [1, 200]");
+  WC4D_CHECK(o->covprod == WC4D_COVPROD_DENSE || o->covprod == WC4D_COVPROD_FFT, WC4D_ERR_ARG, "bad covprod");
+  if (o->covprod == WC4D_COVPROD_FFT) {
+    WC4D_CHECK(circ_size_ok(d->s), WC4D_ERR_ARG, "covprod FFT needs s a power of two in [64, 8192]");
+    WC4D_CHECK(o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_DF32 ||
+                   o->precision == WC4D_PREC_OZAKI,
+               WC4D_ERR_ARG, "covprod FFT runs with precision FP64, DF32 or OZAKI");
+    WC4D_CHECK(o->shat != WC4D_SHAT_EXACT, WC4D_ERR_ARG,
+               "covprod FFT does not assemble the exact Schur complement (shat PAPER or LEARNED)");
+  }
 }
 
 static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
@@ -849,6 +942,35 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   launch_check_finite(f.B, (int64_t)s * s, d_flag + 1, st);
   launch_check_finite(f.Q, (int64_t)s * s, d_flag + 1, st);
   launch_check_finite(f.R, (int64_t)p * p, d_flag + 1, st);
+  // circulant B and Q (WC4D_COVPROD_FFT): twiddles and spectra
+  P->circ = (o->covprod == WC4D_COVPROD_FFT);
+  if (P->circ) {
+    if (d->cov_kind == WC4D_COV_DENSE) {
+      // the caller's B and Q must equal the circulants of their first columns
+      launch_circ_check(f.B, s, 1e-12, d_flag + 3, st);
+      launch_circ_check(f.Q, s, 1e-12, d_flag + 3, st);
+      WC4D_CHECK(read_flag(d_flag + 3, st) == 0, WC4D_ERR_ARG,
+                 "covprod FFT: B or Q is not circulant (entries differ from the circulant of the first column by "
+                 "more than 1e-12 of the diagonal)");
+    }
+    P->tw = P->alloc<double2>(s);
+    launch_circ_twiddles(P->tw, s, st);
+    auto spectrum = [&](const double* M, double shift, int invert, const char* what) {
+      WC4D_CHECK(P->chol_checks.size() < 12, WC4D_ERR_ARG, "internal: too many setup checks");
+      int* slot = P->d_flags + 4 + (int)P->chol_checks.size();
+      P->chol_checks.push_back({slot - P->d_flags, what, s, true});
+      double* lam = P->alloc<double>(s);
+      launch_circ_spectrum(M, s, P->tw, shift, invert, lam, slot, st);
+      return lam;
+    };
+    P->lamB = spectrum(f.B, 0.0, 0, "B");
+    P->lamQ = spectrum(f.Q, 0.0, 0, "Q");
+    if (o->precond == WC4D_PRECOND_PD) {
+      const double delta = (o->dhat == WC4D_DHAT_SHIFT) ? o->dhat_delta : 0.0;
+      P->lamBi = spectrum(f.B, delta, 1, "Bhat");
+      P->lamQi = spectrum(f.Q, delta, 1, "Qhat");
+    }
+  }
   const int mmax = std::max(s, p);
   double* scratch = P->alloc<double>((int64_t)mmax * 64 + 64 * 64 * 2);
   double* work = P->alloc<double>((int64_t)mmax * mmax);
@@ -861,7 +983,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   factor_inverse(P, work, p, f.WR, f.WRt, scratch, "Rhat");
   // Dhat factors (P_D only)
   P->have_pd = (o->precond == WC4D_PRECOND_PD);
-  if (P->have_pd) {
+  if (P->have_pd && !P->circ) {
     const double delta = (o->dhat == WC4D_DHAT_SHIFT) ? o->dhat_delta : 0.0;
     f.WB = P->alloc<double>((int64_t)s * s);
     f.WBt = P->alloc<double>((int64_t)s * s);
@@ -903,6 +1025,16 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   const bool ozm = (o->precision == WC4D_PREC_OZAKI);
   const int C = ozm ? oz_resident_ctas() : max_gemm_ctas(dfm);
   const int cm = ozm ? COST_TC : (dfm ? COST_DF32 : COST_FP64);
+  if (P->circ) {
+    // only the R family remains on the product path
+    plan_build(P->plan_A, {{p, p, N + 1, TRI_FULL}}, C, cm);
+    if (P->have_pd) {
+      plan_build(P->plan_pd1, {{p, p, N + 1, TRI_LOWER}}, C, cm);
+      plan_build(P->plan_pd2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
+    }
+    plan_build(P->plan_pi1, {{p, p, N + 1, TRI_LOWER}}, C, cm);
+    plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
+  } else {
   plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}, {p, p, N + 1, TRI_FULL}}, C, cm);
   if (P->have_pd) {
     if (o->shat == WC4D_SHAT_EXACT) {
@@ -919,6 +1051,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   }
   plan_build(P->plan_pi1, {{p, p, N + 1, TRI_LOWER}, {s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C, cm);
   plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
+  }
   int slots = std::max({P->plan_A.nslots, P->plan_pd1.nslots, P->plan_pd2.nslots, P->plan_pi1.nslots,
                         P->plan_pi2.nslots, 1});
   const GemmPlan* plans[5] = {&P->plan_A, &P->plan_pd1, &P->plan_pd2, &P->plan_pi1, &P->plan_pi2};
@@ -940,8 +1073,10 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       launch_split_df(m, h, l, cnt, st);
       f.splits.push_back({m, Split{h, l}});
     };
-    add(f.B, (int64_t)s * s);
-    add(f.Q, (int64_t)s * s);
+    if (!P->circ) {  // circulant B, Q never meet the product kernels
+      add(f.B, (int64_t)s * s);
+      add(f.Q, (int64_t)s * s);
+    }
     add(f.R, (int64_t)p * p);
     add(f.WR, (int64_t)p * p);
     add(f.WRt, (int64_t)p * p);
@@ -966,7 +1101,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       launch_oz_rows(m, rows, rows, rows, d, sc, st);
       f.digits.push_back({m, Digits{d, sc}});
     };
-    if (N >= 2) {
+    if (N >= 2 && !P->circ) {
       dig(f.Q, s);
       dig(f.WQ, s);
       dig(f.WQt, s);
@@ -1122,6 +1257,11 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   pinned_put(hf);
   WC4D_CHECK(hflags[1] == 0, WC4D_ERR_NONFINITE, "non-finite entries in the model or covariance inputs");
   for (const auto& ck : P->chol_checks) {
+    if (hflags[ck.slot] != 0 && ck.spectrum) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "circulant %s is not SPD: a spectrum value (plus the shift) is not positive", ck.what);
+      throw Error{WC4D_ERR_NOT_SPD, buf};
+    }
     if (hflags[ck.slot] != 0) {
       char buf[160];
       snprintf(buf, sizeof buf, "Cholesky of %s failed: non-positive pivot %d of %d", ck.what, hflags[ck.slot], ck.m);

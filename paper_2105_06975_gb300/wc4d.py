@@ -59,6 +59,8 @@ WC4D_PREC_MIXED = 1
 WC4D_PREC_DF32 = 2
 WC4D_PREC_DF32_P32 = 3
 WC4D_PREC_OZAKI = 4
+WC4D_COVPROD_DENSE = 0
+WC4D_COVPROD_FFT = 1
 
 RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG,
         "block": WC4D_RHAT_BLOCK}
@@ -87,7 +89,8 @@ class SolveOpts(ctypes.Structure):
                 ("maxit", ctypes.c_int32), ("precision", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("lhat", ctypes.c_int32), ("rblock_count", ctypes.c_int32),
                 ("rblock_sizes", ctypes.POINTER(ctypes.c_int32)), ("rblock_tol", ctypes.c_double),
-                ("rblock_maxsize", ctypes.c_int32), ("rblock_numproc", ctypes.c_int32)]
+                ("rblock_maxsize", ctypes.c_int32), ("rblock_numproc", ctypes.c_int32),
+                ("covprod", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -394,7 +397,7 @@ def wc4d_last_error() -> str:
 # -------------------------------------------------------------- convenience
 def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dhat="exact", dhat_delta=0.01,
               krylov=None, tol=1e-6, maxit=1000, precision="fp64", inner_iters=20, check_every=4, lhat="lm",
-              rblock=None) -> SolveOpts:
+              rblock=None, covprod="dense") -> SolveOpts:
     """``rblock`` = (channel block sizes, tol, maxsize, numproc) for rhat="block"
     (Alg. 3; maxsize / numproc None or 0 switch their rule off)."""
     o = wc4d_default_opts()
@@ -424,6 +427,7 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
                    "df32p32": WC4D_PREC_DF32_P32, "ozaki": WC4D_PREC_OZAKI}[precision]
     o.inner_iters = int(inner_iters)
     o.check_every = int(check_every)
+    o.covprod = {"dense": WC4D_COVPROD_DENSE, "fft": WC4D_COVPROD_FFT}[covprod]
     return o
 
 

@@ -102,6 +102,23 @@ def test_option_checks(lib, edits, needle):
     refused(lib, d, o, needle)
 
 
+@pytest.mark.parametrize("s,edits,needle", [
+    (16, {}, "power of two in [64, 8192]"),                 # base s = 16: below the FFT's smallest size
+    (96, {}, "power of two in [64, 8192]"),
+    (64, {"precision": L.WC4D_PREC_MIXED, "krylov": L.WC4D_KRYLOV_FGMRES}, "covprod FFT runs with precision"),
+    (64, {"precision": L.WC4D_PREC_DF32_P32}, "covprod FFT runs with precision"),
+    (64, {"precond": L.WC4D_PRECOND_PD, "krylov": L.WC4D_KRYLOV_MINRES, "shat": L.WC4D_SHAT_EXACT},
+     "exact Schur complement"),
+    (64, {"covprod": 5}, "bad covprod"),
+])
+def test_fft_covprod_checks(lib, s, edits, needle):
+    d, obs = base(s=s, N=2, p=8)
+    o = L.make_opts(covprod="fft")
+    for k, v in edits.items():
+        setattr(o, k, v)
+    refused(lib, d, o, needle)
+
+
 def test_exact_schur_size_limit(lib):
     d, obs = base(s=4096, N=2, p=8)
     refused(lib, d, L.make_opts(precond="PD", shat="exact"), "exact Schur complement limited")
