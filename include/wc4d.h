@@ -21,8 +21,9 @@
  *       [eta_0..eta_N (each s) | nu_0..nu_N (each p) | x_0..x_N (each s)],
  *   each block contiguous, so block k of a part is the column k of an
  *   s x (N+1) (or p x (N+1)) column-major matrix.
- * - Q_i = Q and R_i = R for every time level and H_i selects the same sorted
- *   observed grid points at every time (Sec. 6.1).
+ * - Q_i = Q for every time level.  By default R_i = R and H_i selects the
+ *   same sorted observed grid points at every time (Sec. 6.1); with
+ *   wc4d_problem_desc.p_t every time level has its own set and R_i.
  * - Dense matrices are column-major, symmetric, FP64.
  * - "device" pointers are CUDA global-memory addresses on the current
  *   device (e.g. torch tensor data_ptr()); "host" pointers are ordinary CPU
@@ -153,6 +154,18 @@ typedef struct {
   double soar_q[2];          /* SOAR: (sigma2, ell) of Q                                */
   double soar_r[2];          /* SOAR: (sigma2, ell) of R                                */
   int32_t mem_kind;          /* where bands/obs_idx/B/Q/R live: WC4D_MEM_HOST|DEVICE    */
+  const int32_t* p_t;        /* NULL: one set obs_idx[p] and one R (p x p) for every time
+                                level (Sec. 6.1).  Else per-time observation sets (Sec. 2.1:
+                                H = blkdiag(H_i), R = blkdiag(R_i)): host array of the N+1
+                                counts p_0..p_N, each in [1, s], summing to p; obs_idx then
+                                holds the N+1 strictly increasing sets one after another, a
+                                DENSE R the N+1 blocks R_0..R_N (p_i x p_i each) one after
+                                another, and SOAR builds each R_i over its own set.  In a
+                                vector nu_i is p_i long and starts at p_0 + .. + p_{i-1}.
+                                Each Rhat_i is built from R_i alone (rhat EXACT, DIAG, RR or
+                                ME); needs shat PAPER and precision FP64, DF32 or OZAKI, and
+                                is not available to wc4d_synthesize_rhs or the Lorenz-96
+                                calls.  Read during setup only.                           */
 } wc4d_problem_desc;
 
 typedef struct {
@@ -400,11 +413,13 @@ int wc4d_l96_gauss_newton(wc4d_problem* prob, const wc4d_l96_params* prm, const 
 int wc4d_l96_linearize(wc4d_problem* prob, const wc4d_l96_params* prm, const double* xb, const double* y,
                        const double* traj, int32_t mem_kind, double* rhs);
 
-/* Problem sizes: n (vector length), s, N, p. */
+/* Problem sizes: n (vector length), s, N, p (with per-time sets: the sum of p_i). */
 int wc4d_problem_dims(const wc4d_problem* prob, int64_t* n, int32_t* s, int32_t* N, int32_t* p);
 
 /* Copy a library-built covariance (which = 0: B, 1: Q, 2: R, 3: Rhat) into
- * dst (device, col-major, s*s or p*p doubles).  For tests and diagnostics. */
+ * dst (device, col-major, s*s or p*p doubles; with per-time sets, R and Rhat
+ * are the N+1 blocks one after another, sum of p_i^2 doubles).  For tests and
+ * diagnostics. */
 int wc4d_get_matrix(wc4d_problem* prob, int32_t which, double* dst);
 
 /* Rhat parameter used at setup: gamma (Alg. 1), T (Alg. 2) or the number of

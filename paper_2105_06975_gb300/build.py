@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwc4d.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["gemm.cu", "setup.cu", "ops.cu", "krylov.cu", "wc4d.cu", "stats.cu", "noalloc.cu", "l96.cu", "learned.cu",
-           "ozaki.cu", "circulant.cu"]
+           "ozaki.cu", "circulant.cu", "pertime.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -151,13 +151,16 @@ void launch_lhat_sweep(const ModelDev& md, int k, const double* v, double* z, bo
   lhat_sweep<double>(md, k, v, z, transpose, identity_model, done, st);
 }
 
-// c3_t[j] = v1_t[j] - [t < N] (M_{t+1}^T v1_{t+1})[j] + (H^T v2_t)[j],
-// H^T scatters nu_t[r] to grid point obs[r]; inv[j] = r or -1.
+// c3_t[j] = v1_t[j] - [t < N] (M_{t+1}^T v1_{t+1})[j] + (H_t^T v2_t)[j],
+// H_t^T scatters nu_t[r] to grid point obs_t[r]; inv[t * inv_stride + j] = r or
+// -1 (inv_stride = 0: one set for every time, nu_t at t p; inv_stride = s:
+// per-time sets, nu_t at nuoff[t]).
 // c3h / c3l (optional): the double-float split of c3 (hi = round(c3), lo = round(c3 - hi))
 template <typename T>
 __global__ void saddle_c3_kernel(ModelDev md, const T* __restrict__ v1, const T* __restrict__ v2,
                                  const int* __restrict__ inv, int p, T* __restrict__ c3, float* __restrict__ c3h,
-                                 float* __restrict__ c3l, const int* done) {
+                                 float* __restrict__ c3l, const int* done, int inv_stride = 0,
+                                 const int* __restrict__ nuoff = nullptr) {
   pdl_wait();
   pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
@@ -168,8 +171,8 @@ __global__ void saddle_c3_kernel(ModelDev md, const T* __restrict__ v1, const T*
     idx_divmod(e, s, total < ((int64_t)1 << 31), t, j);
     T val = v1[e];
     if (t < N) val -= model_apply_T<T>(md, t + 1, v1 + (int64_t)(t + 1) * s, j);
-    const int r = inv[j];
-    if (r >= 0) val += v2[(int64_t)t * p + r];
+    const int r = inv[(int64_t)t * inv_stride + j];
+    if (r >= 0) val += v2[(nuoff ? (int64_t)nuoff[t] : (int64_t)t * p) + r];
     c3[e] = val;
     if (c3h != nullptr) {
       const float h = (float)val;
@@ -185,14 +188,23 @@ void saddle_c3(const ModelDev& md, const T* v1, const T* v2, const int* inv, int
   const int64_t total = (int64_t)(md.N + 1) * md.s;
   const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   WC4D_CUDA(launch_pdl(saddle_c3_kernel<T>, dim3(nb), dim3(256), 0, st, md, v1, v2, inv, p, c3, (float*)nullptr,
-                       (float*)nullptr, done));
+                       (float*)nullptr, done, 0, (const int*)nullptr));
   WC4D_LAUNCH_CHECK();
 }
 void saddle_c3_split(const ModelDev& md, const double* v1, const double* v2, const int* inv, int p, double* c3,
                      float* c3h, float* c3l, const int* done, cudaStream_t st) {
   const int64_t total = (int64_t)(md.N + 1) * md.s;
   const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
-  WC4D_CUDA(launch_pdl(saddle_c3_kernel<double>, dim3(nb), dim3(256), 0, st, md, v1, v2, inv, p, c3, c3h, c3l, done));
+  WC4D_CUDA(launch_pdl(saddle_c3_kernel<double>, dim3(nb), dim3(256), 0, st, md, v1, v2, inv, p, c3, c3h, c3l, done,
+                       0, (const int*)nullptr));
+  WC4D_LAUNCH_CHECK();
+}
+void saddle_c3_pertime(const ModelDev& md, const double* v1, const double* v2, const int* inv_all, const int* nuoff,
+                       double* c3, float* c3h, float* c3l, const int* done, cudaStream_t st) {
+  const int64_t total = (int64_t)(md.N + 1) * md.s;
+  const int nb = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  WC4D_CUDA(launch_pdl(saddle_c3_kernel<double>, dim3(nb), dim3(256), 0, st, md, v1, v2, inv_all, 0, c3, c3h, c3l,
+                       done, md.s, nuoff));
   WC4D_LAUNCH_CHECK();
 }
 template void saddle_c3<double>(const ModelDev&, const double*, const double*, const int*, int, double*, const int*,

@@ -20,6 +20,7 @@
 #include "krylov.cuh"
 #include "learned.cuh"
 #include "ozaki.cuh"
+#include "pertime.cuh"
 #include "rblock.h"
 
 namespace wc4d {
@@ -35,6 +36,8 @@ void saddle_c3(const ModelDev& md, const T* v1, const T* v2, const int* inv, int
                cudaStream_t st);
 void saddle_c3_split(const ModelDev& md, const double* v1, const double* v2, const int* inv, int p, double* c3,
                      float* c3h, float* c3l, const int* done, cudaStream_t st);
+void saddle_c3_pertime(const ModelDev& md, const double* v1, const double* v2, const int* inv_all, const int* nuoff,
+                       double* c3, float* c3h, float* c3l, const int* done, cudaStream_t st);
 
 // Operator data in one precision: covariances, inverse Cholesky factors and
 // the GEMM partial buffer.
@@ -251,6 +254,14 @@ struct wc4d_problem {
   bool circ = false;
   double2* tw = nullptr;
   double *lamB = nullptr, *lamQ = nullptr, *lamBi = nullptr, *lamQi = nullptr;
+  // per-time observation sets (desc.p_t): counts, device layout of the nu
+  // blocks and of the R_i, Rhat_i, W_i = chol(Rhat_i)^-1 and W_i^T blocks
+  // (one after another); the inverse maps are (N+1) x s
+  bool pertime = false;
+  std::vector<int> pt;
+  PtLayout ptl{};
+  int64_t pt_elems = 0;  // sum of p_i^2
+  double *ptR = nullptr, *ptRh = nullptr, *ptW = nullptr, *ptWt = nullptr;
   GemmPlan plan_A, plan_pd1, plan_pd2, plan_pi1, plan_pi2;
   // MIXED inner GMRES(m) workspace (FP32 basis, FP64 Hessenberg/rotations)
   int mi = 0;
@@ -339,6 +350,47 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
   T* c3 = out + P->ns + P->np;
   const bool split = (sizeof(T) == 8) && wh != nullptr;
   if constexpr (sizeof(T) == 8) {
+    if (P->pertime) {
+      // c3 with each time's own set; D v1 + L v3 as usual; c2_t = R_t v2_t + H_t v3_t
+      saddle_c3_pertime(P->md, v1, v2, P->d_inv, P->ptl.nuoff, c3, split ? wh + P->ns + P->np : nullptr,
+                        split ? wl + P->ns + P->np : nullptr, done, P->st);
+      if (P->circ) {
+        CircJobs cj{};
+        circ_add(cj, CircJob{v1, s, 1, P->lamB, EPI_SADDLE_C1, c1, s, 0, v3, nullptr, split ? wh : nullptr,
+                             split ? wl : nullptr});
+        if (N > 0)
+          circ_add(cj, CircJob{v1 + s, s, N, P->lamQ, EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr,
+                               split ? wh + s : nullptr, split ? wl + s : nullptr});
+        launch_circ(cj, s, P->tw, P->md, done, P->st);
+      } else {
+        GemmOpsT<T> ops{};
+        EpisT<T> ep{};
+        ops.nops = 2;
+        ops.op[0] = {os.B, s, v1, s, s, s, 1, TRI_FULL};
+        ops.op[1] = {os.Q, s, v1 + s, s, s, s, N, TRI_FULL};
+        ep.e[0] = {EPI_SADDLE_C1, c1, s, 0, v3, nullptr};
+        ep.e[1] = {EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr};
+        if (split) {
+          ep.e[0].Ch = wh;
+          ep.e[0].Cl = wl;
+          ep.e[1].Ch = wh + s;
+          ep.e[1].Cl = wl + s;
+        }
+        os.attach(ops, P->st);
+        gemm_run<T>(plan, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+      }
+      PtProd pr{};
+      pr.A = P->ptR;
+      pr.tri = TRI_FULL;
+      pr.X = v2;
+      pr.mode = EPI_SADDLE_C2;
+      pr.C = c2;
+      pr.v3 = v3;
+      pr.Ch = split ? wh + P->ns : nullptr;
+      pr.Cl = split ? wl + P->ns : nullptr;
+      launch_pertime(P->ptl, pr, done, P->st);
+      return;
+    }
     if (split)
       saddle_c3_split(P->md, v1, v2, P->d_inv, p, c3, wh + P->ns + P->np, wl + P->ns + P->np, done, P->st);
     else
@@ -423,6 +475,56 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   const bool exactS = (P->o.shat == WC4D_SHAT_EXACT);
   if (!exactS) lhat_sweep<T>(P->md, k, v3, y3, true, ident, done, P->st);
   if constexpr (sizeof(T) == 8) {
+    if (P->pertime) {
+      // Rhat_t^{-1} v2_t = W_t^T (W_t v2_t) per time level; D parts as usual
+      PtProd pr{};
+      pr.A = P->ptWt;
+      pr.tri = TRI_LOWER;
+      pr.X = v2;
+      pr.mode = EPI_STORE;
+      pr.C = y2;
+      launch_pertime(P->ptl, pr, done, P->st);
+      if (P->circ) {
+        CircJobs cj{};
+        circ_add(cj, CircJob{v1, s, 1, P->lamBi, EPI_STORE, o1, s, 0, nullptr, nullptr});
+        if (N > 0) circ_add(cj, CircJob{v1 + s, s, N, P->lamQi, EPI_STORE, o1 + s, s, 0, nullptr, nullptr});
+        circ_add(cj, CircJob{y3, s, 1, P->lamB, EPI_STORE, u3, s, 0, nullptr, nullptr});
+        if (N > 0) circ_add(cj, CircJob{y3 + s, s, N, P->lamQ, EPI_STORE, u3 + s, s, 0, nullptr, nullptr});
+        launch_circ(cj, s, P->tw, P->md, done, P->st);
+      } else {
+        GemmOpsT<T> ops{};
+        EpisT<T> ep{};
+        ops.nops = 3;
+        ops.op[0] = {os.WBt, s, v1, s, s, s, 1, TRI_LOWER};
+        ops.op[1] = {os.WQt, s, v1 + s, s, s, s, N, TRI_LOWER};
+        ops.op[2] = {os.Q, s, y3 + s, s, s, s, N, TRI_FULL};
+        ep.e[0] = {EPI_STORE, y1, s, 0, nullptr, nullptr};
+        ep.e[1] = {EPI_STORE, y1 + s, s, 0, nullptr, nullptr};
+        ep.e[2] = {EPI_STORE, u3 + s, s, 0, nullptr, nullptr};
+        os.attach(ops, P->st);
+        gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+        GemmOpsT<T> ops2{};
+        EpisT<T> ep2{};
+        ops2.nops = 3;
+        ops2.op[0] = {os.WB, s, y1, s, s, s, 1, TRI_UPPER};
+        ops2.op[1] = {os.WQ, s, y1 + s, s, s, s, N, TRI_UPPER};
+        ops2.op[2] = {os.B, s, y3, s, s, s, 1, TRI_FULL};
+        ep2.e[0] = {EPI_STORE, o1, s, 0, nullptr, nullptr};
+        ep2.e[1] = {EPI_STORE, o1 + s, s, 0, nullptr, nullptr};
+        ep2.e[2] = {EPI_STORE, u3, s, 0, nullptr, nullptr};
+        os.attach(ops2, P->st);
+        gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
+      }
+      PtProd pr2{};
+      pr2.A = P->ptW;
+      pr2.tri = TRI_UPPER;
+      pr2.X = y2;
+      pr2.mode = EPI_STORE;
+      pr2.C = o2;
+      launch_pertime(P->ptl, pr2, done, P->st);
+      lhat_sweep<T>(P->md, k, u3, o3, false, ident, done, P->st);
+      return;
+    }
     if (P->circ) {
       // Dhat^{-1} v1 and D y3 by FFT in one launch; Rhat^{-1} v2 = W^T (W v2)
       GemmOpsT<T> ops{};
@@ -515,6 +617,40 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   const bool ident = (P->o.lhat == WC4D_LHAT_I);
   lhat_sweep<T>(P->md, k, v3, o1, true, ident, done, P->st);
   if constexpr (sizeof(T) == 8) {
+    if (P->pertime) {
+      PtProd pr{};
+      pr.A = P->ptWt;
+      pr.tri = TRI_LOWER;
+      pr.X = v2;
+      pr.mode = EPI_STORE;
+      pr.C = y2;
+      launch_pertime(P->ptl, pr, done, P->st);
+      if (P->circ) {
+        CircJobs cj{};
+        circ_add(cj, CircJob{o1, s, 1, P->lamB, EPI_SUB_FROM, u, s, 0, nullptr, v1});
+        if (N > 0) circ_add(cj, CircJob{o1 + s, s, N, P->lamQ, EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s});
+        launch_circ(cj, s, P->tw, P->md, done, P->st);
+      } else {
+        GemmOpsT<T> ops{};
+        EpisT<T> ep{};
+        ops.nops = 2;
+        ops.op[0] = {os.B, s, o1, s, s, s, 1, TRI_FULL};
+        ops.op[1] = {os.Q, s, o1 + s, s, s, s, N, TRI_FULL};
+        ep.e[0] = {EPI_SUB_FROM, u, s, 0, nullptr, v1};
+        ep.e[1] = {EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s};
+        os.attach(ops, P->st);
+        gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+      }
+      PtProd pr2{};
+      pr2.A = P->ptW;
+      pr2.tri = TRI_UPPER;
+      pr2.X = y2;
+      pr2.mode = EPI_STORE;
+      pr2.C = o2;
+      launch_pertime(P->ptl, pr2, done, P->st);
+      lhat_sweep<T>(P->md, k, u, o3, false, ident, done, P->st);
+      return;
+    }
     if (P->circ) {
       GemmOpsT<T> ops{};
       EpisT<T> ep{};
@@ -739,11 +875,9 @@ static void build_rblock(wc4d_problem* P, double* Rh) {
 }
 
 // Rhat (Sec. 5): copy of R, its diagonal, Alg. 1, Alg. 2 or Alg. 3.
-static void build_rhat(wc4d_problem* P, double* scratch, int* d_count) {
-  NvtxRange nvtx_range("wc4d.build_rhat");
-  const int p = P->p;
-  double* Rh = P->d_Rhat;
-  launch_copy_d(Rh, P->f64.R, (int64_t)p * p, P->st);
+// Rh (p x p) from R (p x p); per-time problems call it once per time level.
+static void build_rhat_of(wc4d_problem* P, const double* R, double* Rh, int p, int* d_count) {
+  launch_copy_d(Rh, R, (int64_t)p * p, P->st);
   const int rh = P->o.rhat;
   if (rh == WC4D_RHAT_EXACT) return;
   if (rh == WC4D_RHAT_DIAG) {
@@ -762,11 +896,11 @@ static void build_rhat(wc4d_problem* P, double* scratch, int* d_count) {
   double* Vv = P->alloc<double>((int64_t)m * m);
   double* rot = P->alloc<double>((int64_t)2 * m);
   launch_fill_d(A, 0.0, (int64_t)m * m, P->st);
-  WC4D_CUDA(cudaMemcpy2DAsync(A, sizeof(double) * m, P->f64.R, sizeof(double) * p, sizeof(double) * p, p,
+  WC4D_CUDA(cudaMemcpy2DAsync(A, sizeof(double) * m, R, sizeof(double) * p, sizeof(double) * p, p,
                               cudaMemcpyDeviceToDevice, P->st));
   if (m != p) {
     std::vector<double> h((size_t)p * p);
-    WC4D_CUDA(cudaMemcpyAsync(h.data(), P->f64.R, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, P->st));
+    WC4D_CUDA(cudaMemcpyAsync(h.data(), R, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, P->st));
     WC4D_CUDA(cudaStreamSynchronize(P->st));
     double tr = 0;
     for (int i = 0; i < p; ++i) tr += h[(size_t)i * p + i];
@@ -795,12 +929,31 @@ static void build_rhat(wc4d_problem* P, double* scratch, int* d_count) {
   WC4D_CUDA(cudaMemcpy2DAsync(Rh, sizeof(double) * p, C, sizeof(double) * m, sizeof(double) * p, p,
                               cudaMemcpyDeviceToDevice, P->st));
   launch_symmetrize(Rh, p, P->st);
-  (void)scratch;
+}
+
+static void build_rhat(wc4d_problem* P, int* d_count) {
+  NvtxRange nvtx_range("wc4d.build_rhat");
+  build_rhat_of(P, P->f64.R, P->d_Rhat, P->p, d_count);
 }
 
 static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(d && o, WC4D_ERR_ARG, "null descriptor or options");
-  WC4D_CHECK(d->s >= 2 && d->N >= 0 && d->p >= 1 && d->p <= d->s, WC4D_ERR_ARG, "need s >= 2, N >= 0, 1 <= p <= s");
+  WC4D_CHECK(d->s >= 2 && d->N >= 0 && d->p >= 1 && (d->p <= d->s || d->p_t != nullptr), WC4D_ERR_ARG,
+             "need s >= 2, N >= 0, 1 <= p <= s");
+  if (d->p_t != nullptr) {
+    int64_t sum = 0;
+    for (int t = 0; t <= d->N; ++t) {
+      WC4D_CHECK(d->p_t[t] >= 1 && d->p_t[t] <= d->s, WC4D_ERR_ARG, "per-time counts p_t must lie in [1, s]");
+      sum += d->p_t[t];
+    }
+    WC4D_CHECK(sum == d->p, WC4D_ERR_ARG, "per-time counts p_t must sum to p");
+    WC4D_CHECK(o != nullptr && (o->rhat == WC4D_RHAT_EXACT || o->rhat == WC4D_RHAT_DIAG ||
+                                o->rhat == WC4D_RHAT_RR || o->rhat == WC4D_RHAT_ME),
+               WC4D_ERR_ARG, "per-time observation sets take rhat EXACT, DIAG, RR or ME");
+    WC4D_CHECK(o->shat == WC4D_SHAT_PAPER, WC4D_ERR_ARG, "per-time observation sets take shat PAPER");
+    WC4D_CHECK(o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_OZAKI,
+               WC4D_ERR_ARG, "per-time observation sets run with precision FP64, DF32 or OZAKI");
+  }
   WC4D_CHECK(d->mem_kind == WC4D_MEM_HOST || d->mem_kind == WC4D_MEM_DEVICE, WC4D_ERR_ARG, "bad mem_kind");
   WC4D_CHECK(d->obs_idx != nullptr, WC4D_ERR_ARG, "obs_idx is null");
   WC4D_CHECK(d->model_kind == WC4D_MODEL_STENCIL3 || d->model_kind == WC4D_MODEL_BANDED, WC4D_ERR_ARG,
@@ -883,8 +1036,9 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->s = s;
   P->N = N;
   P->p = p;
+  P->pertime = (d->p_t != nullptr);
   P->ns = (int64_t)(N + 1) * s;
-  P->np = (int64_t)(N + 1) * p;
+  P->np = P->pertime ? (int64_t)p : (int64_t)(N + 1) * p;  // per-time: p = sum of p_t
   P->n = 2 * P->ns + P->np;
   cudaStream_t st = P->st;
   // flag slots: 0 observation indices, 1 non-finite inputs, 2 R reconditioning,
@@ -895,8 +1049,50 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * 17, st));
   // observation operator (the inverse map indexes by obs_idx: checked before it runs)
   P->d_obs = P->alloc<int>(p);
-  P->d_inv = P->alloc<int>(s);
-  if (d->mem_kind == WC4D_MEM_HOST) {
+  P->d_inv = P->alloc<int>(P->pertime ? (int64_t)(N + 1) * s : s);
+  int pmax = p;  // largest R block
+  if (P->pertime) {
+    // layout of the per-time nu blocks, R_i blocks and kernel tasks
+    P->pt.assign(d->p_t, d->p_t + N + 1);
+    std::vector<int> nuoff(N + 2, 0), taskoff(N + 2, 0);
+    std::vector<int64_t> aoff(N + 1, 0);
+    int64_t el = 0;
+    pmax = 0;
+    for (int t = 0; t <= N; ++t) {
+      const int pi = P->pt[t];
+      pmax = std::max(pmax, pi);
+      nuoff[t + 1] = nuoff[t] + pi;
+      taskoff[t + 1] = taskoff[t] + (pi + PT_ROWS - 1) / PT_ROWS;
+      aoff[t] = el;
+      el += (int64_t)pi * pi;
+    }
+    P->pt_elems = el;
+    int* d_pt = P->alloc<int>(N + 1);
+    int* d_nuoff = P->alloc<int>(N + 2);
+    int* d_taskoff = P->alloc<int>(N + 2);
+    int64_t* d_aoff = P->alloc<int64_t>(N + 1);
+    WC4D_CUDA(cudaMemcpyAsync(d_pt, P->pt.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
+    WC4D_CUDA(cudaMemcpyAsync(d_nuoff, nuoff.data(), sizeof(int) * (N + 2), cudaMemcpyHostToDevice, st));
+    WC4D_CUDA(cudaMemcpyAsync(d_taskoff, taskoff.data(), sizeof(int) * (N + 2), cudaMemcpyHostToDevice, st));
+    WC4D_CUDA(cudaMemcpyAsync(d_aoff, aoff.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+    P->ptl = PtLayout{N + 1, s, d_pt, d_nuoff, d_aoff, d_taskoff, P->d_obs, taskoff[N + 1]};
+    copy_in(P->d_obs, d->obs_idx, sizeof(int) * p, d->mem_kind, st);
+    for (int t = 0; t <= N; ++t) {
+      const int o0 = nuoff[t], pi = P->pt[t];
+      if (d->mem_kind == WC4D_MEM_HOST) {
+        for (int r = 0; r < pi; ++r)
+          WC4D_CHECK(d->obs_idx[o0 + r] >= 0 && d->obs_idx[o0 + r] < s &&
+                         (r == 0 || d->obs_idx[o0 + r] > d->obs_idx[o0 + r - 1]),
+                     WC4D_ERR_ARG, "each per-time set of obs_idx must be strictly increasing in [0, s)");
+      } else {
+        launch_check_obs(P->d_obs + o0, pi, s, d_flag, st);
+      }
+    }
+    WC4D_CHECK(read_flag(d_flag, st) == 0, WC4D_ERR_ARG,
+               "each per-time set of obs_idx must be strictly increasing in [0, s)");
+    for (int t = 0; t <= N; ++t) launch_inv_map(P->d_obs + nuoff[t], P->pt[t], P->d_inv + (int64_t)t * s, s, st);
+    WC4D_CUDA(cudaStreamSynchronize(st));  // the host layout arrays go out of scope
+  } else if (d->mem_kind == WC4D_MEM_HOST) {
     for (int r = 0; r < p; ++r)
       WC4D_CHECK(d->obs_idx[r] >= 0 && d->obs_idx[r] < s && (r == 0 || d->obs_idx[r] > d->obs_idx[r - 1]),
                  WC4D_ERR_ARG, "obs_idx must be strictly increasing in [0, s)");
@@ -906,7 +1102,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     launch_check_obs(P->d_obs, p, s, d_flag, st);
     WC4D_CHECK(read_flag(d_flag, st) == 0, WC4D_ERR_ARG, "obs_idx must be strictly increasing in [0, s)");
   }
-  launch_inv_map(P->d_obs, p, P->d_inv, s, st);
+  if (!P->pertime) launch_inv_map(P->d_obs, p, P->d_inv, s, st);
   // model
   P->md.kind = d->model_kind;
   P->md.s = s;
@@ -928,20 +1124,39 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   OpSet<double>& f = P->f64;
   f.B = P->alloc<double>((int64_t)s * s);
   f.Q = P->alloc<double>((int64_t)s * s);
-  f.R = P->alloc<double>((int64_t)p * p);
+  // R: one p x p matrix, or the per-time blocks R_0..R_N one after another
+  double* Rdst = nullptr;
+  int64_t Rcnt = 0;
+  if (P->pertime) {
+    P->ptR = P->alloc<double>(P->pt_elems);
+    Rdst = P->ptR;
+    Rcnt = P->pt_elems;
+  } else {
+    f.R = P->alloc<double>((int64_t)p * p);
+    Rdst = f.R;
+    Rcnt = (int64_t)p * p;
+  }
   if (d->cov_kind == WC4D_COV_DENSE) {
     copy_in(f.B, d->B, sizeof(double) * (size_t)s * s, d->mem_kind, st);
     copy_in(f.Q, d->Q, sizeof(double) * (size_t)s * s, d->mem_kind, st);
-    copy_in(f.R, d->R, sizeof(double) * (size_t)p * p, d->mem_kind, st);
+    copy_in(Rdst, d->R, sizeof(double) * (size_t)Rcnt, d->mem_kind, st);
   } else {
     double* tab = P->alloc<double>(s);
     launch_soar_fill(f.B, s, nullptr, s, d->soar_b[0], d->soar_b[1], tab, st);
     launch_soar_fill(f.Q, s, nullptr, s, d->soar_q[0], d->soar_q[1], tab, st);
-    launch_soar_fill(f.R, p, P->d_obs, s, d->soar_r[0], d->soar_r[1], tab, st);
+    if (P->pertime) {
+      for (int t = 0, o0 = 0; t <= N; o0 += P->pt[t], ++t) {
+        int64_t a0 = 0;
+        for (int u = 0; u < t; ++u) a0 += (int64_t)P->pt[u] * P->pt[u];
+        launch_soar_fill(P->ptR + a0, P->pt[t], P->d_obs + o0, s, d->soar_r[0], d->soar_r[1], tab, st);
+      }
+    } else {
+      launch_soar_fill(f.R, p, P->d_obs, s, d->soar_r[0], d->soar_r[1], tab, st);
+    }
   }
   launch_check_finite(f.B, (int64_t)s * s, d_flag + 1, st);
   launch_check_finite(f.Q, (int64_t)s * s, d_flag + 1, st);
-  launch_check_finite(f.R, (int64_t)p * p, d_flag + 1, st);
+  launch_check_finite(Rdst, Rcnt, d_flag + 1, st);
   // circulant B and Q (WC4D_COVPROD_FFT): twiddles and spectra
   P->circ = (o->covprod == WC4D_COVPROD_FFT);
   if (P->circ) {
@@ -971,16 +1186,40 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       P->lamQi = spectrum(f.Q, delta, 1, "Qhat");
     }
   }
-  const int mmax = std::max(s, p);
+  const int mmax = std::max(s, pmax);
   double* scratch = P->alloc<double>((int64_t)mmax * 64 + 64 * 64 * 2);
   double* work = P->alloc<double>((int64_t)mmax * mmax);
+  if (P->pertime) {
+    // Rhat_i from each R_i alone (Sec. 5), then W_i = chol(Rhat_i)^-1 and W_i^T;
+    // one pivot-check slot for all time levels
+    NvtxRange nvtx_r("wc4d.build_rhat");
+    P->ptRh = P->alloc<double>(P->pt_elems);
+    P->ptW = P->alloc<double>(P->pt_elems);
+    P->ptWt = P->alloc<double>(P->pt_elems);
+    WC4D_CHECK(P->chol_checks.size() < 12, WC4D_ERR_ARG, "internal: too many setup checks");
+    int* slot = P->d_flags + 4 + (int)P->chol_checks.size();
+    P->chol_checks.push_back({slot - P->d_flags, "a per-time Rhat_i", pmax});
+    double param0 = 0.0;
+    int64_t a0 = 0;
+    for (int t = 0; t <= N; ++t) {
+      const int pi = P->pt[t];
+      build_rhat_of(P, P->ptR + a0, P->ptRh + a0, pi, d_flag + 2);
+      if (t == 0) param0 = P->rhat_param;
+      launch_copy_d(work, P->ptRh + a0, (int64_t)pi * pi, st);
+      cholesky(work, pi, slot, st, scratch);
+      tri_inverse(work, P->ptW + a0, P->ptWt + a0, pi, st, scratch);
+      a0 += (int64_t)pi * pi;
+    }
+    P->rhat_param = param0;
+  } else {
   // Rhat and its inverse factor
   P->d_Rhat = P->alloc<double>((int64_t)p * p);
-  build_rhat(P, scratch, d_flag + 2);
+  build_rhat(P, d_flag + 2);
   f.WR = P->alloc<double>((int64_t)p * p);
   f.WRt = P->alloc<double>((int64_t)p * p);
   launch_copy_d(work, P->d_Rhat, (int64_t)p * p, st);
   factor_inverse(P, work, p, f.WR, f.WRt, scratch, "Rhat");
+  }
   // Dhat factors (P_D only)
   P->have_pd = (o->precond == WC4D_PRECOND_PD);
   if (P->have_pd && !P->circ) {
@@ -1025,7 +1264,17 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   const bool ozm = (o->precision == WC4D_PREC_OZAKI);
   const int C = ozm ? oz_resident_ctas() : max_gemm_ctas(dfm);
   const int cm = ozm ? COST_TC : (dfm ? COST_DF32 : COST_FP64);
-  if (P->circ) {
+  if (P->pertime && P->circ) {
+    // every product is a transform or a per-time product: no GEMM plans
+  } else if (P->pertime) {
+    // the R family runs in the per-time kernel: plans for the D products only
+    plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C, cm);
+    if (P->have_pd) {
+      plan_build(P->plan_pd1, {{s, s, 1, TRI_LOWER}, {s, s, N, TRI_LOWER}, {s, s, N, TRI_FULL}}, C, cm);
+      plan_build(P->plan_pd2, {{s, s, 1, TRI_UPPER}, {s, s, N, TRI_UPPER}, {s, s, 1, TRI_FULL}}, C, cm);
+    }
+    plan_build(P->plan_pi1, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C, cm);
+  } else if (P->circ) {
     // only the R family remains on the product path
     plan_build(P->plan_A, {{p, p, N + 1, TRI_FULL}}, C, cm);
     if (P->have_pd) {
@@ -1748,6 +1997,7 @@ void gn_rhs(const double* xb, const double* traj, const double* fc, const double
 static void l96_check(wc4d_problem* P, const wc4d_l96_params* prm) {
   WC4D_CHECK(prm != nullptr, WC4D_ERR_ARG, "null parameters");
   WC4D_CHECK(P->md.kind == WC4D_MODEL_BANDED, WC4D_ERR_ARG, "Gauss-Newton for Lorenz-96 needs a BANDED problem");
+  WC4D_CHECK(!P->pertime, WC4D_ERR_ARG, "the Lorenz-96 calls observe one set at every time (no per-time sets)");
   WC4D_CHECK(prm->steps_per_obs >= 1 && prm->outer_loops >= 0 && prm->dt > 0, WC4D_ERR_ARG, "bad L96 parameters");
   WC4D_CHECK(P->md.lo == 8 * prm->steps_per_obs && P->md.hi == 4 * prm->steps_per_obs, WC4D_ERR_ARG,
              "band offsets must be lo = 8 steps, hi = 4 steps");
@@ -1855,6 +2105,7 @@ __global__ void obs_rhs_kernel(const double* traj, const double* E, const int* o
 
 static void synthesize_rhs(wc4d_problem* P, const double* zb_in, const double* zr_in, int mem_kind, double* rhs_out) {
   WC4D_CHECK(P->md.kind == WC4D_MODEL_STENCIL3, WC4D_ERR_ARG, "synthesize_rhs needs a linear (STENCIL3) model");
+  WC4D_CHECK(!P->pertime, WC4D_ERR_ARG, "synthesize_rhs observes one set at every time (no per-time sets)");
   const int s = P->s, p = P->p, N = P->N;
   cudaStream_t st = P->st;
   const int mmax = std::max(s, p);
@@ -2575,8 +2826,14 @@ int wc4d_get_matrix(wc4d_problem* P, int32_t which, double* dst) {
   switch (which) {
     case 0: src = P->f64.B; cnt = (int64_t)P->s * P->s; break;
     case 1: src = P->f64.Q; cnt = (int64_t)P->s * P->s; break;
-    case 2: src = P->f64.R; cnt = (int64_t)P->p * P->p; break;
-    case 3: src = P->d_Rhat; cnt = (int64_t)P->p * P->p; break;
+    case 2:
+      src = P->pertime ? P->ptR : P->f64.R;
+      cnt = P->pertime ? P->pt_elems : (int64_t)P->p * P->p;
+      break;
+    case 3:
+      src = P->pertime ? P->ptRh : P->d_Rhat;
+      cnt = P->pertime ? P->pt_elems : (int64_t)P->p * P->p;
+      break;
     default: throw wc4d::Error{WC4D_ERR_ARG, "which must be 0..3"};
   }
   WC4D_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, P->st));

@@ -79,7 +79,7 @@ class ProblemDesc(ctypes.Structure):
                 ("obs_idx", ctypes.c_void_p), ("cov_kind", ctypes.c_int32),
                 ("B", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("R", ctypes.c_void_p),
                 ("soar_b", ctypes.c_double * 2), ("soar_q", ctypes.c_double * 2), ("soar_r", ctypes.c_double * 2),
-                ("mem_kind", ctypes.c_int32)]
+                ("mem_kind", ctypes.c_int32), ("p_t", ctypes.POINTER(ctypes.c_int32))]
 
 
 class SolveOpts(ctypes.Structure):
@@ -437,16 +437,27 @@ class Problem:
 
     def __init__(self, s, N, p, obs_idx, opts: SolveOpts, *, stencil=None, bands=None, band_lo=0, band_hi=0,
                  banded=False, B=None, Q=None, R=None, soar_b=None, soar_q=None, soar_r=None,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, obs_list=None):
+        """``obs_list``: per-time observation sets (N+1 sorted index arrays);
+        then ``p`` and ``obs_idx`` are ignored and a dense ``R`` is a list of
+        the N+1 blocks R_i."""
         import torch
         d = ProblemDesc()
-        d.s, d.N, d.p = int(s), int(N), int(p)
         keep = []
 
         def host(a, dtype):
             a = np.ascontiguousarray(a, dtype=dtype)
             keep.append(a)
             return a.ctypes.data
+        if obs_list is not None:
+            pt = np.array([len(o) for o in obs_list], dtype=np.int32)
+            keep.append(pt)
+            d.p_t = pt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            p = int(pt.sum())
+            obs_idx = np.concatenate([np.asarray(o, dtype=np.int32) for o in obs_list])
+            if R is not None and not isinstance(R, np.ndarray):
+                R = np.concatenate([np.ascontiguousarray(Ri, dtype=np.float64).ravel() for Ri in R])
+        d.s, d.N, d.p = int(s), int(N), int(p)
         d.obs_idx = host(obs_idx, np.int32)
         if bands is not None or banded:
             d.model_kind = WC4D_MODEL_BANDED
@@ -479,6 +490,8 @@ class Problem:
         c = w.stencil()
         if dense:
             return cls(w.s, w.N, w.p, dr.obs_idx, opts, stencil=c, **kw)
+        if w.obs_per_time and "obs_list" not in kw:
+            kw["obs_list"] = dr.extra["obs_list"]
         return cls(w.s, w.N, w.p, dr.obs_idx, opts, stencil=kw.pop("stencil", c), soar_b=w.soar_b,
                    soar_q=w.soar_q, soar_r=w.soar_r, **kw)
 

@@ -119,6 +119,27 @@ def test_fft_covprod_checks(lib, s, edits, needle):
     refused(lib, d, o, needle)
 
 
+@pytest.mark.parametrize("counts,opt_edits,needle", [
+    ([4, 4, 3], {}, "must sum to p"),                       # p = 12 in the descriptor
+    ([4, 0, 8], {}, "must lie in [1, s]"),
+    ([4, 4, 17], {}, "must lie in [1, s]"),
+    ([4, 4, 4], {"rhat": L.WC4D_RHAT_BLOCK}, "rhat EXACT, DIAG, RR or ME"),
+    ([4, 4, 4], {"precond": L.WC4D_PRECOND_PD, "krylov": L.WC4D_KRYLOV_MINRES, "shat": L.WC4D_SHAT_EXACT},
+     "shat PAPER"),
+    ([4, 4, 4], {"precision": L.WC4D_PREC_MIXED, "krylov": L.WC4D_KRYLOV_FGMRES}, "precision FP64, DF32 or OZAKI"),
+])
+def test_per_time_checks(lib, counts, opt_edits, needle):
+    d, obs = base(s=16, N=2, p=12)
+    pt = np.array(counts, dtype=np.int32)
+    d.p_t = pt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    allobs = np.concatenate([np.arange(max(c, 1), dtype=np.int32) for c in counts])
+    d.obs_idx = allobs.ctypes.data
+    o = L.make_opts()
+    for k, v in opt_edits.items():
+        setattr(o, k, v)
+    refused(lib, d, o, needle)
+
+
 def test_exact_schur_size_limit(lib):
     d, obs = base(s=4096, N=2, p=8)
     refused(lib, d, L.make_opts(precond="PD", shat="exact"), "exact Schur complement limited")
