@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--maxit", type=int, default=1000, help="Krylov iteration cap (workspace size)")
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
-    ap.add_argument("--chosen", default="ozaki", choices=["fp64", "df32", "df32p32", "mixed", "ozaki"])
+    ap.add_argument("--chosen", default="ozaki", choices=["fp64", "df32", "df32p32", "mixed", "ozaki", "fp64_fft",
+                                                          "df32_fft", "ozaki_fft"])
     ap.add_argument("--precision", default="ozaki", choices=["df32", "ozaki"],
                     help="product precision of the batched and learned workloads")
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
@@ -236,13 +237,22 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA: 128/clk/SM (measu
 DF32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 12 / 1e12
 MODE_DTYPE = {"fp64": "f64", "df32": "df32 products (2 x f32, ~48-bit) / f64 recurrences",
               "mixed": "f32 inner / df32-f64 outer",
-              "ozaki": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / df32 / f64 recurrences"}
+              "ozaki": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / df32 / f64 recurrences",
+              "fp64_fft": "f64 (B, Q by f64 FFT)",
+              "df32_fft": "f64 FFT for B, Q; df32 R-family products / f64 recurrences",
+              "ozaki_fft": "f64 FFT for B, Q; bf16 digit products exact in f32 for the R family / df32 / f64 "
+                           "recurrences"}
 MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
              "df32": "FP64 GMRES; covariance / factor products in double-float on the FP32 pipe",
              "ozaki": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
                       "on the tensor cores (tcgen05, TMEM accumulators), one-column products in double-float",
              "mixed": "FGMRES outer (double-float A, FP64 true residual) around FP32 inner GMRES({inner}) "
-                      "preconditioned by FP32 {pc}"}
+                      "preconditioned by FP32 {pc}",
+             "fp64_fft": "plain FP64 with circulant B, Q (and Bhat^-1, Qhat^-1) by FP64 FFT",
+             "df32_fft": "FP64 Krylov; circulant B, Q by FP64 FFT; R-family products in double-float",
+             "ozaki_fft": "FP64 Krylov; circulant B, Q (and Bhat^-1, Qhat^-1) by FP64 FFT (cluster-split "
+                          "four-step transform); multi-column R-family products as exact BF16 digit products "
+                          "on tcgen05"}
 
 
 # DRAM bytes per launch of gemm_streamk_df32_kernel, ncu dram__bytes_read.sum + dram__bytes_write.sum,
@@ -316,6 +326,25 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                              "flops_per_launch": st.gemm32_flops / st.gemm32_launches,
                              "share_of_step": st.gemm32_ms / step_ms,
                              "peak_source": "derived: 152 SM x 256 FP32 flop/clk x 2.07 GHz"}
+    if st.circ_launches:
+        a = st.circ_flops / (st.circ_ms * 1e-3) / 1e12
+        rows["circ_fft"] = {"kernel": "circ_kernel (circulant B, Q and their inverses by FP64 FFT, 8-CTA clusters)",
+                            "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": a / FP64_PEAK_TFLOPS, "launches": st.circ_launches,
+                            "ms_per_launch": st.circ_ms / st.circ_launches,
+                            "flops_per_launch": st.circ_flops / st.circ_launches,
+                            "bytes_per_launch": st.circ_bytes / st.circ_launches,
+                            "hbm_gbs": st.circ_bytes / (st.circ_ms * 1e-3) / 1e9,
+                            "share_of_step": st.circ_ms / step_ms,
+                            "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz; flops counted as "
+                                           "5 s log2 s per complex transform"}
+    if st.pt_launches:
+        a = st.pt_bytes / (st.pt_ms * 1e-3) / 1e9
+        rows["pertime"] = {"kernel": "pertime_kernel (per-time R_i family products)", "bound": "hbm",
+                           "achieved": a, "peak": hbm, "unit": "GB/s", "frac": (a / hbm) if hbm else None,
+                           "launches": st.pt_launches, "ms_per_launch": st.pt_ms / st.pt_launches,
+                           "bytes_per_launch": st.pt_bytes / st.pt_launches, "share_of_step": st.pt_ms / step_ms,
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     if st.orth_launches:
         a = st.orth_bytes / (st.orth_ms * 1e-3) / 1e9
         name = ("gm_dc_dot/gm_dc_update (delayed-CGS2 Arnoldi passes)" if dcgs
@@ -354,6 +383,11 @@ def run_gpu(args):
         "ozaki": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
                                 precision="ozaki", check_every=ce),
     }
+    # circulant B and Q applied by FFT (Sec. 6.1), the R family as in the base mode
+    for m in ("fp64", "df32", "ozaki"):
+        if args.chosen == m + "_fft" or (args.modes and m + "_fft" in args.modes.split(",")):
+            modes[m + "_fft"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
+                                               maxit=args.maxit, precision=m, check_every=ce, covprod="fft")
     if args.chosen == "df32p32" or (args.modes and "df32p32" in args.modes.split(",")):
         # FP32 preconditioner: only for covariances with kappa * eps32 << 1 (not this workload's R)
         modes["df32p32"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
@@ -432,7 +466,8 @@ def run_gpu(args):
             ms = float(tt.item())
         assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
         results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
-                         "kernels": kernel_rows(st, prof_ms, hbm, dcgs=mode in ("df32", "df32p32", "ozaki")),
+                         "kernels": kernel_rows(st, prof_ms, hbm, dcgs=mode in ("df32", "df32p32", "ozaki", "df32_fft",
+                                                                              "ozaki_fft")),
                          "profiled_ms_per_step": prof_ms / args.steps,
                          "setup_ms": statistics.mean(a for a, _ in split),
                          "solve_ms": statistics.mean(b for _, b in split)}

@@ -457,6 +457,15 @@ typedef struct {
                                        partial tiles written                                       */
   double gemmtc_mma_flops;          /* BF16 tensor-core flops of the digit products issued         */
   int64_t gemmtc_launches;
+  double circ_ms, circ_flops;       /* circulant FFT products (WC4D_COVPROD_FFT): FP64 flops counted
+                                       as 5 s log2 s per complex transform (two per column pair) plus
+                                       the spectrum scaling                                          */
+  double circ_bytes;                /* input columns read and output columns written (+ epilogue
+                                       operands)                                                    */
+  int64_t circ_launches;
+  double pt_ms, pt_bytes;           /* per-time R-family products: operator blocks (their triangle
+                                       for factors) read once, vectors read and written             */
+  int64_t pt_launches;
 } wc4d_stats;
 void wc4d_set_profiling(int32_t enable);
 void wc4d_reset_stats(void);

@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "circulant.cuh"
 #include "model_dev.cuh"
@@ -117,12 +118,13 @@ __device__ __forceinline__ void epilogue_store(const CircJob& J, const ModelDev&
 }
 
 __global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s, const double2* __restrict__ tw,
-                                                            ModelDev md, const int* __restrict__ done) {
+                                                            ModelDev md, const int* __restrict__ done, int* ran) {
   pdl_wait();
   pdl_trigger();
   // every CTA of a cluster reads the same flag (written by an earlier grid),
   // so a cluster exits as a whole or not at all
   if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
   cg::cluster_group cl = cg::this_cluster();
   // distributed shared memory may be written only once every CTA of the
   // cluster runs
@@ -327,8 +329,22 @@ void launch_circ(const CircJobs& jobs, int s, const double2* tw, const ModelDev&
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  WC4D_CUDA(cudaLaunchKernelEx(&cfg, circ_kernel, jobs, s, tw, md, done));
+  // algorithmic work: 5 s log2 s flops per complex transform, two transforms
+  // and the real spectrum scaling (2 flops per entry) per column pair; bytes:
+  // every column read and written once, plus the epilogue operands
+  int* ran = nullptr;
+  if (prof_enabled()) {
+    const double lg = std::log2((double)s);
+    double bytes = 0.0;
+    for (int q = 0; q < jobs.n; ++q) {
+      const int ep = (jobs.j[q].mode == EPI_SADDLE_C1 || jobs.j[q].mode == EPI_SUB_FROM) ? 1 : 0;
+      bytes += 8.0 * s * jobs.j[q].ncols * (2 + ep);
+    }
+    ran = prof_begin(PROF_CIRC, transforms * (10.0 * s * lg + 2.0 * s), st, bytes);
+  }
+  WC4D_CUDA(cudaLaunchKernelEx(&cfg, circ_kernel, jobs, s, tw, md, done, ran));
   WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
 }
 
 }  // namespace wc4d

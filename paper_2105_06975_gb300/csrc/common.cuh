@@ -349,7 +349,8 @@ int gemm_resident_ctas(bool df32);
 // Opt-in kernel profile: CUDA events around the timed kernel classes on the
 // launching stream; the kernel itself marks whether it did work (launches that
 // exit early on a converged solve do not count).
-enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_GEMM32 = 2, PROF_GEMMDF = 3, PROF_GEMMTC = 4, PROF_CLASSES = 5 };
+enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_GEMM32 = 2, PROF_GEMMDF = 3, PROF_GEMMTC = 4, PROF_CIRC = 5,
+       PROF_PERTIME = 6, PROF_CLASSES = 7 };
 bool prof_enabled();
 // returns a device int* the kernel sets to 1 when it runs (nullptr when off)
 int* prof_begin(int cls, double work, cudaStream_t st, double work2 = 0.0, double work3 = 0.0);

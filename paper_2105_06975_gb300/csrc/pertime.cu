@@ -12,10 +12,12 @@
 namespace wc4d {
 namespace {
 
-__global__ void __launch_bounds__(PT_THREADS) pertime_kernel(PtLayout L, PtProd op, const int* __restrict__ done) {
+__global__ void __launch_bounds__(PT_THREADS) pertime_kernel(PtLayout L, PtProd op, const int* __restrict__ done,
+                                                              int* ran) {
   pdl_wait();
   pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int task = blockIdx.x; task < L.tasks; task += gridDim.x) {
     // time level of this task: the last t with taskoff[t] <= task
@@ -70,11 +72,13 @@ __global__ void __launch_bounds__(PT_THREADS) pertime_kernel(PtLayout L, PtProd 
 
 }  // namespace
 
-void launch_pertime(const PtLayout& L, const PtProd& op, const int* done, cudaStream_t st) {
+void launch_pertime(const PtLayout& L, const PtProd& op, double bytes, const int* done, cudaStream_t st) {
   if (L.tasks <= 0) return;
   const int grid = std::min(L.tasks, 152 * 8);
-  WC4D_CUDA(launch_pdl(pertime_kernel, dim3(grid), dim3(PT_THREADS), 0, st, L, op, done));
+  int* ran = prof_enabled() ? prof_begin(PROF_PERTIME, bytes, st) : nullptr;
+  WC4D_CUDA(launch_pdl(pertime_kernel, dim3(grid), dim3(PT_THREADS), 0, st, L, op, done, ran));
   WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
 }
 
 }  // namespace wc4d

@@ -37,6 +37,7 @@ struct PtLayout {
 constexpr int PT_ROWS = 32;     // rows per CTA task (4 per warp)
 constexpr int PT_THREADS = 256;
 
-void launch_pertime(const PtLayout& L, const PtProd& op, const int* done, cudaStream_t st);
+// bytes: the launch's algorithmic bytes, recorded when profiling is on
+void launch_pertime(const PtLayout& L, const PtProd& op, double bytes, const int* done, cudaStream_t st);
 
 }  // namespace wc4d

@@ -128,6 +128,15 @@ int wc4d_get_stats(wc4d_stats* out) {
       out->gemmtc_bytes += p.recs[i].work2;
       out->gemmtc_mma_flops += p.recs[i].work3;
       out->gemmtc_launches += 1;
+    } else if (p.recs[i].cls == PROF_CIRC) {
+      out->circ_ms += ms;
+      out->circ_flops += p.recs[i].work;
+      out->circ_bytes += p.recs[i].work2;
+      out->circ_launches += 1;
+    } else if (p.recs[i].cls == PROF_PERTIME) {
+      out->pt_ms += ms;
+      out->pt_bytes += p.recs[i].work;
+      out->pt_launches += 1;
     } else if (p.recs[i].cls == PROF_GEMM32) {
       out->gemm32_ms += ms;
       out->gemm32_flops += p.recs[i].work;

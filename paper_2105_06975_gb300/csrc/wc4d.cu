@@ -336,6 +336,14 @@ namespace wc4d {
 
 static int max_gemm_ctas(bool df32 = false) { return gemm_resident_ctas(df32); }
 
+// algorithmic bytes of one per-time product: each block (its triangle for the
+// factors) read once, x read and the output written once (+ the gathered v3)
+static double pt_bytes(const wc4d_problem* P, const PtProd& pr) {
+  double a = 0.0;
+  for (int pi : P->pt) a += (pr.tri == TRI_FULL) ? (double)pi * pi : 0.5 * (double)pi * (pi + 1);
+  return 8.0 * (a + (double)P->np * (pr.mode == EPI_SADDLE_C2 ? 3 : 2));
+}
+
 // ------------------------------------------------------------ A v (Sec. 6.2)
 // wh / wl (T = double, optional): also write the double-float split of out
 template <typename T>
@@ -388,7 +396,7 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
       pr.v3 = v3;
       pr.Ch = split ? wh + P->ns : nullptr;
       pr.Cl = split ? wl + P->ns : nullptr;
-      launch_pertime(P->ptl, pr, done, P->st);
+      launch_pertime(P->ptl, pr, pt_bytes(P, pr), done, P->st);
       return;
     }
     if (split)
@@ -483,7 +491,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       pr.X = v2;
       pr.mode = EPI_STORE;
       pr.C = y2;
-      launch_pertime(P->ptl, pr, done, P->st);
+      launch_pertime(P->ptl, pr, pt_bytes(P, pr), done, P->st);
       if (P->circ) {
         CircJobs cj{};
         circ_add(cj, CircJob{v1, s, 1, P->lamBi, EPI_STORE, o1, s, 0, nullptr, nullptr});
@@ -521,7 +529,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       pr2.X = y2;
       pr2.mode = EPI_STORE;
       pr2.C = o2;
-      launch_pertime(P->ptl, pr2, done, P->st);
+      launch_pertime(P->ptl, pr2, pt_bytes(P, pr2), done, P->st);
       lhat_sweep<T>(P->md, k, u3, o3, false, ident, done, P->st);
       return;
     }
@@ -624,7 +632,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       pr.X = v2;
       pr.mode = EPI_STORE;
       pr.C = y2;
-      launch_pertime(P->ptl, pr, done, P->st);
+      launch_pertime(P->ptl, pr, pt_bytes(P, pr), done, P->st);
       if (P->circ) {
         CircJobs cj{};
         circ_add(cj, CircJob{o1, s, 1, P->lamB, EPI_SUB_FROM, u, s, 0, nullptr, v1});
@@ -647,7 +655,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       pr2.X = y2;
       pr2.mode = EPI_STORE;
       pr2.C = o2;
-      launch_pertime(P->ptl, pr2, done, P->st);
+      launch_pertime(P->ptl, pr2, pt_bytes(P, pr2), done, P->st);
       lhat_sweep<T>(P->md, k, u, o3, false, ident, done, P->st);
       return;
     }
