@@ -742,8 +742,11 @@ def run_profile(args):
     torch.cuda.set_device(0)
     w = W.SCALE
     dr = W.draws(w, args.seed)
+    base = args.chosen.replace("_fft", "")
     o = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-30, maxit=args.maxit,
-                       precision=args.chosen if args.chosen in ("df32", "ozaki") else "ozaki")
+                       precision=base if base in ("df32", "ozaki") else "ozaki",
+                       covprod="fft" if args.chosen.endswith("_fft") else "dense",
+                       krylov="gmres" if args.precond == "PI" else "minres")
     G = wc4d.Problem.from_workload(w, dr, o)
     v = torch.from_numpy(W.random_vector(w.n, 3)).cuda()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]

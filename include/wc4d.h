@@ -190,6 +190,15 @@ typedef struct {
   int32_t rblock_maxsize;    /* RHAT_BLOCK: Alg. 3 maxsize in rows; 0 = no size rule        */
   int32_t rblock_numproc;    /* RHAT_BLOCK: Alg. 3 numproc; 0 = no count rule              */
   int32_t covprod;           /* WC4D_COVPROD_*: how B, Q (and Bhat^-1, Qhat^-1) are applied */
+  int32_t prec_digits;       /* OZAKI + GMRES: leading BF16 digits (1..7; 0 = 7) of each operand
+                                in the preconditioner's tensor-core products.  7 digits keep the
+                                47-bit operands (FP64-class); d < 7 digits is a reduced-precision
+                                product of about 7d - 1 bits (d = 1: BF16 inputs, d = 3: about
+                                FP32) that reads d/7 of the digit bytes and issues d(d+1)/2 of
+                                the 28 digit products, with exact FP32 accumulation.  The GMRES
+                                keeps the computed preconditioned vectors (flexible), so the
+                                rounding costs iterations, not accuracy; A v, the Arnoldi process
+                                and the true residual stay FP64-class (not in the paper).       */
 } wc4d_solve_opts;
 
 typedef struct {

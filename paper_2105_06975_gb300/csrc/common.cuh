@@ -276,6 +276,7 @@ struct GemmOpsT {
   int tc = 0;    // T = double only: wide tiles by Ozaki digit products on the tensor cores
   int* err = nullptr;  // tc: device flag set if a wait of the kernel gave up
   unsigned long long wait_ns = 0;  // tc: time limit of the pipeline waits (0: the default, 1 s)
+  int ndig = 7;                    // tc: leading digits of each operand the products use (1..7)
 };
 using GemmOp = GemmOpT<double>;
 using GemmOps = GemmOpsT<double>;
@@ -337,6 +338,7 @@ struct GemmPlan {
   double tc_bytes = 0;            // tensor-core plan: operator digit tiles and GEMV operands read once,
                                   // X digit tiles once per op, partial tiles written
   double tc_mma_flops = 0;        // tensor-core plan: BF16 flops of the issued digit products
+  double tc_digit_bytes = 0;      // the part of tc_bytes that is digit tiles (scales with the digits used)
   std::shared_ptr<void> owner;    // keeps the device arrays alive (plans are shared through a cache)
 };
 

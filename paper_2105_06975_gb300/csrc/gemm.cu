@@ -215,9 +215,9 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
   seg_start[C] = (int)segs.size();
   plan.nslots = slot;
   if (tc) {
-    double bytes = 0, mma = 0;
+    double bytes = 0, mma = 0, dbytes = 0;
     for (int o = 0; o < plan.nops; ++o)  // X digits (once per op; the row tiles re-read them from L2)
-      bytes += 2.0 * (double)oz_x_elems(shapes[o].kdim, shapes[o].ncols);
+      dbytes += 2.0 * (double)oz_x_elems(shapes[o].kdim, shapes[o].ncols);
     for (const GemmSeg& sg : segs) {
       const OpShape& sh = shapes[sg.op];
       const int cols = std::min(sg.colw, sh.ncols - sg.col0);
@@ -226,13 +226,15 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
                  "internal: tensor-core plan segment longer than its exact / GEMV limit");
       const int kbs = (sg.k1 + OZ_BK - 1) / OZ_BK - sg.k0 / OZ_BK;
       if (cols >= 2) {
-        bytes += (double)kbs * 2.0 * OZ_DIGITS * OZ_A_TILE + 8.0 * rows * cols;
+        dbytes += (double)kbs * 2.0 * OZ_DIGITS * OZ_A_TILE;
+        bytes += 8.0 * rows * cols;
         mma += (double)kbs * (OZ_DIGITS * (OZ_DIGITS + 1) / 2) * 2.0 * OZ_BM * OZ_BN * OZ_BK;
       } else {
         bytes += 8.0 * rows * (double)(sg.k1 - sg.k0) + 8.0 * (sg.k1 - sg.k0) + 8.0 * rows;
       }
     }
-    plan.tc_bytes = bytes;
+    plan.tc_bytes = bytes + dbytes;
+    plan.tc_digit_bytes = dbytes;
     plan.tc_mma_flops = mma;
   }
   // slots of a tile in k order (segments were appended in k order per CTA and
@@ -660,7 +662,11 @@ template <>
 void launch_products<double>(const GemmPlan& plan, const GemmOpsT<double>& ops, double* partial, const int* done,
                              cudaStream_t st) {
   if (ops.tc) {
-    int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, plan.tc_bytes, plan.tc_mma_flops);
+    // with nd of the 7 digits: the digit tiles' bytes and the digit products shrink
+    const int nd = ops.ndig;
+    const double bytes = plan.tc_bytes - plan.tc_digit_bytes * (1.0 - nd / (double)OZ_DIGITS);
+    const double mma = plan.tc_mma_flops * (nd * (nd + 1) / 2) / (double)(OZ_DIGITS * (OZ_DIGITS + 1) / 2);
+    int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, bytes, mma);
     launch_gemm_tc(ops, plan.d_segs, plan.d_seg_start, plan.nctas, partial, done, ran, ops.err, st);
     if (ran) prof_end(st);
     return;

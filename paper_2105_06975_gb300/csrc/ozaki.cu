@@ -386,6 +386,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   // the pipeline waits give up after lim; the drains at the end keep the full
   // OZ_WAIT_NS so that no copy or product is in flight when the CTA exits
   const unsigned long long lim = ops.wait_ns ? ops.wait_ns : OZ_WAIT_NS;
+  // the leading nd digits of each operand: the first nd tiles of every digit
+  // block are copied and the levels 0..nd-1 accumulated (nd = 7: exact to the
+  // 47-bit operands; fewer: a reduced-precision product, 7 nd - 1 bits)
+  const int nd = ops.ndig;
+  const uint32_t a_bytes = (uint32_t)nd * OZ_A_TILE * 2, x_bytes = (uint32_t)nd * OZ_X_TILE * 2;
   if (tid == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -429,15 +434,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           const uint32_t dA = sbase + s * OZ_STAGE_BYTES, dX = dA + OZ_A_BYTES;
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full_bar[s])),
-                       "r"(OZ_STAGE_BYTES)
+                       "r"(a_bytes + x_bytes)
                        : "memory");
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dA),
-              "l"(asrc + (int64_t)kb * OZ_DIGITS * OZ_A_TILE), "r"(OZ_A_BYTES), "r"(smem_u32(&full_bar[s]))
+              "l"(asrc + (int64_t)kb * OZ_DIGITS * OZ_A_TILE), "r"(a_bytes), "r"(smem_u32(&full_bar[s]))
               : "memory");
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dX),
-              "l"(xsrc + (int64_t)kb * OZ_DIGITS * OZ_X_TILE), "r"(OZ_X_BYTES), "r"(smem_u32(&full_bar[s]))
+              "l"(xsrc + (int64_t)kb * OZ_DIGITS * OZ_X_TILE), "r"(x_bytes), "r"(smem_u32(&full_bar[s]))
               : "memory");
         }
       }
@@ -481,9 +486,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           // from shared memory once or twice instead of 7-t times.
 #pragma unroll
           for (int t = 0; t < OZ_DIGITS; ++t) {
+            if (t >= nd) break;
 #pragma unroll
             for (int u0 = 0; u0 < OZ_DIGITS - t; u0 += 4) {
-              const int cnt = min(4, OZ_DIGITS - t - u0);
+              if (u0 >= nd - t) break;
+              const int cnt = min(4, nd - t - u0);
               const uint64_t da = sdesc(aA + t * (OZ_A_TILE * 2));
               const uint64_t db = sdesc(aX + u0 * (OZ_X_TILE * 2));
               const uint32_t idesc = OZ_IDESC_MK | ((uint32_t)((cnt * OZ_BN) >> 3) << 17);
@@ -534,6 +541,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         uint32_t v[OZ_DIGITS][16];
 #pragma unroll
         for (int l = 0; l < OZ_DIGITS; ++l) {
+          if (l >= nd) {  // levels the launch does not accumulate (uniform over the warp)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[l][j] = 0u;
+            continue;
+          }
           const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(l * OZ_BN + cc * 16);
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"

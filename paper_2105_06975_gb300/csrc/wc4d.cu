@@ -251,6 +251,7 @@ struct wc4d_problem {
   OpSet<float> f32;  // MIXED: FP32 copies for the inner solve
   // WC4D_COVPROD_FFT: B and Q are circulant and applied by FFT (twiddle table,
   // spectra of B, Q and of Bhat^-1, Qhat^-1 in the FFT kernel's cluster layout)
+  int pdig = 7;  // OZAKI: digits of the preconditioner's tensor-core products
   bool circ = false;
   double2* tw = nullptr;
   double *lamB = nullptr, *lamQ = nullptr, *lamBi = nullptr, *lamQi = nullptr;
@@ -503,6 +504,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
         GemmOpsT<T> ops{};
         EpisT<T> ep{};
         ops.nops = 3;
+        ops.ndig = P->pdig;
         ops.op[0] = {os.WBt, s, v1, s, s, s, 1, TRI_LOWER};
         ops.op[1] = {os.WQt, s, v1 + s, s, s, s, N, TRI_LOWER};
         ops.op[2] = {os.Q, s, y3 + s, s, s, s, N, TRI_FULL};
@@ -514,6 +516,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
         GemmOpsT<T> ops2{};
         EpisT<T> ep2{};
         ops2.nops = 3;
+        ops2.ndig = P->pdig;
         ops2.op[0] = {os.WB, s, y1, s, s, s, 1, TRI_UPPER};
         ops2.op[1] = {os.WQ, s, y1 + s, s, s, s, N, TRI_UPPER};
         ops2.op[2] = {os.B, s, y3, s, s, s, 1, TRI_FULL};
@@ -538,6 +541,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       GemmOpsT<T> ops{};
       EpisT<T> ep{};
       ops.nops = 1;
+      ops.ndig = P->pdig;
       ops.op[0] = {os.WRt, p, v2, p, p, p, N + 1, TRI_LOWER};
       ep.e[0] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
       os.attach(ops, P->st);
@@ -551,6 +555,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       GemmOpsT<T> ops2{};
       EpisT<T> ep2{};
       ops2.nops = 1;
+      ops2.ndig = P->pdig;
       ops2.op[0] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
       ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
       os.attach(ops2, P->st);
@@ -570,10 +575,12 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   ep.e[2] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
   if (exactS) {
     ops.nops = 4;
+    ops.ndig = P->pdig;
     ops.op[3] = {os.WSt, P->nS, v3, P->nS, P->nS, P->nS, 1, TRI_LOWER};
     ep.e[3] = {EPI_STORE, u3, P->nS, 0, nullptr, nullptr};
   } else {
     ops.nops = 4;
+    ops.ndig = P->pdig;
     // D y3 = [B y3_0 | Q y3_1..N]: two ops packed as one B-column op and one Q op
     // exceed GEMM_MAX_OPS together with the three factors, so B's column rides
     // in a second launch below.
@@ -592,12 +599,14 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   ep2.e[2] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
   if (exactS) {
     ops2.nops = 4;
+    ops2.ndig = P->pdig;
     ops2.op[3] = {os.WS, P->nS, u3, P->nS, P->nS, P->nS, 1, TRI_UPPER};
     ep2.e[3] = {EPI_STORE, o3, P->nS, 0, nullptr, nullptr};
     os.attach(ops2, P->st);
     gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
   } else {
     ops2.nops = 4;
+    ops2.ndig = P->pdig;
     ops2.op[3] = {os.B, s, y3, s, s, s, 1, TRI_FULL};
     ep2.e[3] = {EPI_STORE, u3, s, 0, nullptr, nullptr};
     os.attach(ops2, P->st);
@@ -642,6 +651,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
         GemmOpsT<T> ops{};
         EpisT<T> ep{};
         ops.nops = 2;
+        ops.ndig = P->pdig;
         ops.op[0] = {os.B, s, o1, s, s, s, 1, TRI_FULL};
         ops.op[1] = {os.Q, s, o1 + s, s, s, s, N, TRI_FULL};
         ep.e[0] = {EPI_SUB_FROM, u, s, 0, nullptr, v1};
@@ -663,6 +673,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       GemmOpsT<T> ops{};
       EpisT<T> ep{};
       ops.nops = 1;
+      ops.ndig = P->pdig;
       ops.op[0] = {os.WRt, p, v2, p, p, p, N + 1, TRI_LOWER};
       ep.e[0] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
       os.attach(ops, P->st);
@@ -675,6 +686,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       GemmOpsT<T> ops2{};
       EpisT<T> ep2{};
       ops2.nops = 1;
+      ops2.ndig = P->pdig;
       ops2.op[0] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
       ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
       os.attach(ops2, P->st);
@@ -686,6 +698,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   GemmOpsT<T> ops{};
   EpisT<T> ep{};
   ops.nops = 3;
+  ops.ndig = P->pdig;
   ops.op[0] = {os.WRt, p, v2, p, p, p, N + 1, TRI_LOWER};
   ops.op[1] = {os.B, s, o1, s, s, s, 1, TRI_FULL};
   ops.op[2] = {os.Q, s, o1 + s, s, s, s, N, TRI_FULL};
@@ -697,6 +710,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   GemmOpsT<T> ops2{};
   EpisT<T> ep2{};
   ops2.nops = 1;
+  ops2.ndig = P->pdig;
   ops2.op[0] = {os.WR, p, y2, p, p, p, N + 1, TRI_UPPER};
   ep2.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
   os.attach(ops2, P->st);
@@ -1021,6 +1035,11 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(o->precision != WC4D_PREC_MIXED || (o->inner_iters >= 1 && o->inner_iters <= 200), WC4D_ERR_ARG,
              "inner_iters must lie in [1, 200]");
   WC4D_CHECK(o->covprod == WC4D_COVPROD_DENSE || o->covprod == WC4D_COVPROD_FFT, WC4D_ERR_ARG, "bad covprod");
+  WC4D_CHECK(o->prec_digits >= 0 && o->prec_digits <= 7, WC4D_ERR_ARG, "prec_digits must lie in [0, 7]");
+  WC4D_CHECK(o->prec_digits == 0 || o->prec_digits == 7 ||
+                 (o->precision == WC4D_PREC_OZAKI && o->krylov == WC4D_KRYLOV_GMRES),
+             WC4D_ERR_ARG,
+             "reduced-digit preconditioner products need precision OZAKI and the flexible (DF32-basis) GMRES");
   if (o->covprod == WC4D_COVPROD_FFT) {
     WC4D_CHECK(circ_size_ok(d->s), WC4D_ERR_ARG, "covprod FFT needs s a power of two in [64, 8192]");
     WC4D_CHECK(o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_DF32 ||
@@ -1045,6 +1064,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->N = N;
   P->p = p;
   P->pertime = (d->p_t != nullptr);
+  P->pdig = (o->precision == WC4D_PREC_OZAKI && o->prec_digits >= 1 && o->prec_digits <= 7) ? o->prec_digits : 7;
   P->ns = (int64_t)(N + 1) * s;
   P->np = P->pertime ? (int64_t)p : (int64_t)(N + 1) * p;  // per-time: p = sum of p_t
   P->n = 2 * P->ns + P->np;

@@ -215,3 +215,51 @@ def test_bounded_wait_gives_up_with_timeout_then_recovers():
     r = rhs - prob.A_apply(x.cpu().numpy())
     assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-8
     G.close()
+
+
+@pytest.mark.parametrize("rhat,kappa", [("rr", 100.0), ("me", 1e4)])
+def test_reduced_digit_preconditioner_products(rhat, kappa):
+    """prec_digits = d < 7 (not in the paper): the preconditioner's tensor-core
+    products keep the leading d BF16 digits of each operand (about 7d - 1 bits,
+    d = 1 being BF16 inputs, d = 3 about FP32) with exact FP32 accumulation.
+    P_I^{-1} v then differs from the oracle by about kappa(Rhat) 2^(2 - 7d)
+    (Rhat reconditioned to kappa_max by Alg. 1 / 2, Sec. 5.2), and the error
+    falls by about 2^7 per digit.  The flexible GMRES (preconditioned vectors
+    kept) still reaches the FP64 true residual of 1e-10 with the oracle's
+    operator, in at most twice the iterations of the 7-digit products."""
+    w, dr = case(256, 12, 128, seed=8)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    P = sd.Preconditioner(prob, sd.PrecondOptions(kind="PI", k=3, rhat=rhat, kappa_max=kappa))
+    v = W.random_vector(prob.n, 10)
+    ref = P.apply(v)
+    errs = {}
+    for d in (2, 3, 4, 7):
+        G = L.Problem.from_workload(w, dr, L.make_opts(precond="PI", k=3, rhat=rhat, kappa_max=kappa,
+                                                       precision="ozaki", prec_digits=d))
+        errs[d] = rel(G.apply_precond("PI", to_dev(v)).cpu().numpy(), ref)
+        # A v keeps all 7 digits whatever the preconditioner uses
+        assert rel(G.apply_saddle(to_dev(v)).cpu().numpy(), prob.A_apply(v)) < 1e-11
+        G.close()
+    assert errs[7] < 1e-9
+    for d in (2, 3, 4):
+        assert errs[d] < 4.0 * kappa * 2.0 ** (2 - 7 * d), errs
+    assert errs[2] > errs[3] > errs[4] > errs[7], errs
+    its = {}
+    for d in (3, 7):
+        G = L.Problem.from_workload(w, dr, L.make_opts(precond="PI", k=3, rhat=rhat, kappa_max=kappa,
+                                                       precision="ozaki", prec_digits=d, tol=1e-10, maxit=1500))
+        x, info = G.solve(to_dev(rhs))
+        assert info.status == 0, (d, L.wc4d_last_error())
+        r = rhs - prob.A_apply(x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-10
+        its[d] = info.iters
+        G.close()
+    assert its[3] <= 2 * its[7] + 5, its
+
+
+def test_reduced_digits_need_ozaki_gmres():
+    w, dr = case(64, 3, 32, seed=1)
+    for kw in ({"precision": "df32"}, {"precision": "ozaki", "precond": "PD", "krylov": "minres"}):
+        with pytest.raises(L.WC4DError) as e:
+            L.Problem.from_workload(w, dr, L.make_opts(**{"precond": "PI", "k": 2, "prec_digits": 3, **kw}))
+        assert e.value.code == L.WC4D_ERR_ARG and "reduced-digit" in str(e.value)
