@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--ref-budget-s", type=float, default=240.0,
                     help="reference arm: time budget for its timed full oracle solves (stops early)")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "batch", "learned", "profile"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "batch", "learned", "profile", "heat"],
                     help="scale: one s=2048 N=64 window (default line); batch: independent uneven windows; "
-                         "learned: learned Schur block vs the plain P_D (s=1024 N=32); profile: a small fixed "
+                         "learned: learned Schur block vs the plain P_D (s=1024 N=32); heat: the heat equation at "
+                         "s=50,000 N=5 p=12,500 with banded B, Q; profile: a small fixed "
                          "run of the hot kernels at the scale sizes for ncu captures (products, then one "
                          "solve of --maxit GMRES steps)")
     ap.add_argument("--pairs", type=int, default=50000, help="training pairs of the learned workload")
@@ -328,7 +329,8 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                              "peak_source": "derived: 152 SM x 256 FP32 flop/clk x 2.07 GHz"}
     if st.circ_launches:
         a = st.circ_flops / (st.circ_ms * 1e-3) / 1e12
-        rows["circ_fft"] = {"kernel": "circ_kernel (circulant B, Q and their inverses by FP64 FFT, 8-CTA clusters)",
+        rows["circ_fft"] = {"kernel": "circ_kernel / band_kernel (circulant B, Q: FP64 FFT in 8-CTA clusters, "
+                                      "or the banded taps)",
                             "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": a / FP64_PEAK_TFLOPS, "launches": st.circ_launches,
                             "ms_per_launch": st.circ_ms / st.circ_launches,
@@ -337,7 +339,7 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                             "hbm_gbs": st.circ_bytes / (st.circ_ms * 1e-3) / 1e9,
                             "share_of_step": st.circ_ms / step_ms,
                             "peak_source": "derived: 152 SM x 4 FP64 flop/clk x 2.07 GHz; flops counted as "
-                                           "5 s log2 s per complex transform"}
+                                           "5 s log2 s per complex transform, 2 per band tap"}
     if st.pt_launches:
         a = st.pt_bytes / (st.pt_ms * 1e-3) / 1e9
         rows["pertime"] = {"kernel": "pertime_kernel (per-time R_i family products)", "bound": "hbm",
@@ -730,6 +732,81 @@ def run_learned(args):
         G.close()
 
 
+def run_heat(args):
+    """The heat-equation window of Sec. 7.2 at its largest size: s = 50,000,
+    N = 5, p = 12,500 random observed points, B and Q the banded circulant
+    modified SOAR of Sec. 6.1 (applied through their taps), R the chordal SOAR
+    over the observed points, P_I + GMRES with L_M(k), right-hand side
+    (0, z_r, 0).  A step is the device problem build (Rhat = R factor and
+    inverse, p = 12,500) and the solve to true relres 1e-6."""
+    import torch
+
+    from paper_2105_06975_gb300 import wc4d, workload as W
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    w = W.HEAT_SOAR_R
+    dr = W.draws(w, args.seed * 1000 + rank)
+    bands = w.heat_bands()
+    rhs = torch.zeros(w.n, dtype=torch.float64, device="cuda")
+    rhs[w.s * (w.N + 1):w.s * (w.N + 1) + w.p * (w.N + 1)] = torch.from_numpy(dr.z_r.ravel())
+    x = torch.zeros_like(rhs)
+    precision = args.precision
+    opts = wc4d.make_opts(precond="PI", k=args.k, tol=1e-6, maxit=args.maxit, precision=precision,
+                          check_every=args.check_every)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        G = wc4d.Problem(w.s, w.N, w.p, dr.obs_idx, opts, bands=bands, band_lo=1, band_hi=1,
+                         msoar=(w.msoar_b, w.msoar_q, dr.extra["psi"]), soar_r=w.soar_r,
+                         stream=stream.cuda_stream)
+        _, info = G.solve(rhs, x)
+        G.close()
+        return info
+    for _ in range(args.warmup):
+        step()
+    clk = ClockSampler(local)
+    if not args.no_clocks:
+        clk.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clk.stop()
+    wc4d.wc4d_reset_stats()
+    wc4d.wc4d_set_profiling(True)
+    torch.cuda.synchronize()
+    p0 = time.perf_counter()
+    step()
+    torch.cuda.synchronize()
+    prof_ms = (time.perf_counter() - p0) * 1e3
+    wc4d.wc4d_set_profiling(False)
+    st = wc4d.wc4d_get_stats()
+    hbm = peaks().get("hbm_gbs")
+    ks = kernel_rows(st, prof_ms, hbm, dcgs=precision in ("df32", "ozaki"))
+    dom = max(ks.values(), key=lambda r: r["share_of_step"]) if ks else None
+    roof = ({k: dom[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "peak_source",
+                                 "share_of_step")} if dom else None)
+    if roof:
+        roof["traffic"] = None
+    assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
+    line = {"metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": MODE_DTYPE.get(precision, precision), "data": "synthetic", "impl": "gpu",
+            "config": {"workload": f"heat equation (Sec. 7.2) s={w.s} N={w.N} p={w.p} (n={w.n}); banded "
+                                   "circulant modified SOAR B, Q; SOAR R over the observed points",
+                       "precond": "PI", "lhat": f"L_M({args.k})", "rhat": "exact", "krylov": "GMRES (no restart)",
+                       "tol": 1e-6, "step": "device problem build (Rhat factor and inverse, p = 12,500) + solve",
+                       "l2": "inputs larger than L2 (each R-family operator 1.25 GB)"},
+            "iterations": statistics.mean(i.iters for i in infos),
+            "relres_true_max": max(i.relres_true for i in infos),
+            "solve_ms_mean": statistics.mean(i.ms for i in infos),
+            "roofline": roof, "kernels": ks, "gpu_launches": int(st.launches), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile(args):
     """The hot kernels at the scale workload's sizes, for ncu captures: 4 x
     (A v, P_I^-1 v) through the C ABI, then one GMRES solve capped at --maxit
@@ -794,6 +871,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "heat":
+        run_heat(args)
     else:
         run_gpu(args)
 

@@ -68,10 +68,20 @@ enum {
 /* covariance source */
 enum {
   WC4D_COV_DENSE = 0,      /* caller passes dense B (s x s), Q (s x s), R (p x p)                   */
-  WC4D_COV_SOAR = 1        /* library builds SOAR matrices on the device (Sec. 6.1, Eq. SOAR):
+  WC4D_COV_SOAR = 1,       /* library builds SOAR matrices on the device (Sec. 6.1, Eq. SOAR):
                               c(r) = sigma2 (1 + r/ell) exp(-r/ell), r = chordal distance between
                               points x_j = j/s of the periodic unit domain, r = sin(pi |dx|)/pi;
                               R uses the observed points x = obs_idx/s                              */
+  WC4D_COV_MSOAR = 2       /* B and Q are the banded circulant "modified SOAR" of the heat-equation
+                              experiments (Sec. 6.1): first row c_i = amp (1 + d_i/L) exp(-d_i/L),
+                              d_i = 2 |sin(i theta / 2)|, theta = pi / maxval, for |i| <= maxval and
+                              zero beyond, plus delta I with delta = |lambda_min| + psi when the
+                              circulant has a negative eigenvalue (lambda from the DFT of the row);
+                              (amp, L, maxval) in msoar_b / msoar_q, psi in msoar_psi.  B and Q are
+                              never formed: their products run through the band (2 maxval + 1 taps
+                              per output).  R is the caller's dense R when R != NULL, else the SOAR
+                              over the observed points (soar_r).  Needs precond PI (no Dhat^-1 of
+                              a band), shat PAPER, covprod DENSE, one observation set             */
 };
 enum { WC4D_MEM_HOST = 0, WC4D_MEM_DEVICE = 1 };
 
@@ -154,6 +164,9 @@ typedef struct {
   double soar_q[2];          /* SOAR: (sigma2, ell) of Q                                */
   double soar_r[2];          /* SOAR: (sigma2, ell) of R                                */
   int32_t mem_kind;          /* where bands/obs_idx/B/Q/R live: WC4D_MEM_HOST|DEVICE    */
+  double msoar_b[3];         /* MSOAR: (amp, L, maxval) of B, maxval integral, 2 maxval + 1 <= s */
+  double msoar_q[3];         /* MSOAR: (amp, L, maxval) of Q                                */
+  double msoar_psi[2];       /* MSOAR: the shifts' draws psi of B and Q (>= 0)              */
   const int32_t* p_t;        /* NULL: one set obs_idx[p] and one R (p x p) for every time
                                 level (Sec. 6.1).  Else per-time observation sets (Sec. 2.1:
                                 H = blkdiag(H_i), R = blkdiag(R_i)): host array of the N+1

@@ -25,7 +25,7 @@ import scipy.linalg as sla
 
 from . import covariance as cov
 from . import model as mdl
-from .saddle import PerTimeProblem, Problem, Preconditioner, PrecondOptions
+from .saddle import BandCovProblem, PerTimeProblem, Problem, Preconditioner, PrecondOptions
 from . import krylov
 from paper_2105_06975_gb300 import workload
 
@@ -40,13 +40,17 @@ def covariances(w, obs_idx, extra=None):
     else:
         B = cov.soar_state(w.s, *w.soar_b)
         Q = cov.soar_state(w.s, *w.soar_q)
+    return B, Q, observation_covariance(w, obs_idx, extra)
+
+
+def observation_covariance(w, obs_idx, extra=None):
+    """R_i of a workload: the channel-block R of Sec. 6.1 or the chordal SOAR
+    over the observed points."""
     if w.r_kind == "block":
         pvec = workload.block_sizes(w.p, w.r_blocks)
         pcorr = cov.pcorr_factors(extra["pcorr_on"], extra["pcorr_u"], w.r_pcorr_max, w.r_uncorrelated)
-        R = cov.block_r_matrix(pvec, w.r_density, pcorr, extra["r_u"], w.r_msoar, w.r_lmin)
-    else:
-        R = cov.soar_obs(w.s, obs_idx, *w.soar_r)
-    return B, Q, R
+        return cov.block_r_matrix(pvec, w.r_density, pcorr, extra["r_u"], w.r_msoar, w.r_lmin)
+    return cov.soar_obs(w.s, obs_idx, *w.soar_r)
 
 
 def linear_model(w):
@@ -58,6 +62,19 @@ def linear_model(w):
 def linear_problem(w, dr) -> Problem:
     B, Q, R = covariances(w, dr.obs_idx, dr.extra)
     return Problem(w.s, w.N, w.p, linear_model(w), np.asarray(dr.obs_idx), B, Q, R)
+
+
+def heat_band_problem(w, dr, R=None) -> BandCovProblem:
+    """The heat workload with B and Q kept as their modified SOAR rows and
+    shifts (Sec. 6.1, 7.2); R is the workload's R (channel-block or SOAR over
+    the observed points) unless given."""
+    rowB = cov.modified_soar_row(w.s, *w.msoar_b)
+    rowQ = cov.modified_soar_row(w.s, *w.msoar_q)
+    dB = cov.modified_soar_shift(rowB, dr.extra["psi"][0])
+    dQ = cov.modified_soar_shift(rowQ, dr.extra["psi"][1])
+    if R is None:
+        R = observation_covariance(w, dr.obs_idx, dr.extra)
+    return BandCovProblem(w.s, w.N, w.p, linear_model(w), np.asarray(dr.obs_idx), rowB, dB, rowQ, dQ, R)
 
 
 def per_time_problem(w, dr) -> PerTimeProblem:

@@ -299,6 +299,26 @@ class PerTimeProblem(Problem):
         return sla.block_diag(*self.R_list)
 
 
+class BandCovProblem(Problem):
+    """The heat-equation window at sizes where dense B and Q do not fit
+    (Sec. 7.2: s up to 50,000): B and Q are the banded circulant modified SOAR
+    of Sec. 6.1, stored as their first rows plus the diagonal shifts, and
+    applied through the band (cov.modified_soar_apply, pinned against the dense
+    circulant product).  Everything else is the shared-set Problem; the dense
+    assemblies that need B or Q are not available."""
+
+    def __init__(self, s, N, p, model, obs_idx, rowB, deltaB, rowQ, deltaQ, R):
+        super().__init__(s, N, p, model, obs_idx, None, None, R)
+        self.rowB, self.deltaB, self.rowQ, self.deltaQ = rowB, deltaB, rowQ, deltaQ
+
+    def D_apply(self, v1: np.ndarray) -> np.ndarray:
+        out = np.empty_like(v1)
+        out[0] = cov.modified_soar_apply(self.rowB, self.deltaB, v1[0])
+        if self.N > 0:
+            out[1:] = cov.modified_soar_apply(self.rowQ, self.deltaQ, v1[1:].T).T
+        return out
+
+
 class PerTimePreconditioner(Preconditioner):
     """P_D / P_I (Eq. prec) with R-hat_i built from each R_i (Sec. 5 applied
     blockwise, as the paper's Remark in Sec. 5 states)."""

@@ -273,6 +273,93 @@ __global__ void circ_spectrum_kernel(const double* __restrict__ col, int s, cons
   }
 }
 
+// Banded circulant product: one CTA per (job, column, tile of BAND_TILE
+// outputs); the tile's inputs with a halo of mv on each side (periodic wrap)
+// and the taps are staged in shared memory, so each input is read from HBM
+// once per tile; each thread forms 4 outputs from the symmetric taps.
+__global__ void __launch_bounds__(256) band_kernel(BandJobs jobs, int s, ModelDev md, const int* __restrict__ done,
+                                                   int* ran) {
+  pdl_wait();
+  pdl_trigger();
+  if (done != nullptr && *(volatile const int*)done) return;
+  if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
+  extern __shared__ double band_smem[];
+  const int tiles = (s + BAND_TILE - 1) / BAND_TILE;
+  int b = blockIdx.x, q = 0;
+  while (q + 1 < jobs.n && b >= jobs.j[q].ncols * tiles) {
+    b -= jobs.j[q].ncols * tiles;
+    ++q;
+  }
+  const BandJob& J = jobs.j[q];
+  const int c = b / tiles, j0 = (b % tiles) * BAND_TILE;
+  const int mv = J.mv, w = BAND_TILE + 2 * mv;
+  double* xs = band_smem;       // x[j0 - mv .. j0 + BAND_TILE + mv)
+  double* taps = band_smem + w;  // row[0 .. mv]: the symmetric half
+  const double* x = J.X + (int64_t)c * J.ldx;
+  for (int i = threadIdx.x; i < w; i += blockDim.x) {
+    int g = j0 - mv + i;
+    g %= s;
+    g += (g < 0) ? s : 0;
+    xs[i] = x[g];
+  }
+  for (int i = threadIdx.x; i <= mv; i += blockDim.x) taps[i] = J.row[mv + i];
+  __syncthreads();
+  for (int o = threadIdx.x; o < BAND_TILE; o += blockDim.x) {
+    const int j = j0 + o;
+    if (j >= s) break;
+    const double* xc = xs + mv + o;
+    double acc = (taps[0] + J.delta) * xc[0];
+    for (int i = 1; i <= mv; ++i) acc = fma(taps[i], xc[i] + xc[-i], acc);
+    double val;
+    switch (J.mode) {
+      case EPI_SADDLE_C1: {
+        const int t = c + J.t0;
+        double pre = J.v3[(int64_t)t * s + j];
+        if (t >= 1) pre -= model_apply<double>(md, t, J.v3 + (int64_t)(t - 1) * s, j);
+        val = acc + pre;
+        break;
+      }
+      case EPI_SUB_FROM:
+        val = J.Y[j + (int64_t)c * J.ldc] - acc;
+        break;
+      default:
+        val = acc;
+    }
+    J.C[j + (int64_t)c * J.ldc] = val;
+    if (J.Ch != nullptr) {
+      const float h = (float)val;
+      J.Ch[j + (int64_t)c * J.ldc] = h;
+      J.Cl[j + (int64_t)c * J.ldc] = (float)(val - (double)h);
+    }
+  }
+}
+
+__device__ __forceinline__ void atomic_min_double(double* addr, double v) {
+  // order-preserving for finite doubles: compare as the double values
+  unsigned long long* a = reinterpret_cast<unsigned long long*>(addr);
+  unsigned long long old = *a, assumed;
+  do {
+    assumed = old;
+    if (__longlong_as_double((long long)assumed) <= v) return;
+    old = atomicCAS(a, assumed, (unsigned long long)__double_as_longlong(v));
+  } while (old != assumed);
+}
+
+__global__ void band_lambda_kernel(const double* __restrict__ row, int mv, int s, double* out) {
+  double mn = INFINITY;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s; k += gridDim.x * blockDim.x) {
+    double lam = row[mv];
+    for (int i = 1; i <= mv; ++i) {
+      // cos(2 pi i k / s) with the angle reduced exactly: (i k) mod s
+      const int m = (int)(((int64_t)i * k) % s);
+      lam = fma(2.0 * row[mv + i], cospi(2.0 * (double)m / (double)s), lam);
+    }
+    mn = fmin(mn, lam);
+  }
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) atomic_min_double(out, mn);
+}
+
 // flag = 1 where |A[i + j s] - A[(i - j) mod s]| > tol A[0] (A SPD: its
 // diagonal bounds every entry)
 __global__ void circ_check_kernel(const double* __restrict__ A, int s, double tol, int* flag) {
@@ -293,6 +380,34 @@ void launch_circ_check(const double* A, int s, double tol, int* flag, cudaStream
   const int64_t total = (int64_t)s * s;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
   circ_check_kernel<<<blocks, 256, 0, st>>>(A, s, tol, flag);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_band(const BandJobs& jobs, int s, const ModelDev& md, const int* done, cudaStream_t st) {
+  if (jobs.n == 0) return;
+  const int tiles = (s + BAND_TILE - 1) / BAND_TILE;
+  int ctas = 0, mvmax = 0;
+  double flops = 0.0, bytes = 0.0;
+  for (int q = 0; q < jobs.n; ++q) {
+    ctas += jobs.j[q].ncols * tiles;
+    mvmax = std::max(mvmax, jobs.j[q].mv);
+    flops += 2.0 * (2 * jobs.j[q].mv + 1) * (double)s * jobs.j[q].ncols;
+    const int ep = (jobs.j[q].mode == EPI_SADDLE_C1 || jobs.j[q].mode == EPI_SUB_FROM) ? 1 : 0;
+    bytes += 8.0 * s * jobs.j[q].ncols * (2 + ep);
+  }
+  if (ctas == 0) return;
+  const size_t smem = sizeof(double) * (BAND_TILE + 2 * mvmax + mvmax + 1);
+  WC4D_CHECK(smem <= 48 * 1024, WC4D_ERR_ARG, "internal: band too wide for the product kernel");
+  int* ran = prof_enabled() ? prof_begin(PROF_CIRC, flops, st, bytes) : nullptr;
+  WC4D_CUDA(launch_pdl(band_kernel, dim3(ctas), dim3(256), smem, st, jobs, s, md, done, ran));
+  WC4D_LAUNCH_CHECK();
+  if (ran) prof_end(st);
+}
+
+void launch_band_lambda_min(const double* row, int mv, int s, double* out, cudaStream_t st) {
+  launch_fill_d(out, INFINITY, 1, st);
+  const int blocks = std::min((s + 255) / 256, 152 * 4);
+  band_lambda_kernel<<<blocks, 256, 0, st>>>(row, mv, s, out);
   WC4D_LAUNCH_CHECK();
 }
 

@@ -62,4 +62,35 @@ inline void circ_add(CircJobs& jobs, const CircJob& jb) {
   ++jobs.n;
 }
 
+// Banded circulant products (the modified SOAR B and Q of the heat-equation
+// experiments, Sec. 6.1): y_j = delta x_j + sum_{|i| <= mv} row[i + mv]
+// x_{(j + i) mod s}, 2 mv + 1 taps, symmetric (row[mv + i] = row[mv - i]).
+// The epilogues of the circulant jobs apply (mode, C, ldc, t0, v3, Y, Ch, Cl).
+struct BandJob {
+  const double* X;
+  int64_t ldx;
+  int ncols;
+  const double* row;  // device, 2 mv + 1 taps
+  int mv;
+  double delta;
+  int mode;
+  double* C;
+  int64_t ldc;
+  int t0;
+  const double* v3;
+  const double* Y;
+  float* Ch = nullptr;
+  float* Cl = nullptr;
+};
+struct BandJobs {
+  BandJob j[CIRC_MAX_JOBS];
+  int n = 0;
+};
+constexpr int BAND_TILE = 1024;  // outputs per CTA
+void launch_band(const BandJobs& jobs, int s, const ModelDev& md, const int* done, cudaStream_t st);
+// lambda_min of the symmetric banded circulant with taps row (setup): written
+// to *out (device double) as the minimum over k of
+// row[mv] + 2 sum_{i >= 1} row[mv + i] cos(2 pi i k / s)
+void launch_band_lambda_min(const double* row, int mv, int s, double* out, cudaStream_t st);
+
 }  // namespace wc4d

@@ -252,6 +252,11 @@ struct wc4d_problem {
   // WC4D_COVPROD_FFT: B and Q are circulant and applied by FFT (twiddle table,
   // spectra of B, Q and of Bhat^-1, Qhat^-1 in the FFT kernel's cluster layout)
   int pdig = 7;  // OZAKI: digits of the preconditioner's tensor-core products
+  // WC4D_COV_MSOAR: banded circulant B and Q, applied through their taps
+  bool band = false;
+  double *bandB = nullptr, *bandQ = nullptr;  // device, 2 mv + 1 taps each
+  int mvB = 0, mvQ = 0;
+  double deltaB = 0.0, deltaQ = 0.0;
   bool circ = false;
   double2* tw = nullptr;
   double *lamB = nullptr, *lamQ = nullptr, *lamBi = nullptr, *lamQi = nullptr;
@@ -345,6 +350,30 @@ static double pt_bytes(const wc4d_problem* P, const PtProd& pr) {
   return 8.0 * (a + (double)P->np * (pr.mode == EPI_SADDLE_C2 ? 3 : 2));
 }
 
+// D x (B on column 0, Q on columns 1..N) off the product path, for circulant
+// (FFT) or banded circulant (taps) B and Q, with the product epilogue: mode
+// EPI_SADDLE_C1 (C_t = (D x)_t + (L v3)_t) or EPI_SUB_FROM (C = Y - D x)
+static void d_offpath(wc4d_problem* P, const double* x, int mode, double* C, const double* v3, const double* Y,
+                      float* Ch, float* Cl, const int* done) {
+  const int s = P->s, N = P->N;
+  const double* Y1 = Y ? Y + s : nullptr;
+  if (P->circ) {
+    CircJobs cj{};
+    circ_add(cj, CircJob{x, s, 1, P->lamB, mode, C, s, 0, v3, Y, Ch, Cl});
+    if (N > 0)
+      circ_add(cj, CircJob{x + s, s, N, P->lamQ, mode, C + s, s, 1, v3, Y1, Ch ? Ch + s : nullptr,
+                           Cl ? Cl + s : nullptr});
+    launch_circ(cj, s, P->tw, P->md, done, P->st);
+    return;
+  }
+  BandJobs bj{};
+  bj.j[bj.n++] = BandJob{x, s, 1, P->bandB, P->mvB, P->deltaB, mode, C, s, 0, v3, Y, Ch, Cl};
+  if (N > 0)
+    bj.j[bj.n++] = BandJob{x + s, s, N, P->bandQ, P->mvQ, P->deltaQ, mode, C + s, s, 1, v3, Y1,
+                           Ch ? Ch + s : nullptr, Cl ? Cl + s : nullptr};
+  launch_band(bj, s, P->md, done, P->st);
+}
+
 // ------------------------------------------------------------ A v (Sec. 6.2)
 // wh / wl (T = double, optional): also write the double-float split of out
 template <typename T>
@@ -363,14 +392,8 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
       // c3 with each time's own set; D v1 + L v3 as usual; c2_t = R_t v2_t + H_t v3_t
       saddle_c3_pertime(P->md, v1, v2, P->d_inv, P->ptl.nuoff, c3, split ? wh + P->ns + P->np : nullptr,
                         split ? wl + P->ns + P->np : nullptr, done, P->st);
-      if (P->circ) {
-        CircJobs cj{};
-        circ_add(cj, CircJob{v1, s, 1, P->lamB, EPI_SADDLE_C1, c1, s, 0, v3, nullptr, split ? wh : nullptr,
-                             split ? wl : nullptr});
-        if (N > 0)
-          circ_add(cj, CircJob{v1 + s, s, N, P->lamQ, EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr,
-                               split ? wh + s : nullptr, split ? wl + s : nullptr});
-        launch_circ(cj, s, P->tw, P->md, done, P->st);
+      if (P->circ || P->band) {
+        d_offpath(P, v1, EPI_SADDLE_C1, c1, v3, nullptr, split ? wh : nullptr, split ? wl : nullptr, done);
       } else {
         GemmOpsT<T> ops{};
         EpisT<T> ep{};
@@ -408,15 +431,9 @@ static void apply_A(wc4d_problem* P, OpSet<T>& os, const GemmPlan& plan, const T
     saddle_c3<T>(P->md, v1, v2, P->d_inv, p, c3, done, P->st);
   }
   if constexpr (sizeof(T) == 8) {
-    if (P->circ) {
-      // D v1 + L v3 by FFT (circulant B, Q), R v2 + H v3 on the product path
-      CircJobs cj{};
-      circ_add(cj, CircJob{v1, s, 1, P->lamB, EPI_SADDLE_C1, c1, s, 0, v3, nullptr, split ? wh : nullptr,
-                           split ? wl : nullptr});
-      if (N > 0)
-        circ_add(cj, CircJob{v1 + s, s, N, P->lamQ, EPI_SADDLE_C1, c1 + s, s, 1, v3, nullptr,
-                             split ? wh + s : nullptr, split ? wl + s : nullptr});
-      launch_circ(cj, s, P->tw, P->md, done, P->st);
+    if (P->circ || P->band) {
+      // D v1 + L v3 by FFT or through the band, R v2 + H v3 on the product path
+      d_offpath(P, v1, EPI_SADDLE_C1, c1, v3, nullptr, split ? wh : nullptr, split ? wl : nullptr, done);
       GemmOpsT<T> ops{};
       EpisT<T> ep{};
       ops.nops = 1;
@@ -642,11 +659,8 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       pr.mode = EPI_STORE;
       pr.C = y2;
       launch_pertime(P->ptl, pr, pt_bytes(P, pr), done, P->st);
-      if (P->circ) {
-        CircJobs cj{};
-        circ_add(cj, CircJob{o1, s, 1, P->lamB, EPI_SUB_FROM, u, s, 0, nullptr, v1});
-        if (N > 0) circ_add(cj, CircJob{o1 + s, s, N, P->lamQ, EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s});
-        launch_circ(cj, s, P->tw, P->md, done, P->st);
+      if (P->circ || P->band) {
+        d_offpath(P, o1, EPI_SUB_FROM, u, nullptr, v1, nullptr, nullptr, done);
       } else {
         GemmOpsT<T> ops{};
         EpisT<T> ep{};
@@ -669,7 +683,7 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       lhat_sweep<T>(P->md, k, u, o3, false, ident, done, P->st);
       return;
     }
-    if (P->circ) {
+    if (P->circ || P->band) {
       GemmOpsT<T> ops{};
       EpisT<T> ep{};
       ops.nops = 1;
@@ -678,11 +692,8 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       ep.e[0] = {EPI_STORE, y2, p, 0, nullptr, nullptr};
       os.attach(ops, P->st);
       gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
-      // u = v1 - D c1 by FFT
-      CircJobs cj{};
-      circ_add(cj, CircJob{o1, s, 1, P->lamB, EPI_SUB_FROM, u, s, 0, nullptr, v1});
-      if (N > 0) circ_add(cj, CircJob{o1 + s, s, N, P->lamQ, EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s});
-      launch_circ(cj, s, P->tw, P->md, done, P->st);
+      // u = v1 - D c1 by FFT or through the band
+      d_offpath(P, o1, EPI_SUB_FROM, u, nullptr, v1, nullptr, nullptr, done);
       GemmOpsT<T> ops2{};
       EpisT<T> ep2{};
       ops2.nops = 1;
@@ -984,13 +995,31 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
     WC4D_CHECK(d->band_lo >= 0 && d->band_hi >= 0 && d->band_lo + d->band_hi + 1 <= d->s, WC4D_ERR_ARG,
                "band offsets must satisfy lo, hi >= 0 and lo + hi + 1 <= s");
   }
-  WC4D_CHECK(d->cov_kind == WC4D_COV_DENSE || d->cov_kind == WC4D_COV_SOAR, WC4D_ERR_ARG, "bad cov_kind");
-  if (d->cov_kind == WC4D_COV_DENSE)
+  WC4D_CHECK(d->cov_kind == WC4D_COV_DENSE || d->cov_kind == WC4D_COV_SOAR || d->cov_kind == WC4D_COV_MSOAR,
+             WC4D_ERR_ARG, "bad cov_kind");
+  if (d->cov_kind == WC4D_COV_DENSE) {
     WC4D_CHECK(d->B && d->Q && d->R, WC4D_ERR_ARG, "dense covariances missing");
-  else
+  } else if (d->cov_kind == WC4D_COV_MSOAR) {
+    for (const double* m : {d->msoar_b, d->msoar_q})
+      WC4D_CHECK(m[0] > 0 && m[1] > 0 && m[2] >= 1 && m[2] == std::floor(m[2]) && 2 * m[2] + 1 <= d->s &&
+                     m[2] <= 2048,
+                 WC4D_ERR_ARG, "modified SOAR needs amp, L > 0 and an integral maxval, 1 <= maxval <= 2048, "
+                               "2 maxval + 1 <= s");
+    WC4D_CHECK(d->msoar_psi[0] >= 0 && d->msoar_psi[1] >= 0, WC4D_ERR_ARG, "modified SOAR shifts psi must be >= 0");
+    WC4D_CHECK(d->R != nullptr || (d->soar_r[0] > 0 && d->soar_r[1] > 0), WC4D_ERR_ARG,
+               "modified SOAR B, Q need a dense R or positive SOAR parameters of R");
+    WC4D_CHECK(o->precond == WC4D_PRECOND_PI && o->shat == WC4D_SHAT_PAPER && o->covprod == WC4D_COVPROD_DENSE &&
+                   d->p_t == nullptr &&
+                   (o->precision == WC4D_PREC_FP64 || o->precision == WC4D_PREC_DF32 ||
+                    o->precision == WC4D_PREC_OZAKI),
+               WC4D_ERR_ARG,
+               "modified SOAR (banded) B, Q run with precond PI, shat PAPER, covprod DENSE, one observation set "
+               "and precision FP64, DF32 or OZAKI");
+  } else {
     WC4D_CHECK(d->soar_b[1] > 0 && d->soar_q[1] > 0 && d->soar_r[1] > 0 && d->soar_b[0] > 0 && d->soar_q[0] > 0 &&
                    d->soar_r[0] > 0,
                WC4D_ERR_ARG, "SOAR variances and lengths must be positive");
+  }
   WC4D_CHECK(o->precond == WC4D_PRECOND_PD || o->precond == WC4D_PRECOND_PI, WC4D_ERR_ARG, "bad precond");
   WC4D_CHECK(o->k >= 1 && o->k <= d->N + 1, WC4D_ERR_ARG, "k must lie in [1, N+1]");
   WC4D_CHECK(o->rhat >= WC4D_RHAT_EXACT && o->rhat <= WC4D_RHAT_BLOCK, WC4D_ERR_ARG, "bad rhat");
@@ -1150,8 +1179,40 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   }
   // covariances
   OpSet<double>& f = P->f64;
-  f.B = P->alloc<double>((int64_t)s * s);
-  f.Q = P->alloc<double>((int64_t)s * s);
+  P->band = (d->cov_kind == WC4D_COV_MSOAR);
+  if (P->band) {
+    // banded circulant B, Q: the taps of the modified SOAR row (Sec. 6.1) and
+    // the diagonal shift |lambda_min| + psi when the circulant is indefinite
+    double* d_lmin = P->alloc<double>(2);
+    auto taps = [&](const double* m, int& mv) {
+      mv = (int)m[2];
+      std::vector<double> row(2 * mv + 1);
+      const double theta = M_PI / mv;
+      for (int i = -mv; i <= mv; ++i) {
+        const double dist = 2.0 * std::fabs(std::sin(i * theta / 2.0));
+        const double q = dist / m[1];
+        row[i + mv] = m[0] * (1.0 + q) * std::exp(-q);
+      }
+      double* dv = P->alloc<double>(2 * mv + 1);
+      WC4D_CUDA(cudaMemcpyAsync(dv, row.data(), sizeof(double) * row.size(), cudaMemcpyHostToDevice, st));
+      WC4D_CUDA(cudaStreamSynchronize(st));  // the host row goes out of scope
+      return dv;
+    };
+    P->bandB = taps(d->msoar_b, P->mvB);
+    P->bandQ = taps(d->msoar_q, P->mvQ);
+    launch_band_lambda_min(P->bandB, P->mvB, s, d_lmin, st);
+    launch_band_lambda_min(P->bandQ, P->mvQ, s, d_lmin + 1, st);
+    double lmin[2];
+    WC4D_CUDA(cudaMemcpyAsync(lmin, d_lmin, sizeof lmin, cudaMemcpyDeviceToHost, st));
+    WC4D_CUDA(cudaStreamSynchronize(st));
+    P->deltaB = lmin[0] < 0.0 ? std::fabs(lmin[0]) + d->msoar_psi[0] : 0.0;
+    P->deltaQ = lmin[1] < 0.0 ? std::fabs(lmin[1]) + d->msoar_psi[1] : 0.0;
+    WC4D_CHECK(lmin[0] + P->deltaB > 0.0 && lmin[1] + P->deltaQ > 0.0, WC4D_ERR_NOT_SPD,
+               "modified SOAR B or Q is singular (lambda_min + shift = 0)");
+  } else {
+    f.B = P->alloc<double>((int64_t)s * s);
+    f.Q = P->alloc<double>((int64_t)s * s);
+  }
   // R: one p x p matrix, or the per-time blocks R_0..R_N one after another
   double* Rdst = nullptr;
   int64_t Rcnt = 0;
@@ -1164,14 +1225,18 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     Rdst = f.R;
     Rcnt = (int64_t)p * p;
   }
-  if (d->cov_kind == WC4D_COV_DENSE) {
-    copy_in(f.B, d->B, sizeof(double) * (size_t)s * s, d->mem_kind, st);
-    copy_in(f.Q, d->Q, sizeof(double) * (size_t)s * s, d->mem_kind, st);
+  if (d->cov_kind == WC4D_COV_DENSE || (P->band && d->R != nullptr)) {
+    if (!P->band) {
+      copy_in(f.B, d->B, sizeof(double) * (size_t)s * s, d->mem_kind, st);
+      copy_in(f.Q, d->Q, sizeof(double) * (size_t)s * s, d->mem_kind, st);
+    }
     copy_in(Rdst, d->R, sizeof(double) * (size_t)Rcnt, d->mem_kind, st);
   } else {
     double* tab = P->alloc<double>(s);
-    launch_soar_fill(f.B, s, nullptr, s, d->soar_b[0], d->soar_b[1], tab, st);
-    launch_soar_fill(f.Q, s, nullptr, s, d->soar_q[0], d->soar_q[1], tab, st);
+    if (!P->band) {
+      launch_soar_fill(f.B, s, nullptr, s, d->soar_b[0], d->soar_b[1], tab, st);
+      launch_soar_fill(f.Q, s, nullptr, s, d->soar_q[0], d->soar_q[1], tab, st);
+    }
     if (P->pertime) {
       for (int t = 0, o0 = 0; t <= N; o0 += P->pt[t], ++t) {
         int64_t a0 = 0;
@@ -1182,8 +1247,10 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       launch_soar_fill(f.R, p, P->d_obs, s, d->soar_r[0], d->soar_r[1], tab, st);
     }
   }
-  launch_check_finite(f.B, (int64_t)s * s, d_flag + 1, st);
-  launch_check_finite(f.Q, (int64_t)s * s, d_flag + 1, st);
+  if (!P->band) {
+    launch_check_finite(f.B, (int64_t)s * s, d_flag + 1, st);
+    launch_check_finite(f.Q, (int64_t)s * s, d_flag + 1, st);
+  }
   launch_check_finite(Rdst, Rcnt, d_flag + 1, st);
   // circulant B and Q (WC4D_COVPROD_FFT): twiddles and spectra
   P->circ = (o->covprod == WC4D_COVPROD_FFT);
@@ -1216,7 +1283,10 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   }
   const int mmax = std::max(s, pmax);
   double* scratch = P->alloc<double>((int64_t)mmax * 64 + 64 * 64 * 2);
-  double* work = P->alloc<double>((int64_t)mmax * mmax);
+  // factorisation workspace: s x s only where B and Q are factored (dense P_D)
+  const bool factor_d = (o->precond == WC4D_PRECOND_PD) && !P->circ && !P->band;
+  const int wdim = factor_d ? mmax : pmax;
+  double* work = P->alloc<double>((int64_t)wdim * wdim);
   if (P->pertime) {
     // Rhat_i from each R_i alone (Sec. 5), then W_i = chol(Rhat_i)^-1 and W_i^T;
     // one pivot-check slot for all time levels
@@ -1302,7 +1372,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       plan_build(P->plan_pd2, {{s, s, 1, TRI_UPPER}, {s, s, N, TRI_UPPER}, {s, s, 1, TRI_FULL}}, C, cm);
     }
     plan_build(P->plan_pi1, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C, cm);
-  } else if (P->circ) {
+  } else if (P->circ || P->band) {
     // only the R family remains on the product path
     plan_build(P->plan_A, {{p, p, N + 1, TRI_FULL}}, C, cm);
     if (P->have_pd) {
@@ -1350,7 +1420,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       launch_split_df(m, h, l, cnt, st);
       f.splits.push_back({m, Split{h, l}});
     };
-    if (!P->circ) {  // circulant B, Q never meet the product kernels
+    if (!P->circ && !P->band) {  // circulant B, Q never meet the product kernels
       add(f.B, (int64_t)s * s);
       add(f.Q, (int64_t)s * s);
     }
@@ -1378,7 +1448,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       launch_oz_rows(m, rows, rows, rows, d, sc, st);
       f.digits.push_back({m, Digits{d, sc}});
     };
-    if (N >= 2 && !P->circ) {
+    if (N >= 2 && !P->circ && !P->band) {
       dig(f.Q, s);
       dig(f.WQ, s);
       dig(f.WQt, s);
@@ -2134,6 +2204,7 @@ __global__ void obs_rhs_kernel(const double* traj, const double* E, const int* o
 static void synthesize_rhs(wc4d_problem* P, const double* zb_in, const double* zr_in, int mem_kind, double* rhs_out) {
   WC4D_CHECK(P->md.kind == WC4D_MODEL_STENCIL3, WC4D_ERR_ARG, "synthesize_rhs needs a linear (STENCIL3) model");
   WC4D_CHECK(!P->pertime, WC4D_ERR_ARG, "synthesize_rhs observes one set at every time (no per-time sets)");
+  WC4D_CHECK(!P->band, WC4D_ERR_ARG, "synthesize_rhs needs dense B (not the banded modified SOAR)");
   const int s = P->s, p = P->p, N = P->N;
   cudaStream_t st = P->st;
   const int mmax = std::max(s, p);
@@ -2852,7 +2923,7 @@ int wc4d_get_matrix(wc4d_problem* P, int32_t which, double* dst) {
   const double* src = nullptr;
   int64_t cnt = 0;
   switch (which) {
-    case 0: src = P->f64.B; cnt = (int64_t)P->s * P->s; break;
+    case 0: src = P->f64.B; cnt = (int64_t)P->s * P->s; break;  // NULL for banded B, Q (refused below)
     case 1: src = P->f64.Q; cnt = (int64_t)P->s * P->s; break;
     case 2:
       src = P->pertime ? P->ptR : P->f64.R;
@@ -2864,6 +2935,7 @@ int wc4d_get_matrix(wc4d_problem* P, int32_t which, double* dst) {
       break;
     default: throw wc4d::Error{WC4D_ERR_ARG, "which must be 0..3"};
   }
+  WC4D_CHECK(src != nullptr, WC4D_ERR_ARG, "this problem keeps no dense copy of that matrix (banded B, Q)");
   WC4D_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, P->st));
   WC4D_CUDA(cudaStreamSynchronize(P->st));
   return WC4D_OK;

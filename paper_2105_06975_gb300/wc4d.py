@@ -35,6 +35,7 @@ WC4D_MODEL_STENCIL3 = 0
 WC4D_MODEL_BANDED = 1
 WC4D_COV_DENSE = 0
 WC4D_COV_SOAR = 1
+WC4D_COV_MSOAR = 2
 WC4D_MEM_HOST = 0
 WC4D_MEM_DEVICE = 1
 WC4D_PRECOND_PD = 0
@@ -79,7 +80,8 @@ class ProblemDesc(ctypes.Structure):
                 ("obs_idx", ctypes.c_void_p), ("cov_kind", ctypes.c_int32),
                 ("B", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("R", ctypes.c_void_p),
                 ("soar_b", ctypes.c_double * 2), ("soar_q", ctypes.c_double * 2), ("soar_r", ctypes.c_double * 2),
-                ("mem_kind", ctypes.c_int32), ("p_t", ctypes.POINTER(ctypes.c_int32))]
+                ("mem_kind", ctypes.c_int32), ("msoar_b", ctypes.c_double * 3), ("msoar_q", ctypes.c_double * 3),
+                ("msoar_psi", ctypes.c_double * 2), ("p_t", ctypes.POINTER(ctypes.c_int32))]
 
 
 class SolveOpts(ctypes.Structure):
@@ -440,7 +442,7 @@ class Problem:
 
     def __init__(self, s, N, p, obs_idx, opts: SolveOpts, *, stencil=None, bands=None, band_lo=0, band_hi=0,
                  banded=False, B=None, Q=None, R=None, soar_b=None, soar_q=None, soar_r=None,
-                 stream: Optional[int] = None, obs_list=None):
+                 stream: Optional[int] = None, obs_list=None, msoar=None):
         """``obs_list``: per-time observation sets (N+1 sorted index arrays);
         then ``p`` and ``obs_idx`` are ignored and a dense ``R`` is a list of
         the N+1 blocks R_i."""
@@ -469,7 +471,17 @@ class Problem:
         else:
             d.model_kind = WC4D_MODEL_STENCIL3
             d.stencil[:] = [float(c) for c in stencil]
-        if B is not None:
+        if msoar is not None:
+            # banded circulant B, Q: ((amp, L, maxval) of B, of Q, (psi_B, psi_Q)); R dense or SOAR
+            d.cov_kind = WC4D_COV_MSOAR
+            d.msoar_b[:] = [float(x) for x in msoar[0]]
+            d.msoar_q[:] = [float(x) for x in msoar[1]]
+            d.msoar_psi[:] = [float(x) for x in msoar[2]]
+            if R is not None:
+                d.R = host(R, np.float64)
+            else:
+                d.soar_r[:] = list(soar_r)
+        elif B is not None:
             d.cov_kind = WC4D_COV_DENSE
             # column-major == row-major for the symmetric covariances
             d.B, d.Q, d.R = host(B, np.float64), host(Q, np.float64), host(R, np.float64)

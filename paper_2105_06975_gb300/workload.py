@@ -101,6 +101,18 @@ class Workload:
         c, d = self.courant, self.diffusion
         return (c + d, 1.0 - c - 2.0 * d, d)
 
+    def heat_bands(self) -> np.ndarray:
+        """The heat model's M_t as bands [N][s][3] (offsets -1, 0, +1): forward
+        Euler with r = heat_r on interior points, homogeneous Dirichlet rows and
+        columns (the boundary points 0 and s-1 carry nothing)."""
+        r, s = self.heat_r, self.s
+        b = np.zeros((self.N, s, 3))
+        j = np.arange(1, s - 1)
+        b[:, j, 0] = np.where(j - 1 >= 1, r, 0.0)
+        b[:, j, 1] = 1.0 - 2.0 * r
+        b[:, j, 2] = np.where(j + 1 <= s - 2, r, 0.0)
+        return b
+
 
 TINY = Workload(name="tiny", s=100, N=10, p=50, obs="even", model="advdiff",
                 soar_b=(1.0, 0.1), soar_q=(0.05, 0.05), soar_r=(0.1, 0.05))
@@ -114,7 +126,11 @@ L96 = Workload(name="l96", s=1000, N=50, p=500, obs="even", model="l96",
 
 HEAT = Workload(name="heat", s=50000, N=5, p=12500, obs="random", model="heat", cov="msoar", r_kind="block")
 
-WORKLOADS = {w.name: w for w in (TINY, SCALE, L96, HEAT)}
+# the heat window at full size with R the chordal SOAR over the observed points
+# (4-point length; the channel-block R of HEAT needs a p x p generator draw)
+HEAT_SOAR_R = HEAT.with_(name="heat-soar-r", r_kind="soar", soar_r=(0.5, 4.0 / 50000))
+
+WORKLOADS = {w.name: w for w in (TINY, SCALE, L96, HEAT, HEAT_SOAR_R)}
 
 
 def block_sizes(p: int, blocks: int) -> np.ndarray:

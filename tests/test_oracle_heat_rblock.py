@@ -271,3 +271,19 @@ def test_r_block_one_cut_spectrum_pairs_about_one():
     ev = np.sort(sla.eigh(R, cov.r_block(R, pvec, tol), eigvals_only=True))
     assert ev[0] + ev[-1] == pytest.approx(2.0, abs=1e-10)
     assert np.allclose(ev + ev[::-1], 2.0, atol=1e-10)
+
+
+def test_band_covariance_problem_equals_dense_problem():
+    """The heat window with B and Q applied through their modified SOAR bands
+    (oracle.saddle.BandCovProblem, for sizes where dense B, Q do not fit) gives
+    the dense problem's A v and P_I^{-1} v on a window where both fit."""
+    w = W.small(W.HEAT, s=300, N=3, p=60)
+    dr = W.draws(w, 2)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    bp = prb.heat_band_problem(w, dr)
+    assert np.array_equal(bp.R, prob.R)
+    v = W.random_vector(prob.n, 4)
+    assert np.linalg.norm(bp.A_apply(v) - prob.A_apply(v)) <= 1e-14 * np.linalg.norm(prob.A_apply(v))
+    o = sd.PrecondOptions(kind="PI", k=2)
+    a, b = sd.Preconditioner(bp, o).apply(v), sd.Preconditioner(prob, o).apply(v)
+    assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(b)

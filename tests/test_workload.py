@@ -65,3 +65,11 @@ def test_small_keeps_length_units():
     assert a.soar_b == W.SCALE.soar_b and a.p == 256 * W.SCALE.p // W.SCALE.s
     b = W.small(W.L96, s=100, N=4)
     assert b.soar_b[1] * 100 == pytest.approx(W.L96.soar_b[1] * W.L96.s)
+
+
+def test_heat_bands_match_the_oracle_model():
+    """The heat model bands the benchmark passes to the library are the
+    oracle's Sec. 7.2 model (Dirichlet rows and columns empty)."""
+    from oracle import model as mdl
+    w = W.small(W.HEAT, s=50, N=3, p=10)
+    assert np.array_equal(w.heat_bands(), mdl.heat_model(w.s, w.N, w.heat_r).bands)
