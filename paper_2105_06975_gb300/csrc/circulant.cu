@@ -35,30 +35,81 @@ namespace cg = cooperative_groups;
 namespace wc4d {
 namespace {
 
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 w) {
-  return make_double2(fma(a.x, w.x, -a.y * w.y), fma(a.x, w.y, a.y * w.x));
+// Scalar arithmetic of the transforms.  FP64 mode runs them in FP64; the
+// double-float modes (DF32, OZAKI) in double-float pairs on the FP32 pipe
+// (value = hi + lo, about 48 significant bits, Dekker / Knuth error-free
+// steps): GB300 issues one FP64 warp instruction per 16 SM cycles but an FP32
+// one per cycle per sub-partition, so the ~20 FP32 instructions of a
+// double-float complex operation still cost far less than its FP64 form.
+struct ArithF64 {
+  using R = double;
+  static __device__ __forceinline__ R add(R a, R b) { return a + b; }
+  static __device__ __forceinline__ R sub(R a, R b) { return a - b; }
+  static __device__ __forceinline__ R mul(R a, R b) { return a * b; }
+  static __device__ __forceinline__ R neg(R a) { return -a; }
+  static __device__ __forceinline__ R from(double x) { return x; }
+  static __device__ __forceinline__ double to(R a) { return a; }
+  static __device__ __forceinline__ R zero() { return 0.0; }
+  static __device__ __forceinline__ R sqrt_half() { return 0.70710678118654752440; }
+};
+struct ArithDF {
+  using R = float2;
+  static __device__ __forceinline__ R add(R a, R b) { return df_add(a, b); }
+  static __device__ __forceinline__ R sub(R a, R b) { return df_add(a, df_neg(b)); }
+  static __device__ __forceinline__ R mul(R a, R b) { return df_mul(a, b); }
+  static __device__ __forceinline__ R neg(R a) { return df_neg(a); }
+  static __device__ __forceinline__ R from(double x) { return df_from(x); }
+  static __device__ __forceinline__ double to(R a) { return (double)a.x + (double)a.y; }
+  static __device__ __forceinline__ R zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ R sqrt_half() { return make_float2(0.70710677f, 1.21016175e-08f); }
+};
+
+// a complex value: 16 bytes in both arithmetics
+template <class A>
+struct Cx {
+  typename A::R re, im;
+};
+template <class A>
+__device__ __forceinline__ Cx<A> cadd(Cx<A> a, Cx<A> b) {
+  return {A::add(a.re, b.re), A::add(a.im, b.im)};
 }
-__device__ __forceinline__ double2 cmulc(double2 a, double2 w) {  // a * conj(w)
-  return make_double2(fma(a.x, w.x, a.y * w.y), fma(a.y, w.x, -a.x * w.y));
+template <class A>
+__device__ __forceinline__ Cx<A> csub(Cx<A> a, Cx<A> b) {
+  return {A::sub(a.re, b.re), A::sub(a.im, b.im)};
+}
+template <class A>
+__device__ __forceinline__ Cx<A> cmul(Cx<A> a, Cx<A> w) {
+  return {A::sub(A::mul(a.re, w.re), A::mul(a.im, w.im)), A::add(A::mul(a.re, w.im), A::mul(a.im, w.re))};
+}
+template <class A>
+__device__ __forceinline__ Cx<A> cmulc(Cx<A> a, Cx<A> w) {  // a * conj(w)
+  return {A::add(A::mul(a.re, w.re), A::mul(a.im, w.im)), A::sub(A::mul(a.im, w.re), A::mul(a.re, w.im))};
 }
 
-// 8-point DFT in registers, natural order in and out.  sign = -1: forward
+// 8-point DFT in registers, natural order in and out.  SIGN = -1: forward
 // (w_8 = exp(-2 pi i / 8)); +1: inverse without the 1/8.  Radix-2
 // decimation in frequency, then the bit-reversed result put back in order.
-template <int SIGN>
-__device__ __forceinline__ void dft8(double2 (&a)[8]) {
-  constexpr double c = 0.70710678118654752440;  // cos(pi/4)
+// Multiplication by w_8^(+-1), w_8^(+-2) = -+i and w_8^(+-3) in closed form.
+template <class A, int SIGN>
+__device__ __forceinline__ void dft8(Cx<A> (&a)[8]) {
+  const typename A::R c = A::sqrt_half();
   // stage h = 4: twiddles w_8^j, j = 0..3
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const double2 u = a[j], v = a[j + 4];
+    const Cx<A> u = a[j], v = a[j + 4];
     a[j] = cadd(u, v);
-    double2 d = csub(u, v);
-    if (j == 1) d = make_double2(c * (d.x - SIGN * d.y), c * (d.y + SIGN * d.x));
-    if (j == 2) d = make_double2(-SIGN * d.y, SIGN * d.x);
-    if (j == 3) d = make_double2(-c * (d.x + SIGN * d.y), c * (SIGN * d.x - d.y));
+    Cx<A> d = csub(u, v);
+    if (j == 1) {
+      const typename A::R x = (SIGN < 0) ? A::add(d.re, d.im) : A::sub(d.re, d.im);
+      const typename A::R y = (SIGN < 0) ? A::sub(d.im, d.re) : A::add(d.im, d.re);
+      d = {A::mul(c, x), A::mul(c, y)};
+    }
+    if (j == 2) d = (SIGN < 0) ? Cx<A>{d.im, A::neg(d.re)} : Cx<A>{A::neg(d.im), d.re};
+    if (j == 3) {
+      const typename A::R x = (SIGN < 0) ? A::sub(d.im, d.re) : A::neg(A::add(d.re, d.im));
+      const typename A::R y = (SIGN < 0) ? A::neg(A::add(d.re, d.im)) : A::sub(d.re, d.im);
+      d = {A::mul(c, x), A::mul(c, y)};
+    }
     a[j + 4] = d;
   }
   // stage h = 2: twiddles w_8^(2j) = w_4^j, j = 0, 1
@@ -66,22 +117,22 @@ __device__ __forceinline__ void dft8(double2 (&a)[8]) {
   for (int b = 0; b < 8; b += 4) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      const double2 u = a[b + j], v = a[b + j + 2];
+      const Cx<A> u = a[b + j], v = a[b + j + 2];
       a[b + j] = cadd(u, v);
-      double2 d = csub(u, v);
-      if (j == 1) d = make_double2(-SIGN * d.y, SIGN * d.x);
+      Cx<A> d = csub(u, v);
+      if (j == 1) d = (SIGN < 0) ? Cx<A>{d.im, A::neg(d.re)} : Cx<A>{A::neg(d.im), d.re};
       a[b + j + 2] = d;
     }
   }
   // stage h = 1
 #pragma unroll
   for (int b = 0; b < 8; b += 2) {
-    const double2 u = a[b], v = a[b + 1];
+    const Cx<A> u = a[b], v = a[b + 1];
     a[b] = cadd(u, v);
     a[b + 1] = csub(u, v);
   }
   // bit-reversed positions 1 <-> 4, 3 <-> 6
-  double2 t = a[1];
+  Cx<A> t = a[1];
   a[1] = a[4];
   a[4] = t;
   t = a[3];
@@ -117,8 +168,21 @@ __device__ __forceinline__ void epilogue_store(const CircJob& J, const ModelDev&
   }
 }
 
-__global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s, const double2* __restrict__ tw,
+template <class A>
+__device__ __forceinline__ const typename A::R* job_lam(const CircJob& J);
+template <>
+__device__ __forceinline__ const double* job_lam<ArithF64>(const CircJob& J) {
+  return J.lam;
+}
+template <>
+__device__ __forceinline__ const float2* job_lam<ArithDF>(const CircJob& J) {
+  return J.lamdf;
+}
+
+template <class A>
+__global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s, const Cx<A>* __restrict__ tw,
                                                             ModelDev md, const int* __restrict__ done, int* ran) {
+  using R = typename A::R;
   pdl_wait();
   pdl_trigger();
   // every CTA of a cluster reads the same flag (written by an earlier grid),
@@ -138,26 +202,26 @@ __global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s
   const int ca = 2 * pr, cb = 2 * pr + 1;
   const bool hasb = cb < J.ncols;
   const int Q = s / CIRC_P, QP = Q / CIRC_P;
-  extern __shared__ double2 circ_smem[];
-  double2* buf = circ_smem;       // phase 2 data: Y[rank, n2], n2 < Q
-  double2* buf2 = circ_smem + Q;  // phase 3 data: V[k1, n2] for this CTA's n2, k1-major
+  extern __shared__ __align__(16) unsigned char circ_raw[];
+  Cx<A>* buf = reinterpret_cast<Cx<A>*>(circ_raw);  // phase 2 data: Y[rank, n2], n2 < Q
+  Cx<A>* buf2 = buf + Q;                             // phase 3 data: V[k1, n2] for this CTA's n2, k1-major
   const double* xa = J.X + (int64_t)ca * J.ldx;
   const double* xb = J.X + (int64_t)(hasb ? cb : ca) * J.ldx;
 
   // ---- phase 1: 8-point DFTs over n1 for this CTA's n2
   for (int t = threadIdx.x; t < QP; t += blockDim.x) {
     const int n2 = rank * QP + t;
-    double2 u[8];
+    Cx<A> u[8];
 #pragma unroll
     for (int n1 = 0; n1 < 8; ++n1) {
       const int idx = Q * n1 + n2;
-      u[n1] = make_double2(xa[idx], hasb ? xb[idx] : 0.0);
+      u[n1] = {A::from(xa[idx]), hasb ? A::from(xb[idx]) : A::zero()};
     }
-    dft8<-1>(u);
+    dft8<A, -1>(u);
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) {
-      const double2 v = (k1 == 0) ? u[0] : cmul(u[k1], tw[n2 * k1]);
-      double2* dst = cl.map_shared_rank(buf, k1);
+      const Cx<A> v = (k1 == 0) ? u[0] : cmul(u[k1], tw[n2 * k1]);
+      Cx<A>* dst = cl.map_shared_rank(buf, k1);
       dst[n2] = v;
     }
   }
@@ -170,18 +234,18 @@ __global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s
     for (int b = threadIdx.x; b < half; b += blockDim.x) {
       const int j = b & (h - 1);
       const int i = ((b / h) * 2 * h) + j;
-      const double2 u = buf[i], v = buf[i + h];
+      const Cx<A> u = buf[i], v = buf[i + h];
       buf[i] = cadd(u, v);
       buf[i + h] = (j == 0) ? csub(u, v) : cmul(csub(u, v), tw[j * stride]);
     }
     __syncthreads();
   }
   {
-    const double* lam = J.lam + (int64_t)rank * Q;
+    const R* lam = job_lam<A>(J) + (int64_t)rank * Q;
     for (int i = threadIdx.x; i < Q; i += blockDim.x) {
-      const double l = lam[i];
-      const double2 u = buf[i];
-      buf[i] = make_double2(u.x * l, u.y * l);
+      const R l = lam[i];
+      const Cx<A> u = buf[i];
+      buf[i] = {A::mul(u.re, l), A::mul(u.im, l)};
     }
   }
   __syncthreads();
@@ -190,8 +254,8 @@ __global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s
     for (int b = threadIdx.x; b < half; b += blockDim.x) {
       const int j = b & (h - 1);
       const int i = ((b / h) * 2 * h) + j;
-      const double2 u = buf[i];
-      const double2 v = (j == 0) ? buf[i + h] : cmulc(buf[i + h], tw[j * stride]);
+      const Cx<A> u = buf[i];
+      const Cx<A> v = (j == 0) ? buf[i + h] : cmulc(buf[i + h], tw[j * stride]);
       buf[i] = cadd(u, v);
       buf[i + h] = csub(u, v);
     }
@@ -199,8 +263,8 @@ __global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s
   }
   // twiddle w^(-n2 k1) and send W[rank, n2] to the CTA owning n2
   for (int n2 = threadIdx.x; n2 < Q; n2 += blockDim.x) {
-    const double2 v = (rank == 0) ? buf[n2] : cmulc(buf[n2], tw[n2 * rank]);
-    double2* dst = cl.map_shared_rank(buf2, n2 / QP);
+    const Cx<A> v = (rank == 0) ? buf[n2] : cmulc(buf[n2], tw[n2 * rank]);
+    Cx<A>* dst = cl.map_shared_rank(buf2, n2 / QP);
     dst[rank * QP + (n2 % QP)] = v;
   }
   cl.sync();
@@ -209,16 +273,25 @@ __global__ void __launch_bounds__(CIRC_THREADS) circ_kernel(CircJobs jobs, int s
   const double inv_s = 1.0 / (double)s;
   for (int t = threadIdx.x; t < QP; t += blockDim.x) {
     const int n2 = rank * QP + t;
-    double2 u[8];
+    Cx<A> u[8];
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) u[k1] = buf2[k1 * QP + t];
-    dft8<1>(u);
+    dft8<A, 1>(u);
 #pragma unroll
     for (int n1 = 0; n1 < 8; ++n1) {
       const int r = Q * n1 + n2;
-      epilogue_store(J, md, s, r, ca, u[n1].x * inv_s);
-      if (hasb) epilogue_store(J, md, s, r, cb, u[n1].y * inv_s);
+      epilogue_store(J, md, s, r, ca, A::to(u[n1].re) * inv_s);
+      if (hasb) epilogue_store(J, md, s, r, cb, A::to(u[n1].im) * inv_s);
     }
+  }
+}
+
+// double -> double-float pairs (twiddle and spectrum tables of the DF kernel)
+__global__ void circ_split_kernel(const double* __restrict__ in, float2* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double x = in[i];
+    const float h = __double2float_rn(x);
+    out[i] = make_float2(h, __double2float_rn(x - (double)h));
   }
 }
 
@@ -424,16 +497,17 @@ void launch_circ_spectrum(const double* col, int s, const double2* tw, double sh
   WC4D_LAUNCH_CHECK();
 }
 
-void launch_circ(const CircJobs& jobs, int s, const double2* tw, const ModelDev& md, const int* done,
-                 cudaStream_t st) {
+void launch_circ(const CircJobs& jobs, int s, const double2* tw, const float4* twdf, const ModelDev& md,
+                 const int* done, cudaStream_t st) {
   if (jobs.n == 0) return;
   const int transforms = jobs.tr_base[jobs.n];
   if (transforms == 0) return;
   WC4D_CHECK(circ_size_ok(s), WC4D_ERR_ARG, "internal: circulant product of an unsupported size");
+  WC4D_CHECK(!jobs.df || twdf != nullptr, WC4D_ERR_ARG, "internal: double-float transform without its tables");
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(transforms * CIRC_P));
   cfg.blockDim = dim3(CIRC_THREADS);
-  cfg.dynamicSmemBytes = sizeof(double2) * 2 * (s / CIRC_P);
+  cfg.dynamicSmemBytes = 16 * 2 * (s / CIRC_P);
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -457,9 +531,19 @@ void launch_circ(const CircJobs& jobs, int s, const double2* tw, const ModelDev&
     }
     ran = prof_begin(PROF_CIRC, transforms * (10.0 * s * lg + 2.0 * s), st, bytes);
   }
-  WC4D_CUDA(cudaLaunchKernelEx(&cfg, circ_kernel, jobs, s, tw, md, done, ran));
+  if (jobs.df)
+    WC4D_CUDA(cudaLaunchKernelEx(&cfg, circ_kernel<ArithDF>, jobs, s, reinterpret_cast<const Cx<ArithDF>*>(twdf), md,
+                                 done, ran));
+  else
+    WC4D_CUDA(cudaLaunchKernelEx(&cfg, circ_kernel<ArithF64>, jobs, s, reinterpret_cast<const Cx<ArithF64>*>(tw),
+                                 md, done, ran));
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
+}
+
+void launch_circ_split(const double* in, float2* out, int n, cudaStream_t st) {
+  circ_split_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+  WC4D_LAUNCH_CHECK();
 }
 
 }  // namespace wc4d

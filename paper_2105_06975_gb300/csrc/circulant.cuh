@@ -22,7 +22,7 @@ struct CircJob {
   const double* X;
   int64_t ldx;
   int ncols;
-  const double* lam;
+  const double* lam;  // FP64 kernel: spectrum in cluster layout
   int mode;
   double* C;
   int64_t ldc;
@@ -31,10 +31,12 @@ struct CircJob {
   const double* Y;   // EPI_SUB_FROM: minuend
   float* Ch = nullptr;  // optional double-float split of C
   float* Cl = nullptr;
+  const float2* lamdf = nullptr;  // double-float kernel: the same spectrum as (hi, lo) pairs
 };
 struct CircJobs {
   CircJob j[CIRC_MAX_JOBS];
   int n = 0;
+  int df = 0;  // 1: transforms in double-float on the FP32 pipe (DF32 / OZAKI modes), 0: FP64
   int tr_base[CIRC_MAX_JOBS + 1];  // complex transforms (column pairs) before each job
 };
 
@@ -51,9 +53,12 @@ void launch_circ_twiddles(double2* tw, int s, cudaStream_t st);
 // finite (the matrix is not SPD).
 void launch_circ_spectrum(const double* col, int s, const double2* tw, double shift, int invert, double* lam,
                           int* flag, cudaStream_t st);
-// all jobs of one launch (products of one dependency level)
-void launch_circ(const CircJobs& jobs, int s, const double2* tw, const ModelDev& md, const int* done,
-                 cudaStream_t st);
+// all jobs of one launch (products of one dependency level); twdf: the
+// twiddle table as double-float pairs (re, im), needed when jobs.df
+void launch_circ(const CircJobs& jobs, int s, const double2* tw, const float4* twdf, const ModelDev& md,
+                 const int* done, cudaStream_t st);
+// out[i] = (hi, lo) of in[i] (setup: the double-float tables)
+void launch_circ_split(const double* in, float2* out, int n, cudaStream_t st);
 // add a job (transforms counted per pair of columns)
 inline void circ_add(CircJobs& jobs, const CircJob& jb) {
   if (jobs.n == 0) jobs.tr_base[0] = 0;

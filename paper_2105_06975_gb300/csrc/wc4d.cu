@@ -260,6 +260,10 @@ struct wc4d_problem {
   bool circ = false;
   double2* tw = nullptr;
   double *lamB = nullptr, *lamQ = nullptr, *lamBi = nullptr, *lamQi = nullptr;
+  // DF32 / OZAKI: the transforms run in double-float (tables as (hi, lo) pairs)
+  bool circ_df = false;
+  float4* twdf = nullptr;
+  float2 *lamBdf = nullptr, *lamQdf = nullptr, *lamBidf = nullptr, *lamQidf = nullptr;
   // per-time observation sets (desc.p_t): counts, device layout of the nu
   // blocks and of the R_i, Rhat_i, W_i = chol(Rhat_i)^-1 and W_i^T blocks
   // (one after another); the inverse maps are (N+1) x s
@@ -350,6 +354,20 @@ static double pt_bytes(const wc4d_problem* P, const PtProd& pr) {
   return 8.0 * (a + (double)P->np * (pr.mode == EPI_SADDLE_C2 ? 3 : 2));
 }
 
+// launch the circulant jobs in the problem's arithmetic: double-float
+// transforms (and their spectrum tables) in the DF32 / OZAKI modes
+static void run_circ(wc4d_problem* P, CircJobs& cj, const int* done) {
+  cj.df = P->circ_df ? 1 : 0;
+  if (cj.df) {
+    for (int q = 0; q < cj.n; ++q) {
+      const double* l = cj.j[q].lam;
+      cj.j[q].lamdf = (l == P->lamB) ? P->lamBdf : (l == P->lamQ) ? P->lamQdf : (l == P->lamBi) ? P->lamBidf
+                                                                                               : P->lamQidf;
+    }
+  }
+  launch_circ(cj, P->s, P->tw, P->twdf, P->md, done, P->st);
+}
+
 // D x (B on column 0, Q on columns 1..N) off the product path, for circulant
 // (FFT) or banded circulant (taps) B and Q, with the product epilogue: mode
 // EPI_SADDLE_C1 (C_t = (D x)_t + (L v3)_t) or EPI_SUB_FROM (C = Y - D x)
@@ -363,7 +381,7 @@ static void d_offpath(wc4d_problem* P, const double* x, int mode, double* C, con
     if (N > 0)
       circ_add(cj, CircJob{x + s, s, N, P->lamQ, mode, C + s, s, 1, v3, Y1, Ch ? Ch + s : nullptr,
                            Cl ? Cl + s : nullptr});
-    launch_circ(cj, s, P->tw, P->md, done, P->st);
+    run_circ(P, cj, done);
     return;
   }
   BandJobs bj{};
@@ -516,7 +534,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
         if (N > 0) circ_add(cj, CircJob{v1 + s, s, N, P->lamQi, EPI_STORE, o1 + s, s, 0, nullptr, nullptr});
         circ_add(cj, CircJob{y3, s, 1, P->lamB, EPI_STORE, u3, s, 0, nullptr, nullptr});
         if (N > 0) circ_add(cj, CircJob{y3 + s, s, N, P->lamQ, EPI_STORE, u3 + s, s, 0, nullptr, nullptr});
-        launch_circ(cj, s, P->tw, P->md, done, P->st);
+        run_circ(P, cj, done);
       } else {
         GemmOpsT<T> ops{};
         EpisT<T> ep{};
@@ -568,7 +586,7 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
       if (N > 0) circ_add(cj, CircJob{v1 + s, s, N, P->lamQi, EPI_STORE, o1 + s, s, 0, nullptr, nullptr});
       circ_add(cj, CircJob{y3, s, 1, P->lamB, EPI_STORE, u3, s, 0, nullptr, nullptr});
       if (N > 0) circ_add(cj, CircJob{y3 + s, s, N, P->lamQ, EPI_STORE, u3 + s, s, 0, nullptr, nullptr});
-      launch_circ(cj, s, P->tw, P->md, done, P->st);
+      run_circ(P, cj, done);
       GemmOpsT<T> ops2{};
       EpisT<T> ep2{};
       ops2.nops = 1;
@@ -1279,6 +1297,21 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       const double delta = (o->dhat == WC4D_DHAT_SHIFT) ? o->dhat_delta : 0.0;
       P->lamBi = spectrum(f.B, delta, 1, "Bhat");
       P->lamQi = spectrum(f.Q, delta, 1, "Qhat");
+    }
+    P->circ_df = (o->precision != WC4D_PREC_FP64);
+    if (P->circ_df) {
+      auto split = [&](const double* l) {
+        if (!l) return (float2*)nullptr;
+        float2* dv = P->alloc<float2>(s);
+        launch_circ_split(l, dv, s, st);
+        return dv;
+      };
+      P->twdf = P->alloc<float4>(s);
+      launch_circ_split(reinterpret_cast<const double*>(P->tw), reinterpret_cast<float2*>(P->twdf), 2 * s, st);
+      P->lamBdf = split(P->lamB);
+      P->lamQdf = split(P->lamQ);
+      P->lamBidf = split(P->lamBi);
+      P->lamQidf = split(P->lamQi);
     }
   }
   const int mmax = std::max(s, pmax);
