@@ -59,6 +59,8 @@ def parse():
                     help="product precision of the batched and learned workloads")
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-comparisons", action="store_true",
+                    help="skip the P_D + MINRES and circulant-FFT comparison solves of the default line")
     ap.add_argument("--ref-budget-s", type=float, default=240.0,
                     help="reference arm: time budget for its timed full oracle solves (stops early)")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi (profiler runs)")
@@ -268,8 +270,6 @@ GEMM_DF32_TRAFFIC_BYTES = 53.3e6
 TRAFFIC_RATIO = {
     "orth": (0.9934, "ncu dram bytes of gm_dc_dot + gm_dc_update at Arnoldi step j = 99 (544.8 MB) over their "
                      "algorithmic bytes (548.5 MB), profiles/gm_dc_arnoldi__advdiff_s2048_N64.md"),
-    "gemm_tc": (0.947, "ncu dram bytes of one A v launch of gemm_tc_kernel (123.2 MB) over its algorithmic "
-                       "bytes (130.1 MB), profiles/gemm_tc__advdiff_s2048_N64.md"),
 }
 
 
@@ -296,7 +296,10 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                                             "FP32 lane operations per double-float multiply-add"}
     if st.gemmtc_launches:
         ms1 = st.gemmtc_ms / st.gemmtc_launches
-        a_hbm = st.gemmtc_bytes / (st.gemmtc_ms * 1e-3) / 1e9
+        # the byte floor of SURVEY's per-unit accounting: each FP64 operator entry read once, vectors once;
+        # the digit form (what the kernel moves: 14 B per operator entry) is reported beside it
+        a_hbm = st.gemmtc_alg_bytes / (st.gemmtc_ms * 1e-3) / 1e9
+        a_dig = st.gemmtc_bytes / (st.gemmtc_ms * 1e-3) / 1e9
         a_tc = st.gemmtc_mma_flops / (st.gemmtc_ms * 1e-3) / 1e12
         bf16 = peaks().get("bf16_tflops")
         f_hbm = (a_hbm / hbm) if hbm else None
@@ -309,12 +312,17 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                            "peak": bf16 if tensor_bound else hbm,
                            "unit": "TFLOP/s" if tensor_bound else "GB/s",
                            "frac": f_tc if tensor_bound else f_hbm,
-                           "hbm": {"achieved_gbs": a_hbm, "frac": f_hbm},
+                           "hbm": {"achieved_gbs": a_hbm, "frac": f_hbm,
+                                   "bytes": "FP64 operator entries (their triangle) once, vectors once"},
+                           "digit_form": {"achieved_gbs": a_dig, "frac": (a_dig / hbm) if hbm else None,
+                                          "bytes_per_launch": st.gemmtc_alg_bytes / st.gemmtc_launches,
+                                          "bytes": "digit tiles (14 B per operator entry), GEMV operands, "
+                                                   "vector digits, partial tiles: what the kernel moves"},
                            "tensor": {"achieved_tflops_bf16": a_tc, "frac": f_tc},
                            "fp64_class_tflops": st.gemmtc_flops / (st.gemmtc_ms * 1e-3) / 1e12,
                            "launches": st.gemmtc_launches, "ms_per_launch": ms1,
                            "flops_per_launch": st.gemmtc_flops / st.gemmtc_launches,
-                           "bytes_per_launch": st.gemmtc_bytes / st.gemmtc_launches,
+                           "bytes_per_launch": st.gemmtc_alg_bytes / st.gemmtc_launches,
                            "mma_flops_per_launch": st.gemmtc_mma_flops / st.gemmtc_launches,
                            "share_of_step": st.gemmtc_ms / step_ms,
                            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) / hbm_gbs (measured)"}
@@ -473,6 +481,29 @@ def run_gpu(args):
                          "profiled_ms_per_step": prof_ms / args.steps,
                          "setup_ms": statistics.mean(a for a, _ in split),
                          "solve_ms": statistics.mean(b for _, b in split)}
+    # the paper's other preconditioner and the circulant products on the same window (Sec. 2.2, 6.1):
+    # P_D + MINRES and P_I + GMRES with B, Q by FFT, timed like the headline steps
+    comparisons = {}
+    if not args.no_comparisons and world == 1:
+        for name, o in (("PD_minres_ozaki_fft", wc4d.make_opts(precond="PD", k=args.k, rhat=args.rhat, tol=1e-6,
+                                                               maxit=3000, precision="ozaki", covprod="fft",
+                                                               check_every=ce)),
+                        ("PI_gmres_ozaki_fft", wc4d.make_opts(precond="PI", k=args.k, rhat=args.rhat, tol=1e-6,
+                                                              maxit=args.maxit, precision="ozaki", covprod="fft",
+                                                              check_every=ce)),
+                        ("PD_minres_ozaki", wc4d.make_opts(precond="PD", k=args.k, rhat=args.rhat, tol=1e-6,
+                                                           maxit=3000, precision="ozaki", check_every=ce))):
+            if name == "PI_gmres_ozaki_fft" and args.precond == "PI" and "ozaki_fft" in results:
+                continue
+            for _ in range(max(1, args.warmup // 2)):
+                step(o)
+            c_ms, c_infos, _ = timed(o, False)
+            assert all(i.status == 0 for i in c_infos), [i.as_dict() for i in c_infos]
+            comparisons[name] = {"solves_per_s": 1e3 * args.steps / c_ms, "ms_per_step": c_ms / args.steps,
+                                 "iterations": statistics.mean(i.iters for i in c_infos),
+                                 "relres_true_max": max(i.relres_true for i in c_infos),
+                                 "setup_ms_host": statistics.mean(a for a, _ in split),
+                                 "solve_ms_host": statistics.mean(b for _, b in split)}
     clocks = clk.stop()
     chosen = results[args.chosen] if args.chosen in results else next(iter(results.values()))
     fp64 = results.get("fp64", chosen)
@@ -547,6 +578,7 @@ def run_gpu(args):
                       "iterations": statistics.mean(i.iters for i in r["infos"]),
                       "setup_ms_host": r["setup_ms"], "solve_ms_host": r["solve_ms"]} for m, r in results.items()},
         "relres_true_max": max(i.relres_true for i in chosen["infos"]),
+        "comparisons": comparisons,
         "fp64_solves_per_s": fp64["value"],
         "chosen_over_fp64": chosen["value"] / fp64["value"],
         "roofline": roof,

@@ -479,6 +479,8 @@ typedef struct {
                                        partial tiles written                                       */
   double gemmtc_mma_flops;          /* BF16 tensor-core flops of the digit products issued         */
   int64_t gemmtc_launches;
+  double gemmtc_alg_bytes;          /* the same launches' floor: each FP64 operator entry (its
+                                       triangle for factors) read once, vectors read and written once */
   double circ_ms, circ_flops;       /* circulant FFT products (WC4D_COVPROD_FFT): FP64 flops counted
                                        as 5 s log2 s per complex transform (two per column pair) plus
                                        the spectrum scaling                                          */

@@ -339,6 +339,8 @@ struct GemmPlan {
                                   // X digit tiles once per op, partial tiles written
   double tc_mma_flops = 0;        // tensor-core plan: BF16 flops of the issued digit products
   double tc_digit_bytes = 0;      // the part of tc_bytes that is digit tiles (scales with the digits used)
+  double alg_bytes = 0;           // each FP64 operator entry (its triangle) read once, X read once, C written
+                                  // once: the floor of any product kernel, whatever its operand form
   std::shared_ptr<void> owner;    // keeps the device arrays alive (plans are shared through a cache)
 };
 
@@ -355,7 +357,8 @@ enum { PROF_GEMM = 0, PROF_ORTH = 1, PROF_GEMM32 = 2, PROF_GEMMDF = 3, PROF_GEMM
        PROF_PERTIME = 6, PROF_CLASSES = 7 };
 bool prof_enabled();
 // returns a device int* the kernel sets to 1 when it runs (nullptr when off)
-int* prof_begin(int cls, double work, cudaStream_t st, double work2 = 0.0, double work3 = 0.0);
+int* prof_begin(int cls, double work, cudaStream_t st, double work2 = 0.0, double work3 = 0.0,
+                double work4 = 0.0);
 void prof_end(cudaStream_t st);
 void plan_free(GemmPlan& plan);
 

@@ -115,9 +115,12 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
         Tile t{o, row0, c * cw, klo / GEMM_BK, (khi + GEMM_BK - 1) / GEMM_BK, cost, cols == 1};
         tiles.push_back(t);
         flops += 2.0 * rows * cols * (double)(khi - klo);
+        if (c == 0) plan.alg_bytes += 8.0 * rows * (double)(khi - klo);  // operator rows of this tile, once
       }
     }
   }
+  for (int o = 0; o < plan.nops; ++o)  // X read once, C written once
+    plan.alg_bytes += 8.0 * ((double)shapes[o].kdim + shapes[o].m) * std::max(0, shapes[o].ncols);
   plan.ntiles = (int)tiles.size();
   plan.total_out = outpos;
   plan.flops = flops;
@@ -666,7 +669,7 @@ void launch_products<double>(const GemmPlan& plan, const GemmOpsT<double>& ops, 
     const int nd = ops.ndig;
     const double bytes = plan.tc_bytes - plan.tc_digit_bytes * (1.0 - nd / (double)OZ_DIGITS);
     const double mma = plan.tc_mma_flops * (nd * (nd + 1) / 2) / (double)(OZ_DIGITS * (OZ_DIGITS + 1) / 2);
-    int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, bytes, mma);
+    int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, bytes, mma, plan.alg_bytes);
     launch_gemm_tc(ops, plan.d_segs, plan.d_seg_start, plan.nctas, partial, done, ran, ops.err, st);
     if (ran) prof_end(st);
     return;

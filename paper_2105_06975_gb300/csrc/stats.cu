@@ -16,7 +16,7 @@ struct Rec {
   int cls;
   double work;
   int flag;
-  double work2, work3;
+  double work2, work3, work4;
 };
 struct Profile {
   std::mutex mu;
@@ -45,12 +45,12 @@ cudaEvent_t get_event(Profile& p) {
 
 bool prof_enabled() { return prof().on; }
 
-int* prof_begin(int cls, double work, cudaStream_t st, double work2, double work3) {
+int* prof_begin(int cls, double work, cudaStream_t st, double work2, double work3, double work4) {
   Profile& p = prof();
   std::lock_guard<std::mutex> lk(p.mu);
   if (!p.on || (int)p.recs.size() >= p.cap) return nullptr;
   // the flag slot is zero: slots are cleared when allocated and on every reset
-  Rec r{get_event(p), get_event(p), cls, work, (int)p.recs.size(), work2, work3};
+  Rec r{get_event(p), get_event(p), cls, work, (int)p.recs.size(), work2, work3, work4};
   WC4D_CUDA(cudaEventRecord(r.e0, st));
   p.recs.push_back(r);
   return p.d_flags + r.flag;
@@ -127,6 +127,7 @@ int wc4d_get_stats(wc4d_stats* out) {
       out->gemmtc_flops += p.recs[i].work;
       out->gemmtc_bytes += p.recs[i].work2;
       out->gemmtc_mma_flops += p.recs[i].work3;
+      out->gemmtc_alg_bytes += p.recs[i].work4;
       out->gemmtc_launches += 1;
     } else if (p.recs[i].cls == PROF_CIRC) {
       out->circ_ms += ms;

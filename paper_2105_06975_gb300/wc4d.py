@@ -116,7 +116,8 @@ class Stats(ctypes.Structure):
                 ("gemmdf_flops", ctypes.c_double), ("gemmdf_launches", ctypes.c_int64),
                 ("gemmtc_ms", ctypes.c_double), ("gemmtc_flops", ctypes.c_double),
                 ("gemmtc_bytes", ctypes.c_double), ("gemmtc_mma_flops", ctypes.c_double),
-                ("gemmtc_launches", ctypes.c_int64), ("circ_ms", ctypes.c_double), ("circ_flops", ctypes.c_double),
+                ("gemmtc_launches", ctypes.c_int64), ("gemmtc_alg_bytes", ctypes.c_double),
+                ("circ_ms", ctypes.c_double), ("circ_flops", ctypes.c_double),
                 ("circ_bytes", ctypes.c_double), ("circ_launches", ctypes.c_int64), ("pt_ms", ctypes.c_double),
                 ("pt_bytes", ctypes.c_double), ("pt_launches", ctypes.c_int64)]
 

@@ -45,11 +45,15 @@ def test_kernel_rows_fractions_and_shares():
 def test_tensor_core_row_takes_the_tighter_roof(monkeypatch):
     monkeypatch.setattr(bench, "peaks", lambda: {"bf16_tflops": 1918.0})
     hbm = 6795.8
-    # bytes-heavy launch: 3 TB/s of 6.8 against 400 TF of 1918 -> HBM is the tighter roof
-    st = _stats(gemmtc_ms=100.0, gemmtc_flops=1e9, gemmtc_bytes=3e11, gemmtc_mma_flops=4e13, gemmtc_launches=10)
+    # bytes-heavy launch: 3 TB/s of FP64-operator bytes (5.25 TB/s in the digit form) against 400 TF of
+    # 1918 -> HBM is the tighter roof, measured on the FP64-operator floor
+    st = _stats(gemmtc_ms=100.0, gemmtc_flops=1e9, gemmtc_bytes=5.25e11, gemmtc_alg_bytes=3e11,
+                gemmtc_mma_flops=4e13, gemmtc_launches=10)
     r = bench.kernel_rows(st, 1000.0, hbm=hbm)["gemm_tc"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["frac"] == pytest.approx(3000.0 / hbm)
+    assert r["bytes_per_launch"] == pytest.approx(3e10)
+    assert r["digit_form"]["frac"] == pytest.approx(5250.0 / hbm)
     assert r["tensor"]["frac"] == pytest.approx(400.0 / 1918.0)
     assert r["mma_flops_per_launch"] == pytest.approx(4e12)
     # flop-heavy launch: 1500 TF -> the tensor roof is the tighter one
