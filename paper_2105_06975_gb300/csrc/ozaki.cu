@@ -369,6 +369,9 @@ __device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float
   }
 }
 
+// FULL: all 7 digits (the digit count is a compile-time constant and the
+// drain and MMA loops unroll as before); otherwise ops.ndig leading digits.
+template <bool FULL>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_tc_kernel(GemmOpsT<double> ops, const GemmSeg* __restrict__ segs, const int* __restrict__ seg_start,
                    float2* __restrict__ partial, const int* __restrict__ done, int* ran, int* err) {
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   // the leading nd digits of each operand: the first nd tiles of every digit
   // block are copied and the levels 0..nd-1 accumulated (nd = 7: exact to the
   // 47-bit operands; fewer: a reduced-precision product, 7 nd - 1 bits)
-  const int nd = ops.ndig;
+  const int nd = FULL ? OZ_DIGITS : ops.ndig;
   const uint32_t a_bytes = (uint32_t)nd * OZ_A_TILE * 2, x_bytes = (uint32_t)nd * OZ_X_TILE * 2;
   if (tid == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -533,6 +536,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       __syncwarp();
       tc_fence_after();
+      // once any role has given up, the launch's outputs are invalid (the host
+      // reports the error): later segments write nothing (this segment's
+      // accumulators are complete, tfull having arrived)
+      const bool write_ok = !abort_flag;
       const int r = 32 * quarter + lane, row = sg.row0 + r;
       const bool rin = row < op.m;
       const float sig = rin ? op.As[row] : 0.f;
@@ -570,9 +577,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           float hh, ll;
           fast_two_sum(h, lo, hh, ll);
-          // once any role has given up, the launch's outputs are invalid (the
-          // host reports the error): nothing more is written
-          if (rin && c < ncv && !abort_flag) {
+          if (rin && c < ncv && write_ok) {
             const float f = sig * op.Xs[sg.col0 + c] * 0x1p-10f;
             dst[c * OZ_BM + r] = make_float2(hh * f, ll * f);
           }
@@ -625,10 +630,16 @@ void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int*
                     double* partial, const int* done, int* ran, int* err, cudaStream_t st) {
   static std::once_flag once;
   std::call_once(once, [] {
-    WC4D_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    WC4D_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    WC4D_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
   });
-  WC4D_CUDA(launch_pdl(gemm_tc_kernel, dim3(nctas), dim3(OZ_THREADS), OZ_SMEM, st, ops, segs, seg_start,
-                       reinterpret_cast<float2*>(partial), done, ran, err));
+  WC4D_CHECK(ops.ndig >= 1 && ops.ndig <= OZ_DIGITS, WC4D_ERR_ARG, "internal: digit count out of range");
+  if (ops.ndig == OZ_DIGITS)
+    WC4D_CUDA(launch_pdl(gemm_tc_kernel<true>, dim3(nctas), dim3(OZ_THREADS), OZ_SMEM, st, ops, segs, seg_start,
+                         reinterpret_cast<float2*>(partial), done, ran, err));
+  else
+    WC4D_CUDA(launch_pdl(gemm_tc_kernel<false>, dim3(nctas), dim3(OZ_THREADS), OZ_SMEM, st, ops, segs, seg_start,
+                         reinterpret_cast<float2*>(partial), done, ran, err));
   WC4D_LAUNCH_CHECK();
 }
 
