@@ -853,7 +853,7 @@ def run_profile(args):
     dr = W.draws(w, args.seed)
     base = args.chosen.replace("_fft", "")
     o = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-30, maxit=args.maxit,
-                       precision=base if base in ("df32", "ozaki") else "ozaki",
+                       precision=base if base in ("fp64", "df32", "ozaki") else "ozaki",
                        covprod="fft" if args.chosen.endswith("_fft") else "dense",
                        krylov="gmres" if args.precond == "PI" else "minres")
     G = wc4d.Problem.from_workload(w, dr, o)
