@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
     ap.add_argument("--chosen", default="ozaki", choices=["fp64", "df32", "df32p32", "mixed", "ozaki", "fp64_fft",
-                                                          "df32_fft", "ozaki_fft"])
+                                                          "df32_fft", "ozaki_fft", "ozaki_rinv"])
     ap.add_argument("--precision", default="ozaki", choices=["df32", "ozaki"],
                     help="product precision of the batched and learned workloads")
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
@@ -244,7 +244,8 @@ MODE_DTYPE = {"fp64": "f64", "df32": "df32 products (2 x f32, ~48-bit) / f64 rec
               "fp64_fft": "f64 (B, Q by f64 FFT)",
               "df32_fft": "f64 FFT for B, Q; df32 R-family products / f64 recurrences",
               "ozaki_fft": "f64 FFT for B, Q; bf16 digit products exact in f32 for the R family / df32 / f64 "
-                           "recurrences"}
+                           "recurrences",
+              "ozaki_rinv": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / df32 / f64 recurrences"}
 MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
              "df32": "FP64 GMRES; covariance / factor products in double-float on the FP32 pipe",
              "ozaki": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
@@ -253,9 +254,12 @@ MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
                       "preconditioned by FP32 {pc}",
              "fp64_fft": "plain FP64 with circulant B, Q (and Bhat^-1, Qhat^-1) by FP64 FFT",
              "df32_fft": "FP64 Krylov; circulant B, Q by FP64 FFT; R-family products in double-float",
-             "ozaki_fft": "FP64 Krylov; circulant B, Q (and Bhat^-1, Qhat^-1) by FP64 FFT (cluster-split "
-                          "four-step transform); multi-column R-family products as exact BF16 digit products "
-                          "on tcgen05"}
+             "ozaki_fft": "FP64 Krylov; circulant B, Q (and Bhat^-1, Qhat^-1) by FFT (cluster-split "
+                          "four-step transform, double-float); multi-column R-family products as exact BF16 digit "
+                          "products on tcgen05",
+             "ozaki_rinv": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products on "
+                           "tcgen05; Rhat^-1 as one product with the explicit inverse W^T W (in the launch of "
+                           "P_I's D c1)"}
 
 
 # DRAM bytes per launch of gemm_streamk_df32_kernel, ncu dram__bytes_read.sum + dram__bytes_write.sum,
@@ -393,6 +397,10 @@ def run_gpu(args):
         "ozaki": wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.maxit,
                                 precision="ozaki", check_every=ce),
     }
+    # Rhat^-1 as one product with the explicit inverse (one dependency level less per preconditioner apply)
+    if args.chosen == "ozaki_rinv" or (args.modes and "ozaki_rinv" in args.modes.split(",")):
+        modes["ozaki_rinv"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
+                                             maxit=args.maxit, precision="ozaki", check_every=ce, rinv_explicit=True)
     # circulant B and Q applied by FFT (Sec. 6.1), the R family as in the base mode
     for m in ("fp64", "df32", "ozaki"):
         if args.chosen == m + "_fft" or (args.modes and m + "_fft" in args.modes.split(",")):
@@ -477,7 +485,7 @@ def run_gpu(args):
         assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
         results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
                          "kernels": kernel_rows(st, prof_ms, hbm, dcgs=mode in ("df32", "df32p32", "ozaki", "df32_fft",
-                                                                              "ozaki_fft")),
+                                                                              "ozaki_fft", "ozaki_rinv")),
                          "profiled_ms_per_step": prof_ms / args.steps,
                          "setup_ms": statistics.mean(a for a, _ in split),
                          "solve_ms": statistics.mean(b for _, b in split)}

@@ -212,6 +212,13 @@ typedef struct {
                                 keeps the computed preconditioned vectors (flexible), so the
                                 rounding costs iterations, not accuracy; A v, the Arnoldi process
                                 and the true residual stay FP64-class (not in the paper).       */
+  int32_t rinv_explicit;     /* 0: Rhat^-1 v = W^T (W v) with W = chol(Rhat)^-1, two dependent
+                                products (Sec. 6.2's triangular solves as products); 1: the
+                                symmetric inverse W^T W is formed once at setup and Rhat^-1 v is
+                                one product, in the same launch as P_I's D c1 (the same bytes,
+                                one dependency level less per preconditioner apply).  Needs one
+                                observation set, precision FP64, DF32 or OZAKI, shat PAPER or
+                                LEARNED (not in the paper)                                      */
 } wc4d_solve_opts;
 
 typedef struct {

@@ -54,6 +54,7 @@ struct OpSet {
   T *B = nullptr, *Q = nullptr, *R = nullptr;
   T *WB = nullptr, *WBt = nullptr, *WQ = nullptr, *WQt = nullptr, *WR = nullptr, *WRt = nullptr;
   T *WS = nullptr, *WSt = nullptr;
+  T* Rinv = nullptr;  // explicit Rhat^-1 = W_R^T W_R (wc4d_solve_opts.rinv_explicit)
   T* partial = nullptr;
   T *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;  // n-length scratch
   // double-float splits of the operators above (DF32 / MIXED outer products)
@@ -252,6 +253,7 @@ struct wc4d_problem {
   // WC4D_COVPROD_FFT: B and Q are circulant and applied by FFT (twiddle table,
   // spectra of B, Q and of Bhat^-1, Qhat^-1 in the FFT kernel's cluster layout)
   int pdig = 7;  // OZAKI: digits of the preconditioner's tensor-core products
+  bool rinv = false;  // Rhat^-1 applied as one product with the explicit inverse
   // WC4D_COV_MSOAR: banded circulant B and Q, applied through their taps
   bool band = false;
   double *bandB = nullptr, *bandQ = nullptr;  // device, 2 mv + 1 taps each
@@ -519,6 +521,50 @@ static void apply_PD(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   const bool exactS = (P->o.shat == WC4D_SHAT_EXACT);
   if (!exactS) lhat_sweep<T>(P->md, k, v3, y3, true, ident, done, P->st);
   if constexpr (sizeof(T) == 8) {
+    if (P->rinv && !exactS) {
+      // Rhat^-1 v2 as one product with the explicit inverse
+      GemmOpsT<T> ops{};
+      EpisT<T> ep{};
+      ops.ndig = P->pdig;
+      ops.op[0] = {os.Rinv, p, v2, p, p, p, N + 1, TRI_FULL};
+      ep.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
+      if (P->circ) {
+        ops.nops = 1;
+        os.attach(ops, P->st);
+        gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+        CircJobs cj{};
+        circ_add(cj, CircJob{v1, s, 1, P->lamBi, EPI_STORE, o1, s, 0, nullptr, nullptr});
+        if (N > 0) circ_add(cj, CircJob{v1 + s, s, N, P->lamQi, EPI_STORE, o1 + s, s, 0, nullptr, nullptr});
+        circ_add(cj, CircJob{y3, s, 1, P->lamB, EPI_STORE, u3, s, 0, nullptr, nullptr});
+        if (N > 0) circ_add(cj, CircJob{y3 + s, s, N, P->lamQ, EPI_STORE, u3 + s, s, 0, nullptr, nullptr});
+        run_circ(P, cj, done);
+      } else {
+        ops.nops = 4;
+        ops.op[1] = {os.WBt, s, v1, s, s, s, 1, TRI_LOWER};
+        ops.op[2] = {os.WQt, s, v1 + s, s, s, s, N, TRI_LOWER};
+        ops.op[3] = {os.Q, s, y3 + s, s, s, s, N, TRI_FULL};
+        ep.e[1] = {EPI_STORE, y1, s, 0, nullptr, nullptr};
+        ep.e[2] = {EPI_STORE, y1 + s, s, 0, nullptr, nullptr};
+        ep.e[3] = {EPI_STORE, u3 + s, s, 0, nullptr, nullptr};
+        os.attach(ops, P->st);
+        gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+        GemmOpsT<T> ops2{};
+        EpisT<T> ep2{};
+        ops2.nops = 3;
+        ops2.ndig = P->pdig;
+        ops2.op[0] = {os.WB, s, y1, s, s, s, 1, TRI_UPPER};
+        ops2.op[1] = {os.WQ, s, y1 + s, s, s, s, N, TRI_UPPER};
+        ops2.op[2] = {os.B, s, y3, s, s, s, 1, TRI_FULL};
+        ep2.e[0] = {EPI_STORE, o1, s, 0, nullptr, nullptr};
+        ep2.e[1] = {EPI_STORE, o1 + s, s, 0, nullptr, nullptr};
+        ep2.e[2] = {EPI_STORE, u3, s, 0, nullptr, nullptr};
+        os.attach(ops2, P->st);
+        gemm_run<T>(p2, ops2, ep2, os.partial, P->md, P->d_obs, done, P->st);
+      }
+      lhat_sweep<T>(P->md, k, u3, o3, false, ident, done, P->st);
+      if (P->net_on) learned_block(P, o3);
+      return;
+    }
     if (P->pertime) {
       // Rhat_t^{-1} v2_t = W_t^T (W_t v2_t) per time level; D parts as usual
       PtProd pr{};
@@ -669,6 +715,28 @@ static void apply_PI(wc4d_problem* P, OpSet<T>& os, const GemmPlan& p1, const Ge
   const bool ident = (P->o.lhat == WC4D_LHAT_I);
   lhat_sweep<T>(P->md, k, v3, o1, true, ident, done, P->st);
   if constexpr (sizeof(T) == 8) {
+    if (P->rinv) {
+      // Rhat^-1 v2 as one product with the explicit inverse, in the launch of D c1
+      GemmOpsT<T> ops{};
+      EpisT<T> ep{};
+      ops.ndig = P->pdig;
+      ops.op[0] = {os.Rinv, p, v2, p, p, p, N + 1, TRI_FULL};
+      ep.e[0] = {EPI_STORE, o2, p, 0, nullptr, nullptr};
+      if (P->circ || P->band) {
+        ops.nops = 1;
+      } else {
+        ops.nops = 3;
+        ops.op[1] = {os.B, s, o1, s, s, s, 1, TRI_FULL};
+        ops.op[2] = {os.Q, s, o1 + s, s, s, s, N, TRI_FULL};
+        ep.e[1] = {EPI_SUB_FROM, u, s, 0, nullptr, v1};
+        ep.e[2] = {EPI_SUB_FROM, u + s, s, 0, nullptr, v1 + s};
+      }
+      os.attach(ops, P->st);
+      gemm_run<T>(p1, ops, ep, os.partial, P->md, P->d_obs, done, P->st);
+      if (P->circ || P->band) d_offpath(P, o1, EPI_SUB_FROM, u, nullptr, v1, nullptr, nullptr, done);
+      lhat_sweep<T>(P->md, k, u, o3, false, ident, done, P->st);
+      return;
+    }
     if (P->pertime) {
       PtProd pr{};
       pr.A = P->ptWt;
@@ -784,15 +852,15 @@ static void factor_inverse(wc4d_problem* P, double* A, int m, double* W, double*
 
 // single-op GEMM C = op(At) X with a throwaway plan
 static void gemm_once(wc4d_problem* P, const double* At, int64_t lda, const double* X, int64_t ldx, int m, int kdim,
-                      int ncols, double* C, int64_t ldc, int mode) {
+                      int ncols, double* C, int64_t ldc, int mode, int tri = TRI_FULL) {
   GemmPlan plan;
-  plan_build(plan, {OpShape{m, kdim, ncols, TRI_FULL}}, max_gemm_ctas());
+  plan_build(plan, {OpShape{m, kdim, ncols, tri}}, max_gemm_ctas());
   double* partial = nullptr;
   WC4D_CUDA(cudaMalloc(&partial, sizeof(double) * (size_t)std::max(1, plan.nslots) * GEMM_BM * GEMM_BN));
   GemmOps ops{};
   Epis ep{};
   ops.nops = 1;
-  ops.op[0] = {At, lda, X, ldx, m, kdim, ncols, TRI_FULL};
+  ops.op[0] = {At, lda, X, ldx, m, kdim, ncols, tri};
   ep.e[0] = {mode, C, ldc, 0, nullptr, nullptr};
   gemm_run<double>(plan, ops, ep, partial, P->md, P->d_obs, nullptr, P->st);
   WC4D_CUDA(cudaStreamSynchronize(P->st));
@@ -1083,6 +1151,11 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
              "inner_iters must lie in [1, 200]");
   WC4D_CHECK(o->covprod == WC4D_COVPROD_DENSE || o->covprod == WC4D_COVPROD_FFT, WC4D_ERR_ARG, "bad covprod");
   WC4D_CHECK(o->prec_digits >= 0 && o->prec_digits <= 7, WC4D_ERR_ARG, "prec_digits must lie in [0, 7]");
+  WC4D_CHECK(o->rinv_explicit == 0 || o->rinv_explicit == 1, WC4D_ERR_ARG, "rinv_explicit must be 0 or 1");
+  WC4D_CHECK(!o->rinv_explicit || (d->p_t == nullptr && o->precision != WC4D_PREC_MIXED &&
+                                   o->precision != WC4D_PREC_DF32_P32 && o->shat != WC4D_SHAT_EXACT),
+             WC4D_ERR_ARG,
+             "rinv_explicit needs one observation set, precision FP64, DF32 or OZAKI and shat PAPER or LEARNED");
   WC4D_CHECK(o->prec_digits == 0 || o->prec_digits == 7 ||
                  (o->precision == WC4D_PREC_OZAKI && o->krylov == WC4D_KRYLOV_GMRES),
              WC4D_ERR_ARG,
@@ -1111,6 +1184,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->N = N;
   P->p = p;
   P->pertime = (d->p_t != nullptr);
+  P->rinv = (o->rinv_explicit != 0);
   P->pdig = (o->precision == WC4D_PREC_OZAKI && o->prec_digits >= 1 && o->prec_digits <= 7) ? o->prec_digits : 7;
   P->ns = (int64_t)(N + 1) * s;
   P->np = P->pertime ? (int64_t)p : (int64_t)(N + 1) * p;  // per-time: p = sum of p_t
@@ -1350,6 +1424,12 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   f.WRt = P->alloc<double>((int64_t)p * p);
   launch_copy_d(work, P->d_Rhat, (int64_t)p * p, st);
   factor_inverse(P, work, p, f.WR, f.WRt, scratch, "Rhat");
+  if (P->rinv) {
+    // Rhat^-1 = W^T W (W = chol(Rhat)^-1 lower: row i of W^T meets k >= i only)
+    f.Rinv = P->alloc<double>((int64_t)p * p);
+    gemm_once(P, f.WR, p, f.WR, p, p, p, p, f.Rinv, p, EPI_STORE, TRI_UPPER);
+    launch_symmetrize(f.Rinv, p, st);
+  }
   }
   // Dhat factors (P_D only)
   P->have_pd = (o->precond == WC4D_PRECOND_PD);
@@ -1408,12 +1488,22 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   } else if (P->circ || P->band) {
     // only the R family remains on the product path
     plan_build(P->plan_A, {{p, p, N + 1, TRI_FULL}}, C, cm);
+    const int t1 = P->rinv ? TRI_FULL : TRI_LOWER;
     if (P->have_pd) {
-      plan_build(P->plan_pd1, {{p, p, N + 1, TRI_LOWER}}, C, cm);
-      plan_build(P->plan_pd2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
+      plan_build(P->plan_pd1, {{p, p, N + 1, t1}}, C, cm);
+      if (!P->rinv) plan_build(P->plan_pd2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
     }
-    plan_build(P->plan_pi1, {{p, p, N + 1, TRI_LOWER}}, C, cm);
-    plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
+    plan_build(P->plan_pi1, {{p, p, N + 1, t1}}, C, cm);
+    if (!P->rinv) plan_build(P->plan_pi2, {{p, p, N + 1, TRI_UPPER}}, C, cm);
+  } else if (P->rinv) {
+    // Rhat^-1 as one full product, in the first launch of each preconditioner
+    plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}, {p, p, N + 1, TRI_FULL}}, C, cm);
+    if (P->have_pd) {
+      plan_build(P->plan_pd1, {{p, p, N + 1, TRI_FULL}, {s, s, 1, TRI_LOWER}, {s, s, N, TRI_LOWER},
+                               {s, s, N, TRI_FULL}}, C, cm);
+      plan_build(P->plan_pd2, {{s, s, 1, TRI_UPPER}, {s, s, N, TRI_UPPER}, {s, s, 1, TRI_FULL}}, C, cm);
+    }
+    plan_build(P->plan_pi1, {{p, p, N + 1, TRI_FULL}, {s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}}, C, cm);
   } else {
   plan_build(P->plan_A, {{s, s, 1, TRI_FULL}, {s, s, N, TRI_FULL}, {p, p, N + 1, TRI_FULL}}, C, cm);
   if (P->have_pd) {
@@ -1458,6 +1548,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       add(f.Q, (int64_t)s * s);
     }
     add(f.R, (int64_t)p * p);
+    add(f.Rinv, (int64_t)p * p);
     add(f.WR, (int64_t)p * p);
     add(f.WRt, (int64_t)p * p);
     add(f.WB, (int64_t)s * s);
@@ -1488,6 +1579,7 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
     }
     if (N + 1 >= 2) {
       dig(f.R, p);
+      dig(f.Rinv, p);
       dig(f.WR, p);
       dig(f.WRt, p);
     }

@@ -92,7 +92,7 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("lhat", ctypes.c_int32), ("rblock_count", ctypes.c_int32),
                 ("rblock_sizes", ctypes.POINTER(ctypes.c_int32)), ("rblock_tol", ctypes.c_double),
                 ("rblock_maxsize", ctypes.c_int32), ("rblock_numproc", ctypes.c_int32),
-                ("covprod", ctypes.c_int32), ("prec_digits", ctypes.c_int32)]
+                ("covprod", ctypes.c_int32), ("prec_digits", ctypes.c_int32), ("rinv_explicit", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -402,7 +402,7 @@ def wc4d_last_error() -> str:
 # -------------------------------------------------------------- convenience
 def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dhat="exact", dhat_delta=0.01,
               krylov=None, tol=1e-6, maxit=1000, precision="fp64", inner_iters=20, check_every=4, lhat="lm",
-              rblock=None, covprod="dense", prec_digits=0) -> SolveOpts:
+              rblock=None, covprod="dense", prec_digits=0, rinv_explicit=False) -> SolveOpts:
     """``rblock`` = (channel block sizes, tol, maxsize, numproc) for rhat="block"
     (Alg. 3; maxsize / numproc None or 0 switch their rule off)."""
     o = wc4d_default_opts()
@@ -434,6 +434,7 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
     o.check_every = int(check_every)
     o.covprod = {"dense": WC4D_COVPROD_DENSE, "fft": WC4D_COVPROD_FFT}[covprod]
     o.prec_digits = int(prec_digits)
+    o.rinv_explicit = int(bool(rinv_explicit))
     return o
 
 

@@ -633,3 +633,55 @@ def test_product_counts_follow_tables_4_5(kind, krylov, k, lhat):
     # the ratios Tables 4 and 5 print: D_i = 2 R_i per iteration, Dhat^-1 = R_i for P_D, none for P_I
     assert perP["D"] == perA["R"] and (perP["Dh"] == T if kind == "PD" else perP["Dh"] == 0)
     G.close()
+
+
+@pytest.mark.parametrize("kind,precision,covprod", [("PI", "fp64", "dense"), ("PD", "fp64", "dense"),
+                                                    ("PI", "ozaki", "dense"), ("PD", "df32", "fft"),
+                                                    ("PI", "ozaki", "fft")])
+def test_explicit_rhat_inverse(kind, precision, covprod):
+    """rinv_explicit (not in the paper): Rhat^-1 = W^T W formed once at setup
+    and applied as one product.  P^-1 v within 1e-9 of the oracle (as the
+    factor pair), the solve within 1e-8 of LU in FP64 mode (1e-6 with the
+    OZAKI products) in the factor pair's iteration count (+-2)."""
+    w, dr = case(128, 6, 48, "random", seed=9)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    krylov = "minres" if kind == "PD" else "gmres"
+    o = dict(precond=kind, k=3, krylov=krylov, precision=precision, covprod=covprod, tol=1e-11, maxit=2000)
+    G = L.Problem.from_workload(w, dr, L.make_opts(rinv_explicit=True, **o))
+    F = L.Problem.from_workload(w, dr, L.make_opts(**o))
+    v = W.random_vector(prob.n, 12)
+    P = sd.Preconditioner(prob, popts(kind, 3))
+    assert rel(G.apply_precond(kind, to_dev(v)).cpu().numpy(), P.apply(v)) < 1e-9
+    x_lu = sd.dense_solve(prob, rhs)
+    x, info = G.solve(to_dev(rhs))
+    _, info_f = F.solve(to_dev(rhs))
+    assert info.status == 0 and abs(info.iters - info_f.iters) <= 2, (info.iters, info_f.iters)
+    assert rel(x.cpu().numpy(), x_lu) < (1e-8 if precision == "fp64" else 1e-6)
+    G.close()
+    F.close()
+
+
+@pytest.mark.slow
+def test_explicit_rhat_inverse_scale_window():
+    """At the scale window (kappa(R) = 2.6e9): P_I^{-1} v within 1e-7 of the
+    oracle (the factor pair's bound, kappa(R) eps), and the OZAKI P_I + GMRES
+    solve reaches 1e-6 with the oracle's operator in the factor pair's count
+    (+-2, 5 %)."""
+    w = W.SCALE
+    dr = W.draws(w, 0)
+    prob, obs, rhs = prb.linear_case(w, dr)
+    its = {}
+    for flag in (True, False):
+        G = L.Problem.from_workload(w, dr, L.make_opts(precond="PI", k=4, precision="ozaki", tol=1e-6, maxit=1000,
+                                                       rinv_explicit=flag))
+        if flag:
+            v = W.random_vector(prob.n, 13)
+            P = sd.Preconditioner(prob, popts("PI", 4))
+            assert rel(G.apply_precond("PI", to_dev(v)).cpu().numpy(), P.apply(v)) < 1e-7
+        x, info = G.solve(to_dev(rhs))
+        assert info.status == 0
+        r = rhs - prob.A_apply(x.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(rhs) <= 1e-6
+        its[flag] = info.iters
+        G.close()
+    assert abs(its[True] - its[False]) <= 2 + 0.05 * its[False], its
