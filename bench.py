@@ -53,10 +53,12 @@ def parse():
     ap.add_argument("--maxit", type=int, default=1000, help="Krylov iteration cap (workspace size)")
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
-    ap.add_argument("--chosen", default="ozaki", choices=["fp64", "df32", "df32p32", "mixed", "ozaki", "fp64_fft",
+    ap.add_argument("--chosen", default="ozaki_rinv", choices=["fp64", "df32", "df32p32", "mixed", "ozaki", "fp64_fft",
                                                           "df32_fft", "ozaki_fft", "ozaki_rinv"])
     ap.add_argument("--precision", default="ozaki", choices=["df32", "ozaki"],
                     help="product precision of the batched and learned workloads")
+    ap.add_argument("--rinv", action="store_true",
+                    help="batched workload: Rhat^-1 as one product with the explicit inverse")
     ap.add_argument("--modes", default=None, help="comma list of modes to time (default: fp64,chosen)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-comparisons", action="store_true",
@@ -651,7 +653,7 @@ def run_batch(args):
     if world > 1:
         torch.distributed.init_process_group("nccl")
     opts = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6, maxit=args.batch_maxit,
-                          precision=args.precision, check_every=args.check_every)
+                          precision=args.precision, check_every=args.check_every, rinv_explicit=args.rinv)
     t0 = time.perf_counter()
     probs, rhs, meta = build_batch(args, wc4d, W, opts)
     torch.cuda.synchronize()
@@ -859,11 +861,12 @@ def run_profile(args):
     torch.cuda.set_device(0)
     w = W.SCALE
     dr = W.draws(w, args.seed)
-    base = args.chosen.replace("_fft", "")
+    base = args.chosen.replace("_fft", "").replace("_rinv", "")
     o = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-30, maxit=args.maxit,
                        precision=base if base in ("fp64", "df32", "ozaki") else "ozaki",
                        covprod="fft" if args.chosen.endswith("_fft") else "dense",
-                       krylov="gmres" if args.precond == "PI" else "minres")
+                       krylov="gmres" if args.precond == "PI" else "minres",
+                       rinv_explicit=args.chosen.endswith("_rinv"))
     G = wc4d.Problem.from_workload(w, dr, o)
     v = torch.from_numpy(W.random_vector(w.n, 3)).cuda()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]

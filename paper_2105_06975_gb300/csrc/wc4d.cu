@@ -1424,8 +1424,9 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   f.WRt = P->alloc<double>((int64_t)p * p);
   launch_copy_d(work, P->d_Rhat, (int64_t)p * p, st);
   factor_inverse(P, work, p, f.WR, f.WRt, scratch, "Rhat");
-  if (P->rinv) {
-    // Rhat^-1 = W^T W (W = chol(Rhat)^-1 lower: row i of W^T meets k >= i only)
+  if (P->rinv && o->precision == WC4D_PREC_FP64) {
+    // Rhat^-1 = W^T W (W = chol(Rhat)^-1 lower: row i of W^T meets k >= i only);
+    // the double-float modes form it below from W's split
     f.Rinv = P->alloc<double>((int64_t)p * p);
     gemm_once(P, f.WR, p, f.WR, p, p, p, p, f.Rinv, p, EPI_STORE, TRI_UPPER);
     launch_symmetrize(f.Rinv, p, st);
@@ -1548,9 +1549,30 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       add(f.Q, (int64_t)s * s);
     }
     add(f.R, (int64_t)p * p);
-    add(f.Rinv, (int64_t)p * p);
     add(f.WR, (int64_t)p * p);
     add(f.WRt, (int64_t)p * p);
+    if (P->rinv) {
+      // Rhat^-1 = W^T W as a double-float product on the FP32 pipe, both
+      // operands W's split (X = W with leading dimension p)
+      f.Rinv = P->alloc<double>((int64_t)p * p);
+      const Split sw = f.split_of(f.WR);
+      GemmPlan plan;
+      plan_build(plan, {OpShape{p, p, p, TRI_UPPER}}, max_gemm_ctas(true), COST_DF32);
+      double* part = P->alloc<double>((int64_t)std::max(1, plan.nslots) * GEMM_BM * GEMM_BN);
+      GemmOps ops{};
+      Epis ep{};
+      ops.nops = 1;
+      ops.df32 = 1;
+      ops.op[0] = {f.WR, p, f.WR, p, p, p, p, TRI_UPPER};
+      ops.op[0].Ah = sw.h;
+      ops.op[0].Al = sw.l;
+      ops.op[0].Xh = sw.h;
+      ops.op[0].Xl = sw.l;
+      ep.e[0] = {EPI_STORE, f.Rinv, p, 0, nullptr, nullptr};
+      gemm_run<double>(plan, ops, ep, part, P->md, P->d_obs, nullptr, st);
+      launch_symmetrize(f.Rinv, p, st);
+      add(f.Rinv, (int64_t)p * p);
+    }
     add(f.WB, (int64_t)s * s);
     add(f.WBt, (int64_t)s * s);
     add(f.WQ, (int64_t)s * s);
