@@ -707,11 +707,15 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
   const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
   const int gn = min(ORTH_G, cnt - i0);
   const bool first = blockIdx.y == 0;
-  // scalar double-float accumulators (the paired form needs more registers than
-  // three resident CTAs per SM allow, and the kernel is latency-bound)
+  // double-float accumulators: per basis vector one paired (against w, against
+  // u) accumulator, so one paired multiply-add (FFMA2 / FADD2: each lane rounds
+  // as its scalar form) serves both dot products of a basis entry, at the
+  // register count of the scalar form; w^T w in a scalar pair
+  float2 s2[ORTH_G], c2[ORTH_G];
   float s[2 * ORTH_G + 1], c[2 * ORTH_G + 1];
 #pragma unroll
-  for (int g = 0; g < 2 * ORTH_G + 1; ++g) s[g] = c[g] = 0.f;
+  for (int g = 0; g < ORTH_G; ++g) s2[g] = c2[g] = make_float2(0.f, 0.f);
+  s[2 * ORTH_G] = c[2 * ORTH_G] = 0.f;
   const float* uhp = Vh + (int64_t)j * ldv;
   const float* ulp = Vl + (int64_t)j * ldv;
   for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
@@ -724,14 +728,14 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
       if (g < gn) {
         const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
         const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
-        df_mac(s[g], c[g], a.x, b.x, xh.x, xl.x);
-        df_mac(s[g], c[g], a.y, b.y, xh.y, xl.y);
-        df_mac(s[g], c[g], a.z, b.z, xh.z, xl.z);
-        df_mac(s[g], c[g], a.w, b.w, xh.w, xl.w);
-        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.x, b.x, uh.x, ul.x);
-        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.y, b.y, uh.y, ul.y);
-        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.z, b.z, uh.z, ul.z);
-        df_mac(s[ORTH_G + g], c[ORTH_G + g], a.w, b.w, uh.w, ul.w);
+        df_mac2(s2[g], c2[g], make_float2(a.x, a.x), make_float2(b.x, b.x), make_float2(xh.x, uh.x),
+                make_float2(xl.x, ul.x));
+        df_mac2(s2[g], c2[g], make_float2(a.y, a.y), make_float2(b.y, b.y), make_float2(xh.y, uh.y),
+                make_float2(xl.y, ul.y));
+        df_mac2(s2[g], c2[g], make_float2(a.z, a.z), make_float2(b.z, b.z), make_float2(xh.z, uh.z),
+                make_float2(xl.z, ul.z));
+        df_mac2(s2[g], c2[g], make_float2(a.w, a.w), make_float2(b.w, b.w), make_float2(xh.w, uh.w),
+                make_float2(xl.w, ul.w));
       }
     }
     if (first) {
@@ -745,6 +749,13 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
   // vector would occupy GB300's 1/64-rate FP64 pipe for a large part of the
   // kernel); one FP64 conversion per warp and vector
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < ORTH_G; ++g) {
+    s[g] = s2[g].x;
+    c[g] = c2[g].x;
+    s[ORTH_G + g] = s2[g].y;
+    c[ORTH_G + g] = c2[g].y;
+  }
 #pragma unroll
   for (int g = 0; g < 2 * ORTH_G + 1; ++g) {
     const float2 v = df_warp_sum(s[g], c[g]);
