@@ -692,7 +692,7 @@ void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done,
 // where Z holds the computed P^-1 q_j).
 
 // part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w
-__global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* __restrict__ Vh,
+__global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __restrict__ Vh,
                                                                 const float* __restrict__ Vl, int64_t ldv, int j,
                                                                 const float* __restrict__ wh,
                                                                 const float* __restrict__ wl, int64_t n4,
@@ -702,20 +702,20 @@ __global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* 
   pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   if (ran != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ran = 1;
-  __shared__ float2 sh[DOT_THREADS / 32][2 * DC_G + 1];
+  __shared__ float2 sh[DOT_THREADS / 32][2 * ORTH_G + 1];
   const int cnt = j + 1;
-  const int chunk = blockIdx.x, i0 = blockIdx.y * DC_G;
-  const int gn = min(DC_G, cnt - i0);
+  const int chunk = blockIdx.x, i0 = blockIdx.y * ORTH_G;
+  const int gn = min(ORTH_G, cnt - i0);
   const bool first = blockIdx.y == 0;
   // double-float accumulators: per basis vector one paired (against w, against
   // u) accumulator, so one paired multiply-add (FFMA2 / FADD2: each lane rounds
   // as its scalar form) serves both dot products of a basis entry, at the
   // register count of the scalar form; w^T w in a scalar pair
-  float2 s2[DC_G], c2[DC_G];
-  float s[2 * DC_G + 1], c[2 * DC_G + 1];
+  float2 s2[ORTH_G], c2[ORTH_G];
+  float s[2 * ORTH_G + 1], c[2 * ORTH_G + 1];
 #pragma unroll
-  for (int g = 0; g < DC_G; ++g) s2[g] = c2[g] = make_float2(0.f, 0.f);
-  s[2 * DC_G] = c[2 * DC_G] = 0.f;
+  for (int g = 0; g < ORTH_G; ++g) s2[g] = c2[g] = make_float2(0.f, 0.f);
+  s[2 * ORTH_G] = c[2 * ORTH_G] = 0.f;
   const float* uhp = Vh + (int64_t)j * ldv;
   const float* ulp = Vl + (int64_t)j * ldv;
   for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* 
     const float4 uh = reinterpret_cast<const float4*>(uhp)[q];
     const float4 ul = reinterpret_cast<const float4*>(ulp)[q];
 #pragma unroll
-    for (int g = 0; g < DC_G; ++g) {
+    for (int g = 0; g < ORTH_G; ++g) {
       if (g < gn) {
         const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
         const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
@@ -739,10 +739,10 @@ __global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* 
       }
     }
     if (first) {
-      df_mac(s[2 * DC_G], c[2 * DC_G], xh.x, xl.x, xh.x, xl.x);
-      df_mac(s[2 * DC_G], c[2 * DC_G], xh.y, xl.y, xh.y, xl.y);
-      df_mac(s[2 * DC_G], c[2 * DC_G], xh.z, xl.z, xh.z, xl.z);
-      df_mac(s[2 * DC_G], c[2 * DC_G], xh.w, xl.w, xh.w, xl.w);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.x, xl.x, xh.x, xl.x);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.y, xl.y, xh.y, xl.y);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.z, xl.z, xh.z, xl.z);
+      df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.w, xl.w, xh.w, xl.w);
     }
   }
   // warp reduction in double-float on the FP32 pipe (an FP64 shuffle tree per
@@ -750,28 +750,28 @@ __global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* 
   // kernel); one FP64 conversion per warp and vector
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int g = 0; g < DC_G; ++g) {
+  for (int g = 0; g < ORTH_G; ++g) {
     s[g] = s2[g].x;
     c[g] = c2[g].x;
-    s[DC_G + g] = s2[g].y;
-    c[DC_G + g] = c2[g].y;
+    s[ORTH_G + g] = s2[g].y;
+    c[ORTH_G + g] = c2[g].y;
   }
 #pragma unroll
-  for (int g = 0; g < 2 * DC_G + 1; ++g) {
+  for (int g = 0; g < 2 * ORTH_G + 1; ++g) {
     const float2 v = df_warp_sum(s[g], c[g]);
     if (lane == 0) sh[wid][g] = v;
   }
   __syncthreads();
-  const int r = threadIdx.x;  // threads 0..2*DC_G of warp 0: one FP64 conversion each
-  if (r < 2 * DC_G + 1) {
+  const int r = threadIdx.x;  // threads 0..2*ORTH_G of warp 0: one FP64 conversion each
+  if (r < 2 * ORTH_G + 1) {
     float2 a2 = sh[0][r];
     for (int k = 1; k < DOT_THREADS / 32; ++k) a2 = df_add(a2, sh[k][r]);
     const double v = (double)a2.x + (double)a2.y;
     int row = -1;
-    if (r < DC_G) {
+    if (r < ORTH_G) {
       if (r < gn) row = i0 + r;
-    } else if (r < 2 * DC_G) {
-      if (r - DC_G < gn) row = cnt + i0 + r - DC_G;
+    } else if (r < 2 * ORTH_G) {
+      if (r - ORTH_G < gn) row = cnt + i0 + r - ORTH_G;
     } else if (first) {
       row = 2 * cnt;
     }
@@ -782,7 +782,7 @@ void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float
                double* part, const int* done, cudaStream_t st) {
   int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st);
   const int64_t n4 = (n + 3) / 4;
-  dim3 grid((unsigned)dc_dot_chunks(n, j + 1), (j + 1 + DC_G - 1) / DC_G);
+  dim3 grid((unsigned)dot_chunks(n, j + 1), (j + 1 + ORTH_G - 1) / ORTH_G);
   WC4D_CUDA(launch_pdl(gm_dc_dot_kernel, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done, ran));
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);

@@ -24,17 +24,6 @@ inline int dot_chunks(int64_t n, int cnt) {
   return c < 1 ? 1 : (c > maxc ? maxc : c);
 }
 
-// The delayed-CGS2 dot pass reads DC_G basis vectors per CTA (twice the
-// CGS2 kernels' group: fewer re-reads of w and u, longer contiguous streams
-// per CTA), two CTAs per SM resident, the grid rounded down to one wave.
-constexpr int DC_G = 8;
-inline int dc_dot_chunks(int64_t n, int cnt) {
-  const int maxc = orth_chunks(n);
-  const int groups = (cnt + DC_G - 1) / DC_G;
-  int c = (152 * 2) / groups;
-  return c < 1 ? 1 : (c > maxc ? maxc : c);
-}
-
 struct DevStatus {
   int done;
   int status;
