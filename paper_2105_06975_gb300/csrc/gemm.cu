@@ -548,7 +548,7 @@ struct ReduceMeta {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) gemm_reduce_kernel(ReduceMeta meta, EpisT<T> epis, const T* __restrict__ partial,
+__global__ void __launch_bounds__(256, 6) gemm_reduce_kernel(ReduceMeta meta, EpisT<T> epis, const T* __restrict__ partial,
                                                           const int* __restrict__ tile_start,
                                                           const int* __restrict__ tile_slots, ModelDev md,
                                                           const int* __restrict__ obs, const int* __restrict__ done) {
@@ -684,6 +684,20 @@ void launch_products<double>(const GemmPlan& plan, const GemmOpsT<double>& ops, 
   if (ran) prof_end(st);
 }
 
+// resident CTAs of the reduction kernel (all SMs)
+template <typename T>
+static int reduce_resident_ctas() {
+  static std::atomic<int> cached{0};  // one per instance; host threads may race to fill it, all with the same value
+  if (const int c = cached.load(std::memory_order_relaxed)) return c;
+  int dev = 0, sms = 0, per = 0;
+  WC4D_CUDA(cudaGetDevice(&dev));
+  WC4D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gemm_reduce_kernel<T>, 256, 0));
+  const int c = std::max(1, sms * std::max(1, per));
+  cached.store(c, std::memory_order_relaxed);
+  return c;
+}
+
 template <typename T>
 void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis, T* partial, const ModelDev& model,
               const int* obs, const int* done, cudaStream_t st) {
@@ -704,7 +718,9 @@ void gemm_run(const GemmPlan& plan, const GemmOpsT<T>& ops, const EpisT<T>& epis
   meta.bm = plan.bm;
   WC4D_CHECK(plan.bm == GEMM_BM || (sizeof(T) == 8 && ops.tc), WC4D_ERR_ARG,
              "internal: tensor-core plan run without the tensor-core operands");
-  const int64_t nb = std::min<int64_t>((plan.total_out + 255) / 256, 152 * 8);
+  // at most one resident wave (six 256-thread CTAs per SM): a few CTAs past it
+  // would run as a second wave of their own and nearly double the launch
+  const int64_t nb = std::min<int64_t>((plan.total_out + 255) / 256, reduce_resident_ctas<T>());
   WC4D_CUDA(launch_pdl(gemm_reduce_kernel<T>, dim3((unsigned)nb), dim3(256), 0, st, meta, epis, (const T*)partial,
                        (const int*)plan.d_tile_start, (const int*)plan.d_tile_slots, model, obs, done));
   WC4D_LAUNCH_CHECK();

@@ -160,8 +160,10 @@ __global__ void __launch_bounds__(128) oz_rows_kernel(const double* __restrict__
   write_digits(row, kdim, nkb, emax, Ad + (int64_t)rt * nkb * OZ_DIGITS * OZ_A_TILE, OZ_A_TILE, r);
 }
 
-// one CTA per (op, wide column tile, column of the tile), and one per op for
-// the double-float split of its one-column (GEMV) column
+// one CTA per (op, wide column tile, column of the tile), and ceil(kdim / 128)
+// per op for the double-float split of its one-column (GEMV) column, one entry
+// per thread (the split's FP64 subtraction and conversions run on the FP64
+// pipe: one CTA over the whole column was the launch's long pole)
 __global__ void __launch_bounds__(128) oz_cols_kernel(OzColJobs jobs) {
   __shared__ uint64_t red[4];
   pdl_wait();
@@ -171,9 +173,9 @@ __global__ void __launch_bounds__(128) oz_cols_kernel(OzColJobs jobs) {
   const OzColJob& jb = jobs.j[o];
   const int local = (int)blockIdx.x - jobs.cta_base[o];
   if (local >= jb.wide * OZ_BN) {
-    const double* xc = jb.X + (int64_t)jb.gemv_col * jb.ldx;
-    for (int k = threadIdx.x; k < jb.kdim; k += blockDim.x) {
-      const double x = xc[k];
+    const int k = (local - jb.wide * OZ_BN) * (int)blockDim.x + (int)threadIdx.x;
+    if (k < jb.kdim) {
+      const double x = jb.X[(int64_t)jb.gemv_col * jb.ldx + k];
       const float h = __double2float_rn(x);
       jb.Xgh[k] = h;
       jb.Xgl[k] = __double2float_rn(x - (double)h);

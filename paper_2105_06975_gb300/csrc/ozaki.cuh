@@ -29,7 +29,7 @@ struct OzColJob {
 };
 struct OzColJobs {
   OzColJob j[GEMM_MAX_OPS];
-  int cta_base[GEMM_MAX_OPS + 1];  // wide * 64 CTAs per op, + 1 with a GEMV column
+  int cta_base[GEMM_MAX_OPS + 1];  // wide * 64 CTAs per op, + oz_gemv_ctas(kdim) with a GEMV column
   int n;
 };
 
@@ -41,6 +41,8 @@ inline int oz_gemv_col(int ncols) {
   return -1;
 }
 
+// CTAs of the digit kernel that split an op's GEMV column (128 entries each)
+inline int oz_gemv_ctas(int kdim) { return (kdim + 127) / 128; }
 // column tiles of an op that run on the tensor cores (width >= 2)
 int oz_wide_tiles(int ncols);
 // BF16 elements of an operator's digit tiles (rows padded to 128, k to 16)

@@ -137,7 +137,7 @@ struct OpSet {
         }
         jobs.cta_base[jobs.n] = ctas;
         ++jobs.n;
-        ctas += wide * OZ_BN + (gcol >= 0 ? 1 : 0);
+        ctas += wide * OZ_BN + (gcol >= 0 ? oz_gemv_ctas(op.kdim) : 0);
       }
       jobs.cta_base[jobs.n] = ctas;
       launch_oz_cols(jobs, st);
