@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--maxit", type=int, default=1000, help="Krylov iteration cap (workspace size)")
     ap.add_argument("--inner", type=int, default=20, help="inner FP32 GMRES steps per outer FGMRES step")
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
-    ap.add_argument("--chosen", default="ozaki_rinv", choices=["fp64", "df32", "df32p32", "mixed", "ozaki", "fp64_fft",
-                                                          "df32_fft", "ozaki_fft", "ozaki_rinv"])
+    ap.add_argument("--chosen", default="ozaki_rinv_b6", choices=["fp64", "df32", "df32p32", "mixed", "ozaki", "fp64_fft",
+                                                          "df32_fft", "ozaki_fft", "ozaki_rinv",
+                                                          "ozaki_rinv_b6"])
     ap.add_argument("--precision", default="ozaki", choices=["df32", "ozaki"],
                     help="product precision of the batched and learned workloads")
     ap.add_argument("--rinv", action="store_true",
@@ -247,7 +248,9 @@ MODE_DTYPE = {"fp64": "f64", "df32": "df32 products (2 x f32, ~48-bit) / f64 rec
               "df32_fft": "f64 FFT for B, Q; df32 R-family products / f64 recurrences",
               "ozaki_fft": "f64 FFT for B, Q; bf16 digit products exact in f32 for the R family / df32 / f64 "
                            "recurrences",
-              "ozaki_rinv": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / df32 / f64 recurrences"}
+              "ozaki_rinv": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / df32 / f64 recurrences",
+              "ozaki_rinv_b6": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / f32+bf16 Arnoldi "
+                               "basis / f64 recurrences"}
 MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
              "df32": "FP64 GMRES; covariance / factor products in double-float on the FP32 pipe",
              "ozaki": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
@@ -261,7 +264,10 @@ MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
                           "products on tcgen05",
              "ozaki_rinv": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products on "
                            "tcgen05; Rhat^-1 as one product with the explicit inverse W^T W (in the launch of "
-                           "P_I's D c1)"}
+                           "P_I's D c1)",
+             "ozaki_rinv_b6": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
+                              "on tcgen05; Rhat^-1 as one product with the explicit inverse W^T W; Arnoldi basis "
+                              "stored as FP32 high + BF16 low parts (6 B per entry, about 32 bits)"}
 
 
 # DRAM bytes per launch of gemm_streamk_df32_kernel, ncu dram__bytes_read.sum + dram__bytes_write.sum,
@@ -369,7 +375,13 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                         "peak": hbm, "unit": "GB/s", "frac": (a / hbm) if hbm else None,
                         "launches": st.orth_launches, "ms_per_launch": st.orth_ms / st.orth_launches,
                         "bytes_per_launch": st.orth_bytes / st.orth_launches, "share_of_step": st.orth_ms / step_ms,
+                        "bytes": "FP64-equivalent: 8 B per basis entry read or written, w and v at 8 B",
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        if st.orth_moved_bytes and abs(st.orth_moved_bytes - st.orth_bytes) > 1e-6 * st.orth_bytes:
+            m = st.orth_moved_bytes / (st.orth_ms * 1e-3) / 1e9
+            rows["orth"]["moved"] = {"achieved_gbs": m, "frac": (m / hbm) if hbm else None,
+                                     "bytes_per_launch": st.orth_moved_bytes / st.orth_launches,
+                                     "bytes": "what the passes move: 6 B per basis entry (FP32 + BF16)"}
     return rows
 
 
@@ -403,6 +415,11 @@ def run_gpu(args):
     if args.chosen == "ozaki_rinv" or (args.modes and "ozaki_rinv" in args.modes.split(",")):
         modes["ozaki_rinv"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
                                              maxit=args.maxit, precision="ozaki", check_every=ce, rinv_explicit=True)
+    # the same with the 6-byte Arnoldi basis (a quarter fewer bytes in both basis passes)
+    if args.chosen == "ozaki_rinv_b6" or (args.modes and "ozaki_rinv_b6" in args.modes.split(",")):
+        modes["ozaki_rinv_b6"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
+                                                maxit=args.maxit, precision="ozaki", check_every=ce,
+                                                rinv_explicit=True, basis_bytes=6)
     # circulant B and Q applied by FFT (Sec. 6.1), the R family as in the base mode
     for m in ("fp64", "df32", "ozaki"):
         if args.chosen == m + "_fft" or (args.modes and m + "_fft" in args.modes.split(",")):
@@ -487,7 +504,7 @@ def run_gpu(args):
         assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
         results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
                          "kernels": kernel_rows(st, prof_ms, hbm, dcgs=mode in ("df32", "df32p32", "ozaki", "df32_fft",
-                                                                              "ozaki_fft", "ozaki_rinv")),
+                                                                              "ozaki_fft", "ozaki_rinv", "ozaki_rinv_b6")),
                          "profiled_ms_per_step": prof_ms / args.steps,
                          "setup_ms": statistics.mean(a for a, _ in split),
                          "solve_ms": statistics.mean(b for _, b in split)}
@@ -549,10 +566,14 @@ def run_gpu(args):
             roof["traffic_source"] = ("ncu dram bytes read+write per launch, mean of one GMRES step's three "
                                       "product launches (profiles/gemm_streamk_df32__advdiff_s2048_N64.md)")
         dom_key = next(k for k, r in ks.items() if r is dom)
-        if dom_key in TRAFFIC_RATIO and dom.get("bytes_per_launch"):
-            ratio, src = TRAFFIC_RATIO[dom_key]
-            roof["traffic"] = ratio * dom["bytes_per_launch"]
-            roof["traffic_source"] = src + "; scaled to this run's mean algorithmic bytes per launch"
+        # the 6-byte basis passes have their own capture, scaled by the bytes they move
+        tkey = dom_key + "_b6" if "moved" in dom else dom_key
+        if tkey in TRAFFIC_RATIO and dom.get("bytes_per_launch"):
+            ratio, src = TRAFFIC_RATIO[tkey]
+            base = dom["moved"]["bytes_per_launch"] if "moved" in dom else dom["bytes_per_launch"]
+            roof["traffic"] = ratio * base
+            roof["traffic_source"] = src + ("; scaled to this run's mean bytes moved per launch" if "moved" in dom
+                                            else "; scaled to this run's mean algorithmic bytes per launch")
     # whole-solve bound: the FP64-class products at the DF32 peak vs the Arnoldi and operator bytes at HBM
     st_c = chosen["stats"]
     solve_roof = None
@@ -861,12 +882,12 @@ def run_profile(args):
     torch.cuda.set_device(0)
     w = W.SCALE
     dr = W.draws(w, args.seed)
-    base = args.chosen.replace("_fft", "").replace("_rinv", "")
+    base = args.chosen.replace("_fft", "").replace("_rinv", "").replace("_b6", "")
     o = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-30, maxit=args.maxit,
                        precision=base if base in ("fp64", "df32", "ozaki") else "ozaki",
                        covprod="fft" if args.chosen.endswith("_fft") else "dense",
                        krylov="gmres" if args.precond == "PI" else "minres",
-                       rinv_explicit=args.chosen.endswith("_rinv"))
+                       rinv_explicit=("_rinv" in args.chosen), basis_bytes=6 if args.chosen.endswith("_b6") else 0)
     G = wc4d.Problem.from_workload(w, dr, o)
     v = torch.from_numpy(W.random_vector(w.n, 3)).cuda()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]

@@ -219,6 +219,13 @@ typedef struct {
                                 one dependency level less per preconditioner apply).  Needs one
                                 observation set, precision FP64, DF32 or OZAKI, shat PAPER or
                                 LEARNED (not in the paper)                                      */
+  int32_t basis_bytes;       /* DF32 / OZAKI GMRES: bytes per entry of the stored Arnoldi basis.
+                                0 or 8: double-float (FP32 high + FP32 low part, about 48
+                                significant bits); 6: FP32 high + BF16 low part (about 32 bits),
+                                a quarter fewer bytes in the two basis passes of every step.  The
+                                stored basis rounding bounds the attainable true residual near
+                                1e-9 relative: use 6 with tol >= 1e-7 (checked: WC4D_ERR_ARG
+                                otherwise).  Any other value is WC4D_ERR_ARG (not in the paper) */
 } wc4d_solve_opts;
 
 typedef struct {
@@ -497,6 +504,9 @@ typedef struct {
   double pt_ms, pt_bytes;           /* per-time R-family products: operator blocks (their triangle
                                        for factors) read once, vectors read and written             */
   int64_t pt_launches;
+  double orth_moved_bytes;          /* bytes the Arnoldi passes counted in orth_bytes actually move:
+                                       orth_bytes counts 8 B per basis entry (the FP64-equivalent
+                                       floor); with basis_bytes = 6 the passes move 6 B per entry   */
 } wc4d_stats;
 void wc4d_set_profiling(int32_t enable);
 void wc4d_reset_stats(void);

@@ -3,6 +3,8 @@
 // a fixed grid of DOT_BLOCKS blocks and warp-shuffle block reductions; the
 // partial sums are added in a fixed order by every consumer, so results are
 // bitwise reproducible run to run.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -665,6 +667,25 @@ __global__ void gm_split_kernel(const double* __restrict__ w, float* __restrict_
     wl[e] = __double2float_rn(x - (double)xh);
   }
 }
+// the first basis vector with BF16 low parts (the 6-byte basis)
+__global__ void gm_split_b6_kernel(const double* __restrict__ w, float* __restrict__ wh, uint16_t* __restrict__ wl,
+                                   int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[e];
+    const float xh = __double2float_rn(x);
+    wh[e] = xh;
+    wl[e] = __bfloat16_as_ushort(__float2bfloat16_rn(__double2float_rn(x - (double)xh)));
+  }
+}
+void gm_split_basis(const double* w, float* vh, float* vl, int64_t n, bool b6, cudaStream_t st) {
+  if (!b6) {
+    gm_split(w, vh, vl, n, nullptr, st);
+    return;
+  }
+  const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  gm_split_b6_kernel<<<nb, 256, 0, st>>>(w, vh, reinterpret_cast<uint16_t*>(vl), n);
+  WC4D_LAUNCH_CHECK();
+}
 void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done, cudaStream_t st) {
   const int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
   gm_split_kernel<<<nb, 256, 0, st>>>(w, wh, wl, n, done);
@@ -691,7 +712,33 @@ void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done,
 // rounding of the preconditioner never enters the residual (as in CGS2 GMRES,
 // where Z holds the computed P^-1 q_j).
 
+// Low parts of the split basis, four entries at a time: FP32 (8-byte basis
+// entries) or, with B6, BF16 (6-byte entries: the low-part array holds 16-bit
+// words with the same leading dimension in elements, so a column's low parts
+// take half the bytes).  off: first element of the column.
+template <bool B6>
+__device__ __forceinline__ float4 lo_load(const float* Vl, int64_t off, int64_t q) {
+  if constexpr (B6) {
+    const uint2 r = reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(Vl) + off)[q];
+    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u), __uint_as_float(r.y << 16),
+                       __uint_as_float(r.y & 0xFFFF0000u));
+  } else {
+    return reinterpret_cast<const float4*>(Vl + off)[q];
+  }
+}
+template <bool B6>
+__device__ __forceinline__ void lo_store(float* Vl, int64_t off, int64_t q, float4 v) {
+  if constexpr (B6) {
+    const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(v.x)), b = __bfloat16_as_ushort(__float2bfloat16_rn(v.y));
+    const uint32_t c = __bfloat16_as_ushort(__float2bfloat16_rn(v.z)), d = __bfloat16_as_ushort(__float2bfloat16_rn(v.w));
+    reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(Vl) + off)[q] = make_uint2(a | (b << 16), c | (d << 16));
+  } else {
+    reinterpret_cast<float4*>(Vl + off)[q] = v;
+  }
+}
+
 // part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w
+template <bool B6>
 __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __restrict__ Vh,
                                                                 const float* __restrict__ Vl, int64_t ldv, int j,
                                                                 const float* __restrict__ wh,
@@ -717,17 +764,16 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
   for (int g = 0; g < ORTH_G; ++g) s2[g] = c2[g] = make_float2(0.f, 0.f);
   s[2 * ORTH_G] = c[2 * ORTH_G] = 0.f;
   const float* uhp = Vh + (int64_t)j * ldv;
-  const float* ulp = Vl + (int64_t)j * ldv;
   for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
     const float4 xh = reinterpret_cast<const float4*>(wh)[q];
     const float4 xl = reinterpret_cast<const float4*>(wl)[q];
     const float4 uh = reinterpret_cast<const float4*>(uhp)[q];
-    const float4 ul = reinterpret_cast<const float4*>(ulp)[q];
+    const float4 ul = lo_load<B6>(Vl, (int64_t)j * ldv, q);
 #pragma unroll
     for (int g = 0; g < ORTH_G; ++g) {
       if (g < gn) {
         const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
-        const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)(i0 + g) * ldv)[q];
+        const float4 b = lo_load<B6>(Vl, (int64_t)(i0 + g) * ldv, q);
         df_mac2(s2[g], c2[g], make_float2(a.x, a.x), make_float2(b.x, b.x), make_float2(xh.x, uh.x),
                 make_float2(xl.x, ul.x));
         df_mac2(s2[g], c2[g], make_float2(a.y, a.y), make_float2(b.y, b.y), make_float2(xh.y, uh.y),
@@ -779,11 +825,17 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
   }
 }
 void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float* wh, const float* wl, int64_t n,
-               double* part, const int* done, cudaStream_t st) {
-  int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st);
+               double* part, const int* done, cudaStream_t st, bool b6) {
+  // profiled bytes: the FP64-equivalent 8 B per basis entry in both forms
+  int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st, b6 ? (double)(j + 2) * n * 6.0 + (double)n * 8.0 : 0.0);
   const int64_t n4 = (n + 3) / 4;
   dim3 grid((unsigned)dot_chunks(n, j + 1), (j + 1 + ORTH_G - 1) / ORTH_G);
-  WC4D_CUDA(launch_pdl(gm_dc_dot_kernel, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done, ran));
+  if (b6)
+    WC4D_CUDA(launch_pdl(gm_dc_dot_kernel<true>, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done,
+                         ran));
+  else
+    WC4D_CUDA(launch_pdl(gm_dc_dot_kernel<false>, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done,
+                         ran));
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
 }
@@ -1008,6 +1060,7 @@ void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cpr
 // 64-thread CTAs: one float4 row per thread, so the grid is n/256 small CTAs
 // that spread evenly over the SMs (256-thread CTAs left 2 or 3 per SM)
 constexpr int UPD_THREADS = 64;
+template <bool B6>
 __global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, float* Vl, int64_t ldv, int j,
                                                                    const double* __restrict__ e,
                                                                    const double* __restrict__ cv,
@@ -1049,9 +1102,7 @@ __global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, fl
   const double ialpha = dc[DC_IALPHA];
   const int64_t n4 = (n + 3) / 4;
   float* qh = Vh + (int64_t)j * ldv;
-  float* ql = Vl + (int64_t)j * ldv;
   float* nh = Vh + (int64_t)(j + 1) * ldv;
-  float* nl = Vl + (int64_t)(j + 1) * ldv;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
     // paired accumulators: [0] elements 0, 1 of the float4, [1] elements 2, 3
     float2 se[2], ce[2], sc[2], cc[2];
@@ -1066,7 +1117,7 @@ __global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, fl
 #pragma unroll
       for (int u = 0; u < UPD_G; ++u) {
         a[u] = reinterpret_cast<const float4*>(Vh + (int64_t)(i + u) * ldv)[q];
-        b[u] = reinterpret_cast<const float4*>(Vl + (int64_t)(i + u) * ldv)[q];
+        b[u] = lo_load<B6>(Vl, (int64_t)(i + u) * ldv, q);
       }
 #pragma unroll
       for (int u = 0; u < UPD_G; ++u) {
@@ -1082,7 +1133,7 @@ __global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, fl
     }
     for (; i < j; ++i) {
       const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)i * ldv)[q];
-      const float4 b = reinterpret_cast<const float4*>(Vl + (int64_t)i * ldv)[q];
+      const float4 b = lo_load<B6>(Vl, (int64_t)i * ldv, q);
       const float2 h1 = make_float2(eh[i], eh[i]), l1 = make_float2(el[i], el[i]);
       const float2 h2 = make_float2(ch[i], ch[i]), l2 = make_float2(cl[i], cl[i]);
       const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
@@ -1095,7 +1146,7 @@ __global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, fl
     const float se_s[4] = {se[0].x, se[0].y, se[1].x, se[1].y}, ce_s[4] = {ce[0].x, ce[0].y, ce[1].x, ce[1].y};
     const float sc_s[4] = {sc[0].x, sc[0].y, sc[1].x, sc[1].y}, cc_s[4] = {cc[0].x, cc[0].y, cc[1].x, cc[1].y};
     const float4 uh = reinterpret_cast<const float4*>(qh)[q];
-    const float4 ul = reinterpret_cast<const float4*>(ql)[q];
+    const float4 ul = lo_load<B6>(Vl, (int64_t)j * ldv, q);
     const float uhs[4] = {uh.x, uh.y, uh.z, uh.w}, uls[4] = {ul.x, ul.y, ul.z, ul.w};
     float oqh[4], oql[4], onh[4], onl[4];
 #pragma unroll
@@ -1122,19 +1173,27 @@ __global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, fl
       onl[u] = nd.y;
     }
     reinterpret_cast<float4*>(qh)[q] = make_float4(oqh[0], oqh[1], oqh[2], oqh[3]);
-    reinterpret_cast<float4*>(ql)[q] = make_float4(oql[0], oql[1], oql[2], oql[3]);
+    lo_store<B6>(Vl, (int64_t)j * ldv, q, make_float4(oql[0], oql[1], oql[2], oql[3]));
     reinterpret_cast<float4*>(nh)[q] = make_float4(onh[0], onh[1], onh[2], onh[3]);
-    reinterpret_cast<float4*>(nl)[q] = make_float4(onl[0], onl[1], onl[2], onl[3]);
+    lo_store<B6>(Vl, (int64_t)(j + 1) * ldv, q, make_float4(onl[0], onl[1], onl[2], onl[3]));
   }
 }
 void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
                   const double* w, double* v, int64_t n, const double* Hraw, int ldh, double* hc, const int* done,
-                  cudaStream_t st) {
-  int* ran = prof_begin(PROF_ORTH, (double)(j + 1) * n * 8.0 + 4.0 * n * 8.0, st);
+                  cudaStream_t st, bool b6) {
+  // FP64-equivalent bytes: j + 1 basis entries and u_j read, q_j and u_{j+1} written at 8 B, w read, v written;
+  // with the 6-byte basis the passes move 6 B per basis entry
+  int* ran = prof_begin(PROF_ORTH, (double)(j + 1) * n * 8.0 + 4.0 * n * 8.0, st,
+                        b6 ? (double)(j + 1) * n * 6.0 + 2.0 * n * 6.0 + 2.0 * n * 8.0 : 0.0);
   const int64_t n4 = (n + 3) / 4;
   const int nb = (int)std::min<int64_t>((n4 + UPD_THREADS - 1) / UPD_THREADS, 152 * 64);
-  WC4D_CUDA(launch_pdl(gm_dc_update_kernel, dim3(nb), dim3(UPD_THREADS), sizeof(float) * 4 * std::max(j, 1), st, Vh, Vl,
-                       ldv, j, e, c, dc, w, v, n, Hraw, ldh, hc, done, ran));
+  const size_t smem = sizeof(float) * 4 * std::max(j, 1);
+  if (b6)
+    WC4D_CUDA(launch_pdl(gm_dc_update_kernel<true>, dim3(nb), dim3(UPD_THREADS), smem, st, Vh, Vl, ldv, j, e, c, dc,
+                         w, v, n, Hraw, ldh, hc, done, ran));
+  else
+    WC4D_CUDA(launch_pdl(gm_dc_update_kernel<false>, dim3(nb), dim3(UPD_THREADS), smem, st, Vh, Vl, ldv, j, e, c, dc,
+                         w, v, n, Hraw, ldh, hc, done, ran));
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
 }

@@ -84,18 +84,22 @@ void gm_mupdate_df(const float* Vh, const float* Vl, int64_t ldv, int cnt, const
 void gm_normalize_df(const double* w, const double* hnext, double* v, float* vh, float* vl, int64_t n,
                      const int* done, cudaStream_t st);
 void gm_split(const double* w, float* wh, float* wl, int64_t n, const int* done, cudaStream_t st);
+// the first vector of the delayed-CGS2 basis in its storage form: FP32 low
+// parts, or BF16 low parts (16-bit words, same leading dimension) with b6
+void gm_split_basis(const double* w, float* vh, float* vl, int64_t n, bool b6, cudaStream_t st);
 
 // delayed CGS2 Arnoldi on the split basis (DF32 GMRES): scalar state slots
 enum { DC_GAMMA = 0, DC_ALPHA, DC_IGAMMA, DC_IALPHA, DC_BETA, DC_COUNT };
+// b6: the basis low parts are BF16 (6-byte entries), else FP32
 void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float* wh, const float* wl, int64_t n,
-               double* part, const int* done, cudaStream_t st);
+               double* part, const int* done, cudaStream_t st, bool b6);
 // hc: Hbar c of the previous step (j rows), written by gm_dc_update
 void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
                 double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
                 const double* bnorm, const double* hc, cudaStream_t st);
 void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
                   const double* w, double* v, int64_t n, const double* Hraw, int ldh, double* hc, const int* done,
-                  cudaStream_t st);
+                  cudaStream_t st, bool b6);
 
 // small vector ops
 template <typename T>

@@ -145,6 +145,7 @@ int wc4d_get_stats(wc4d_stats* out) {
     } else {
       out->orth_ms += ms;
       out->orth_bytes += p.recs[i].work;
+      out->orth_moved_bytes += p.recs[i].work2 > 0.0 ? p.recs[i].work2 : p.recs[i].work;
       out->orth_launches += 1;
     }
   }

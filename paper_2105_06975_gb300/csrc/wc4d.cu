@@ -296,6 +296,7 @@ struct wc4d_problem {
   // DF32 GMRES with delayed reorthogonalisation: raw Hessenberg, scalar state,
   // previous b and c, update coefficients, reduced dot rows, operator scratch
   bool dcgs = false;
+  bool b6 = false;  // delayed-CGS2 basis with BF16 low parts (6-byte entries)
   double *Hraw = nullptr, *Tm = nullptr, *dcst = nullptr, *bprev = nullptr, *cprev = nullptr, *ecoef = nullptr;
   double *red = nullptr, *yhat = nullptr, *hcbuf = nullptr;
   // learned Schur-block correction (shat = LEARNED): weights, inference scratch
@@ -1152,6 +1153,14 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
   WC4D_CHECK(o->covprod == WC4D_COVPROD_DENSE || o->covprod == WC4D_COVPROD_FFT, WC4D_ERR_ARG, "bad covprod");
   WC4D_CHECK(o->prec_digits >= 0 && o->prec_digits <= 7, WC4D_ERR_ARG, "prec_digits must lie in [0, 7]");
   WC4D_CHECK(o->rinv_explicit == 0 || o->rinv_explicit == 1, WC4D_ERR_ARG, "rinv_explicit must be 0 or 1");
+  WC4D_CHECK(o->basis_bytes == 0 || o->basis_bytes == 6 || o->basis_bytes == 8, WC4D_ERR_ARG,
+             "basis_bytes must be 0, 6 or 8");
+  WC4D_CHECK(o->basis_bytes != 6 || (o->krylov == WC4D_KRYLOV_GMRES &&
+                                     (o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_DF32_P32 ||
+                                      o->precision == WC4D_PREC_OZAKI)),
+             WC4D_ERR_ARG, "basis_bytes 6 needs GMRES with precision DF32, DF32_P32 or OZAKI");
+  WC4D_CHECK(o->basis_bytes != 6 || o->tol >= 1e-7, WC4D_ERR_ARG,
+             "basis_bytes 6 bounds the true residual near 1e-9: needs tol >= 1e-7");
   WC4D_CHECK(!o->rinv_explicit || (d->p_t == nullptr && o->precision != WC4D_PREC_MIXED &&
                                    o->precision != WC4D_PREC_DF32_P32 && o->shat != WC4D_SHAT_EXACT),
              WC4D_ERR_ARG,
@@ -1679,17 +1688,22 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->dcgs = (o->krylov == WC4D_KRYLOV_GMRES) &&
             (o->precision == WC4D_PREC_DF32 || o->precision == WC4D_PREC_DF32_P32 ||
              o->precision == WC4D_PREC_OZAKI);
+  P->b6 = P->dcgs && o->basis_bytes == 6;
   if (P->split_basis) {
-    // leading dimension padded to 4 floats (16-byte loads); padding stays zero
+    // leading dimension padded to 4 floats (16-byte loads); padding stays zero.
+    // The 6-byte basis keeps its BF16 low parts in half the low-part array
+    // (16-bit words, the same leading dimension in elements).
     P->ldb = (n + 3) / 4 * 4;
+    const size_t lo_size = P->b6 ? 2 : sizeof(float);
     P->Vh = P->alloc<float>(nvec * P->ldb);
-    P->Vl = P->alloc<float>(nvec * P->ldb);
+    P->Vl = P->alloc<float>(P->b6 ? nvec * P->ldb / 2 : nvec * P->ldb);
     P->wh = P->alloc<float>(P->ldb);
     P->wl = P->alloc<float>(P->ldb);
     if (P->ldb != n) {  // only the padding of each basis vector must read zero
       const size_t pitch = sizeof(float) * P->ldb, width = sizeof(float) * (P->ldb - n);
       WC4D_CUDA(cudaMemset2DAsync(P->Vh + n, pitch, 0, width, nvec, st));
-      WC4D_CUDA(cudaMemset2DAsync(P->Vl + n, pitch, 0, width, nvec, st));
+      WC4D_CUDA(cudaMemset2DAsync(reinterpret_cast<char*>(P->Vl) + lo_size * n, lo_size * P->ldb, 0,
+                                  lo_size * (P->ldb - n), nvec, st));
     }
     WC4D_CUDA(cudaMemsetAsync(P->wh, 0, sizeof(float) * P->ldb, st));
     WC4D_CUDA(cudaMemsetAsync(P->wl, 0, sizeof(float) * P->ldb, st));
@@ -1996,7 +2010,7 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   dot_partial<double>(r0, r0, n, P->part2, nullptr, st);
   gm_init<double>(r0, P->part2, P->vcur, P->g, P->stat, P->o.tol, n, st);
   WC4D_CUDA(cudaMemcpyAsync(P->dcst + DC_BETA, P->g, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  gm_split(P->vcur, P->Vh, P->Vl, n, nullptr, st);
+  gm_split_basis(P->vcur, P->Vh, P->Vl, n, P->b6, st);
   WC4D_CUDA(cudaMemsetAsync(P->H, 0, sizeof(double) * (size_t)ldh * P->maxit, st));
   WC4D_CUDA(cudaMemsetAsync(P->Hraw, 0, sizeof(double) * (size_t)ldh * P->maxit, st));
   int status = WC4D_OK;
@@ -2020,7 +2034,7 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
   while (!converged && status == WC4D_OK) {
     if (pending_update) {  // the step that stopped on a false convergence still owes its update pass
       gm_dc_update(P->Vh, P->Vl, lb, next - 1, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, P->Hraw, ldh,
-                   P->hcbuf, nullptr, st);
+                   P->hcbuf, nullptr, st, P->b6);
       pending_update = false;
     }
     const int batch = std::min(P->o.check_every, P->maxit + 1 - next);
@@ -2037,13 +2051,13 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       }
       // w = A z_j, written with its double-float split for the dot pass
       apply_A<double>(P, P->f64, P->plan_A, zj, P->wbuf, done, P->wh, P->wl);
-      gm_dc_dot(P->Vh, P->Vl, lb, j, P->wh, P->wl, n, P->part, done, st);
+      gm_dc_dot(P->Vh, P->Vl, lb, j, P->wh, P->wl, n, P->part, done, st, P->b6);
       gm_mdot_reduce(P->part, 2 * (j + 1) + 1, dot_chunks(n, j + 1), P->red, done, st);
       gm_dc_coef(j, P->red, P->dcst, P->bprev, P->cprev, P->ecoef, P->Hraw, P->H, P->Tm, ldh, P->cs, P->sn, P->g,
                  P->hnext, P->stat, P->bnorm, P->hcbuf, st);
       if (j < P->maxit)
         gm_dc_update(P->Vh, P->Vl, lb, j, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, P->Hraw, ldh,
-                     P->hcbuf, done, st);
+                     P->hcbuf, done, st, P->b6);
     }
     fetch_stat(P);
     it = P->h_stat->iters;

@@ -92,7 +92,8 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("lhat", ctypes.c_int32), ("rblock_count", ctypes.c_int32),
                 ("rblock_sizes", ctypes.POINTER(ctypes.c_int32)), ("rblock_tol", ctypes.c_double),
                 ("rblock_maxsize", ctypes.c_int32), ("rblock_numproc", ctypes.c_int32),
-                ("covprod", ctypes.c_int32), ("prec_digits", ctypes.c_int32), ("rinv_explicit", ctypes.c_int32)]
+                ("covprod", ctypes.c_int32), ("prec_digits", ctypes.c_int32), ("rinv_explicit", ctypes.c_int32),
+                ("basis_bytes", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -119,7 +120,8 @@ class Stats(ctypes.Structure):
                 ("gemmtc_launches", ctypes.c_int64), ("gemmtc_alg_bytes", ctypes.c_double),
                 ("circ_ms", ctypes.c_double), ("circ_flops", ctypes.c_double),
                 ("circ_bytes", ctypes.c_double), ("circ_launches", ctypes.c_int64), ("pt_ms", ctypes.c_double),
-                ("pt_bytes", ctypes.c_double), ("pt_launches", ctypes.c_int64)]
+                ("pt_bytes", ctypes.c_double), ("pt_launches", ctypes.c_int64),
+                ("orth_moved_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -402,7 +404,7 @@ def wc4d_last_error() -> str:
 # -------------------------------------------------------------- convenience
 def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dhat="exact", dhat_delta=0.01,
               krylov=None, tol=1e-6, maxit=1000, precision="fp64", inner_iters=20, check_every=4, lhat="lm",
-              rblock=None, covprod="dense", prec_digits=0, rinv_explicit=False) -> SolveOpts:
+              rblock=None, covprod="dense", prec_digits=0, rinv_explicit=False, basis_bytes=0) -> SolveOpts:
     """``rblock`` = (channel block sizes, tol, maxsize, numproc) for rhat="block"
     (Alg. 3; maxsize / numproc None or 0 switch their rule off)."""
     o = wc4d_default_opts()
@@ -435,6 +437,7 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
     o.covprod = {"dense": WC4D_COVPROD_DENSE, "fft": WC4D_COVPROD_FFT}[covprod]
     o.prec_digits = int(prec_digits)
     o.rinv_explicit = int(bool(rinv_explicit))
+    o.basis_bytes = int(basis_bytes)
     return o
 
 

@@ -189,3 +189,19 @@ def test_batch_and_stats_arguments(lib):
     lib.wc4d_reset_stats()
     assert lib.wc4d_get_stats(ctypes.byref(st)) == L.WC4D_OK
     assert st.launches == 0 and st.gemm_launches == 0
+
+
+@pytest.mark.parametrize("basis, kw, needle", [
+    (7, dict(), "basis_bytes must be 0, 6 or 8"),
+    (6, dict(precision="fp64"), "basis_bytes 6 needs GMRES"),
+    (6, dict(precision="ozaki", krylov="minres", precond="PD"), "basis_bytes 6 needs GMRES"),
+    (6, dict(precision="ozaki", tol=1e-8), "needs tol >= 1e-7"),
+])
+def test_basis_bytes_checks(lib, basis, kw, needle):
+    """The 6-byte Arnoldi basis (FP32 high + BF16 low part) is an option of
+    the delayed-CGS2 GMRES only, at tolerances its rounding allows."""
+    d, _ = base()
+    args = dict(precond="PI", k=1, tol=1e-6)
+    args.update(kw)
+    o = L.make_opts(basis_bytes=basis, **args)
+    refused(lib, d, o, needle)
