@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "krylov.cuh"
 
@@ -743,7 +744,7 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
                                                                 const float* __restrict__ Vl, int64_t ldv, int j,
                                                                 const float* __restrict__ wh,
                                                                 const float* __restrict__ wl, int64_t n4,
-                                                                double* __restrict__ part, const int* done,
+                                                                float2* __restrict__ part, const int* done,
                                                                 int* ran) {
   pdl_wait();
   pdl_trigger();
@@ -812,7 +813,6 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
   if (r < 2 * ORTH_G + 1) {
     float2 a2 = sh[0][r];
     for (int k = 1; k < DOT_THREADS / 32; ++k) a2 = df_add(a2, sh[k][r]);
-    const double v = (double)a2.x + (double)a2.y;
     int row = -1;
     if (r < ORTH_G) {
       if (r < gn) row = i0 + r;
@@ -821,11 +821,11 @@ __global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __r
     } else if (first) {
       row = 2 * cnt;
     }
-    if (row >= 0) part[(int64_t)row * gridDim.x + chunk] = v;
+    if (row >= 0) part[(int64_t)row * gridDim.x + chunk] = a2;  // summed by the coefficient kernel
   }
 }
 void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float* wh, const float* wl, int64_t n,
-               double* part, const int* done, cudaStream_t st, bool b6) {
+               float2* part, const int* done, cudaStream_t st, bool b6) {
   // profiled bytes: the FP64-equivalent 8 B per basis entry in both forms
   int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st, b6 ? (double)(j + 2) * n * 6.0 + (double)n * 8.0 : 0.0);
   const int64_t n4 = (n + 3) / 4;
@@ -845,42 +845,49 @@ void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float
 // (a_i, col[i+1]) to (rc_i a_i + rs_i col[i+1], -rs_i a_i + rc_i col[i+1]),
 // where a_0 = col[0] and a_{i+1} is the second component: an affine recurrence
 // a_{i+1} = alpha_i a_i + beta_i with alpha_i = -rs_i, beta_i = rc_i col[i+1].
-// Affine maps compose associatively, so the chain is a block-wide inclusive
-// scan of (A, B) pairs (a -> A a + B) instead of m dependent steps: on GB300 a
-// serial FP64 chain in one thread costs tens of cycles per operation.  Ends
-// with col[0..m-1] rotated and col[m] = a_m; col[m+1] is untouched.  Needs
-// m <= SCAN_PER * blockDim.x; sh: 64 doubles of shared scratch (two per warp).
+// Affine maps compose associatively, so the chain is an inclusive scan of
+// (A, B) pairs (a -> A a + B) instead of m dependent steps: on GB300 a serial
+// FP64 chain in one thread costs tens of cycles per operation.  Only the
+// first nt threads (a multiple of 32, as few as keep at most SCAN_PER
+// rotations per thread) take part: GB300 issues one warp FP64 instruction
+// per 16 SM cycles, so every idle warp's share of the scan would be pure
+// cost.  Every thread of the block must call it (it has block barriers).
+// Ends with col[0..m-1] rotated and col[m] = a_m; col[m+1] is untouched.
+// Needs m <= SCAN_PER * blockDim.x; sh: 64 doubles of shared scratch.
 constexpr int SCAN_PER = 8;
 __device__ void rotate_column_scan(double* col, const double* rc, const double* rs, int m, double* sh) {
-  const int per = (m + blockDim.x - 1) / blockDim.x;  // at most SCAN_PER rotations per thread
+  const int nt = min((int)blockDim.x, 32 * ((m + 32 * SCAN_PER - 1) / (32 * SCAN_PER)));
+  const int per = (m + nt - 1) / nt;  // at most SCAN_PER rotations per thread
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwa = nt >> 5;
+  const bool act = (int)threadIdx.x < nt;  // warp-uniform
   const int i0 = threadIdx.x * per;
-  const int i1 = min(i0 + per, m);
-  double LA = 1.0, LB = 0.0;  // this thread's rotations composed, in order
-  for (int i = i0; i < i1; ++i) {
-    const double al = -rs[i], be = rc[i] * col[i + 1];
-    LB = al * LB + be;
-    LA = al * LA;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  double A = LA, B = LB;  // inclusive scan within the warp: later o earlier
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const double Ap = __shfl_up_sync(0xffffffffu, A, off), Bp = __shfl_up_sync(0xffffffffu, B, off);
-    if (lane >= off) {
-      B = A * Bp + B;
-      A = A * Ap;
-    }
-  }
+  const int i1 = act ? min(i0 + per, m) : i0;
+  double A = 1.0, B = 0.0;
   double* wa = sh;
   double* wb = sh + 32;
+  if (act) {
+    for (int i = i0; i < i1; ++i) {  // this thread's rotations composed, in order
+      const double al = -rs[i], be = rc[i] * col[i + 1];
+      B = al * B + be;
+      A = al * A;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {  // inclusive scan within the warp: later o earlier
+      const double Ap = __shfl_up_sync(0xffffffffu, A, off), Bp = __shfl_up_sync(0xffffffffu, B, off);
+      if (lane >= off) {
+        B = A * Bp + B;
+        A = A * Ap;
+      }
+    }
+  }
   __syncthreads();  // sh may hold a previous reduction's partials
-  if (lane == 31) {
+  if (act && lane == 31) {
     wa[wid] = A;
     wb[wid] = B;
   }
   __syncthreads();
-  if (wid == 0) {
-    double X = lane < nw ? wa[lane] : 1.0, Y = lane < nw ? wb[lane] : 0.0;
+  if (wid == 0 && nwa > 1) {
+    double X = lane < nwa ? wa[lane] : 1.0, Y = lane < nwa ? wb[lane] : 0.0;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const double Xp = __shfl_up_sync(0xffffffffu, X, off), Yp = __shfl_up_sync(0xffffffffu, Y, off);
@@ -889,90 +896,185 @@ __device__ void rotate_column_scan(double* col, const double* rc, const double* 
         X = X * Xp;
       }
     }
-    if (lane < nw) {
+    if (lane < nwa) {
       wa[lane] = X;
       wb[lane] = Y;
     }
   }
   __syncthreads();
-  // exclusive prefix of this thread = (lane-exclusive within the warp) o (warps before)
-  double eA = __shfl_up_sync(0xffffffffu, A, 1), eB = __shfl_up_sync(0xffffffffu, B, 1);
-  if (lane == 0) {
-    eA = 1.0;
-    eB = 0.0;
-  }
-  if (wid > 0) {
-    const double PA = wa[wid - 1], PB = wb[wid - 1];
-    eB = eA * PB + eB;
-    eA = eA * PA;
-  }
-  const double a0 = col[0];
-  double av = eA * a0 + eB;  // a_{i0}
   double outv[SCAN_PER];
-  for (int i = i0; i < i1; ++i) {
-    const double y = col[i + 1];
-    outv[i - i0] = rc[i] * av + rs[i] * y;
-    av = -rs[i] * av + rc[i] * y;
+  double av = 0.0;
+  if (act) {
+    // exclusive prefix of this thread = (lane-exclusive within the warp) o (warps before)
+    double eA = __shfl_up_sync(0xffffffffu, A, 1), eB = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) {
+      eA = 1.0;
+      eB = 0.0;
+    }
+    if (wid > 0) {
+      const double PA = wa[wid - 1], PB = wb[wid - 1];
+      eB = eA * PB + eB;
+      eA = eA * PA;
+    }
+    av = eA * col[0] + eB;  // a_{i0}
+    for (int i = i0; i < i1; ++i) {
+      const double y = col[i + 1];
+      outv[i - i0] = rc[i] * av + rs[i] * y;
+      av = -rs[i] * av + rc[i] * y;
+    }
   }
   __syncthreads();  // every thread has read the unrotated column
   for (int i = i0; i < i1; ++i) col[i] = outv[i - i0];
-  if (i0 < m && i1 == m) col[m] = av;
+  if (act && i0 < m && i1 == m) col[m] = av;
   __syncthreads();
 }
 
-// One CTA.  red: the reduced dot rows (a, c, w^T w).  dc: scalar state
+// One CTA.  part: the dot pass's per-chunk partials (double-float pairs,
+// nchunks per row; rows a_0..a_j | c_0..c_j | w^T w).  dc: scalar state
 // (DC_* slots), bprev / cprev: b and c of the previous step, e: the update
-// coefficients.  Completes Hessenberg column j-1 (raw into Hraw, rotated into
-// H), updates the Givens rotations, g and the status, and writes column j of
-// the triangular T with u_j = Q_j c_j + gamma_j q_j (T = [c_j; gamma_j]), so
-// that P^-1 Q = Z~ T^-1 for the stored Z~_j = P^-1 u_j.  Shared memory: the
-// column and the rotations (3j + 2 doubles, as the CGS2 Hessenberg kernel).
-__global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const double* __restrict__ red, double* dc,
-                                                         double* bprev, double* cprev, double* e, double* Hraw,
-                                                         double* H, double* T, int ldh, double* cs, double* sn,
-                                                         double* g, double* hnext, DevStatus* stat,
+// coefficients.  Sums the partials (the dot reduction), completes Hessenberg
+// column j-1 (raw into Hraw, rotated into H), updates the Givens rotations, g
+// and the status, and writes column j of the triangular T with
+// u_j = Q_j c_j + gamma_j q_j (T = [c_j; gamma_j]), so that P^-1 Q = Z~ T^-1
+// for the stored Z~_j = P^-1 u_j.  GB300 issues one warp FP64 instruction per
+// 16 SM cycles, so the FP64 work is laid out by instruction count: the sums
+// of the partials run in double-float on the FP32 pipe (one FP64 conversion
+// per row), the scalar chain runs in one warp, not redundantly in eight.
+// Shared memory: the reduced rows, the column, the rotations, b and Hbar c
+// of the previous step (7 j + 5 doubles), then the staged partials.
+__global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const float2* __restrict__ part, int nchunks,
+                                                         double* dc, double* bprev, double* cprev, double* e,
+                                                         double* Hraw, double* H, double* T, int ldh, double* cs,
+                                                         double* sn, double* g, double* hnext, DevStatus* stat,
                                                          const double* bnorm, const double* __restrict__ hc) {
   extern __shared__ double sm[];
   __shared__ double sh[64];
+  __shared__ double scal[4];
+  __shared__ double pre[8];  // dc[ALPHA], dc[GAMMA], dc[BETA], g[j-1], ||b||, tol_est
+  __shared__ int sdone;
   pdl_wait();
   pdl_trigger();
-  if (*(volatile const int*)&stat->done) return;
-  const int cnt = j + 1;
-  const double* a = red;        // a_0..a_j
-  const double* c = red + cnt;  // c_0..c_{j-1}, c_j = u_j^T u_j
-  double* col = sm;             // [j + 2]
-  double* rc = col + j + 2;     // [j]
-  double* rs = rc + j;          // [j]
-  for (int i = threadIdx.x; i + 1 < j; i += blockDim.x) {
-    rc[i] = cs[i];
-    rs[i] = sn[i];
+  const int cnt = j + 1, rows = 2 * cnt + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* red = sm;           // [2 j + 3]: a_0..a_j | c_0..c_j | w^T w
+  double* col = red + rows;   // [j + 2]
+  double* rc = col + j + 2;   // [j]
+  double* rs = rc + j;        // [j]
+  double* bp = rs + j;        // [j]: b of the previous step
+  double* hcs = bp + j;       // [j]: Hbar c of the previous step
+  // every operand the kernel reads, in flight at once: the serial chain
+  // below then waits on shared memory, not on a global round trip per use
+  if (threadIdx.x == 0) {
+    sdone = *(volatile const int*)&stat->done;
+    pre[0] = dc[DC_ALPHA];
+    pre[1] = dc[DC_GAMMA];
+    pre[2] = dc[DC_BETA];
+    pre[3] = j >= 1 ? g[j - 1] : 0.0;
+    pre[4] = *bnorm;
+    pre[5] = stat->tol_est;
   }
-  const double ww = red[2 * cnt];
-  const double uu = c[j];
-  double cc = 0.0, ca = 0.0;
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
-    cc += c[i] * c[i];
-    ca += c[i] * a[i];
+    if (i + 1 < j) {
+      rc[i] = cs[i];
+      rs[i] = sn[i];
+    }
+    bp[i] = bprev[i];
+    hcs[i] = j >= 2 ? hc[i] : 0.0;
   }
-  block_sum2(cc, ca, sh);
-  const double gam = sqrt_clamped(uu - cc);
-  const double igam = gam > 0.0 ? 1.0 / gam : 0.0;
-  const double bj = (a[j] - ca) * igam;  // q_j^T w
-  const double alpha = dc[DC_ALPHA];     // scale of u_j
-  const double gprev = dc[DC_GAMMA];
-  // column j-1: (b_{j-1} - Hbar c_{j-1} + alpha c_j) / gamma_{j-1}, sub-diagonal alpha gamma / gamma_{j-1};
-  // hc = Hbar c_{j-1} was formed by the previous step's update kernel
-  if (j >= 1) {
-    const double ig = 1.0 / gprev;
-    // Hbar_{j-1} has columns 0..j-2: none at j = 1
-    for (int r = threadIdx.x; r < j; r += blockDim.x)
-      col[r] = (bprev[r] - (j >= 2 ? hc[r] : 0.0) + alpha * c[r]) * ig;
-    if (threadIdx.x == 0) col[j] = alpha * gam * ig;
+  // the dot reduction: the whole partial block (rows x nchunks pairs, at most
+  // about 4.1k) is staged in shared memory by every thread with eight loads
+  // in flight each, then each row is summed by tpr lanes (a power of two, as
+  // many as keep every thread busy) over the chunks in a fixed order
+  float2* pst = reinterpret_cast<float2*>(hcs + j);  // [rows * nchunks]
+  const int total = rows * nchunks;
+  for (int i0 = threadIdx.x; i0 < total; i0 += 8 * blockDim.x) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = i < total ? part[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < total) pst[i] = v[u];
+    }
   }
   __syncthreads();
+  int tpr = 32;
+  while (tpr > 1 && tpr * rows > (int)blockDim.x) tpr >>= 1;
+  const int sub = lane & (tpr - 1), per_round = blockDim.x / tpr;
+  for (int r0 = 0; r0 < rows; r0 += per_round) {
+    const int r = r0 + (int)threadIdx.x / tpr;
+    float2 acc = make_float2(0.f, 0.f);
+    if (r < rows)
+      for (int k = sub; k < nchunks; k += tpr) acc = df_add(acc, pst[r * nchunks + k]);
+    // rows never straddle a warp (tpr divides 32); lanes past the last row add zeros
+    for (int o = tpr >> 1; o > 0; o >>= 1)
+      acc = df_add(acc, make_float2(__shfl_xor_sync(0xffffffffu, acc.x, o), __shfl_xor_sync(0xffffffffu, acc.y, o)));
+    if (sub == 0 && r < rows) red[r] = (double)acc.x + (double)acc.y;
+  }
+  __syncthreads();
+  if (sdone) return;  // block-uniform
+  const double* a = red;        // a_0..a_j
+  const double* c = red + cnt;  // c_0..c_{j-1}, c_j = u_j^T u_j
+  const double ww = red[2 * cnt];
+  const double alpha = pre[0];  // scale of u_j
+  const double gprev = pre[1];
+  // Independent FP64 chains run in different warps, so their latencies
+  // overlap: warp 0 gamma and b_j (and column j-1 from them), warp 1 the
+  // reciprocals 1 / gamma_{j-1} and 1 / ||b|| (before warp 0 needs the first),
+  // warp 2 the next candidate's scale alpha (after the first barrier).
+  if (wid == 1 && lane == 0) {
+    pre[6] = 1.0 / gprev;
+    pre[7] = 1.0 / pre[4];
+  }
+  if (wid == 0) {
+    // gamma by Pythagoras, b_j = q_j^T w, |b|^2 (one warp; every lane holds the values)
+    double cc = 0.0, ca = 0.0, bb = 0.0;
+    for (int i = lane; i < j; i += 32) {
+      cc += c[i] * c[i];
+      ca += c[i] * a[i];
+      bb += a[i] * a[i];
+    }
+    cc = warp_sum(cc);
+    ca = warp_sum(ca);
+    bb = warp_sum(bb);
+    const double g2 = c[j] - cc;
+    const double rg = g2 > 0.0 ? rsqrt(g2) : 0.0;  // 1 / gamma
+    const double gam = g2 > 0.0 ? g2 * rg : sqrt_clamped(g2);
+    const double bj = (a[j] - ca) * rg;
+    if (lane == 0) {
+      scal[0] = gam;
+      scal[1] = rg;
+      scal[2] = bj;
+      scal[3] = bb + bj * bj;  // |w - Q b|^2 = w^T w - b^T b
+    }
+  }
+  __syncthreads();
+  const double gam = scal[0], igam = scal[1], bj = scal[2];
+  if (wid == 2 && lane == 0) {
+    const double a2 = fmax(ww - scal[3], ww * 1e-30);
+    const double ra = a2 > 0.0 ? rsqrt(a2) : 0.0;
+    dc[DC_ALPHA] = a2 > 0.0 ? a2 * ra : 1.0;
+    dc[DC_IALPHA] = ra;
+    dc[DC_GAMMA] = gam;
+    dc[DC_IGAMMA] = igam;
+  }
+  // column j-1: (b_{j-1} - Hbar c_{j-1} + alpha c_j) / gamma_{j-1}, sub-diagonal alpha gamma / gamma_{j-1};
+  // hc = Hbar c_{j-1} was formed by the previous step's update kernel (Hbar_{j-1} has no columns at j = 1)
   if (j >= 1) {
+    const double ig = pre[6];
     double* raw = Hraw + (int64_t)(j - 1) * ldh;
-    for (int r = threadIdx.x; r <= j; r += blockDim.x) raw[r] = col[r];
+    for (int r = threadIdx.x; r < j; r += blockDim.x) {
+      const double v = (bp[r] - hcs[r] + alpha * c[r]) * ig;
+      col[r] = v;
+      raw[r] = v;
+    }
+    if (threadIdx.x == 0) {
+      col[j] = alpha * gam * ig;
+      raw[j] = col[j];
+    }
   }
   {
     double* tc = T + (int64_t)j * ldh;
@@ -980,10 +1082,10 @@ __global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const double* __
     if (threadIdx.x == 0) tc[j] = gam;
   }
   __syncthreads();
-  if (j >= 2) rotate_column_scan(col, rc, rs, j - 1, sh);
+  if (j >= 2) rotate_column_scan(col, rc, rs, j - 1, sh);  // ends with a barrier
   if (threadIdx.x == 0) {
     if (j == 0) {
-      g[0] = dc[DC_BETA] * gam;  // r0 = ||r0|| u_0 = (||r0|| gamma_0) q_0
+      g[0] = pre[2] * gam;  // r0 = ||r0|| u_0 = (||r0|| gamma_0) q_0
       stat->iters = 0;
       if (!isfinite(gam) || !isfinite(ww) || !isfinite(bj)) {
         stat->status = WC4D_ERR_NONFINITE;
@@ -996,38 +1098,34 @@ __global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const double* __
       const int jc = j - 1;  // column being completed (rows 0..jc already rotated)
       *hnext = col[j];
       double cr = 1.0, sr = 0.0;
-      if (col[jc + 1] != 0.0) {
-        const double rr = hypot(col[jc], col[jc + 1]);
-        cr = col[jc] / rr;
-        sr = col[jc + 1] / rr;
+      const double x = col[jc], y = col[jc + 1];
+      if (y != 0.0) {
+        // the rotation from 1 / sqrt(x^2 + y^2) (one reciprocal square root instead of hypot and a
+        // division); hypot's scaling only where the sum of squares leaves the normal range
+        const double s2 = x * x + y * y;
+        const double ir = (s2 > 1e-300 && s2 < 1e300) ? rsqrt(s2) : 1.0 / hypot(x, y);
+        cr = x * ir;
+        sr = y * ir;
       }
       cs[jc] = cr;
       sn[jc] = sr;
-      col[jc] = cr * col[jc] + sr * col[jc + 1];
+      col[jc] = cr * x + sr * y;
       col[jc + 1] = 0.0;
-      const double gj = g[jc];
+      const double gj = pre[3];
       g[jc + 1] = -sr * gj;
       g[jc] = cr * gj;
-      const double est = fabs(g[jc + 1]) / *bnorm;
+      const double est = fabs(sr * gj) * pre[7];
       stat->iters = j;
       stat->est = est;
       if (!isfinite(est) || !isfinite(gam) || !isfinite(ww) || !isfinite(bj)) {
         stat->status = WC4D_ERR_NONFINITE;
         stat->done = 1;
-      } else if (est <= stat->tol_est || !(gam > 0.0)) {
+      } else if (est <= pre[5] || !(gam > 0.0)) {
         stat->done = 1;
       }
     }
   }
-  __syncthreads();
-  if (j >= 1) {
-    double* out = H + (int64_t)(j - 1) * ldh;
-    for (int r = threadIdx.x; r <= j; r += blockDim.x) out[r] = col[r];
-  }
-  // b = (a_0..a_{j-1}, bj); next candidate scale by Pythagoras: |w - Q b|^2 = w^T w - b^T b
-  double bb = 0.0;
-  for (int i = threadIdx.x; i < j; i += blockDim.x) bb += a[i] * a[i];
-  bb = block_sum(bb, sh) + bj * bj;  // block_sum ends with a barrier: bprev / cprev reads are done
+  // b = (a_0..a_{j-1}, bj) and the update coefficients e' = b - (b_j / gamma) c
   const double ratio = bj * igam;
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
     bprev[i] = a[i];
@@ -1037,20 +1135,27 @@ __global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const double* __
   if (threadIdx.x == 0) {
     bprev[j] = bj;
     e[j] = ratio;
-    const double a2 = fmax(ww - bb, ww * 1e-30);
-    const double an = a2 > 0.0 ? sqrt(a2) : 1.0;
-    dc[DC_GAMMA] = gam;
-    dc[DC_ALPHA] = an;
-    dc[DC_IGAMMA] = igam;
-    dc[DC_IALPHA] = a2 > 0.0 ? 1.0 / an : 0.0;
+  }
+  __syncthreads();
+  if (j >= 1) {
+    double* out = H + (int64_t)(j - 1) * ldh;
+    for (int r = threadIdx.x; r <= j; r += blockDim.x) out[r] = col[r];
   }
 }
-void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
-                double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
-                const double* bnorm, const double* hc, cudaStream_t st) {
-  const size_t smem = sizeof(double) * (3 * (size_t)j + 2);  // column + rotations
-  WC4D_CUDA(launch_pdl(gm_dc_coef_kernel, dim3(1), dim3(256), smem, st, j, red, dc, bprev, cprev, e, Hraw, H, T, ldh,
-                       cs, sn, g, hnext, stat, bnorm, hc));
+// (7 j + 5) doubles and (2 j + 3) x nchunks partials (at most about 4.1k: the dot pass's chunk count falls as
+// its vector groups grow) for j <= 2000 (GMRES maxit <= 2000)
+constexpr int COEF_SMEM_MAX = 160 * 1024;
+void gm_dc_coef(int j, const float2* part, int nchunks, double* dc, double* bprev, double* cprev, double* e,
+                double* Hraw, double* H, double* T, int ldh, double* cs, double* sn, double* g, double* hnext,
+                DevStatus* stat, const double* bnorm, const double* hc, cudaStream_t st) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    WC4D_CUDA(cudaFuncSetAttribute(gm_dc_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, COEF_SMEM_MAX));
+  });
+  const size_t smem = sizeof(double) * (7 * (size_t)j + 5) + sizeof(float2) * (2 * (size_t)j + 3) * nchunks;
+  WC4D_CHECK(smem <= (size_t)COEF_SMEM_MAX, WC4D_ERR_ARG, "internal: Arnoldi step beyond the coefficient kernel");
+  WC4D_CUDA(launch_pdl(gm_dc_coef_kernel, dim3(1), dim3(256), smem, st, j, part, nchunks, dc, bprev, cprev, e, Hraw,
+                       H, T, ldh, cs, sn, g, hnext, stat, bnorm, hc));
   WC4D_LAUNCH_CHECK();
 }
 

@@ -91,12 +91,14 @@ void gm_split_basis(const double* w, float* vh, float* vl, int64_t n, bool b6, c
 // delayed CGS2 Arnoldi on the split basis (DF32 GMRES): scalar state slots
 enum { DC_GAMMA = 0, DC_ALPHA, DC_IGAMMA, DC_IALPHA, DC_BETA, DC_COUNT };
 // b6: the basis low parts are BF16 (6-byte entries), else FP32
+// part: dot_chunks(n, j + 1) double-float partials per row (rows a_0..a_j | c_0..c_j | w^T w), summed by
+// gm_dc_coef
 void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float* wh, const float* wl, int64_t n,
-               double* part, const int* done, cudaStream_t st, bool b6);
+               float2* part, const int* done, cudaStream_t st, bool b6);
 // hc: Hbar c of the previous step (j rows), written by gm_dc_update
-void gm_dc_coef(int j, const double* red, double* dc, double* bprev, double* cprev, double* e, double* Hraw, double* H,
-                double* T, int ldh, double* cs, double* sn, double* g, double* hnext, DevStatus* stat,
-                const double* bnorm, const double* hc, cudaStream_t st);
+void gm_dc_coef(int j, const float2* part, int nchunks, double* dc, double* bprev, double* cprev, double* e,
+                double* Hraw, double* H, double* T, int ldh, double* cs, double* sn, double* g, double* hnext,
+                DevStatus* stat, const double* bnorm, const double* hc, cudaStream_t st);
 void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
                   const double* w, double* v, int64_t n, const double* Hraw, int ldh, double* hc, const int* done,
                   cudaStream_t st, bool b6);
