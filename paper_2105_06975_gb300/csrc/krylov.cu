@@ -738,9 +738,10 @@ __device__ __forceinline__ void lo_store(float* Vl, int64_t off, int64_t q, floa
   }
 }
 
-// part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w
+// part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w.  Four CTAs per SM
+// (64 registers): the pass is bound by the loads in flight per SM.
 template <bool B6>
-__global__ void __launch_bounds__(DOT_THREADS) gm_dc_dot_kernel(const float* __restrict__ Vh,
+__global__ void __launch_bounds__(DOT_THREADS, 4) gm_dc_dot_kernel(const float* __restrict__ Vh,
                                                                 const float* __restrict__ Vl, int64_t ldv, int j,
                                                                 const float* __restrict__ wh,
                                                                 const float* __restrict__ wl, int64_t n4,
@@ -829,7 +830,7 @@ void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float
   // profiled bytes: the FP64-equivalent 8 B per basis entry in both forms
   int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st, b6 ? (double)(j + 2) * n * 6.0 + (double)n * 8.0 : 0.0);
   const int64_t n4 = (n + 3) / 4;
-  dim3 grid((unsigned)dot_chunks(n, j + 1), (j + 1 + ORTH_G - 1) / ORTH_G);
+  dim3 grid((unsigned)dc_dot_chunks(n, j + 1), (j + 1 + ORTH_G - 1) / ORTH_G);
   if (b6)
     WC4D_CUDA(launch_pdl(gm_dc_dot_kernel<true>, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done,
                          ran));
@@ -982,7 +983,7 @@ __global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const float2* __
     hcs[i] = j >= 2 ? hc[i] : 0.0;
   }
   // the dot reduction: the whole partial block (rows x nchunks pairs, at most
-  // about 4.1k) is staged in shared memory by every thread with eight loads
+  // about 5.5k) is staged in shared memory by every thread with eight loads
   // in flight each, then each row is summed by tpr lanes (a power of two, as
   // many as keep every thread busy) over the chunks in a fixed order
   float2* pst = reinterpret_cast<float2*>(hcs + j);  // [rows * nchunks]
@@ -1142,7 +1143,7 @@ __global__ void __launch_bounds__(256) gm_dc_coef_kernel(int j, const float2* __
     for (int r = threadIdx.x; r <= j; r += blockDim.x) out[r] = col[r];
   }
 }
-// (7 j + 5) doubles and (2 j + 3) x nchunks partials (at most about 4.1k: the dot pass's chunk count falls as
+// (7 j + 5) doubles and (2 j + 3) x nchunks partials (at most about 5.5k: the dot pass's chunk count falls as
 // its vector groups grow) for j <= 2000 (GMRES maxit <= 2000)
 constexpr int COEF_SMEM_MAX = 160 * 1024;
 void gm_dc_coef(int j, const float2* part, int nchunks, double* dc, double* bprev, double* cprev, double* e,
@@ -1165,8 +1166,9 @@ void gm_dc_coef(int j, const float2* part, int nchunks, double* dc, double* bpre
 // 64-thread CTAs: one float4 row per thread, so the grid is n/256 small CTAs
 // that spread evenly over the SMs (256-thread CTAs left 2 or 3 per SM)
 constexpr int UPD_THREADS = 64;
+// sixteen 64-thread CTAs per SM (64 registers): 32 warps' loads in flight
 template <bool B6>
-__global__ void __launch_bounds__(UPD_THREADS) gm_dc_update_kernel(float* Vh, float* Vl, int64_t ldv, int j,
+__global__ void __launch_bounds__(UPD_THREADS, 16) gm_dc_update_kernel(float* Vh, float* Vl, int64_t ldv, int j,
                                                                    const double* __restrict__ e,
                                                                    const double* __restrict__ cv,
                                                                    const double* __restrict__ dc,

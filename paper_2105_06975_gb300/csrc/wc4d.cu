@@ -2053,7 +2053,7 @@ static int solve_gmres_dc(wc4d_problem* P, wc4d_info* info, bool use_x0) {
       apply_A<double>(P, P->f64, P->plan_A, zj, P->wbuf, done, P->wh, P->wl);
       float2* part2 = reinterpret_cast<float2*>(P->part);  // one double-float pair per (row, chunk)
       gm_dc_dot(P->Vh, P->Vl, lb, j, P->wh, P->wl, n, part2, done, st, P->b6);
-      gm_dc_coef(j, part2, dot_chunks(n, j + 1), P->dcst, P->bprev, P->cprev, P->ecoef, P->Hraw, P->H, P->Tm, ldh,
+      gm_dc_coef(j, part2, dc_dot_chunks(n, j + 1), P->dcst, P->bprev, P->cprev, P->ecoef, P->Hraw, P->H, P->Tm, ldh,
                  P->cs, P->sn, P->g, P->hnext, P->stat, P->bnorm, P->hcbuf, st);
       if (j < P->maxit)
         gm_dc_update(P->Vh, P->Vl, lb, j, P->ecoef, P->cprev, P->dcst, P->wbuf, P->vcur, n, P->Hraw, ldh,
