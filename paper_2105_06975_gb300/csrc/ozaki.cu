@@ -567,10 +567,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = cc * 16 + j;
-          // sum_l acc_l 2^(-7l) in double-float, smallest level first (each term exact)
-          float h = __uint_as_float(v[OZ_DIGITS - 1][j]) * 0x1p-42f, lo = 0.f;
+          // sum_l acc_l 2^(-7l) in double-float, smallest level first (each term
+          // exact).  Levels 6, 5, 4 (below 2^-4 together, every accumulator being
+          // below 2^24) are summed in plain FP32: their rounding, at most 2^-28 in
+          // these units, is a sixth of what the dropped levels 7..12 may already
+          // contribute (up to about 2^-25.3); levels 3..0 enter through
+          // error-free TwoSum steps.
+          float h = fmaf(__uint_as_float(v[OZ_DIGITS - 3][j]), 0x1p-28f,
+                         fmaf(__uint_as_float(v[OZ_DIGITS - 2][j]), 0x1p-35f,
+                              __uint_as_float(v[OZ_DIGITS - 1][j]) * 0x1p-42f)),
+                lo = 0.f;
+          static_assert(OZ_DIGITS == 7, "the level split above assumes seven levels");
 #pragma unroll
-          for (int l = OZ_DIGITS - 2; l >= 0; --l) {
+          for (int l = OZ_DIGITS - 4; l >= 0; --l) {
             const float tl = __uint_as_float(v[l][j]) * __int_as_float((127 - 7 * l) << 23);
             float s, e;
             two_sum(tl, h, s, e);
