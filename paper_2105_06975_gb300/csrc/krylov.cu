@@ -738,10 +738,26 @@ __device__ __forceinline__ void lo_store(float* Vl, int64_t off, int64_t q, floa
   }
 }
 
-// part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w.  Four CTAs per SM
-// (64 registers): the pass is bound by the loads in flight per SM.
+// asynchronous global -> shared copies of 16 and 8 bytes (cp.async; the
+// issuing thread waits for its own groups with cp.async.wait_group)
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+constexpr int DC_NS = 2;                    // stages of each thread's private copy ring
+constexpr int DC_SLOTS = 2 * ORTH_G + 4;    // per stage: G basis hi, G basis lo, w hi, w lo, u hi, u lo
+constexpr size_t DC_DOT_SMEM = (size_t)DC_NS * DC_SLOTS * DOT_THREADS * 16;
+// part rows: a_0..a_j | c_0..c_j (c_j = u_j^T u_j) | w^T w.  The pass is
+// bound by the bytes in flight per SM: each thread keeps its next stage of
+// entries in flight through a private shared-memory ring (two stages, 96 KB
+// per CTA, two CTAs per SM) instead of in registers (39.1 against 44.3 us per
+// pass at the scale window, the update pass unchanged).
 template <bool B6>
-__global__ void __launch_bounds__(DOT_THREADS, 4) gm_dc_dot_kernel(const float* __restrict__ Vh,
+__global__ void __launch_bounds__(DOT_THREADS, 2) gm_dc_dot_kernel(const float* __restrict__ Vh,
                                                                 const float* __restrict__ Vl, int64_t ldv, int j,
                                                                 const float* __restrict__ wh,
                                                                 const float* __restrict__ wl, int64_t n4,
@@ -766,16 +782,63 @@ __global__ void __launch_bounds__(DOT_THREADS, 4) gm_dc_dot_kernel(const float* 
   for (int g = 0; g < ORTH_G; ++g) s2[g] = c2[g] = make_float2(0.f, 0.f);
   s[2 * ORTH_G] = c[2 * ORTH_G] = 0.f;
   const float* uhp = Vh + (int64_t)j * ldv;
-  for (int64_t q = (int64_t)chunk * DOT_THREADS + threadIdx.x; q < n4; q += (int64_t)gridDim.x * DOT_THREADS) {
-    const float4 xh = reinterpret_cast<const float4*>(wh)[q];
-    const float4 xl = reinterpret_cast<const float4*>(wl)[q];
-    const float4 uh = reinterpret_cast<const float4*>(uhp)[q];
-    const float4 ul = lo_load<B6>(Vl, (int64_t)j * ldv, q);
+  // every thread streams its own entries through a private ring of DC_NS
+  // stages in shared memory with asynchronous 16-byte copies (8-byte for BF16
+  // low parts): the loads of the next stages are in flight while this one is
+  // summed, and no register holds a load in flight
+  extern __shared__ float4 dring[];  // [DC_NS][DC_SLOTS][DOT_THREADS]
+  const int tid = threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * DOT_THREADS;
+  const int64_t qbeg = (int64_t)chunk * DOT_THREADS + tid;
+  auto issue = [&](int stg, int64_t q) {
+    if (q < n4) {
+      float4* S = dring + (size_t)stg * DC_SLOTS * DOT_THREADS + tid;
+#pragma unroll
+      for (int g = 0; g < ORTH_G; ++g) {
+        if (g < gn) {
+          cpa16(S + g * DOT_THREADS, Vh + (int64_t)(i0 + g) * ldv + 4 * q);
+          if constexpr (B6)
+            cpa8(S + (ORTH_G + g) * DOT_THREADS, reinterpret_cast<const uint16_t*>(Vl) + (int64_t)(i0 + g) * ldv + 4 * q);
+          else
+            cpa16(S + (ORTH_G + g) * DOT_THREADS, Vl + (int64_t)(i0 + g) * ldv + 4 * q);
+        }
+      }
+      cpa16(S + (2 * ORTH_G) * DOT_THREADS, wh + 4 * q);
+      cpa16(S + (2 * ORTH_G + 1) * DOT_THREADS, wl + 4 * q);
+      cpa16(S + (2 * ORTH_G + 2) * DOT_THREADS, uhp + 4 * q);
+      if constexpr (B6)
+        cpa8(S + (2 * ORTH_G + 3) * DOT_THREADS, reinterpret_cast<const uint16_t*>(Vl) + (int64_t)j * ldv + 4 * q);
+      else
+        cpa16(S + (2 * ORTH_G + 3) * DOT_THREADS, Vl + (int64_t)j * ldv + 4 * q);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto lo_of = [&](const float4* p) -> float4 {
+    if constexpr (B6) {
+      const uint2 r = *reinterpret_cast<const uint2*>(p);
+      return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u), __uint_as_float(r.y << 16),
+                         __uint_as_float(r.y & 0xFFFF0000u));
+    } else {
+      return *p;
+    }
+  };
+#pragma unroll
+  for (int st0 = 0; st0 < DC_NS - 1; ++st0) issue(st0, qbeg + st0 * stride);
+  int stg = 0;
+  for (int64_t q = qbeg; q < n4; q += stride) {
+    issue((stg + DC_NS - 1) % DC_NS, q + (DC_NS - 1) * stride);
+    asm volatile("cp.async.wait_group %0;" ::"n"(DC_NS - 1) : "memory");
+    const float4* S = dring + (size_t)stg * DC_SLOTS * DOT_THREADS + tid;
+    stg = (stg + 1) % DC_NS;
+    const float4 xh = S[(2 * ORTH_G) * DOT_THREADS];
+    const float4 xl = S[(2 * ORTH_G + 1) * DOT_THREADS];
+    const float4 uh = S[(2 * ORTH_G + 2) * DOT_THREADS];
+    const float4 ul = lo_of(S + (2 * ORTH_G + 3) * DOT_THREADS);
 #pragma unroll
     for (int g = 0; g < ORTH_G; ++g) {
       if (g < gn) {
-        const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)(i0 + g) * ldv)[q];
-        const float4 b = lo_load<B6>(Vl, (int64_t)(i0 + g) * ldv, q);
+        const float4 a = S[g * DOT_THREADS];
+        const float4 b = lo_of(S + (ORTH_G + g) * DOT_THREADS);
         df_mac2(s2[g], c2[g], make_float2(a.x, a.x), make_float2(b.x, b.x), make_float2(xh.x, uh.x),
                 make_float2(xl.x, ul.x));
         df_mac2(s2[g], c2[g], make_float2(a.y, a.y), make_float2(b.y, b.y), make_float2(xh.y, uh.y),
@@ -793,6 +856,7 @@ __global__ void __launch_bounds__(DOT_THREADS, 4) gm_dc_dot_kernel(const float* 
       df_mac(s[2 * ORTH_G], c[2 * ORTH_G], xh.w, xl.w, xh.w, xl.w);
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight past the loop
   // warp reduction in double-float on the FP32 pipe (an FP64 shuffle tree per
   // vector would occupy GB300's 1/64-rate FP64 pipe for a large part of the
   // kernel); one FP64 conversion per warp and vector
@@ -831,12 +895,17 @@ void gm_dc_dot(const float* Vh, const float* Vl, int64_t ldv, int j, const float
   int* ran = prof_begin(PROF_ORTH, (double)(j + 3) * n * 8.0, st, b6 ? (double)(j + 2) * n * 6.0 + (double)n * 8.0 : 0.0);
   const int64_t n4 = (n + 3) / 4;
   dim3 grid((unsigned)dc_dot_chunks(n, j + 1), (j + 1 + ORTH_G - 1) / ORTH_G);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    WC4D_CUDA(cudaFuncSetAttribute(gm_dc_dot_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DC_DOT_SMEM));
+    WC4D_CUDA(cudaFuncSetAttribute(gm_dc_dot_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DC_DOT_SMEM));
+  });
   if (b6)
-    WC4D_CUDA(launch_pdl(gm_dc_dot_kernel<true>, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done,
-                         ran));
+    WC4D_CUDA(launch_pdl(gm_dc_dot_kernel<true>, grid, dim3(DOT_THREADS), DC_DOT_SMEM, st, Vh, Vl, ldv, j, wh, wl, n4, part,
+                         done, ran));
   else
-    WC4D_CUDA(launch_pdl(gm_dc_dot_kernel<false>, grid, dim3(DOT_THREADS), 0, st, Vh, Vl, ldv, j, wh, wl, n4, part, done,
-                         ran));
+    WC4D_CUDA(launch_pdl(gm_dc_dot_kernel<false>, grid, dim3(DOT_THREADS), DC_DOT_SMEM, st, Vh, Vl, ldv, j, wh, wl, n4,
+                         part, done, ran));
   WC4D_LAUNCH_CHECK();
   if (ran) prof_end(st);
 }

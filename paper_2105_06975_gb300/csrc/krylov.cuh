@@ -25,13 +25,12 @@ inline int dot_chunks(int64_t n, int cnt) {
 }
 
 // Chunk count of the delayed-CGS2 dot pass (DF32 / OZAKI GMRES): as
-// dot_chunks, but four CTAs per SM (the kernel is held to 64 registers: more
-// warps in flight per SM raise its achieved bandwidth, 50.6 -> 48.6 us per
-// pass at the scale window).
+// dot_chunks, but two CTAs per SM, the residency its shared-memory copy ring
+// (96 KB per CTA) allows.
 inline int dc_dot_chunks(int64_t n, int cnt) {
   const int maxc = orth_chunks(n);
   const int groups = (cnt + ORTH_G - 1) / ORTH_G;
-  int c = (152 * 4) / groups;
+  int c = (152 * 2) / groups;
   return c < 1 ? 1 : (c > maxc ? maxc : c);
 }
 
