@@ -519,13 +519,24 @@ def run_gpu(args):
                                                               maxit=args.maxit, precision="ozaki", covprod="fft",
                                                               check_every=ce)),
                         ("PD_minres_ozaki", wc4d.make_opts(precond="PD", k=args.k, rhat=args.rhat, tol=1e-6,
-                                                           maxit=3000, precision="ozaki", check_every=ce))):
+                                                           maxit=3000, precision="ozaki", check_every=ce)),
+                        # the chosen mode with reduced-precision preconditioner products: 5 of the 7 BF16
+                        # digits (about 34-bit operands) in P_I's tensor-core products, the flexible GMRES
+                        # keeping the computed P^-1 u (A v and the residual stay FP64-class)
+                        ("PI_gmres_ozaki_rinv_b6_prec5", wc4d.make_opts(precond="PI", k=args.k, rhat=args.rhat,
+                                                                        tol=1e-6, maxit=args.maxit, precision="ozaki",
+                                                                        check_every=ce, rinv_explicit=True,
+                                                                        basis_bytes=6, prec_digits=5)))):
             if name == "PI_gmres_ozaki_fft" and args.precond == "PI" and "ozaki_fft" in results:
                 continue
             for _ in range(max(1, args.warmup // 2)):
                 step(o)
             c_ms, c_infos, _ = timed(o, False)
-            assert all(i.status == 0 for i in c_infos), [i.as_dict() for i in c_infos]
+            if not all(i.status == 0 for i in c_infos):  # reported, not fatal: a comparison, not the headline
+                comparisons[name] = {"converged": False, "status": [i.status for i in c_infos],
+                                     "iterations": statistics.mean(i.iters for i in c_infos),
+                                     "relres_true_max": max(i.relres_true for i in c_infos)}
+                continue
             comparisons[name] = {"solves_per_s": 1e3 * args.steps / c_ms, "ms_per_step": c_ms / args.steps,
                                  "iterations": statistics.mean(i.iters for i in c_infos),
                                  "relres_true_max": max(i.relres_true for i in c_infos),
