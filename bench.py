@@ -526,7 +526,7 @@ def run_gpu(args):
                         ("PI_gmres_ozaki_rinv_b6_prec5", wc4d.make_opts(precond="PI", k=args.k, rhat=args.rhat,
                                                                         tol=1e-6, maxit=args.maxit, precision="ozaki",
                                                                         check_every=ce, rinv_explicit=True,
-                                                                        basis_bytes=6, prec_digits=5)))):
+                                                                        basis_bytes=6, prec_digits=5))):
             if name == "PI_gmres_ozaki_fft" and args.precond == "PI" and "ozaki_fft" in results:
                 continue
             for _ in range(max(1, args.warmup // 2)):
