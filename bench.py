@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--mixed", action="store_true", help="also time the nested FP32-inner mode")
     ap.add_argument("--chosen", default="ozaki_rinv_b6", choices=["fp64", "df32", "df32p32", "mixed", "ozaki", "fp64_fft",
                                                           "df32_fft", "ozaki_fft", "ozaki_rinv",
-                                                          "ozaki_rinv_b6"])
+                                                          "ozaki_rinv_b6", "ozaki_fft_rinv_b6"])
     ap.add_argument("--precision", default="ozaki", choices=["df32", "ozaki"],
                     help="product precision of the batched and learned workloads")
     ap.add_argument("--rinv", action="store_true",
@@ -250,7 +250,9 @@ MODE_DTYPE = {"fp64": "f64", "df32": "df32 products (2 x f32, ~48-bit) / f64 rec
                            "recurrences",
               "ozaki_rinv": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / df32 / f64 recurrences",
               "ozaki_rinv_b6": "bf16 digit products exact in f32 (47-bit operands as 7 digits) / f32+bf16 Arnoldi "
-                               "basis / f64 recurrences"}
+                               "basis / f64 recurrences",
+              "ozaki_fft_rinv_b6": "df32 FFT for B, Q; bf16 digit products exact in f32 for the R family / f32+bf16 "
+                                   "Arnoldi basis / f64 recurrences"}
 MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
              "df32": "FP64 GMRES; covariance / factor products in double-float on the FP32 pipe",
              "ozaki": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
@@ -267,7 +269,10 @@ MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
                            "P_I's D c1)",
              "ozaki_rinv_b6": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
                               "on tcgen05; Rhat^-1 as one product with the explicit inverse W^T W; Arnoldi basis "
-                              "stored as FP32 high + BF16 low parts (6 B per entry, about 32 bits)"}
+                              "stored as FP32 high + BF16 low parts (6 B per entry, about 32 bits)",
+             "ozaki_fft_rinv_b6": "FP64 GMRES; circulant B, Q (and Bhat^-1, Qhat^-1) by double-float FFT (cluster-"
+                                  "split four-step transform); R-family products as exact BF16 digit products on "
+                                  "tcgen05 with the explicit Rhat^-1; 6-byte Arnoldi basis"}
 
 
 # DRAM bytes per launch of gemm_streamk_df32_kernel, ncu dram__bytes_read.sum + dram__bytes_write.sum,
@@ -420,6 +425,10 @@ def run_gpu(args):
         modes["ozaki_rinv_b6"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
                                                 maxit=args.maxit, precision="ozaki", check_every=ce,
                                                 rinv_explicit=True, basis_bytes=6)
+    if args.chosen == "ozaki_fft_rinv_b6" or (args.modes and "ozaki_fft_rinv_b6" in args.modes.split(",")):
+        modes["ozaki_fft_rinv_b6"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
+                                                    maxit=args.maxit, precision="ozaki", check_every=ce,
+                                                    covprod="fft", rinv_explicit=True, basis_bytes=6)
     # circulant B and Q applied by FFT (Sec. 6.1), the R family as in the base mode
     for m in ("fp64", "df32", "ozaki"):
         if args.chosen == m + "_fft" or (args.modes and m + "_fft" in args.modes.split(",")):
@@ -504,7 +513,8 @@ def run_gpu(args):
         assert all(i.status == 0 for i in infos), [i.as_dict() for i in infos]
         results[mode] = {"ms": ms, "value": world * 1e3 / ms, "infos": infos, "stats": st,
                          "kernels": kernel_rows(st, prof_ms, hbm, dcgs=mode in ("df32", "df32p32", "ozaki", "df32_fft",
-                                                                              "ozaki_fft", "ozaki_rinv", "ozaki_rinv_b6")),
+                                                                              "ozaki_fft", "ozaki_rinv", "ozaki_rinv_b6",
+                                                                              "ozaki_fft_rinv_b6")),
                          "profiled_ms_per_step": prof_ms / args.steps,
                          "setup_ms": statistics.mean(a for a, _ in split),
                          "solve_ms": statistics.mean(b for _, b in split)}
@@ -899,7 +909,7 @@ def run_profile(args):
     o = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat,
                        tol=1e-7 if args.chosen.endswith("_b6") else 1e-30, maxit=args.maxit,
                        precision=base if base in ("fp64", "df32", "ozaki") else "ozaki",
-                       covprod="fft" if args.chosen.endswith("_fft") else "dense",
+                       covprod="fft" if "_fft" in args.chosen else "dense",
                        krylov="gmres" if args.precond == "PI" else "minres",
                        rinv_explicit=("_rinv" in args.chosen), basis_bytes=6 if args.chosen.endswith("_b6") else 0)
     G = wc4d.Problem.from_workload(w, dr, o)
