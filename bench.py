@@ -313,7 +313,7 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                                             "FP32 lane operations per double-float multiply-add"}
     if st.gemmtc_launches:
         ms1 = st.gemmtc_ms / st.gemmtc_launches
-        # the byte floor of SURVEY's per-unit accounting: each FP64 operator entry read once, vectors once;
+        # the byte floor of the per-unit accounting: each FP64 operator entry read once, vectors once;
         # the digit form (what the kernel moves: 14 B per operator entry) is reported beside it
         a_hbm = st.gemmtc_alg_bytes / (st.gemmtc_ms * 1e-3) / 1e9
         a_dig = st.gemmtc_bytes / (st.gemmtc_ms * 1e-3) / 1e9
