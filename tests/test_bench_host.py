@@ -42,6 +42,23 @@ def test_kernel_rows_fractions_and_shares():
     assert bench.kernel_rows(st, 1000.0, hbm=None)["orth"]["frac"] is None
 
 
+def test_orth_row_with_the_six_byte_basis():
+    """orth_bytes count 8 B per basis entry (the FP64-equivalent floor the
+    fraction uses); with the 6-byte basis the row adds what the passes move,
+    and the roofline traffic is scaled from the 6-byte capture."""
+    hbm = 6794.5
+    st = _stats(orth_ms=100.0, orth_bytes=4e11, orth_moved_bytes=3e11, orth_launches=1000)
+    o = bench.kernel_rows(st, step_ms=400.0, hbm=hbm, dcgs=True)["orth"]
+    assert o["frac"] == pytest.approx(4000.0 / hbm)
+    assert o["moved"]["achieved_gbs"] == pytest.approx(3000.0)
+    assert o["moved"]["frac"] == pytest.approx(3000.0 / hbm)
+    assert o["moved"]["bytes_per_launch"] == pytest.approx(3e8)
+    assert "orth_b6" in bench.TRAFFIC_RATIO and 0.9 < bench.TRAFFIC_RATIO["orth_b6"][0] < 1.1
+    # the 8-byte basis: no moved block (both counts agree)
+    st8 = _stats(orth_ms=100.0, orth_bytes=4e11, orth_moved_bytes=4e11, orth_launches=1000)
+    assert "moved" not in bench.kernel_rows(st8, 400.0, hbm=hbm, dcgs=True)["orth"]
+
+
 def test_tensor_core_row_takes_the_tighter_roof(monkeypatch):
     monkeypatch.setattr(bench, "peaks", lambda: {"bf16_tflops": 1918.0})
     hbm = 6795.8
