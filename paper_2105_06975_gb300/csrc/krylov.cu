@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
@@ -1231,9 +1232,10 @@ void gm_dc_coef(int j, const float2* part, int nchunks, double* dc, double* bpre
 
 // q_j = (u_j - Q_j c) / gamma into slot j (in place), u_{j+1} = (w - Q_j e' - e_j u_j) / alpha
 // into slot j+1 and into v (double, the next operator input).  Both sums and
-// the q_j epilogue in double-float; 4 elements per thread, 16-byte loads.
-// 64-thread CTAs: one float4 row per thread, so the grid is n/256 small CTAs
-// that spread evenly over the SMs (256-thread CTAs left 2 or 3 per SM)
+// the q_j epilogue in double-float; 2 elements per thread (8-byte loads):
+// one float4 per thread gave n/4 threads, about 17 warps per SM at the scale
+// window; with a float2 the resident wave of 64-thread CTAs keeps 32 warps'
+// loads in flight (orth passes 39.1 -> 38.0 µs mean)
 constexpr int UPD_THREADS = 64;
 // sixteen 64-thread CTAs per SM (64 registers): 32 warps' loads in flight
 template <bool B6>
@@ -1276,58 +1278,65 @@ __global__ void __launch_bounds__(UPD_THREADS, 16) gm_dc_update_kernel(float* Vh
   // scalars as double-float pairs: the per-element epilogue stays on the FP32 pipe
   const float2 eJ = df_from(e[j]), gI = df_from(dc[DC_IGAMMA]);
   const double ialpha = dc[DC_IALPHA];
-  const int64_t n4 = (n + 3) / 4;
+  // two elements per thread (one float2 of each basis vector): n/2 threads,
+  // about twice the warps per SM of one float4 per thread, for the latency of
+  // the basis loads
+  const int64_t n2 = (n + 1) / 2;
   float* qh = Vh + (int64_t)j * ldv;
   float* nh = Vh + (int64_t)(j + 1) * ldv;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
-    // paired accumulators: [0] elements 0, 1 of the float4, [1] elements 2, 3
-    float2 se[2], ce[2], sc[2], cc[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) se[u] = ce[u] = sc[u] = cc[u] = make_float2(0.f, 0.f);
+  auto lo2 = [&](int64_t off, int64_t q) -> float2 {
+    if constexpr (B6) {
+      const uint32_t r = reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint16_t*>(Vl) + off)[q];
+      return make_float2(__uint_as_float(r << 16), __uint_as_float(r & 0xFFFF0000u));
+    } else {
+      return reinterpret_cast<const float2*>(Vl + off)[q];
+    }
+  };
+  auto lo2_store = [&](int64_t off, int64_t q, float2 v) {
+    if constexpr (B6) {
+      const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(v.x)), b = __bfloat16_as_ushort(__float2bfloat16_rn(v.y));
+      reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(Vl) + off)[q] = a | (b << 16);
+    } else {
+      reinterpret_cast<float2*>(Vl + off)[q] = v;
+    }
+  };
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x) {
+    float2 se = make_float2(0.f, 0.f), ce = se, sc = se, cc = se;  // paired accumulators: elements 0, 1
     int i = 0;
-    // groups of UPD_G basis vectors: 2 UPD_G 16-byte loads in flight per thread
-    // (about two CTAs per SM, so registers are not the limit)
+    // groups of UPD_G basis vectors: 2 UPD_G 8-byte loads in flight per thread
     constexpr int UPD_G = 8;
     for (; i + UPD_G <= j; i += UPD_G) {
-      float4 a[UPD_G], b[UPD_G];
+      float2 a[UPD_G], b[UPD_G];
 #pragma unroll
       for (int u = 0; u < UPD_G; ++u) {
-        a[u] = reinterpret_cast<const float4*>(Vh + (int64_t)(i + u) * ldv)[q];
-        b[u] = lo_load<B6>(Vl, (int64_t)(i + u) * ldv, q);
+        a[u] = reinterpret_cast<const float2*>(Vh + (int64_t)(i + u) * ldv)[q];
+        b[u] = lo2((int64_t)(i + u) * ldv, q);
       }
 #pragma unroll
       for (int u = 0; u < UPD_G; ++u) {
         const float2 h1 = make_float2(eh[i + u], eh[i + u]), l1 = make_float2(el[i + u], el[i + u]);
         const float2 h2 = make_float2(ch[i + u], ch[i + u]), l2 = make_float2(cl[i + u], cl[i + u]);
-        const float2 a0 = make_float2(a[u].x, a[u].y), a1 = make_float2(a[u].z, a[u].w);
-        const float2 b0 = make_float2(b[u].x, b[u].y), b1 = make_float2(b[u].z, b[u].w);
-        df_mac2(se[0], ce[0], h1, l1, a0, b0);
-        df_mac2(se[1], ce[1], h1, l1, a1, b1);
-        df_mac2(sc[0], cc[0], h2, l2, a0, b0);
-        df_mac2(sc[1], cc[1], h2, l2, a1, b1);
+        df_mac2(se, ce, h1, l1, a[u], b[u]);
+        df_mac2(sc, cc, h2, l2, a[u], b[u]);
       }
     }
     for (; i < j; ++i) {
-      const float4 a = reinterpret_cast<const float4*>(Vh + (int64_t)i * ldv)[q];
-      const float4 b = lo_load<B6>(Vl, (int64_t)i * ldv, q);
+      const float2 a = reinterpret_cast<const float2*>(Vh + (int64_t)i * ldv)[q];
+      const float2 b = lo2((int64_t)i * ldv, q);
       const float2 h1 = make_float2(eh[i], eh[i]), l1 = make_float2(el[i], el[i]);
       const float2 h2 = make_float2(ch[i], ch[i]), l2 = make_float2(cl[i], cl[i]);
-      const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
-      const float2 b0 = make_float2(b.x, b.y), b1 = make_float2(b.z, b.w);
-      df_mac2(se[0], ce[0], h1, l1, a0, b0);
-      df_mac2(se[1], ce[1], h1, l1, a1, b1);
-      df_mac2(sc[0], cc[0], h2, l2, a0, b0);
-      df_mac2(sc[1], cc[1], h2, l2, a1, b1);
+      df_mac2(se, ce, h1, l1, a, b);
+      df_mac2(sc, cc, h2, l2, a, b);
     }
-    const float se_s[4] = {se[0].x, se[0].y, se[1].x, se[1].y}, ce_s[4] = {ce[0].x, ce[0].y, ce[1].x, ce[1].y};
-    const float sc_s[4] = {sc[0].x, sc[0].y, sc[1].x, sc[1].y}, cc_s[4] = {cc[0].x, cc[0].y, cc[1].x, cc[1].y};
-    const float4 uh = reinterpret_cast<const float4*>(qh)[q];
-    const float4 ul = lo_load<B6>(Vl, (int64_t)j * ldv, q);
-    const float uhs[4] = {uh.x, uh.y, uh.z, uh.w}, uls[4] = {ul.x, ul.y, ul.z, ul.w};
-    float oqh[4], oql[4], onh[4], onl[4];
+    const float se_s[2] = {se.x, se.y}, ce_s[2] = {ce.x, ce.y};
+    const float sc_s[2] = {sc.x, sc.y}, cc_s[2] = {cc.x, cc.y};
+    const float2 uh = reinterpret_cast<const float2*>(qh)[q];
+    const float2 ul = lo2((int64_t)j * ldv, q);
+    const float uhs[2] = {uh.x, uh.y}, uls[2] = {ul.x, ul.y};
+    float oqh[2], oql[2], onh[2], onl[2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t el_ = 4 * q + u;
+    for (int u = 0; u < 2; ++u) {
+      const int64_t el_ = 2 * q + u;
       const float2 uj = make_float2(uhs[u], uls[u]);
       float2 scs, ses;
       two_sum(sc_s[u], cc_s[u], scs.x, scs.y);
@@ -1348,10 +1357,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 16) gm_dc_update_kernel(float* Vh
       onh[u] = nd.x;
       onl[u] = nd.y;
     }
-    reinterpret_cast<float4*>(qh)[q] = make_float4(oqh[0], oqh[1], oqh[2], oqh[3]);
-    lo_store<B6>(Vl, (int64_t)j * ldv, q, make_float4(oql[0], oql[1], oql[2], oql[3]));
-    reinterpret_cast<float4*>(nh)[q] = make_float4(onh[0], onh[1], onh[2], onh[3]);
-    lo_store<B6>(Vl, (int64_t)(j + 1) * ldv, q, make_float4(onl[0], onl[1], onl[2], onl[3]));
+    reinterpret_cast<float2*>(qh)[q] = make_float2(oqh[0], oqh[1]);
+    lo2_store((int64_t)j * ldv, q, make_float2(oql[0], oql[1]));
+    reinterpret_cast<float2*>(nh)[q] = make_float2(onh[0], onh[1]);
+    lo2_store((int64_t)(j + 1) * ldv, q, make_float2(onl[0], onl[1]));
   }
 }
 void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, const double* c, const double* dc,
@@ -1361,8 +1370,28 @@ void gm_dc_update(float* Vh, float* Vl, int64_t ldv, int j, const double* e, con
   // with the 6-byte basis the passes move 6 B per basis entry
   int* ran = prof_begin(PROF_ORTH, (double)(j + 1) * n * 8.0 + 4.0 * n * 8.0, st,
                         b6 ? (double)(j + 1) * n * 6.0 + 2.0 * n * 6.0 + 2.0 * n * 8.0 : 0.0);
-  const int64_t n4 = (n + 3) / 4;
-  const int nb = (int)std::min<int64_t>((n4 + UPD_THREADS - 1) / UPD_THREADS, 152 * 64);
+  const int64_t n2 = (n + 1) / 2;
+  // one resident wave (at most 16 CTAs of 64 threads per SM at 64 registers;
+  // fewer once the 16 j bytes of coefficients per CTA limit them), the
+  // threads striding over the float2 positions; cached per 4 KB of
+  // coefficients (host threads may race to fill an entry, all with one value)
+  static std::atomic<int> resident[2][64];
+  const int key = (int)std::min<int64_t>(63, (int64_t)16 * j / 4096);
+  int res = resident[b6][key].load(std::memory_order_relaxed);
+  if (res == 0) {
+    int dev = 0, sms = 0, per = 0;
+    const size_t smem_key = (size_t)(key + 1) * 4096;  // at least the launch's coefficient bytes
+    WC4D_CUDA(cudaGetDevice(&dev));
+    WC4D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (b6)
+      WC4D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gm_dc_update_kernel<true>, UPD_THREADS, smem_key));
+    else
+      WC4D_CUDA(
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gm_dc_update_kernel<false>, UPD_THREADS, smem_key));
+    res = std::max(1, sms * std::max(per, 1));
+    resident[b6][key].store(res, std::memory_order_relaxed);
+  }
+  const int nb = (int)std::min<int64_t>((n2 + UPD_THREADS - 1) / UPD_THREADS, res);
   const size_t smem = sizeof(float) * 4 * std::max(j, 1);
   if (b6)
     WC4D_CUDA(launch_pdl(gm_dc_update_kernel<true>, dim3(nb), dim3(UPD_THREADS), smem, st, Vh, Vl, ldv, j, e, c, dc,
