@@ -285,8 +285,8 @@ GEMM_DF32_TRAFFIC_BYTES = 53.3e6
 # ratio x the live algorithmic bytes per launch.  Captured on a GB300 with
 # `bench.py --workload profile --maxit 110` (summaries and commands in profiles/).
 TRAFFIC_RATIO = {
-    "orth_b6": (0.9975, "ncu dram bytes of gm_dc_dot + gm_dc_update at Arnoldi step j = 99 with the 6-byte basis "
-                        "(412.3 MB) over the bytes they move (413.3 MB), profiles/gm_dc_arnoldi__advdiff_s2048_N64.md"),
+    "orth_b6": (0.9972, "ncu dram bytes of gm_dc_dot + gm_dc_update at Arnoldi step j = 99 with the 6-byte basis "
+                        "(412.2 MB) over the bytes they move (413.3 MB), profiles/gm_dc_arnoldi__advdiff_s2048_N64.md"),
 }
 
 
