@@ -377,7 +377,12 @@ template <bool FULL>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     gemm_tc_kernel(GemmOpsT<double> ops, const GemmSeg* __restrict__ segs, const int* __restrict__ seg_start,
                    float2* __restrict__ partial, const int* __restrict__ done, int* ran, int* err) {
-  pdl_wait();
+  // No pdl_wait here: the operator digit tiles (written at setup) stream in
+  // while the preceding X-digit kernel still runs; only what that kernel
+  // writes waits for it (the X digit copies in the copy warp, the scales and
+  // GEMV operands in the epilogue warps).  Every kernel before the X-digit
+  // kernel has completed (it triggers this launch after its own wait), so the
+  // convergence flag and the partial buffer are already safe to use.
   pdl_trigger();
   if (done != nullptr && *(volatile const int*)done) return;
   if (ran != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *ran = 1;
@@ -423,6 +428,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (lane == 0) {
       int it = 0;
       bool ok = true;
+      // the first OZ_STAGES fills: operator tiles at once, their X tiles once
+      // the X-digit kernel has finished (before any stage is waited on again)
+      bool waited = false;
+      uint32_t pend_dst[OZ_STAGES];
+      const uint16_t* pend_src[OZ_STAGES];
+      auto flush = [&]() {
+        pdl_wait();
+        for (int f = 0; f < min(it, OZ_STAGES); ++f)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  pend_dst[f]),
+              "l"(pend_src[f]), "r"(x_bytes), "r"(smem_u32(&full_bar[f]))
+              : "memory");
+        waited = true;
+      };
       for (int si = sbeg; si < send && ok; ++si) {
         const GemmSeg sg = segs[si];
         const GemmOpT<double>& op = ops.op[sg.op];
@@ -432,6 +452,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const uint16_t* xsrc = op.Xd + (int64_t)(sg.col0 / OZ_BN) * nkb * OZ_DIGITS * OZ_X_TILE;
         for (int kb = sg.k0 / OZ_BK; kb < (sg.k1 + OZ_BK - 1) / OZ_BK; ++kb, ++it) {
           const int s = it % OZ_STAGES;
+          if (!waited && it == OZ_STAGES) flush();
           if (it >= OZ_STAGES && !mbar_wait(&empty_bar[s], ((it / OZ_STAGES) - 1) & 1, &abort_flag, lim)) {
             give_up(&abort_flag, err, 1);
             ok = false;
@@ -445,12 +466,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dA),
               "l"(asrc + (int64_t)kb * OZ_DIGITS * OZ_A_TILE), "r"(a_bytes), "r"(smem_u32(&full_bar[s]))
               : "memory");
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dX),
-              "l"(xsrc + (int64_t)kb * OZ_DIGITS * OZ_X_TILE), "r"(x_bytes), "r"(smem_u32(&full_bar[s]))
-              : "memory");
+          if (waited) {
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dX),
+                "l"(xsrc + (int64_t)kb * OZ_DIGITS * OZ_X_TILE), "r"(x_bytes), "r"(smem_u32(&full_bar[s]))
+                : "memory");
+          } else {  // it < OZ_STAGES: stage it, issued by flush()
+            pend_dst[it] = dX;
+            pend_src[it] = xsrc + (int64_t)kb * OZ_DIGITS * OZ_X_TILE;
+          }
         }
       }
+      if (!waited) flush();  // fewer than OZ_STAGES fills, or a give-up before the first reuse
       // no copy may still be landing when the CTA exits: wait for the last fill
       // of every stage (already complete unless a wait above gave up)
       for (int f = max(0, it - OZ_STAGES); f < it; ++f) {
@@ -521,6 +548,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   } else {
     // ---- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of
     // the tile) and columns 32 (w / 4) .. + 31 of every level
+    pdl_wait();  // the GEMV operands and the X scales come from the X-digit kernel
     const int quarter = warp & 3, half = warp >> 2;
     int nseg = 0;
     for (int si = sbeg; si < send; ++si) {
