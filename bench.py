@@ -332,7 +332,7 @@ def kernel_rows(st, step_ms, hbm, dcgs=False):
                            "hbm": {"achieved_gbs": a_hbm, "frac": f_hbm,
                                    "bytes": "FP64 operator entries (their triangle) once, vectors once"},
                            "digit_form": {"achieved_gbs": a_dig, "frac": (a_dig / hbm) if hbm else None,
-                                          "bytes_per_launch": st.gemmtc_alg_bytes / st.gemmtc_launches,
+                                          "bytes_per_launch": st.gemmtc_bytes / st.gemmtc_launches,
                                           "bytes": "digit tiles (14 B per operator entry), GEMV operands, "
                                                    "vector digits, partial tiles: what the kernel moves"},
                            "tensor": {"achieved_tflops_bf16": a_tc, "frac": f_tc},

@@ -71,6 +71,7 @@ def test_tensor_core_row_takes_the_tighter_roof(monkeypatch):
     assert r["frac"] == pytest.approx(3000.0 / hbm)
     assert r["bytes_per_launch"] == pytest.approx(3e10)
     assert r["digit_form"]["frac"] == pytest.approx(5250.0 / hbm)
+    assert r["digit_form"]["bytes_per_launch"] == pytest.approx(5.25e10)
     assert r["tensor"]["frac"] == pytest.approx(400.0 / 1918.0)
     assert r["mma_flops_per_launch"] == pytest.approx(4e12)
     # flop-heavy launch: 1500 TF -> the tensor roof is the tighter one
