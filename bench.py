@@ -269,7 +269,8 @@ MODE_DESC = {"fp64": "plain FP64: native DFMA products, FP64 GMRES",
                            "P_I's D c1)",
              "ozaki_rinv_b6": "FP64 GMRES; multi-column covariance / factor products as exact BF16 digit products "
                               "on tcgen05; Rhat^-1 as one product with the explicit inverse W^T W; Arnoldi basis "
-                              "stored as FP32 high + BF16 low parts (6 B per entry, about 32 bits)",
+                              "stored as FP32 high + BF16 low parts (6 B per entry, about 32 bits); B's one-column "
+                              "products in double-float from its first row (B is symmetric Toeplitz)",
              "ozaki_fft_rinv_b6": "FP64 GMRES; circulant B, Q (and Bhat^-1, Qhat^-1) by double-float FFT (cluster-"
                                   "split four-step transform); R-family products as exact BF16 digit products on "
                                   "tcgen05 with the explicit Rhat^-1; 6-byte Arnoldi basis"}
@@ -425,6 +426,12 @@ def run_gpu(args):
         modes["ozaki_rinv_b6"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
                                                 maxit=args.maxit, precision="ozaki", check_every=ce,
                                                 rinv_explicit=True, basis_bytes=6)
+    # the same reading B's s x s entries for its one-column products (its first row otherwise: B is Toeplitz)
+    if args.modes and "ozaki_rinv_b6_dense" in args.modes.split(","):
+        modes["ozaki_rinv_b6_dense"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
+                                                      maxit=args.maxit, precision="ozaki", check_every=ce,
+                                                      rinv_explicit=True, basis_bytes=6,
+                                                      toeplitz_gemv=wc4d.WC4D_TOEPLITZ_OFF)
     if args.chosen == "ozaki_fft_rinv_b6" or (args.modes and "ozaki_fft_rinv_b6" in args.modes.split(",")):
         modes["ozaki_fft_rinv_b6"] = wc4d.make_opts(precond=args.precond, k=args.k, rhat=args.rhat, tol=1e-6,
                                                     maxit=args.maxit, precision="ozaki", check_every=ce,

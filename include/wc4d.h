@@ -120,6 +120,7 @@ enum { WC4D_COVPROD_DENSE = 0,    /* B, Q as dense s x s products; Dhat^-1 throu
                                      from their first columns.  A spectrum value <= 0 gives
                                      NOT_SPD.  R stays a dense product (the observed points are
                                      not a uniform grid).                                       */
+enum { WC4D_TOEPLITZ_AUTO = 0, WC4D_TOEPLITZ_OFF = 1 };  /* wc4d_solve_opts.toeplitz_gemv */
 enum { WC4D_PREC_FP64 = 0,        /* every product in native FP64 (DFMA)                       */
        WC4D_PREC_MIXED = 1,       /* FGMRES outer (FP64-accurate A) around an FP32 inner GMRES
                                      preconditioned by an FP32 copy of the chosen preconditioner
@@ -226,6 +227,15 @@ typedef struct {
                                 stored basis rounding bounds the attainable true residual near
                                 1e-9 relative: use 6 with tol >= 1e-7 (checked: WC4D_ERR_ARG
                                 otherwise).  Any other value is WC4D_ERR_ARG (not in the paper) */
+  int32_t toeplitz_gemv;     /* OZAKI: WC4D_TOEPLITZ_AUTO (0, the default) or WC4D_TOEPLITZ_OFF.
+                                AUTO: when B (Q) is symmetric Toeplitz -- every entry bitwise equal
+                                to its first row's entry at |i - j|, as the SOAR covariances of the
+                                periodic uniform grid (Sec. 6.1) that WC4D_COV_SOAR builds -- its
+                                one-column products (B on time level 0; Q on a single or a 65th
+                                column) read the split first row instead of the s x s entries: the
+                                same operand values in the same order, so bitwise the same result,
+                                from 8 s instead of 8 s^2 bytes.  Checked once at setup; any other
+                                operator, or OFF, reads the dense rows.  Other values: ARG       */
 } wc4d_solve_opts;
 
 typedef struct {

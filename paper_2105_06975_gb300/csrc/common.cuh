@@ -267,6 +267,14 @@ struct GemmOpT {
   const float* As = nullptr;
   uint16_t* Xd = nullptr;
   float* Xs = nullptr;
+  // a symmetric Toeplitz operator's one-column products (ozaki.cu): its split
+  // first row in four reflected copies, copy g holding entry |v - toff - g| at
+  // position v, so that row i reads its entries at copy (i % 4), offset
+  // toff + (i % 4) - i: contiguous, 16-byte aligned.  nullptr: the dense rows.
+  const float* Th = nullptr;
+  const float* Tl = nullptr;
+  int64_t tstride = 0;  // floats per copy (2 toff + 4)
+  int toff = 0;         // 4 ceil(kdim / 4)
 };
 template <typename T>
 struct GemmOpsT {
@@ -341,6 +349,8 @@ struct GemmPlan {
   double tc_digit_bytes = 0;      // the part of tc_bytes that is digit tiles (scales with the digits used)
   double alg_bytes = 0;           // each FP64 operator entry (its triangle) read once, X read once, C written
                                   // once: the floor of any product kernel, whatever its operand form
+  double alg_op_bytes[GEMM_MAX_OPS] = {};  // the operator part of alg_bytes, per op
+  double tc_gemv_op_bytes[GEMM_MAX_OPS] = {};  // tensor-core plan: GEMV operator rows read, per op
   std::shared_ptr<void> owner;    // keeps the device arrays alive (plans are shared through a cache)
 };
 

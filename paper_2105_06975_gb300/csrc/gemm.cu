@@ -115,7 +115,10 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
         Tile t{o, row0, c * cw, klo / GEMM_BK, (khi + GEMM_BK - 1) / GEMM_BK, cost, cols == 1};
         tiles.push_back(t);
         flops += 2.0 * rows * cols * (double)(khi - klo);
-        if (c == 0) plan.alg_bytes += 8.0 * rows * (double)(khi - klo);  // operator rows of this tile, once
+        if (c == 0) {  // operator rows of this tile, once
+          plan.alg_bytes += 8.0 * rows * (double)(khi - klo);
+          plan.alg_op_bytes[o] += 8.0 * rows * (double)(khi - klo);
+        }
       }
     }
   }
@@ -234,6 +237,7 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
         mma += (double)kbs * (OZ_DIGITS * (OZ_DIGITS + 1) / 2) * 2.0 * OZ_BM * OZ_BN * OZ_BK;
       } else {
         bytes += 8.0 * rows * (double)(sg.k1 - sg.k0) + 8.0 * (sg.k1 - sg.k0) + 8.0 * rows;
+        plan.tc_gemv_op_bytes[sg.op] += 8.0 * rows * (double)(sg.k1 - sg.k0);
       }
     }
     plan.tc_bytes = bytes + dbytes;
@@ -667,9 +671,18 @@ void launch_products<double>(const GemmPlan& plan, const GemmOpsT<double>& ops, 
   if (ops.tc) {
     // with nd of the 7 digits: the digit tiles' bytes and the digit products shrink
     const int nd = ops.ndig;
-    const double bytes = plan.tc_bytes - plan.tc_digit_bytes * (1.0 - nd / (double)OZ_DIGITS);
+    double bytes = plan.tc_bytes - plan.tc_digit_bytes * (1.0 - nd / (double)OZ_DIGITS);
     const double mma = plan.tc_mma_flops * (nd * (nd + 1) / 2) / (double)(OZ_DIGITS * (OZ_DIGITS + 1) / 2);
-    int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, bytes, mma, plan.alg_bytes);
+    double alg = plan.alg_bytes;
+    for (int o = 0; o < plan.nops; ++o) {
+      if (!ops.op[o].Th) continue;
+      // a Toeplitz operator's GEMV rows come from its first row: 8 B per k
+      // instead of 8 B per entry; with no wide tile that row is its floor too
+      const double row = 8.0 * plan.shape[o].kdim;
+      bytes += row - plan.tc_gemv_op_bytes[o];
+      if (oz_wide_tiles(plan.shape[o].ncols) == 0) alg += row - plan.alg_op_bytes[o];
+    }
+    int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, bytes, mma, alg);
     launch_gemm_tc(ops, plan.d_segs, plan.d_seg_start, plan.nctas, partial, done, ran, ops.err, st);
     if (ran) prof_end(st);
     return;

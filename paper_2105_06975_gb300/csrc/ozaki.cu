@@ -349,8 +349,18 @@ __device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float
 #pragma unroll
     for (int i = 0; i < OZ_GEMV_ROWS; ++i) {
       const int row = sg.row0 + base + 4 * i;
-      const int64_t o = (int64_t)min(row, op.m - 1) * op.lda;
-      load16(op.Ah + o, op.Al + o, kb, row < op.m ? sg.k1 : kb, vec, ah[i], al[i]);
+      const int rr = min(row, op.m - 1);
+      const int kend = row < op.m ? sg.k1 : kb;
+      if (op.Th) {
+        // symmetric Toeplitz operator: entry (rr, k) is the first row's entry
+        // |k - rr|, found at k in copy rr % 4 from offset toff + rr % 4 - rr
+        // (a multiple of 4 floats: 16-byte loads)
+        const int64_t o = (int64_t)(rr & 3) * op.tstride + op.toff + (rr & 3) - rr;
+        load16(op.Th + o, op.Tl + o, kb, kend, true, ah[i], al[i]);
+      } else {
+        const int64_t o = (int64_t)rr * op.lda;
+        load16(op.Ah + o, op.Al + o, kb, kend, vec, ah[i], al[i]);
+      }
     }
     float sv[OZ_GEMV_ROWS], cv[OZ_GEMV_ROWS];
 #pragma unroll
@@ -368,6 +378,29 @@ __device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float
         v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
       if (j == 0 && sg.row0 + base + 4 * i < op.m) dst[base + 4 * i] = v;
     }
+  }
+}
+
+// Setup of the Toeplitz one-column products: the bitwise check, and copy g of
+// the reflected first row, entry |v - toff - g| at position v (zero beyond the
+// row), so that row i's entries k lie at copy i % 4, position toff + i % 4 - i + k.
+__global__ void oz_toeplitz_check_kernel(const double* __restrict__ A, int64_t lda, int m, int* flag) {
+  for (int i = blockIdx.y; i < m; i += gridDim.y) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+      const int d = i > k ? i - k : k - i;
+      if (__double_as_longlong(A[(int64_t)i * lda + k]) != __double_as_longlong(A[d])) atomicExch(flag, 1);
+    }
+  }
+}
+__global__ void oz_toeplitz_rows_kernel(const float* __restrict__ Ah, const float* __restrict__ Al, int m, int toff,
+                                        int64_t tstride, float* __restrict__ Th, float* __restrict__ Tl) {
+  const int64_t total = 4 * tstride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(e / tstride);
+    const int64_t v = e - g * tstride;
+    const int64_t d = v - toff - g >= 0 ? v - toff - g : toff + g - v;
+    Th[e] = d < m ? Ah[d] : 0.f;
+    Tl[e] = d < m ? Al[d] : 0.f;
   }
 }
 
@@ -655,6 +688,18 @@ void launch_oz_rows(const double* At, int64_t lda, int m, int kdim, uint16_t* Ad
   const int rt = (m + OZ_BM - 1) / OZ_BM, nkb = (kdim + OZ_BK - 1) / OZ_BK;
   if (rt == 0 || nkb == 0) return;
   oz_rows_kernel<<<rt * OZ_BM, 128, 0, st>>>(At, lda, m, kdim, nkb, Ad, As);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_oz_toeplitz(const double* At, int64_t lda, int m, const float* Ah, const float* Al, float* Th,
+                        float* Tl, int* flag, cudaStream_t st) {
+  if (m <= 0) return;
+  const dim3 grid((unsigned)std::min((m + 255) / 256, 8), (unsigned)std::min(m, 1024));
+  oz_toeplitz_check_kernel<<<grid, 256, 0, st>>>(At, lda, m, flag);
+  WC4D_LAUNCH_CHECK();
+  const int64_t total = 4 * oz_toeplitz_stride(m);
+  oz_toeplitz_rows_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 1024), 256, 0, st>>>(
+      Ah, Al, m, oz_toeplitz_off(m), oz_toeplitz_stride(m), Th, Tl);
   WC4D_LAUNCH_CHECK();
 }
 

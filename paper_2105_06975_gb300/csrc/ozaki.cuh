@@ -54,6 +54,18 @@ int64_t oz_x_elems(int kdim, int ncols);
 void launch_oz_rows(const double* At, int64_t lda, int m, int kdim, uint16_t* Ad, float* As, cudaStream_t st);
 // X digits of every op of one launch
 void launch_oz_cols(const OzColJobs& jobs, cudaStream_t st);
+// One-column products of a symmetric Toeplitz operator (every entry a function
+// of |i - k|, as the SOAR covariances of the periodic uniform grid): the GEMV
+// segments read the operator's split first row instead of its m x m entries,
+// the same values in the same order (GemmOpT::Th).  Layout of the row copies:
+inline int oz_toeplitz_off(int m) { return (m + 3) / 4 * 4; }
+inline int64_t oz_toeplitz_stride(int m) { return 2 * (int64_t)oz_toeplitz_off(m) + 4; }
+// setup: *flag (device) is set to 1 unless every entry At[i lda + k] of the
+// m x m operator is bitwise equal to At[|i - k|]; Th / Tl (4 oz_toeplitz_stride(m)
+// floats each) receive the copies of the first row of the split (Ah, Al),
+// to be used only if the flag stays 0
+void launch_oz_toeplitz(const double* At, int64_t lda, int m, const float* Ah, const float* Al, float* Th,
+                        float* Tl, int* flag, cudaStream_t st);
 // the tensor-core stream-K products of a plan built with COST_TC; err (device
 // int, may be NULL) receives a non-zero code if a wait gave up
 void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int* seg_start, int nctas,

@@ -76,6 +76,14 @@ struct OpSet {
       if (d.first == m) return d.second;
     return Digits{};
   }
+  // symmetric Toeplitz operators (B, Q): copies of the split first row that
+  // their one-column products read instead of the s x s split
+  std::vector<std::pair<const T*, Split>> toeps;
+  Split toep_of(const T* m) const {
+    for (auto& t : toeps)
+      if (t.first == m) return t.second;
+    return Split{};
+  }
   uint16_t* xd = nullptr;
   int64_t xdcap = 0;
   float* xs = nullptr;
@@ -134,6 +142,13 @@ struct OpSet {
           op.Xh = jb.Xgh;
           op.Xl = jb.Xgl;
           goff += 2 * ge;
+          const Split tp = toep_of(op.At);
+          if (tp.h && op.lda == op.m && op.kdim == op.m && op.tri == TRI_FULL) {
+            op.Th = tp.h;
+            op.Tl = tp.l;
+            op.toff = oz_toeplitz_off(op.m);
+            op.tstride = oz_toeplitz_stride(op.m);
+          }
         }
         jobs.cta_base[jobs.n] = ctas;
         ++jobs.n;
@@ -190,6 +205,8 @@ namespace wc4d {
 // list: cudaMallocHost / cudaFreeHost per problem cost more than a setup's
 // kernels and cudaFreeHost synchronises the device.
 constexpr size_t PINNED_BLOCK = 256;
+constexpr int SETUP_FLAGS = 19;  // setup flag slots (device ints), read back through one pinned block
+static_assert(sizeof(int) * SETUP_FLAGS <= PINNED_BLOCK, "setup flags exceed the pinned block");
 inline std::mutex& pinned_mu() {
   static std::mutex m;
   return m;
@@ -317,6 +334,12 @@ struct wc4d_problem {
     bool spectrum = false;  // a circulant spectrum check instead of a Cholesky pivot
   };
   std::vector<CholCheck> chol_checks;
+  struct ToepCheck {  // Toeplitz row copies of B or Q, registered if the check's slot stays 0
+    const double* op;
+    Split rows;
+    int slot;
+  };
+  std::vector<ToepCheck> toep_checks;
   std::vector<void*> allocs;
 
   // Stream-ordered allocation from the device's default pool, which keeps up to
@@ -1161,6 +1184,8 @@ static void validate(const wc4d_problem_desc* d, const wc4d_solve_opts* o) {
              WC4D_ERR_ARG, "basis_bytes 6 needs GMRES with precision DF32, DF32_P32 or OZAKI");
   WC4D_CHECK(o->basis_bytes != 6 || o->tol >= 1e-7, WC4D_ERR_ARG,
              "basis_bytes 6 bounds the true residual near 1e-9: needs tol >= 1e-7");
+  WC4D_CHECK(o->toeplitz_gemv == WC4D_TOEPLITZ_AUTO || o->toeplitz_gemv == WC4D_TOEPLITZ_OFF, WC4D_ERR_ARG,
+             "toeplitz_gemv must be WC4D_TOEPLITZ_AUTO (0) or WC4D_TOEPLITZ_OFF (1)");
   WC4D_CHECK(!o->rinv_explicit || (d->p_t == nullptr && o->precision != WC4D_PREC_MIXED &&
                                    o->precision != WC4D_PREC_DF32_P32 && o->shat != WC4D_SHAT_EXACT),
              WC4D_ERR_ARG,
@@ -1200,11 +1225,13 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->n = 2 * P->ns + P->np;
   cudaStream_t st = P->st;
   // flag slots: 0 observation indices, 1 non-finite inputs, 2 R reconditioning,
-  // 4.. one per Cholesky factorisation (read once at the end of setup)
-  int* d_flag = P->alloc<int>(17);
+  // 3 circulant check, 4..15 one per Cholesky factorisation, 16 the tensor-core
+  // kernel's give-up code, 17 / 18 the Toeplitz checks of B / Q (the setup
+  // slots are read once at the end of setup)
+  int* d_flag = P->alloc<int>(SETUP_FLAGS);
   P->d_flags = d_flag;
   P->d_kerr = d_flag + 16;
-  WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * 17, st));
+  WC4D_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int) * SETUP_FLAGS, st));
   // observation operator (the inverse map indexes by obs_idx: checked before it runs)
   P->d_obs = P->alloc<int>(p);
   P->d_inv = P->alloc<int>(P->pertime ? (int64_t)(N + 1) * s : s);
@@ -1614,6 +1641,21 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       dig(f.WR, p);
       dig(f.WRt, p);
     }
+    if (!P->circ && !P->band && o->toeplitz_gemv == WC4D_TOEPLITZ_AUTO) {
+      // one-column products of B and Q from their first row when they are
+      // symmetric Toeplitz (checked bitwise; registered at the end of setup)
+      auto toep = [&](const double* m, int slot) {
+        const Split sp = f.split_of(m);
+        if (!m || !sp.h) return;
+        const int64_t cnt = 4 * oz_toeplitz_stride(s);
+        float* th = P->alloc<float>(cnt);
+        float* tl = P->alloc<float>(cnt);
+        launch_oz_toeplitz(m, s, s, sp.h, sp.l, th, tl, d_flag + slot, st);
+        P->toep_checks.push_back({m, Split{th, tl}, slot});
+      };
+      toep(f.B, 17);
+      toep(f.Q, 18);
+    }
     int64_t xe = 0, xsc = 0, xgc = 0;
     for (const GemmPlan* pl : plans) {
       int64_t e = 0, c = 0, gg = 0;
@@ -1758,9 +1800,9 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   P->h_scal = (double*)pinned_get();
   // the deferred checks: non-finite inputs, then each factorisation's pivots
   int* hf = (int*)pinned_get();
-  WC4D_CUDA(cudaMemcpyAsync(hf, d_flag, sizeof(int) * 16, cudaMemcpyDeviceToHost, st));
+  WC4D_CUDA(cudaMemcpyAsync(hf, d_flag, sizeof(int) * SETUP_FLAGS, cudaMemcpyDeviceToHost, st));
   WC4D_CUDA(cudaStreamSynchronize(st));
-  int hflags[16];
+  int hflags[SETUP_FLAGS];
   std::memcpy(hflags, hf, sizeof hflags);
   pinned_put(hf);
   WC4D_CHECK(hflags[1] == 0, WC4D_ERR_NONFINITE, "non-finite entries in the model or covariance inputs");
@@ -1776,6 +1818,8 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       throw Error{WC4D_ERR_NOT_SPD, buf};
     }
   }
+  for (const auto& tc : P->toep_checks)
+    if (hflags[tc.slot] == 0) P->f64.toeps.push_back({tc.op, tc.rows});
 }
 
 // ------------------------------------------------------------------ solves

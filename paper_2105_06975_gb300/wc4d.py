@@ -62,6 +62,8 @@ WC4D_PREC_DF32_P32 = 3
 WC4D_PREC_OZAKI = 4
 WC4D_COVPROD_DENSE = 0
 WC4D_COVPROD_FFT = 1
+WC4D_TOEPLITZ_AUTO = 0
+WC4D_TOEPLITZ_OFF = 1
 
 RHAT = {"exact": WC4D_RHAT_EXACT, "rr": WC4D_RHAT_RR, "me": WC4D_RHAT_ME, "diag": WC4D_RHAT_DIAG,
         "block": WC4D_RHAT_BLOCK}
@@ -93,7 +95,7 @@ class SolveOpts(ctypes.Structure):
                 ("rblock_sizes", ctypes.POINTER(ctypes.c_int32)), ("rblock_tol", ctypes.c_double),
                 ("rblock_maxsize", ctypes.c_int32), ("rblock_numproc", ctypes.c_int32),
                 ("covprod", ctypes.c_int32), ("prec_digits", ctypes.c_int32), ("rinv_explicit", ctypes.c_int32),
-                ("basis_bytes", ctypes.c_int32)]
+                ("basis_bytes", ctypes.c_int32), ("toeplitz_gemv", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -404,7 +406,8 @@ def wc4d_last_error() -> str:
 # -------------------------------------------------------------- convenience
 def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dhat="exact", dhat_delta=0.01,
               krylov=None, tol=1e-6, maxit=1000, precision="fp64", inner_iters=20, check_every=4, lhat="lm",
-              rblock=None, covprod="dense", prec_digits=0, rinv_explicit=False, basis_bytes=0) -> SolveOpts:
+              rblock=None, covprod="dense", prec_digits=0, rinv_explicit=False, basis_bytes=0,
+              toeplitz_gemv=WC4D_TOEPLITZ_AUTO) -> SolveOpts:
     """``rblock`` = (channel block sizes, tol, maxsize, numproc) for rhat="block"
     (Alg. 3; maxsize / numproc None or 0 switch their rule off)."""
     o = wc4d_default_opts()
@@ -438,6 +441,7 @@ def make_opts(precond="PI", k=1, rhat="exact", kappa_max=100.0, shat="paper", dh
     o.prec_digits = int(prec_digits)
     o.rinv_explicit = int(bool(rinv_explicit))
     o.basis_bytes = int(basis_bytes)
+    o.toeplitz_gemv = int(toeplitz_gemv)
     return o
 
 

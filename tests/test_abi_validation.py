@@ -205,3 +205,11 @@ def test_basis_bytes_checks(lib, basis, kw, needle):
     args.update(kw)
     o = L.make_opts(basis_bytes=basis, **args)
     refused(lib, d, o, needle)
+
+
+def test_toeplitz_gemv_checks(lib):
+    """toeplitz_gemv takes WC4D_TOEPLITZ_AUTO (0) or WC4D_TOEPLITZ_OFF (1)."""
+    d, _ = base()
+    for bad in (2, -1):
+        o = L.make_opts(precond="PI", k=1, precision="ozaki", toeplitz_gemv=bad)
+        refused(lib, d, o, "toeplitz_gemv must be")
