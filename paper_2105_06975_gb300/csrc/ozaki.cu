@@ -362,17 +362,23 @@ __device__ void gemv_segment(const GemmOpT<double>& op, const GemmSeg& sg, float
         load16(op.Ah + o, op.Al + o, kb, kend, vec, ah[i], al[i]);
       }
     }
-    float sv[OZ_GEMV_ROWS], cv[OZ_GEMV_ROWS];
+    // paired accumulators (even k, odd k of the lane's 16): one FFMA2 / FADD2
+    // multiply-add serves two entries, half the issue slots of the scalar form
+    float2 sv[OZ_GEMV_ROWS], cv[OZ_GEMV_ROWS];
 #pragma unroll
-    for (int i = 0; i < OZ_GEMV_ROWS; ++i) sv[i] = cv[i] = 0.f;
+    for (int i = 0; i < OZ_GEMV_ROWS; ++i) sv[i] = cv[i] = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
+    for (int q = 0; q < 16; q += 2)
 #pragma unroll
-      for (int i = 0; i < OZ_GEMV_ROWS; ++i) df_mac(sv[i], cv[i], ah[i][q], al[i][q], xh[q], xl[q]);
+      for (int i = 0; i < OZ_GEMV_ROWS; ++i)
+        df_mac2(sv[i], cv[i], make_float2(ah[i][q], ah[i][q + 1]), make_float2(al[i][q], al[i][q + 1]),
+                make_float2(xh[q], xh[q + 1]), make_float2(xl[q], xl[q + 1]));
 #pragma unroll
     for (int i = 0; i < OZ_GEMV_ROWS; ++i) {
-      float2 v;
-      two_sum(sv[i], cv[i], v.x, v.y);
+      float2 ev, od;
+      two_sum(sv[i].x, cv[i].x, ev.x, ev.y);
+      two_sum(sv[i].y, cv[i].y, od.x, od.y);
+      float2 v = df_add(ev, od);
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1)
         v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
