@@ -275,6 +275,11 @@ struct GemmOpT {
   const float* Tl = nullptr;
   int64_t tstride = 0;  // floats per copy (2 toff + 4)
   int toff = 0;         // 4 ceil(kdim / 4)
+  // the same operator's digit tiles (ozaki.cu): tile (R, K) equals the tile
+  // of the same offset 128 R - 16 K in row tile 0 or in the first 8 blocks of
+  // a row tile, so only those (their union: 8 (rows/128 - 1) + kdim/16
+  // tiles) are read; 0: every tile from its own place
+  int toep_tiles = 0;
 };
 template <typename T>
 struct GemmOpsT {
@@ -351,6 +356,7 @@ struct GemmPlan {
                                   // once: the floor of any product kernel, whatever its operand form
   double alg_op_bytes[GEMM_MAX_OPS] = {};  // the operator part of alg_bytes, per op
   double tc_gemv_op_bytes[GEMM_MAX_OPS] = {};  // tensor-core plan: GEMV operator rows read, per op
+  double tc_digit_op_bytes[GEMM_MAX_OPS] = {};  // tensor-core plan: operator digit tiles read, per op
   std::shared_ptr<void> owner;    // keeps the device arrays alive (plans are shared through a cache)
 };
 

@@ -233,6 +233,7 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
       const int kbs = (sg.k1 + OZ_BK - 1) / OZ_BK - sg.k0 / OZ_BK;
       if (cols >= 2) {
         dbytes += (double)kbs * 2.0 * OZ_DIGITS * OZ_A_TILE;
+        plan.tc_digit_op_bytes[sg.op] += (double)kbs * 2.0 * OZ_DIGITS * OZ_A_TILE;
         bytes += 8.0 * rows * cols;
         mma += (double)kbs * (OZ_DIGITS * (OZ_DIGITS + 1) / 2) * 2.0 * OZ_BM * OZ_BN * OZ_BK;
       } else {
@@ -675,12 +676,23 @@ void launch_products<double>(const GemmPlan& plan, const GemmOpsT<double>& ops, 
     const double mma = plan.tc_mma_flops * (nd * (nd + 1) / 2) / (double)(OZ_DIGITS * (OZ_DIGITS + 1) / 2);
     double alg = plan.alg_bytes;
     for (int o = 0; o < plan.nops; ++o) {
-      if (!ops.op[o].Th) continue;
+      const GemmOpT<double>& op = ops.op[o];
+      const OpShape& sh = plan.shape[o];
+      const bool wide = oz_wide_tiles(sh.ncols) > 0, gemv = oz_gemv_col(sh.ncols) >= 0;
       // a Toeplitz operator's GEMV rows come from its first row: 8 B per k
-      // instead of 8 B per entry; with no wide tile that row is its floor too
-      const double row = 8.0 * plan.shape[o].kdim;
-      bytes += row - plan.tc_gemv_op_bytes[o];
-      if (oz_wide_tiles(plan.shape[o].ncols) == 0) alg += row - plan.alg_op_bytes[o];
+      // instead of 8 B per entry
+      const double row = 8.0 * sh.kdim;
+      if (op.Th) bytes += row - plan.tc_gemv_op_bytes[o];
+      // its shared digit tiles: each distinct tile once, the rest L2 re-reads
+      if (op.toep_tiles) {
+        const int64_t nkb = (sh.kdim + OZ_BK - 1) / OZ_BK, rt = (sh.m + OZ_BM - 1) / OZ_BM;
+        const double distinct = (double)std::min<int64_t>(rt * nkb, nkb + (OZ_BM / OZ_BK) * (rt - 1));
+        bytes -= (plan.tc_digit_op_bytes[o] - distinct * 2.0 * OZ_DIGITS * OZ_A_TILE) * (nd / (double)OZ_DIGITS);
+      }
+      // with every tile of the op served from the first row or the shared
+      // tiles, the row is the op's floor too
+      if ((op.Th || !gemv) && (op.toep_tiles || !wide) && (op.Th || op.toep_tiles))
+        alg += row - plan.alg_op_bytes[o];
     }
     int* ran = prof_begin(PROF_GEMMTC, plan.flops, st, bytes, mma, alg);
     launch_gemm_tc(ops, plan.d_segs, plan.d_seg_start, plan.nctas, partial, done, ran, ops.err, st);

@@ -398,6 +398,25 @@ __global__ void oz_toeplitz_check_kernel(const double* __restrict__ A, int64_t l
     }
   }
 }
+// every digit tile (R, K) of the operator (rt row tiles, nkb blocks) against
+// the tile of its offset 128 R - 16 K that the product kernel reads instead:
+// one CTA per tile, *flag set on any difference
+__global__ void __launch_bounds__(256) oz_toeplitz_tiles_check_kernel(const uint16_t* __restrict__ Ad, int rt,
+                                                                      int nkb, int* flag) {
+  constexpr int QB = OZ_BM / OZ_BK;
+  constexpr int W = OZ_DIGITS * OZ_A_TILE / 8;  // 16-byte words per tile
+  for (int64_t t = blockIdx.x; t < (int64_t)rt * nkb; t += gridDim.x) {
+    const int R = (int)(t / nkb), K = (int)(t % nkb);
+    const int64_t rep = K >= QB * R ? (int64_t)(K - QB * R) : (int64_t)(R - K / QB) * nkb + K % QB;
+    if (rep == t) continue;
+    const uint4* a = reinterpret_cast<const uint4*>(Ad + t * OZ_DIGITS * OZ_A_TILE);
+    const uint4* b = reinterpret_cast<const uint4*>(Ad + rep * OZ_DIGITS * OZ_A_TILE);
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+      const uint4 x = a[w], y = b[w];
+      if (x.x != y.x || x.y != y.y || x.z != y.z || x.w != y.w) atomicExch(flag, 1);
+    }
+  }
+}
 __global__ void oz_toeplitz_rows_kernel(const float* __restrict__ Ah, const float* __restrict__ Al, int m, int toff,
                                         int64_t tstride, float* __restrict__ Th, float* __restrict__ Tl) {
   const int64_t total = 4 * tstride;
@@ -487,7 +506,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const GemmOpT<double>& op = ops.op[sg.op];
         if (min(sg.colw, op.ncols - sg.col0) < 2) continue;
         const int nkb = (op.kdim + OZ_BK - 1) / OZ_BK;
-        const uint16_t* asrc = op.Ad + (int64_t)(sg.row0 / OZ_BM) * nkb * OZ_DIGITS * OZ_A_TILE;
+        const int rtile = sg.row0 / OZ_BM;
+        const uint16_t* asrc = op.Ad + (int64_t)rtile * nkb * OZ_DIGITS * OZ_A_TILE;
         const uint16_t* xsrc = op.Xd + (int64_t)(sg.col0 / OZ_BN) * nkb * OZ_DIGITS * OZ_X_TILE;
         for (int kb = sg.k0 / OZ_BK; kb < (sg.k1 + OZ_BK - 1) / OZ_BK; ++kb, ++it) {
           const int s = it % OZ_STAGES;
@@ -501,9 +521,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full_bar[s])),
                        "r"(a_bytes + x_bytes)
                        : "memory");
+          // a Toeplitz operator's tile (R, kb) is the tile of the same offset
+          // 128 R - 16 kb in row tile 0 (kb >= 8 R) or in blocks 0..7 of row
+          // tile R - kb / 8 (setup checked every tile against it bitwise)
+          constexpr int QB = OZ_BM / OZ_BK;
+          const uint16_t* at = !op.toep_tiles ? asrc + (int64_t)kb * OZ_DIGITS * OZ_A_TILE
+                               : kb >= QB * rtile
+                                   ? op.Ad + (int64_t)(kb - QB * rtile) * OZ_DIGITS * OZ_A_TILE
+                                   : op.Ad + ((int64_t)(rtile - kb / QB) * nkb + kb % QB) * OZ_DIGITS * OZ_A_TILE;
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dA),
-              "l"(asrc + (int64_t)kb * OZ_DIGITS * OZ_A_TILE), "r"(a_bytes), "r"(smem_u32(&full_bar[s]))
+              "l"(at), "r"(a_bytes), "r"(smem_u32(&full_bar[s]))
               : "memory");
           if (waited) {
             asm volatile(
@@ -706,6 +734,13 @@ void launch_oz_toeplitz(const double* At, int64_t lda, int m, const float* Ah, c
   const int64_t total = 4 * oz_toeplitz_stride(m);
   oz_toeplitz_rows_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 1024), 256, 0, st>>>(
       Ah, Al, m, oz_toeplitz_off(m), oz_toeplitz_stride(m), Th, Tl);
+  WC4D_LAUNCH_CHECK();
+}
+
+void launch_oz_toeplitz_tiles(const uint16_t* Ad, int m, int kdim, int* flag, cudaStream_t st) {
+  const int rt = (m + OZ_BM - 1) / OZ_BM, nkb = (kdim + OZ_BK - 1) / OZ_BK;
+  if (rt <= 0 || nkb <= 0) return;
+  oz_toeplitz_tiles_check_kernel<<<(unsigned)std::min(rt * nkb, 152 * 8), 256, 0, st>>>(Ad, rt, nkb, flag);
   WC4D_LAUNCH_CHECK();
 }
 

@@ -66,6 +66,11 @@ inline int64_t oz_toeplitz_stride(int m) { return 2 * (int64_t)oz_toeplitz_off(m
 // to be used only if the flag stays 0
 void launch_oz_toeplitz(const double* At, int64_t lda, int m, const float* Ah, const float* Al, float* Th,
                         float* Tl, int* flag, cudaStream_t st);
+// setup: *flag (device) is set to 1 unless every digit tile (R, K) of the
+// operator's digit form (launch_oz_rows of an m x kdim operator) is bitwise
+// equal to the tile of the same offset 128 R - 16 K that the product kernel
+// then reads in its place (GemmOpT::toep_tiles)
+void launch_oz_toeplitz_tiles(const uint16_t* Ad, int m, int kdim, int* flag, cudaStream_t st);
 // the tensor-core stream-K products of a plan built with COST_TC; err (device
 // int, may be NULL) receives a non-zero code if a wait gave up
 void launch_gemm_tc(const GemmOpsT<double>& ops, const GemmSeg* segs, const int* seg_start, int nctas,

@@ -84,6 +84,8 @@ struct OpSet {
       if (t.first == m) return t.second;
     return Split{};
   }
+  std::vector<const T*> toep_tiled;  // operators whose digit tiles are shared by offset
+  bool tiles_shared(const T* m) const { return std::find(toep_tiled.begin(), toep_tiled.end(), m) != toep_tiled.end(); }
   uint16_t* xd = nullptr;
   int64_t xdcap = 0;
   float* xs = nullptr;
@@ -123,6 +125,7 @@ struct OpSet {
           if (!dg.d) throw Error{WC4D_ERR_ARG, "internal: no digit form for a tensor-core operator"};
           op.Ad = dg.d;
           op.As = dg.s;
+          op.toep_tiles = (tiles_shared(op.At) && op.lda == op.m && op.kdim == op.m && op.tri == TRI_FULL) ? 1 : 0;
           const int64_t xe = oz_x_elems(op.kdim, op.ncols);
           if (xoff + xe > xdcap || soff + (int64_t)wide * OZ_BN > xscap)
             throw Error{WC4D_ERR_ARG, "internal: digit operand buffer too small"};
@@ -205,7 +208,7 @@ namespace wc4d {
 // list: cudaMallocHost / cudaFreeHost per problem cost more than a setup's
 // kernels and cudaFreeHost synchronises the device.
 constexpr size_t PINNED_BLOCK = 256;
-constexpr int SETUP_FLAGS = 19;  // setup flag slots (device ints), read back through one pinned block
+constexpr int SETUP_FLAGS = 20;  // setup flag slots (device ints), read back through one pinned block
 static_assert(sizeof(int) * SETUP_FLAGS <= PINNED_BLOCK, "setup flags exceed the pinned block");
 inline std::mutex& pinned_mu() {
   static std::mutex m;
@@ -334,8 +337,8 @@ struct wc4d_problem {
     bool spectrum = false;  // a circulant spectrum check instead of a Cholesky pivot
   };
   std::vector<CholCheck> chol_checks;
-  struct ToepCheck {  // Toeplitz row copies of B or Q, registered if the check's slot stays 0
-    const double* op;
+  struct ToepCheck {  // Toeplitz row copies of B or Q (or Q's shared digit tiles: rows.h == nullptr),
+    const double* op;  // registered if the check's slot stays 0
     Split rows;
     int slot;
   };
@@ -1226,8 +1229,8 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
   cudaStream_t st = P->st;
   // flag slots: 0 observation indices, 1 non-finite inputs, 2 R reconditioning,
   // 3 circulant check, 4..15 one per Cholesky factorisation, 16 the tensor-core
-  // kernel's give-up code, 17 / 18 the Toeplitz checks of B / Q (the setup
-  // slots are read once at the end of setup)
+  // kernel's give-up code, 17 / 18 the Toeplitz checks of B / Q, 19 that of
+  // Q's digit tiles (the setup slots are read once at the end of setup)
   int* d_flag = P->alloc<int>(SETUP_FLAGS);
   P->d_flags = d_flag;
   P->d_kerr = d_flag + 16;
@@ -1655,6 +1658,13 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       };
       toep(f.B, 17);
       toep(f.Q, 18);
+      // Q's digit tiles (N >= 2): the product kernel reads one tile per
+      // offset 128 R - 16 K when every tile equals that one (checked bitwise)
+      const Digits dq = f.digits_of(f.Q);
+      if (f.Q && dq.d) {
+        launch_oz_toeplitz_tiles(dq.d, s, s, d_flag + 19, st);
+        P->toep_checks.push_back({f.Q, Split{}, 19});
+      }
     }
     int64_t xe = 0, xsc = 0, xgc = 0;
     for (const GemmPlan* pl : plans) {
@@ -1818,8 +1828,13 @@ static void setup(wc4d_problem* P, const wc4d_problem_desc* d, const wc4d_solve_
       throw Error{WC4D_ERR_NOT_SPD, buf};
     }
   }
-  for (const auto& tc : P->toep_checks)
-    if (hflags[tc.slot] == 0) P->f64.toeps.push_back({tc.op, tc.rows});
+  for (const auto& tc : P->toep_checks) {
+    if (hflags[tc.slot] != 0) continue;
+    if (tc.rows.h)
+      P->f64.toeps.push_back({tc.op, tc.rows});
+    else
+      P->f64.toep_tiled.push_back(tc.op);
+  }
 }
 
 // ------------------------------------------------------------------ solves

@@ -109,19 +109,22 @@ def test_ozaki_column_maxima_next_to_a_power_of_two():
     Z.close()
 
 
-@pytest.mark.parametrize("s,N,p,ops", [
-    (256, 64, 128, 1),   # B on one column; Q's 64 columns on the tensor cores
-    (203, 6, 77, 1),     # rows and k ragged (not multiples of 4, 16, 128)
-    (130, 1, 40, 2),     # N = 1: B and Q both on one column
+@pytest.mark.parametrize("s,N,p,gemv_ops,tiles", [
+    (256, 64, 128, 1, 1),   # B on one column; Q's 64 columns from its shared digit tiles
+    (203, 6, 77, 1, 0),     # rows and k ragged: Q's padded tiles are not shared
+    (130, 1, 40, 2, 0),     # N = 1: B and Q both on one column
 ])
-def test_toeplitz_one_column_products(s, N, p, ops):
+def test_toeplitz_products(s, N, p, gemv_ops, tiles):
     """The library's SOAR B and Q of the periodic grid are symmetric Toeplitz
-    (entry (i, k) a function of |i - k| only, Sec. 6.1): their one-column
-    products read the split first row (toeplitz_gemv AUTO, the default) and
-    must give bitwise the product of the dense rows (OFF), A v and P_I^-1 v
-    alike, with the launch's FP64 byte floor 8 (s^2 - s) lower per such
-    operator.  A B and Q perturbed off the Toeplitz structure (one interior
-    entry pair, 1e-12 relative) keep the dense rows under AUTO."""
+    (entry (i, k) a function of |i - k| only, Sec. 6.1).  Under toeplitz_gemv
+    AUTO (the default) their one-column products read the split first row,
+    and Q's tensor-core products read one digit tile per offset 128 R - 16 K
+    when every tile equals it (not with padded tiles); both must give bitwise
+    the products of the dense operator (OFF), A v and P_I^-1 v alike.  The
+    launch's FP64 byte floor counts the first row instead of the s^2 entries
+    of each such operator, and its digit-form bytes each shared tile once.  A
+    B and Q perturbed off the Toeplitz structure (one interior entry pair,
+    1e-12 relative) keep the dense path under AUTO."""
     w, dr = case(s, N, p, seed=5)
     prob = prb.linear_problem(w, dr)
     k = min(3, N + 1)
@@ -140,23 +143,26 @@ def test_toeplitz_one_column_products(s, N, p, ops):
             L.wc4d_set_profiling(False)
             G.close()
         assert st.gemmtc_launches == 1
-        return az, pz, st.gemmtc_alg_bytes
+        return az, pz, st.gemmtc_alg_bytes, st.gemmtc_bytes
 
-    az1, pz1, alg1 = run(L.WC4D_TOEPLITZ_AUTO)
-    az0, pz0, alg0 = run(L.WC4D_TOEPLITZ_OFF)
+    az1, pz1, alg1, by1 = run(L.WC4D_TOEPLITZ_AUTO)
+    az0, pz0, alg0, by0 = run(L.WC4D_TOEPLITZ_OFF)
     assert np.all(np.isfinite(az1))
     assert np.array_equal(az1, az0) and np.array_equal(pz1, pz0)
-    assert alg0 - alg1 == ops * 8.0 * (s * s - s)
+    assert alg0 - alg1 == (gemv_ops + tiles) * 8.0 * (s * s - s)
+    rt, nkb = -(-s // 128), -(-s // 16)
+    shared = tiles * (rt * nkb - min(rt * nkb, nkb + 8 * (rt - 1))) * 7 * 128 * 16 * 2
+    assert by0 - by1 == gemv_ops * 8.0 * (s * s - s) + shared
     assert rel(az1, prob.A_apply(v.cpu().numpy())) < 1e-11
     Bp, Qp = prob.B.copy(), prob.Q.copy()
     for M in (Bp, Qp):
         M[1, 2] *= 1.0 + 1e-12
         M[2, 1] = M[1, 2]
     dense = dict(B=Bp, Q=Qp, R=prob.R)
-    azp1, pzp1, algp1 = run(L.WC4D_TOEPLITZ_AUTO, **dense)
-    azp0, pzp0, algp0 = run(L.WC4D_TOEPLITZ_OFF, **dense)
+    azp1, pzp1, algp1, byp1 = run(L.WC4D_TOEPLITZ_AUTO, **dense)
+    azp0, pzp0, algp0, byp0 = run(L.WC4D_TOEPLITZ_OFF, **dense)
     assert np.array_equal(azp1, azp0) and np.array_equal(pzp1, pzp0)
-    assert algp1 == algp0 == alg0
+    assert algp1 == algp0 == alg0 and byp1 == byp0 == by0
 
 
 def test_ozaki_block_diagonal_preconditioner():
