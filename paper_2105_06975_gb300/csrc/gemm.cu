@@ -151,7 +151,13 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
     if (Wp <= 0) return;
     double cum = 0;
     int cur_cta = -1;
-    for (int ti = 0; ti < (int)tiles.size(); ++ti) {
+    // the tensor-core plan walks its GEMV tiles from the last op to the first:
+    // the ops listed last (the R family) then share no CTA between their GEMV
+    // rows and their digit tiles, both streamed from DRAM, while the first
+    // ops' (B, Q: first-row and shared-tile reads from L2) land beside them
+    const int nt = (int)tiles.size();
+    for (int tj = 0; tj < nt; ++tj) {
+      const int ti = (tc && pass == 0) ? nt - 1 - tj : tj;
       const Tile& t = tiles[ti];
       if (tc && (pass == 0) != t.gemv) continue;
       for (int kb = t.kb0; kb < t.kb1; ++kb) {
@@ -176,9 +182,45 @@ void plan_build(GemmPlan& plan, const std::vector<OpShape>& shapes, int max_ctas
       }
     }
   };
+  // Tensor-core tiles in whole-tile chunks: a CTA whose k-range crossed a
+  // tile boundary ran two accumulations in TMEM with a drain between them
+  // (the MMAs wait for it) and a second drain at its end, and set the
+  // launch's end.  Each tile t gets n_t chunks of near-equal k, with the
+  // smallest longest chunk for which sum n_t <= C and every chunk fits one
+  // exact segment; where no such split exists (more k per CTA than one
+  // segment holds), the cost walk above cuts across tiles as before.
+  auto assign_chunks = [&]() -> bool {
+    std::vector<int> wide;
+    int64_t longest = 0;
+    for (int ti = 0; ti < (int)tiles.size(); ++ti)
+      if (!tiles[ti].gemv) {
+        wide.push_back(ti);
+        longest = std::max<int64_t>(longest, tiles[ti].kb1 - tiles[ti].kb0);
+      }
+    if (wide.empty()) return true;
+    const int64_t cap = OZ_KMAX / GEMM_BK;
+    for (int64_t L = 1; L <= std::min(longest, cap); ++L) {
+      int64_t used = 0;
+      for (int ti : wide) used += (tiles[ti].kb1 - tiles[ti].kb0 + L - 1) / L;
+      if (used > C) continue;
+      int cta = 0;
+      for (int ti : wide) {
+        const Tile& t = tiles[ti];
+        const int64_t len = t.kb1 - t.kb0, n = (len + L - 1) / L;
+        for (int64_t q = 0; q < n; ++q, ++cta) {
+          const int64_t b0 = t.kb0 + len * q / n, b1 = t.kb0 + len * (q + 1) / n;
+          if (b1 <= b0) continue;
+          per_cta[cta].push_back(GemmSeg{t.op, t.row0, t.col0, (int)b0 * GEMM_BK,
+                                         std::min(shapes[t.op].kdim, (int)b1 * GEMM_BK), ti, plan.col_width[t.op]});
+        }
+      }
+      return true;
+    }
+    return false;
+  };
   assign(0);
   if (tc) {
-    assign(1);
+    if (!assign_chunks()) assign(1);
     // order of a CTA's list: g_0, T_0, g_1, T_1, ..., g_{n-1}, T_{n-1}, with the
     // GEMV segments g_i sized like the tensor-core segment T_i.  The epilogue
     // warps run g_i while the MMAs of T_i proceed, then drain T_i just before
