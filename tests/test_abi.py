@@ -88,3 +88,36 @@ def test_every_field_offset_matches_header():
     for cname, cls in structs.items():
         for fname, _ in cls._fields_:
             assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
+
+
+def header_enums():
+    """Every WC4D_* enumerator of include/wc4d.h with its value (implicit
+    values counted from the previous one, as C does)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    values = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, val = item.partition("=")
+            name = name.strip()
+            nxt = int(val.strip(), 0) if val.strip() else nxt
+            values[name] = nxt
+            nxt += 1
+    return values
+
+
+def test_binding_constants_match_header_enums():
+    """The Python binding's WC4D_* constants are the header's enumerators: a
+    value or a name drifting between the two would pass options the library
+    reads differently."""
+    from paper_2105_06975_gb300 import wc4d
+    enums = header_enums()
+    assert "WC4D_TOEPLITZ_OFF" in enums and "WC4D_PREC_OZAKI" in enums
+    py = {k: getattr(wc4d, k) for k in dir(wc4d) if k.startswith("WC4D_") and isinstance(getattr(wc4d, k), int)}
+    missing = sorted(set(enums) - set(py))
+    assert not missing, missing
+    for name, value in enums.items():
+        assert py[name] == value, (name, py[name], value)
